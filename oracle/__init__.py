@@ -1,0 +1,155 @@
+"""FP64 CPU oracle of the MBOIT puzzle-piece render (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg import this package.  The product library never does: it shares no code
+with the oracle.  The C source (``mboit_oracle.c``) is compiled with the host
+C compiler on first use (or by ``build()``) and called through ctypes.
+
+Functions that are "parity unpinned": none; every routine here is pinned by
+``tests/test_oracle_pins.py`` (closed forms, brute force, invariants).
+"""
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mboit_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libmboit_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+BIAS_VECTOR_POWER4 = (0.0, 0.375, 0.0, 0.375)
+
+
+class _View(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("u", ctypes.c_float * 3), ("v", ctypes.c_float * 3),
+                ("w", ctypes.c_float * 3), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("projection", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("scale_u", ctypes.c_float), ("scale_v", ctypes.c_float),
+                ("znear", ctypes.c_float), ("zfar", ctypes.c_float)]
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("field", ctypes.c_void_p), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("brick_log2", ctypes.c_int32),
+                ("piece_of_brick", ctypes.c_void_p), ("n_pieces", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("piece_selected", ctypes.c_void_p),
+                ("tf", ctypes.c_void_p), ("vmin", ctypes.c_double), ("vmax", ctypes.c_double),
+                ("step", ctypes.c_double), ("moment_bias", ctypes.c_double),
+                ("overestimation", ctypes.c_double), ("absorbance_max", ctypes.c_double),
+                ("bias_vector", ctypes.c_double * 4)]
+
+
+def build(force=False):
+    """Compile the oracle with the host C compiler (no FMA contraction)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mboit_oracle.h"))):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    subprocess.check_call(["cc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                           "-shared", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.orc_mboit_bound.restype = ctypes.c_double
+            lib.orc_mboit_bound.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+            lib.orc_log_warp.restype = ctypes.c_double
+            lib.orc_log_warp.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            lib.orc_render_grid.restype = ctypes.c_int
+            lib.orc_render_grid.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64] + \
+                [ctypes.c_void_p] * 8
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def mboit_bound(m, z0, moment_bias, overestimation, bias_vector=BIAS_VECTOR_POWER4):
+    """Alg. 3's absorbance fraction A(z0); returns (A, branch) with branch 0
+    generic, 1 one-atom, 2 two-atom."""
+    lib = _load()
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    bv = np.ascontiguousarray(bias_vector, dtype=np.float64)
+    fl = ctypes.c_int(0)
+    A = lib.orc_mboit_bound(m.ctypes.data, float(z0), float(moment_bias), bv.ctypes.data,
+                            float(overestimation), ctypes.byref(fl))
+    return A, fl.value
+
+
+def transmittance(m, z0, moment_bias, overestimation, bias_vector=BIAS_VECTOR_POWER4):
+    A, _ = mboit_bound(m, z0, moment_bias, overestimation, bias_vector)
+    return float(np.clip(np.exp(-m[0] * A), 0.0, 1.0))
+
+
+def log_warp(t, znear, zfar):
+    return _load().orc_log_warp(float(t), float(znear), float(zfar))
+
+
+def _view_struct(v):
+    s = _View()
+    for name in ("eye", "u", "v", "w"):
+        arr = np.asarray(getattr(v, name), dtype=np.float32)
+        getattr(s, name)[:] = [float(x) for x in arr]
+    s.width, s.height, s.projection = int(v.width), int(v.height), int(v.projection)
+    s.scale_u, s.scale_v = float(v.scale_u), float(v.scale_v)
+    s.znear, s.zfar = float(v.near), float(v.far)
+    return s
+
+
+def render_grid(scene, view=0, pixels=None, pieces=None, want=("mboit",)):
+    """Runs the oracle on the listed pixels (flat indices y*W + x; None = all).
+
+    `pieces`: iterable of selected piece ids (None = all).  `want` picks the
+    outputs among: moments, piece_moments, piece_color, mboit, raw, exact,
+    sortlast, nsamples.  Returns a dict of float64 arrays (nsamples int64).
+    """
+    lib = _load()
+    v = scene.views[view] if isinstance(view, int) else view
+    npx = v.width * v.height
+    pix = np.arange(npx, dtype=np.int64) if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
+    n = pix.size
+    K = scene.n_pieces
+    field = np.ascontiguousarray(scene.field, dtype=np.float32)
+    pob = np.ascontiguousarray(scene.piece_of_brick, dtype=np.int32)
+    tf = np.ascontiguousarray(scene.tf, dtype=np.float32)
+    sel = None
+    if pieces is not None:
+        sel = np.zeros(K, dtype=np.uint8)
+        sel[np.asarray(list(pieces), dtype=np.int64)] = 1
+    g = _Grid()
+    nx, ny, nz = scene.dims
+    g.field, g.nx, g.ny, g.nz, g.brick_log2 = field.ctypes.data, nx, ny, nz, scene.brick_log2
+    g.piece_of_brick, g.n_pieces = pob.ctypes.data, K
+    g.piece_selected = _ptr(sel)
+    g.tf = tf.ctypes.data
+    g.vmin, g.vmax = float(scene.tf_range[0]), float(scene.tf_range[1])
+    g.step = float(scene.step)
+    g.moment_bias, g.overestimation = float(scene.moment_bias), float(scene.overestimation)
+    g.absorbance_max = float(scene.absorbance_max)
+    g.bias_vector[:] = list(getattr(scene, "bias_vector", BIAS_VECTOR_POWER4))
+    shapes = {"moments": (n, 5), "piece_moments": (n, K, 5), "piece_color": (n, K, 4), "mboit": (n, 4),
+              "raw": (n, 4), "exact": (n, 4), "sortlast": (n, 4)}
+    out = {k: np.zeros(shapes[k]) for k in want if k in shapes}
+    if "nsamples" in want:
+        out["nsamples"] = np.zeros(n, dtype=np.int64)
+    vs = _view_struct(v)
+    rc = lib.orc_render_grid(ctypes.byref(g), ctypes.byref(vs), pix.ctypes.data, n,
+                             _ptr(out.get("moments")), _ptr(out.get("piece_moments")),
+                             _ptr(out.get("piece_color")), _ptr(out.get("mboit")), _ptr(out.get("raw")),
+                             _ptr(out.get("exact")), _ptr(out.get("sortlast")), _ptr(out.get("nsamples")))
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments")
+    return out

@@ -1,0 +1,438 @@
+/*
+ * FP64 CPU oracle of the two-pass MBOIT puzzle-piece render.
+ *
+ * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the
+ * benchmark's CPU baseline; the product library never links or calls it.
+ * Single-threaded, plain loops, one pixel at a time, in the order of the
+ * paper:
+ *   Alg. 1 (RenderMBOIT): loop 1 accumulates moments, loop 2 adds
+ *          getTransmittance(b, depth) * colour;
+ *   Alg. 2 (GeneratePowerMoments): warp depth, absorbance = -log(transmittance)
+ *          clamped, b_i += depth^i * absorbance;
+ *   Alg. 3 (getTransmittance): warp, mix with the bias vector, Cholesky of the
+ *          Hankel matrix, roots, weights (overestimation, indicators),
+ *          interpolating polynomial, absorbance = p . (1, b), exp;
+ *   Sec. 4.1: per-piece ("per-rank") moment images, summed (Allreduce add);
+ *   Sec. 4.2: per-piece colour images from the global moments, summed
+ *          (Reduce add).
+ * Readings where the paper is silent:
+ *   - sample lattice t_k = (k + 1/2) * step from the eye; rays and sample
+ *     positions are specified in float32 (correctly rounded ops in a fixed
+ *     order, positions by fmaf); everything after the position is FP64;
+ *   - a lattice point belongs to the piece owning the brick of its cell
+ *     (half-open cells; pieces never overlap, Sec. 6);
+ *   - transfer-function alpha is the opacity of one voxel of material,
+ *     sigma = -ln(1 - alpha); (r, g, b, sigma) interpolate linearly;
+ *     absorbance a = min(sigma * step, ABSORBANCE_MAX), opacity 1 - e^-a;
+ *   - the resolve renormalises: alpha = 1 - e^-b0 (zeroth moment), colour =
+ *     (sum T a c) / (sum T a) * alpha (the renormalisation of Sec. 4.3);
+ *   - singular Hankel matrices (one or two absorbers, zero bias) take the
+ *     one- or two-atom canonical measure;
+ *   - the exact reference blends the same samples front to back; the
+ *     sort-last route turns each contiguous per-piece run into a segment.
+ * Build: cc -O2 -std=c11 -ffp-contract=off -fPIC -shared (no FMA contraction
+ * so the float32 ray set-up rounds exactly as written).
+ */
+#include "mboit_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_TAU 1e-12
+
+/* ------------------------------------------------------------------------ */
+/* depth warp (Alg. 2, Alg. 3: "rescale logged depth value to [-1, 1]")     */
+
+double orc_log_warp(double t, double znear, double zfar)
+{
+    double z = 2.0 * (log(t) - log(znear)) / (log(zfar) - log(znear)) - 1.0;
+    if (z < -1.0) z = -1.0;
+    if (z > 1.0) z = 1.0;
+    return z;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 3                                                                    */
+
+/* Real roots of a*x^2 + b*x + c with the cancellation-free formula; the
+ * discriminant is clamped at zero.  Returns the number of finite roots. */
+static int quadratic_roots(double a, double b, double c, double* r1, double* r2)
+{
+    if (a == 0.0) {
+        if (b == 0.0) return 0;
+        *r1 = -c / b;
+        return 1;
+    }
+    double disc = b * b - 4.0 * a * c;
+    if (disc < 0.0) disc = 0.0;
+    double q = -0.5 * (b + copysign(sqrt(disc), b));
+    double x1 = q / a;
+    double x2 = (q != 0.0) ? c / q : x1;
+    if (x1 > x2) { double s = x1; x1 = x2; x2 = s; }
+    *r1 = x1;
+    *r2 = x2;
+    return 2;
+}
+
+static double step_weight(double x, double z0, double w0)
+{
+    if (x < z0) return 1.0;
+    if (x == z0) return w0;
+    return 0.0;
+}
+
+double orc_mboit_bound(const double m[5], double z0, double moment_bias,
+                       const double bias_vector[4], double overestimation, int* flags)
+{
+    if (flags) *flags = 0;
+    if (!(m[0] > 0.0)) return 0.0;
+
+    /* b_tmp = (b1..b4) / b0, then mix with the bias vector */
+    double b[5];
+    b[0] = 1.0;
+    for (int j = 1; j <= 4; ++j) {
+        double bj = m[j] / m[0];
+        b[j] = (1.0 - moment_bias) * bj + moment_bias * bias_vector[j - 1];
+    }
+
+    /* SolveMat: Hankel matrix B[i][j] = b[i+j] (i, j = 0..2) as L D L^T */
+    double D22 = b[2] - b[1] * b[1];
+    if (D22 <= ORC_TAU) {
+        /* single atom at b1 */
+        if (flags) *flags = 1;
+        return step_weight(b[1], z0, overestimation);
+    }
+    double L32 = (b[3] - b[1] * b[2]) / D22;
+    double D33 = b[4] - b[2] * b[2] - L32 * L32 * D22;
+    double scale = fabs(b[4]) > 1.0 ? fabs(b[4]) : 1.0;
+    if (D33 <= ORC_TAU * scale) {
+        /* two atoms: roots of x^2 + e1 x + e0 with
+         * [[1, b1], [b1, b2]] (e0, e1)^T = -(b2, b3)^T */
+        double det = b[2] - b[1] * b[1];
+        double e0 = (-b[2] * b[2] + b[1] * b[3]) / det;
+        double e1 = (-b[3] + b[1] * b[2]) / det;
+        double x1, x2;
+        if (quadratic_roots(1.0, e1, e0, &x1, &x2) != 2) return step_weight(b[1], z0, overestimation);
+        double rho2 = (x2 != x1) ? (b[1] - x1) / (x2 - x1) : 0.0;
+        double rho1 = 1.0 - rho2;
+        if (flags) *flags = 2;
+        return rho1 * step_weight(x1, z0, overestimation) + rho2 * step_weight(x2, z0, overestimation);
+    }
+
+    /* solve B q = (1, z0, z0^2): forward, diagonal, backward */
+    double y1 = 1.0;
+    double y2 = z0 - b[1] * y1;
+    double y3 = z0 * z0 - b[2] * y1 - L32 * y2;
+    y2 /= D22;
+    y3 /= D33;
+    double q2 = y3;
+    double q1 = y2 - L32 * q2;
+    double q0 = y1 - b[1] * q1 - b[2] * q2;
+
+    /* SolvePowerEquation: the other two support points, roots of
+     * q2 x^2 + q1 x + q0 */
+    double z[3];
+    z[0] = z0;
+    int nroot = quadratic_roots(q2, q1, q0, &z[1], &z[2]);
+
+    /* weights: overestimation at z0, indicator z_i < z0 elsewhere */
+    double w[3];
+    w[0] = overestimation;
+    w[1] = (z[1] < z0) ? 1.0 : 0.0;
+    w[2] = (nroot == 2 && z[2] < z0) ? 1.0 : 0.0;
+
+    /* solvePolynomial: Newton interpolation of the weights at the nodes,
+     * p(x) = w0 + f01 (x - z0) + f012 (x - z0)(x - z1), expanded */
+    double p0, p1, p2;
+    if (z[1] == z0) return w[0];  /* measure-zero: z0 is a support point */
+    double f01 = (w[1] - w[0]) / (z[1] - z0);
+    if (nroot == 2 && z[2] != z[1] && z[2] != z0) {
+        double f12 = (w[2] - w[1]) / (z[2] - z[1]);
+        double f012 = (f12 - f01) / (z[2] - z0);
+        p2 = f012;
+        p1 = f01 - f012 * (z0 + z[1]);
+        p0 = w[0] - f01 * z0 + f012 * z0 * z[1];
+    } else {
+        p2 = 0.0;
+        p1 = f01;
+        p0 = w[0] - f01 * z0;
+    }
+    /* absorbance = p . (1, b_tmp) */
+    return p0 + p1 * b[1] + p2 * b[2];
+}
+
+static double transmittance(const double m[5], double z0, const orc_grid* g)
+{
+    double A = orc_mboit_bound(m, z0, g->moment_bias, g->bias_vector, g->overestimation, NULL);
+    double T = exp(-m[0] * A);
+    if (T < 0.0) T = 0.0;
+    if (T > 1.0) T = 1.0;
+    return T;
+}
+
+/* ------------------------------------------------------------------------ */
+/* rays: float32, correctly rounded, in this exact order                     */
+
+static void make_ray(const orc_view* V, int64_t px, int64_t py, float o[3], float d[3])
+{
+    float fx = (float)px + 0.5f;
+    float fy = (float)py + 0.5f;
+    if (V->projection == 0) {
+        float sx = (fx / (float)V->width - 0.5f) * V->scale_u;
+        float sy = (fy / (float)V->height - 0.5f) * V->scale_v;
+        for (int c = 0; c < 3; ++c) {
+            o[c] = (V->eye[c] + sx * V->u[c]) + sy * V->v[c];
+            d[c] = V->w[c];
+        }
+    } else {
+        float sx = ((2.0f * fx) / (float)V->width - 1.0f) * V->scale_u;
+        float sy = ((2.0f * fy) / (float)V->height - 1.0f) * V->scale_v;
+        float dir[3];
+        for (int c = 0; c < 3; ++c) dir[c] = (V->w[c] + sx * V->u[c]) + sy * V->v[c];
+        float len = sqrtf((dir[0] * dir[0] + dir[1] * dir[1]) + dir[2] * dir[2]);
+        for (int c = 0; c < 3; ++c) {
+            o[c] = V->eye[c];
+            d[c] = dir[c] / len;
+        }
+    }
+}
+
+/* Lattice index range [k_lo, k_hi] that surely contains every lattice point
+ * whose float32 position is inside the domain (the position test decides). */
+static int lattice_range(const orc_grid* g, const float o[3], const float d[3], int64_t* k_lo, int64_t* k_hi)
+{
+    double hi[3] = {g->nx - 1.0, g->ny - 1.0, g->nz - 1.0};
+    double t0 = 0.0, t1 = INFINITY;
+    for (int c = 0; c < 3; ++c) {
+        if (d[c] == 0.0f) {
+            if (!(o[c] >= 0.0f && o[c] < (float)hi[c])) return 0;
+            continue;
+        }
+        double a = (0.0 - o[c]) / d[c], b = (hi[c] - o[c]) / d[c];
+        if (a > b) { double s = a; a = b; b = s; }
+        double pad = ldexp(fabs((double)o[c]) + hi[c] + 1.0, -20) / fabs((double)d[c]);
+        a -= pad;
+        b += pad;
+        if (a > t0) t0 = a;
+        if (b < t1) t1 = b;
+    }
+    if (!(t1 >= t0)) return 0;
+    double lo = ceil(t0 / g->step - 0.5) - 2.0, up = floor(t1 / g->step - 0.5) + 2.0;
+    if (lo < 0.0) lo = 0.0;
+    if (up < lo) return 0;
+    *k_lo = (int64_t)lo;
+    *k_hi = (int64_t)up;
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* one sample                                                                */
+
+typedef struct {
+    int64_t k;
+    int32_t piece;
+    double t, z, a, alpha, rgb[3];
+} sample_t;
+
+/* Classifies lattice point k; returns 1 and fills s if it is inside the
+ * domain and owned by a selected piece. */
+static int take_sample(const orc_grid* g, const orc_view* V, const float o[3], const float d[3],
+                       int64_t k, const double* sig_tab, sample_t* s)
+{
+    float t = ((float)k + 0.5f) * (float)g->step;
+    float p[3];
+    for (int c = 0; c < 3; ++c) p[c] = fmaf(t, d[c], o[c]);
+    const float hi[3] = {(float)(g->nx - 1), (float)(g->ny - 1), (float)(g->nz - 1)};
+    for (int c = 0; c < 3; ++c)
+        if (!(p[c] >= 0.0f && p[c] < hi[c])) return 0;
+    int cell[3];
+    for (int c = 0; c < 3; ++c) cell[c] = (int)floorf(p[c]);
+    int B = 1 << g->brick_log2;
+    int nbx = (g->nx - 1 + B - 1) / B, nby = (g->ny - 1 + B - 1) / B;
+    int brick = ((cell[2] >> g->brick_log2) * nby + (cell[1] >> g->brick_log2)) * nbx + (cell[0] >> g->brick_log2);
+    int piece = g->piece_of_brick[brick];
+    if (g->piece_selected && !g->piece_selected[piece]) return 0;
+
+    /* trilinear interpolation of the cell's 8 vertex values */
+    double fx = (double)p[0] - cell[0], fy = (double)p[1] - cell[1], fz = (double)p[2] - cell[2];
+    double val = 0.0;
+    for (int dz = 0; dz <= 1; ++dz)
+        for (int dy = 0; dy <= 1; ++dy)
+            for (int dx = 0; dx <= 1; ++dx) {
+                double wgt = (dx ? fx : 1.0 - fx) * (dy ? fy : 1.0 - fy) * (dz ? fz : 1.0 - fz);
+                int64_t idx = ((int64_t)(cell[2] + dz) * g->ny + (cell[1] + dy)) * g->nx + (cell[0] + dx);
+                val += wgt * (double)g->field[idx];
+            }
+
+    /* transfer function: normalise, 256-entry linear lookup of (r, g, b, sigma) */
+    double x = (val - g->vmin) / (g->vmax - g->vmin);
+    if (x < 0.0) x = 0.0;
+    if (x > 1.0) x = 1.0;
+    x *= 255.0;
+    int i = (int)floor(x);
+    if (i > 254) i = 254;
+    double f = x - i;
+    for (int c = 0; c < 3; ++c) s->rgb[c] = (1.0 - f) * g->tf[4 * i + c] + f * g->tf[4 * (i + 1) + c];
+    double sigma = (1.0 - f) * sig_tab[i] + f * sig_tab[i + 1];
+
+    /* Alg. 2: absorbance = -log(transmittance of the sample), clamped */
+    double a = sigma * g->step;
+    if (a > g->absorbance_max) a = g->absorbance_max;
+    s->k = k;
+    s->piece = piece;
+    s->t = (double)t;
+    s->z = orc_log_warp((double)t, V->znear, V->zfar);
+    s->a = a;
+    s->alpha = 1.0 - exp(-a);
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* one pixel                                                                 */
+
+int orc_render_grid(const orc_grid* g, const orc_view* V,
+                    const int64_t* pixels, int64_t n_pixels,
+                    double* moments, double* piece_moments, double* piece_color,
+                    double* mboit_rgba, double* raw_rgba, double* exact_rgba,
+                    double* sortlast_rgba, int64_t* nsamples)
+{
+    if (!g || !V || !g->field || !g->piece_of_brick || !g->tf || g->n_pieces <= 0) return -1;
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2 || !(g->step > 0.0) || !(g->vmax > g->vmin)) return -1;
+    const int K = g->n_pieces;
+
+    double sig_tab[256];
+    for (int j = 0; j < 256; ++j) sig_tab[j] = -log(1.0 - (double)g->tf[4 * j + 3]);
+
+    size_t cap = 1024;
+    sample_t* S = (sample_t*)malloc(cap * sizeof(sample_t));
+    double* mP = (double*)malloc((size_t)K * 5 * sizeof(double));
+    double* cP = (double*)malloc((size_t)K * 4 * sizeof(double));
+    if (!S || !mP || !cP) { free(S); free(mP); free(cP); return -1; }
+
+    for (int64_t n = 0; n < n_pixels; ++n) {
+        int64_t pix = pixels[n];
+        if (pix < 0 || pix >= (int64_t)V->width * V->height) { free(S); free(mP); free(cP); return -1; }
+        float o[3], d[3];
+        make_ray(V, pix % V->width, pix / V->width, o, d);
+
+        /* gather this ray's owned samples in lattice order */
+        size_t ns = 0;
+        int64_t k_lo, k_hi;
+        if (lattice_range(g, o, d, &k_lo, &k_hi)) {
+            for (int64_t k = k_lo; k <= k_hi; ++k) {
+                if (ns == cap) {
+                    cap *= 2;
+                    sample_t* S2 = (sample_t*)realloc(S, cap * sizeof(sample_t));
+                    if (!S2) { free(S); free(mP); free(cP); return -1; }
+                    S = S2;
+                }
+                if (take_sample(g, V, o, d, k, sig_tab, &S[ns])) ++ns;
+            }
+        }
+
+        /* stage one (Sec. 4.1): local moment image of each piece ... */
+        memset(mP, 0, (size_t)K * 5 * sizeof(double));
+        for (size_t i = 0; i < ns; ++i) {
+            double* mp = mP + 5 * S[i].piece;
+            double zp = 1.0;
+            for (int j = 0; j <= 4; ++j) {
+                mp[j] += zp * S[i].a;
+                zp *= S[i].z;
+            }
+        }
+        /* ... summed over pieces (the Allreduce add) */
+        double m[5] = {0, 0, 0, 0, 0};
+        for (int P = 0; P < K; ++P)
+            for (int j = 0; j <= 4; ++j) m[j] += mP[5 * P + j];
+
+        /* stage two (Sec. 4.2): each piece blends its own samples with the
+         * transmittance reconstructed from the global moments */
+        memset(cP, 0, (size_t)K * 4 * sizeof(double));
+        for (size_t i = 0; i < ns; ++i) {
+            double T = transmittance(m, S[i].z, g);
+            double* cp = cP + 4 * S[i].piece;
+            for (int c = 0; c < 3; ++c) cp[c] += T * S[i].alpha * S[i].rgb[c];
+            cp[3] += T * S[i].alpha;
+        }
+        /* final image: sum of the partial images (the Reduce add) */
+        double C[4] = {0, 0, 0, 0};
+        for (int P = 0; P < K; ++P)
+            for (int c = 0; c < 4; ++c) C[c] += cP[4 * P + c];
+
+        if (moments) memcpy(moments + 5 * n, m, sizeof m);
+        if (piece_moments) memcpy(piece_moments + (size_t)n * K * 5, mP, (size_t)K * 5 * sizeof(double));
+        if (piece_color) memcpy(piece_color + (size_t)n * K * 4, cP, (size_t)K * 4 * sizeof(double));
+        if (raw_rgba) memcpy(raw_rgba + 4 * n, C, sizeof C);
+        if (mboit_rgba) {
+            /* renormalisation: total opacity from the zeroth moment */
+            double A = 1.0 - exp(-m[0]);
+            double* out = mboit_rgba + 4 * n;
+            for (int c = 0; c < 3; ++c) out[c] = (C[3] > 0.0) ? C[c] * A / C[3] : 0.0;
+            out[3] = A;
+        }
+        if (exact_rgba) {
+            /* front-to-back over all samples in depth order */
+            double acc[3] = {0, 0, 0}, tau = 0.0;
+            for (size_t i = 0; i < ns; ++i) {
+                double T = exp(-tau);
+                for (int c = 0; c < 3; ++c) acc[c] += T * S[i].alpha * S[i].rgb[c];
+                tau += S[i].a;
+            }
+            double* out = exact_rgba + 4 * n;
+            for (int c = 0; c < 3; ++c) out[c] = acc[c];
+            out[3] = 1.0 - exp(-tau);
+        }
+        if (sortlast_rgba) {
+            /* each maximal run of consecutive lattice points of one piece is a
+             * segment, composited in front-to-back order inside itself; the
+             * segments are then sorted by their first lattice index (runs
+             * are disjoint) and composited with "over" */
+            size_t nseg = 0;
+            double* seg = (double*)malloc((ns + 1) * 5 * sizeof(double)); /* k_first, r, g, b, alpha */
+            if (!seg) { free(S); free(mP); free(cP); return -1; }
+            for (int P = 0; P < K; ++P) {
+                /* piece P's own samples, as its rank would produce them */
+                int64_t prev_k = -2;
+                double* sg = NULL;
+                double tr = 1.0;
+                for (size_t i = 0; i < ns; ++i) {
+                    if (S[i].piece != P) continue;
+                    if (S[i].k != prev_k + 1) {
+                        if (sg) sg[4] = 1.0 - tr;
+                        sg = seg + 5 * nseg++;
+                        sg[0] = (double)S[i].k;
+                        sg[1] = sg[2] = sg[3] = 0.0;
+                        tr = 1.0;
+                    }
+                    for (int c = 0; c < 3; ++c) sg[1 + c] += tr * S[i].alpha * S[i].rgb[c];
+                    tr *= 1.0 - S[i].alpha;
+                    prev_k = S[i].k;
+                }
+                if (sg) sg[4] = 1.0 - tr;
+            }
+            /* insertion sort of all pieces' segments on k_first */
+            for (size_t a = 1; a < nseg; ++a)
+                for (size_t b = a; b > 0 && seg[5 * (b - 1)] > seg[5 * b]; --b)
+                    for (int c = 0; c < 5; ++c) {
+                        double s = seg[5 * b + c];
+                        seg[5 * b + c] = seg[5 * (b - 1) + c];
+                        seg[5 * (b - 1) + c] = s;
+                    }
+            double acc[3] = {0, 0, 0}, tr = 1.0;
+            for (size_t a = 0; a < nseg; ++a) {
+                for (int c = 0; c < 3; ++c) acc[c] += tr * seg[5 * a + 1 + c];
+                tr *= 1.0 - seg[5 * a + 4];
+            }
+            double* out = sortlast_rgba + 4 * n;
+            for (int c = 0; c < 3; ++c) out[c] = acc[c];
+            out[3] = 1.0 - tr;
+            free(seg);
+        }
+        if (nsamples) nsamples[n] = (int64_t)ns;
+    }
+    free(S);
+    free(mP);
+    free(cP);
+    return 0;
+}

@@ -1,0 +1,66 @@
+/*
+ * FP64 CPU oracle of the two-pass MBOIT puzzle-piece render.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this code; only the tests, the smoke check and the benchmark's CPU
+ * baseline do.  It shares no source with the CUDA path.
+ *
+ * Coordinates follow the `scenes` module: field[z][y][x] float32 vertex
+ * values, vertex (x,y,z) at point (x,y,z), bricks of 2^brick_log2 cells,
+ * brick id (bz*nby + by)*nbx + bx.
+ */
+#ifndef MBOIT_ORACLE_H
+#define MBOIT_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    float eye[3], u[3], v[3], w[3];
+    int32_t width, height, projection, reserved;
+    float scale_u, scale_v, znear, zfar;
+} orc_view;
+
+typedef struct {
+    const float* field;            /* [nz][ny][nx] */
+    int32_t nx, ny, nz, brick_log2;
+    const int32_t* piece_of_brick; /* [nbz*nby*nbx] */
+    int32_t n_pieces, reserved;
+    const uint8_t* piece_selected; /* [n_pieces], NULL = every piece */
+    const float* tf;               /* [256][4] r, g, b, alpha per voxel */
+    double vmin, vmax;
+    double step;                   /* sample spacing, voxel units */
+    double moment_bias;            /* mix amount of the bias vector (Alg. 3) */
+    double overestimation;         /* weight w0 of the sample's own depth (Alg. 3) */
+    double absorbance_max;         /* ABSORBANCE_MAX_VALUE (Alg. 2) */
+    double bias_vector[4];
+} orc_grid;
+
+/* Alg. 3 core: the moment-bound absorbance fraction A(z0) in [0,1] for raw
+ * power moments m[0..4]; the transmittance is clamp(exp(-m[0]*A)).
+ * *flags (optional) gets 1 for the one-atom, 2 for the two-atom branch. */
+double orc_mboit_bound(const double m[5], double z0, double moment_bias,
+                       const double bias_vector[4], double overestimation, int* flags);
+
+/* Logarithmic depth warp of Alg. 2/3: [near, far] -> [-1, 1], clamped. */
+double orc_log_warp(double t, double znear, double zfar);
+
+/* Renders the listed pixels (index y*width + x) of one view.  Every output
+ * pointer may be NULL.  Per pixel: moments = summed global moments [5];
+ * piece_moments [K][5]; piece_color [K][4] (stage 2 partial images);
+ * mboit_rgba = renormalised resolve; raw_rgba = sum of T*alpha*(c,1);
+ * exact_rgba = front-to-back blend of the same samples; sortlast_rgba =
+ * per-piece segments sorted and blended; nsamples = owned samples.
+ * Returns 0, or -1 on bad arguments / allocation failure. */
+int orc_render_grid(const orc_grid* g, const orc_view* view,
+                    const int64_t* pixels, int64_t n_pixels,
+                    double* moments, double* piece_moments, double* piece_color,
+                    double* mboit_rgba, double* raw_rgba, double* exact_rgba,
+                    double* sortlast_rgba, int64_t* nsamples);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,281 @@
+"""Seeded synthetic inputs for the MBOIT puzzle-piece render.
+
+This module only *describes* workloads: scalar fields, brick partitions into
+pieces, RGBA transfer-function tables and camera specifications.  It holds
+none of the method's arithmetic (no ray set-up, sampling, opacity conversion,
+moments or reconstruction).  Both the FP64 oracle (`oracle/`) and the CUDA
+library consume the arrays it returns, so the two sides see bit-identical
+inputs.
+
+Coordinates: the field is a float32 array ``field[z][y][x]`` of vertex values;
+vertex (x, y, z) sits at point (x, y, z), so the domain is the box
+[0, nx-1] x [0, ny-1] x [0, nz-1] and cell (i, j, k) spans [i, i+1) etc.
+Bricks are cubes of ``2**brick_log2`` cells; brick (bx, by, bz) has id
+``(bz*nby + by)*nbx + bx``.  A piece is a set of bricks (Morton-order ranges,
+as p4est partitions a Morton curve, §3), so pieces are disjoint and jagged.
+
+Views are given in the same index space.  All camera numbers are float32 so
+both sides read the same bits.  ``near``/``far`` bound the logarithmic depth
+warp of the view (Alg. 2): they bracket the domain's bounding sphere.
+"""
+from dataclasses import dataclass, field as dc_field
+from typing import List
+
+import numpy as np
+
+from .rng import Stream
+
+ORTHO = 0
+PERSPECTIVE = 1
+
+
+@dataclass
+class View:
+    eye: np.ndarray
+    u: np.ndarray
+    v: np.ndarray
+    w: np.ndarray
+    width: int
+    height: int
+    projection: int
+    scale_u: np.float32
+    scale_v: np.float32
+    near: np.float32
+    far: np.float32
+
+
+@dataclass
+class GridScene:
+    name: str
+    field: np.ndarray            # float32 [nz][ny][nx]
+    brick_log2: int
+    piece_of_brick: np.ndarray   # int32 [nbz*nby*nbx]
+    n_pieces: int
+    tf: np.ndarray               # float32 [256][4]: r, g, b, alpha (opacity per unit length)
+    tf_range: tuple              # (vmin, vmax) float32
+    step: float                  # sample spacing along the ray, voxel units (power of two)
+    views: List[View] = dc_field(default_factory=list)
+    moment_bias: float = 5e-5
+    overestimation: float = 0.3
+    absorbance_max: float = 10.0
+
+    @property
+    def dims(self):
+        nz, ny, nx = self.field.shape
+        return (nx, ny, nz)
+
+    @property
+    def brick_dims(self):
+        b = 1 << self.brick_log2
+        return tuple((n - 1 + b - 1) // b for n in self.dims)
+
+    def piece_bricks(self, p):
+        return np.nonzero(self.piece_of_brick == p)[0].astype(np.int32)
+
+
+# ---------------------------------------------------------------------------
+# fields
+
+def _axis_gauss(n, centres, sigmas):
+    x = np.arange(n, dtype=np.float64)
+    return np.exp(-((x[None, :] - centres[:, None]) ** 2) / (2.0 * sigmas[:, None] ** 2))
+
+
+def blob_field(shape_xyz, n_blobs, sigma_lo, sigma_hi, stream):
+    """Sum of isotropic Gaussians A*exp(-|x-c|^2/(2 s^2)), evaluated at vertices."""
+    nx, ny, nz = shape_xyz
+    c = stream.uniform(3 * n_blobs).reshape(n_blobs, 3) * np.array([nx, ny, nz], dtype=np.float64)
+    s = stream.uniform(n_blobs, sigma_lo, sigma_hi)
+    a = stream.uniform(n_blobs, 0.3, 1.0)
+    gx = _axis_gauss(nx, c[:, 0], s) * a[:, None]
+    gy = _axis_gauss(ny, c[:, 1], s)
+    gz = _axis_gauss(nz, c[:, 2], s)
+    out = np.empty((nz, ny, nx), dtype=np.float32)
+    chunk = max(1, (1 << 22) // (ny * nx) * 8)
+    for z0 in range(0, nz, chunk):
+        z1 = min(nz, z0 + chunk)
+        zy = (gz[:, z0:z1, None] * gy[:, None, :]).reshape(n_blobs, -1)  # [blob][(z,y)]
+        out[z0:z1] = (zy.T @ gx).reshape(z1 - z0, ny, nx).astype(np.float32)
+    return out
+
+
+def _lerp_matrix(n, spacing):
+    """[n][L] weights of piecewise-linear interpolation from a lattice of the given spacing."""
+    L = int(np.ceil((n - 1) / spacing)) + 1
+    x = np.arange(n, dtype=np.float64) / spacing
+    i = np.minimum(np.floor(x).astype(np.int64), L - 2)
+    f = x - i
+    W = np.zeros((n, L))
+    W[np.arange(n), i] = 1.0 - f
+    W[np.arange(n), i + 1] += f
+    return W
+
+
+def value_noise(shape_xyz, spacing, stream):
+    """Lattice value noise: U[0,1) values on a lattice, trilinearly interpolated."""
+    nx, ny, nz = shape_xyz
+    Wx, Wy, Wz = (_lerp_matrix(n, spacing) for n in (nx, ny, nz))
+    V = stream.uniform(Wz.shape[1] * Wy.shape[1] * Wx.shape[1]).reshape(Wz.shape[1], Wy.shape[1], Wx.shape[1])
+    t = np.einsum("abc,xc->abx", V, Wx)
+    t = np.einsum("abx,yb->ayx", t, Wy).reshape(Wz.shape[1], -1)
+    out = np.empty((nz, ny, nx), dtype=np.float64)
+    for z0 in range(0, nz, 64):
+        z1 = min(nz, z0 + 64)
+        out[z0:z1] = (Wz[z0:z1] @ t).reshape(z1 - z0, ny, nx)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# partitions
+
+def morton3(bx, by, bz, bits):
+    code = np.zeros(np.shape(bx), dtype=np.int64)
+    for b in range(bits):
+        code |= ((bx >> b) & 1) << (3 * b)
+        code |= ((by >> b) & 1) << (3 * b + 1)
+        code |= ((bz >> b) & 1) << (3 * b + 2)
+    return code
+
+
+def morton_pieces(brick_dims, n_pieces, stream, jitter=0.45, weights=None):
+    """Split the Morton-ordered brick list into contiguous ranges, one per piece.
+
+    Interior split points are moved by round(U[-jitter, jitter] * range), so
+    pieces straddle Morton octants and are non-convex.  `weights` (optional)
+    gives relative piece sizes before jitter.
+    """
+    nbx, nby, nbz = brick_dims
+    bz, by, bx = np.meshgrid(np.arange(nbz), np.arange(nby), np.arange(nbx), indexing="ij")
+    bits = int(np.ceil(np.log2(max(nbx, nby, nbz, 2))))
+    code = morton3(bx.ravel(), by.ravel(), bz.ravel(), bits)
+    order = np.argsort(code, kind="stable")
+    n = order.size
+    if weights is None:
+        weights = np.ones(n_pieces)
+    cum = np.concatenate([[0.0], np.cumsum(weights) / np.sum(weights)]) * n
+    nominal = np.diff(cum)
+    j = stream.uniform(n_pieces - 1, -jitter, jitter)
+    splits = [0]
+    for i in range(1, n_pieces):
+        s = int(round(cum[i] + j[i - 1] * min(nominal[i - 1], nominal[i])))
+        splits.append(min(max(s, splits[-1] + 1), n - (n_pieces - i)))
+    splits.append(n)
+    piece = np.empty(n, dtype=np.int32)
+    for p in range(n_pieces):
+        piece[order[splits[p]:splits[p + 1]]] = p
+    return piece
+
+
+# ---------------------------------------------------------------------------
+# transfer function
+
+def tf_table(stream, alpha_max, n_ctrl=6):
+    """256-entry piecewise-linear RGBA table from n_ctrl seeded control points.
+
+    Control positions are 0, 1 and n_ctrl-2 sorted U(0,1) draws; colours are
+    U[0,1); alpha is U[0, alpha_max) (opacity of one voxel of material).
+    """
+    pos = np.concatenate([[0.0], np.sort(stream.uniform(n_ctrl - 2)), [1.0]])
+    rgb = stream.uniform(3 * n_ctrl).reshape(n_ctrl, 3)
+    alpha = stream.uniform(n_ctrl, 0.0, alpha_max)
+    x = np.arange(256, dtype=np.float64) / 255.0
+    tab = np.stack([np.interp(x, pos, rgb[:, 0]), np.interp(x, pos, rgb[:, 1]),
+                    np.interp(x, pos, rgb[:, 2]), np.interp(x, pos, alpha)], axis=1)
+    return tab.astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# cameras
+
+def _basis(wdir):
+    w = np.asarray(wdir, dtype=np.float64)
+    w = w / np.linalg.norm(w)
+    up = np.array([0.0, 0.0, 1.0])
+    u = np.cross(w, up)
+    u /= np.linalg.norm(u)
+    v = np.cross(u, w)
+    return u, v, w
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32)
+
+
+def ortho_view(dims, wdir, width, height, margin=1.02):
+    """Orthographic view whose window covers the domain's bounding sphere.
+
+    The view plane sits one domain diagonal in front of the sphere's near
+    side, so depth is positive everywhere and the log warp is defined.
+    """
+    ext = np.array(dims, dtype=np.float64) - 1.0
+    c = ext / 2.0
+    diag = float(np.linalg.norm(ext))
+    r = diag / 2.0
+    u, v, w = _basis(wdir)
+    dist = r + diag
+    eye = c - dist * w
+    size = 2.0 * r * margin
+    return View(_f32(eye), _f32(u), _f32(v), _f32(w), width, height, ORTHO,
+                np.float32(size * width / max(width, height)), np.float32(size * height / max(width, height)),
+                np.float32(dist - r), np.float32(dist + r))
+
+
+def perspective_view(dims, wdir, width, height, fov_deg=30.0, dist_diag=1.8):
+    ext = np.array(dims, dtype=np.float64) - 1.0
+    c = ext / 2.0
+    diag = float(np.linalg.norm(ext))
+    r = diag / 2.0
+    u, v, w = _basis(wdir)
+    dist = dist_diag * diag
+    eye = c - dist * w
+    th = np.tan(np.radians(fov_deg) / 2.0)
+    aspect = width / height
+    return View(_f32(eye), _f32(u), _f32(v), _f32(w), width, height, PERSPECTIVE,
+                np.float32(th * aspect), np.float32(th),
+                np.float32(max(dist - r, 0.25)), np.float32(dist + r))
+
+
+# ---------------------------------------------------------------------------
+# named workloads
+
+# Per-workload alpha_max: chosen so the median zeroth moment b0 over hit
+# pixels is about 3 (a semi-transparent volume), measured with the oracle.
+ALPHA_MAX = {"blobs64": 0.13, "blobs512": 0.053}
+
+
+def blobs64(width=256, height=256, n_pieces=4, seed=1001):
+    """64^3 float32 field = 8 Gaussian blobs (sigma 4-12 voxels, amplitude
+    U[0.3,1]); 8^3-cell bricks split into 4 jittered Morton pieces; 6-point
+    transfer function; orthographic view, step 0.5 voxel."""
+    s = Stream(seed)
+    dims = (64, 64, 64)
+    f = blob_field(dims, 8, 4.0, 12.0, s)
+    tf = tf_table(s, ALPHA_MAX["blobs64"])
+    bl = 3
+    bd = tuple((n - 1 + (1 << bl) - 1) >> bl for n in dims)
+    piece = morton_pieces(bd, n_pieces, s)
+    view = ortho_view(dims, (0.62, 0.48, 0.62), width, height)
+    return GridScene("blobs64", f, bl, piece, n_pieces, tf,
+                     (np.float32(f.min()), np.float32(f.max())), 0.5, [view])
+
+
+def blobs512(width=2048, height=2048, n_pieces=64, seed=1002, n=512):
+    """512^3 float32 field = 64 Gaussian blobs (sigma 32-96 voxels) plus
+    3-octave value noise (lattice spacing 64, 32, 16 voxels, weight 0.15 *
+    0.5^octave); 16^3-cell bricks split into 64 jittered Morton pieces;
+    perspective view (fov 30 degrees, eye 1.8 diagonals from the centre),
+    step 0.5 voxel.  `n` shrinks the grid for tests (sizes scale with n)."""
+    s = Stream(seed)
+    dims = (n, n, n)
+    k = n / 64.0
+    f = blob_field(dims, 64, 4.0 * k, 12.0 * k, s).astype(np.float64)
+    for o in range(3):
+        f += 0.15 * 0.5 ** o * value_noise(dims, max(2.0, 64.0 * k / 8.0 / 2 ** o), s)
+    f = f.astype(np.float32)
+    tf = tf_table(s, ALPHA_MAX["blobs512"] * 512.0 / n)
+    bl = 4
+    bd = tuple((m - 1 + (1 << bl) - 1) >> bl for m in dims)
+    piece = morton_pieces(bd, n_pieces, s)
+    view = perspective_view(dims, (0.57, 0.49, 0.66), width, height)
+    return GridScene("blobs512" if n == 512 else f"blobs{n}", f, bl, piece, n_pieces, tf,
+                     (np.float32(f.min()), np.float32(f.max())), 0.5, [view])

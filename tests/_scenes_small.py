@@ -1,0 +1,66 @@
+"""Small hand-built scenes for pins and edge cases (inputs only, no method arithmetic)."""
+import numpy as np
+
+import scenes
+
+
+def axis_view(dims, width, height, eye_z, scale, w=(0.0, 0.0, 1.0), u=(1.0, 0.0, 0.0), v=(0.0, 1.0, 0.0),
+              near=5.0, far=60.0, centre=None):
+    nx, ny, nz = dims
+    c = centre if centre is not None else ((nx - 1) / 2.0, (ny - 1) / 2.0)
+    return scenes.View(np.array([c[0], c[1], eye_z], np.float32), np.array(u, np.float32),
+                       np.array(v, np.float32), np.array(w, np.float32), width, height, scenes.ORTHO,
+                       np.float32(scale), np.float32(scale), np.float32(near), np.float32(far))
+
+
+def constant_tf(alpha, rgb=(0.8, 0.4, 0.2)):
+    tf = np.zeros((256, 4), np.float32)
+    tf[:, 0:3] = rgb
+    tf[:, 3] = alpha
+    return tf
+
+
+def linear_tf(s0, s1):
+    """sigma_j = s0 + s1*j/255 (opacity alpha_j = 1 - exp(-sigma_j)); r = j/255,
+    g = 1 - j/255, b = 0.5, so every channel is linear in the normalised value."""
+    j = np.arange(256) / 255.0
+    tf = np.zeros((256, 4), np.float64)
+    tf[:, 0] = j
+    tf[:, 1] = 1.0 - j
+    tf[:, 2] = 0.5
+    tf[:, 3] = 1.0 - np.exp(-(s0 + s1 * j))
+    return tf.astype(np.float32)
+
+
+def slab_scene(alpha=0.1, n=33, brick_log2=3, slab_layer=1):
+    """Constant field; piece 1 = the bricks of one z-layer, piece 0 = the rest."""
+    field = np.ones((n, n, n), np.float32)
+    B = 1 << brick_log2
+    nb = (n - 1 + B - 1) // B
+    bz = np.repeat(np.arange(nb), nb * nb)
+    piece = (bz == slab_layer).astype(np.int32)
+    return scenes.GridScene("slab", field, brick_log2, piece, 2, constant_tf(alpha),
+                            (np.float32(0.0), np.float32(2.0)), 0.5, [])
+
+
+def linear_scene(dims=(17, 13, 11), brick_log2=2, n_pieces=3, seed=7):
+    nx, ny, nz = dims
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    field = (0.25 + x / 16.0 + y / 32.0 + z / 8.0).astype(np.float32)
+    B = 1 << brick_log2
+    bd = tuple((m - 1 + B - 1) // B for m in dims)
+    piece = scenes.morton_pieces(bd, n_pieces, scenes.Stream(seed))
+    return scenes.GridScene("linear", field, brick_log2, piece, n_pieces, linear_tf(0.05, 0.3),
+                            (np.float32(field.min()), np.float32(field.max())), 0.5, [])
+
+
+def sandwich_scene(n=25, brick_log2=2, ranks=3, seed=11):
+    """Fig. 6: each of `ranks` pieces owns interleaved z-slices of one cube."""
+    s = scenes.Stream(seed)
+    field = scenes.blob_field((n, n, n), 4, 3.0, 8.0, s)
+    B = 1 << brick_log2
+    nb = (n - 1 + B - 1) // B
+    bz = np.repeat(np.arange(nb), nb * nb)
+    piece = (bz % ranks).astype(np.int32)
+    return scenes.GridScene("sandwich", field, brick_log2, piece, ranks, scenes.tf_table(s, 0.35),
+                            (np.float32(field.min()), np.float32(field.max())), 0.5, [])

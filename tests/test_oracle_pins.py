@@ -1,0 +1,305 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, brute-force enumeration on tiny inputs, the moment-bound theory the
+reconstruction rests on, or invariants the paper states (Sec. 4.1: moment
+addition commutes, so per-piece moments sum to the single-node ones; Sec. 5.2:
+APC reproduces single-node MBOIT; Fig. 6: per-rank partial images add up).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from tests import _scenes_small as small
+
+W0 = 0.3  # overestimation used in the paper's evaluation (Sec. 5)
+
+
+def raw_moments(x, a):
+    x = np.asarray(x, float)
+    a = np.asarray(a, float)
+    return np.array([np.sum(a * x ** j) for j in range(5)])
+
+
+# --------------------------------------------------------------------------
+# Alg. 3: the moment bound
+
+
+@pytest.mark.parametrize("x", [-0.7, 0.0, 0.42])
+def test_one_absorber_exact(x):
+    """One absorber, no bias: T(z) = 1 before it and e^-a after it."""
+    a = 1.7
+    m = raw_moments([x], [a])
+    for z in np.linspace(-1, 1, 41):
+        if abs(z - x) < 1e-9:
+            continue
+        A, branch = oracle.mboit_bound(m, z, 0.0, W0)
+        assert branch == 1
+        T = math.exp(-m[0] * A)
+        assert T == pytest.approx(1.0 if z < x else math.exp(-a), abs=1e-12)
+
+
+def test_two_absorbers_exact():
+    """Two absorbers, no bias: T(z) = exp(-sum of the absorbances in front)."""
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        x = np.sort(rng.uniform(-1, 1, 2))
+        if x[1] - x[0] < 0.05:
+            continue
+        a = rng.uniform(0.05, 3.0, 2)
+        m = raw_moments(x, a)
+        for z in rng.uniform(-1, 1, 8):
+            if np.min(np.abs(z - x)) < 1e-6:
+                continue
+            A, branch = oracle.mboit_bound(m, z, 0.0, W0)
+            assert branch == 2
+            assert math.exp(-m[0] * A) == pytest.approx(math.exp(-a[x < z].sum()), abs=1e-10)
+
+
+def test_three_absorbers_canonical():
+    """Generic branch.  A three-atom measure is the unique canonical
+    representation through each of its atoms, so at z0 = x_j the bound is
+    exactly (sum_{x_i < x_j} a_i + w0 a_j) / sum a."""
+    rng = np.random.default_rng(2)
+    n = 0
+    while n < 500:
+        x = np.sort(rng.uniform(-1, 1, 3))
+        if np.diff(x).min() < 0.1:
+            continue
+        a = rng.uniform(0.1, 2.0, 3)
+        w0 = rng.uniform(0, 1)
+        m = raw_moments(x, a)
+        for j in range(3):
+            A, branch = oracle.mboit_bound(m, x[j], 0.0, w0)
+            assert branch == 0
+            assert A == pytest.approx((a[x < x[j]].sum() + w0 * a[j]) / a.sum(), abs=1e-11)
+        n += 1
+
+
+def test_full_bias_is_bias_vector_measure():
+    """With mix amount 1 the moments become the bias vector (0, 3/8, 0, 3/8),
+    the moments of the measure {-1: 3/16, 0: 5/8, 1: 3/16}."""
+    m = raw_moments([0.3, -0.2, 0.9], [0.5, 1.0, 0.2])
+    for w0 in (0.0, 0.3, 1.0):
+        assert oracle.mboit_bound(m, -1.0, 1.0, w0)[0] == pytest.approx(w0 * 3 / 16, abs=1e-14)
+        assert oracle.mboit_bound(m, 0.0, 1.0, w0)[0] == pytest.approx(3 / 16 + w0 * 5 / 8, abs=1e-14)
+        assert oracle.mboit_bound(m, 1.0, 1.0, w0)[0] == pytest.approx(13 / 16 + w0 * 3 / 16, abs=1e-14)
+
+
+def test_bound_containment():
+    """Chebyshev-Markov-Stieltjes: with w0 = 0 the bound is a lower bound on
+    the mass strictly in front of z, with w0 = 1 an upper bound on the mass
+    up to and including z, for every measure with these moments."""
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        k = rng.integers(3, 12)
+        x = rng.uniform(-1, 1, k)
+        a = rng.uniform(0.01, 1.0, k)
+        m = raw_moments(x, a)
+        for z in rng.uniform(-1, 1, 10):
+            lo = oracle.mboit_bound(m, z, 0.0, 0.0)[0]
+            hi = oracle.mboit_bound(m, z, 0.0, 1.0)[0]
+            before = a[x < z].sum() / a.sum()
+            upto = a[x <= z].sum() / a.sum()
+            assert lo <= before + 1e-9
+            assert upto <= hi + 1e-9
+
+
+def test_bound_monotone_and_in_range():
+    """A(z) = (1 - w0) * lower + w0 * upper is non-decreasing in z, in [0, 1]."""
+    rng = np.random.default_rng(4)
+    zs = np.linspace(-1, 1, 201)
+    for _ in range(100):
+        k = rng.integers(1, 20)
+        m = raw_moments(rng.uniform(-1, 1, k), rng.uniform(0.01, 2.0, k))
+        beta = 10 ** rng.uniform(-6, -1)
+        A = np.array([oracle.mboit_bound(m, z, beta, W0)[0] for z in zs])
+        assert np.all(A >= -1e-9) and np.all(A <= 1 + 1e-9)
+        assert np.all(np.diff(A) >= -1e-7)
+
+
+def test_log_warp_closed_form():
+    n, f = 3.0, 48.0
+    assert oracle.log_warp(n, n, f) == pytest.approx(-1.0, abs=1e-15)
+    assert oracle.log_warp(f, n, f) == pytest.approx(1.0, abs=1e-15)
+    assert oracle.log_warp(math.sqrt(n * f), n, f) == pytest.approx(0.0, abs=1e-14)
+    assert oracle.log_warp(0.5, n, f) == -1.0
+    assert oracle.log_warp(100.0, n, f) == 1.0
+
+
+# --------------------------------------------------------------------------
+# sampling, Alg. 2, stage one
+
+
+def _f32_fma(a, b, c):
+    # a*b of two float32 is exact in float64; the one rounding to float32
+    # that follows matches fmaf except at exact float32 midpoints.
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def _brute_samples(view, dims, step, px, py, kmax=6000):
+    """Lattice points of one orthographic ray inside the domain, by enumeration."""
+    f32 = np.float32
+    fx, fy = f32(px) + f32(0.5), f32(py) + f32(0.5)
+    sx = (fx / f32(view.width) - f32(0.5)) * view.scale_u
+    sy = (fy / f32(view.height) - f32(0.5)) * view.scale_v
+    o = [(view.eye[c] + sx * view.u[c]) + sy * view.v[c] for c in range(3)]
+    d = [view.w[c] for c in range(3)]
+    out = []
+    for k in range(kmax):
+        t = (f32(k) + f32(0.5)) * f32(step)
+        p = [_f32_fma(t, d[c], o[c]) for c in range(3)]
+        if all(f32(0) <= p[c] < f32(dims[c] - 1) for c in range(3)):
+            out.append((float(t), [float(q) for q in p]))
+    return out
+
+
+def test_linear_field_brute_force():
+    """Trilinear interpolation reproduces a linear field, and a linear sigma
+    table is reproduced by linear lookup, so b_j = sum sigma(f(p_k)) step
+    z(t_k)^j over the enumerated lattice points (catches axis transposition,
+    lost or extra samples, wrong warp or power)."""
+    sc = small.linear_scene()
+    dims = sc.dims
+    view = small.axis_view(dims, 7, 6, -9.0, 14.0, w=(0.36, 0.48, 0.8), u=(0.8, -0.6, 0.0),
+                           v=(0.48, 0.64, -0.6), near=4.0, far=40.0, centre=(6.0, 7.0))
+    view.eye = np.array([2.0, 1.0, -9.0], np.float32)
+    sc.views = [view]
+    r = oracle.render_grid(sc, want=("moments", "exact", "nsamples"))
+    vmin, vmax = float(sc.tf_range[0]), float(sc.tf_range[1])
+    hit = 0
+    for py in range(view.height):
+        for px in range(view.width):
+            idx = py * view.width + px
+            S = _brute_samples(view, dims, sc.step, px, py)
+            assert r["nsamples"][idx] == len(S)
+            m = np.zeros(5)
+            acc = np.zeros(3)
+            tau = 0.0
+            for t, p in S:
+                val = 0.25 + p[0] / 16 + p[1] / 32 + p[2] / 8
+                xn = (val - vmin) / (vmax - vmin)
+                a = (0.05 + 0.3 * xn) * sc.step
+                z = min(max(2 * math.log(t / 4.0) / math.log(10.0) - 1, -1), 1)
+                m += a * z ** np.arange(5)
+                alpha = 1 - math.exp(-a)
+                acc += math.exp(-tau) * alpha * np.array([xn, 1 - xn, 0.5])
+                tau += a
+            hit += len(S) > 0
+            np.testing.assert_allclose(r["moments"][idx], m, rtol=2e-6, atol=1e-9)
+            np.testing.assert_allclose(r["exact"][idx, :3], acc, rtol=2e-6, atol=1e-9)
+            assert r["exact"][idx, 3] == pytest.approx(1 - math.exp(-tau), rel=2e-6, abs=1e-9)
+    assert hit > 20
+
+
+def test_constant_slab_zeroth_moment():
+    """Field = 1, constant opacity, the slab is one z-layer of bricks, rays
+    along +z with lattice points on the slab faces' half-step offsets: b0 =
+    sigma L exactly; b_j is the midpoint rule of the integral of
+    sigma z(t)^j, within its O(step^2) error bound."""
+    alpha = 0.1
+    sc = small.slab_scene(alpha=alpha)
+    sigma = -math.log(1 - np.float64(np.float32(alpha)))
+    view = small.axis_view(sc.dims, 8, 8, -10.0, 16.0, near=5.0, far=60.0)
+    sc.views = [view]
+    r = oracle.render_grid(sc, pieces=[1], want=("moments", "nsamples"))
+    L = 8.0  # one 8-cell brick layer, z in [8, 16)
+    assert np.all(r["nsamples"] == 16)
+    np.testing.assert_allclose(r["moments"][:, 0], sigma * L, rtol=1e-14)
+    # midpoint rule of int_{18}^{26} sigma z(t)^j dt (t from the eye plane)
+    ln = math.log(60.0 / 5.0)
+    t = np.linspace(18.0, 26.0, 20001)
+    for j in range(1, 5):
+        g = sigma * (2 * np.log(t / 5.0) / ln - 1) ** j
+        integ = np.trapezoid(g, t)
+        g2 = np.abs(np.gradient(np.gradient(g, t), t)).max()
+        bound = 8.0 * 0.5 ** 2 / 24 * g2 * 1.5 + 1e-9
+        assert abs(r["moments"][0, j] - integ) <= bound
+
+
+def test_oblique_slab_zeroth_moment():
+    """Oblique rays: b0 is within sigma*step of sigma times the chord."""
+    alpha = 0.1
+    sc = small.slab_scene(alpha=alpha)
+    sigma = -math.log(1 - np.float64(np.float32(alpha)))
+    w = np.array([0.3, 0.2, 1.0])
+    w /= np.linalg.norm(w)
+    u = np.cross(w, [0, 1, 0])
+    u /= np.linalg.norm(u)
+    v = np.cross(u, w)
+    view = small.axis_view(sc.dims, 6, 6, -10.0, 6.0, w=w, u=u, v=v)
+    sc.views = [view]
+    r = oracle.render_grid(sc, pieces=[1], want=("moments",))
+    chord = 8.0 / w[2]
+    assert np.all(np.abs(r["moments"][:, 0] - sigma * chord) <= sigma * 0.5 + 1e-12)
+
+
+# --------------------------------------------------------------------------
+# stage one / two invariants (Sec. 4.1, 4.2, 5.2, Fig. 6)
+
+
+def _one_piece(sc):
+    import copy
+    s1 = copy.copy(sc)
+    s1.piece_of_brick = np.zeros_like(sc.piece_of_brick)
+    s1.n_pieces = 1
+    return s1
+
+
+def test_union_equals_sum(blobs64):
+    """Per-piece moment images summed equal the single-node moments."""
+    r = oracle.render_grid(blobs64, want=("piece_moments", "moments"))
+    u = oracle.render_grid(_one_piece(blobs64), want=("moments",))
+    s = r["piece_moments"].sum(axis=1)
+    scale = np.abs(u["moments"]).max(axis=1, keepdims=True) + 1e-300
+    assert np.max(np.abs(s - u["moments"]) / scale) <= 1e-12
+    # every piece contributes somewhere: the partition is really used
+    assert np.all(np.abs(r["piece_moments"][:, :, 0]).sum(axis=0) > 0)
+
+
+def test_piece_order_independence(blobs64):
+    """Relabelling pieces (a different reduction order) changes nothing."""
+    import copy
+    perm = np.array([2, 0, 3, 1], np.int32)
+    s2 = copy.copy(blobs64)
+    s2.piece_of_brick = perm[blobs64.piece_of_brick]
+    a = oracle.render_grid(blobs64, want=("moments", "mboit"))
+    b = oracle.render_grid(s2, want=("moments", "mboit"))
+    np.testing.assert_allclose(a["moments"], b["moments"], rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(a["mboit"], b["mboit"], rtol=1e-12, atol=1e-14)
+
+
+def test_alpha_identity_and_sortlast(blobs64):
+    """Renormalised MBOIT alpha = exact alpha = 1 - e^-b0; per-piece segments
+    sorted and blended equal the global front-to-back march."""
+    r = oracle.render_grid(blobs64, want=("moments", "mboit", "exact", "sortlast"))
+    np.testing.assert_allclose(r["mboit"][:, 3], r["exact"][:, 3], atol=1e-12)
+    np.testing.assert_allclose(r["mboit"][:, 3], 1 - np.exp(-r["moments"][:, 0]), atol=1e-15)
+    np.testing.assert_allclose(r["sortlast"], r["exact"], atol=1e-12)
+    # MBOIT is an approximation of the exact blend, not a copy of it
+    assert 1e-4 < np.abs(r["mboit"] - r["exact"]).max() < 0.2
+
+
+def test_sandwich_partials_add_up():
+    """Fig. 6: three ranks of interleaved slices; the per-rank partial images
+    rendered with the global moments sum to the single-node MBOIT image."""
+    sc = small.sandwich_scene()
+    sc.views = [scenes.ortho_view(sc.dims, (0.3, 0.25, 0.92), 24, 24)]
+    r = oracle.render_grid(sc, want=("piece_color", "raw", "mboit"))
+    u = oracle.render_grid(_one_piece(sc), want=("raw", "mboit"))
+    np.testing.assert_allclose(r["piece_color"].sum(axis=1), u["raw"], atol=1e-12)
+    np.testing.assert_allclose(r["mboit"], u["mboit"], atol=1e-12)
+    for P in range(3):
+        assert r["piece_color"][:, P, 3].max() > 1e-3
+
+
+def test_empty_and_missing_rays():
+    """Rays that miss the domain produce zero moments and a zero image."""
+    sc = small.slab_scene()
+    sc.views = [small.axis_view(sc.dims, 4, 4, -10.0, 4.0, centre=(100.0, 100.0))]
+    r = oracle.render_grid(sc, want=("moments", "mboit", "exact", "nsamples"))
+    assert np.all(r["nsamples"] == 0)
+    assert np.all(r["moments"] == 0) and np.all(r["mboit"] == 0) and np.all(r["exact"] == 0)
