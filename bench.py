@@ -1,0 +1,339 @@
+"""Benchmark of the MBOIT puzzle-piece render on GB300.
+
+Workload (default): 512^3 float32 field (64 Gaussian blobs + 3-octave value
+noise), 64 jittered Morton pieces of 16^3-cell bricks, 2048x2048
+perspective view, step 0.5 voxel, 4 power moments in float32.
+
+One step = one frame: pass 1 (moments of all pieces, summed) + pass 2
+(transmittance reconstruction, blend, colour sum and renormalisation),
+replayed from a CUDA graph.  value = owned lattice samples per frame (each
+marched once per pass) / frame time, in Gsamples/s, summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on a bounded pixel sample of the same workload.  Under torchrun (N > 1)
+every rank renders its own replica (no data-path collective); rank 0 prints.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gsamples/s & ms/frame: batched mixed-prec vs plain FP32, RMSE vs FP64 oracle"
+UNIT = "Gsamples/s"
+# FP32 FLOPs per owned sample executed by the fused kernels' per-sample code
+# (position 6, trilinear 21, table coordinate 2, extinction lerp 3, warp 2,
+# moment update 9 for pass 1; pass 2 replaces the moment update by opacity 2,
+# colour lerps 9, moment-bound reconstruction 20 (outside case) and the
+# colour accumulation 9).  FMA = 2 FLOPs.
+FLOP_PASS1 = 43
+FLOP_PASS2 = 76
+# FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x
+# 2 FLOP x 2.070 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+KERNEL_SOURCES = ["paper_2501_12581_gb300/csrc/mboit_kernels.cu", "paper_2501_12581_gb300/csrc/mboit_device.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pass2_fused_blobs512_traffic.txt")
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per pass-2 launch from the committed ncu summary, or None
+    when the kernel sources changed since it was captured."""
+    try:
+        kv = dict(tok.split("=", 1) for tok in open(TRAFFIC_FILE).read().split() if "=" in tok)
+        if kv.get("kernel_sha") == kernel_hash():
+            return int(kv["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, flag in zip(names, p[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def sample_pixels(width, height, row_stride, col_stride):
+    ys, xs = np.meshgrid(np.arange(row_stride // 2, height, row_stride), np.arange(col_stride // 2, width, col_stride),
+                         indexing="ij")
+    return (ys * width + xs).ravel()
+
+
+def time_oracle(sc, pixels):
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.render_grid(sc, pixels=pixels, want=("mboit", "exact", "nsamples"))
+    dt = time.perf_counter() - t0
+    return r, dt
+
+
+def workload(name):
+    import scenes
+    if name == "blobs512":
+        return scenes.blobs512()
+    if name == "blobs64":
+        return scenes.blobs64()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def config_of(sc, name):
+    v = sc.views[0]
+    return {"workload": name, "field": "x".join(str(n) for n in sc.dims) + " float32",
+            "pieces": sc.n_pieces, "brick_cells": 1 << sc.brick_log2, "image": f"{v.width}x{v.height}",
+            "projection": "perspective" if v.projection else "orthographic", "step_voxels": sc.step,
+            "moments": "4 power, float32", "moment_bias": sc.moment_bias, "overestimation": sc.overestimation,
+            "l2": f"inputs larger than L2 ({sc.field.nbytes >> 20} MiB field re-read every frame)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    sc = workload(args.workload)
+    v = sc.views[0]
+    pix = sample_pixels(v.width, v.height, 32, 16) if args.workload == "blobs512" else sample_pixels(v.width, v.height, 4, 4)
+    for _ in range(args.warmup):
+        time_oracle(sc, pix[: max(1, pix.size // 8)])
+    times, samples = [], 0
+    for _ in range(args.steps):
+        r, dt = time_oracle(sc, pix)
+        times.append(dt)
+        samples = int(r["nsamples"].sum())
+    total = sum(times)
+    value = samples * args.steps / total / 1e9
+    sample_desc = f"{pix.size} pixels of the {v.width}x{v.height} frame (every 32nd row, 16th column), {samples} samples"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(sc, args.workload),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="blobs512", choices=["blobs512", "blobs64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-per-piece", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    import paper_2501_12581_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    __graft_entry__.build()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    sc = workload(args.workload)
+    vol = pkg.Volume(sc)
+    views = sc.views
+    v = views[0]
+    mom = pkg.Volume.moment_buffer(views)
+    rgba = pkg.Volume.color_buffer(views)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return ev0.elapsed_time(ev1) / steps
+
+    frame = lambda: vol.render_frame(views, mom, rgba)  # noqa: E731
+    for _ in range(args.warmup):
+        frame()
+    vol.synchronize()
+    with ClockSampler(local) as clk:
+        ms = timed(frame, args.steps)
+    vol.synchronize()
+    st = vol.stats()
+    samples = st["samples_pass1"]
+    ms_max = max_over_ranks(ms)
+    value = samples * world / (ms_max * 1e-3) / 1e9
+
+    # the two kernels of the frame, each timed alone on the launching stream
+    for _ in range(3):
+        vol.render_moments(views, mom)
+        vol.reconstruct_blend(views, mom, rgba, mode=pkg.MBOIT_COLOR_RESOLVED)
+    k = max(5, args.steps // 2)
+    ms_p1 = timed(lambda: vol.render_moments(views, mom), k)
+    ms_p2 = timed(lambda: vol.reconstruct_blend(views, mom, rgba, mode=pkg.MBOIT_COLOR_RESOLVED), k)
+    vol.synchronize()
+    achieved = FLOP_PASS2 * samples / (ms_p2 * 1e-3) / 1e12
+    traffic = measured_traffic()
+    roofline = {"bound": "alu", "kernel": "k_pass2_fused (pass 2: reconstruct + blend + resolve)",
+                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": traffic, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "flop_per_sample": FLOP_PASS2, "launch_ms": ms_p2,
+                "pass1": {"launch_ms": ms_p1, "flop_per_sample": FLOP_PASS1,
+                          "achieved_tflops": FLOP_PASS1 * samples / (ms_p1 * 1e-3) / 1e12}}
+
+    # the plain per-piece FP32 form (one launch per piece and pass, K images summed)
+    per_piece = None
+    if not args.no_per_piece:
+        K = sc.n_pieces
+        per_m = pkg.Volume.moment_buffer(views, K)
+        per_c = pkg.Volume.color_buffer(views, K)
+        glob = pkg.Volume.moment_buffer(views)
+
+        def plain():
+            vol.render_moments(views, per_m, mode=pkg.MBOIT_MOMENTS_PER_PIECE)
+            vol.composite(pkg.MBOIT_OP_MOMENTS_SUM, v.width, v.height, 1, K, per_m, glob)
+            vol.reconstruct_blend(views, glob, per_c, mode=pkg.MBOIT_COLOR_PER_PIECE)
+            vol.composite(pkg.MBOIT_OP_COLOR_SUM_RESOLVE, v.width, v.height, 1, K, per_c, rgba, glob)
+        plain()
+        ms_pp = timed(plain, max(3, args.steps // 6))
+        vol.synchronize()
+        per_piece = {"ms_per_frame": ms_pp, "gsamples_per_s": samples / (ms_pp * 1e-3) / 1e9,
+                     "launches_per_frame": 2 * K + 2, "speedup_of_batched": ms_pp / ms}
+        del per_m, per_c, glob
+        torch.cuda.empty_cache()
+        frame()
+
+    # end to end through the host API: field upload, frame, image download
+    field_host = torch.from_numpy(np.ascontiguousarray(sc.field)).pin_memory()
+    rgba_host = torch.empty(rgba.numel(), dtype=torch.float32).pin_memory()
+    e2e_step = lambda: pkg.mboit_render_frame_host(vol.handle, field_host, views, mom, rgba, rgba_host)  # noqa: E731
+    e2e_step()
+    t0 = time.perf_counter()
+    barrier()
+    for _ in range(max(3, args.steps // 3)):
+        e2e_step()
+    barrier()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / max(3, args.steps // 3))
+    e2e = {"value": samples * world / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": int(sc.field.nbytes), "d2h_bytes_per_step": int(rgba_host.numel() * 4)}
+
+    # parity on a pixel sample and the oracle's own speed (rank 0, one GPU)
+    cpu_baseline, quality = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        frame()
+        vol.synchronize()
+        pix = sample_pixels(v.width, v.height, 8, 4) if args.workload == "blobs512" else sample_pixels(v.width, v.height, 1, 1)
+        r, dt = time_oracle(sc, pix)
+        ns = int(r["nsamples"].sum())
+        got = rgba.view(-1, 4)[torch.from_numpy(pix).cuda()].double().cpu().numpy()
+        d = got - r["mboit"]
+        quality = {"pixels": int(pix.size), "max_abs_vs_oracle": float(np.abs(d).max()),
+                   "rmse_vs_oracle": float(np.sqrt((d ** 2).mean())),
+                   "oracle_mboit_vs_exact_rmse": float(np.sqrt(((r["mboit"] - r["exact"]) ** 2).mean())),
+                   "oracle_mboit_vs_exact_max": float(np.abs(r["mboit"] - r["exact"]).max())}
+        cpu_baseline = {"value": ns / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                        "sample": f"{pix.size} pixels (every 8th row, 4th column) of the frame, {ns} samples, "
+                                  f"{dt:.1f} s, FP64 single thread"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": dict(config_of(sc, args.workload), parallelism="replicas" if world > 1 else "single",
+                          form="batched: 2 persistent kernels per frame, CUDA graph"),
+           "samples_per_frame": samples, "ms_per_frame": ms_max, "per_piece_fp32": per_piece,
+           "quality": quality, "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
+           "gpu_launches": 2 * args.steps, "clocks": clk.summary()}
+    vol.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * mboit.h -- C ABI of the GB300 library for Approximate Puzzlepiece
+ * Compositing: the two-pass moment-based order-independent transparency
+ * (MBOIT) volume render of non-convex subdomains ("puzzle pieces").
+ *
+ * Method (arXiv 2501.12581):
+ *   Sec. 4.1 / Alg. 2   pass 1: every piece ray-marches its own samples and
+ *                       accumulates per-pixel power moments of the warped
+ *                       depth, b_j += absorbance * z^j (j = 0..4);
+ *   Sec. 4.1            the per-piece moment images are summed
+ *                       (the paper's MPI_Allreduce add);
+ *   Sec. 4.2 / Alg. 3   pass 2: every piece re-marches its samples, gets the
+ *                       transmittance T(z) from the summed moments (Hankel /
+ *                       Cholesky moment bound with bias) and adds
+ *                       T * alpha * (r, g, b, 1);
+ *   Sec. 4.2, 4.3       the colour images are summed (MPI_Reduce add) and
+ *                       renormalised so that total opacity = 1 - e^-b0.
+ * On one GPU all pieces live on the device; both reductions are on-device.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an mboit_status; MBOIT_OK = 0.  On failure
+ *     mboit_last_error() returns a message (thread-local, valid until the
+ *     next call on the same thread).  Arguments are validated before any
+ *     work is enqueued; nothing is enqueued when a call fails validation.
+ *   - "device" pointers are CUDA global-memory addresses on the volume's
+ *     device; "host" pointers are ordinary CPU memory.  The library never
+ *     frees memory it did not allocate.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Render calls are asynchronous on that stream; errors raised
+ *     inside kernels (a wait limit or an index check) are reported by
+ *     mboit_synchronize().
+ *   - Images are row-major, pixel index y * width + x, x to the right.
+ *   - Moment images: per (view[, piece]) one slab of 20 * P bytes, P = width *
+ *     height rounded up to a multiple of 4: b0 as P float32, then (b1, b2,
+ *     b3, b4) as P float4 (16-byte aligned).  mboit_moment_image_bytes()
+ *     gives the slab size.
+ *   - Colour images: float32 RGBA [height][width][4] per (view[, piece]),
+ *     premultiplied (sum of T * alpha * (r, g, b) and sum of T * alpha).
+ */
+#ifndef MBOIT_H
+#define MBOIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MBOIT_API __attribute__((visibility("default")))
+#else
+#define MBOIT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MBOIT_OK = 0,
+    MBOIT_ERR_INVALID_ARG = 1,
+    MBOIT_ERR_OUT_OF_MEMORY = 2,
+    MBOIT_ERR_CUDA = 3,
+    MBOIT_ERR_UNSUPPORTED = 4,
+    MBOIT_ERR_STATE = 5,
+    MBOIT_ERR_TIMEOUT = 6,
+    MBOIT_ERR_DEVICE_ASSERT = 7
+} mboit_status;
+
+typedef enum { MBOIT_GRID = 0, MBOIT_AMR = 1, MBOIT_TET = 2 } mboit_volume_kind;
+typedef enum { MBOIT_POWER4 = 0 } mboit_moment_set;
+typedef enum { MBOIT_STORE_F32 = 0 } mboit_storage;
+typedef enum { MBOIT_ORTHO = 0, MBOIT_PERSPECTIVE = 1 } mboit_projection;
+
+/* pass-1 output layout */
+typedef enum {
+    MBOIT_MOMENTS_PER_PIECE = 0, /* one slab per (view, selected piece): the per-rank local images */
+    MBOIT_MOMENTS_REDUCED = 1    /* one slab per view: pieces summed on the fly */
+} mboit_moment_out;
+
+/* pass-2 output layout */
+typedef enum {
+    MBOIT_COLOR_PER_PIECE = 0, /* one RGBA image per (view, selected piece): the per-rank partials */
+    MBOIT_COLOR_REDUCED = 1,   /* one RGBA image per view: partials summed on the fly */
+    MBOIT_COLOR_RESOLVED = 2   /* one RGBA image per view, summed and renormalised (final image) */
+} mboit_color_out;
+
+typedef enum {
+    MBOIT_OP_MOMENTS_SUM = 0,      /* n_inputs moment slabs per view -> one (the Allreduce add) */
+    MBOIT_OP_COLOR_SUM_RESOLVE = 1 /* n_inputs colour images per view -> final RGBA (the Reduce add) */
+} mboit_composite_op;
+
+/* volume flags */
+#define MBOIT_FLAG_RAW_SUM 0x1u       /* resolve without renormalisation: out = sum T*alpha*(c, 1) */
+#define MBOIT_FLAG_DETERMINISTIC 0x2u /* accepted; every path here is run-to-run deterministic */
+
+typedef struct mboit_volume_s* mboit_volume;
+
+typedef struct {
+    int32_t kind;               /* mboit_volume_kind; MBOIT_GRID is implemented */
+    int32_t moment_set;         /* mboit_moment_set */
+    int32_t storage;            /* mboit_storage */
+    uint32_t flags;             /* MBOIT_FLAG_* */
+    /* regular grid: float32 vertex values field[z][y][x] (device pointer,
+     * BORROWED: it must stay valid and unchanged while the volume renders).
+     * Vertex (x, y, z) sits at point (x, y, z); the domain is
+     * [0, nx-1] x [0, ny-1] x [0, nz-1]; cells are half-open unit cubes. */
+    const float* field;
+    int32_t dims[3];            /* nx, ny, nz >= 2 */
+    int32_t brick_log2;         /* bricks are cubes of 2^brick_log2 cells (0..7) */
+    /* transfer function: 256 entries of (r, g, b, alpha) float32, HOST
+     * pointer, COPIED.  alpha in [0, 1) is the opacity of one voxel of
+     * material; the value range [tf_range[0], tf_range[1]] maps linearly onto
+     * the table, values outside are clamped. */
+    const float* tf_rgba;
+    float tf_range[2];
+    float step;                 /* sample spacing in voxels, a power of two (Sec. 5.3: fixed step) */
+    float moment_bias;          /* mix amount of the bias vector (Alg. 3 "mix"), in [0, 1) */
+    float overestimation;       /* weight of the sample's own depth (Alg. 3), paper: 0.3 */
+    float absorbance_max;       /* ABSORBANCE_MAX_VALUE of Alg. 2, > 0 */
+} mboit_volume_desc;
+
+typedef struct {
+    float eye[3];               /* ortho: centre of the view window; perspective: eye point */
+    float u[3], v[3], w[3];     /* right, up, forward (w need not be unit for ortho: ray direction = w) */
+    int32_t width, height;
+    int32_t projection;         /* mboit_projection */
+    int32_t reserved;
+    /* ortho: window extents along u and v; perspective: tan(fov/2)*aspect and tan(fov/2) */
+    float scale_u, scale_v;
+    /* the log-depth warp maps ray parameter t in [near, far] to [-1, 1]
+     * (Alg. 2 logDepthWarp); must bracket the volume, 0 < near < far */
+    float near, far;
+} mboit_view;
+
+typedef struct {
+    int64_t samples_pass1;      /* owned samples marched by the last render_moments */
+    int64_t samples_pass2;      /* owned samples marched by the last reconstruct_blend */
+    int64_t singular_pixels;    /* pixels of the last pass 2 whose Hankel matrix took a 1- or 2-atom branch */
+    int32_t n_pieces;
+    int32_t device;
+} mboit_stats;
+
+/* Message of the last failing call on this thread ("" if none). */
+MBOIT_API const char* mboit_last_error(void);
+
+/* Bytes of one moment slab for a width x height image (20 * P, P = w*h rounded up to 4). */
+MBOIT_API size_t mboit_moment_image_bytes(int32_t width, int32_t height, int32_t moment_set, int32_t storage);
+
+/* Creates a volume on the current CUDA device.  Validates the descriptor,
+ * copies the transfer function (converted to extinction sigma = -ln(1-alpha)
+ * per voxel), allocates the brick-ownership table.  The field stays
+ * borrowed.  *out is set only on success. */
+MBOIT_API mboit_status mboit_create_volume(const mboit_volume_desc* desc, mboit_volume* out);
+
+/* Releases everything the volume owns (not the field).  NULL is a no-op.
+ * Synchronises the volume's device first. */
+MBOIT_API mboit_status mboit_destroy_volume(mboit_volume v);
+
+/* Adds one piece: `ids` lists brick ids ((bz*nby + by)*nbx + bx) of the
+ * piece; copied.  `ids_on_device` = 1 if ids is a device pointer.  Pieces
+ * must not overlap (Sec. 6: reconstruction requires non-overlapping
+ * volumes); a brick already owned -> MBOIT_ERR_INVALID_ARG and the volume is
+ * unchanged.  Piece ids are 0, 1, ... in call order.  Bricks that belong to
+ * no piece are never sampled.  Synchronous. */
+MBOIT_API mboit_status mboit_add_piece(mboit_volume v, const int32_t* ids, int64_t n, int32_t ids_on_device,
+                             int32_t* piece_id_out);
+
+/* Pass 1 (Sec. 4.1, Alg. 2).  views: HOST array of n_views views.  pieces:
+ * HOST array of n_pieces selected piece ids, or NULL = all pieces (then
+ * n_pieces is ignored).  moments: DEVICE buffer of n_views * S bytes
+ * (REDUCED) or n_views * n_pieces * S bytes (PER_PIECE), S =
+ * mboit_moment_image_bytes(); fully overwritten. */
+MBOIT_API mboit_status mboit_render_moments(mboit_volume v, const mboit_view* views, int32_t n_views,
+                                  const int32_t* pieces, int32_t n_pieces, int32_t mode, void* moments,
+                                  void* stream);
+
+/* Pass 2 (Sec. 4.2, Alg. 1 loop 2, Alg. 3).  global_moments: DEVICE
+ * buffer of n_views REDUCED slabs (the summed moments of ALL pieces).
+ * color: DEVICE float32 RGBA, n_views (REDUCED, RESOLVED) or n_views *
+ * n_pieces (PER_PIECE) images; fully overwritten.  RESOLVED applies the
+ * renormalisation of mboit_composite with a zero background. */
+MBOIT_API mboit_status mboit_reconstruct_blend(mboit_volume v, const mboit_view* views, int32_t n_views,
+                                     const int32_t* pieces, int32_t n_pieces, const void* global_moments,
+                                     int32_t mode, float* color, void* stream);
+
+/* Image-space reductions (the paper's Allreduce add and Reduce add).
+ *   MOMENTS_SUM: in = n_views * n_inputs moment slabs of width x height,
+ *     out = n_views slabs; compensated (Neumaier) float32 sum in input order.
+ *   COLOR_SUM_RESOLVE: in = n_views * n_inputs RGBA images; out = n_views RGBA
+ *     images: C = sum of inputs (compensated); alpha = 1 - e^-b0 from
+ *     global_moments; rgb = C.rgb * alpha / C.a (0 if C.a = 0); then
+ *     out += e^-b0 * bg.  With MBOIT_FLAG_RAW_SUM on the volume, out = C
+ *     (the plain sum of Alg. 1) and global_moments may be NULL.
+ * All buffers are DEVICE pointers; bg is a HOST float[4] or NULL (zero). */
+MBOIT_API mboit_status mboit_composite(mboit_volume v, int32_t op, int32_t width, int32_t height, int32_t n_views,
+                             int32_t n_inputs, const void* in, void* out, const void* global_moments,
+                             const float* bg, void* stream);
+
+/* Whole frame, batched: pass 1 (REDUCED) -> pass 2 (RESOLVED) for all pieces
+ * and all views, recorded once into a CUDA graph per (views, stream kind)
+ * and replayed.  moments_scratch: DEVICE buffer of n_views moment slabs
+ * (kept, so the caller can inspect the global moments); rgba: DEVICE
+ * float32 RGBA n_views images. */
+MBOIT_API mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch,
+                                float* rgba, void* stream);
+
+/* End-to-end frame from HOST memory: copies `field_host` (nx*ny*nz
+ * float32, preferably pinned) into the volume's borrowed device field,
+ * renders the frame as mboit_render_frame, and copies the RGBA images to
+ * `rgba_host` (n_views * width * height * 4 float32).  Returns after the
+ * image has arrived on the host. */
+MBOIT_API mboit_status mboit_render_frame_host(mboit_volume v, const float* field_host, const mboit_view* views,
+                                     int32_t n_views, void* moments_scratch, float* rgba_device,
+                                     float* rgba_host, void* stream);
+
+/* Waits for `stream` and reports kernel-side errors recorded by this
+ * volume's launches (MBOIT_ERR_TIMEOUT / MBOIT_ERR_DEVICE_ASSERT). */
+MBOIT_API mboit_status mboit_synchronize(mboit_volume v, void* stream);
+
+/* Counters of the last passes (synchronises the stream of the last render). */
+MBOIT_API mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,319 @@
+"""GB300 MBOIT puzzle-piece renderer (Approximate Puzzlepiece Compositing,
+arXiv 2501.12581): Python binding of the C ABI in ``include/mboit.h``.
+
+The functions ``mboit_*`` below have the names of the C entry points and only
+marshal arguments (torch CUDA tensors -> device pointers, the current torch
+stream -> cudaStream_t, views -> ``mboit_view`` structs); every step of the
+render runs in the CUDA library ``_lib/libmboit.so``.  There is no CPU path:
+if the library is missing or fails to load, every call raises.
+
+``Volume`` wraps a volume handle for the common case of a regular grid built
+from a ``scenes.GridScene``-like object.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmboit.so")
+
+MBOIT_OK = 0
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "UNSUPPORTED", 5: "STATE",
+                6: "TIMEOUT", 7: "DEVICE_ASSERT"}
+MBOIT_GRID, MBOIT_AMR, MBOIT_TET = 0, 1, 2
+MBOIT_POWER4 = 0
+MBOIT_STORE_F32 = 0
+MBOIT_ORTHO, MBOIT_PERSPECTIVE = 0, 1
+MBOIT_MOMENTS_PER_PIECE, MBOIT_MOMENTS_REDUCED = 0, 1
+MBOIT_COLOR_PER_PIECE, MBOIT_COLOR_REDUCED, MBOIT_COLOR_RESOLVED = 0, 1, 2
+MBOIT_OP_MOMENTS_SUM, MBOIT_OP_COLOR_SUM_RESOLVE = 0, 1
+MBOIT_FLAG_RAW_SUM, MBOIT_FLAG_DETERMINISTIC = 0x1, 0x2
+
+EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume", "mboit_destroy_volume",
+            "mboit_add_piece", "mboit_render_moments", "mboit_reconstruct_blend", "mboit_composite",
+            "mboit_render_frame", "mboit_render_frame_host", "mboit_synchronize", "mboit_get_stats"]
+
+
+class MboitError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class mboit_view(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("u", ctypes.c_float * 3), ("v", ctypes.c_float * 3),
+                ("w", ctypes.c_float * 3), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("projection", ctypes.c_int32), ("reserved", ctypes.c_int32), ("scale_u", ctypes.c_float),
+                ("scale_v", ctypes.c_float), ("near", ctypes.c_float), ("far", ctypes.c_float)]
+
+
+class mboit_volume_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("moment_set", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("field", ctypes.c_void_p), ("dims", ctypes.c_int32 * 3),
+                ("brick_log2", ctypes.c_int32), ("tf_rgba", ctypes.c_void_p), ("tf_range", ctypes.c_float * 2),
+                ("step", ctypes.c_float), ("moment_bias", ctypes.c_float), ("overestimation", ctypes.c_float),
+                ("absorbance_max", ctypes.c_float)]
+
+
+class mboit_stats(ctypes.Structure):
+    _fields_ = [("samples_pass1", ctypes.c_int64), ("samples_pass2", ctypes.c_int64),
+                ("singular_pixels", ctypes.c_int64), ("n_pieces", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Loads libmboit.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise MboitError(3, f"CUDA library {path} is not built; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "mboit_last_error": (ctypes.c_char_p, []),
+        "mboit_moment_image_bytes": (ctypes.c_size_t, [I32, I32, I32, I32]),
+        "mboit_create_volume": (ctypes.c_int, [P, P]),
+        "mboit_destroy_volume": (ctypes.c_int, [P]),
+        "mboit_add_piece": (ctypes.c_int, [P, P, I64, I32, P]),
+        "mboit_render_moments": (ctypes.c_int, [P, P, I32, P, I32, I32, P, P]),
+        "mboit_reconstruct_blend": (ctypes.c_int, [P, P, I32, P, I32, P, I32, P, P]),
+        "mboit_composite": (ctypes.c_int, [P, I32, I32, I32, I32, I32, P, P, P, P, P]),
+        "mboit_render_frame": (ctypes.c_int, [P, P, I32, P, P, P]),
+        "mboit_render_frame_host": (ctypes.c_int, [P, P, P, I32, P, P, P, P]),
+        "mboit_synchronize": (ctypes.c_int, [P, P]),
+        "mboit_get_stats": (ctypes.c_int, [P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != MBOIT_OK:
+        raise MboitError(status, load_library().mboit_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    """Device/host address of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensors passed to libmboit must be contiguous")
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def make_view(v):
+    """``scenes.View``-like object (or an mboit_view) -> mboit_view."""
+    if isinstance(v, mboit_view):
+        return v
+    s = mboit_view()
+    for name in ("eye", "u", "v", "w"):
+        getattr(s, name)[:] = [float(x) for x in np.asarray(getattr(v, name), dtype=np.float32)]
+    s.width, s.height, s.projection = int(v.width), int(v.height), int(v.projection)
+    s.scale_u, s.scale_v = float(v.scale_u), float(v.scale_v)
+    s.near, s.far = float(v.near), float(v.far)
+    return s
+
+
+def _views(views):
+    views = list(views)
+    arr = (mboit_view * len(views))()
+    for i, v in enumerate(views):
+        arr[i] = make_view(v)
+    return arr, len(views)
+
+
+def _pieces(pieces):
+    if pieces is None:
+        return None, 0, None
+    a = np.ascontiguousarray(np.asarray(list(pieces), dtype=np.int32))
+    return a.ctypes.data, a.size, a
+
+
+# ---------------------------------------------------------------------------
+# the C entry points, same names
+
+
+def mboit_last_error():
+    return load_library().mboit_last_error().decode(errors="replace")
+
+
+def mboit_moment_image_bytes(width, height, moment_set=MBOIT_POWER4, storage=MBOIT_STORE_F32):
+    return int(load_library().mboit_moment_image_bytes(width, height, moment_set, storage))
+
+
+def mboit_create_volume(desc):
+    h = ctypes.c_void_p()
+    _check(load_library().mboit_create_volume(ctypes.byref(desc), ctypes.byref(h)))
+    return h.value
+
+
+def mboit_destroy_volume(v):
+    _check(load_library().mboit_destroy_volume(v))
+
+
+def mboit_add_piece(v, ids, ids_on_device=None):
+    if ids_on_device is None:
+        ids_on_device = bool(hasattr(ids, "is_cuda") and ids.is_cuda)
+    keep = ids if hasattr(ids, "data_ptr") else np.ascontiguousarray(ids, dtype=np.int32)
+    if hasattr(keep, "dtype") and str(keep.dtype) not in ("int32", "torch.int32"):
+        raise ValueError("brick ids must be int32")
+    out = ctypes.c_int32(-1)
+    n = keep.numel() if hasattr(keep, "numel") else keep.size
+    _check(load_library().mboit_add_piece(v, _ptr(keep), n, int(ids_on_device), ctypes.byref(out)))
+    return out.value
+
+
+def mboit_render_moments(v, views, moments, pieces=None, mode=MBOIT_MOMENTS_REDUCED, stream=None):
+    arr, n = _views(views)
+    pp, npc, _keep = _pieces(pieces)
+    _check(load_library().mboit_render_moments(v, arr, n, pp, npc, mode, _ptr(moments), _stream(stream)))
+
+
+def mboit_reconstruct_blend(v, views, global_moments, color, pieces=None, mode=MBOIT_COLOR_RESOLVED, stream=None):
+    arr, n = _views(views)
+    pp, npc, _keep = _pieces(pieces)
+    _check(load_library().mboit_reconstruct_blend(v, arr, n, pp, npc, _ptr(global_moments), mode, _ptr(color),
+                                                  _stream(stream)))
+
+
+def mboit_composite(v, op, width, height, n_views, n_inputs, inp, out, global_moments=None, bg=None, stream=None):
+    bgp = None
+    if bg is not None:
+        bga = (ctypes.c_float * 4)(*[float(x) for x in bg])
+        bgp = ctypes.cast(bga, ctypes.c_void_p).value
+    _check(load_library().mboit_composite(v, op, width, height, n_views, n_inputs, _ptr(inp), _ptr(out),
+                                          _ptr(global_moments), bgp, _stream(stream)))
+
+
+def mboit_render_frame(v, views, moments_scratch, rgba, stream=None):
+    arr, n = _views(views)
+    _check(load_library().mboit_render_frame(v, arr, n, _ptr(moments_scratch), _ptr(rgba), _stream(stream)))
+
+
+def mboit_render_frame_host(v, field_host, views, moments_scratch, rgba_device, rgba_host, stream=None):
+    arr, n = _views(views)
+    _check(load_library().mboit_render_frame_host(v, _ptr(field_host), arr, n, _ptr(moments_scratch),
+                                                  _ptr(rgba_device), _ptr(rgba_host), _stream(stream)))
+
+
+def mboit_synchronize(v, stream=None):
+    _check(load_library().mboit_synchronize(v, _stream(stream)))
+
+
+def mboit_get_stats(v):
+    s = mboit_stats()
+    _check(load_library().mboit_get_stats(v, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in mboit_stats._fields_}
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+
+
+class Volume:
+    """A regular-grid volume on the current CUDA device, built from a scene
+    with ``field``, ``brick_log2``, ``piece_of_brick``, ``n_pieces``, ``tf``,
+    ``tf_range``, ``step``, ``moment_bias``, ``overestimation``,
+    ``absorbance_max``.  Keeps the device field tensor alive."""
+
+    def __init__(self, scene, field=None, flags=0):
+        import torch
+        load_library()
+        self.scene = scene
+        self.field = field if field is not None else torch.from_numpy(np.ascontiguousarray(scene.field)).cuda()
+        tf = np.ascontiguousarray(scene.tf, dtype=np.float32)
+        d = mboit_volume_desc()
+        d.kind, d.moment_set, d.storage, d.flags = MBOIT_GRID, MBOIT_POWER4, MBOIT_STORE_F32, flags
+        d.field = self.field.data_ptr()
+        nz, ny, nx = scene.field.shape
+        d.dims[:] = [nx, ny, nz]
+        d.brick_log2 = scene.brick_log2
+        d.tf_rgba = tf.ctypes.data
+        d.tf_range[:] = [float(scene.tf_range[0]), float(scene.tf_range[1])]
+        d.step, d.moment_bias = float(scene.step), float(scene.moment_bias)
+        d.overestimation, d.absorbance_max = float(scene.overestimation), float(scene.absorbance_max)
+        self.handle = mboit_create_volume(d)
+        pob = np.asarray(scene.piece_of_brick)
+        for p in range(scene.n_pieces):
+            mboit_add_piece(self.handle, np.nonzero(pob == p)[0].astype(np.int32))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mboit_destroy_volume(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def moment_buffer(views, n_slots=1):
+        import torch
+        total = sum(mboit_moment_image_bytes(v.width, v.height) for v in views) * n_slots
+        return torch.zeros(total // 4, dtype=torch.float32, device="cuda")
+
+    @staticmethod
+    def color_buffer(views, n_slots=1):
+        import torch
+        total = sum(v.width * v.height * 4 for v in views) * n_slots
+        return torch.zeros(total, dtype=torch.float32, device="cuda")
+
+    @staticmethod
+    def unpack_moments(buf, views, n_slots=1):
+        """Device slab buffer -> list per view of [n_slots][H*W][5] float32 tensors."""
+        out, off = [], 0
+        for v in views:
+            npx = v.width * v.height
+            P = (npx + 3) // 4 * 4
+            slabs = []
+            for j in range(n_slots):
+                s = buf[off + j * 5 * P: off + (j + 1) * 5 * P]
+                slabs.append(torch_cat_moments(s, P, npx))
+            out.append(slabs)
+            off += n_slots * 5 * P
+        return out
+
+    def render_moments(self, views, moments, pieces=None, mode=MBOIT_MOMENTS_REDUCED, stream=None):
+        mboit_render_moments(self.handle, views, moments, pieces, mode, stream)
+
+    def reconstruct_blend(self, views, global_moments, color, pieces=None, mode=MBOIT_COLOR_RESOLVED, stream=None):
+        mboit_reconstruct_blend(self.handle, views, global_moments, color, pieces, mode, stream)
+
+    def composite(self, op, width, height, n_views, n_inputs, inp, out, global_moments=None, bg=None, stream=None):
+        mboit_composite(self.handle, op, width, height, n_views, n_inputs, inp, out, global_moments, bg, stream)
+
+    def render_frame(self, views, moments_scratch, rgba, stream=None):
+        mboit_render_frame(self.handle, views, moments_scratch, rgba, stream)
+
+    def synchronize(self, stream=None):
+        mboit_synchronize(self.handle, stream)
+
+    def stats(self):
+        return mboit_get_stats(self.handle)
+
+
+def torch_cat_moments(slab, P, npx):
+    """One moment slab (5*P floats: b0 plane, then float4 plane) -> [npx][5]."""
+    import torch
+    b0 = slab[:P][:npx, None]
+    rest = slab[P:5 * P].view(P, 4)[:npx]
+    return torch.cat([b0, rest], dim=1)

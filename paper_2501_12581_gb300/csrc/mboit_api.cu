@@ -1,0 +1,561 @@
+// C ABI of the MBOIT puzzle-piece renderer (see include/mboit.h).
+//
+// Host side only: argument validation, the volume registry (transfer
+// function, brick ownership, piece boxes), view tables, CUDA-graph capture of
+// the batched frame, and error reporting.  Every step of the render runs in
+// the kernels of mboit_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mboit.h"
+#include "mboit_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+mboit_status fail(mboit_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define MB_CUDA(call)                                                                            \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return fail(MBOIT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Makes the volume's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite3(const float* a) { return std::isfinite(a[0]) && std::isfinite(a[1]) && std::isfinite(a[2]); }
+
+struct GraphEntry {
+    std::vector<char> key;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct mboit_volume_s {
+    int device = 0;
+    mboit_volume_desc desc{};
+    mb::GridD grid{};
+    int64_t nbricks = 0;
+    size_t field_bytes = 0;
+    float4* d_tf = nullptr;
+    int32_t* d_pob = nullptr;
+    uint8_t* d_sel = nullptr;
+    mb::Counters* d_ctr = nullptr;
+    std::vector<int32_t> pob;
+    std::vector<mb::PieceBox> boxes;
+    int64_t owned = 0;
+    std::vector<uint8_t> sel_host;
+    bool sel_uploaded = false;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<GraphEntry> graphs;
+    std::mutex mu;
+};
+
+namespace {
+
+void drop_graphs(mboit_volume v) {
+    for (auto& g : v->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    v->graphs.clear();
+}
+
+mboit_status check_volume(mboit_volume v) {
+    if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
+    if (v->boxes.empty()) return fail(MBOIT_ERR_STATE, "volume has no pieces (mboit_add_piece first)");
+    return MBOIT_OK;
+}
+
+// Validates views and lays out tiles and output offsets.
+mboit_status build_views(const mboit_view* views, int32_t n_views, mb::ViewTable& vt) {
+    if (!views) return fail(MBOIT_ERR_INVALID_ARG, "views is NULL");
+    if (n_views < 1 || n_views > mb::kMaxViews)
+        return fail(MBOIT_ERR_INVALID_ARG, "n_views must be in [1, " + std::to_string(mb::kMaxViews) + "]");
+    std::memset(&vt, 0, sizeof vt);
+    vt.n = n_views;
+    int64_t tiles = 0, moff = 0, coff = 0;
+    for (int i = 0; i < n_views; ++i) {
+        const mboit_view& V = views[i];
+        const std::string at = "view " + std::to_string(i) + ": ";
+        if (V.width < 1 || V.height < 1 || V.width > 32768 || V.height > 32768)
+            return fail(MBOIT_ERR_INVALID_ARG, at + "width and height must be in [1, 32768]");
+        if (V.projection != MBOIT_ORTHO && V.projection != MBOIT_PERSPECTIVE)
+            return fail(MBOIT_ERR_INVALID_ARG, at + "unknown projection");
+        if (!finite3(V.eye) || !finite3(V.u) || !finite3(V.v) || !finite3(V.w) || !std::isfinite(V.scale_u) ||
+            !std::isfinite(V.scale_v))
+            return fail(MBOIT_ERR_INVALID_ARG, at + "non-finite camera parameter");
+        if (V.w[0] == 0.0f && V.w[1] == 0.0f && V.w[2] == 0.0f)
+            return fail(MBOIT_ERR_INVALID_ARG, at + "w (ray direction) is zero");
+        if (!(V.near > 0.0f) || !(V.far > V.near) || !std::isfinite(V.far))
+            return fail(MBOIT_ERR_INVALID_ARG, at + "need 0 < near < far");
+        mb::ViewSlot& S = vt.s[i];
+        for (int c = 0; c < 3; ++c) {
+            S.v.eye[c] = V.eye[c];
+            S.v.u[c] = V.u[c];
+            S.v.v[c] = V.v[c];
+            S.v.w[c] = V.w[c];
+        }
+        S.v.width = V.width;
+        S.v.height = V.height;
+        S.v.projection = V.projection;
+        S.v.scale_u = V.scale_u;
+        S.v.scale_v = V.scale_v;
+        // z = 2 (ln t - ln n) / (ln f - ln n) - 1 = warp_a * log2(t) + warp_b
+        const double ln_n = std::log((double)V.near), ln_f = std::log((double)V.far);
+        S.v.warp_a = (float)(2.0 * std::log(2.0) / (ln_f - ln_n));
+        S.v.warp_b = (float)(-2.0 * ln_n / (ln_f - ln_n) - 1.0);
+        S.ntx = (V.width + mb::kTileW - 1) / mb::kTileW;
+        const int64_t nty = (V.height + mb::kTileH - 1) / mb::kTileH;
+        S.tile_base = (int32_t)tiles;
+        tiles += (int64_t)S.ntx * nty;
+        S.plane = (int32_t)((((int64_t)V.width * V.height) + 3) / 4 * 4);
+        S.moment_off = moff;
+        S.color_off = coff;
+        moff += (int64_t)20 * S.plane;
+        coff += (int64_t)4 * V.width * V.height;
+    }
+    if (tiles >= (int64_t)1 << 31) return fail(MBOIT_ERR_INVALID_ARG, "too many pixels in one call");
+    vt.total_tiles = (int32_t)tiles;
+    return MBOIT_OK;
+}
+
+// Image-only table for the composite op (offsets of n_views equal images).
+mboit_status build_images(int32_t width, int32_t height, int32_t n_views, mb::ViewTable& vt) {
+    if (n_views < 1 || n_views > mb::kMaxViews) return fail(MBOIT_ERR_INVALID_ARG, "n_views out of range");
+    if (width < 1 || height < 1 || width > 32768 || height > 32768)
+        return fail(MBOIT_ERR_INVALID_ARG, "width and height must be in [1, 32768]");
+    std::memset(&vt, 0, sizeof vt);
+    vt.n = n_views;
+    for (int i = 0; i < n_views; ++i) {
+        mb::ViewSlot& S = vt.s[i];
+        S.v.width = width;
+        S.v.height = height;
+        S.plane = (int32_t)((((int64_t)width * height) + 3) / 4 * 4);
+        S.moment_off = (int64_t)i * 20 * S.plane;
+        S.color_off = (int64_t)i * 4 * width * height;
+    }
+    return MBOIT_OK;
+}
+
+// Piece list -> selection; returns the brick mask to use (nullptr = every brick).
+mboit_status select_pieces(mboit_volume v, const int32_t* pieces, int32_t n_pieces, std::vector<int32_t>& list,
+                           const uint8_t** mask) {
+    const int32_t K = (int32_t)v->boxes.size();
+    list.clear();
+    if (!pieces) {
+        for (int32_t p = 0; p < K; ++p) list.push_back(p);
+    } else {
+        if (n_pieces < 1) return fail(MBOIT_ERR_INVALID_ARG, "n_pieces must be >= 1 when pieces is given");
+        for (int32_t i = 0; i < n_pieces; ++i) {
+            if (pieces[i] < 0 || pieces[i] >= K)
+                return fail(MBOIT_ERR_INVALID_ARG, "piece id " + std::to_string(pieces[i]) + " out of range");
+            list.push_back(pieces[i]);
+        }
+    }
+    std::vector<uint8_t> want_piece(K, 0);
+    for (int32_t p : list) want_piece[p] = 1;
+    bool all = true;
+    for (int32_t p = 0; p < K; ++p) all = all && want_piece[p];
+    if (all && v->owned == v->nbricks) {
+        *mask = nullptr;
+        return MBOIT_OK;
+    }
+    std::vector<uint8_t> sel((size_t)v->nbricks);
+    for (int64_t b = 0; b < v->nbricks; ++b) sel[b] = v->pob[b] >= 0 && want_piece[v->pob[b]];
+    if (!v->sel_uploaded || sel != v->sel_host) {
+        // the mask is read by kernels still in flight: wait for them first
+        MB_CUDA(cudaDeviceSynchronize());
+        MB_CUDA(cudaMemcpy(v->d_sel, sel.data(), sel.size(), cudaMemcpyHostToDevice));
+        v->sel_host.swap(sel);
+        v->sel_uploaded = true;
+        drop_graphs(v);
+    }
+    *mask = v->d_sel;
+    return MBOIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mboit_last_error(void) { return g_err.c_str(); }
+
+size_t mboit_moment_image_bytes(int32_t width, int32_t height, int32_t moment_set, int32_t storage) {
+    if (width < 1 || height < 1 || moment_set != MBOIT_POWER4 || storage != MBOIT_STORE_F32) return 0;
+    const size_t P = (((size_t)width * (size_t)height) + 3) / 4 * 4;
+    return 20 * P;
+}
+
+mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) {
+    g_err.clear();
+    if (!d || !out) return fail(MBOIT_ERR_INVALID_ARG, "desc and out must be non-NULL");
+    if (d->kind != MBOIT_GRID) return fail(MBOIT_ERR_UNSUPPORTED, "only MBOIT_GRID volumes are implemented");
+    if (d->moment_set != MBOIT_POWER4) return fail(MBOIT_ERR_UNSUPPORTED, "only MBOIT_POWER4 moments are implemented");
+    if (d->storage != MBOIT_STORE_F32) return fail(MBOIT_ERR_UNSUPPORTED, "only float32 moment storage is implemented");
+    if (d->flags & ~(MBOIT_FLAG_RAW_SUM | MBOIT_FLAG_DETERMINISTIC)) return fail(MBOIT_ERR_INVALID_ARG, "unknown flag bits");
+    if (!d->field) return fail(MBOIT_ERR_INVALID_ARG, "field is NULL");
+    for (int c = 0; c < 3; ++c)
+        if (d->dims[c] < 2 || d->dims[c] > (1 << 20)) return fail(MBOIT_ERR_INVALID_ARG, "dims must be in [2, 2^20]");
+    if (d->brick_log2 < 0 || d->brick_log2 > 7) return fail(MBOIT_ERR_INVALID_ARG, "brick_log2 must be in [0, 7]");
+    if (!d->tf_rgba) return fail(MBOIT_ERR_INVALID_ARG, "tf_rgba is NULL");
+    if (!std::isfinite(d->tf_range[0]) || !std::isfinite(d->tf_range[1]) || !(d->tf_range[1] > d->tf_range[0]))
+        return fail(MBOIT_ERR_INVALID_ARG, "tf_range must be finite with tf_range[1] > tf_range[0]");
+    int ex = 0;
+    if (!(d->step > 0.0f) || !std::isfinite(d->step) || std::frexp(d->step, &ex) != 0.5f)
+        return fail(MBOIT_ERR_INVALID_ARG, "step must be a positive power of two");
+    if (!(d->moment_bias >= 0.0f && d->moment_bias < 1.0f)) return fail(MBOIT_ERR_INVALID_ARG, "moment_bias must be in [0, 1)");
+    if (!(d->overestimation >= 0.0f && d->overestimation <= 1.0f))
+        return fail(MBOIT_ERR_INVALID_ARG, "overestimation must be in [0, 1]");
+    if (!(d->absorbance_max > 0.0f) || !std::isfinite(d->absorbance_max))
+        return fail(MBOIT_ERR_INVALID_ARG, "absorbance_max must be positive");
+    std::vector<float4> tf(256);
+    for (int j = 0; j < 256; ++j) {
+        const float* e = d->tf_rgba + 4 * j;
+        for (int c = 0; c < 4; ++c)
+            if (!std::isfinite(e[c])) return fail(MBOIT_ERR_INVALID_ARG, "non-finite transfer-function entry");
+        if (!(e[3] >= 0.0f && e[3] < 1.0f)) return fail(MBOIT_ERR_INVALID_ARG, "transfer-function alpha must be in [0, 1)");
+        // extinction per voxel, times the step: absorbance of one sample
+        const double sigma = -std::log1p(-(double)e[3]);
+        tf[j] = make_float4(e[0], e[1], e[2], (float)(sigma * (double)d->step));
+    }
+    int dev = 0;
+    MB_CUDA(cudaGetDevice(&dev));
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, d->field) != cudaSuccess ||
+        (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return fail(MBOIT_ERR_INVALID_ARG, "field must be a device pointer");
+    }
+    if (attr.device != dev) return fail(MBOIT_ERR_INVALID_ARG, "field lives on another device than the current one");
+
+    mboit_volume v = new (std::nothrow) mboit_volume_s();
+    if (!v) return fail(MBOIT_ERR_OUT_OF_MEMORY, "host allocation failed");
+    v->device = dev;
+    v->desc = *d;
+    v->desc.tf_rgba = nullptr;
+    const int B = 1 << d->brick_log2;
+    mb::GridD& g = v->grid;
+    g.field = d->field;
+    g.nx = d->dims[0];
+    g.ny = d->dims[1];
+    g.nz = d->dims[2];
+    g.brick_log2 = d->brick_log2;
+    g.nbx = (g.nx - 1 + B - 1) / B;
+    g.nby = (g.ny - 1 + B - 1) / B;
+    g.nbz = (g.nz - 1 + B - 1) / B;
+    g.hx = (float)(g.nx - 1);
+    g.hy = (float)(g.ny - 1);
+    g.hz = (float)(g.nz - 1);
+    g.step = d->step;
+    g.tf_scale = (float)(255.0 / ((double)d->tf_range[1] - (double)d->tf_range[0]));
+    g.tf_bias = (float)(-(double)d->tf_range[0] * 255.0 / ((double)d->tf_range[1] - (double)d->tf_range[0]));
+    g.absorbance_max = d->absorbance_max;
+    g.moment_bias = d->moment_bias;
+    g.overestimation = d->overestimation;
+    g.bias_vector[0] = 0.0f;
+    g.bias_vector[1] = 0.375f;
+    g.bias_vector[2] = 0.0f;
+    g.bias_vector[3] = 0.375f;
+    g.flags = d->flags;
+    v->nbricks = (int64_t)g.nbx * g.nby * g.nbz;
+    v->field_bytes = (size_t)g.nx * g.ny * g.nz * sizeof(float);
+    v->pob.assign((size_t)v->nbricks, -1);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&v->d_tf, 256 * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&v->d_pob, (size_t)v->nbricks * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&v->d_sel, (size_t)v->nbricks);
+    if (e == cudaSuccess) e = cudaMalloc(&v->d_ctr, sizeof(mb::Counters));
+    if (e == cudaSuccess) e = cudaMemcpy(v->d_tf, tf.data(), 256 * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(v->d_pob, 0xff, (size_t)v->nbricks * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(v->d_ctr, 0, sizeof(mb::Counters));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&v->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = mb::prepare_kernels();
+    if (e != cudaSuccess) {
+        const mboit_status s = (e == cudaErrorMemoryAllocation) ? MBOIT_ERR_OUT_OF_MEMORY : MBOIT_ERR_CUDA;
+        const std::string msg = std::string("volume set-up failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        mboit_destroy_volume(v);
+        return fail(s, msg);
+    }
+    *out = v;
+    return MBOIT_OK;
+}
+
+mboit_status mboit_destroy_volume(mboit_volume v) {
+    g_err.clear();
+    if (!v) return MBOIT_OK;
+    {
+        DeviceGuard dg(v->device);
+        cudaDeviceSynchronize();
+        drop_graphs(v);
+        if (v->cap_stream) cudaStreamDestroy(v->cap_stream);
+        cudaFree(v->d_tf);
+        cudaFree(v->d_pob);
+        cudaFree(v->d_sel);
+        cudaFree(v->d_ctr);
+    }
+    delete v;
+    return MBOIT_OK;
+}
+
+mboit_status mboit_add_piece(mboit_volume v, const int32_t* ids, int64_t n, int32_t ids_on_device,
+                             int32_t* piece_id_out) {
+    g_err.clear();
+    if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
+    if (!ids || n < 1) return fail(MBOIT_ERR_INVALID_ARG, "a piece needs at least one brick id");
+    if (n > v->nbricks) return fail(MBOIT_ERR_INVALID_ARG, "more brick ids than bricks");
+    std::lock_guard<std::mutex> lk(v->mu);
+    DeviceGuard dg(v->device);
+    std::vector<int32_t> h((size_t)n);
+    if (ids_on_device) {
+        MB_CUDA(cudaMemcpy(h.data(), ids, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(h.data(), ids, (size_t)n * sizeof(int32_t));
+    }
+    const int32_t K = (int32_t)v->boxes.size();
+    std::vector<uint8_t> seen((size_t)v->nbricks, 0);
+    int bmin[3] = {1 << 30, 1 << 30, 1 << 30}, bmax[3] = {-1, -1, -1};
+    const mb::GridD& g = v->grid;
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t b = h[i];
+        if (b < 0 || b >= v->nbricks) return fail(MBOIT_ERR_INVALID_ARG, "brick id " + std::to_string(b) + " out of range");
+        if (seen[b]) return fail(MBOIT_ERR_INVALID_ARG, "brick id " + std::to_string(b) + " listed twice");
+        if (v->pob[b] >= 0)
+            return fail(MBOIT_ERR_INVALID_ARG, "brick " + std::to_string(b) + " already belongs to piece " +
+                                                   std::to_string(v->pob[b]) + " (pieces must not overlap)");
+        seen[b] = 1;
+        const int bc[3] = {b % g.nbx, (b / g.nbx) % g.nby, b / (g.nbx * g.nby)};
+        for (int c = 0; c < 3; ++c) {
+            bmin[c] = bc[c] < bmin[c] ? bc[c] : bmin[c];
+            bmax[c] = bc[c] > bmax[c] ? bc[c] : bmax[c];
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) v->pob[h[i]] = K;
+    cudaError_t e = cudaMemcpy(v->d_pob, v->pob.data(), (size_t)v->nbricks * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        for (int64_t i = 0; i < n; ++i) v->pob[h[i]] = -1;
+        return fail(MBOIT_ERR_CUDA, std::string("uploading brick ownership: ") + cudaGetErrorString(e));
+    }
+    const int B = 1 << g.brick_log2;
+    const float hi[3] = {g.hx, g.hy, g.hz};
+    mb::PieceBox box;
+    for (int c = 0; c < 3; ++c) {
+        box.lo[c] = (float)(bmin[c] * B);
+        const float top = (float)((bmax[c] + 1) * B);
+        box.hi[c] = top < hi[c] ? top : hi[c];
+    }
+    v->boxes.push_back(box);
+    v->owned += n;
+    v->sel_uploaded = false;
+    drop_graphs(v);
+    if (piece_id_out) *piece_id_out = K;
+    return MBOIT_OK;
+}
+
+mboit_status mboit_render_moments(mboit_volume v, const mboit_view* views, int32_t n_views, const int32_t* pieces,
+                                  int32_t n_pieces, int32_t mode, void* moments, void* stream) {
+    g_err.clear();
+    mboit_status st = check_volume(v);
+    if (st != MBOIT_OK) return st;
+    if (mode != MBOIT_MOMENTS_PER_PIECE && mode != MBOIT_MOMENTS_REDUCED) return fail(MBOIT_ERR_INVALID_ARG, "unknown mode");
+    if (!moments) return fail(MBOIT_ERR_INVALID_ARG, "moments is NULL");
+    std::lock_guard<std::mutex> lk(v->mu);
+    DeviceGuard dg(v->device);
+    mb::ViewTable vt;
+    if ((st = build_views(views, n_views, vt)) != MBOIT_OK) return st;
+    std::vector<int32_t> list;
+    const uint8_t* mask = nullptr;
+    if ((st = select_pieces(v, pieces, n_pieces, list, &mask)) != MBOIT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MB_CUDA(cudaMemsetAsync(&v->d_ctr->samples[0], 0, sizeof(unsigned long long), s));
+    if (mode == MBOIT_MOMENTS_REDUCED) {
+        MB_CUDA(mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s));
+    } else {
+        const int32_t slots = (int32_t)list.size();
+        for (int32_t j = 0; j < slots; ++j)
+            MB_CUDA(mb::launch_pass1_piece(v->grid, v->d_tf, v->d_pob, list[j], v->boxes[list[j]], vt, j, slots, moments,
+                                           v->d_ctr, s));
+    }
+    return MBOIT_OK;
+}
+
+mboit_status mboit_reconstruct_blend(mboit_volume v, const mboit_view* views, int32_t n_views, const int32_t* pieces,
+                                     int32_t n_pieces, const void* global_moments, int32_t mode, float* color,
+                                     void* stream) {
+    g_err.clear();
+    mboit_status st = check_volume(v);
+    if (st != MBOIT_OK) return st;
+    if (mode != MBOIT_COLOR_PER_PIECE && mode != MBOIT_COLOR_REDUCED && mode != MBOIT_COLOR_RESOLVED)
+        return fail(MBOIT_ERR_INVALID_ARG, "unknown mode");
+    if (!global_moments || !color) return fail(MBOIT_ERR_INVALID_ARG, "global_moments and color must be non-NULL");
+    std::lock_guard<std::mutex> lk(v->mu);
+    DeviceGuard dg(v->device);
+    mb::ViewTable vt;
+    if ((st = build_views(views, n_views, vt)) != MBOIT_OK) return st;
+    std::vector<int32_t> list;
+    const uint8_t* mask = nullptr;
+    if ((st = select_pieces(v, pieces, n_pieces, list, &mask)) != MBOIT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MB_CUDA(cudaMemsetAsync(&v->d_ctr->samples[1], 0, 2 * sizeof(unsigned long long), s));
+    if (mode == MBOIT_COLOR_PER_PIECE) {
+        const int32_t slots = (int32_t)list.size();
+        for (int32_t j = 0; j < slots; ++j)
+            MB_CUDA(mb::launch_pass2_piece(v->grid, v->d_tf, v->d_pob, list[j], v->boxes[list[j]], vt, j, slots,
+                                           global_moments, color, v->d_ctr, s));
+    } else {
+        MB_CUDA(mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, global_moments, color,
+                                       mode == MBOIT_COLOR_RESOLVED ? mb::kColorResolved : mb::kColorReduced, v->d_ctr,
+                                       s));
+    }
+    return MBOIT_OK;
+}
+
+mboit_status mboit_composite(mboit_volume v, int32_t op, int32_t width, int32_t height, int32_t n_views,
+                             int32_t n_inputs, const void* in, void* out, const void* global_moments, const float* bg,
+                             void* stream) {
+    g_err.clear();
+    if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
+    if (op != MBOIT_OP_MOMENTS_SUM && op != MBOIT_OP_COLOR_SUM_RESOLVE) return fail(MBOIT_ERR_INVALID_ARG, "unknown op");
+    if (n_inputs < 1) return fail(MBOIT_ERR_INVALID_ARG, "n_inputs must be >= 1");
+    if (!in || !out) return fail(MBOIT_ERR_INVALID_ARG, "in and out must be non-NULL");
+    const bool raw = (v->grid.flags & MBOIT_FLAG_RAW_SUM) != 0;
+    if (op == MBOIT_OP_COLOR_SUM_RESOLVE && !raw && !global_moments)
+        return fail(MBOIT_ERR_INVALID_ARG, "global_moments is needed to renormalise");
+    float4 b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (bg) {
+        if (!std::isfinite(bg[0]) || !std::isfinite(bg[1]) || !std::isfinite(bg[2]) || !std::isfinite(bg[3]))
+            return fail(MBOIT_ERR_INVALID_ARG, "non-finite background");
+        b = make_float4(bg[0], bg[1], bg[2], bg[3]);
+    }
+    std::lock_guard<std::mutex> lk(v->mu);
+    DeviceGuard dg(v->device);
+    mb::ViewTable vt;
+    mboit_status st = build_images(width, height, n_views, vt);
+    if (st != MBOIT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (op == MBOIT_OP_MOMENTS_SUM) {
+        MB_CUDA(mb::launch_moments_sum(vt, n_inputs, in, out, s));
+    } else {
+        MB_CUDA(mb::launch_color_resolve(vt, n_inputs, static_cast<const float*>(in), static_cast<float*>(out),
+                                         global_moments, b, raw ? 1 : 0, s));
+    }
+    return MBOIT_OK;
+}
+
+mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch,
+                                float* rgba, void* stream) {
+    g_err.clear();
+    mboit_status st = check_volume(v);
+    if (st != MBOIT_OK) return st;
+    if (!moments_scratch || !rgba) return fail(MBOIT_ERR_INVALID_ARG, "moments_scratch and rgba must be non-NULL");
+    std::lock_guard<std::mutex> lk(v->mu);
+    DeviceGuard dg(v->device);
+    mb::ViewTable vt;
+    if ((st = build_views(views, n_views, vt)) != MBOIT_OK) return st;
+    std::vector<int32_t> list;
+    const uint8_t* mask = nullptr;
+    if ((st = select_pieces(v, nullptr, 0, list, &mask)) != MBOIT_OK) return st;
+    // graph key: the view table and the output pointers
+    std::vector<char> key(sizeof vt + 2 * sizeof(void*));
+    std::memcpy(key.data(), &vt, sizeof vt);
+    std::memcpy(key.data() + sizeof vt, &moments_scratch, sizeof(void*));
+    std::memcpy(key.data() + sizeof vt + sizeof(void*), &rgba, sizeof(void*));
+    cudaGraphExec_t exec = nullptr;
+    for (auto& ge : v->graphs)
+        if (ge.key == key) exec = ge.exec;
+    if (!exec) {
+        cudaStream_t cs = v->cap_stream;
+        MB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemsetAsync(&v->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), cs);
+        if (e == cudaSuccess) e = mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, cs);
+        if (e == cudaSuccess)
+            e = mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba, mb::kColorResolved, v->d_ctr, cs);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return fail(MBOIT_ERR_CUDA, std::string("capturing the frame: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(MBOIT_ERR_CUDA, std::string("instantiating the frame graph: ") + cudaGetErrorString(e));
+        if (v->graphs.size() >= 8) drop_graphs(v);
+        v->graphs.push_back(GraphEntry{key, exec});
+    }
+    MB_CUDA(cudaGraphLaunch(exec, static_cast<cudaStream_t>(stream)));
+    return MBOIT_OK;
+}
+
+mboit_status mboit_render_frame_host(mboit_volume v, const float* field_host, const mboit_view* views, int32_t n_views,
+                                     void* moments_scratch, float* rgba_device, float* rgba_host, void* stream) {
+    g_err.clear();
+    mboit_status st = check_volume(v);
+    if (st != MBOIT_OK) return st;
+    if (!field_host || !rgba_host || !rgba_device) return fail(MBOIT_ERR_INVALID_ARG, "NULL buffer");
+    mb::ViewTable vt;
+    if ((st = build_views(views, n_views, vt)) != MBOIT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        DeviceGuard dg(v->device);
+        MB_CUDA(cudaMemcpyAsync(const_cast<float*>(v->grid.field), field_host, v->field_bytes, cudaMemcpyHostToDevice, s));
+    }
+    if ((st = mboit_render_frame(v, views, n_views, moments_scratch, rgba_device, stream)) != MBOIT_OK) return st;
+    int64_t floats = 0;
+    for (int i = 0; i < n_views; ++i) floats += (int64_t)4 * views[i].width * views[i].height;
+    DeviceGuard dg(v->device);
+    MB_CUDA(cudaMemcpyAsync(rgba_host, rgba_device, (size_t)floats * sizeof(float), cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    return MBOIT_OK;
+}
+
+mboit_status mboit_synchronize(mboit_volume v, void* stream) {
+    g_err.clear();
+    if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
+    DeviceGuard dg(v->device);
+    MB_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int32_t err = 0;
+    MB_CUDA(cudaMemcpy(&err, &v->d_ctr->error, sizeof err, cudaMemcpyDeviceToHost));
+    if (err == 1) return fail(MBOIT_ERR_TIMEOUT, "a kernel gave up waiting");
+    if (err != 0) return fail(MBOIT_ERR_DEVICE_ASSERT, "a kernel-side check failed (code " + std::to_string(err) + ")");
+    return MBOIT_OK;
+}
+
+mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out) {
+    g_err.clear();
+    if (!v || !out) return fail(MBOIT_ERR_INVALID_ARG, "volume and out must be non-NULL");
+    std::lock_guard<std::mutex> lk(v->mu);
+    DeviceGuard dg(v->device);
+    MB_CUDA(cudaDeviceSynchronize());
+    mb::Counters c;
+    MB_CUDA(cudaMemcpy(&c, v->d_ctr, sizeof c, cudaMemcpyDeviceToHost));
+    out->samples_pass1 = (int64_t)c.samples[0];
+    out->samples_pass2 = (int64_t)c.samples[1];
+    out->singular_pixels = (int64_t)c.singular;
+    out->n_pieces = (int32_t)v->boxes.size();
+    out->device = v->device;
+    return MBOIT_OK;
+}
+
+}  // extern "C"

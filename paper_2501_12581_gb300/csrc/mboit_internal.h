@@ -1,0 +1,67 @@
+// Internal launch interface between the C ABI (mboit_api.cu) and the
+// kernels (mboit_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mboit_device.cuh"
+
+namespace mb {
+
+constexpr int kMaxViews = 16;
+constexpr int kTileW = 8;   // a warp's ray tile: 8 x 4 pixels
+constexpr int kTileH = 4;
+
+struct ViewSlot {
+    ViewD v;
+    int32_t tile_base;      // first global tile index of this view
+    int32_t ntx;            // tiles per row
+    int64_t moment_off;     // byte offset of this view's first moment slab
+    int64_t color_off;      // float offset of this view's first RGBA image
+    int32_t plane;          // pixels per moment plane (w*h rounded up to 4)
+    int32_t pad0;
+};
+
+struct ViewTable {
+    int32_t n;
+    int32_t total_tiles;
+    ViewSlot s[kMaxViews];
+};
+
+// Device counters owned by a volume.
+struct Counters {
+    int32_t tile_next[4];            // work-queue heads, one per concurrent pass
+    int32_t error;                   // nonzero: a kernel-side check failed
+    int32_t pad;
+    unsigned long long samples[2];   // pass 1, pass 2
+    unsigned long long singular;     // pixels on a 1-/2-atom branch
+};
+
+struct PieceBox {
+    float lo[3], hi[3];              // voxel-space box covering the piece's bricks
+};
+
+enum ColorMode : int32_t { kColorPerPiece = 0, kColorReduced = 1, kColorResolved = 2 };
+
+// Loads all kernels and caches launch shapes (call before any capture).
+cudaError_t prepare_kernels();
+// Fused pass 1 over all selected pieces, REDUCED output.  `brick_sel` NULL
+// means every brick is sampled.
+cudaError_t launch_pass1_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
+                               void* moments, Counters* ctr, cudaStream_t s);
+// Fused pass 2 over all selected pieces, REDUCED or RESOLVED output.
+cudaError_t launch_pass2_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
+                               const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s);
+// Plain per-piece passes: one launch = one piece, its own slab.
+cudaError_t launch_pass1_piece(const GridD& g, const float4* tf, const int32_t* piece_of_brick, int32_t piece,
+                               const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
+                               void* moments, Counters* ctr, cudaStream_t s);
+cudaError_t launch_pass2_piece(const GridD& g, const float4* tf, const int32_t* piece_of_brick, int32_t piece,
+                               const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
+                               const void* moments, float* color, Counters* ctr, cudaStream_t s);
+// Image-space reductions.
+cudaError_t launch_moments_sum(const ViewTable& vt, int32_t n_inputs, const void* in, void* out, cudaStream_t s);
+cudaError_t launch_color_resolve(const ViewTable& vt, int32_t n_inputs, const float* in, float* out,
+                                 const void* moments, float4 bg, int32_t raw_sum, cudaStream_t s);
+
+}  // namespace mb

@@ -1,0 +1,551 @@
+// CUDA kernels of the MBOIT puzzle-piece render for sm_103a.
+//
+// Work decomposition.  One thread marches one ray; a warp owns an 8 x 4
+// pixel tile, so the 32 rays of a warp are spatial neighbours and their
+// trilinear gathers at the same lattice index hit a few adjacent cache lines.
+// The fused passes are persistent: grid = SMs x resident CTAs, each warp pops
+// tiles from an atomic work-queue head (no waits, no spins), which balances
+// long centre rays against short silhouette rays.  The transfer function
+// (256 x float4, 4 KB) is staged once per CTA in shared memory.
+//
+// Pass 1 (Sec. 4.1, Alg. 2) accumulates b_j += a z^j in registers over all
+// selected pieces: summing the pieces' moment images (the Allreduce add) is
+// done in registers because addition commutes.  Pass 2 (Sec. 4.2, Alg. 1
+// loop 2, Alg. 3) builds the per-pixel reconstruction frame from the global
+// moments in FP64 once per ray, then adds T * alpha * (r, g, b, 1) per sample
+// in FP32; the resolved mode also applies the renormalisation (Sec. 4.3) in
+// the epilogue, so the frame needs no separate colour reduction.
+//
+// The per-piece kernels are the plain form: one launch per piece, the rays
+// clipped to the piece's box, non-owned bricks skipped forward, one image per
+// piece; the image-space kernels then sum the K images (compensated).
+#include <cuda_runtime.h>
+
+#include "mboit_internal.h"
+
+namespace mb {
+
+namespace {
+
+__device__ __forceinline__ float one_minus_exp_neg(float a) {
+    // 1 - e^-a without cancellation: Taylor series a * sum_{n>=0} (-a)^n / (n+1)!
+    // for a < 1/2 (truncation error < 1e-8 relative), direct form above.
+    if (a < 0.5f) {
+        float p = ffma(a, -1.0f / 40320.0f, 1.0f / 5040.0f);
+        p = ffma(a, p, -1.0f / 720.0f);
+        p = ffma(a, p, 1.0f / 120.0f);
+        p = ffma(a, p, -1.0f / 24.0f);
+        p = ffma(a, p, 1.0f / 6.0f);
+        p = ffma(a, p, -0.5f);
+        p = ffma(a, p, 1.0f);
+        return a * p;
+    }
+    return 1.0f - fexp2(-a * kLog2e);
+}
+
+// Position of lattice point t on the ray, domain test, optional brick
+// selection, trilinear value.  Cells are half-open, so a point inside
+// [0, n-1) has all 8 corner vertices in range.
+template <bool kSel>
+__device__ __forceinline__ bool field_sample(const GridD& g, const uint8_t* __restrict__ sel, float t,
+                                             const float o[3], const float d[3], float& val) {
+    const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
+    if (!(p0 >= 0.0f && p0 < g.hx && p1 >= 0.0f && p1 < g.hy && p2 >= 0.0f && p2 < g.hz)) return false;
+    const int ix = (int)p0, iy = (int)p1, iz = (int)p2;
+    if (kSel) {
+        const int b = ((iz >> g.brick_log2) * g.nby + (iy >> g.brick_log2)) * g.nbx + (ix >> g.brick_log2);
+        if (!__ldg(sel + b)) return false;
+    }
+    const float fx = p0 - (float)ix, fy = p1 - (float)iy, fz = p2 - (float)iz;
+    const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * (size_t)g.ny;
+    const float* __restrict__ c = g.field + (size_t)iz * sz + (size_t)iy * sy + (size_t)ix;
+    const float v000 = __ldg(c), v100 = __ldg(c + 1);
+    const float v010 = __ldg(c + sy), v110 = __ldg(c + sy + 1);
+    const float v001 = __ldg(c + sz), v101 = __ldg(c + sz + 1);
+    const float v011 = __ldg(c + sz + sy), v111 = __ldg(c + sz + sy + 1);
+    const float a00 = ffma(fx, v100 - v000, v000), a10 = ffma(fx, v110 - v010, v010);
+    const float a01 = ffma(fx, v101 - v001, v001), a11 = ffma(fx, v111 - v011, v011);
+    const float b0 = ffma(fy, a10 - a00, a00), b1 = ffma(fy, a11 - a01, a01);
+    val = ffma(fz, b1 - b0, b0);
+    return true;
+}
+
+__device__ __forceinline__ float tf_coord(const GridD& g, float v, int& i) {
+    const float xt = fclamp(ffma(v, g.tf_scale, g.tf_bias), 0.0f, 255.0f);
+    i = min((int)xt, 254);
+    return xt - (float)i;
+}
+
+__device__ __forceinline__ int find_view(const ViewTable& vt, int tile) {
+    int vi = 0;
+    while (vi + 1 < vt.n && tile >= vt.s[vi + 1].tile_base) ++vi;
+    return vi;
+}
+
+__device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned n) {
+    unsigned long long v = n;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+__device__ __forceinline__ void store_moments(char* base, const ViewSlot& S, int64_t slab_off, int pix,
+                                              float m0, float m1, float m2, float m3, float m4) {
+    char* slab = base + slab_off;
+    reinterpret_cast<float*>(slab)[pix] = m0;
+    reinterpret_cast<float4*>(slab + (size_t)4 * S.plane)[pix] = make_float4(m1, m2, m3, m4);
+}
+
+__device__ __forceinline__ void load_moments(const char* base, const ViewSlot& S, int64_t slab_off, int pix,
+                                             float m[5]) {
+    const char* slab = base + slab_off;
+    m[0] = __ldg(reinterpret_cast<const float*>(slab) + pix);
+    const float4 q = __ldg(reinterpret_cast<const float4*>(slab + (size_t)4 * S.plane) + pix);
+    m[1] = q.x; m[2] = q.y; m[3] = q.z; m[4] = q.w;
+}
+
+__device__ __forceinline__ float4 resolve_pixel(float4 C, float m0, float4 bg, bool raw) {
+    if (raw) return C;
+    const float A = -expm1f(-m0);
+    const float T = 1.0f - A;
+    const float k = C.w > 0.0f ? A / C.w : 0.0f;
+    return make_float4(ffma(C.x, k, T * bg.x), ffma(C.y, k, T * bg.y), ffma(C.z, k, T * bg.z), A + T * bg.w);
+}
+
+// ------------------------------------------------------------------------
+// fused, persistent passes
+
+template <bool kSel>
+__global__ void __launch_bounds__(256) k_pass1_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
+                                                     const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
+                                                     char* __restrict__ moments, Counters* __restrict__ ctr) {
+    __shared__ float s_sig[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_sig[i] = tf[i].w;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const float lo[3] = {0.0f, 0.0f, 0.0f};
+    const float hi[3] = {g.hx, g.hy, g.hz};
+    for (;;) {
+        int tile = 0;
+        if (lane == 0) tile = atomicAdd(&ctr->tile_next[0], 1);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= vt.total_tiles) break;
+        const int vi = find_view(vt, tile);
+        const ViewSlot& S = vt.s[vi];
+        const int lt = tile - S.tile_base;
+        const int px = (lt % S.ntx) * kTileW + (lane & 7);
+        const int py = (lt / S.ntx) * kTileH + (lane >> 3);
+        unsigned n = 0;
+        if (px < S.v.width && py < S.v.height) {
+            float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f;
+            float o[3], d[3];
+            make_ray(S.v, px, py, o, d);
+            int k0, k1;
+            if (lattice_range(o, d, lo, hi, g.step, &k0, &k1)) {
+                const float wa = S.v.warp_a, wb = S.v.warp_b;
+                for (int k = k0; k <= k1; ++k) {
+                    const float t = lattice_t(k, g.step);
+                    float val;
+                    if (!field_sample<kSel>(g, sel, t, o, d, val)) continue;
+                    int i;
+                    const float f = tf_coord(g, val, i);
+                    const float s0 = s_sig[i], s1 = s_sig[i + 1];
+                    const float a = fmin_(ffma(f, s1 - s0, s0), g.absorbance_max);
+                    const float z = warp_depth(t, wa, wb);
+                    m0 += a;
+                    float az = a * z;
+                    m1 += az;
+                    az *= z;
+                    m2 += az;
+                    az *= z;
+                    m3 += az;
+                    az *= z;
+                    m4 += az;
+                    ++n;
+                }
+            }
+            store_moments(moments, S, S.moment_off, py * S.v.width + px, m0, m1, m2, m3, m4);
+        }
+        warp_add_u64(&ctr->samples[0], n);
+    }
+}
+
+template <bool kSel, int kMode>
+__global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
+                                                     const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
+                                                     const char* __restrict__ moments, float* __restrict__ color,
+                                                     Counters* __restrict__ ctr) {
+    __shared__ float4 s_tf[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = tf[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const float lo[3] = {0.0f, 0.0f, 0.0f};
+    const float hi[3] = {g.hx, g.hy, g.hz};
+    const float w0 = g.overestimation;
+    const bool raw = (g.flags & 1u) != 0;
+    for (;;) {
+        int tile = 0;
+        if (lane == 0) tile = atomicAdd(&ctr->tile_next[1], 1);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= vt.total_tiles) break;
+        const int vi = find_view(vt, tile);
+        const ViewSlot& S = vt.s[vi];
+        const int lt = tile - S.tile_base;
+        const int px = (lt % S.ntx) * kTileW + (lane & 7);
+        const int py = (lt / S.ntx) * kTileH + (lane >> 3);
+        unsigned n = 0;
+        if (px < S.v.width && py < S.v.height) {
+            const int pix = py * S.v.width + px;
+            float m[5];
+            load_moments(moments, S, S.moment_off, pix, m);
+            const Frame F = make_frame(m, g.moment_bias, g.bias_vector);
+            if (F.kind == kFrameOneAtom || F.kind == kFrameTwoAtoms) atomicAdd(&ctr->singular, 1ull);
+            float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float o[3], d[3];
+            make_ray(S.v, px, py, o, d);
+            int k0, k1;
+            if (lattice_range(o, d, lo, hi, g.step, &k0, &k1)) {
+                const float wa = S.v.warp_a, wb = S.v.warp_b;
+                for (int k = k0; k <= k1; ++k) {
+                    const float t = lattice_t(k, g.step);
+                    float val;
+                    if (!field_sample<kSel>(g, sel, t, o, d, val)) continue;
+                    int i;
+                    const float f = tf_coord(g, val, i);
+                    const float4 e0 = s_tf[i], e1 = s_tf[i + 1];
+                    const float a = fmin_(ffma(f, e1.w - e0.w, e0.w), g.absorbance_max);
+                    const float alpha = one_minus_exp_neg(a);
+                    const float z = warp_depth(t, wa, wb);
+                    const float wgt = transmittance(F, z, w0) * alpha;
+                    C.x = ffma(wgt, ffma(f, e1.x - e0.x, e0.x), C.x);
+                    C.y = ffma(wgt, ffma(f, e1.y - e0.y, e0.y), C.y);
+                    C.z = ffma(wgt, ffma(f, e1.z - e0.z, e0.z), C.z);
+                    C.w += wgt;
+                    ++n;
+                }
+            }
+            float4* out = reinterpret_cast<float4*>(color + S.color_off) + pix;
+            if (kMode == kColorResolved)
+                *out = resolve_pixel(C, m[0], make_float4(0.0f, 0.0f, 0.0f, 0.0f), raw);
+            else
+                *out = C;
+        }
+        warp_add_u64(&ctr->samples[1], n);
+    }
+}
+
+// ------------------------------------------------------------------------
+// plain per-piece passes
+
+// Next lattice index worth testing after point k fell in a brick the piece
+// does not own: the ray's exit from that brick, pulled back by a padding
+// that covers float32 position rounding, and by one lattice step.
+__device__ __forceinline__ int skip_brick(const GridD& g, const float o[3], const float d[3], float t, int k) {
+    const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+    const float B = (float)(1 << g.brick_log2);
+    float t_exit = 3.0e38f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (d[c] == 0.0f) continue;
+        const float cell0 = floorf(p[c] / B) * B;
+        const float face = d[c] > 0.0f ? cell0 + B : cell0;
+        const float inv = 1.0f / d[c];
+        const float tc = (face - o[c]) * inv;
+        const float pad = (fabsf(o[c]) + fabsf(face) + 1.0f) * 3.814697265625e-06f * fabsf(inv);
+        t_exit = fmin_(t_exit, tc - pad);
+    }
+    const float kn = ceilf(t_exit / g.step - 0.5f) - 1.0f;
+    if (!(kn > (float)(k + 1))) return k + 1;
+    return kn > 16777000.0f ? 16777000 : (int)kn;
+}
+
+// One owned sample of `piece` at lattice index k, or the next index to try.
+__device__ __forceinline__ bool piece_sample(const GridD& g, const int32_t* __restrict__ pob, int piece, float t,
+                                             const float o[3], const float d[3], int k, float& val, int& k_next) {
+    k_next = k + 1;
+    const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
+    if (!(p0 >= 0.0f && p0 < g.hx && p1 >= 0.0f && p1 < g.hy && p2 >= 0.0f && p2 < g.hz)) return false;
+    const int ix = (int)p0, iy = (int)p1, iz = (int)p2;
+    const int b = ((iz >> g.brick_log2) * g.nby + (iy >> g.brick_log2)) * g.nbx + (ix >> g.brick_log2);
+    if (__ldg(pob + b) != piece) {
+        k_next = skip_brick(g, o, d, t, k);
+        return false;
+    }
+    return field_sample<false>(g, nullptr, t, o, d, val);
+}
+
+__global__ void __launch_bounds__(128) k_pass1_piece(const __grid_constant__ GridD g, const float4* __restrict__ tf,
+                                                     const int32_t* __restrict__ pob, int piece, const __grid_constant__ PieceBox box,
+                                                     const __grid_constant__ ViewTable vt, int slot, int n_slots,
+                                                     char* __restrict__ moments, Counters* __restrict__ ctr) {
+    __shared__ float s_sig[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_sig[i] = tf[i].w;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tile >= vt.total_tiles) return;
+    const int vi = find_view(vt, tile);
+    const ViewSlot& S = vt.s[vi];
+    const int lt = tile - S.tile_base;
+    const int px = (lt % S.ntx) * kTileW + (lane & 7);
+    const int py = (lt / S.ntx) * kTileH + (lane >> 3);
+    unsigned n = 0;
+    if (px < S.v.width && py < S.v.height) {
+        float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f;
+        float o[3], d[3];
+        make_ray(S.v, px, py, o, d);
+        int k0, k1;
+        if (lattice_range(o, d, box.lo, box.hi, g.step, &k0, &k1)) {
+            const float wa = S.v.warp_a, wb = S.v.warp_b;
+            for (int k = k0; k <= k1;) {
+                const float t = lattice_t(k, g.step);
+                float val;
+                int kn;
+                if (!piece_sample(g, pob, piece, t, o, d, k, val, kn)) {
+                    k = kn;
+                    continue;
+                }
+                k = kn;
+                int i;
+                const float f = tf_coord(g, val, i);
+                const float s0 = s_sig[i], s1 = s_sig[i + 1];
+                const float a = fmin_(ffma(f, s1 - s0, s0), g.absorbance_max);
+                const float z = warp_depth(t, wa, wb);
+                m0 += a;
+                float az = a * z;
+                m1 += az;
+                az *= z;
+                m2 += az;
+                az *= z;
+                m3 += az;
+                az *= z;
+                m4 += az;
+                ++n;
+            }
+        }
+        const int64_t slab = (int64_t)20 * S.plane;
+        store_moments(moments, S, S.moment_off * n_slots + slot * slab, py * S.v.width + px, m0, m1, m2, m3, m4);
+    }
+    warp_add_u64(&ctr->samples[0], n);
+}
+
+__global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ GridD g, const float4* __restrict__ tf,
+                                                     const int32_t* __restrict__ pob, int piece, const __grid_constant__ PieceBox box,
+                                                     const __grid_constant__ ViewTable vt, int slot, int n_slots,
+                                                     const char* __restrict__ moments, float* __restrict__ color,
+                                                     Counters* __restrict__ ctr) {
+    __shared__ float4 s_tf[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = tf[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tile >= vt.total_tiles) return;
+    const int vi = find_view(vt, tile);
+    const ViewSlot& S = vt.s[vi];
+    const int lt = tile - S.tile_base;
+    const int px = (lt % S.ntx) * kTileW + (lane & 7);
+    const int py = (lt / S.ntx) * kTileH + (lane >> 3);
+    const float w0 = g.overestimation;
+    unsigned n = 0;
+    if (px < S.v.width && py < S.v.height) {
+        const int pix = py * S.v.width + px;
+        float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float o[3], d[3];
+        make_ray(S.v, px, py, o, d);
+        int k0, k1;
+        if (lattice_range(o, d, box.lo, box.hi, g.step, &k0, &k1)) {
+            float m[5];
+            load_moments(moments, S, S.moment_off, pix, m);
+            const Frame F = make_frame(m, g.moment_bias, g.bias_vector);
+            const float wa = S.v.warp_a, wb = S.v.warp_b;
+            for (int k = k0; k <= k1;) {
+                const float t = lattice_t(k, g.step);
+                float val;
+                int kn;
+                if (!piece_sample(g, pob, piece, t, o, d, k, val, kn)) {
+                    k = kn;
+                    continue;
+                }
+                k = kn;
+                int i;
+                const float f = tf_coord(g, val, i);
+                const float4 e0 = s_tf[i], e1 = s_tf[i + 1];
+                const float a = fmin_(ffma(f, e1.w - e0.w, e0.w), g.absorbance_max);
+                const float alpha = one_minus_exp_neg(a);
+                const float z = warp_depth(t, wa, wb);
+                const float wgt = transmittance(F, z, w0) * alpha;
+                C.x = ffma(wgt, ffma(f, e1.x - e0.x, e0.x), C.x);
+                C.y = ffma(wgt, ffma(f, e1.y - e0.y, e0.y), C.y);
+                C.z = ffma(wgt, ffma(f, e1.z - e0.z, e0.z), C.z);
+                C.w += wgt;
+                ++n;
+            }
+        }
+        const int64_t img = (int64_t)4 * S.v.width * S.v.height;
+        reinterpret_cast<float4*>(color + S.color_off * n_slots + slot * img)[pix] = C;
+    }
+    warp_add_u64(&ctr->samples[1], n);
+}
+
+// ------------------------------------------------------------------------
+// image-space reductions (compensated, fixed input order)
+
+struct Neumaier {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ float get() const { return s + c; }
+};
+
+__global__ void k_moments_sum(const float4* __restrict__ in, float4* __restrict__ out, int64_t n4, int n_inputs) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        Neumaier x, y, z, w;
+        for (int j = 0; j < n_inputs; ++j) {
+            const float4 v = __ldg(in + (int64_t)j * n4 + i);
+            x.add(v.x);
+            y.add(v.y);
+            z.add(v.z);
+            w.add(v.w);
+        }
+        out[i] = make_float4(x.get(), y.get(), z.get(), w.get());
+    }
+}
+
+__global__ void k_color_resolve(const float4* __restrict__ in, float4* __restrict__ out, const float* __restrict__ b0,
+                                int64_t npix, int n_inputs, float4 bg, int raw) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
+        Neumaier x, y, z, w;
+        for (int j = 0; j < n_inputs; ++j) {
+            const float4 v = __ldg(in + (int64_t)j * npix + i);
+            x.add(v.x);
+            y.add(v.y);
+            z.add(v.z);
+            w.add(v.w);
+        }
+        const float4 C = make_float4(x.get(), y.get(), z.get(), w.get());
+        out[i] = resolve_pixel(C, raw ? 0.0f : __ldg(b0 + i), bg, raw != 0);
+    }
+}
+
+template <typename K>
+int persistent_blocks(K kernel, int threads) {
+    static int cached_dev = -1, cached = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != cached_dev) {
+        int sms = 0, occ = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0);
+        cached = sms * (occ > 0 ? occ : 1);
+        cached_dev = dev;
+    }
+    return cached;
+}
+
+}  // namespace
+
+cudaError_t prepare_kernels() {
+    // Loads every kernel and fills the occupancy caches, so that no module
+    // loading happens later inside a stream capture.
+    const void* fns[] = {(const void*)k_pass1_fused<true>, (const void*)k_pass1_fused<false>,
+                         (const void*)k_pass2_fused<true, kColorReduced>, (const void*)k_pass2_fused<true, kColorResolved>,
+                         (const void*)k_pass2_fused<false, kColorReduced>, (const void*)k_pass2_fused<false, kColorResolved>,
+                         (const void*)k_pass1_piece, (const void*)k_pass2_piece, (const void*)k_moments_sum,
+                         (const void*)k_color_resolve};
+    for (const void* f : fns) {
+        cudaFuncAttributes a;
+        const cudaError_t e = cudaFuncGetAttributes(&a, f);
+        if (e != cudaSuccess) return e;
+    }
+    persistent_blocks(k_pass1_fused<true>, 256);
+    persistent_blocks(k_pass1_fused<false>, 256);
+    persistent_blocks(k_pass2_fused<true, kColorReduced>, 256);
+    persistent_blocks(k_pass2_fused<true, kColorResolved>, 256);
+    persistent_blocks(k_pass2_fused<false, kColorReduced>, 256);
+    persistent_blocks(k_pass2_fused<false, kColorResolved>, 256);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass1_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
+                               void* moments, Counters* ctr, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    if (brick_sel) {
+        const int nb = persistent_blocks(k_pass1_fused<true>, 256);
+        k_pass1_fused<true><<<nb, 256, 0, s>>>(g, tf, brick_sel, vt, static_cast<char*>(moments), ctr);
+    } else {
+        const int nb = persistent_blocks(k_pass1_fused<false>, 256);
+        k_pass1_fused<false><<<nb, 256, 0, s>>>(g, tf, brick_sel, vt, static_cast<char*>(moments), ctr);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass2_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
+                               const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&ctr->tile_next[1], 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const char* m = static_cast<const char*>(moments);
+#define MB_LAUNCH2(SEL, MODE)                                                         \
+    do {                                                                              \
+        const int nb = persistent_blocks(k_pass2_fused<SEL, MODE>, 256);              \
+        k_pass2_fused<SEL, MODE><<<nb, 256, 0, s>>>(g, tf, brick_sel, vt, m, color, ctr); \
+    } while (0)
+    if (brick_sel) {
+        if (mode == kColorResolved) MB_LAUNCH2(true, kColorResolved);
+        else MB_LAUNCH2(true, kColorReduced);
+    } else {
+        if (mode == kColorResolved) MB_LAUNCH2(false, kColorResolved);
+        else MB_LAUNCH2(false, kColorReduced);
+    }
+#undef MB_LAUNCH2
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass1_piece(const GridD& g, const float4* tf, const int32_t* pob, int32_t piece,
+                               const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
+                               void* moments, Counters* ctr, cudaStream_t s) {
+    const int blocks = (vt.total_tiles + 3) / 4;
+    k_pass1_piece<<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, static_cast<char*>(moments), ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass2_piece(const GridD& g, const float4* tf, const int32_t* pob, int32_t piece,
+                               const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
+                               const void* moments, float* color, Counters* ctr, cudaStream_t s) {
+    const int blocks = (vt.total_tiles + 3) / 4;
+    k_pass2_piece<<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots,
+                                         static_cast<const char*>(moments), color, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_sum(const ViewTable& vt, int32_t n_inputs, const void* in, void* out, cudaStream_t s) {
+    for (int v = 0; v < vt.n; ++v) {
+        const ViewSlot& S = vt.s[v];
+        const int64_t n4 = (int64_t)5 * S.plane / 4;
+        const float4* src = reinterpret_cast<const float4*>(static_cast<const char*>(in) + S.moment_off * n_inputs);
+        float4* dst = reinterpret_cast<float4*>(static_cast<char*>(out) + S.moment_off);
+        const int blocks = (int)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096);
+        k_moments_sum<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(src, dst, n4, n_inputs);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_color_resolve(const ViewTable& vt, int32_t n_inputs, const float* in, float* out,
+                                 const void* moments, float4 bg, int32_t raw_sum, cudaStream_t s) {
+    for (int v = 0; v < vt.n; ++v) {
+        const ViewSlot& S = vt.s[v];
+        const int64_t npix = (int64_t)S.v.width * S.v.height;
+        const float4* src = reinterpret_cast<const float4*>(in + S.color_off * n_inputs);
+        float4* dst = reinterpret_cast<float4*>(out + S.color_off);
+        const float* b0 = moments ? reinterpret_cast<const float*>(static_cast<const char*>(moments) + S.moment_off)
+                                  : nullptr;
+        const int blocks = (int)((npix + 255) / 256 < 4096 ? (npix + 255) / 256 : 4096);
+        k_color_resolve<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(src, dst, b0, npix, n_inputs, bg, raw_sum);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mb

@@ -1,0 +1,113 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every entry point the header declares, and rejects bad
+descriptors before touching CUDA."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2501_12581_gb300 as pkg
+from paper_2501_12581_gb300 import build as pkg_build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mboit.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg_build.build()
+    return pkg.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^MBOIT_API\s+[\w\s\*]+?\b(mboit_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for n in ("mboit_create_volume", "mboit_add_piece", "mboit_render_moments", "mboit_reconstruct_blend",
+              "mboit_composite", "mboit_render_frame", "mboit_destroy_volume"):
+        assert n in names
+    assert set(names) == set(pkg.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert callable(getattr(pkg, name)), name
+
+
+def test_moment_image_bytes(lib):
+    assert pkg.mboit_moment_image_bytes(256, 256) == 20 * 65536
+    assert pkg.mboit_moment_image_bytes(7, 3) == 20 * 24       # plane rounded up to 4 pixels
+    assert pkg.mboit_moment_image_bytes(0, 3) == 0
+    assert pkg.mboit_moment_image_bytes(4, 4, moment_set=9) == 0
+
+
+def _desc(**kw):
+    d = pkg.mboit_volume_desc()
+    d.kind, d.moment_set, d.storage = pkg.MBOIT_GRID, pkg.MBOIT_POWER4, pkg.MBOIT_STORE_F32
+    d.field = 0x1000
+    d.dims[:] = [9, 9, 9]
+    d.brick_log2 = 2
+    tf = np.zeros((256, 4), np.float32)
+    tf[:, 3] = 0.1
+    d._tf = tf
+    d.tf_rgba = tf.ctypes.data
+    d.tf_range[:] = [0.0, 1.0]
+    d.step, d.moment_bias, d.overestimation, d.absorbance_max = 0.5, 5e-5, 0.3, 10.0
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("bad, status", [
+    (dict(kind=pkg.MBOIT_AMR), 4),
+    (dict(moment_set=3), 4),
+    (dict(field=None), 1),
+    (dict(brick_log2=9), 1),
+    (dict(step=0.3), 1),
+    (dict(step=-0.5), 1),
+    (dict(moment_bias=1.5), 1),
+    (dict(overestimation=-0.1), 1),
+    (dict(absorbance_max=0.0), 1),
+    (dict(flags=0x80), 1),
+])
+def test_create_volume_rejects_bad_descriptors(lib, bad, status):
+    d = _desc(**bad)
+    h = ctypes.c_void_p()
+    rc = lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h))
+    assert rc == status
+    assert h.value is None
+    assert len(pkg.mboit_last_error()) > 0
+
+
+def test_bad_tf_and_dims_rejected(lib):
+    d = _desc()
+    d.dims[:] = [1, 9, 9]
+    h = ctypes.c_void_p()
+    assert lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h)) == 1
+    d = _desc()
+    d._tf[5, 3] = 1.0  # opacity 1 has no finite extinction
+    assert lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h)) == 1
+    d = _desc()
+    d.tf_range[:] = [1.0, 1.0]
+    assert lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h)) == 1
+
+
+def test_null_handles_rejected(lib):
+    assert lib.mboit_add_piece(None, None, 0, 0, None) == 1
+    assert lib.mboit_render_moments(None, None, 0, None, 0, 1, None, None) == 1
+    assert lib.mboit_reconstruct_blend(None, None, 0, None, 0, None, 2, None, None) == 1
+    assert lib.mboit_composite(None, 0, 1, 1, 1, 1, None, None, None, None, None) == 1
+    assert lib.mboit_render_frame(None, None, 0, None, None, None) == 1
+    assert lib.mboit_get_stats(None, None) == 1
+    assert lib.mboit_destroy_volume(None) == 0
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(pkg, "_lib", None)
+    with pytest.raises(pkg.MboitError):
+        pkg.load_library(str(tmp_path / "nope.so"))
