@@ -218,6 +218,36 @@ MBOIT_API mboit_status mboit_synchronize(mboit_volume v, void* stream);
 /* Counters of the last passes (synchronises the stream of the last render). */
 MBOIT_API mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out);
 
+/* Pass 1 for callers that must not allocate device memory.  The paper has
+ * no counterpart; it serves embedders such as an in-situ adaptor linked into
+ * a simulation whose memory pool owns the whole device, a plugin whose host
+ * application forbids side allocations, or a latency-critical loop that
+ * cannot afford the implicit synchronisation a cudaMalloc/cudaFree may
+ * cause.  Every other entry point needs a volume, and creating one
+ * allocates.
+ *
+ * Computes exactly what mboit_render_moments(MBOIT_MOMENTS_REDUCED) computes
+ * for a volume described by `desc` whose selected bricks are those with
+ * brick_selected[b] != 0 (HOST array of nbx*nby*nbz bytes; NULL = every
+ * brick), with no volume object.  The caller passes everything else: desc
+ * (field DEVICE pointer, borrowed; transfer function HOST pointer, read
+ * during the call), views (HOST), moments (DEVICE, n_views REDUCED slabs).
+ *
+ * Its scratch (work-queue head and counters, the converted transfer
+ * function, the brick mask) lives in one fixed device array of
+ * 256 + 4096 + 1,048,576 bytes inside the library, which every device that
+ * loads the library keeps until the process exits.  Limit: at most
+ * 1,048,576 bricks (MBOIT_ERR_INVALID_ARG beyond).  The call makes no
+ * cudaMalloc, cudaFree or other allocating call.  Its first call on a
+ * device looks up the array's device address (set-up) and should come
+ * before any stream capture on that device.  All calls share the array:
+ * calls whose work overlaps on the GPU (two streams, or two host threads)
+ * race and give wrong results; order them on one stream.  A brick mask from
+ * pinned memory must stay unchanged until the call's work has run. */
+MBOIT_API mboit_status mboit_render_moments_noalloc(const mboit_volume_desc* desc, const uint8_t* brick_selected,
+                                                    const mboit_view* views, int32_t n_views, void* moments,
+                                                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,8 @@ MBOIT_FLAG_RAW_SUM, MBOIT_FLAG_DETERMINISTIC = 0x1, 0x2
 
 EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume", "mboit_destroy_volume",
             "mboit_add_piece", "mboit_render_moments", "mboit_reconstruct_blend", "mboit_composite",
-            "mboit_render_frame", "mboit_render_frame_host", "mboit_synchronize", "mboit_get_stats"]
+            "mboit_render_frame", "mboit_render_frame_host", "mboit_synchronize", "mboit_get_stats",
+            "mboit_render_moments_noalloc"]
 
 
 class MboitError(RuntimeError):
@@ -86,6 +87,7 @@ def load_library(path=LIB_PATH):
         "mboit_render_frame_host": (ctypes.c_int, [P, P, P, I32, P, P, P, P]),
         "mboit_synchronize": (ctypes.c_int, [P, P]),
         "mboit_get_stats": (ctypes.c_int, [P, P]),
+        "mboit_render_moments_noalloc": (ctypes.c_int, [P, P, P, I32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -221,6 +223,31 @@ def mboit_get_stats(v):
     s = mboit_stats()
     _check(load_library().mboit_get_stats(v, ctypes.byref(s)))
     return {k: getattr(s, k) for k, _ in mboit_stats._fields_}
+
+
+def grid_desc(scene, field, flags=0):
+    """mboit_volume_desc for a regular-grid scene whose field is the CUDA
+    tensor `field`; returns (desc, keepalive) - keep both while in use."""
+    tf = np.ascontiguousarray(scene.tf, dtype=np.float32)
+    d = mboit_volume_desc()
+    d.kind, d.moment_set, d.storage, d.flags = MBOIT_GRID, MBOIT_POWER4, MBOIT_STORE_F32, flags
+    d.field = field.data_ptr()
+    nz, ny, nx = scene.field.shape
+    d.dims[:] = [nx, ny, nz]
+    d.brick_log2 = scene.brick_log2
+    d.tf_rgba = tf.ctypes.data
+    d.tf_range[:] = [float(scene.tf_range[0]), float(scene.tf_range[1])]
+    d.step, d.moment_bias = float(scene.step), float(scene.moment_bias)
+    d.overestimation, d.absorbance_max = float(scene.overestimation), float(scene.absorbance_max)
+    return d, (tf, field)
+
+
+def mboit_render_moments_noalloc(desc, views, moments, brick_selected=None, stream=None):
+    """Pass 1 without any device allocation (see include/mboit.h)."""
+    arr, n = _views(views)
+    sel = None if brick_selected is None else np.ascontiguousarray(brick_selected, dtype=np.uint8)
+    _check(load_library().mboit_render_moments_noalloc(ctypes.byref(desc), _ptr(sel), arr, n, _ptr(moments),
+                                                       _stream(stream)))
 
 
 # ---------------------------------------------------------------------------

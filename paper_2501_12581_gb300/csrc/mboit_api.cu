@@ -559,3 +559,122 @@ mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Pass 1 with no device allocation: scratch in a fixed device array.
+
+namespace {
+
+constexpr size_t kNoallocMaxBricks = size_t(1) << 20;
+constexpr size_t kNoallocTfOff = 256;
+constexpr size_t kNoallocSelOff = kNoallocTfOff + 256 * sizeof(float4);
+constexpr size_t kNoallocBytes = kNoallocSelOff + kNoallocMaxBricks;
+static_assert(sizeof(mb::Counters) <= kNoallocTfOff, "counters must fit their slot");
+
+// Work-queue head, sample counters, transfer function and brick mask of
+// mboit_render_moments_noalloc.  Host code must not use its name as an
+// address: the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_dev[kNoallocMaxDevices] = {};
+
+}  // namespace
+
+extern "C" mboit_status mboit_render_moments_noalloc(const mboit_volume_desc* d, const uint8_t* brick_selected,
+                                                     const mboit_view* views, int32_t n_views, void* moments,
+                                                     void* stream) {
+    g_err.clear();
+    if (!d || !moments) return fail(MBOIT_ERR_INVALID_ARG, "desc and moments must be non-NULL");
+    if (d->kind != MBOIT_GRID) return fail(MBOIT_ERR_UNSUPPORTED, "only MBOIT_GRID volumes are implemented");
+    if (d->moment_set != MBOIT_POWER4 || d->storage != MBOIT_STORE_F32)
+        return fail(MBOIT_ERR_UNSUPPORTED, "only float32 power moments are implemented");
+    if (d->flags & ~(MBOIT_FLAG_RAW_SUM | MBOIT_FLAG_DETERMINISTIC)) return fail(MBOIT_ERR_INVALID_ARG, "unknown flag bits");
+    if (!d->field || !d->tf_rgba) return fail(MBOIT_ERR_INVALID_ARG, "field and tf_rgba must be non-NULL");
+    for (int c = 0; c < 3; ++c)
+        if (d->dims[c] < 2 || d->dims[c] > (1 << 20)) return fail(MBOIT_ERR_INVALID_ARG, "dims must be in [2, 2^20]");
+    if (d->brick_log2 < 0 || d->brick_log2 > 7) return fail(MBOIT_ERR_INVALID_ARG, "brick_log2 must be in [0, 7]");
+    if (!std::isfinite(d->tf_range[0]) || !std::isfinite(d->tf_range[1]) || !(d->tf_range[1] > d->tf_range[0]))
+        return fail(MBOIT_ERR_INVALID_ARG, "tf_range must be finite with tf_range[1] > tf_range[0]");
+    int ex = 0;
+    if (!(d->step > 0.0f) || !std::isfinite(d->step) || std::frexp(d->step, &ex) != 0.5f)
+        return fail(MBOIT_ERR_INVALID_ARG, "step must be a positive power of two");
+    if (!(d->moment_bias >= 0.0f && d->moment_bias < 1.0f)) return fail(MBOIT_ERR_INVALID_ARG, "moment_bias must be in [0, 1)");
+    if (!(d->absorbance_max > 0.0f) || !std::isfinite(d->absorbance_max))
+        return fail(MBOIT_ERR_INVALID_ARG, "absorbance_max must be positive");
+    const int B = 1 << d->brick_log2;
+    const int64_t nbx = (d->dims[0] - 1 + B - 1) / B, nby = (d->dims[1] - 1 + B - 1) / B,
+                  nbz = (d->dims[2] - 1 + B - 1) / B;
+    const int64_t nbricks = nbx * nby * nbz;
+    if (nbricks > (int64_t)kNoallocMaxBricks)
+        return fail(MBOIT_ERR_INVALID_ARG, "the volume has " + std::to_string(nbricks) +
+                                               " bricks; the allocation-free pass 1 handles at most " +
+                                               std::to_string(kNoallocMaxBricks) + " (use a larger brick_log2)");
+    float4 tf[256];  // converted on the stack: the copy below stages pageable memory before returning
+    for (int j = 0; j < 256; ++j) {
+        const float* e = d->tf_rgba + 4 * j;
+        for (int c = 0; c < 4; ++c)
+            if (!std::isfinite(e[c])) return fail(MBOIT_ERR_INVALID_ARG, "non-finite transfer-function entry");
+        if (!(e[3] >= 0.0f && e[3] < 1.0f)) return fail(MBOIT_ERR_INVALID_ARG, "transfer-function alpha must be in [0, 1)");
+        tf[j] = make_float4(e[0], e[1], e[2], (float)(-std::log1p(-(double)e[3]) * (double)d->step));
+    }
+    mb::ViewTable vt;
+    mboit_status st = build_views(views, n_views, vt);
+    if (st != MBOIT_OK) return st;
+
+    int dev = 0;
+    MB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(MBOIT_ERR_UNSUPPORTED, "device index too large");
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, d->field) != cudaSuccess ||
+        (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) || attr.device != dev) {
+        cudaGetLastError();
+        return fail(MBOIT_ERR_INVALID_ARG, "field must be a device pointer on the current device");
+    }
+    unsigned char* scratch = nullptr;
+    {
+        // set-up, once per device, with that device current
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_dev[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p)
+                return fail(MBOIT_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+            g_noalloc_dev[dev] = static_cast<unsigned char*>(p);
+        }
+        scratch = g_noalloc_dev[dev];
+    }
+
+    mb::GridD g{};
+    g.field = d->field;
+    g.nx = d->dims[0];
+    g.ny = d->dims[1];
+    g.nz = d->dims[2];
+    g.brick_log2 = d->brick_log2;
+    g.nbx = (int32_t)nbx;
+    g.nby = (int32_t)nby;
+    g.nbz = (int32_t)nbz;
+    g.hx = (float)(g.nx - 1);
+    g.hy = (float)(g.ny - 1);
+    g.hz = (float)(g.nz - 1);
+    g.step = d->step;
+    g.tf_scale = (float)(255.0 / ((double)d->tf_range[1] - (double)d->tf_range[0]));
+    g.tf_bias = (float)(-(double)d->tf_range[0] * 255.0 / ((double)d->tf_range[1] - (double)d->tf_range[0]));
+    g.absorbance_max = d->absorbance_max;
+    g.moment_bias = d->moment_bias;
+    g.overestimation = d->overestimation;
+    g.bias_vector[1] = 0.375f;
+    g.bias_vector[3] = 0.375f;
+    g.flags = d->flags;
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    mb::Counters* ctr = reinterpret_cast<mb::Counters*>(scratch);
+    float4* tf_dev = reinterpret_cast<float4*>(scratch + kNoallocTfOff);
+    uint8_t* sel_dev = brick_selected ? scratch + kNoallocSelOff : nullptr;
+    MB_CUDA(cudaMemsetAsync(ctr, 0, sizeof(mb::Counters), s));  // the array keeps the last call's contents
+    MB_CUDA(cudaMemcpyAsync(tf_dev, tf, sizeof tf, cudaMemcpyHostToDevice, s));
+    if (sel_dev) MB_CUDA(cudaMemcpyAsync(sel_dev, brick_selected, (size_t)nbricks, cudaMemcpyHostToDevice, s));
+    MB_CUDA(mb::launch_pass1_fused(g, tf_dev, sel_dev, vt, moments, ctr, s));
+    return MBOIT_OK;
+}
