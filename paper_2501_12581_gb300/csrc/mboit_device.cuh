@@ -82,9 +82,19 @@ MB_HD float flog2(float x) {
 }
 MB_HD float fexp2(float x) {
 #if defined(__CUDA_ARCH__)
-    return exp2f(x);
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));  // one MUFU op, ~2 ulp
+    return y;
 #else
     return exp2f(x);
+#endif
+}
+// square root for values that only steer a continuous result (not correctly rounded)
+MB_HD float fsqrt_fast(float x) {
+#if defined(__CUDA_ARCH__)
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+#else
+    return sqrtf(x);
 #endif
 }
 MB_HD float fdiv_fast(float a, float b) {
@@ -269,7 +279,7 @@ MB_HD float bound_fraction(const Frame& F, float z0, float w0) {
             float c1 = ffma(-g, e, x0);
             float c0 = 1.0f - e;
             float disc = fmax_(ffma(c1, c1, -4.0f * e * c0), 0.0f);
-            float sq = fsqrt(disc);
+            float sq = fsqrt_fast(disc);
             float h = -0.5f * (c1 + (c1 >= 0.0f ? sq : -sq));
             float ra = fdiv_fast(h, e), rb = fdiv_fast(c0, h);
             float x1 = fmin_(ra, rb);

@@ -29,11 +29,10 @@ namespace {
 
 __device__ __forceinline__ float one_minus_exp_neg(float a) {
     // 1 - e^-a without cancellation: Taylor series a * sum_{n>=0} (-a)^n / (n+1)!
-    // for a < 1/2 (truncation error < 1e-8 relative), direct form above.
-    if (a < 0.5f) {
-        float p = ffma(a, -1.0f / 40320.0f, 1.0f / 5040.0f);
-        p = ffma(a, p, -1.0f / 720.0f);
-        p = ffma(a, p, 1.0f / 120.0f);
+    // truncated after (-a)^5/6! for a < 1/4 (relative error < 5e-8); the
+    // direct form above, where cancellation costs at most a few ulp.
+    if (a < 0.25f) {
+        float p = ffma(a, -1.0f / 720.0f, 1.0f / 120.0f);
         p = ffma(a, p, -1.0f / 24.0f);
         p = ffma(a, p, 1.0f / 6.0f);
         p = ffma(a, p, -0.5f);
@@ -114,123 +113,283 @@ __device__ __forceinline__ float4 resolve_pixel(float4 C, float m0, float4 bg, b
 
 // ------------------------------------------------------------------------
 // fused, persistent passes
+//
+// Warp-cooperative staging.  The 32 rays of a warp advance in lockstep over
+// the lattice index k; at one k their sample points lie a few voxels apart.
+// For a window of S consecutive indices the warp takes the bounding box of
+// the cells its samples can touch (from the exact float32 positions of each
+// lane's first and last sample in the window: positions are monotone in t,
+// so every sample in between lies inside), and if the box fits a WX x WY x WZ
+// block, the warp copies that block of the field into its own shared-memory
+// slot once, then reads all trilinear corners from shared memory.  Each field
+// row is fetched once per window instead of eight times per lattice step.  A
+// box that does not fit (widely spread rays) falls back to direct loads.
 
-template <bool kSel>
-__global__ void __launch_bounds__(256) k_pass1_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
-                                                     const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
-                                                     char* __restrict__ moments, Counters* __restrict__ ctr) {
-    __shared__ float s_sig[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_sig[i] = tf[i].w;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const float lo[3] = {0.0f, 0.0f, 0.0f};
-    const float hi[3] = {g.hx, g.hy, g.hz};
-    for (;;) {
-        int tile = 0;
-        if (lane == 0) tile = atomicAdd(&ctr->tile_next[0], 1);
-        tile = __shfl_sync(0xffffffffu, tile, 0);
-        if (tile >= vt.total_tiles) break;
-        const int vi = find_view(vt, tile);
-        const ViewSlot& S = vt.s[vi];
-        const int lt = tile - S.tile_base;
-        const int px = (lt % S.ntx) * kTileW + (lane & 7);
-        const int py = (lt / S.ntx) * kTileH + (lane >> 3);
-        unsigned n = 0;
-        if (px < S.v.width && py < S.v.height) {
-            float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f;
-            float o[3], d[3];
-            make_ray(S.v, px, py, o, d);
-            int k0, k1;
-            if (lattice_range(o, d, lo, hi, g.step, &k0, &k1)) {
-                const float wa = S.v.warp_a, wb = S.v.warp_b;
-                for (int k = k0; k <= k1; ++k) {
-                    const float t = lattice_t(k, g.step);
-                    float val;
-                    if (!field_sample<kSel>(g, sel, t, o, d, val)) continue;
-                    int i;
-                    const float f = tf_coord(g, val, i);
-                    const float s0 = s_sig[i], s1 = s_sig[i + 1];
-                    const float a = fmin_(ffma(f, s1 - s0, s0), g.absorbance_max);
-                    const float z = warp_depth(t, wa, wb);
-                    m0 += a;
-                    float az = a * z;
-                    m1 += az;
-                    az *= z;
-                    m2 += az;
-                    az *= z;
-                    m3 += az;
-                    az *= z;
-                    m4 += az;
-                    ++n;
-                }
-            }
-            store_moments(moments, S, S.moment_off, py * S.v.width + px, m0, m1, m2, m3, m4);
+template <int S_, int WX_, int WY_, int WZ_>
+struct StageCfg {
+    static constexpr int S = S_, WX = WX_, WY = WY_, WZ = WZ_;
+    static constexpr int Pitch = WX_ + 1;          // padded row: spreads shared-memory banks
+    static constexpr int Plane = WY_ * Pitch;
+    static constexpr int Floats = WZ_ * Plane;
+    static constexpr int Elems = WX_ * WY_ * WZ_;
+};
+using DefaultStage = StageCfg<6, 8, 8, 8>;
+constexpr int kFusedWarps = 8;  // 256 threads per CTA
+
+__device__ __forceinline__ float trilinear8(float v000, float v100, float v010, float v110, float v001, float v101,
+                                            float v011, float v111, float fx, float fy, float fz) {
+    const float a00 = ffma(fx, v100 - v000, v000), a10 = ffma(fx, v110 - v010, v010);
+    const float a01 = ffma(fx, v101 - v001, v001), a11 = ffma(fx, v111 - v011, v011);
+    const float b0 = ffma(fy, a10 - a00, a00), b1 = ffma(fy, a11 - a01, a01);
+    return ffma(fz, b1 - b0, b0);
+}
+
+// Bounding box of the cells that lane samples in [ka, kz] can touch, reduced
+// over the warp; true if it fits the window.
+template <class Cfg>
+__device__ __forceinline__ bool window_box(const GridD& g, const float o[3], const float d[3], int ka, int kz,
+                                           int LO[3]) {
+    const unsigned full = 0xffffffffu;
+    const int nmax[3] = {g.nx - 1, g.ny - 1, g.nz - 1};
+    int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-1, -1, -1};
+    if (ka <= kz) {
+        const float ta = lattice_t(ka, g.step), tz = lattice_t(kz, g.step);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float pa = ffma(ta, d[c], o[c]), pz = ffma(tz, d[c], o[c]);
+            lo[c] = max((int)floorf(fmin_(pa, pz)), 0);
+            hi[c] = min((int)floorf(fmax_(pa, pz)) + 1, nmax[c]);
         }
-        warp_add_u64(&ctr->samples[0], n);
+    }
+    bool fits = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        LO[c] = __reduce_min_sync(full, lo[c]);
+        const int HI = __reduce_max_sync(full, hi[c]);
+        const int ext = c == 0 ? Cfg::WX : (c == 1 ? Cfg::WY : Cfg::WZ);
+        fits = fits && HI >= LO[c] && HI - LO[c] < ext;
+    }
+    return fits;
+}
+
+// Marches the lattice indices [k0, k1] of this lane's ray (exactly the
+// in-domain points; k0 > k1: none), calling body(t, value) for every owned
+// sample in depth order.  All 32 lanes of the warp call it together.
+template <class Cfg, bool kSel, class Body>
+__device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __restrict__ sel, float* __restrict__ win,
+                                            const float o[3], const float d[3], int k0, int k1, Body& body) {
+    const unsigned full = 0xffffffffu;
+    const int kmin = __reduce_min_sync(full, k0);
+    const int kmax = __reduce_max_sync(full, k1);
+    const int nmax[3] = {g.nx - 1, g.ny - 1, g.nz - 1};
+    for (int kb = kmin; kb <= kmax;) {
+        // the longest window (2S, then S steps) whose box fits
+        int LO[3];
+        int ke = min(kb + 2 * Cfg::S - 1, kmax);
+        bool fits = window_box<Cfg>(g, o, d, max(kb, k0), min(ke, k1), LO);
+        if (!fits && ke > kb + Cfg::S - 1) {
+            ke = kb + Cfg::S - 1;
+            fits = window_box<Cfg>(g, o, d, max(kb, k0), min(ke, k1), LO);
+        }
+        const int ka = max(kb, k0), kz = min(ke, k1);
+        if (fits) {
+            __syncwarp();
+            const int lane = threadIdx.x & 31;
+#pragma unroll 4
+            for (int e = lane; e < Cfg::Elems; e += 32) {
+                const int x = e % Cfg::WX, y = (e / Cfg::WX) % Cfg::WY, z = e / (Cfg::WX * Cfg::WY);
+                const int gx = min(LO[0] + x, nmax[0]), gy = min(LO[1] + y, nmax[1]), gz = min(LO[2] + z, nmax[2]);
+                win[z * Cfg::Plane + y * Cfg::Pitch + x] =
+                    __ldg(g.field + ((size_t)gz * g.ny + gy) * (size_t)g.nx + gx);
+            }
+            __syncwarp();
+            const float* wbase = win - (LO[2] * Cfg::WY + LO[1]) * Cfg::Pitch - LO[0];
+            float t = lattice_t(ka, g.step);  // t_{k+1} = t_k + step exactly (multiples of step/2 below 2^24)
+            for (int k = ka; k <= kz; ++k, t += g.step) {
+                const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
+                const int ix = (int)p0, iy = (int)p1, iz = (int)p2;
+                if (kSel) {
+                    const int b = ((iz >> g.brick_log2) * g.nby + (iy >> g.brick_log2)) * g.nbx + (ix >> g.brick_log2);
+                    if (!__ldg(sel + b)) continue;
+                }
+                const float* c = wbase + (iz * Cfg::WY + iy) * Cfg::Pitch + ix;
+                const float val = trilinear8(c[0], c[1], c[Cfg::Pitch], c[Cfg::Pitch + 1], c[Cfg::Plane],
+                                             c[Cfg::Plane + 1], c[Cfg::Plane + Cfg::Pitch],
+                                             c[Cfg::Plane + Cfg::Pitch + 1], p0 - (float)ix, p1 - (float)iy,
+                                             p2 - (float)iz);
+                body(t, val);
+            }
+        } else {
+            float t = lattice_t(ka, g.step);
+            for (int k = ka; k <= kz; ++k, t += g.step) {
+                float val;
+                if (!field_sample<kSel>(g, sel, t, o, d, val)) continue;
+                body(t, val);
+            }
+        }
+        kb = ke + 1;
     }
 }
 
-template <bool kSel, int kMode>
+// Alg. 2 per sample: absorbance a = min(sigma*step, A_max), b_j += a z^j.
+struct MomentBody {
+    const float2* s_sig;  // (sigma*step of entry i, of entry i+1 minus entry i)
+    float tf_scale, tf_bias, amax, wa, wb;
+    float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f;
+    unsigned n = 0;
+    __device__ __forceinline__ void operator()(float t, float val) {
+        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+        const int i = min((int)xt, 254);
+        const float f = xt - (float)i;
+        const float2 s = s_sig[i];
+        const float a = fmin_(ffma(f, s.y, s.x), amax);
+        const float z = warp_depth(t, wa, wb);
+        m0 += a;
+        float az = a * z;
+        m1 += az;
+        az *= z;
+        m2 += az;
+        az *= z;
+        m3 += az;
+        az *= z;
+        m4 += az;
+        ++n;
+    }
+};
+
+// Alg. 1 loop 2 per sample: colour += T(z) * alpha * (r, g, b, 1).
+struct BlendBody {
+    const float4* s_tf;   // [2*i] = entry i (r, g, b, sigma*step), [2*i+1] = entry i+1 minus entry i
+    Frame F;
+    float tf_scale, tf_bias, amax, wa, wb, w0;
+    float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    unsigned n = 0;
+    __device__ __forceinline__ void operator()(float t, float val) {
+        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+        const int i = min((int)xt, 254);
+        const float f = xt - (float)i;
+        const float4 e0 = s_tf[2 * i], de = s_tf[2 * i + 1];
+        const float a = fmin_(ffma(f, de.w, e0.w), amax);
+        const float alpha = one_minus_exp_neg(a);
+        const float z = warp_depth(t, wa, wb);
+        const float wgt = transmittance(F, z, w0) * alpha;
+        C.x = ffma(wgt, ffma(f, de.x, e0.x), C.x);
+        C.y = ffma(wgt, ffma(f, de.y, e0.y), C.y);
+        C.z = ffma(wgt, ffma(f, de.z, e0.z), C.z);
+        C.w += wgt;
+        ++n;
+    }
+};
+
+// Pops the next 8x4 ray tile of the work queue; returns false when empty.
+__device__ __forceinline__ bool next_tile(const ViewTable& vt, int32_t* head, int& vi, int& px, int& py) {
+    const int lane = threadIdx.x & 31;
+    int tile = 0;
+    if (lane == 0) tile = atomicAdd(head, 1);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= vt.total_tiles) return false;
+    vi = find_view(vt, tile);
+    const ViewSlot& S = vt.s[vi];
+    const int lt = tile - S.tile_base;
+    px = (lt % S.ntx) * kTileW + (lane & 7);
+    py = (lt / S.ntx) * kTileH + (lane >> 3);
+    return true;
+}
+
+__device__ __forceinline__ bool inside_domain(const GridD& g, const float o[3], const float d[3], int k) {
+    const float t = lattice_t(k, g.step);
+    const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
+    return p0 >= 0.0f && p0 < g.hx && p1 >= 0.0f && p1 < g.hy && p2 >= 0.0f && p2 < g.hz;
+}
+
+// Ray of pixel (px, py) and the exact interval [k0, k1] of lattice indices
+// whose float32 positions lie inside the domain (k0 > k1 if none).  Each
+// coordinate of fma(t, d, o) is monotone in t, so the inside set of a box is
+// one interval: it is found by shrinking the conservative range.
+__device__ __forceinline__ void ray_range(const GridD& g, const ViewD& V, bool valid, int px, int py, float o[3],
+                                          float d[3], int& k0, int& k1) {
+    k0 = 0x7fffffff;
+    k1 = -1;
+    o[0] = o[1] = o[2] = 0.0f;
+    d[0] = d[1] = d[2] = 0.0f;
+    if (!valid) return;
+    make_ray(V, px, py, o, d);
+    const float lo[3] = {0.0f, 0.0f, 0.0f};
+    const float hi[3] = {g.hx, g.hy, g.hz};
+    int a, b;
+    if (!lattice_range(o, d, lo, hi, g.step, &a, &b)) return;
+    while (a <= b && !inside_domain(g, o, d, a)) ++a;
+    while (b >= a && !inside_domain(g, o, d, b)) --b;
+    if (a <= b) {
+        k0 = a;
+        k1 = b;
+    }
+}
+
+template <bool kSel, class Cfg>
+__global__ void __launch_bounds__(256) k_pass1_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
+                                                     const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
+                                                     char* __restrict__ moments, Counters* __restrict__ ctr) {
+    __shared__ float2 s_sig[256];
+    __shared__ float s_win[kFusedWarps][Cfg::Floats];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const float s0 = tf[i].w;
+        s_sig[i] = make_float2(s0, i < 255 ? tf[i + 1].w - s0 : 0.0f);
+    }
+    __syncthreads();
+    float* win = s_win[threadIdx.x >> 5];
+    int vi, px, py;
+    while (next_tile(vt, &ctr->tile_next[0], vi, px, py)) {
+        const ViewSlot& S = vt.s[vi];
+        const bool valid = px < S.v.width && py < S.v.height;
+        float o[3], d[3];
+        int k0, k1;
+        ray_range(g, S.v, valid, px, py, o, d, k0, k1);
+        MomentBody body{s_sig, g.tf_scale, g.tf_bias, g.absorbance_max, S.v.warp_a, S.v.warp_b};
+        march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
+        if (valid)
+            store_moments(moments, S, S.moment_off, py * S.v.width + px, body.m0, body.m1, body.m2, body.m3, body.m4);
+        warp_add_u64(&ctr->samples[0], body.n);
+    }
+}
+
+template <bool kSel, int kMode, class Cfg>
 __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
                                                      const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                      const char* __restrict__ moments, float* __restrict__ color,
                                                      Counters* __restrict__ ctr) {
-    __shared__ float4 s_tf[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = tf[i];
+    __shared__ float4 s_tf[512];
+    __shared__ float s_win[kFusedWarps][Cfg::Floats];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const float4 e0 = tf[i], e1 = i < 255 ? tf[i + 1] : tf[i];
+        s_tf[2 * i] = e0;
+        s_tf[2 * i + 1] = make_float4(e1.x - e0.x, e1.y - e0.y, e1.z - e0.z, e1.w - e0.w);
+    }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const float lo[3] = {0.0f, 0.0f, 0.0f};
-    const float hi[3] = {g.hx, g.hy, g.hz};
-    const float w0 = g.overestimation;
+    float* win = s_win[threadIdx.x >> 5];
     const bool raw = (g.flags & 1u) != 0;
-    for (;;) {
-        int tile = 0;
-        if (lane == 0) tile = atomicAdd(&ctr->tile_next[1], 1);
-        tile = __shfl_sync(0xffffffffu, tile, 0);
-        if (tile >= vt.total_tiles) break;
-        const int vi = find_view(vt, tile);
+    int vi, px, py;
+    while (next_tile(vt, &ctr->tile_next[1], vi, px, py)) {
         const ViewSlot& S = vt.s[vi];
-        const int lt = tile - S.tile_base;
-        const int px = (lt % S.ntx) * kTileW + (lane & 7);
-        const int py = (lt / S.ntx) * kTileH + (lane >> 3);
-        unsigned n = 0;
-        if (px < S.v.width && py < S.v.height) {
-            const int pix = py * S.v.width + px;
-            float m[5];
-            load_moments(moments, S, S.moment_off, pix, m);
-            const Frame F = make_frame(m, g.moment_bias, g.bias_vector);
-            if (F.kind == kFrameOneAtom || F.kind == kFrameTwoAtoms) atomicAdd(&ctr->singular, 1ull);
-            float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            float o[3], d[3];
-            make_ray(S.v, px, py, o, d);
-            int k0, k1;
-            if (lattice_range(o, d, lo, hi, g.step, &k0, &k1)) {
-                const float wa = S.v.warp_a, wb = S.v.warp_b;
-                for (int k = k0; k <= k1; ++k) {
-                    const float t = lattice_t(k, g.step);
-                    float val;
-                    if (!field_sample<kSel>(g, sel, t, o, d, val)) continue;
-                    int i;
-                    const float f = tf_coord(g, val, i);
-                    const float4 e0 = s_tf[i], e1 = s_tf[i + 1];
-                    const float a = fmin_(ffma(f, e1.w - e0.w, e0.w), g.absorbance_max);
-                    const float alpha = one_minus_exp_neg(a);
-                    const float z = warp_depth(t, wa, wb);
-                    const float wgt = transmittance(F, z, w0) * alpha;
-                    C.x = ffma(wgt, ffma(f, e1.x - e0.x, e0.x), C.x);
-                    C.y = ffma(wgt, ffma(f, e1.y - e0.y, e0.y), C.y);
-                    C.z = ffma(wgt, ffma(f, e1.z - e0.z, e0.z), C.z);
-                    C.w += wgt;
-                    ++n;
-                }
-            }
+        const bool valid = px < S.v.width && py < S.v.height;
+        const int pix = valid ? py * S.v.width + px : 0;
+        float m[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (valid) load_moments(moments, S, S.moment_off, pix, m);
+        BlendBody body{s_tf, make_frame(m, g.moment_bias, g.bias_vector), g.tf_scale, g.tf_bias, g.absorbance_max,
+                       S.v.warp_a, S.v.warp_b, g.overestimation};
+        if (valid && (body.F.kind == kFrameOneAtom || body.F.kind == kFrameTwoAtoms)) atomicAdd(&ctr->singular, 1ull);
+        float o[3], d[3];
+        int k0, k1;
+        ray_range(g, S.v, valid, px, py, o, d, k0, k1);
+        march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
+        if (valid) {
             float4* out = reinterpret_cast<float4*>(color + S.color_off) + pix;
             if (kMode == kColorResolved)
-                *out = resolve_pixel(C, m[0], make_float4(0.0f, 0.0f, 0.0f, 0.0f), raw);
+                *out = resolve_pixel(body.C, m[0], make_float4(0.0f, 0.0f, 0.0f, 0.0f), raw);
             else
-                *out = C;
+                *out = body.C;
         }
-        warp_add_u64(&ctr->samples[1], n);
+        warp_add_u64(&ctr->samples[1], body.n);
     }
 }
 
@@ -450,9 +609,9 @@ int persistent_blocks(K kernel, int threads) {
 cudaError_t prepare_kernels() {
     // Loads every kernel and fills the occupancy caches, so that no module
     // loading happens later inside a stream capture.
-    const void* fns[] = {(const void*)k_pass1_fused<true>, (const void*)k_pass1_fused<false>,
-                         (const void*)k_pass2_fused<true, kColorReduced>, (const void*)k_pass2_fused<true, kColorResolved>,
-                         (const void*)k_pass2_fused<false, kColorReduced>, (const void*)k_pass2_fused<false, kColorResolved>,
+    const void* fns[] = {(const void*)k_pass1_fused<true, DefaultStage>, (const void*)k_pass1_fused<false, DefaultStage>,
+                         (const void*)k_pass2_fused<true, kColorReduced, DefaultStage>, (const void*)k_pass2_fused<true, kColorResolved, DefaultStage>,
+                         (const void*)k_pass2_fused<false, kColorReduced, DefaultStage>, (const void*)k_pass2_fused<false, kColorResolved, DefaultStage>,
                          (const void*)k_pass1_piece, (const void*)k_pass2_piece, (const void*)k_moments_sum,
                          (const void*)k_color_resolve};
     for (const void* f : fns) {
@@ -460,12 +619,12 @@ cudaError_t prepare_kernels() {
         const cudaError_t e = cudaFuncGetAttributes(&a, f);
         if (e != cudaSuccess) return e;
     }
-    persistent_blocks(k_pass1_fused<true>, 256);
-    persistent_blocks(k_pass1_fused<false>, 256);
-    persistent_blocks(k_pass2_fused<true, kColorReduced>, 256);
-    persistent_blocks(k_pass2_fused<true, kColorResolved>, 256);
-    persistent_blocks(k_pass2_fused<false, kColorReduced>, 256);
-    persistent_blocks(k_pass2_fused<false, kColorResolved>, 256);
+    persistent_blocks(k_pass1_fused<true, DefaultStage>, 256);
+    persistent_blocks(k_pass1_fused<false, DefaultStage>, 256);
+    persistent_blocks(k_pass2_fused<true, kColorReduced, DefaultStage>, 256);
+    persistent_blocks(k_pass2_fused<true, kColorResolved, DefaultStage>, 256);
+    persistent_blocks(k_pass2_fused<false, kColorReduced, DefaultStage>, 256);
+    persistent_blocks(k_pass2_fused<false, kColorResolved, DefaultStage>, 256);
     return cudaGetLastError();
 }
 
@@ -474,11 +633,11 @@ cudaError_t launch_pass1_fused(const GridD& g, const float4* tf, const uint8_t* 
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     if (brick_sel) {
-        const int nb = persistent_blocks(k_pass1_fused<true>, 256);
-        k_pass1_fused<true><<<nb, 256, 0, s>>>(g, tf, brick_sel, vt, static_cast<char*>(moments), ctr);
+        const int nb = persistent_blocks(k_pass1_fused<true, DefaultStage>, 256);
+        k_pass1_fused<true, DefaultStage><<<nb, 256, 0, s>>>(g, tf, brick_sel, vt, static_cast<char*>(moments), ctr);
     } else {
-        const int nb = persistent_blocks(k_pass1_fused<false>, 256);
-        k_pass1_fused<false><<<nb, 256, 0, s>>>(g, tf, brick_sel, vt, static_cast<char*>(moments), ctr);
+        const int nb = persistent_blocks(k_pass1_fused<false, DefaultStage>, 256);
+        k_pass1_fused<false, DefaultStage><<<nb, 256, 0, s>>>(g, tf, brick_sel, vt, static_cast<char*>(moments), ctr);
     }
     return cudaGetLastError();
 }
@@ -490,8 +649,8 @@ cudaError_t launch_pass2_fused(const GridD& g, const float4* tf, const uint8_t* 
     const char* m = static_cast<const char*>(moments);
 #define MB_LAUNCH2(SEL, MODE)                                                         \
     do {                                                                              \
-        const int nb = persistent_blocks(k_pass2_fused<SEL, MODE>, 256);              \
-        k_pass2_fused<SEL, MODE><<<nb, 256, 0, s>>>(g, tf, brick_sel, vt, m, color, ctr); \
+        const int nb = persistent_blocks(k_pass2_fused<SEL, MODE, DefaultStage>, 256);              \
+        k_pass2_fused<SEL, MODE, DefaultStage><<<nb, 256, 0, s>>>(g, tf, brick_sel, vt, m, color, ctr); \
     } while (0)
     if (brick_sel) {
         if (mode == kColorResolved) MB_LAUNCH2(true, kColorResolved);
