@@ -136,7 +136,15 @@ typedef struct {
     int64_t singular_pixels;    /* pixels of the last pass 2 whose Hankel matrix took a 1- or 2-atom branch */
     int32_t n_pieces;
     int32_t device;
+    int32_t tuning_pass1;       /* window configuration of the fused passes (see mboit_set_tuning) */
+    int32_t tuning_pass2;
 } mboit_stats;
+
+/* Number of window configurations of the fused passes.  Each fused kernel
+ * stages, per warp, the block of the field its 32 rays traverse over the
+ * next S lattice steps in shared memory; configurations differ in block
+ * shape, S and load width.  All give bit-identical results. */
+#define MBOIT_NUM_TUNINGS 5
 
 /* Message of the last failing call on this thread ("" if none). */
 MBOIT_API const char* mboit_last_error(void);
@@ -217,6 +225,21 @@ MBOIT_API mboit_status mboit_synchronize(mboit_volume v, void* stream);
 
 /* Counters of the last passes (synchronises the stream of the last render). */
 MBOIT_API mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out);
+
+/* Selects the window configuration (0 .. MBOIT_NUM_TUNINGS-1) of the fused
+ * pass 1 and pass 2.  Configurations 2-4 read 16-byte chunks and need
+ * dims[0] % 4 == 0 and a 16-byte aligned field; otherwise
+ * MBOIT_ERR_INVALID_ARG and nothing changes.  Takes effect for the next call;
+ * captured frame graphs are re-recorded. */
+MBOIT_API mboit_status mboit_set_tuning(mboit_volume v, int32_t pass1, int32_t pass2);
+
+/* Autotuner (the benchmark spec batching pattern): times every eligible
+ * configuration of pass 1 and of pass 2 on these views (3 launches each,
+ * CUDA events on `stream`, after one warm launch), keeps the fastest of
+ * each, and writes them to chosen[0..1] (HOST, may be NULL).  The buffers
+ * are as for mboit_render_frame and are overwritten.  Synchronous. */
+MBOIT_API mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch,
+                                      float* rgba, void* stream, int32_t* chosen);
 
 /* Pass 1 for callers that must not allocate device memory.  The paper has
  * no counterpart; it serves embedders such as an in-situ adaptor linked into

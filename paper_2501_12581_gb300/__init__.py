@@ -33,7 +33,8 @@ MBOIT_FLAG_RAW_SUM, MBOIT_FLAG_DETERMINISTIC = 0x1, 0x2
 EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume", "mboit_destroy_volume",
             "mboit_add_piece", "mboit_render_moments", "mboit_reconstruct_blend", "mboit_composite",
             "mboit_render_frame", "mboit_render_frame_host", "mboit_synchronize", "mboit_get_stats",
-            "mboit_render_moments_noalloc"]
+            "mboit_render_moments_noalloc", "mboit_set_tuning", "mboit_autotune"]
+MBOIT_NUM_TUNINGS = 5
 
 
 class MboitError(RuntimeError):
@@ -59,7 +60,8 @@ class mboit_volume_desc(ctypes.Structure):
 
 class mboit_stats(ctypes.Structure):
     _fields_ = [("samples_pass1", ctypes.c_int64), ("samples_pass2", ctypes.c_int64),
-                ("singular_pixels", ctypes.c_int64), ("n_pieces", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("singular_pixels", ctypes.c_int64), ("n_pieces", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("tuning_pass1", ctypes.c_int32), ("tuning_pass2", ctypes.c_int32)]
 
 
 _lib = None
@@ -88,6 +90,8 @@ def load_library(path=LIB_PATH):
         "mboit_synchronize": (ctypes.c_int, [P, P]),
         "mboit_get_stats": (ctypes.c_int, [P, P]),
         "mboit_render_moments_noalloc": (ctypes.c_int, [P, P, P, I32, P, P]),
+        "mboit_set_tuning": (ctypes.c_int, [P, I32, I32]),
+        "mboit_autotune": (ctypes.c_int, [P, P, I32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -225,6 +229,17 @@ def mboit_get_stats(v):
     return {k: getattr(s, k) for k, _ in mboit_stats._fields_}
 
 
+def mboit_set_tuning(v, pass1, pass2):
+    _check(load_library().mboit_set_tuning(v, int(pass1), int(pass2)))
+
+
+def mboit_autotune(v, views, moments_scratch, rgba, stream=None):
+    arr, n = _views(views)
+    out = (ctypes.c_int32 * 2)()
+    _check(load_library().mboit_autotune(v, arr, n, _ptr(moments_scratch), _ptr(rgba), _stream(stream), out))
+    return int(out[0]), int(out[1])
+
+
 def grid_desc(scene, field, flags=0):
     """mboit_volume_desc for a regular-grid scene whose field is the CUDA
     tensor `field`; returns (desc, keepalive) - keep both while in use."""
@@ -333,6 +348,12 @@ class Volume:
 
     def synchronize(self, stream=None):
         mboit_synchronize(self.handle, stream)
+
+    def set_tuning(self, pass1, pass2):
+        mboit_set_tuning(self.handle, pass1, pass2)
+
+    def autotune(self, views, moments_scratch, rgba, stream=None):
+        return mboit_autotune(self.handle, views, moments_scratch, rgba, stream)
 
     def stats(self):
         return mboit_get_stats(self.handle)

@@ -70,6 +70,7 @@ struct mboit_volume_s {
     bool sel_uploaded = false;
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphEntry> graphs;
+    int32_t tune1 = 0, tune2 = 0;
     std::mutex mu;
 };
 
@@ -390,7 +391,7 @@ mboit_status mboit_render_moments(mboit_volume v, const mboit_view* views, int32
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->samples[0], 0, sizeof(unsigned long long), s));
     if (mode == MBOIT_MOMENTS_REDUCED) {
-        MB_CUDA(mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s));
+        MB_CUDA(mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1));
     } else {
         const int32_t slots = (int32_t)list.size();
         for (int32_t j = 0; j < slots; ++j)
@@ -426,7 +427,7 @@ mboit_status mboit_reconstruct_blend(mboit_volume v, const mboit_view* views, in
     } else {
         MB_CUDA(mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, global_moments, color,
                                        mode == MBOIT_COLOR_RESOLVED ? mb::kColorResolved : mb::kColorReduced, v->d_ctr,
-                                       s));
+                                       s, v->tune2));
     }
     return MBOIT_OK;
 }
@@ -488,9 +489,11 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
         cudaStream_t cs = v->cap_stream;
         MB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemsetAsync(&v->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), cs);
-        if (e == cudaSuccess) e = mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, cs);
         if (e == cudaSuccess)
-            e = mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba, mb::kColorResolved, v->d_ctr, cs);
+            e = mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, cs, v->tune1);
+        if (e == cudaSuccess)
+            e = mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba, mb::kColorResolved, v->d_ctr, cs,
+                                       v->tune2);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -555,6 +558,81 @@ mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out) {
     out->singular_pixels = (int64_t)c.singular;
     out->n_pieces = (int32_t)v->boxes.size();
     out->device = v->device;
+    out->tuning_pass1 = v->tune1;
+    out->tuning_pass2 = v->tune2;
+    return MBOIT_OK;
+}
+
+mboit_status mboit_set_tuning(mboit_volume v, int32_t pass1, int32_t pass2) {
+    g_err.clear();
+    if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
+    if (!mb::stage_config_eligible(v->grid, pass1) || !mb::stage_config_eligible(v->grid, pass2))
+        return fail(MBOIT_ERR_INVALID_ARG, "tuning must be in [0, " + std::to_string(mb::kNumStageConfigs - 1) +
+                                               "]; 2-4 need dims[0] % 4 == 0 and a 16-byte aligned field");
+    std::lock_guard<std::mutex> lk(v->mu);
+    v->tune1 = pass1;
+    v->tune2 = pass2;
+    drop_graphs(v);
+    return MBOIT_OK;
+}
+
+mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch, float* rgba,
+                            void* stream, int32_t* chosen) {
+    g_err.clear();
+    mboit_status st = check_volume(v);
+    if (st != MBOIT_OK) return st;
+    if (!moments_scratch || !rgba) return fail(MBOIT_ERR_INVALID_ARG, "moments_scratch and rgba must be non-NULL");
+    std::lock_guard<std::mutex> lk(v->mu);
+    DeviceGuard dg(v->device);
+    mb::ViewTable vt;
+    if ((st = build_views(views, n_views, vt)) != MBOIT_OK) return st;
+    std::vector<int32_t> list;
+    const uint8_t* mask = nullptr;
+    if ((st = select_pieces(v, nullptr, 0, list, &mask)) != MBOIT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MB_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(MBOIT_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
+    }
+    float best_ms[2] = {3.0e38f, 3.0e38f};
+    int best[2] = {v->tune1, v->tune2};
+    for (int pass = 0; pass < 2 && ce == cudaSuccess; ++pass) {
+        for (int cfg = 0; cfg < mb::kNumStageConfigs && ce == cudaSuccess; ++cfg) {
+            if (!mb::stage_config_eligible(v->grid, cfg)) continue;
+            auto launch = [&]() {
+                return pass == 0 ? mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s, cfg)
+                                 : mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba,
+                                                          mb::kColorResolved, v->d_ctr, s, cfg);
+            };
+            ce = launch();
+            if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+            for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = launch();
+            if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (ce == cudaSuccess && ms < best_ms[pass]) {
+                best_ms[pass] = ms;
+                best[pass] = cfg;
+            }
+        }
+        // pass 2 is timed on the moments of the fastest pass 1
+        if (pass == 0 && ce == cudaSuccess)
+            ce = mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s, best[0]);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ce != cudaSuccess) return fail(MBOIT_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+    v->tune1 = best[0];
+    v->tune2 = best[1];
+    drop_graphs(v);
+    if (chosen) {
+        chosen[0] = best[0];
+        chosen[1] = best[1];
+    }
     return MBOIT_OK;
 }
 

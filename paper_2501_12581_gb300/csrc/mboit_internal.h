@@ -43,15 +43,22 @@ struct PieceBox {
 
 enum ColorMode : int32_t { kColorPerPiece = 0, kColorReduced = 1, kColorResolved = 2 };
 
+// Number of shared-memory window configurations of the fused passes (the
+// autotuner's choices).  Configurations 2-4 use 16-byte loads and need
+// nx % 4 == 0 and a 16-byte aligned field; 0 and 1 work everywhere.
+constexpr int kNumStageConfigs = 5;
+bool stage_config_eligible(const GridD& g, int cfg);
+
 // Loads all kernels and caches launch shapes (call before any capture).
 cudaError_t prepare_kernels();
 // Fused pass 1 over all selected pieces, REDUCED output.  `brick_sel` NULL
-// means every brick is sampled.
+// means every brick is sampled.  An ineligible `cfg` falls back to 0.
 cudaError_t launch_pass1_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
-                               void* moments, Counters* ctr, cudaStream_t s);
+                               void* moments, Counters* ctr, cudaStream_t s, int cfg = 0);
 // Fused pass 2 over all selected pieces, REDUCED or RESOLVED output.
 cudaError_t launch_pass2_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
-                               const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s);
+                               const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
+                               int cfg = 0);
 // Plain per-piece passes: one launch = one piece, its own slab.
 cudaError_t launch_pass1_piece(const GridD& g, const float4* tf, const int32_t* piece_of_brick, int32_t piece,
                                const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,

@@ -21,6 +21,11 @@
 // piece; the image-space kernels then sum the K images (compensated).
 #include <cuda_runtime.h>
 
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "mboit_internal.h"
 
 namespace mb {
@@ -125,15 +130,24 @@ __device__ __forceinline__ float4 resolve_pixel(float4 C, float m0, float4 bg, b
 // row is fetched once per window instead of eight times per lattice step.  A
 // box that does not fit (widely spread rays) falls back to direct loads.
 
-template <int S_, int WX_, int WY_, int WZ_>
+template <int S_, int WX_, int WY_, int WZ_, bool kVec_>
 struct StageCfg {
     static constexpr int S = S_, WX = WX_, WY = WY_, WZ = WZ_;
-    static constexpr int Pitch = WX_ + 1;          // padded row: spreads shared-memory banks
-    static constexpr int Plane = WY_ * Pitch;
+    static constexpr bool kVec = kVec_;  // 16-byte loads: x origin rounded down to a multiple of 4
+    // scalar windows pad rows to an odd pitch; vector windows keep 16-byte rows
+    // and shift each plane by 4 floats, both to spread shared-memory banks
+    static constexpr int Pitch = kVec_ ? WX_ : WX_ + 1;
+    static constexpr int Plane = kVec_ ? WY_ * WX_ + 4 : WY_ * (WX_ + 1);
     static constexpr int Floats = WZ_ * Plane;
     static constexpr int Elems = WX_ * WY_ * WZ_;
+    static_assert(!kVec_ || WX_ % 4 == 0, "vector windows need a multiple of 4 in x");
 };
-using DefaultStage = StageCfg<6, 8, 8, 8>;
+// The configurations the autotuner chooses from (index = tuning id).
+using Stage0 = StageCfg<6, 8, 8, 8, false>;
+using Stage1 = StageCfg<8, 8, 8, 8, false>;
+using Stage2 = StageCfg<6, 12, 8, 8, true>;
+using Stage3 = StageCfg<8, 12, 10, 10, true>;
+using Stage4 = StageCfg<10, 12, 12, 12, true>;
 constexpr int kFusedWarps = 8;  // 256 threads per CTA
 
 __device__ __forceinline__ float trilinear8(float v000, float v100, float v010, float v110, float v001, float v101,
@@ -166,6 +180,7 @@ __device__ __forceinline__ bool window_box(const GridD& g, const float o[3], con
     for (int c = 0; c < 3; ++c) {
         LO[c] = __reduce_min_sync(full, lo[c]);
         const int HI = __reduce_max_sync(full, hi[c]);
+        if (c == 0 && Cfg::kVec) LO[0] &= ~3;
         const int ext = c == 0 ? Cfg::WX : (c == 1 ? Cfg::WY : Cfg::WZ);
         fits = fits && HI >= LO[c] && HI - LO[c] < ext;
     }
@@ -195,15 +210,29 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
         if (fits) {
             __syncwarp();
             const int lane = threadIdx.x & 31;
+            if (Cfg::kVec) {
+                // nx % 4 == 0 and a 16-byte aligned field (checked by the launcher):
+                // every chunk start gx is a multiple of 4 and gx + 3 < nx
+                constexpr int QX = Cfg::WX / 4;
+#pragma unroll 2
+                for (int e = lane; e < QX * Cfg::WY * Cfg::WZ; e += 32) {
+                    const int xq = e % QX, y = (e / QX) % Cfg::WY, z = e / (QX * Cfg::WY);
+                    const int gx = min(LO[0] + 4 * xq, g.nx - 4), gy = min(LO[1] + y, nmax[1]),
+                              gz = min(LO[2] + z, nmax[2]);
+                    *reinterpret_cast<float4*>(win + z * Cfg::Plane + y * Cfg::Pitch + 4 * xq) =
+                        __ldg(reinterpret_cast<const float4*>(g.field + ((size_t)gz * g.ny + gy) * (size_t)g.nx + gx));
+                }
+            } else {
 #pragma unroll 4
-            for (int e = lane; e < Cfg::Elems; e += 32) {
-                const int x = e % Cfg::WX, y = (e / Cfg::WX) % Cfg::WY, z = e / (Cfg::WX * Cfg::WY);
-                const int gx = min(LO[0] + x, nmax[0]), gy = min(LO[1] + y, nmax[1]), gz = min(LO[2] + z, nmax[2]);
-                win[z * Cfg::Plane + y * Cfg::Pitch + x] =
-                    __ldg(g.field + ((size_t)gz * g.ny + gy) * (size_t)g.nx + gx);
+                for (int e = lane; e < Cfg::Elems; e += 32) {
+                    const int x = e % Cfg::WX, y = (e / Cfg::WX) % Cfg::WY, z = e / (Cfg::WX * Cfg::WY);
+                    const int gx = min(LO[0] + x, nmax[0]), gy = min(LO[1] + y, nmax[1]), gz = min(LO[2] + z, nmax[2]);
+                    win[z * Cfg::Plane + y * Cfg::Pitch + x] =
+                        __ldg(g.field + ((size_t)gz * g.ny + gy) * (size_t)g.nx + gx);
+                }
             }
             __syncwarp();
-            const float* wbase = win - (LO[2] * Cfg::WY + LO[1]) * Cfg::Pitch - LO[0];
+            const float* wbase = win - LO[2] * Cfg::Plane - LO[1] * Cfg::Pitch - LO[0];
             float t = lattice_t(ka, g.step);  // t_{k+1} = t_k + step exactly (multiples of step/2 below 2^24)
             for (int k = ka; k <= kz; ++k, t += g.step) {
                 const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
@@ -212,7 +241,7 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
                     const int b = ((iz >> g.brick_log2) * g.nby + (iy >> g.brick_log2)) * g.nbx + (ix >> g.brick_log2);
                     if (!__ldg(sel + b)) continue;
                 }
-                const float* c = wbase + (iz * Cfg::WY + iy) * Cfg::Pitch + ix;
+                const float* c = wbase + iz * Cfg::Plane + iy * Cfg::Pitch + ix;
                 const float val = trilinear8(c[0], c[1], c[Cfg::Pitch], c[Cfg::Pitch + 1], c[Cfg::Plane],
                                              c[Cfg::Plane + 1], c[Cfg::Plane + Cfg::Pitch],
                                              c[Cfg::Plane + Cfg::Pitch + 1], p0 - (float)ix, p1 - (float)iy,
@@ -353,11 +382,11 @@ __global__ void __launch_bounds__(256) k_pass1_fused(const __grid_constant__ Gri
     }
 }
 
-template <bool kSel, int kMode, class Cfg>
+template <bool kSel, class Cfg>
 __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
                                                      const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                      const char* __restrict__ moments, float* __restrict__ color,
-                                                     Counters* __restrict__ ctr) {
+                                                     int mode, Counters* __restrict__ ctr) {
     __shared__ float4 s_tf[512];
     __shared__ float s_win[kFusedWarps][Cfg::Floats];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
@@ -384,7 +413,7 @@ __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ Gri
         march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
         if (valid) {
             float4* out = reinterpret_cast<float4*>(color + S.color_off) + pix;
-            if (kMode == kColorResolved)
+            if (mode == kColorResolved)
                 *out = resolve_pixel(body.C, m[0], make_float4(0.0f, 0.0f, 0.0f, 0.0f), raw);
             else
                 *out = body.C;
@@ -589,78 +618,100 @@ __global__ void k_color_resolve(const float4* __restrict__ in, float4* __restric
     }
 }
 
-template <typename K>
-int persistent_blocks(K kernel, int threads) {
-    static int cached_dev = -1, cached = 0;
+// Resident CTAs per SM x SMs for a persistent kernel, cached per function.
+int persistent_blocks(const void* fn, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> cache;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev != cached_dev) {
-        int sms = 0, occ = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0);
-        cached = sms * (occ > 0 ? occ : 1);
-        cached_dev = dev;
-    }
-    return cached;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({dev, fn});
+    if (it != cache.end()) return it->second;
+    int sms = 0, occ = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
+    const int nb = sms * (occ > 0 ? occ : 1);
+    cache[{dev, fn}] = nb;
+    return nb;
 }
+
+const void* pass1_fn(int cfg, bool sel) {
+    if (sel) return (const void*)k_pass1_fused<true, Stage0>;
+    switch (cfg) {
+        case 1: return (const void*)k_pass1_fused<false, Stage1>;
+        case 2: return (const void*)k_pass1_fused<false, Stage2>;
+        case 3: return (const void*)k_pass1_fused<false, Stage3>;
+        case 4: return (const void*)k_pass1_fused<false, Stage4>;
+        default: return (const void*)k_pass1_fused<false, Stage0>;
+    }
+}
+
+const void* pass2_fn(int cfg, bool sel) {
+    if (sel) return (const void*)k_pass2_fused<true, Stage0>;
+    switch (cfg) {
+        case 1: return (const void*)k_pass2_fused<false, Stage1>;
+        case 2: return (const void*)k_pass2_fused<false, Stage2>;
+        case 3: return (const void*)k_pass2_fused<false, Stage3>;
+        case 4: return (const void*)k_pass2_fused<false, Stage4>;
+        default: return (const void*)k_pass2_fused<false, Stage0>;
+    }
+}
+
+bool vec_config(int cfg) { return cfg == 2 || cfg == 3 || cfg == 4; }
 
 }  // namespace
 
+bool stage_config_eligible(const GridD& g, int cfg) {
+    if (cfg < 0 || cfg >= kNumStageConfigs) return false;
+    if (!vec_config(cfg)) return true;
+    return g.nx % 4 == 0 && g.nx >= 4 && (reinterpret_cast<uintptr_t>(g.field) & 15u) == 0;
+}
+
 cudaError_t prepare_kernels() {
-    // Loads every kernel and fills the occupancy caches, so that no module
+    // Loads every kernel and fills the occupancy cache, so that no module
     // loading happens later inside a stream capture.
-    const void* fns[] = {(const void*)k_pass1_fused<true, DefaultStage>, (const void*)k_pass1_fused<false, DefaultStage>,
-                         (const void*)k_pass2_fused<true, kColorReduced, DefaultStage>, (const void*)k_pass2_fused<true, kColorResolved, DefaultStage>,
-                         (const void*)k_pass2_fused<false, kColorReduced, DefaultStage>, (const void*)k_pass2_fused<false, kColorResolved, DefaultStage>,
-                         (const void*)k_pass1_piece, (const void*)k_pass2_piece, (const void*)k_moments_sum,
+    const void* fns[] = {(const void*)k_pass1_piece, (const void*)k_pass2_piece, (const void*)k_moments_sum,
                          (const void*)k_color_resolve};
     for (const void* f : fns) {
         cudaFuncAttributes a;
         const cudaError_t e = cudaFuncGetAttributes(&a, f);
         if (e != cudaSuccess) return e;
     }
-    persistent_blocks(k_pass1_fused<true, DefaultStage>, 256);
-    persistent_blocks(k_pass1_fused<false, DefaultStage>, 256);
-    persistent_blocks(k_pass2_fused<true, kColorReduced, DefaultStage>, 256);
-    persistent_blocks(k_pass2_fused<true, kColorResolved, DefaultStage>, 256);
-    persistent_blocks(k_pass2_fused<false, kColorReduced, DefaultStage>, 256);
-    persistent_blocks(k_pass2_fused<false, kColorResolved, DefaultStage>, 256);
+    for (int cfg = 0; cfg < kNumStageConfigs; ++cfg)
+        for (int sel = 0; sel < 2; ++sel) {
+            cudaFuncAttributes a;
+            cudaError_t e = cudaFuncGetAttributes(&a, pass1_fn(cfg, sel));
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, pass2_fn(cfg, sel));
+            if (e != cudaSuccess) return e;
+            persistent_blocks(pass1_fn(cfg, sel), 256, 0);
+            persistent_blocks(pass2_fn(cfg, sel), 256, 0);
+        }
     return cudaGetLastError();
 }
 
 cudaError_t launch_pass1_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
-                               void* moments, Counters* ctr, cudaStream_t s) {
+                               void* moments, Counters* ctr, cudaStream_t s, int cfg) {
+    if (!stage_config_eligible(g, cfg)) cfg = 0;
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    if (brick_sel) {
-        const int nb = persistent_blocks(k_pass1_fused<true, DefaultStage>, 256);
-        k_pass1_fused<true, DefaultStage><<<nb, 256, 0, s>>>(g, tf, brick_sel, vt, static_cast<char*>(moments), ctr);
-    } else {
-        const int nb = persistent_blocks(k_pass1_fused<false, DefaultStage>, 256);
-        k_pass1_fused<false, DefaultStage><<<nb, 256, 0, s>>>(g, tf, brick_sel, vt, static_cast<char*>(moments), ctr);
-    }
-    return cudaGetLastError();
+    const void* fn = pass1_fn(cfg, brick_sel != nullptr);
+    char* m = static_cast<char*>(moments);
+    void* args[] = {(void*)&g, (void*)&tf, (void*)&brick_sel, (void*)&vt, (void*)&m, (void*)&ctr};
+    return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
 }
 
 cudaError_t launch_pass2_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
-                               const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s) {
+                               const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
+                               int cfg) {
+    if (!stage_config_eligible(g, cfg)) cfg = 0;
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[1], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
+    const void* fn = pass2_fn(cfg, brick_sel != nullptr);
     const char* m = static_cast<const char*>(moments);
-#define MB_LAUNCH2(SEL, MODE)                                                         \
-    do {                                                                              \
-        const int nb = persistent_blocks(k_pass2_fused<SEL, MODE, DefaultStage>, 256);              \
-        k_pass2_fused<SEL, MODE, DefaultStage><<<nb, 256, 0, s>>>(g, tf, brick_sel, vt, m, color, ctr); \
-    } while (0)
-    if (brick_sel) {
-        if (mode == kColorResolved) MB_LAUNCH2(true, kColorResolved);
-        else MB_LAUNCH2(true, kColorReduced);
-    } else {
-        if (mode == kColorResolved) MB_LAUNCH2(false, kColorResolved);
-        else MB_LAUNCH2(false, kColorReduced);
-    }
-#undef MB_LAUNCH2
-    return cudaGetLastError();
+    int md = mode;
+    void* args[] = {(void*)&g, (void*)&tf, (void*)&brick_sel, (void*)&vt, (void*)&m, (void*)&color, (void*)&md,
+                    (void*)&ctr};
+    return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
 }
 
 cudaError_t launch_pass1_piece(const GridD& g, const float4* tf, const int32_t* pob, int32_t piece,
