@@ -111,7 +111,9 @@ typedef struct {
      * the table, values outside are clamped. */
     const float* tf_rgba;
     float tf_range[2];
-    float step;                 /* sample spacing in voxels, a power of two (Sec. 5.3: fixed step) */
+    float step;                 /* sample spacing in voxels, a power of two (Sec. 5.3: fixed step);
+                                 * lattice point k sits at t = (k + 1/2) step from the eye, and only
+                                 * k < 2^22 is sampled (t exact in float32) */
     float moment_bias;          /* mix amount of the bias vector (Alg. 3 "mix"), in [0, 1) */
     float overestimation;       /* weight of the sample's own depth (Alg. 3), paper: 0.3 */
     float absorbance_max;       /* ABSORBANCE_MAX_VALUE of Alg. 2, > 0 */

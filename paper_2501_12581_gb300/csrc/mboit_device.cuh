@@ -75,7 +75,9 @@ MB_HD float ffma(float a, float b, float c) {
 // fast transcendental approximations (accuracy ~2 ulp, ample for 2e-4 images)
 MB_HD float flog2(float x) {
 #if defined(__CUDA_ARCH__)
-    return __log2f(x);
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));  // one MUFU op; lattice depths are never denormal
+    return y;
 #else
     return log2f(x);
 #endif
@@ -183,14 +185,16 @@ MB_HD bool lattice_range(const float o[3], const float d[3], const float lo[3], 
     float klo = ceilf(t0 * inv_step - 0.5f) - 2.0f;
     float khi = floorf(t1 * inv_step - 0.5f) + 2.0f;
     if (klo < 0.0f) klo = 0.0f;
-    if (khi > 16777000.0f) khi = 16777000.0f;  // t_k stays exact in float32 below 2^24
+    // t_k = (k + 1/2) step is exact in float32, and t_{k+1} = t_k + step
+    // exactly, for k < 2^22: farther lattice points are not sampled
+    if (khi > 4194303.0f) khi = 4194303.0f;
     if (khi < klo) return false;
     *k0 = (int)klo;
     *k1 = (int)khi;
     return true;
 }
 
-// Lattice parameter of point k: exact in float32 for k < 2^23 and a power-of-two step.
+// Lattice parameter of point k: exact in float32 for k < 2^22 and a power-of-two step.
 MB_HD float lattice_t(int k, float step) { return fmul(fadd((float)k, 0.5f), step); }
 
 MB_HD float warp_depth(float t, float wa, float wb) { return fclamp(ffma(flog2(t), wa, wb), -1.0f, 1.0f); }

@@ -146,8 +146,8 @@ struct StageCfg {
 using Stage0 = StageCfg<6, 8, 8, 8, false>;
 using Stage1 = StageCfg<8, 8, 8, 8, false>;
 using Stage2 = StageCfg<6, 12, 8, 8, true>;
-using Stage3 = StageCfg<8, 12, 10, 10, true>;
-using Stage4 = StageCfg<10, 12, 12, 12, true>;
+using Stage3 = StageCfg<6, 16, 8, 8, true>;
+using Stage4 = StageCfg<8, 16, 8, 10, true>;
 constexpr int kFusedWarps = 8;  // 256 threads per CTA
 
 __device__ __forceinline__ float trilinear8(float v000, float v100, float v010, float v110, float v001, float v101,
@@ -214,13 +214,28 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
                 // nx % 4 == 0 and a 16-byte aligned field (checked by the launcher):
                 // every chunk start gx is a multiple of 4 and gx + 3 < nx
                 constexpr int QX = Cfg::WX / 4;
+                if (QX * Cfg::WY == 32) {
+                    // one plane per warp-wide step: lane -> fixed (xq, y), z = step
+                    const int xq = lane % QX, y = lane / QX;
+                    const int gx = min(LO[0] + 4 * xq, g.nx - 4), gy = min(LO[1] + y, nmax[1]);
+                    const float* src = g.field + (size_t)gy * g.nx + gx;
+                    float* dst = win + y * Cfg::Pitch + 4 * xq;
+                    const size_t zs = (size_t)g.nx * g.ny;
+#pragma unroll
+                    for (int z = 0; z < Cfg::WZ; ++z) {
+                        const int gz = min(LO[2] + z, nmax[2]);
+                        *reinterpret_cast<float4*>(dst + z * Cfg::Plane) =
+                            __ldg(reinterpret_cast<const float4*>(src + gz * zs));
+                    }
+                } else {
 #pragma unroll 2
-                for (int e = lane; e < QX * Cfg::WY * Cfg::WZ; e += 32) {
-                    const int xq = e % QX, y = (e / QX) % Cfg::WY, z = e / (QX * Cfg::WY);
-                    const int gx = min(LO[0] + 4 * xq, g.nx - 4), gy = min(LO[1] + y, nmax[1]),
-                              gz = min(LO[2] + z, nmax[2]);
-                    *reinterpret_cast<float4*>(win + z * Cfg::Plane + y * Cfg::Pitch + 4 * xq) =
-                        __ldg(reinterpret_cast<const float4*>(g.field + ((size_t)gz * g.ny + gy) * (size_t)g.nx + gx));
+                    for (int e = lane; e < QX * Cfg::WY * Cfg::WZ; e += 32) {
+                        const int xq = e % QX, y = (e / QX) % Cfg::WY, z = e / (QX * Cfg::WY);
+                        const int gx = min(LO[0] + 4 * xq, g.nx - 4), gy = min(LO[1] + y, nmax[1]),
+                                  gz = min(LO[2] + z, nmax[2]);
+                        *reinterpret_cast<float4*>(win + z * Cfg::Plane + y * Cfg::Pitch + 4 * xq) = __ldg(
+                            reinterpret_cast<const float4*>(g.field + ((size_t)gz * g.ny + gy) * (size_t)g.nx + gx));
+                    }
                 }
             } else {
 #pragma unroll 4
@@ -233,8 +248,10 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
             }
             __syncwarp();
             const float* wbase = win - LO[2] * Cfg::Plane - LO[1] * Cfg::Pitch - LO[0];
-            float t = lattice_t(ka, g.step);  // t_{k+1} = t_k + step exactly (multiples of step/2 below 2^24)
-            for (int k = ka; k <= kz; ++k, t += g.step) {
+            // t_{k+1} = t_k + step exactly (odd multiples of step/2 below 2^24), so the
+            // loop runs on t itself
+            const float tz = lattice_t(kz, g.step);
+            for (float t = lattice_t(ka, g.step); t <= tz; t += g.step) {
                 const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
                 const int ix = (int)p0, iy = (int)p1, iz = (int)p2;
                 if (kSel) {
@@ -249,8 +266,8 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
                 body(t, val);
             }
         } else {
-            float t = lattice_t(ka, g.step);
-            for (int k = ka; k <= kz; ++k, t += g.step) {
+            const float tz = lattice_t(kz, g.step);
+            for (float t = lattice_t(ka, g.step); t <= tz; t += g.step) {
                 float val;
                 if (!field_sample<kSel>(g, sel, t, o, d, val)) continue;
                 body(t, val);
@@ -267,21 +284,20 @@ struct MomentBody {
     float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f;
     unsigned n = 0;
     __device__ __forceinline__ void operator()(float t, float val) {
+        // entry 255 has a zero delta, so xt = 255 needs no special index
         const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
-        const int i = min((int)xt, 254);
+        const int i = (int)xt;
         const float f = xt - (float)i;
         const float2 s = s_sig[i];
         const float a = fmin_(ffma(f, s.y, s.x), amax);
         const float z = warp_depth(t, wa, wb);
         m0 += a;
-        float az = a * z;
-        m1 += az;
-        az *= z;
-        m2 += az;
-        az *= z;
-        m3 += az;
-        az *= z;
-        m4 += az;
+        m1 = ffma(a, z, m1);
+        const float az = a * z;
+        m2 = ffma(az, z, m2);
+        const float az2 = az * z;
+        m3 = ffma(az2, z, m3);
+        m4 = ffma(az2 * z, z, m4);
         ++n;
     }
 };
@@ -295,7 +311,7 @@ struct BlendBody {
     unsigned n = 0;
     __device__ __forceinline__ void operator()(float t, float val) {
         const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
-        const int i = min((int)xt, 254);
+        const int i = (int)xt;
         const float f = xt - (float)i;
         const float4 e0 = s_tf[2 * i], de = s_tf[2 * i + 1];
         const float a = fmin_(ffma(f, de.w, e0.w), amax);
@@ -444,7 +460,7 @@ __device__ __forceinline__ int skip_brick(const GridD& g, const float o[3], cons
     }
     const float kn = ceilf(t_exit / g.step - 0.5f) - 1.0f;
     if (!(kn > (float)(k + 1))) return k + 1;
-    return kn > 16777000.0f ? 16777000 : (int)kn;
+    return kn > 4194303.0f ? 4194304 : (int)kn;
 }
 
 // One owned sample of `piece` at lattice index k, or the next index to try.
