@@ -186,6 +186,7 @@ def main():
     ap.add_argument("--workload", default="blobs512", choices=["blobs512", "blobs64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-piece", action="store_true")
+    ap.add_argument("--no-sortlast", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -289,6 +290,23 @@ def main():
         torch.cuda.empty_cache()
         frame()
 
+    # the on-GPU exact sort-last baseline (segment layers) and the MBOIT error against it
+    sortlast = None
+    if not args.no_sortlast:
+        exact = pkg.Volume.color_buffer(views)
+        vol.render_sortlast(views, exact)
+        ms_sl = timed(lambda: vol.render_sortlast(views, exact), max(3, args.steps // 6))
+        frame()
+        vol.synchronize()
+        d = (rgba - exact).view(-1, 4).double()
+        st_sl = vol.stats()
+        sortlast = {"ms_per_frame": ms_sl, "gsamples_per_s": samples / (ms_sl * 1e-3) / 1e9,
+                    "segments": st_sl["sortlast_segments"], "max_segments_per_pixel": st_sl["sortlast_max_segments"],
+                    "speedup_of_batched_mboit": ms_sl / ms,
+                    "mboit_vs_exact_rmse": float(d.pow(2).mean().sqrt()), "mboit_vs_exact_max": float(d.abs().max())}
+        del exact
+        torch.cuda.empty_cache()
+
     # end to end through the host API: field upload, frame, image download
     field_host = torch.from_numpy(np.ascontiguousarray(sc.field)).pin_memory()
     rgba_host = torch.empty(rgba.numel(), dtype=torch.float32).pin_memory()
@@ -328,6 +346,7 @@ def main():
                           form="batched: 2 persistent kernels per frame, CUDA graph",
                           tuning={"pass1": tuning[0], "pass2": tuning[1]}),
            "samples_per_frame": samples, "ms_per_frame": ms_max, "per_piece_fp32": per_piece,
+           "sortlast_gpu": sortlast,
            "quality": quality, "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
            "gpu_launches": 2 * args.steps, "clocks": clk.summary()}
     vol.close()

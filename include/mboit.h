@@ -140,6 +140,9 @@ typedef struct {
     int32_t device;
     int32_t tuning_pass1;       /* window configuration of the fused passes (see mboit_set_tuning) */
     int32_t tuning_pass2;
+    int64_t sortlast_segments;  /* segments of the last mboit_render_sortlast */
+    int32_t sortlast_max_segments; /* most segments on one pixel in it */
+    int32_t reserved;
 } mboit_stats;
 
 /* Number of window configurations of the fused passes.  Each fused kernel
@@ -227,6 +230,20 @@ MBOIT_API mboit_status mboit_synchronize(mboit_volume v, void* stream);
 
 /* Counters of the last passes (synchronises the stream of the last render). */
 MBOIT_API mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out);
+
+/* GPU exact sort-last baseline (the segment-layer compositor the paper
+ * compares against, Sec. 5; no moments, exact front-to-back result).  Every
+ * piece turns each maximal run of consecutive lattice points it owns into
+ * one segment (premultiplied colour and opacity of the run, keyed by its
+ * first lattice index); per pixel the segments of all pieces are sorted by
+ * key and composited with "over".  rgba: DEVICE float32 RGBA, n_views
+ * images (premultiplied colour, alpha = 1 - transmittance, no background).
+ * segments_per_pixel: DEVICE int32 [pixels of all views] or NULL (the
+ * segment-density image).  Uses library-owned buffers that grow to the
+ * largest frame seen; synchronises `stream` once (to size the segment
+ * buffer), so it cannot be captured into a graph. */
+MBOIT_API mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int32_t n_views, float* rgba,
+                                             int32_t* segments_per_pixel, void* stream);
 
 /* Selects the window configuration (0 .. MBOIT_NUM_TUNINGS-1) of the fused
  * pass 1 and pass 2.  Configurations 2-4 read 16-byte chunks and need

@@ -69,6 +69,9 @@ def _load():
             lib.orc_render_grid.restype = ctypes.c_int
             lib.orc_render_grid.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64] + \
                 [ctypes.c_void_p] * 8
+            lib.orc_render_grid_segments.restype = ctypes.c_int
+            lib.orc_render_grid_segments.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
             _lib = lib
     return _lib
 
@@ -107,6 +110,44 @@ def _view_struct(v):
     s.scale_u, s.scale_v = float(v.scale_u), float(v.scale_v)
     s.znear, s.zfar = float(v.near), float(v.far)
     return s
+
+
+def _grid_struct(scene, pieces):
+    K = scene.n_pieces
+    keep = dict(field=np.ascontiguousarray(scene.field, dtype=np.float32),
+                pob=np.ascontiguousarray(scene.piece_of_brick, dtype=np.int32),
+                tf=np.ascontiguousarray(scene.tf, dtype=np.float32), sel=None)
+    if pieces is not None:
+        keep["sel"] = np.zeros(K, dtype=np.uint8)
+        keep["sel"][np.asarray(list(pieces), dtype=np.int64)] = 1
+    g = _Grid()
+    nx, ny, nz = scene.dims
+    g.field, g.nx, g.ny, g.nz, g.brick_log2 = keep["field"].ctypes.data, nx, ny, nz, scene.brick_log2
+    g.piece_of_brick, g.n_pieces = keep["pob"].ctypes.data, K
+    g.piece_selected = _ptr(keep["sel"])
+    g.tf = keep["tf"].ctypes.data
+    g.vmin, g.vmax = float(scene.tf_range[0]), float(scene.tf_range[1])
+    g.step = float(scene.step)
+    g.moment_bias, g.overestimation = float(scene.moment_bias), float(scene.overestimation)
+    g.absorbance_max = float(scene.absorbance_max)
+    g.bias_vector[:] = list(getattr(scene, "bias_vector", BIAS_VECTOR_POWER4))
+    return g, keep
+
+
+def render_segments(scene, view=0, pixels=None, pieces=None):
+    """Sort-last route only: (rgba [n][4] float64, segments per pixel [n] int64)."""
+    lib = _load()
+    v = scene.views[view] if isinstance(view, int) else view
+    pix = np.arange(v.width * v.height, dtype=np.int64) if pixels is None else \
+        np.ascontiguousarray(pixels, dtype=np.int64)
+    g, keep = _grid_struct(scene, pieces)
+    rgba = np.zeros((pix.size, 4))
+    nseg = np.zeros(pix.size, dtype=np.int64)
+    vs = _view_struct(v)
+    if lib.orc_render_grid_segments(ctypes.byref(g), ctypes.byref(vs), pix.ctypes.data, pix.size,
+                                    rgba.ctypes.data, nseg.ctypes.data) != 0:
+        raise ValueError("oracle rejected its arguments")
+    return rgba, nseg
 
 
 def render_grid(scene, view=0, pixels=None, pieces=None, want=("mboit",)):

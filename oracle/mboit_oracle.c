@@ -291,11 +291,42 @@ static int take_sample(const orc_grid* g, const orc_view* V, const float o[3], c
 /* ------------------------------------------------------------------------ */
 /* one pixel                                                                 */
 
+static int render_grid_impl(const orc_grid* g, const orc_view* V,
+                            const int64_t* pixels, int64_t n_pixels,
+                            double* moments, double* piece_moments, double* piece_color,
+                            double* mboit_rgba, double* raw_rgba, double* exact_rgba,
+                            double* sortlast_rgba, int64_t* nsamples, int64_t* nsegments);
+
 int orc_render_grid(const orc_grid* g, const orc_view* V,
                     const int64_t* pixels, int64_t n_pixels,
                     double* moments, double* piece_moments, double* piece_color,
                     double* mboit_rgba, double* raw_rgba, double* exact_rgba,
                     double* sortlast_rgba, int64_t* nsamples)
+{
+    return render_grid_impl(g, V, pixels, n_pixels, moments, piece_moments, piece_color, mboit_rgba, raw_rgba,
+                            exact_rgba, sortlast_rgba, nsamples, NULL);
+}
+
+int orc_render_grid_segments(const orc_grid* g, const orc_view* V,
+                             const int64_t* pixels, int64_t n_pixels,
+                             double* sortlast_rgba, int64_t* nsegments)
+{
+    double* tmp = NULL;
+    if (!sortlast_rgba) {
+        tmp = (double*)malloc((size_t)(n_pixels > 0 ? n_pixels : 1) * 4 * sizeof(double));
+        if (!tmp) return -1;
+    }
+    int rc = render_grid_impl(g, V, pixels, n_pixels, NULL, NULL, NULL, NULL, NULL, NULL,
+                              sortlast_rgba ? sortlast_rgba : tmp, NULL, nsegments);
+    free(tmp);
+    return rc;
+}
+
+static int render_grid_impl(const orc_grid* g, const orc_view* V,
+                            const int64_t* pixels, int64_t n_pixels,
+                            double* moments, double* piece_moments, double* piece_color,
+                            double* mboit_rgba, double* raw_rgba, double* exact_rgba,
+                            double* sortlast_rgba, int64_t* nsamples, int64_t* nsegments)
 {
     if (!g || !V || !g->field || !g->piece_of_brick || !g->tf || g->n_pieces <= 0) return -1;
     if (g->nx < 2 || g->ny < 2 || g->nz < 2 || !(g->step > 0.0) || !(g->vmax > g->vmin)) return -1;
@@ -427,6 +458,7 @@ int orc_render_grid(const orc_grid* g, const orc_view* V,
             double* out = sortlast_rgba + 4 * n;
             for (int c = 0; c < 3; ++c) out[c] = acc[c];
             out[3] = 1.0 - tr;
+            if (nsegments) nsegments[n] = (int64_t)nseg;
             free(seg);
         }
         if (nsamples) nsamples[n] = (int64_t)ns;

@@ -60,6 +60,12 @@ int orc_render_grid(const orc_grid* g, const orc_view* view,
                     double* mboit_rgba, double* raw_rgba, double* exact_rgba,
                     double* sortlast_rgba, int64_t* nsamples);
 
+/* As orc_render_grid, plus nsegments[n_pixels]: segments of the sort-last
+ * route (maximal runs of consecutive lattice points of one piece). */
+int orc_render_grid_segments(const orc_grid* g, const orc_view* view,
+                             const int64_t* pixels, int64_t n_pixels,
+                             double* sortlast_rgba, int64_t* nsegments);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ MBOIT_FLAG_RAW_SUM, MBOIT_FLAG_DETERMINISTIC = 0x1, 0x2
 EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume", "mboit_destroy_volume",
             "mboit_add_piece", "mboit_render_moments", "mboit_reconstruct_blend", "mboit_composite",
             "mboit_render_frame", "mboit_render_frame_host", "mboit_synchronize", "mboit_get_stats",
-            "mboit_render_moments_noalloc", "mboit_set_tuning", "mboit_autotune"]
+            "mboit_render_moments_noalloc", "mboit_set_tuning", "mboit_autotune", "mboit_render_sortlast"]
 MBOIT_NUM_TUNINGS = 5
 
 
@@ -61,7 +61,9 @@ class mboit_volume_desc(ctypes.Structure):
 class mboit_stats(ctypes.Structure):
     _fields_ = [("samples_pass1", ctypes.c_int64), ("samples_pass2", ctypes.c_int64),
                 ("singular_pixels", ctypes.c_int64), ("n_pieces", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("tuning_pass1", ctypes.c_int32), ("tuning_pass2", ctypes.c_int32)]
+                ("tuning_pass1", ctypes.c_int32), ("tuning_pass2", ctypes.c_int32),
+                ("sortlast_segments", ctypes.c_int64), ("sortlast_max_segments", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -92,6 +94,7 @@ def load_library(path=LIB_PATH):
         "mboit_render_moments_noalloc": (ctypes.c_int, [P, P, P, I32, P, P]),
         "mboit_set_tuning": (ctypes.c_int, [P, I32, I32]),
         "mboit_autotune": (ctypes.c_int, [P, P, I32, P, P, P, P]),
+        "mboit_render_sortlast": (ctypes.c_int, [P, P, I32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -240,6 +243,11 @@ def mboit_autotune(v, views, moments_scratch, rgba, stream=None):
     return int(out[0]), int(out[1])
 
 
+def mboit_render_sortlast(v, views, rgba, segments_per_pixel=None, stream=None):
+    arr, n = _views(views)
+    _check(load_library().mboit_render_sortlast(v, arr, n, _ptr(rgba), _ptr(segments_per_pixel), _stream(stream)))
+
+
 def grid_desc(scene, field, flags=0):
     """mboit_volume_desc for a regular-grid scene whose field is the CUDA
     tensor `field`; returns (desc, keepalive) - keep both while in use."""
@@ -348,6 +356,9 @@ class Volume:
 
     def synchronize(self, stream=None):
         mboit_synchronize(self.handle, stream)
+
+    def render_sortlast(self, views, rgba, segments_per_pixel=None, stream=None):
+        mboit_render_sortlast(self.handle, views, rgba, segments_per_pixel, stream)
 
     def set_tuning(self, pass1, pass2):
         mboit_set_tuning(self.handle, pass1, pass2)

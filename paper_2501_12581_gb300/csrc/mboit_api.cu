@@ -71,10 +71,31 @@ struct mboit_volume_s {
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphEntry> graphs;
     int32_t tune1 = 0, tune2 = 0;
+    // sort-last baseline buffers (grow only)
+    int32_t* sl_counts = nullptr;
+    int64_t* sl_starts = nullptr;
+    int32_t* sl_totals = nullptr;
+    int64_t* sl_base = nullptr;
+    int64_t* sl_bsum = nullptr;
+    int32_t* sl_key = nullptr;
+    float4* sl_col = nullptr;
+    size_t cap_counts = 0, cap_starts = 0, cap_totals = 0, cap_base = 0, cap_bsum = 0, cap_seg = 0, cap_col = 0;
+    int64_t sl_segments = 0;
     std::mutex mu;
 };
 
 namespace {
+
+template <class T>
+cudaError_t ensure_capacity(T*& p, size_t& cap, size_t n) {
+    if (n <= cap) return cudaSuccess;
+    cudaFree(p);  // waits for work that may still read the old buffer
+    p = nullptr;
+    cap = 0;
+    const cudaError_t e = cudaMalloc(&p, (n > 0 ? n : 1) * sizeof(T));
+    if (e == cudaSuccess) cap = n;
+    return e;
+}
 
 void drop_graphs(mboit_volume v) {
     for (auto& g : v->graphs)
@@ -315,6 +336,13 @@ mboit_status mboit_destroy_volume(mboit_volume v) {
         cudaFree(v->d_pob);
         cudaFree(v->d_sel);
         cudaFree(v->d_ctr);
+        cudaFree(v->sl_counts);
+        cudaFree(v->sl_starts);
+        cudaFree(v->sl_totals);
+        cudaFree(v->sl_base);
+        cudaFree(v->sl_bsum);
+        cudaFree(v->sl_key);
+        cudaFree(v->sl_col);
     }
     delete v;
     return MBOIT_OK;
@@ -560,6 +588,52 @@ mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out) {
     out->device = v->device;
     out->tuning_pass1 = v->tune1;
     out->tuning_pass2 = v->tune2;
+    out->sortlast_segments = v->sl_segments;
+    out->sortlast_max_segments = c.max_segments;
+    out->reserved = 0;
+    return MBOIT_OK;
+}
+
+mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int32_t n_views, float* rgba,
+                                   int32_t* segments_per_pixel, void* stream) {
+    g_err.clear();
+    mboit_status st = check_volume(v);
+    if (st != MBOIT_OK) return st;
+    if (!rgba) return fail(MBOIT_ERR_INVALID_ARG, "rgba is NULL");
+    std::lock_guard<std::mutex> lk(v->mu);
+    DeviceGuard dg(v->device);
+    mb::ViewTable vt;
+    if ((st = build_views(views, n_views, vt)) != MBOIT_OK) return st;
+    int64_t total_px = 0;
+    for (int i = 0; i < n_views; ++i) total_px += (int64_t)views[i].width * views[i].height;
+    const int32_t K = (int32_t)v->boxes.size();
+    const size_t slots_px = (size_t)K * (size_t)total_px;
+    const size_t nb = (size_t)((total_px + 1023) / 1024);
+    MB_CUDA(ensure_capacity(v->sl_counts, v->cap_counts, slots_px));
+    MB_CUDA(ensure_capacity(v->sl_starts, v->cap_starts, slots_px));
+    MB_CUDA(ensure_capacity(v->sl_totals, v->cap_totals, (size_t)total_px));
+    MB_CUDA(ensure_capacity(v->sl_base, v->cap_base, (size_t)total_px + 1));
+    MB_CUDA(ensure_capacity(v->sl_bsum, v->cap_bsum, nb));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MB_CUDA(cudaMemsetAsync(&v->d_ctr->segments, 0, sizeof(unsigned long long) + sizeof(int32_t), s));
+    for (int32_t p = 0; p < K; ++p)
+        MB_CUDA(mb::launch_sortlast_march(false, v->grid, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts,
+                                          nullptr, nullptr, nullptr, s));
+    MB_CUDA(mb::launch_sortlast_offsets(vt, K, v->sl_counts, v->sl_totals, v->sl_base, v->sl_bsum, v->sl_starts,
+                                        total_px, s));
+    int64_t total = 0;
+    MB_CUDA(cudaMemcpyAsync(&total, v->sl_base + total_px, sizeof total, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    MB_CUDA(ensure_capacity(v->sl_key, v->cap_seg, (size_t)total));
+    MB_CUDA(ensure_capacity(v->sl_col, v->cap_col, (size_t)total));
+    for (int32_t p = 0; p < K; ++p)
+        MB_CUDA(mb::launch_sortlast_march(true, v->grid, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts,
+                                          v->sl_starts, v->sl_key, v->sl_col, s));
+    MB_CUDA(mb::launch_sortlast_blend(v->sl_base, v->sl_key, v->sl_col, rgba, total_px, v->d_ctr, s));
+    if (segments_per_pixel)
+        MB_CUDA(cudaMemcpyAsync(segments_per_pixel, v->sl_totals, (size_t)total_px * sizeof(int32_t),
+                                cudaMemcpyDeviceToDevice, s));
+    v->sl_segments = total;
     return MBOIT_OK;
 }
 

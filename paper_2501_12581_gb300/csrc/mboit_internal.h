@@ -35,6 +35,9 @@ struct Counters {
     int32_t pad;
     unsigned long long samples[2];   // pass 1, pass 2
     unsigned long long singular;     // pixels on a 1-/2-atom branch
+    unsigned long long segments;     // sort-last segments of the last baseline frame
+    int32_t max_segments;            // most segments on one pixel
+    int32_t pad2;
 };
 
 struct PieceBox {
@@ -66,6 +69,18 @@ cudaError_t launch_pass1_piece(const GridD& g, const float4* tf, const int32_t* 
 cudaError_t launch_pass2_piece(const GridD& g, const float4* tf, const int32_t* piece_of_brick, int32_t piece,
                                const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
                                const void* moments, float* color, Counters* ctr, cudaStream_t s);
+// GPU exact sort-last baseline: per-piece segment count / fill marches,
+// offsets (per-pixel totals, exclusive scan, per-(piece, pixel) starts),
+// per-pixel sort and blend.  counts/starts: [pixels of all views][n_slots]
+// laid out per view as [slot][pixel].
+cudaError_t launch_sortlast_march(bool fill, const GridD& g, const float4* tf, const int32_t* pob, int32_t piece,
+                                  const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
+                                  int32_t* counts, const int64_t* starts, int32_t* seg_key, float4* seg_col,
+                                  cudaStream_t s);
+cudaError_t launch_sortlast_offsets(const ViewTable& vt, int32_t n_slots, const int32_t* counts, int32_t* totals,
+                                   int64_t* base, int64_t* bsum, int64_t* starts, int64_t total_px, cudaStream_t s);
+cudaError_t launch_sortlast_blend(const int64_t* base, int32_t* seg_key, float4* seg_col, float* rgba, int64_t total_px,
+                                  Counters* ctr, cudaStream_t s);
 // Image-space reductions.
 cudaError_t launch_moments_sum(const ViewTable& vt, int32_t n_inputs, const void* in, void* out, cudaStream_t s);
 cudaError_t launch_color_resolve(const ViewTable& vt, int32_t n_inputs, const float* in, float* out,

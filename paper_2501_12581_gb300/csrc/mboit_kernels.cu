@@ -592,6 +592,255 @@ __global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ Gri
 }
 
 // ------------------------------------------------------------------------
+// GPU exact sort-last baseline (the segment-layer compositor of Sec. 5).
+// Every piece, like a rank, turns each maximal run of consecutive lattice
+// points it owns into one segment (front-to-back "over" inside the run:
+// premultiplied colour and opacity, keyed by the run's first lattice index);
+// per pixel the segments of all pieces are sorted by that key and blended
+// front to back.  Counting and filling are separate marches so the segment
+// buffer can be sized exactly.
+
+template <bool kFill>
+__global__ void __launch_bounds__(128) k_sortlast_piece(const __grid_constant__ GridD g, const float4* __restrict__ tf,
+                                                        const int32_t* __restrict__ pob, int piece,
+                                                        const __grid_constant__ PieceBox box,
+                                                        const __grid_constant__ ViewTable vt, int slot, int n_slots,
+                                                        int32_t* __restrict__ counts, const int64_t* __restrict__ starts,
+                                                        int32_t* __restrict__ seg_key, float4* __restrict__ seg_col) {
+    __shared__ float4 s_tf[256];
+    if (kFill) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = tf[i];
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tile >= vt.total_tiles) return;
+    const int vi = find_view(vt, tile);
+    const ViewSlot& S = vt.s[vi];
+    const int lt = tile - S.tile_base;
+    const int px = (lt % S.ntx) * kTileW + (lane & 7);
+    const int py = (lt / S.ntx) * kTileH + (lane >> 3);
+    if (px >= S.v.width || py >= S.v.height) return;
+    const int64_t npix = (int64_t)S.v.width * S.v.height;
+    const int64_t gpix = S.color_off / 4 + py * S.v.width + px;  // pixel index over all views
+    const int64_t cidx = (S.color_off / 4) * n_slots + slot * npix + (py * S.v.width + px);
+    float o[3], d[3];
+    make_ray(S.v, px, py, o, d);
+    int k0, k1;
+    int nseg = 0;
+    if (lattice_range(o, d, box.lo, box.hi, g.step, &k0, &k1)) {
+        int64_t out = kFill ? starts[cidx] : 0;
+        int prev = -2, key = 0;
+        float4 cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float tr = 1.0f;
+        for (int k = k0; k <= k1;) {
+            const float t = lattice_t(k, g.step);
+            float val;
+            int kn;
+            if (!piece_sample(g, pob, piece, t, o, d, k, val, kn)) {
+                k = kn;
+                continue;
+            }
+            if (k != prev + 1) {
+                if (kFill && nseg > 0) {
+                    seg_key[out] = key;
+                    seg_col[out] = make_float4(cur.x, cur.y, cur.z, 1.0f - tr);
+                    ++out;
+                }
+                ++nseg;
+                key = k;
+                cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                tr = 1.0f;
+            }
+            prev = k;
+            k = kn;
+            if (kFill) {
+                int i;
+                const float f = tf_coord(g, val, i);
+                const float4 e0 = s_tf[i], e1 = s_tf[i + 1];
+                const float a = fmin_(ffma(f, e1.w - e0.w, e0.w), g.absorbance_max);
+                const float w = tr * one_minus_exp_neg(a);
+                cur.x = ffma(w, ffma(f, e1.x - e0.x, e0.x), cur.x);
+                cur.y = ffma(w, ffma(f, e1.y - e0.y, e0.y), cur.y);
+                cur.z = ffma(w, ffma(f, e1.z - e0.z, e0.z), cur.z);
+                tr *= fexp2(-a * kLog2e);
+            }
+        }
+        if (kFill && nseg > 0) {
+            seg_key[out] = key;
+            seg_col[out] = make_float4(cur.x, cur.y, cur.z, 1.0f - tr);
+        }
+    }
+    if (!kFill) counts[cidx] = nseg;
+    (void)gpix;
+}
+
+// Per pixel: total segments over the pieces, and each (piece, pixel) run of
+// counts turned into start offsets in place (given the pixel's base offset).
+__global__ void k_sortlast_totals(const ViewTable vt, int n_slots, const int32_t* __restrict__ counts,
+                                  int32_t* __restrict__ totals, int64_t total_px) {
+    for (int64_t gp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gp < total_px;
+         gp += (int64_t)gridDim.x * blockDim.x) {
+        int vi = 0;
+        while (vi + 1 < vt.n && gp >= vt.s[vi + 1].color_off / 4) ++vi;
+        const ViewSlot& S = vt.s[vi];
+        const int64_t npix = (int64_t)S.v.width * S.v.height, local = gp - S.color_off / 4;
+        const int32_t* c = counts + (S.color_off / 4) * n_slots + local;
+        int32_t sum = 0;
+        for (int j = 0; j < n_slots; ++j) sum += c[j * npix];
+        totals[gp] = sum;
+    }
+}
+
+__global__ void k_sortlast_starts(const ViewTable vt, int n_slots, const int32_t* __restrict__ counts,
+                                  const int64_t* __restrict__ base, int64_t* __restrict__ starts, int64_t total_px) {
+    for (int64_t gp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gp < total_px;
+         gp += (int64_t)gridDim.x * blockDim.x) {
+        int vi = 0;
+        while (vi + 1 < vt.n && gp >= vt.s[vi + 1].color_off / 4) ++vi;
+        const ViewSlot& S = vt.s[vi];
+        const int64_t npix = (int64_t)S.v.width * S.v.height, local = gp - S.color_off / 4;
+        const int64_t off = (S.color_off / 4) * n_slots + local;
+        int64_t run = base[gp];
+        for (int j = 0; j < n_slots; ++j) {
+            starts[off + j * npix] = run;
+            run += counts[off + j * npix];
+        }
+    }
+}
+
+// Exclusive scan of int32 counts into int64 offsets, out[n] = total
+// (three phases: 1024-element blocks, block sums, block offsets).
+__global__ void __launch_bounds__(1024) k_scan_blocks(const int32_t* __restrict__ in, int64_t* __restrict__ out,
+                                                      int64_t* __restrict__ bsum, int64_t n) {
+    __shared__ int64_t wtot[32];
+    const int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t x = i < n ? in[i] : 0;
+    int64_t v = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += y;
+    }
+    if (lane == 31) wtot[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = wtot[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        wtot[lane] = w;
+    }
+    __syncthreads();
+    const int64_t incl = v + (warp > 0 ? wtot[warp - 1] : 0);
+    if (i < n) out[i] = incl - x;
+    if (threadIdx.x == 1023) bsum[blockIdx.x] = incl;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(int64_t* __restrict__ bsum, int64_t nb, int64_t* __restrict__ total) {
+    __shared__ int64_t wtot[32];
+    __shared__ int64_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t x = i < nb ? bsum[i] : 0;
+        int64_t v = x;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += y;
+        }
+        if (lane == 31) wtot[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = wtot[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, w, off);
+                if (lane >= off) w += y;
+            }
+            wtot[lane] = w;
+        }
+        __syncthreads();
+        const int64_t incl = v + (warp > 0 ? wtot[warp - 1] : 0) + carry;
+        if (i < nb) bsum[i] = incl - x;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(int64_t* __restrict__ out, const int64_t* __restrict__ bsum, int64_t n) {
+    const int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+    if (i < n) out[i] += bsum[blockIdx.x];
+}
+
+// Per pixel: sort its segments by first lattice index (insertion sort; up to
+// 64 in registers-backed local arrays, longer lists in place in global
+// memory) and composite them front to back.
+__global__ void k_sortlast_blend(const int64_t* __restrict__ base, int32_t* __restrict__ seg_key,
+                                 float4* __restrict__ seg_col, float* __restrict__ rgba, int64_t total_px,
+                                 Counters* __restrict__ ctr) {
+    constexpr int kLocal = 64;
+    for (int64_t gp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gp < total_px;
+         gp += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = base[gp], n = base[gp + 1] - b;
+        float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float tr = 1.0f;
+        if (n <= kLocal) {
+            int key[kLocal];
+            int idx[kLocal];
+            for (int j = 0; j < n; ++j) {
+                const int kj = seg_key[b + j];
+                int m = j;
+                while (m > 0 && key[m - 1] > kj) {
+                    key[m] = key[m - 1];
+                    idx[m] = idx[m - 1];
+                    --m;
+                }
+                key[m] = kj;
+                idx[m] = j;
+            }
+            for (int j = 0; j < n; ++j) {
+                const float4 c = seg_col[b + idx[j]];
+                acc.x = ffma(tr, c.x, acc.x);
+                acc.y = ffma(tr, c.y, acc.y);
+                acc.z = ffma(tr, c.z, acc.z);
+                tr *= 1.0f - c.w;
+            }
+        } else {
+            for (int64_t j = 1; j < n; ++j) {
+                const int kj = seg_key[b + j];
+                const float4 cj = seg_col[b + j];
+                int64_t m = j;
+                while (m > 0 && seg_key[b + m - 1] > kj) {
+                    seg_key[b + m] = seg_key[b + m - 1];
+                    seg_col[b + m] = seg_col[b + m - 1];
+                    --m;
+                }
+                seg_key[b + m] = kj;
+                seg_col[b + m] = cj;
+            }
+            for (int64_t j = 0; j < n; ++j) {
+                const float4 c = seg_col[b + j];
+                acc.x = ffma(tr, c.x, acc.x);
+                acc.y = ffma(tr, c.y, acc.y);
+                acc.z = ffma(tr, c.z, acc.z);
+                tr *= 1.0f - c.w;
+            }
+        }
+        reinterpret_cast<float4*>(rgba)[gp] = make_float4(acc.x, acc.y, acc.z, 1.0f - tr);
+        if (n > 0) atomicMax(&ctr->max_segments, (int)n);
+    }
+}
+
+// ------------------------------------------------------------------------
 // image-space reductions (compensated, fixed input order)
 
 struct Neumaier {
@@ -686,8 +935,12 @@ bool stage_config_eligible(const GridD& g, int cfg) {
 cudaError_t prepare_kernels() {
     // Loads every kernel and fills the occupancy cache, so that no module
     // loading happens later inside a stream capture.
-    const void* fns[] = {(const void*)k_pass1_piece, (const void*)k_pass2_piece, (const void*)k_moments_sum,
-                         (const void*)k_color_resolve};
+    const void* fns[] = {(const void*)k_pass1_piece,        (const void*)k_pass2_piece,
+                         (const void*)k_moments_sum,        (const void*)k_color_resolve,
+                         (const void*)k_sortlast_piece<true>, (const void*)k_sortlast_piece<false>,
+                         (const void*)k_sortlast_totals,    (const void*)k_sortlast_starts,
+                         (const void*)k_scan_blocks,        (const void*)k_scan_sums,
+                         (const void*)k_scan_add,           (const void*)k_sortlast_blend};
     for (const void* f : fns) {
         cudaFuncAttributes a;
         const cudaError_t e = cudaFuncGetAttributes(&a, f);
@@ -771,6 +1024,39 @@ cudaError_t launch_color_resolve(const ViewTable& vt, int32_t n_inputs, const fl
         const int blocks = (int)((npix + 255) / 256 < 4096 ? (npix + 255) / 256 : 4096);
         k_color_resolve<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(src, dst, b0, npix, n_inputs, bg, raw_sum);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sortlast_march(bool fill, const GridD& g, const float4* tf, const int32_t* pob, int32_t piece,
+                                  const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
+                                  int32_t* counts, const int64_t* starts, int32_t* seg_key, float4* seg_col,
+                                  cudaStream_t s) {
+    const int blocks = (vt.total_tiles + 3) / 4;
+    if (fill)
+        k_sortlast_piece<true><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, counts, starts, seg_key,
+                                                      seg_col);
+    else
+        k_sortlast_piece<false><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, counts, starts,
+                                                       seg_key, seg_col);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sortlast_offsets(const ViewTable& vt, int32_t n_slots, const int32_t* counts, int32_t* totals,
+                                   int64_t* base, int64_t* bsum, int64_t* starts, int64_t total_px, cudaStream_t s) {
+    const int grid = (int)((total_px + 255) / 256 < 8192 ? (total_px + 255) / 256 : 8192);
+    k_sortlast_totals<<<grid, 256, 0, s>>>(vt, n_slots, counts, totals, total_px);
+    const int64_t nb = (total_px + 1023) / 1024;
+    k_scan_blocks<<<(unsigned)nb, 1024, 0, s>>>(totals, base, bsum, total_px);
+    k_scan_sums<<<1, 1024, 0, s>>>(bsum, nb, base + total_px);
+    k_scan_add<<<(unsigned)nb, 1024, 0, s>>>(base, bsum, total_px);
+    k_sortlast_starts<<<grid, 256, 0, s>>>(vt, n_slots, counts, base, starts, total_px);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sortlast_blend(const int64_t* base, int32_t* seg_key, float4* seg_col, float* rgba, int64_t total_px,
+                                  Counters* ctr, cudaStream_t s) {
+    const int grid = (int)((total_px + 127) / 128 < 16384 ? (total_px + 127) / 128 : 16384);
+    k_sortlast_blend<<<grid, 128, 0, s>>>(base, seg_key, seg_col, rgba, total_px, ctr);
     return cudaGetLastError();
 }
 

@@ -296,6 +296,16 @@ def test_sandwich_partials_add_up():
         assert r["piece_color"][:, P, 3].max() > 1e-3
 
 
+def test_sortlast_segments_of_interleaved_slabs():
+    """Fig. 6 geometry: six z-slabs dealt to three pieces in turn; a ray along
+    +z crosses six slabs, so each piece contributes two segments."""
+    sc = small.sandwich_scene()
+    sc.views = [small.axis_view(sc.dims, 6, 6, -10.0, 10.0, near=5.0, far=60.0)]
+    rgba, nseg = oracle.render_segments(sc)
+    assert np.all(nseg == 6)
+    np.testing.assert_allclose(rgba, oracle.render_grid(sc, want=("exact",))["exact"], atol=1e-12)
+
+
 def test_empty_and_missing_rays():
     """Rays that miss the domain produce zero moments and a zero image."""
     sc = small.slab_scene()
