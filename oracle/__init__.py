@@ -43,6 +43,16 @@ class _Grid(ctypes.Structure):
                 ("bias_vector", ctypes.c_double * 4)]
 
 
+class _Amr(ctypes.Structure):
+    _fields_ = [("values", ctypes.c_void_p), ("leaves", ctypes.c_void_p), ("n_leaves", ctypes.c_int32),
+                ("max_level", ctypes.c_int32), ("finest_cells", ctypes.c_int32), ("brick_log2", ctypes.c_int32),
+                ("piece_of_leaf", ctypes.c_void_p), ("n_pieces", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("piece_selected", ctypes.c_void_p), ("tf", ctypes.c_void_p), ("vmin", ctypes.c_double),
+                ("vmax", ctypes.c_double), ("step", ctypes.c_double), ("moment_bias", ctypes.c_double),
+                ("overestimation", ctypes.c_double), ("absorbance_max", ctypes.c_double),
+                ("bias_vector", ctypes.c_double * 4)]
+
+
 def build(force=False):
     """Compile the oracle with the host C compiler (no FMA contraction)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
@@ -69,6 +79,9 @@ def _load():
             lib.orc_render_grid.restype = ctypes.c_int
             lib.orc_render_grid.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64] + \
                 [ctypes.c_void_p] * 8
+            lib.orc_render_amr.restype = ctypes.c_int
+            lib.orc_render_amr.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64] + \
+                [ctypes.c_void_p] * 9
             lib.orc_render_grid_segments.restype = ctypes.c_int
             lib.orc_render_grid_segments.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
@@ -134,8 +147,71 @@ def _grid_struct(scene, pieces):
     return g, keep
 
 
+def _amr_struct(scene, pieces):
+    K = scene.n_pieces
+    keep = dict(values=np.ascontiguousarray(scene.values, dtype=np.float32),
+                leaves=np.ascontiguousarray(scene.leaves, dtype=np.int32),
+                pol=np.ascontiguousarray(scene.piece_of_leaf, dtype=np.int32),
+                tf=np.ascontiguousarray(scene.tf, dtype=np.float32), sel=None)
+    if pieces is not None:
+        keep["sel"] = np.zeros(K, dtype=np.uint8)
+        keep["sel"][np.asarray(list(pieces), dtype=np.int64)] = 1
+    a = _Amr()
+    a.values, a.leaves, a.n_leaves = keep["values"].ctypes.data, keep["leaves"].ctypes.data, scene.leaves.shape[0]
+    a.max_level, a.finest_cells, a.brick_log2 = scene.max_level, scene.finest_cells, scene.brick_log2
+    a.piece_of_leaf, a.n_pieces = keep["pol"].ctypes.data, K
+    a.piece_selected = _ptr(keep["sel"])
+    a.tf = keep["tf"].ctypes.data
+    a.vmin, a.vmax = float(scene.tf_range[0]), float(scene.tf_range[1])
+    a.step = float(scene.step)
+    a.moment_bias, a.overestimation = float(scene.moment_bias), float(scene.overestimation)
+    a.absorbance_max = float(scene.absorbance_max)
+    a.bias_vector[:] = list(getattr(scene, "bias_vector", BIAS_VECTOR_POWER4))
+    return a, keep
+
+
+def _is_amr(scene):
+    return hasattr(scene, "leaves")
+
+
+def render_amr(scene, view=0, pixels=None, pieces=None, want=("mboit",)):
+    """render_grid for a brick-octree scene (`scenes.AmrScene`); `want` may
+    also name "nsegments"."""
+    lib = _load()
+    v = scene.views[view] if isinstance(view, int) else view
+    pix = np.arange(v.width * v.height, dtype=np.int64) if pixels is None else \
+        np.ascontiguousarray(pixels, dtype=np.int64)
+    n, K = pix.size, scene.n_pieces
+    shapes = {"moments": (n, 5), "piece_moments": (n, K, 5), "piece_color": (n, K, 4), "mboit": (n, 4),
+              "raw": (n, 4), "exact": (n, 4), "sortlast": (n, 4)}
+    out = {k: np.zeros(shapes[k]) for k in want if k in shapes}
+    for k in ("nsamples", "nsegments"):
+        if k in want:
+            out[k] = np.zeros(n, dtype=np.int64)
+    if "nsegments" in out and "sortlast" not in out:
+        out["sortlast"] = np.zeros((n, 4))
+    a, keep = _amr_struct(scene, pieces)
+    vs = _view_struct(v)
+    rc = lib.orc_render_amr(ctypes.byref(a), ctypes.byref(vs), pix.ctypes.data, n,
+                            _ptr(out.get("moments")), _ptr(out.get("piece_moments")), _ptr(out.get("piece_color")),
+                            _ptr(out.get("mboit")), _ptr(out.get("raw")), _ptr(out.get("exact")),
+                            _ptr(out.get("sortlast")), _ptr(out.get("nsamples")), _ptr(out.get("nsegments")))
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments (bad or overlapping leaves?)")
+    return out
+
+
+def render(scene, view=0, pixels=None, pieces=None, want=("mboit",)):
+    """render_grid or render_amr, by scene type."""
+    f = render_amr if _is_amr(scene) else render_grid
+    return f(scene, view=view, pixels=pixels, pieces=pieces, want=want)
+
+
 def render_segments(scene, view=0, pixels=None, pieces=None):
     """Sort-last route only: (rgba [n][4] float64, segments per pixel [n] int64)."""
+    if _is_amr(scene):
+        r = render_amr(scene, view=view, pixels=pixels, pieces=pieces, want=("sortlast", "nsegments"))
+        return r["sortlast"], r["nsegments"]
     lib = _load()
     v = scene.views[view] if isinstance(view, int) else view
     pix = np.arange(v.width * v.height, dtype=np.int64) if pixels is None else \

@@ -134,7 +134,9 @@ double orc_mboit_bound(const double m[5], double z0, double moment_bias,
      * q2 x^2 + q1 x + q0 */
     double z[3];
     z[0] = z0;
+    z[1] = z[2] = z0;
     int nroot = quadratic_roots(q2, q1, q0, &z[1], &z[2]);
+    if (nroot == 0) return overestimation;  /* constant kernel polynomial: all mass at z0 */
 
     /* weights: overestimation at z0, indicator z_i < z0 elsewhere */
     double w[3];
@@ -162,7 +164,24 @@ double orc_mboit_bound(const double m[5], double z0, double moment_bias,
     return p0 + p1 * b[1] + p2 * b[2];
 }
 
-static double transmittance(const double m[5], double z0, const orc_grid* g)
+/* ------------------------------------------------------------------------ */
+/* the volume being rendered: a regular grid or a brick octree               */
+
+typedef struct {
+    int kind;                      /* 0 grid, 1 brick octree */
+    const orc_grid* g;
+    const orc_amr* a;
+    int32_t* fmap;                 /* octree: finest brick -> leaf (-1 none) */
+    int64_t fdim;                  /* finest bricks per axis */
+    double hi[3];                  /* the domain is [0, hi) per axis */
+    int n_pieces;
+    const uint8_t* piece_selected;
+    const float* tf;
+    double vmin, vmax, step, moment_bias, overestimation, absorbance_max;
+    const double* bias_vector;
+} vol_t;
+
+static double transmittance(const double m[5], double z0, const vol_t* g)
 {
     double A = orc_mboit_bound(m, z0, g->moment_bias, g->bias_vector, g->overestimation, NULL);
     double T = exp(-m[0] * A);
@@ -200,9 +219,9 @@ static void make_ray(const orc_view* V, int64_t px, int64_t py, float o[3], floa
 
 /* Lattice index range [k_lo, k_hi] that surely contains every lattice point
  * whose float32 position is inside the domain (the position test decides). */
-static int lattice_range(const orc_grid* g, const float o[3], const float d[3], int64_t* k_lo, int64_t* k_hi)
+static int lattice_range(const vol_t* g, const float o[3], const float d[3], int64_t* k_lo, int64_t* k_hi)
 {
-    double hi[3] = {g->nx - 1.0, g->ny - 1.0, g->nz - 1.0};
+    const double* hi = g->hi;
     double t0 = 0.0, t1 = INFINITY;
     for (int c = 0; c < 3; ++c) {
         if (d[c] == 0.0f) {
@@ -235,35 +254,80 @@ typedef struct {
     double t, z, a, alpha, rgb[3];
 } sample_t;
 
-/* Classifies lattice point k; returns 1 and fills s if it is inside the
- * domain and owned by a selected piece. */
-static int take_sample(const orc_grid* g, const orc_view* V, const float o[3], const float d[3],
-                       int64_t k, const double* sig_tab, sample_t* s)
+/* Grid: the piece owning the brick of the point's cell, and the trilinear
+ * value of the cell's 8 vertices; -1 if the brick belongs to no piece. */
+static int locate_grid(const orc_grid* g, const float p[3], double* val)
 {
-    float t = ((float)k + 0.5f) * (float)g->step;
-    float p[3];
-    for (int c = 0; c < 3; ++c) p[c] = fmaf(t, d[c], o[c]);
-    const float hi[3] = {(float)(g->nx - 1), (float)(g->ny - 1), (float)(g->nz - 1)};
-    for (int c = 0; c < 3; ++c)
-        if (!(p[c] >= 0.0f && p[c] < hi[c])) return 0;
     int cell[3];
     for (int c = 0; c < 3; ++c) cell[c] = (int)floorf(p[c]);
     int B = 1 << g->brick_log2;
     int nbx = (g->nx - 1 + B - 1) / B, nby = (g->ny - 1 + B - 1) / B;
     int brick = ((cell[2] >> g->brick_log2) * nby + (cell[1] >> g->brick_log2)) * nbx + (cell[0] >> g->brick_log2);
     int piece = g->piece_of_brick[brick];
-    if (g->piece_selected && !g->piece_selected[piece]) return 0;
-
-    /* trilinear interpolation of the cell's 8 vertex values */
+    if (piece < 0) return -1;
     double fx = (double)p[0] - cell[0], fy = (double)p[1] - cell[1], fz = (double)p[2] - cell[2];
-    double val = 0.0;
+    double v = 0.0;
     for (int dz = 0; dz <= 1; ++dz)
         for (int dy = 0; dy <= 1; ++dy)
             for (int dx = 0; dx <= 1; ++dx) {
                 double wgt = (dx ? fx : 1.0 - fx) * (dy ? fy : 1.0 - fy) * (dz ? fz : 1.0 - fz);
                 int64_t idx = ((int64_t)(cell[2] + dz) * g->ny + (cell[1] + dy)) * g->nx + (cell[0] + dx);
-                val += wgt * (double)g->field[idx];
+                v += wgt * (double)g->field[idx];
             }
+    *val = v;
+    return piece;
+}
+
+/* Octree: the leaf whose half-open box holds the point; local coordinates in
+ * the leaf's cells; trilinear value of that cell's 8 vertices. */
+static int locate_amr(const vol_t* vol, const float p[3], double* val)
+{
+    const orc_amr* a = vol->a;
+    int64_t fb[3];
+    for (int c = 0; c < 3; ++c) fb[c] = (int64_t)floorf(p[c]) >> a->brick_log2;
+    int32_t leaf = vol->fmap[(fb[2] * vol->fdim + fb[1]) * vol->fdim + fb[0]];
+    if (leaf < 0) return -1;
+    int piece = a->piece_of_leaf[leaf];
+    if (piece < 0) return -1;
+    const int32_t* L = a->leaves + 4 * (int64_t)leaf;
+    double h = ldexp(1.0, a->max_level - L[3]);    /* finest cells per leaf cell */
+    int n = 1 << a->brick_log2, nv = n + 1;
+    int cell[3];
+    double f[3];
+    for (int c = 0; c < 3; ++c) {
+        double q = ((double)p[c] - L[c]) / h;
+        int ci = (int)floor(q);
+        if (ci < 0) ci = 0;
+        if (ci > n - 1) ci = n - 1;
+        cell[c] = ci;
+        f[c] = q - ci;
+    }
+    const float* vals = a->values + (int64_t)leaf * nv * nv * nv;
+    double v = 0.0;
+    for (int dz = 0; dz <= 1; ++dz)
+        for (int dy = 0; dy <= 1; ++dy)
+            for (int dx = 0; dx <= 1; ++dx) {
+                double wgt = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+                v += wgt * (double)vals[((cell[2] + dz) * nv + (cell[1] + dy)) * nv + (cell[0] + dx)];
+            }
+    *val = v;
+    return piece;
+}
+
+/* Classifies lattice point k; returns 1 and fills s if it is inside the
+ * domain and owned by a selected piece. */
+static int take_sample(const vol_t* g, const orc_view* V, const float o[3], const float d[3],
+                       int64_t k, const double* sig_tab, sample_t* s)
+{
+    float t = ((float)k + 0.5f) * (float)g->step;
+    float p[3];
+    for (int c = 0; c < 3; ++c) p[c] = fmaf(t, d[c], o[c]);
+    for (int c = 0; c < 3; ++c)
+        if (!(p[c] >= 0.0f && p[c] < (float)g->hi[c])) return 0;
+    double val;
+    int piece = (g->kind == 0) ? locate_grid(g->g, p, &val) : locate_amr(g, p, &val);
+    if (piece < 0) return 0;
+    if (g->piece_selected && !g->piece_selected[piece]) return 0;
 
     /* transfer function: normalise, 256-entry linear lookup of (r, g, b, sigma) */
     double x = (val - g->vmin) / (g->vmax - g->vmin);
@@ -291,11 +355,100 @@ static int take_sample(const orc_grid* g, const orc_view* V, const float o[3], c
 /* ------------------------------------------------------------------------ */
 /* one pixel                                                                 */
 
+static int render_impl(const vol_t* g, const orc_view* V,
+                       const int64_t* pixels, int64_t n_pixels,
+                       double* moments, double* piece_moments, double* piece_color,
+                       double* mboit_rgba, double* raw_rgba, double* exact_rgba,
+                       double* sortlast_rgba, int64_t* nsamples, int64_t* nsegments);
+
+static int grid_vol(const orc_grid* g, vol_t* v)
+{
+    if (!g || !g->field || !g->piece_of_brick || !g->tf || g->n_pieces <= 0) return -1;
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2) return -1;
+    memset(v, 0, sizeof *v);
+    v->kind = 0;
+    v->g = g;
+    v->hi[0] = g->nx - 1.0;
+    v->hi[1] = g->ny - 1.0;
+    v->hi[2] = g->nz - 1.0;
+    v->n_pieces = g->n_pieces;
+    v->piece_selected = g->piece_selected;
+    v->tf = g->tf;
+    v->vmin = g->vmin;
+    v->vmax = g->vmax;
+    v->step = g->step;
+    v->moment_bias = g->moment_bias;
+    v->overestimation = g->overestimation;
+    v->absorbance_max = g->absorbance_max;
+    v->bias_vector = g->bias_vector;
+    return 0;
+}
+
 static int render_grid_impl(const orc_grid* g, const orc_view* V,
                             const int64_t* pixels, int64_t n_pixels,
                             double* moments, double* piece_moments, double* piece_color,
                             double* mboit_rgba, double* raw_rgba, double* exact_rgba,
-                            double* sortlast_rgba, int64_t* nsamples, int64_t* nsegments);
+                            double* sortlast_rgba, int64_t* nsamples, int64_t* nsegments)
+{
+    vol_t v;
+    if (grid_vol(g, &v) != 0) return -1;
+    return render_impl(&v, V, pixels, n_pixels, moments, piece_moments, piece_color, mboit_rgba, raw_rgba,
+                       exact_rgba, sortlast_rgba, nsamples, nsegments);
+}
+
+int orc_render_amr(const orc_amr* a, const orc_view* V,
+                   const int64_t* pixels, int64_t n_pixels,
+                   double* moments, double* piece_moments, double* piece_color,
+                   double* mboit_rgba, double* raw_rgba, double* exact_rgba,
+                   double* sortlast_rgba, int64_t* nsamples, int64_t* nsegments)
+{
+    if (!a || !a->values || !a->leaves || !a->piece_of_leaf || !a->tf || a->n_pieces <= 0 || a->n_leaves <= 0)
+        return -1;
+    if (a->brick_log2 < 0 || a->brick_log2 > 7 || a->max_level < 0 || a->finest_cells < 1) return -1;
+    int64_t fdim = ((int64_t)a->finest_cells + (1 << a->brick_log2) - 1) >> a->brick_log2;
+    int32_t* fmap = (int32_t*)malloc((size_t)(fdim * fdim * fdim) * sizeof(int32_t));
+    if (!fmap) return -1;
+    for (int64_t i = 0; i < fdim * fdim * fdim; ++i) fmap[i] = -1;
+    for (int32_t l = 0; l < a->n_leaves; ++l) {
+        const int32_t* L = a->leaves + 4 * (int64_t)l;
+        if (L[3] < 0 || L[3] > a->max_level) { free(fmap); return -1; }
+        int64_t nb = (int64_t)1 << (a->max_level - L[3]);      /* finest bricks per side */
+        int64_t b0[3];
+        for (int c = 0; c < 3; ++c) {
+            if (L[c] < 0 || (L[c] & ((1 << a->brick_log2) - 1))) { free(fmap); return -1; }
+            b0[c] = L[c] >> a->brick_log2;
+            if (b0[c] + nb > fdim) { free(fmap); return -1; }
+        }
+        for (int64_t z = b0[2]; z < b0[2] + nb; ++z)
+            for (int64_t y = b0[1]; y < b0[1] + nb; ++y)
+                for (int64_t x = b0[0]; x < b0[0] + nb; ++x) {
+                    int32_t* m = fmap + (z * fdim + y) * fdim + x;
+                    if (*m >= 0) { free(fmap); return -1; }   /* overlapping leaves */
+                    *m = l;
+                }
+    }
+    vol_t v;
+    memset(&v, 0, sizeof v);
+    v.kind = 1;
+    v.a = a;
+    v.fmap = fmap;
+    v.fdim = fdim;
+    v.hi[0] = v.hi[1] = v.hi[2] = (double)a->finest_cells;
+    v.n_pieces = a->n_pieces;
+    v.piece_selected = a->piece_selected;
+    v.tf = a->tf;
+    v.vmin = a->vmin;
+    v.vmax = a->vmax;
+    v.step = a->step;
+    v.moment_bias = a->moment_bias;
+    v.overestimation = a->overestimation;
+    v.absorbance_max = a->absorbance_max;
+    v.bias_vector = a->bias_vector;
+    int rc = render_impl(&v, V, pixels, n_pixels, moments, piece_moments, piece_color, mboit_rgba, raw_rgba,
+                         exact_rgba, sortlast_rgba, nsamples, nsegments);
+    free(fmap);
+    return rc;
+}
 
 int orc_render_grid(const orc_grid* g, const orc_view* V,
                     const int64_t* pixels, int64_t n_pixels,
@@ -322,14 +475,13 @@ int orc_render_grid_segments(const orc_grid* g, const orc_view* V,
     return rc;
 }
 
-static int render_grid_impl(const orc_grid* g, const orc_view* V,
-                            const int64_t* pixels, int64_t n_pixels,
-                            double* moments, double* piece_moments, double* piece_color,
-                            double* mboit_rgba, double* raw_rgba, double* exact_rgba,
-                            double* sortlast_rgba, int64_t* nsamples, int64_t* nsegments)
+static int render_impl(const vol_t* g, const orc_view* V,
+                       const int64_t* pixels, int64_t n_pixels,
+                       double* moments, double* piece_moments, double* piece_color,
+                       double* mboit_rgba, double* raw_rgba, double* exact_rgba,
+                       double* sortlast_rgba, int64_t* nsamples, int64_t* nsegments)
 {
-    if (!g || !V || !g->field || !g->piece_of_brick || !g->tf || g->n_pieces <= 0) return -1;
-    if (g->nx < 2 || g->ny < 2 || g->nz < 2 || !(g->step > 0.0) || !(g->vmax > g->vmin)) return -1;
+    if (!V || !(g->step > 0.0) || !(g->vmax > g->vmin)) return -1;
     const int K = g->n_pieces;
 
     double sig_tab[256];

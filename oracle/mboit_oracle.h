@@ -38,6 +38,20 @@ typedef struct {
     double bias_vector[4];
 } orc_grid;
 
+typedef struct {
+    const float* values;           /* [n_leaves][9][9][9]: vertex values of each leaf at its level */
+    const int32_t* leaves;         /* [n_leaves][4]: origin x, y, z in finest cells, level */
+    int32_t n_leaves, max_level;
+    int32_t finest_cells;          /* D: the domain is [0, D]^3 in finest-cell units */
+    int32_t brick_log2;            /* a leaf is 2^brick_log2 cells of its level on a side */
+    const int32_t* piece_of_leaf;  /* [n_leaves] */
+    int32_t n_pieces, reserved;
+    const uint8_t* piece_selected; /* [n_pieces], NULL = every piece */
+    const float* tf;
+    double vmin, vmax, step, moment_bias, overestimation, absorbance_max;
+    double bias_vector[4];
+} orc_amr;
+
 /* Alg. 3 core: the moment-bound absorbance fraction A(z0) in [0,1] for raw
  * power moments m[0..4]; the transmittance is clamp(exp(-m[0]*A)).
  * *flags (optional) gets 1 for the one-atom, 2 for the two-atom branch. */
@@ -65,6 +79,16 @@ int orc_render_grid(const orc_grid* g, const orc_view* view,
 int orc_render_grid_segments(const orc_grid* g, const orc_view* view,
                              const int64_t* pixels, int64_t n_pixels,
                              double* sortlast_rgba, int64_t* nsegments);
+
+/* The same outputs for a brick-octree (AMR) volume: a lattice point belongs
+ * to the leaf whose half-open box contains it, and takes the trilinear
+ * interpolation of that leaf's vertex values at the leaf's resolution.
+ * Returns -1 also for overlapping leaves. */
+int orc_render_amr(const orc_amr* a, const orc_view* view,
+                   const int64_t* pixels, int64_t n_pixels,
+                   double* moments, double* piece_moments, double* piece_color,
+                   double* mboit_rgba, double* raw_rgba, double* exact_rgba,
+                   double* sortlast_rgba, int64_t* nsamples, int64_t* nsegments);
 
 #ifdef __cplusplus
 }

@@ -279,3 +279,198 @@ def blobs512(width=2048, height=2048, n_pieces=64, seed=1002, n=512):
     view = perspective_view(dims, (0.57, 0.49, 0.66), width, height)
     return GridScene("blobs512" if n == 512 else f"blobs{n}", f, bl, piece, n_pieces, tf,
                      (np.float32(f.min()), np.float32(f.max())), 0.5, [view])
+
+
+# ---------------------------------------------------------------------------
+# AMR brick octree
+
+@dataclass
+class AmrScene:
+    """Leaves of a brick octree.  Leaf i covers origin_i + [0, 8 * 2^(max_level -
+    level_i))^3 in finest-cell units and stores 9^3 vertex-centred values of
+    the field at its own resolution, values[i][z][y][x].  The domain is
+    [0, D]^3 with D = base_bricks * 8 * 2^max_level finest cells."""
+    name: str
+    leaves: np.ndarray          # int32 [n][4]: origin x, y, z (finest cells), level
+    values: np.ndarray          # float32 [n][9][9][9]
+    max_level: int
+    finest_cells: int           # D
+    piece_of_leaf: np.ndarray   # int32 [n]
+    n_pieces: int
+    tf: np.ndarray
+    tf_range: tuple
+    step: float
+    views: List[View] = dc_field(default_factory=list)
+    moment_bias: float = 5e-5
+    overestimation: float = 0.3
+    absorbance_max: float = 10.0
+    brick_log2: int = 3
+
+    @property
+    def dims(self):
+        return (self.finest_cells + 1,) * 3
+
+    @property
+    def n_units(self):
+        return self.leaves.shape[0]
+
+
+class AnalyticField:
+    """The 512^3 workload's field as a function of position (Gaussian blobs
+    plus lattice value noise, trilinear between lattice values), so it can be
+    sampled at any resolution."""
+
+    def __init__(self, seed=1002, n=512):
+        s = Stream(seed)
+        k = n / 64.0
+        nb = 64
+        self.c = s.uniform(3 * nb).reshape(nb, 3) * n
+        self.s = s.uniform(nb, 4.0 * k, 12.0 * k)
+        self.a = s.uniform(nb, 0.3, 1.0)
+        self.noise = []
+        for o in range(3):
+            sp = max(2.0, 64.0 * k / 8.0 / 2 ** o)
+            L = int(np.ceil((n - 1) / sp)) + 1
+            V = s.uniform(L * L * L).reshape(L, L, L)   # [z][y][x]
+            self.noise.append((0.15 * 0.5 ** o, sp, V))
+
+    def grid_values(self, xs, ys, zs):
+        """Values on the tensor grid xs x ys x zs (1-D arrays, coordinates of
+        the 512^3 vertex space), returned [z][y][x]."""
+        gx = np.exp(-(xs[None, :] - self.c[:, 0:1]) ** 2 / (2 * self.s[:, None] ** 2)) * self.a[:, None]
+        gy = np.exp(-(ys[None, :] - self.c[:, 1:2]) ** 2 / (2 * self.s[:, None] ** 2))
+        gz = np.exp(-(zs[None, :] - self.c[:, 2:3]) ** 2 / (2 * self.s[:, None] ** 2))
+        out = np.einsum("bz,by,bx->zyx", gz, gy, gx)
+        for w, sp, V in self.noise:
+            L = V.shape[0]
+            def lerp_w(q):
+                x = q / sp
+                i = np.minimum(np.floor(x).astype(np.int64), L - 2)
+                f = x - i
+                W = np.zeros((q.size, L))
+                W[np.arange(q.size), i] = 1.0 - f
+                W[np.arange(q.size), i + 1] += f
+                return W
+            Wx, Wy, Wz = lerp_w(xs), lerp_w(ys), lerp_w(zs)
+            out += w * np.einsum("zc,yb,xa,cba->zyx", Wz, Wy, Wx, V, optimize=True)
+        return out
+
+
+def _leaf_values(field, origins_f, size_f, scale, batch=2048):
+    """9^3 samples of each leaf (finest-unit origins, one finest-unit size for
+    all) of the analytic field, whose coordinates are finest units * scale."""
+    n = len(origins_f)
+    out = np.empty((n, 9, 9, 9), np.float32)
+    h = float(size_f[0]) / 8.0 if n else 1.0
+    j = np.arange(9, dtype=np.float64)
+    for b0 in range(0, n, batch):
+        o = origins_f[b0:b0 + batch].astype(np.float64)
+        X = (o[:, 0:1] + j * h) * scale           # [B][9] coordinates per axis
+        Y = (o[:, 1:2] + j * h) * scale
+        Z = (o[:, 2:3] + j * h) * scale
+        B = len(o)
+        # Gaussian blobs, separable: [B][blob][9] per axis, then (z,y) x x products
+        gx = np.exp(-(X[:, None, :] - field.c[None, :, 0:1]) ** 2 / (2 * field.s[None, :, None] ** 2)) * field.a[None, :, None]
+        gy = np.exp(-(Y[:, None, :] - field.c[None, :, 1:2]) ** 2 / (2 * field.s[None, :, None] ** 2))
+        gz = np.exp(-(Z[:, None, :] - field.c[None, :, 2:3]) ** 2 / (2 * field.s[None, :, None] ** 2))
+        zy = (gz[:, :, :, None] * gy[:, :, None, :]).reshape(B, gx.shape[1], 81)
+        v = np.matmul(zy.transpose(0, 2, 1), gx).reshape(B, 9, 9, 9)
+        # value noise: trilinear weights restricted to a 4x4x4 lattice block per leaf
+        for w, sp, V in field.noise:
+            L = V.shape[0]
+            nb = min(L, int(np.ceil(8 * h * scale / sp)) + 2)   # lattice block covering one leaf
+
+            def local(q):
+                x = q / sp
+                idx = np.minimum(np.floor(x).astype(np.int64), L - 2)
+                i0 = np.clip(idx[:, 0], 0, L - nb)
+                f = x - idx
+                W = np.zeros((q.shape[0], 9, nb))
+                rel = idx - i0[:, None]
+                bi = np.arange(q.shape[0])[:, None]
+                ji = np.arange(9)[None, :]
+                W[bi, ji, rel] = 1.0 - f
+                W[bi, ji, rel + 1] += f
+                return W, i0
+            Wx, ix = local(X)
+            Wy, iy = local(Y)
+            Wz, iz = local(Z)
+            r = np.arange(nb)
+            blk = V[(iz[:, None] + r)[:, :, None, None], (iy[:, None] + r)[:, None, :, None], (ix[:, None] + r)[:, None, None, :]]
+            v += w * np.einsum("bzc,byd,bxe,bcde->bzyx", Wz, Wy, Wx, blk, optimize=True)
+        out[b0:b0 + batch] = v.astype(np.float32)
+    return out
+
+
+def _max_gradient(vals, h):
+    g = np.zeros(vals.shape[0])
+    for ax in (1, 2, 3):
+        d = np.abs(np.diff(vals, axis=ax)) / h[:, None, None, None]
+        g = np.maximum(g, d.reshape(d.shape[0], -1).max(axis=1))
+    return g
+
+
+def amr_blobs(width=2560, height=2560, n_pieces=72, seed=1003, base=26, max_level=2, refine_frac=0.2,
+              alpha_max=None):
+    """Brick octree over the 512^3 workload's field: 26^3 base bricks of 8^3
+    cells, refined twice (the top 20 % of bricks by maximum gradient
+    magnitude each time), ~81.6k leaves / ~41.8M cells; 72 pieces of uneven
+    size (ratio 8) by Morton order of leaf origins; perspective view; step
+    0.5 finest voxel.  Smaller `base` / `max_level` shrink it for tests."""
+    field = AnalyticField()
+    D = base * 8 * (1 << max_level)
+    scale = 511.0 / D
+    bsz0 = 8 * (1 << max_level)
+    o = np.stack(np.meshgrid(np.arange(base), np.arange(base), np.arange(base), indexing="ij"), -1).reshape(-1, 3)
+    cur = o[:, ::-1] * bsz0                      # (x, y, z) finest-unit origins of level-0 bricks
+    leaves, values = [], []
+    for level in range(max_level + 1):
+        size = bsz0 >> level
+        vals = _leaf_values(field, cur, np.full(len(cur), size, np.float64), scale)
+        if level == max_level:
+            refine = np.zeros(len(cur), bool)
+        else:
+            g = _max_gradient(vals.astype(np.float64), np.full(len(cur), size / 8.0 * scale))
+            k = int(round(refine_frac * len(cur)))
+            refine = np.zeros(len(cur), bool)
+            refine[np.argsort(-g, kind="stable")[:k]] = True
+        keep = ~refine
+        leaves.append(np.concatenate([cur[keep], np.full((keep.sum(), 1), level)], axis=1))
+        values.append(vals[keep])
+        half = size // 2
+        kids = []
+        for dz in (0, half):
+            for dy in (0, half):
+                for dx in (0, half):
+                    kids.append(cur[refine] + np.array([dx, dy, dz]))
+        cur = np.concatenate(kids) if kids and refine.any() else np.zeros((0, 3), np.int64)
+    leaves = np.concatenate(leaves).astype(np.int32)
+    values = np.concatenate(values).astype(np.float32)
+    s = Stream(seed)
+    bits = int(np.ceil(np.log2(D)))
+    code = morton3(leaves[:, 0].astype(np.int64), leaves[:, 1].astype(np.int64), leaves[:, 2].astype(np.int64), bits)
+    order = np.argsort(code, kind="stable")
+    leaves, values = leaves[order], values[order]
+    u = s.uniform(n_pieces)
+    u = (u - u.min()) / (u.max() - u.min())
+    piece = morton_pieces_linear(len(leaves), n_pieces, 8.0 ** u, s)
+    vmin, vmax = float(values.min()), float(values.max())
+    am = alpha_max if alpha_max is not None else 0.053 * 512.0 / D
+    tf = tf_table(Stream(1002 + 7), am)
+    dims = (D + 1,) * 3
+    view = perspective_view(dims, (0.57, 0.49, 0.66), width, height)
+    return AmrScene("amr_blobs" if base == 26 else f"amr_blobs{base}", leaves, values, max_level, D, piece,
+                    n_pieces, tf, (np.float32(vmin), np.float32(vmax)), 0.5, [view])
+
+
+def morton_pieces_linear(n, n_pieces, weights, stream, jitter=0.0):
+    """Contiguous ranges of an already Morton-sorted list with relative sizes `weights`."""
+    cum = np.concatenate([[0.0], np.cumsum(weights) / np.sum(weights)]) * n
+    splits = [0]
+    for i in range(1, n_pieces):
+        splits.append(min(max(int(round(cum[i])), splits[-1] + 1), n - (n_pieces - i)))
+    splits.append(n)
+    piece = np.empty(n, dtype=np.int32)
+    for p in range(n_pieces):
+        piece[splits[p]:splits[p + 1]] = p
+    return piece

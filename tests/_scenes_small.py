@@ -64,3 +64,52 @@ def sandwich_scene(n=25, brick_log2=2, ranks=3, seed=11):
     piece = (bz % ranks).astype(np.int32)
     return scenes.GridScene("sandwich", field, brick_log2, piece, ranks, scenes.tf_table(s, 0.35),
                             (np.float32(field.min()), np.float32(field.max())), 0.5, [])
+
+
+def linear_amr(base=3, max_level=2, refine=((0, 0, 0), (1, 2, 1))):
+    """Brick octree with a dyadic linear field (exact in float32 at every
+    vertex): base^3 level-0 bricks of 8^3 cells; the listed level-0 bricks are
+    refined once, and the first child of each is refined again.  Returns the
+    octree scene and the finest regular grid holding the same field."""
+    bsz = 8 << max_level
+    D = base * bsz
+    lin = lambda x, y, z: 0.25 + x / 64.0 + y / 128.0 + z / 32.0  # noqa: E731
+    leaves = []
+
+    def add(o, level):
+        leaves.append((o[0], o[1], o[2], level))
+
+    for bz in range(base):
+        for by in range(base):
+            for bx in range(base):
+                o0 = (bx * bsz, by * bsz, bz * bsz)
+                if (bx, by, bz) not in refine:
+                    add(o0, 0)
+                    continue
+                half = bsz // 2
+                kids = [(o0[0] + dx, o0[1] + dy, o0[2] + dz) for dz in (0, half) for dy in (0, half) for dx in (0, half)]
+                for i, kidx in enumerate(kids):
+                    if i == 0 and max_level >= 2:
+                        q = half // 2
+                        for dz in (0, q):
+                            for dy in (0, q):
+                                for dx in (0, q):
+                                    add((kidx[0] + dx, kidx[1] + dy, kidx[2] + dz), 2)
+                    else:
+                        add(kidx, 1)
+    leaves = np.array(leaves, np.int32)
+    j = np.arange(9.0)
+    vals = np.empty((len(leaves), 9, 9, 9), np.float32)
+    for i, (ox, oy, oz, L) in enumerate(leaves):
+        h = (bsz >> L) / 8.0
+        z, y, x = np.meshgrid(oz + j * h, oy + j * h, ox + j * h, indexing="ij")
+        vals[i] = lin(x, y, z)
+    tf = linear_tf(0.04, 0.2)
+    g = np.arange(D + 1.0)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    field = lin(X, Y, Z).astype(np.float32)
+    vmin, vmax = np.float32(field.min()), np.float32(field.max())
+    amr = scenes.AmrScene("linear_amr", leaves, vals, max_level, D, np.zeros(len(leaves), np.int32), 1, tf,
+                          (vmin, vmax), 0.5, [])
+    grid = scenes.GridScene("linear_grid", field, 3, np.zeros(((D + 7) // 8) ** 3, np.int32), 1, tf, (vmin, vmax), 0.5, [])
+    return amr, grid
