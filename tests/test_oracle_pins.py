@@ -355,3 +355,39 @@ def test_amr_overlapping_leaves_rejected():
     bad.views = [scenes.ortho_view(amr.dims, (0.4, 0.5, 0.77), 4, 4)]
     with pytest.raises(ValueError):
         oracle.render_amr(bad)
+
+
+def test_amr_leaf_lookup_brute_force():
+    """A different constant in every leaf, a linear extinction table: each
+    ray's b0 and b1 must equal the sums over the enumerated lattice points of
+    the containing leaf's extinction, the leaf found by testing every box."""
+    amr, _ = small.linear_amr()
+    n = len(amr.leaves)
+    const = (np.arange(n) % 7) / 8.0 + 0.125
+    amr.values = np.broadcast_to(const[:, None, None, None], (n, 9, 9, 9)).astype(np.float32).copy()
+    amr.tf_range = (np.float32(0.0), np.float32(1.0))
+    view = small.axis_view(amr.dims, 9, 7, -20.0, 60.0, w=(0.36, 0.48, 0.8), u=(0.8, -0.6, 0.0),
+                           v=(0.48, 0.64, -0.6), near=4.0, far=300.0, centre=(40.0, 44.0))
+    view.eye = np.array([30.0, 20.0, -20.0], np.float32)
+    r = oracle.render_amr(amr, view=view, want=("moments", "nsamples"))
+    size = (8 << amr.max_level) >> amr.leaves[:, 3]
+    lo, hi = amr.leaves[:, :3].astype(np.float64), amr.leaves[:, :3] + size[:, None]
+    dims = amr.dims
+    hit = 0
+    for py in range(view.height):
+        for px in range(view.width):
+            S = _brute_samples(view, dims, amr.step, px, py)
+            m0 = m1 = 0.0
+            for t, p in S:
+                inside = np.all((lo <= p) & (np.array(p) < hi), axis=1)
+                assert inside.sum() == 1
+                val = const[np.argmax(inside)]
+                a = (0.04 + 0.2 * val) * amr.step
+                z = min(max(2 * math.log(t / 4.0) / math.log(300.0 / 4.0) - 1, -1), 1)
+                m0 += a
+                m1 += a * z
+            idx = py * view.width + px
+            assert r["nsamples"][idx] == len(S)
+            np.testing.assert_allclose(r["moments"][idx, :2], [m0, m1], rtol=2e-6, atol=1e-9)
+            hit += len(S) > 0
+    assert hit > 30
