@@ -140,16 +140,25 @@ def workload(name):
         return scenes.blobs512()
     if name == "blobs64":
         return scenes.blobs64()
+    if name == "amr":
+        return scenes.amr_blobs()
     raise SystemExit(f"unknown workload {name}")
 
 
 def config_of(sc, name):
     v = sc.views[0]
-    return {"workload": name, "field": "x".join(str(n) for n in sc.dims) + " float32",
+    if hasattr(sc, "leaves"):
+        lv = np.bincount(sc.leaves[:, 3])
+        field = (f"brick octree, {sc.leaves.shape[0]} leaves of 8^3 cells (per level {lv.tolist()}), "
+                 f"{sc.leaves.shape[0] * 512 / 1e6:.1f} M cells, finest {sc.finest_cells}^3, float32")
+    else:
+        field = "x".join(str(n) for n in sc.dims) + " float32"
+    return {"workload": name, "field": field,
             "pieces": sc.n_pieces, "brick_cells": 1 << sc.brick_log2, "image": f"{v.width}x{v.height}",
             "projection": "perspective" if v.projection else "orthographic", "step_voxels": sc.step,
             "moments": "4 power, float32", "moment_bias": sc.moment_bias, "overestimation": sc.overestimation,
-            "l2": f"inputs larger than L2 ({sc.field.nbytes >> 20} MiB field re-read every frame)"}
+            "l2": f"inputs larger than L2 ({(sc.values if hasattr(sc, 'leaves') else sc.field).nbytes >> 20} MiB "
+                  "volume re-read every frame)"}
 
 
 def run_reference(args, rank):
@@ -183,7 +192,8 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="blobs512", choices=["blobs512", "blobs64"])
+    ap.add_argument("--workload", default="blobs512", choices=["blobs512", "blobs64", "amr"])
+    ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-piece", action="store_true")
     ap.add_argument("--no-sortlast", action="store_true")
@@ -307,8 +317,49 @@ def main():
         del exact
         torch.cuda.empty_cache()
 
+    # the 72-piece brick-octree workload (2560x2560) as a second line of results
+    amr = None
+    if args.workload == "blobs512" and not args.no_amr:
+        asc = workload("amr")
+        avol = pkg.Volume(asc)
+        av = asc.views
+        amom, argba = pkg.Volume.moment_buffer(av), pkg.Volume.color_buffer(av)
+        aframe = lambda: avol.render_frame(av, amom, argba)  # noqa: E731
+        for _ in range(3):
+            aframe()
+        ms_a = timed(aframe, max(3, args.steps // 3))
+        avol.synchronize()
+        sa = avol.stats()["samples_pass1"]
+        K = asc.n_pieces
+        pm, pc, gm = pkg.Volume.moment_buffer(av, K), pkg.Volume.color_buffer(av, K), pkg.Volume.moment_buffer(av)
+        aw, ah = av[0].width, av[0].height
+
+        def aplain():
+            avol.render_moments(av, pm, mode=pkg.MBOIT_MOMENTS_PER_PIECE)
+            avol.composite(pkg.MBOIT_OP_MOMENTS_SUM, aw, ah, 1, K, pm, gm)
+            avol.reconstruct_blend(av, gm, pc, mode=pkg.MBOIT_COLOR_PER_PIECE)
+            avol.composite(pkg.MBOIT_OP_COLOR_SUM_RESOLVE, aw, ah, 1, K, pc, argba, gm)
+        aplain()
+        ms_ap = timed(aplain, 3)
+        del pm, pc, gm
+        torch.cuda.empty_cache()
+        aframe()
+        avol.synchronize()
+        amr = {"config": config_of(asc, "amr"), "samples_per_frame": sa, "ms_per_frame": ms_a,
+               "gsamples_per_s": sa / (ms_a * 1e-3) / 1e9, "per_piece_fp32_ms_per_frame": ms_ap,
+               "speedup_of_batched": ms_ap / ms_a}
+        if rank == 0 and not args.no_cpu_baseline:
+            apix = sample_pixels(aw, ah, 64, 32)
+            ref = __import__("oracle").render_amr(asc, pixels=apix, want=("mboit",))["mboit"]
+            got = argba.view(-1, 4)[torch.from_numpy(apix).cuda()].double().cpu().numpy()
+            amr["quality"] = {"pixels": int(apix.size), "max_abs_vs_oracle": float(np.abs(got - ref).max()),
+                              "rmse_vs_oracle": float(np.sqrt(((got - ref) ** 2).mean()))}
+        avol.close()
+        del avol, amom, argba
+        torch.cuda.empty_cache()
+
     # end to end through the host API: field upload, frame, image download
-    field_host = torch.from_numpy(np.ascontiguousarray(sc.field)).pin_memory()
+    field_host = torch.from_numpy(np.ascontiguousarray(sc.values if hasattr(sc, "leaves") else sc.field)).pin_memory()
     rgba_host = torch.empty(rgba.numel(), dtype=torch.float32).pin_memory()
     e2e_step = lambda: pkg.mboit_render_frame_host(vol.handle, field_host, views, mom, rgba, rgba_host)  # noqa: E731
     e2e_step()
@@ -319,7 +370,7 @@ def main():
     barrier()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / max(3, args.steps // 3))
     e2e = {"value": samples * world / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
-           "h2d_bytes_per_step": int(sc.field.nbytes), "d2h_bytes_per_step": int(rgba_host.numel() * 4)}
+           "h2d_bytes_per_step": int(field_host.numel() * 4), "d2h_bytes_per_step": int(rgba_host.numel() * 4)}
 
     # parity on a pixel sample and the oracle's own speed (rank 0, one GPU)
     cpu_baseline, quality = None, None
@@ -346,7 +397,7 @@ def main():
                           form="batched: 2 persistent kernels per frame, CUDA graph",
                           tuning={"pass1": tuning[0], "pass2": tuning[1]}),
            "samples_per_frame": samples, "ms_per_frame": ms_max, "per_piece_fp32": per_piece,
-           "sortlast_gpu": sortlast,
+           "sortlast_gpu": sortlast, "amr_72_pieces": amr,
            "quality": quality, "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
            "gpu_launches": 2 * args.steps, "clocks": clk.summary()}
     vol.close()

@@ -94,7 +94,7 @@ typedef enum {
 typedef struct mboit_volume_s* mboit_volume;
 
 typedef struct {
-    int32_t kind;               /* mboit_volume_kind; MBOIT_GRID is implemented */
+    int32_t kind;               /* mboit_volume_kind; MBOIT_GRID and MBOIT_AMR are implemented */
     int32_t moment_set;         /* mboit_moment_set */
     int32_t storage;            /* mboit_storage */
     uint32_t flags;             /* MBOIT_FLAG_* */
@@ -117,6 +117,17 @@ typedef struct {
     float moment_bias;          /* mix amount of the bias vector (Alg. 3 "mix"), in [0, 1) */
     float overestimation;       /* weight of the sample's own depth (Alg. 3), paper: 0.3 */
     float absorbance_max;       /* ABSORBANCE_MAX_VALUE of Alg. 2, > 0 */
+    /* MBOIT_AMR (brick octree) only; `field` is then unused.  dims = finest
+     * cells per axis + 1 (the domain is [0, dims-1] in finest-cell units, all
+     * three equal); brick_log2 = log2 of a leaf's cells per side.  Leaf i of
+     * level L covers origin_i + [0, 2^(brick_log2 + max_level - L)) per axis
+     * and stores nv = 2^brick_log2 + 1 vertex values per side at its own
+     * resolution.  Leaves must not overlap; origins are multiples of
+     * 2^brick_log2.  Pieces are lists of leaf ids. */
+    const float* leaf_values;   /* DEVICE float32 [n_leaves][nv][nv][nv] ([z][y][x]), borrowed */
+    const int32_t* leaf_table;  /* HOST int32 [n_leaves][4]: origin x, y, z (finest cells), level; copied */
+    int32_t n_leaves;
+    int32_t max_level;          /* 0..10 */
 } mboit_volume_desc;
 
 typedef struct {

@@ -55,7 +55,8 @@ class mboit_volume_desc(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("field", ctypes.c_void_p), ("dims", ctypes.c_int32 * 3),
                 ("brick_log2", ctypes.c_int32), ("tf_rgba", ctypes.c_void_p), ("tf_range", ctypes.c_float * 2),
                 ("step", ctypes.c_float), ("moment_bias", ctypes.c_float), ("overestimation", ctypes.c_float),
-                ("absorbance_max", ctypes.c_float)]
+                ("absorbance_max", ctypes.c_float), ("leaf_values", ctypes.c_void_p), ("leaf_table", ctypes.c_void_p),
+                ("n_leaves", ctypes.c_int32), ("max_level", ctypes.c_int32)]
 
 
 class mboit_stats(ctypes.Structure):
@@ -278,29 +279,39 @@ def mboit_render_moments_noalloc(desc, views, moments, brick_selected=None, stre
 
 
 class Volume:
-    """A regular-grid volume on the current CUDA device, built from a scene
-    with ``field``, ``brick_log2``, ``piece_of_brick``, ``n_pieces``, ``tf``,
-    ``tf_range``, ``step``, ``moment_bias``, ``overestimation``,
-    ``absorbance_max``.  Keeps the device field tensor alive."""
+    """A volume on the current CUDA device built from a scene: a regular grid
+    (``field``, ``brick_log2``, ``piece_of_brick``) or a brick octree
+    (``leaves``, ``values``, ``max_level``, ``piece_of_leaf``), plus
+    ``n_pieces``, ``tf``, ``tf_range``, ``step``, ``moment_bias``,
+    ``overestimation``, ``absorbance_max``.  Keeps the device data alive."""
 
     def __init__(self, scene, field=None, flags=0):
         import torch
         load_library()
         self.scene = scene
-        self.field = field if field is not None else torch.from_numpy(np.ascontiguousarray(scene.field)).cuda()
+        amr = hasattr(scene, "leaves")
+        data = scene.values if amr else scene.field
+        self.field = field if field is not None else torch.from_numpy(np.ascontiguousarray(data)).cuda()
         tf = np.ascontiguousarray(scene.tf, dtype=np.float32)
         d = mboit_volume_desc()
-        d.kind, d.moment_set, d.storage, d.flags = MBOIT_GRID, MBOIT_POWER4, MBOIT_STORE_F32, flags
-        d.field = self.field.data_ptr()
-        nz, ny, nx = scene.field.shape
-        d.dims[:] = [nx, ny, nz]
+        d.kind = MBOIT_AMR if amr else MBOIT_GRID
+        d.moment_set, d.storage, d.flags = MBOIT_POWER4, MBOIT_STORE_F32, flags
+        if amr:
+            table = np.ascontiguousarray(scene.leaves, dtype=np.int32)
+            d.leaf_values, d.leaf_table = self.field.data_ptr(), table.ctypes.data
+            d.n_leaves, d.max_level = table.shape[0], scene.max_level
+            d.dims[:] = list(scene.dims)
+        else:
+            d.field = self.field.data_ptr()
+            nz, ny, nx = scene.field.shape
+            d.dims[:] = [nx, ny, nz]
         d.brick_log2 = scene.brick_log2
         d.tf_rgba = tf.ctypes.data
         d.tf_range[:] = [float(scene.tf_range[0]), float(scene.tf_range[1])]
         d.step, d.moment_bias = float(scene.step), float(scene.moment_bias)
         d.overestimation, d.absorbance_max = float(scene.overestimation), float(scene.absorbance_max)
         self.handle = mboit_create_volume(d)
-        pob = np.asarray(scene.piece_of_brick)
+        pob = np.asarray(scene.piece_of_leaf if amr else scene.piece_of_brick)
         for p in range(scene.n_pieces):
             mboit_add_piece(self.handle, np.nonzero(pob == p)[0].astype(np.int32))
 

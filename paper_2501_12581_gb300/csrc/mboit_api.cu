@@ -6,6 +6,7 @@
 // the kernels of mboit_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -56,7 +57,12 @@ struct GraphEntry {
 struct mboit_volume_s {
     int device = 0;
     mboit_volume_desc desc{};
+    int32_t kind = MBOIT_GRID;
     mb::GridD grid{};
+    mb::AmrD amr{};             // octree volumes: amr.g aliases the sampling parameters
+    int4* d_leaves = nullptr;
+    int32_t* d_fmap = nullptr;
+    std::vector<int32_t> leaf_table;
     int64_t nbricks = 0;
     size_t field_bytes = 0;
     float4* d_tf = nullptr;
@@ -232,11 +238,20 @@ size_t mboit_moment_image_bytes(int32_t width, int32_t height, int32_t moment_se
 mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) {
     g_err.clear();
     if (!d || !out) return fail(MBOIT_ERR_INVALID_ARG, "desc and out must be non-NULL");
-    if (d->kind != MBOIT_GRID) return fail(MBOIT_ERR_UNSUPPORTED, "only MBOIT_GRID volumes are implemented");
+    if (d->kind != MBOIT_GRID && d->kind != MBOIT_AMR)
+        return fail(MBOIT_ERR_UNSUPPORTED, "only MBOIT_GRID and MBOIT_AMR volumes are implemented");
+    const bool is_amr = d->kind == MBOIT_AMR;
     if (d->moment_set != MBOIT_POWER4) return fail(MBOIT_ERR_UNSUPPORTED, "only MBOIT_POWER4 moments are implemented");
     if (d->storage != MBOIT_STORE_F32) return fail(MBOIT_ERR_UNSUPPORTED, "only float32 moment storage is implemented");
     if (d->flags & ~(MBOIT_FLAG_RAW_SUM | MBOIT_FLAG_DETERMINISTIC)) return fail(MBOIT_ERR_INVALID_ARG, "unknown flag bits");
-    if (!d->field) return fail(MBOIT_ERR_INVALID_ARG, "field is NULL");
+    if (!is_amr && !d->field) return fail(MBOIT_ERR_INVALID_ARG, "field is NULL");
+    if (is_amr) {
+        if (!d->leaf_values || !d->leaf_table) return fail(MBOIT_ERR_INVALID_ARG, "leaf_values and leaf_table are required");
+        if (d->n_leaves < 1) return fail(MBOIT_ERR_INVALID_ARG, "n_leaves must be >= 1");
+        if (d->max_level < 0 || d->max_level > 10) return fail(MBOIT_ERR_INVALID_ARG, "max_level must be in [0, 10]");
+        if (d->dims[0] != d->dims[1] || d->dims[0] != d->dims[2])
+            return fail(MBOIT_ERR_INVALID_ARG, "octree domains are cubes: dims must be equal");
+    }
     for (int c = 0; c < 3; ++c)
         if (d->dims[c] < 2 || d->dims[c] > (1 << 20)) return fail(MBOIT_ERR_INVALID_ARG, "dims must be in [2, 2^20]");
     if (d->brick_log2 < 0 || d->brick_log2 > 7) return fail(MBOIT_ERR_INVALID_ARG, "brick_log2 must be in [0, 7]");
@@ -261,15 +276,48 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
         const double sigma = -std::log1p(-(double)e[3]);
         tf[j] = make_float4(e[0], e[1], e[2], (float)(sigma * (double)d->step));
     }
+    // octree: leaf table checks and the finest-brick -> leaf map (host)
+    std::vector<int32_t> fmap;
+    int64_t fdim = 0;
+    if (is_amr) {
+        const int64_t D = d->dims[0] - 1;
+        const int64_t fb = int64_t(1) << d->brick_log2;
+        fdim = (D + fb - 1) / fb;
+        if (fdim * fdim * fdim > (int64_t(1) << 31)) return fail(MBOIT_ERR_INVALID_ARG, "octree domain too large");
+        fmap.assign((size_t)(fdim * fdim * fdim), -1);
+        for (int32_t l = 0; l < d->n_leaves; ++l) {
+            const int32_t* L = d->leaf_table + 4 * (size_t)l;
+            if (L[3] < 0 || L[3] > d->max_level)
+                return fail(MBOIT_ERR_INVALID_ARG, "leaf " + std::to_string(l) + ": level out of range");
+            const int64_t nb = int64_t(1) << (d->max_level - L[3]);
+            int64_t b0[3];
+            for (int c = 0; c < 3; ++c) {
+                if (L[c] < 0 || (L[c] % fb) != 0)
+                    return fail(MBOIT_ERR_INVALID_ARG, "leaf " + std::to_string(l) + ": origin not on the brick lattice");
+                b0[c] = L[c] / fb;
+                if (b0[c] + nb > fdim) return fail(MBOIT_ERR_INVALID_ARG, "leaf " + std::to_string(l) + " leaves the domain");
+            }
+            for (int64_t z = b0[2]; z < b0[2] + nb; ++z)
+                for (int64_t y = b0[1]; y < b0[1] + nb; ++y)
+                    for (int64_t x = b0[0]; x < b0[0] + nb; ++x) {
+                        int32_t& m = fmap[(size_t)((z * fdim + y) * fdim + x)];
+                        if (m >= 0)
+                            return fail(MBOIT_ERR_INVALID_ARG, "leaves " + std::to_string(m) + " and " +
+                                                                   std::to_string(l) + " overlap");
+                        m = l;
+                    }
+        }
+    }
     int dev = 0;
     MB_CUDA(cudaGetDevice(&dev));
     cudaPointerAttributes attr{};
-    if (cudaPointerGetAttributes(&attr, d->field) != cudaSuccess ||
+    const void* data_ptr = is_amr ? (const void*)d->leaf_values : (const void*)d->field;
+    if (cudaPointerGetAttributes(&attr, data_ptr) != cudaSuccess ||
         (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
         cudaGetLastError();
-        return fail(MBOIT_ERR_INVALID_ARG, "field must be a device pointer");
+        return fail(MBOIT_ERR_INVALID_ARG, is_amr ? "leaf_values must be a device pointer" : "field must be a device pointer");
     }
-    if (attr.device != dev) return fail(MBOIT_ERR_INVALID_ARG, "field lives on another device than the current one");
+    if (attr.device != dev) return fail(MBOIT_ERR_INVALID_ARG, "volume data lives on another device than the current one");
 
     mboit_volume v = new (std::nothrow) mboit_volume_s();
     if (!v) return fail(MBOIT_ERR_OUT_OF_MEMORY, "host allocation failed");
@@ -302,6 +350,15 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
     g.flags = d->flags;
     v->nbricks = (int64_t)g.nbx * g.nby * g.nbz;
     v->field_bytes = (size_t)g.nx * g.ny * g.nz * sizeof(float);
+    v->kind = d->kind;
+    if (is_amr) {
+        g.field = nullptr;
+        v->nbricks = d->n_leaves;  // the units of an octree are its leaves
+        const int nv = (1 << d->brick_log2) + 1;
+        v->field_bytes = (size_t)d->n_leaves * nv * nv * nv * sizeof(float);
+        v->leaf_table.assign(d->leaf_table, d->leaf_table + 4 * (size_t)d->n_leaves);
+        v->desc.leaf_table = nullptr;
+    }
     v->pob.assign((size_t)v->nbricks, -1);
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&v->d_tf, 256 * sizeof(float4));
@@ -311,6 +368,21 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
     if (e == cudaSuccess) e = cudaMemcpy(v->d_tf, tf.data(), 256 * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(v->d_pob, 0xff, (size_t)v->nbricks * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(v->d_ctr, 0, sizeof(mb::Counters));
+    if (e == cudaSuccess && is_amr) {
+        e = cudaMalloc(&v->d_leaves, (size_t)d->n_leaves * sizeof(int4));
+        if (e == cudaSuccess) e = cudaMalloc(&v->d_fmap, fmap.size() * sizeof(int32_t));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(v->d_leaves, d->leaf_table, (size_t)d->n_leaves * sizeof(int4), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(v->d_fmap, fmap.data(), fmap.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+        v->amr.g = g;
+        v->amr.values = d->leaf_values;
+        v->amr.leaves = v->d_leaves;
+        v->amr.fmap = v->d_fmap;
+        v->amr.fdim = (int32_t)fdim;
+        v->amr.nv = (1 << d->brick_log2) + 1;
+        v->amr.max_level = d->max_level;
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&v->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = mb::prepare_kernels();
     if (e != cudaSuccess) {
@@ -333,6 +405,8 @@ mboit_status mboit_destroy_volume(mboit_volume v) {
         drop_graphs(v);
         if (v->cap_stream) cudaStreamDestroy(v->cap_stream);
         cudaFree(v->d_tf);
+        cudaFree(v->d_leaves);
+        cudaFree(v->d_fmap);
         cudaFree(v->d_pob);
         cudaFree(v->d_sel);
         cudaFree(v->d_ctr);
@@ -389,10 +463,26 @@ mboit_status mboit_add_piece(mboit_volume v, const int32_t* ids, int64_t n, int3
     const int B = 1 << g.brick_log2;
     const float hi[3] = {g.hx, g.hy, g.hz};
     mb::PieceBox box;
-    for (int c = 0; c < 3; ++c) {
-        box.lo[c] = (float)(bmin[c] * B);
-        const float top = (float)((bmax[c] + 1) * B);
-        box.hi[c] = top < hi[c] ? top : hi[c];
+    if (v->kind == MBOIT_AMR) {
+        // union of the leaves' boxes
+        for (int c = 0; c < 3; ++c) {
+            box.lo[c] = 3.0e38f;
+            box.hi[c] = 0.0f;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            const int32_t* L = &v->leaf_table[4 * (size_t)h[i]];
+            const float size = (float)(B << (v->desc.max_level - L[3]));
+            for (int c = 0; c < 3; ++c) {
+                box.lo[c] = std::min(box.lo[c], (float)L[c]);
+                box.hi[c] = std::max(box.hi[c], std::min((float)L[c] + size, hi[c]));
+            }
+        }
+    } else {
+        for (int c = 0; c < 3; ++c) {
+            box.lo[c] = (float)(bmin[c] * B);
+            const float top = (float)((bmax[c] + 1) * B);
+            box.hi[c] = top < hi[c] ? top : hi[c];
+        }
     }
     v->boxes.push_back(box);
     v->owned += n;
@@ -418,13 +508,22 @@ mboit_status mboit_render_moments(mboit_volume v, const mboit_view* views, int32
     if ((st = select_pieces(v, pieces, n_pieces, list, &mask)) != MBOIT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->samples[0], 0, sizeof(unsigned long long), s));
+    const bool amr = v->kind == MBOIT_AMR;
     if (mode == MBOIT_MOMENTS_REDUCED) {
-        MB_CUDA(mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1));
+        if (amr)
+            MB_CUDA(mb::launch_pass1_amr(v->amr, v->d_tf, mask, vt, moments, v->d_ctr, s));
+        else
+            MB_CUDA(mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1));
     } else {
         const int32_t slots = (int32_t)list.size();
-        for (int32_t j = 0; j < slots; ++j)
-            MB_CUDA(mb::launch_pass1_piece(v->grid, v->d_tf, v->d_pob, list[j], v->boxes[list[j]], vt, j, slots, moments,
-                                           v->d_ctr, s));
+        for (int32_t j = 0; j < slots; ++j) {
+            if (amr)
+                MB_CUDA(mb::launch_pass1_piece(v->amr, v->d_tf, v->d_pob, list[j], v->boxes[list[j]], vt, j, slots,
+                                               moments, v->d_ctr, s));
+            else
+                MB_CUDA(mb::launch_pass1_piece(v->grid, v->d_tf, v->d_pob, list[j], v->boxes[list[j]], vt, j, slots,
+                                               moments, v->d_ctr, s));
+        }
     }
     return MBOIT_OK;
 }
@@ -447,15 +546,23 @@ mboit_status mboit_reconstruct_blend(mboit_volume v, const mboit_view* views, in
     if ((st = select_pieces(v, pieces, n_pieces, list, &mask)) != MBOIT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->samples[1], 0, 2 * sizeof(unsigned long long), s));
+    const bool amr = v->kind == MBOIT_AMR;
     if (mode == MBOIT_COLOR_PER_PIECE) {
         const int32_t slots = (int32_t)list.size();
-        for (int32_t j = 0; j < slots; ++j)
-            MB_CUDA(mb::launch_pass2_piece(v->grid, v->d_tf, v->d_pob, list[j], v->boxes[list[j]], vt, j, slots,
-                                           global_moments, color, v->d_ctr, s));
+        for (int32_t j = 0; j < slots; ++j) {
+            if (amr)
+                MB_CUDA(mb::launch_pass2_piece(v->amr, v->d_tf, v->d_pob, list[j], v->boxes[list[j]], vt, j, slots,
+                                               global_moments, color, v->d_ctr, s));
+            else
+                MB_CUDA(mb::launch_pass2_piece(v->grid, v->d_tf, v->d_pob, list[j], v->boxes[list[j]], vt, j, slots,
+                                               global_moments, color, v->d_ctr, s));
+        }
     } else {
-        MB_CUDA(mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, global_moments, color,
-                                       mode == MBOIT_COLOR_RESOLVED ? mb::kColorResolved : mb::kColorReduced, v->d_ctr,
-                                       s, v->tune2));
+        const int32_t md = mode == MBOIT_COLOR_RESOLVED ? mb::kColorResolved : mb::kColorReduced;
+        if (amr)
+            MB_CUDA(mb::launch_pass2_amr(v->amr, v->d_tf, mask, vt, global_moments, color, md, v->d_ctr, s));
+        else
+            MB_CUDA(mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, global_moments, color, md, v->d_ctr, s, v->tune2));
     }
     return MBOIT_OK;
 }
@@ -517,11 +624,15 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
         cudaStream_t cs = v->cap_stream;
         MB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemsetAsync(&v->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), cs);
+        const bool amr = v->kind == MBOIT_AMR;
         if (e == cudaSuccess)
-            e = mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, cs, v->tune1);
+            e = amr ? mb::launch_pass1_amr(v->amr, v->d_tf, mask, vt, moments_scratch, v->d_ctr, cs)
+                    : mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, cs, v->tune1);
         if (e == cudaSuccess)
-            e = mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba, mb::kColorResolved, v->d_ctr, cs,
-                                       v->tune2);
+            e = amr ? mb::launch_pass2_amr(v->amr, v->d_tf, mask, vt, moments_scratch, rgba, mb::kColorResolved,
+                                           v->d_ctr, cs)
+                    : mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba, mb::kColorResolved,
+                                             v->d_ctr, cs, v->tune2);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -550,7 +661,8 @@ mboit_status mboit_render_frame_host(mboit_volume v, const float* field_host, co
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     {
         DeviceGuard dg(v->device);
-        MB_CUDA(cudaMemcpyAsync(const_cast<float*>(v->grid.field), field_host, v->field_bytes, cudaMemcpyHostToDevice, s));
+        float* dst = const_cast<float*>(v->kind == MBOIT_AMR ? v->amr.values : v->grid.field);
+        MB_CUDA(cudaMemcpyAsync(dst, field_host, v->field_bytes, cudaMemcpyHostToDevice, s));
     }
     if ((st = mboit_render_frame(v, views, n_views, moments_scratch, rgba_device, stream)) != MBOIT_OK) return st;
     int64_t floats = 0;
@@ -616,9 +728,15 @@ mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int3
     MB_CUDA(ensure_capacity(v->sl_bsum, v->cap_bsum, nb));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->segments, 0, sizeof(unsigned long long) + sizeof(int32_t), s));
-    for (int32_t p = 0; p < K; ++p)
-        MB_CUDA(mb::launch_sortlast_march(false, v->grid, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts,
-                                          nullptr, nullptr, nullptr, s));
+    const bool amr = v->kind == MBOIT_AMR;
+    for (int32_t p = 0; p < K; ++p) {
+        if (amr)
+            MB_CUDA(mb::launch_sortlast_march(false, v->amr, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts,
+                                              nullptr, nullptr, nullptr, s));
+        else
+            MB_CUDA(mb::launch_sortlast_march(false, v->grid, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts,
+                                              nullptr, nullptr, nullptr, s));
+    }
     MB_CUDA(mb::launch_sortlast_offsets(vt, K, v->sl_counts, v->sl_totals, v->sl_base, v->sl_bsum, v->sl_starts,
                                         total_px, s));
     int64_t total = 0;
@@ -626,9 +744,14 @@ mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int3
     MB_CUDA(cudaStreamSynchronize(s));
     MB_CUDA(ensure_capacity(v->sl_key, v->cap_seg, (size_t)total));
     MB_CUDA(ensure_capacity(v->sl_col, v->cap_col, (size_t)total));
-    for (int32_t p = 0; p < K; ++p)
-        MB_CUDA(mb::launch_sortlast_march(true, v->grid, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts,
-                                          v->sl_starts, v->sl_key, v->sl_col, s));
+    for (int32_t p = 0; p < K; ++p) {
+        if (amr)
+            MB_CUDA(mb::launch_sortlast_march(true, v->amr, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts,
+                                              v->sl_starts, v->sl_key, v->sl_col, s));
+        else
+            MB_CUDA(mb::launch_sortlast_march(true, v->grid, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts,
+                                              v->sl_starts, v->sl_key, v->sl_col, s));
+    }
     MB_CUDA(mb::launch_sortlast_blend(v->sl_base, v->sl_key, v->sl_col, rgba, total_px, v->d_ctr, s));
     if (segments_per_pixel)
         MB_CUDA(cudaMemcpyAsync(segments_per_pixel, v->sl_totals, (size_t)total_px * sizeof(int32_t),
@@ -640,6 +763,8 @@ mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int3
 mboit_status mboit_set_tuning(mboit_volume v, int32_t pass1, int32_t pass2) {
     g_err.clear();
     if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
+    if (v->kind == MBOIT_AMR && (pass1 != 0 || pass2 != 0))
+        return fail(MBOIT_ERR_INVALID_ARG, "octree volumes have one configuration (0)");
     if (!mb::stage_config_eligible(v->grid, pass1) || !mb::stage_config_eligible(v->grid, pass2))
         return fail(MBOIT_ERR_INVALID_ARG, "tuning must be in [0, " + std::to_string(mb::kNumStageConfigs - 1) +
                                                "]; 2-4 need dims[0] % 4 == 0 and a 16-byte aligned field");
@@ -663,6 +788,10 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
     std::vector<int32_t> list;
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, nullptr, 0, list, &mask)) != MBOIT_OK) return st;
+    if (v->kind == MBOIT_AMR) {  // one configuration only
+        if (chosen) chosen[0] = chosen[1] = 0;
+        return MBOIT_OK;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     MB_CUDA(cudaEventCreate(&e0));

@@ -46,6 +46,17 @@ struct PieceBox {
 
 enum ColorMode : int32_t { kColorPerPiece = 0, kColorReduced = 1, kColorResolved = 2 };
 
+// Brick octree (AMR) as the kernels see it.  `g` carries the domain
+// [0, hx) x [0, hy) x [0, hz) in finest cells and every sampling and
+// transfer-function parameter (its field/brick members are unused).
+struct AmrD {
+    GridD g;
+    const float* values;    // [n_leaves][nv^3] vertex values, [z][y][x]
+    const int4* leaves;     // origin x, y, z (finest cells), level
+    const int32_t* fmap;    // [fdim^3] finest brick (2^brick_log2 cells) -> leaf, -1 none
+    int32_t fdim, nv, max_level, pad;
+};
+
 // Number of shared-memory window configurations of the fused passes (the
 // autotuner's choices).  Configurations 2-4 use 16-byte loads and need
 // nx % 4 == 0 and a 16-byte aligned field; 0 and 1 work everywhere.
@@ -81,6 +92,21 @@ cudaError_t launch_sortlast_offsets(const ViewTable& vt, int32_t n_slots, const 
                                    int64_t* base, int64_t* bsum, int64_t* starts, int64_t total_px, cudaStream_t s);
 cudaError_t launch_sortlast_blend(const int64_t* base, int32_t* seg_key, float4* seg_col, float* rgba, int64_t total_px,
                                   Counters* ctr, cudaStream_t s);
+// Octree versions of the passes (direct gathers; same output layouts).
+cudaError_t launch_pass1_amr(const AmrD& a, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
+                             void* moments, Counters* ctr, cudaStream_t s);
+cudaError_t launch_pass2_amr(const AmrD& a, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
+                             const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s);
+cudaError_t launch_pass1_piece(const AmrD& a, const float4* tf, const int32_t* piece_of_unit, int32_t piece,
+                               const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
+                               void* moments, Counters* ctr, cudaStream_t s);
+cudaError_t launch_pass2_piece(const AmrD& a, const float4* tf, const int32_t* piece_of_unit, int32_t piece,
+                               const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
+                               const void* moments, float* color, Counters* ctr, cudaStream_t s);
+cudaError_t launch_sortlast_march(bool fill, const AmrD& a, const float4* tf, const int32_t* piece_of_unit,
+                                  int32_t piece, const PieceBox& box, const ViewTable& vt, int32_t slot,
+                                  int32_t n_slots, int32_t* counts, const int64_t* starts, int32_t* seg_key,
+                                  float4* seg_col, cudaStream_t s);
 // Image-space reductions.
 cudaError_t launch_moments_sum(const ViewTable& vt, int32_t n_inputs, const void* in, void* out, cudaStream_t s);
 cudaError_t launch_color_resolve(const ViewTable& vt, int32_t n_inputs, const float* in, float* out,

@@ -441,18 +441,73 @@ __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ Gri
 // ------------------------------------------------------------------------
 // plain per-piece passes
 
-// Next lattice index worth testing after point k fell in a brick the piece
-// does not own: the ray's exit from that brick, pulled back by a padding
-// that covers float32 position rounding, and by one lattice step.
-__device__ __forceinline__ int skip_brick(const GridD& g, const float o[3], const float d[3], float t, int k) {
+// Sampling units: the bricks of a grid or the leaves of an octree.  For a
+// point inside the domain: its unit (-1: none), the trilinear value there,
+// and the unit's box (for skipping units a piece does not own).
+__device__ __forceinline__ const GridD& common(const GridD& g) { return g; }
+__device__ __forceinline__ const GridD& common(const AmrD& a) { return a.g; }
+
+__device__ __forceinline__ int unit_of(const GridD& g, const float p[3]) {
+    const int ix = (int)p[0], iy = (int)p[1], iz = (int)p[2];
+    return ((iz >> g.brick_log2) * g.nby + (iy >> g.brick_log2)) * g.nbx + (ix >> g.brick_log2);
+}
+
+__device__ __forceinline__ float unit_value(const GridD& g, const float p[3], int) {
+    const int ix = (int)p[0], iy = (int)p[1], iz = (int)p[2];
+    const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * (size_t)g.ny;
+    const float* __restrict__ c = g.field + (size_t)iz * sz + (size_t)iy * sy + (size_t)ix;
+    return trilinear8(__ldg(c), __ldg(c + 1), __ldg(c + sy), __ldg(c + sy + 1), __ldg(c + sz), __ldg(c + sz + 1),
+                      __ldg(c + sz + sy), __ldg(c + sz + sy + 1), p[0] - (float)ix, p[1] - (float)iy, p[2] - (float)iz);
+}
+
+__device__ __forceinline__ void unit_box(const GridD& g, const float p[3], int, float lo[3], float& size) {
+    size = (float)(1 << g.brick_log2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) lo[c] = floorf(p[c] / size) * size;
+}
+
+__device__ __forceinline__ int unit_of(const AmrD& a, const float p[3]) {
+    const int bl = a.g.brick_log2;
+    const int fx = (int)p[0] >> bl, fy = (int)p[1] >> bl, fz = (int)p[2] >> bl;
+    return __ldg(a.fmap + ((size_t)fz * a.fdim + fy) * (size_t)a.fdim + fx);
+}
+
+// Local coordinates (p - origin) / h are exact in float32 (h a power of two,
+// |p - origin| below the leaf size), so cells match the oracle's.
+__device__ __forceinline__ float unit_value(const AmrD& a, const float p[3], int leaf) {
+    const int4 L = __ldg(a.leaves + leaf);
+    const float inv_h = __int_as_float((127 - (a.max_level - L.w)) << 23);  // 2^-(max_level - level)
+    const float qx = (p[0] - (float)L.x) * inv_h, qy = (p[1] - (float)L.y) * inv_h, qz = (p[2] - (float)L.z) * inv_h;
+    const int cx = min((int)qx, a.nv - 2), cy = min((int)qy, a.nv - 2), cz = min((int)qz, a.nv - 2);
+    const int nv = a.nv;
+    const float* __restrict__ c = a.values + (size_t)leaf * nv * nv * nv + (cz * nv + cy) * nv + cx;
+    const int sy = nv, sz = nv * nv;
+    return trilinear8(__ldg(c), __ldg(c + 1), __ldg(c + sy), __ldg(c + sy + 1), __ldg(c + sz), __ldg(c + sz + 1),
+                      __ldg(c + sz + sy), __ldg(c + sz + sy + 1), qx - (float)cx, qy - (float)cy, qz - (float)cz);
+}
+
+__device__ __forceinline__ void unit_box(const AmrD& a, const float[3], int leaf, float lo[3], float& size) {
+    const int4 L = __ldg(a.leaves + leaf);
+    size = (float)((1 << a.g.brick_log2) << (a.max_level - L.w));
+    lo[0] = (float)L.x;
+    lo[1] = (float)L.y;
+    lo[2] = (float)L.z;
+}
+
+// Next lattice index worth testing after point k fell in a unit the piece
+// does not own: the ray's exit from that unit's box, pulled back by a
+// padding that covers float32 position rounding, and by one lattice step.
+template <class V>
+__device__ __forceinline__ int skip_unit(const V& vol, int unit, const float o[3], const float d[3], float t, int k) {
+    const GridD& g = common(vol);
     const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
-    const float B = (float)(1 << g.brick_log2);
+    float lo[3], size;
+    unit_box(vol, p, unit, lo, size);
     float t_exit = 3.0e38f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         if (d[c] == 0.0f) continue;
-        const float cell0 = floorf(p[c] / B) * B;
-        const float face = d[c] > 0.0f ? cell0 + B : cell0;
+        const float face = d[c] > 0.0f ? lo[c] + size : lo[c];
         const float inv = 1.0f / d[c];
         const float tc = (face - o[c]) * inv;
         const float pad = (fabsf(o[c]) + fabsf(face) + 1.0f) * 3.814697265625e-06f * fabsf(inv);
@@ -464,24 +519,29 @@ __device__ __forceinline__ int skip_brick(const GridD& g, const float o[3], cons
 }
 
 // One owned sample of `piece` at lattice index k, or the next index to try.
-__device__ __forceinline__ bool piece_sample(const GridD& g, const int32_t* __restrict__ pob, int piece, float t,
+template <class V>
+__device__ __forceinline__ bool piece_sample(const V& vol, const int32_t* __restrict__ pou, int piece, float t,
                                              const float o[3], const float d[3], int k, float& val, int& k_next) {
+    const GridD& g = common(vol);
     k_next = k + 1;
-    const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
-    if (!(p0 >= 0.0f && p0 < g.hx && p1 >= 0.0f && p1 < g.hy && p2 >= 0.0f && p2 < g.hz)) return false;
-    const int ix = (int)p0, iy = (int)p1, iz = (int)p2;
-    const int b = ((iz >> g.brick_log2) * g.nby + (iy >> g.brick_log2)) * g.nbx + (ix >> g.brick_log2);
-    if (__ldg(pob + b) != piece) {
-        k_next = skip_brick(g, o, d, t, k);
+    const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+    if (!(p[0] >= 0.0f && p[0] < g.hx && p[1] >= 0.0f && p[1] < g.hy && p[2] >= 0.0f && p[2] < g.hz)) return false;
+    const int u = unit_of(vol, p);
+    if (u < 0) return false;
+    if (__ldg(pou + u) != piece) {
+        k_next = skip_unit(vol, u, o, d, t, k);
         return false;
     }
-    return field_sample<false>(g, nullptr, t, o, d, val);
+    val = unit_value(vol, p, u);
+    return true;
 }
 
-__global__ void __launch_bounds__(128) k_pass1_piece(const __grid_constant__ GridD g, const float4* __restrict__ tf,
+template <class V>
+__global__ void __launch_bounds__(128) k_pass1_piece(const __grid_constant__ V vol, const float4* __restrict__ tf,
                                                      const int32_t* __restrict__ pob, int piece, const __grid_constant__ PieceBox box,
                                                      const __grid_constant__ ViewTable vt, int slot, int n_slots,
                                                      char* __restrict__ moments, Counters* __restrict__ ctr) {
+    const GridD& g = common(vol);
     __shared__ float s_sig[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_sig[i] = tf[i].w;
     __syncthreads();
@@ -505,7 +565,7 @@ __global__ void __launch_bounds__(128) k_pass1_piece(const __grid_constant__ Gri
                 const float t = lattice_t(k, g.step);
                 float val;
                 int kn;
-                if (!piece_sample(g, pob, piece, t, o, d, k, val, kn)) {
+                if (!piece_sample(vol, pob, piece, t, o, d, k, val, kn)) {
                     k = kn;
                     continue;
                 }
@@ -533,11 +593,13 @@ __global__ void __launch_bounds__(128) k_pass1_piece(const __grid_constant__ Gri
     warp_add_u64(&ctr->samples[0], n);
 }
 
-__global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ GridD g, const float4* __restrict__ tf,
+template <class V>
+__global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ V vol, const float4* __restrict__ tf,
                                                      const int32_t* __restrict__ pob, int piece, const __grid_constant__ PieceBox box,
                                                      const __grid_constant__ ViewTable vt, int slot, int n_slots,
                                                      const char* __restrict__ moments, float* __restrict__ color,
                                                      Counters* __restrict__ ctr) {
+    const GridD& g = common(vol);
     __shared__ float4 s_tf[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = tf[i];
     __syncthreads();
@@ -566,7 +628,7 @@ __global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ Gri
                 const float t = lattice_t(k, g.step);
                 float val;
                 int kn;
-                if (!piece_sample(g, pob, piece, t, o, d, k, val, kn)) {
+                if (!piece_sample(vol, pob, piece, t, o, d, k, val, kn)) {
                     k = kn;
                     continue;
                 }
@@ -592,6 +654,89 @@ __global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ Gri
 }
 
 // ------------------------------------------------------------------------
+// fused, persistent passes over a brick octree (direct gathers): the leaf of
+// each lattice point comes from the finest-brick map, its value from the
+// leaf's own vertex block
+
+template <bool kSel, class Body>
+__device__ __forceinline__ void march_amr(const AmrD& a, const uint8_t* __restrict__ sel, const float o[3],
+                                          const float d[3], int k0, int k1, Body& body) {
+    const GridD& g = a.g;
+    if (k0 > k1) return;
+    const float tz = lattice_t(k1, g.step);
+    for (float t = lattice_t(k0, g.step); t <= tz; t += g.step) {
+        const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+        const int u = unit_of(a, p);
+        if (u < 0) continue;
+        if (kSel && !__ldg(sel + u)) continue;
+        body(t, unit_value(a, p, u));
+    }
+}
+
+template <bool kSel>
+__global__ void __launch_bounds__(256) k_pass1_amr(const __grid_constant__ AmrD a, const float4* __restrict__ tf,
+                                                   const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
+                                                   char* __restrict__ moments, Counters* __restrict__ ctr) {
+    __shared__ float2 s_sig[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const float s0 = tf[i].w;
+        s_sig[i] = make_float2(s0, i < 255 ? tf[i + 1].w - s0 : 0.0f);
+    }
+    __syncthreads();
+    const GridD& g = a.g;
+    int vi, px, py;
+    while (next_tile(vt, &ctr->tile_next[0], vi, px, py)) {
+        const ViewSlot& S = vt.s[vi];
+        const bool valid = px < S.v.width && py < S.v.height;
+        float o[3], d[3];
+        int k0, k1;
+        ray_range(g, S.v, valid, px, py, o, d, k0, k1);
+        MomentBody body{s_sig, g.tf_scale, g.tf_bias, g.absorbance_max, S.v.warp_a, S.v.warp_b};
+        march_amr<kSel>(a, sel, o, d, k0, k1, body);
+        if (valid)
+            store_moments(moments, S, S.moment_off, py * S.v.width + px, body.m0, body.m1, body.m2, body.m3, body.m4);
+        warp_add_u64(&ctr->samples[0], body.n);
+    }
+}
+
+template <bool kSel>
+__global__ void __launch_bounds__(256) k_pass2_amr(const __grid_constant__ AmrD a, const float4* __restrict__ tf,
+                                                   const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
+                                                   const char* __restrict__ moments, float* __restrict__ color, int mode,
+                                                   Counters* __restrict__ ctr) {
+    __shared__ float4 s_tf[512];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const float4 e0 = tf[i], e1 = i < 255 ? tf[i + 1] : tf[i];
+        s_tf[2 * i] = e0;
+        s_tf[2 * i + 1] = make_float4(e1.x - e0.x, e1.y - e0.y, e1.z - e0.z, e1.w - e0.w);
+    }
+    __syncthreads();
+    const GridD& g = a.g;
+    const bool raw = (g.flags & 1u) != 0;
+    int vi, px, py;
+    while (next_tile(vt, &ctr->tile_next[1], vi, px, py)) {
+        const ViewSlot& S = vt.s[vi];
+        const bool valid = px < S.v.width && py < S.v.height;
+        const int pix = valid ? py * S.v.width + px : 0;
+        float m[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (valid) load_moments(moments, S, S.moment_off, pix, m);
+        BlendBody body{s_tf, make_frame(m, g.moment_bias, g.bias_vector), g.tf_scale, g.tf_bias, g.absorbance_max,
+                       S.v.warp_a, S.v.warp_b, g.overestimation};
+        if (valid && (body.F.kind == kFrameOneAtom || body.F.kind == kFrameTwoAtoms)) atomicAdd(&ctr->singular, 1ull);
+        float o[3], d[3];
+        int k0, k1;
+        ray_range(g, S.v, valid, px, py, o, d, k0, k1);
+        march_amr<kSel>(a, sel, o, d, k0, k1, body);
+        if (valid) {
+            float4* out = reinterpret_cast<float4*>(color + S.color_off) + pix;
+            *out = mode == kColorResolved ? resolve_pixel(body.C, m[0], make_float4(0.0f, 0.0f, 0.0f, 0.0f), raw)
+                                          : body.C;
+        }
+        warp_add_u64(&ctr->samples[1], body.n);
+    }
+}
+
+// ------------------------------------------------------------------------
 // GPU exact sort-last baseline (the segment-layer compositor of Sec. 5).
 // Every piece, like a rank, turns each maximal run of consecutive lattice
 // points it owns into one segment (front-to-back "over" inside the run:
@@ -600,13 +745,14 @@ __global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ Gri
 // front to back.  Counting and filling are separate marches so the segment
 // buffer can be sized exactly.
 
-template <bool kFill>
-__global__ void __launch_bounds__(128) k_sortlast_piece(const __grid_constant__ GridD g, const float4* __restrict__ tf,
+template <class V, bool kFill>
+__global__ void __launch_bounds__(128) k_sortlast_piece(const __grid_constant__ V vol, const float4* __restrict__ tf,
                                                         const int32_t* __restrict__ pob, int piece,
                                                         const __grid_constant__ PieceBox box,
                                                         const __grid_constant__ ViewTable vt, int slot, int n_slots,
                                                         int32_t* __restrict__ counts, const int64_t* __restrict__ starts,
                                                         int32_t* __restrict__ seg_key, float4* __restrict__ seg_col) {
+    const GridD& g = common(vol);
     __shared__ float4 s_tf[256];
     if (kFill) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = tf[i];
@@ -637,7 +783,7 @@ __global__ void __launch_bounds__(128) k_sortlast_piece(const __grid_constant__ 
             const float t = lattice_t(k, g.step);
             float val;
             int kn;
-            if (!piece_sample(g, pob, piece, t, o, d, k, val, kn)) {
+            if (!piece_sample(vol, pob, piece, t, o, d, k, val, kn)) {
                 k = kn;
                 continue;
             }
@@ -935,9 +1081,13 @@ bool stage_config_eligible(const GridD& g, int cfg) {
 cudaError_t prepare_kernels() {
     // Loads every kernel and fills the occupancy cache, so that no module
     // loading happens later inside a stream capture.
-    const void* fns[] = {(const void*)k_pass1_piece,        (const void*)k_pass2_piece,
+    const void* fns[] = {(const void*)k_pass1_piece<GridD>, (const void*)k_pass2_piece<GridD>,
+                         (const void*)k_pass1_piece<AmrD>, (const void*)k_pass2_piece<AmrD>,
+                         (const void*)k_pass1_amr<true>, (const void*)k_pass1_amr<false>,
+                         (const void*)k_pass2_amr<true>, (const void*)k_pass2_amr<false>,
                          (const void*)k_moments_sum,        (const void*)k_color_resolve,
-                         (const void*)k_sortlast_piece<true>, (const void*)k_sortlast_piece<false>,
+                         (const void*)k_sortlast_piece<GridD, true>, (const void*)k_sortlast_piece<GridD, false>,
+                         (const void*)k_sortlast_piece<AmrD, true>, (const void*)k_sortlast_piece<AmrD, false>,
                          (const void*)k_sortlast_totals,    (const void*)k_sortlast_starts,
                          (const void*)k_scan_blocks,        (const void*)k_scan_sums,
                          (const void*)k_scan_add,           (const void*)k_sortlast_blend};
@@ -955,6 +1105,10 @@ cudaError_t prepare_kernels() {
             persistent_blocks(pass1_fn(cfg, sel), 256, 0);
             persistent_blocks(pass2_fn(cfg, sel), 256, 0);
         }
+    persistent_blocks((const void*)k_pass1_amr<true>, 256, 0);
+    persistent_blocks((const void*)k_pass1_amr<false>, 256, 0);
+    persistent_blocks((const void*)k_pass2_amr<true>, 256, 0);
+    persistent_blocks((const void*)k_pass2_amr<false>, 256, 0);
     return cudaGetLastError();
 }
 
@@ -987,7 +1141,7 @@ cudaError_t launch_pass1_piece(const GridD& g, const float4* tf, const int32_t* 
                                const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
                                void* moments, Counters* ctr, cudaStream_t s) {
     const int blocks = (vt.total_tiles + 3) / 4;
-    k_pass1_piece<<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, static_cast<char*>(moments), ctr);
+    k_pass1_piece<GridD><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, static_cast<char*>(moments), ctr);
     return cudaGetLastError();
 }
 
@@ -995,7 +1149,7 @@ cudaError_t launch_pass2_piece(const GridD& g, const float4* tf, const int32_t* 
                                const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
                                const void* moments, float* color, Counters* ctr, cudaStream_t s) {
     const int blocks = (vt.total_tiles + 3) / 4;
-    k_pass2_piece<<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots,
+    k_pass2_piece<GridD><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots,
                                          static_cast<const char*>(moments), color, ctr);
     return cudaGetLastError();
 }
@@ -1033,10 +1187,10 @@ cudaError_t launch_sortlast_march(bool fill, const GridD& g, const float4* tf, c
                                   cudaStream_t s) {
     const int blocks = (vt.total_tiles + 3) / 4;
     if (fill)
-        k_sortlast_piece<true><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, counts, starts, seg_key,
+        k_sortlast_piece<GridD, true><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, counts, starts, seg_key,
                                                       seg_col);
     else
-        k_sortlast_piece<false><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, counts, starts,
+        k_sortlast_piece<GridD, false><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, counts, starts,
                                                        seg_key, seg_col);
     return cudaGetLastError();
 }
@@ -1057,6 +1211,60 @@ cudaError_t launch_sortlast_blend(const int64_t* base, int32_t* seg_key, float4*
                                   Counters* ctr, cudaStream_t s) {
     const int grid = (int)((total_px + 127) / 128 < 16384 ? (total_px + 127) / 128 : 16384);
     k_sortlast_blend<<<grid, 128, 0, s>>>(base, seg_key, seg_col, rgba, total_px, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass1_amr(const AmrD& a, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
+                             void* moments, Counters* ctr, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const void* fn = unit_sel ? (const void*)k_pass1_amr<true> : (const void*)k_pass1_amr<false>;
+    char* m = static_cast<char*>(moments);
+    void* args[] = {(void*)&a, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&m, (void*)&ctr};
+    return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
+}
+
+cudaError_t launch_pass2_amr(const AmrD& a, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
+                             const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&ctr->tile_next[1], 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const void* fn = unit_sel ? (const void*)k_pass2_amr<true> : (const void*)k_pass2_amr<false>;
+    const char* m = static_cast<const char*>(moments);
+    int md = mode;
+    void* args[] = {(void*)&a, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&m, (void*)&color, (void*)&md,
+                    (void*)&ctr};
+    return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
+}
+
+cudaError_t launch_pass1_piece(const AmrD& a, const float4* tf, const int32_t* pou, int32_t piece, const PieceBox& box,
+                               const ViewTable& vt, int32_t slot, int32_t n_slots, void* moments, Counters* ctr,
+                               cudaStream_t s) {
+    const int blocks = (vt.total_tiles + 3) / 4;
+    k_pass1_piece<AmrD><<<blocks, 128, 0, s>>>(a, tf, pou, piece, box, vt, slot, n_slots, static_cast<char*>(moments),
+                                               ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass2_piece(const AmrD& a, const float4* tf, const int32_t* pou, int32_t piece, const PieceBox& box,
+                               const ViewTable& vt, int32_t slot, int32_t n_slots, const void* moments, float* color,
+                               Counters* ctr, cudaStream_t s) {
+    const int blocks = (vt.total_tiles + 3) / 4;
+    k_pass2_piece<AmrD><<<blocks, 128, 0, s>>>(a, tf, pou, piece, box, vt, slot, n_slots,
+                                               static_cast<const char*>(moments), color, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sortlast_march(bool fill, const AmrD& a, const float4* tf, const int32_t* pou, int32_t piece,
+                                  const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
+                                  int32_t* counts, const int64_t* starts, int32_t* seg_key, float4* seg_col,
+                                  cudaStream_t s) {
+    const int blocks = (vt.total_tiles + 3) / 4;
+    if (fill)
+        k_sortlast_piece<AmrD, true><<<blocks, 128, 0, s>>>(a, tf, pou, piece, box, vt, slot, n_slots, counts, starts,
+                                                            seg_key, seg_col);
+    else
+        k_sortlast_piece<AmrD, false><<<blocks, 128, 0, s>>>(a, tf, pou, piece, box, vt, slot, n_slots, counts, starts,
+                                                             seg_key, seg_col);
     return cudaGetLastError();
 }
 

@@ -64,7 +64,7 @@ def _desc(**kw):
 
 
 @pytest.mark.parametrize("bad, status", [
-    (dict(kind=pkg.MBOIT_AMR), 4),
+    (dict(kind=pkg.MBOIT_TET), 4),
     (dict(moment_set=3), 4),
     (dict(field=None), 1),
     (dict(brick_log2=9), 1),
@@ -111,3 +111,40 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(pkg, "_lib", None)
     with pytest.raises(pkg.MboitError):
         pkg.load_library(str(tmp_path / "nope.so"))
+
+
+def _amr_desc(leaves, dims=17, max_level=1):
+    d = _desc(kind=pkg.MBOIT_AMR, field=None)
+    d.dims[:] = [dims, dims, dims]
+    d.brick_log2 = 3
+    t = np.ascontiguousarray(leaves, dtype=np.int32)
+    d._table = t
+    d.leaf_values = 0x2000
+    d.leaf_table = t.ctypes.data
+    d.n_leaves = t.shape[0]
+    d.max_level = max_level
+    return d
+
+
+@pytest.mark.parametrize("leaves, dims, word", [
+    ([[0, 0, 0, 0], [8, 0, 0, 1]], 17, "overlap"),          # a level-1 leaf inside the level-0 one
+    ([[4, 0, 0, 1]], 17, "lattice"),                        # origin off the 8-cell brick lattice
+    ([[8, 8, 8, 0]], 17, "domain"),                         # a 16-cell leaf past the 16-cell domain
+    ([[0, 0, 0, 2]], 17, "level"),                          # level above max_level
+])
+def test_amr_descriptor_validation(lib, leaves, dims, word):
+    d = _amr_desc(leaves, dims)
+    h = ctypes.c_void_p()
+    assert lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert word in pkg.mboit_last_error()
+    assert h.value is None
+
+
+def test_amr_needs_cubic_domain_and_tables(lib):
+    d = _amr_desc([[0, 0, 0, 0]])
+    d.dims[:] = [17, 17, 33]
+    h = ctypes.c_void_p()
+    assert lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h)) == 1
+    d = _amr_desc([[0, 0, 0, 0]])
+    d.leaf_table = None
+    assert lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h)) == 1
