@@ -40,7 +40,8 @@ class _Grid(ctypes.Structure):
                 ("tf", ctypes.c_void_p), ("vmin", ctypes.c_double), ("vmax", ctypes.c_double),
                 ("step", ctypes.c_double), ("moment_bias", ctypes.c_double),
                 ("overestimation", ctypes.c_double), ("absorbance_max", ctypes.c_double),
-                ("bias_vector", ctypes.c_double * 4)]
+                ("bias_vector", ctypes.c_double * 4), ("moment_set", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("trig_zone", ctypes.c_double)]
 
 
 class _Amr(ctypes.Structure):
@@ -50,7 +51,23 @@ class _Amr(ctypes.Structure):
                 ("piece_selected", ctypes.c_void_p), ("tf", ctypes.c_void_p), ("vmin", ctypes.c_double),
                 ("vmax", ctypes.c_double), ("step", ctypes.c_double), ("moment_bias", ctypes.c_double),
                 ("overestimation", ctypes.c_double), ("absorbance_max", ctypes.c_double),
-                ("bias_vector", ctypes.c_double * 4)]
+                ("bias_vector", ctypes.c_double * 4), ("moment_set", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("trig_zone", ctypes.c_double)]
+
+MOMENT_SETS = {"power4": 0, "trig6": 3, "trig8": 4}
+STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
+TRIG_ZONE = 0.1
+
+
+def _nm(scene):
+    n = MOMENT_SETS[getattr(scene, "moment_set", "power4")]
+    return 1 + 2 * n if n else 5
+
+
+def _set_moment_fields(st, scene):
+    st.moment_set = MOMENT_SETS[getattr(scene, "moment_set", "power4")]
+    st.storage = STORAGES[getattr(scene, "storage", "f32")]
+    st.trig_zone = float(getattr(scene, "trig_zone", TRIG_ZONE))
 
 
 def build(force=False):
@@ -79,6 +96,14 @@ def _load():
             lib.orc_render_grid.restype = ctypes.c_int
             lib.orc_render_grid.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64] + \
                 [ctypes.c_void_p] * 8
+            lib.orc_trig_nodes.restype = ctypes.c_int
+            lib.orc_trig_nodes.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_void_p, ctypes.c_void_p]
+            lib.orc_store_round.restype = ctypes.c_double
+            lib.orc_store_round.argtypes = [ctypes.c_double, ctypes.c_int]
+            lib.orc_trig_bound.restype = ctypes.c_double
+            lib.orc_trig_bound.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_render_amr.restype = ctypes.c_int
             lib.orc_render_amr.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64] + \
                 [ctypes.c_void_p] * 9
@@ -103,6 +128,32 @@ def mboit_bound(m, z0, moment_bias, overestimation, bias_vector=BIAS_VECTOR_POWE
     A = lib.orc_mboit_bound(m.ctypes.data, float(z0), float(moment_bias), bv.ctypes.data,
                             float(overestimation), ctypes.byref(fl))
     return A, fl.value
+
+
+def trig_nodes(m, n, phi0, moment_bias):
+    """Nodes (complex, node 0 = e^{i phi0}) and weights of the canonical representation."""
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    nodes = np.zeros(2 * (n + 1))
+    w = np.zeros(n + 1)
+    st = _load().orc_trig_nodes(m.ctypes.data, int(n), float(phi0), float(moment_bias), nodes.ctypes.data,
+                                w.ctypes.data)
+    return nodes[0::2] + 1j * nodes[1::2], w, st
+
+
+def store_round(x, storage):
+    """float64 -> float32 -> float16 / bfloat16 (nearest even), as stored."""
+    return _load().orc_store_round(float(x), STORAGES[storage] if isinstance(storage, str) else int(storage))
+
+
+def trig_bound(m, n, phi0, moment_bias, overestimation):
+    """Trigonometric moment bound: (A, status, sum of the representation's weights)."""
+    lib = _load()
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    st = ctypes.c_int(0)
+    ws = ctypes.c_double(0.0)
+    A = lib.orc_trig_bound(m.ctypes.data, int(n), float(phi0), float(moment_bias), float(overestimation),
+                           ctypes.byref(st), ctypes.byref(ws))
+    return A, st.value, ws.value
 
 
 def transmittance(m, z0, moment_bias, overestimation, bias_vector=BIAS_VECTOR_POWER4):
@@ -144,6 +195,7 @@ def _grid_struct(scene, pieces):
     g.moment_bias, g.overestimation = float(scene.moment_bias), float(scene.overestimation)
     g.absorbance_max = float(scene.absorbance_max)
     g.bias_vector[:] = list(getattr(scene, "bias_vector", BIAS_VECTOR_POWER4))
+    _set_moment_fields(g, scene)
     return g, keep
 
 
@@ -167,6 +219,7 @@ def _amr_struct(scene, pieces):
     a.moment_bias, a.overestimation = float(scene.moment_bias), float(scene.overestimation)
     a.absorbance_max = float(scene.absorbance_max)
     a.bias_vector[:] = list(getattr(scene, "bias_vector", BIAS_VECTOR_POWER4))
+    _set_moment_fields(a, scene)
     return a, keep
 
 
@@ -181,8 +234,8 @@ def render_amr(scene, view=0, pixels=None, pieces=None, want=("mboit",)):
     v = scene.views[view] if isinstance(view, int) else view
     pix = np.arange(v.width * v.height, dtype=np.int64) if pixels is None else \
         np.ascontiguousarray(pixels, dtype=np.int64)
-    n, K = pix.size, scene.n_pieces
-    shapes = {"moments": (n, 5), "piece_moments": (n, K, 5), "piece_color": (n, K, 4), "mboit": (n, 4),
+    n, K, nm = pix.size, scene.n_pieces, _nm(scene)
+    shapes = {"moments": (n, nm), "piece_moments": (n, K, nm), "piece_color": (n, K, 4), "mboit": (n, 4),
               "raw": (n, 4), "exact": (n, 4), "sortlast": (n, 4)}
     out = {k: np.zeros(shapes[k]) for k in want if k in shapes}
     for k in ("nsamples", "nsegments"):
@@ -231,33 +284,16 @@ def render_grid(scene, view=0, pixels=None, pieces=None, want=("mboit",)):
 
     `pieces`: iterable of selected piece ids (None = all).  `want` picks the
     outputs among: moments, piece_moments, piece_color, mboit, raw, exact,
-    sortlast, nsamples.  Returns a dict of float64 arrays (nsamples int64).
+    sortlast, nsamples.  Returns a dict of float64 arrays (nsamples int64);
+    moments have 5 entries (power) or 1 + 2n (n trigonometric moments).
     """
     lib = _load()
     v = scene.views[view] if isinstance(view, int) else view
     npx = v.width * v.height
     pix = np.arange(npx, dtype=np.int64) if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
-    n = pix.size
-    K = scene.n_pieces
-    field = np.ascontiguousarray(scene.field, dtype=np.float32)
-    pob = np.ascontiguousarray(scene.piece_of_brick, dtype=np.int32)
-    tf = np.ascontiguousarray(scene.tf, dtype=np.float32)
-    sel = None
-    if pieces is not None:
-        sel = np.zeros(K, dtype=np.uint8)
-        sel[np.asarray(list(pieces), dtype=np.int64)] = 1
-    g = _Grid()
-    nx, ny, nz = scene.dims
-    g.field, g.nx, g.ny, g.nz, g.brick_log2 = field.ctypes.data, nx, ny, nz, scene.brick_log2
-    g.piece_of_brick, g.n_pieces = pob.ctypes.data, K
-    g.piece_selected = _ptr(sel)
-    g.tf = tf.ctypes.data
-    g.vmin, g.vmax = float(scene.tf_range[0]), float(scene.tf_range[1])
-    g.step = float(scene.step)
-    g.moment_bias, g.overestimation = float(scene.moment_bias), float(scene.overestimation)
-    g.absorbance_max = float(scene.absorbance_max)
-    g.bias_vector[:] = list(getattr(scene, "bias_vector", BIAS_VECTOR_POWER4))
-    shapes = {"moments": (n, 5), "piece_moments": (n, K, 5), "piece_color": (n, K, 4), "mboit": (n, 4),
+    n, K, nm = pix.size, scene.n_pieces, _nm(scene)
+    g, keep = _grid_struct(scene, pieces)
+    shapes = {"moments": (n, nm), "piece_moments": (n, K, nm), "piece_color": (n, K, 4), "mboit": (n, 4),
               "raw": (n, 4), "exact": (n, 4), "sortlast": (n, 4)}
     out = {k: np.zeros(shapes[k]) for k in want if k in shapes}
     if "nsamples" in want:

@@ -35,8 +35,11 @@
  */
 #include "mboit_oracle.h"
 
+#include <complex.h>
 #include <math.h>
 #include <stdlib.h>
+
+#define ORC_PI 3.14159265358979323846
 #include <string.h>
 
 #define ORC_TAU 1e-12
@@ -179,11 +182,227 @@ typedef struct {
     const float* tf;
     double vmin, vmax, step, moment_bias, overestimation, absorbance_max;
     const double* bias_vector;
+    int n_trig;                    /* 0: power moments; 3 or 4 complex trigonometric moments */
+    int storage;                   /* 0, 1 float16, 2 bfloat16 (normalised trig moments) */
+    double trig_zone;
 } vol_t;
 
-static double transmittance(const double m[5], double z0, const vol_t* g)
+#define ORC_MAX_NM 9
+
+static int n_moments(const vol_t* g) { return g->n_trig ? 1 + 2 * g->n_trig : 5; }
+
+/* round-to-nearest-even float -> float16 -> float (finite inputs) */
+static float round_f16(float x)
 {
-    double A = orc_mboit_bound(m, z0, g->moment_bias, g->bias_vector, g->overestimation, NULL);
+    union { float f; uint32_t u; } v = {x};
+    uint32_t sign = v.u & 0x80000000u, ax = v.u & 0x7fffffffu;
+    float a = fabsf(x);
+    if (a >= 65520.0f) return sign ? -INFINITY : INFINITY;
+    if (a < 6.103515625e-05f) {                       /* subnormal half: quantum 2^-24 */
+        float q = nearbyintf(a * 16777216.0f) / 16777216.0f;
+        return sign ? -q : q;
+    }
+    uint32_t lsb = (ax >> 13) & 1u;
+    ax += 0x0fffu + lsb;                               /* RNE on the 13 dropped bits */
+    ax &= 0xffffe000u;
+    v.u = sign | ax;
+    return v.f;
+}
+
+/* round-to-nearest-even float -> bfloat16 -> float (finite inputs) */
+static float round_bf16(float x)
+{
+    union { float f; uint32_t u; } v = {x};
+    uint32_t lsb = (v.u >> 16) & 1u;
+    v.u += 0x7fffu + lsb;
+    v.u &= 0xffff0000u;
+    return v.f;
+}
+
+double orc_store_round(double x, int storage)
+{
+    float f = (float)x;
+    return storage == 1 ? (double)round_f16(f) : storage == 2 ? (double)round_bf16(f) : (double)f;
+}
+
+/* The moments as the renderer stores them: trigonometric moments normalised
+ * by b0 in float32, then rounded to the 16-bit format. */
+static void store_moments(const vol_t* g, double* m)
+{
+    if (!g->n_trig || !g->storage || !(m[0] > 0.0)) return;
+    for (int j = 1; j <= 2 * g->n_trig; ++j) {
+        float t = (float)(m[j] / m[0]);
+        t = (g->storage == 1) ? round_f16(t) : round_bf16(t);
+        m[j] = (double)t * m[0];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* trigonometric moments                                                     */
+
+/* Hermitian Toeplitz G[k][l] = tau[l - k] (tau[-j] = conj tau[j]) as
+ * L D L^H; returns -1 unless every pivot is positive. */
+static int toeplitz_ldl(int n1, const double complex* tau, double complex L[5][5], double D[5])
+{
+    double complex G[5][5];
+    for (int k = 0; k < n1; ++k)
+        for (int l = 0; l < n1; ++l) G[k][l] = (l >= k) ? tau[l - k] : conj(tau[k - l]);
+    for (int j = 0; j < n1; ++j) {
+        double complex s = G[j][j];
+        for (int k = 0; k < j; ++k) s -= L[j][k] * conj(L[j][k]) * D[k];
+        D[j] = creal(s);
+        if (!(D[j] > 0.0)) return -1;
+        L[j][j] = 1.0;
+        for (int i = j + 1; i < n1; ++i) {
+            double complex t = G[i][j];
+            for (int k = 0; k < j; ++k) t -= L[i][k] * conj(L[j][k]) * D[k];
+            L[i][j] = t / D[j];
+        }
+    }
+    return 0;
+}
+
+/* x = G^-1 b with G = L D L^H */
+static void toeplitz_solve(int n1, double complex L[5][5], const double D[5], const double complex* b,
+                           double complex* x)
+{
+    double complex y[5];
+    for (int i = 0; i < n1; ++i) {
+        y[i] = b[i];
+        for (int k = 0; k < i; ++k) y[i] -= L[i][k] * y[k];
+    }
+    for (int i = 0; i < n1; ++i) y[i] /= D[i];
+    for (int i = n1 - 1; i >= 0; --i) {
+        x[i] = y[i];
+        for (int k = i + 1; k < n1; ++k) x[i] -= conj(L[k][i]) * x[k];
+    }
+}
+
+/* Reproducing kernel K(u, u) = v(u)^T G^-1 conj(v(u)), v(u) = (1, u, .., u^n) */
+static double kernel_diag(int n1, double complex L[5][5], const double D[5], double complex u)
+{
+    double complex w[5], x[5];
+    double complex p = 1.0;
+    for (int k = 0; k < n1; ++k) {
+        w[k] = conj(p);
+        p *= u;
+    }
+    toeplitz_solve(n1, L, D, w, x);
+    double complex s = 0.0;
+    p = 1.0;
+    for (int k = 0; k < n1; ++k) {
+        s += p * x[k];
+        p *= u;
+    }
+    return creal(s);
+}
+
+/* Roots of c[0] + c[1] u + ... + c[n] u^n by the Aberth-Ehrlich iteration. */
+static int poly_roots(int n, const double complex* c, double complex* r)
+{
+    for (int i = 0; i < n; ++i) r[i] = 0.9 * cexp(I * (2.0 * ORC_PI * i / n + 0.4));
+    double last = INFINITY;
+    for (int it = 0; it < 500; ++it) {
+        double change = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double complex pv = c[n], dv = 0.0;
+            for (int k = n - 1; k >= 0; --k) {
+                dv = dv * r[i] + pv;
+                pv = pv * r[i] + c[k];
+            }
+            if (pv == 0.0) continue;
+            double complex ratio = pv / dv;
+            double complex sum = 0.0;
+            for (int j = 0; j < n; ++j)
+                if (j != i) sum += 1.0 / (r[i] - r[j]);
+            double complex step = ratio / (1.0 - ratio * sum);
+            r[i] -= step;
+            double a = cabs(step);
+            if (a > change) change = a;
+        }
+        if (change < 4e-15) return 0;
+        last = change;
+    }
+    return last < 1e-10 ? 0 : -2;
+}
+
+static double trig_bound_impl(const double* m, int n, double phi0, double moment_bias, double overestimation,
+                              int* status, double* weights_sum, double* nodes, double* weights);
+
+double orc_trig_bound(const double* m, int n, double phi0, double moment_bias, double overestimation,
+                      int* status, double* weights_sum)
+{
+    return trig_bound_impl(m, n, phi0, moment_bias, overestimation, status, weights_sum, NULL, NULL);
+}
+
+int orc_trig_nodes(const double* m, int n, double phi0, double moment_bias, double* nodes, double* weights)
+{
+    int st = 0;
+    trig_bound_impl(m, n, phi0, moment_bias, 0.0, &st, NULL, nodes, weights);
+    return st;
+}
+
+static double trig_bound_impl(const double* m, int n, double phi0, double moment_bias, double overestimation,
+                              int* status, double* weights_sum, double* nodes, double* weights)
+{
+    if (status) *status = 0;
+    if (weights_sum) *weights_sum = 0.0;
+    if (!(m[0] > 0.0)) return 0.0;
+    int n1 = n + 1;
+    double complex tau[5];
+    tau[0] = 1.0;
+    for (int j = 1; j <= n; ++j) tau[j] = (1.0 - moment_bias) * (m[2 * j - 1] + I * m[2 * j]) / m[0];
+    double complex L[5][5];
+    double D[5] = {0, 0, 0, 0, 0};
+    if (toeplitz_ldl(n1, tau, L, D) != 0) {
+        if (status) *status = -1;
+        return 0.0;
+    }
+    /* kernel polynomial through u0: coefficients y = G^-1 conj(v(u0)) */
+    double complex u0 = cexp(I * phi0), w[5], y[5], p = 1.0;
+    for (int k = 0; k < n1; ++k) {
+        w[k] = conj(p);
+        p *= u0;
+    }
+    toeplitz_solve(n1, L, D, w, y);
+    double k00 = 0.0;
+    p = 1.0;
+    for (int k = 0; k < n1; ++k) {
+        k00 += creal(p * y[k]);
+        p *= u0;
+    }
+    double rho0 = 1.0 / k00;
+    double complex roots[4];
+    if (poly_roots(n, y, roots) != 0 && status) *status = -2;
+    double A = overestimation * rho0, sum = rho0;
+    if (nodes) {
+        nodes[0] = creal(u0);
+        nodes[1] = cimag(u0);
+        weights[0] = rho0;
+    }
+    for (int i = 0; i < n; ++i) {
+        double complex ui = roots[i] / cabs(roots[i]);  /* the nodes lie on the unit circle */
+        double rho = 1.0 / kernel_diag(n1, L, D, ui);
+        sum += rho;
+        if (carg(ui) < phi0) A += rho;
+        if (nodes) {
+            nodes[2 * i + 2] = creal(ui);
+            nodes[2 * i + 3] = cimag(ui);
+            weights[i + 1] = rho;
+        }
+    }
+    if (weights_sum) *weights_sum = sum;
+    return A;
+}
+
+static double transmittance(const double* m, double z0, const vol_t* g)
+{
+    double A;
+    if (g->n_trig)
+        A = orc_trig_bound(m, g->n_trig, z0 * (1.0 - g->trig_zone) * ORC_PI, g->moment_bias, g->overestimation,
+                           NULL, NULL);
+    else
+        A = orc_mboit_bound(m, z0, g->moment_bias, g->bias_vector, g->overestimation, NULL);
     double T = exp(-m[0] * A);
     if (T < 0.0) T = 0.0;
     if (T > 1.0) T = 1.0;
@@ -381,6 +600,11 @@ static int grid_vol(const orc_grid* g, vol_t* v)
     v->overestimation = g->overestimation;
     v->absorbance_max = g->absorbance_max;
     v->bias_vector = g->bias_vector;
+    if (g->moment_set != 0 && g->moment_set != 3 && g->moment_set != 4) return -1;
+    if (g->storage < 0 || g->storage > 2 || (g->storage && !g->moment_set)) return -1;
+    v->n_trig = g->moment_set;
+    v->storage = g->storage;
+    v->trig_zone = g->trig_zone;
     return 0;
 }
 
@@ -444,6 +668,14 @@ int orc_render_amr(const orc_amr* a, const orc_view* V,
     v.overestimation = a->overestimation;
     v.absorbance_max = a->absorbance_max;
     v.bias_vector = a->bias_vector;
+    if ((a->moment_set != 0 && a->moment_set != 3 && a->moment_set != 4) || a->storage < 0 || a->storage > 2 ||
+        (a->storage && !a->moment_set)) {
+        free(fmap);
+        return -1;
+    }
+    v.n_trig = a->moment_set;
+    v.storage = a->storage;
+    v.trig_zone = a->trig_zone;
     int rc = render_impl(&v, V, pixels, n_pixels, moments, piece_moments, piece_color, mboit_rgba, raw_rgba,
                          exact_rgba, sortlast_rgba, nsamples, nsegments);
     free(fmap);
@@ -489,7 +721,8 @@ static int render_impl(const vol_t* g, const orc_view* V,
 
     size_t cap = 1024;
     sample_t* S = (sample_t*)malloc(cap * sizeof(sample_t));
-    double* mP = (double*)malloc((size_t)K * 5 * sizeof(double));
+    const int NM = n_moments(g);
+    double* mP = (double*)malloc((size_t)K * NM * sizeof(double));
     double* cP = (double*)malloc((size_t)K * 4 * sizeof(double));
     if (!S || !mP || !cP) { free(S); free(mP); free(cP); return -1; }
 
@@ -515,25 +748,38 @@ static int render_impl(const vol_t* g, const orc_view* V,
         }
 
         /* stage one (Sec. 4.1): local moment image of each piece ... */
-        memset(mP, 0, (size_t)K * 5 * sizeof(double));
+        memset(mP, 0, (size_t)K * NM * sizeof(double));
         for (size_t i = 0; i < ns; ++i) {
-            double* mp = mP + 5 * S[i].piece;
-            double zp = 1.0;
-            for (int j = 0; j <= 4; ++j) {
-                mp[j] += zp * S[i].a;
-                zp *= S[i].z;
+            double* mp = mP + (size_t)NM * S[i].piece;
+            if (g->n_trig) {
+                /* b0 += a, t_j += a e^{i j phi} */
+                double phi = S[i].z * (1.0 - g->trig_zone) * ORC_PI;
+                mp[0] += S[i].a;
+                for (int j = 1; j <= g->n_trig; ++j) {
+                    mp[2 * j - 1] += S[i].a * cos(j * phi);
+                    mp[2 * j] += S[i].a * sin(j * phi);
+                }
+            } else {
+                double zp = 1.0;
+                for (int j = 0; j <= 4; ++j) {
+                    mp[j] += zp * S[i].a;
+                    zp *= S[i].z;
+                }
             }
         }
         /* ... summed over pieces (the Allreduce add) */
-        double m[5] = {0, 0, 0, 0, 0};
+        double m[ORC_MAX_NM] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int P = 0; P < K; ++P)
-            for (int j = 0; j <= 4; ++j) m[j] += mP[5 * P + j];
+            for (int j = 0; j < NM; ++j) m[j] += mP[(size_t)NM * P + j];
+        double ms[ORC_MAX_NM];
+        memcpy(ms, m, sizeof m);
+        store_moments(g, ms);
 
         /* stage two (Sec. 4.2): each piece blends its own samples with the
-         * transmittance reconstructed from the global moments */
+         * transmittance reconstructed from the (stored) global moments */
         memset(cP, 0, (size_t)K * 4 * sizeof(double));
         for (size_t i = 0; i < ns; ++i) {
-            double T = transmittance(m, S[i].z, g);
+            double T = transmittance(ms, S[i].z, g);
             double* cp = cP + 4 * S[i].piece;
             for (int c = 0; c < 3; ++c) cp[c] += T * S[i].alpha * S[i].rgb[c];
             cp[3] += T * S[i].alpha;
@@ -543,8 +789,8 @@ static int render_impl(const vol_t* g, const orc_view* V,
         for (int P = 0; P < K; ++P)
             for (int c = 0; c < 4; ++c) C[c] += cP[4 * P + c];
 
-        if (moments) memcpy(moments + 5 * n, m, sizeof m);
-        if (piece_moments) memcpy(piece_moments + (size_t)n * K * 5, mP, (size_t)K * 5 * sizeof(double));
+        if (moments) memcpy(moments + (size_t)NM * n, m, (size_t)NM * sizeof(double));
+        if (piece_moments) memcpy(piece_moments + (size_t)n * K * NM, mP, (size_t)K * NM * sizeof(double));
         if (piece_color) memcpy(piece_color + (size_t)n * K * 4, cP, (size_t)K * 4 * sizeof(double));
         if (raw_rgba) memcpy(raw_rgba + 4 * n, C, sizeof C);
         if (mboit_rgba) {

@@ -36,6 +36,9 @@ typedef struct {
     double overestimation;         /* weight w0 of the sample's own depth (Alg. 3) */
     double absorbance_max;         /* ABSORBANCE_MAX_VALUE (Alg. 2) */
     double bias_vector[4];
+    int32_t moment_set;            /* 0: 4 power moments; 3 / 4: that many complex trigonometric moments */
+    int32_t storage;               /* 0 FP64 moments; 1 / 2: normalised trig moments rounded to float16 / bfloat16 */
+    double trig_zone;              /* zeta: angles phi = z (1 - zeta) pi leave a wrapping zone of 2 zeta pi */
 } orc_grid;
 
 typedef struct {
@@ -50,6 +53,8 @@ typedef struct {
     const float* tf;
     double vmin, vmax, step, moment_bias, overestimation, absorbance_max;
     double bias_vector[4];
+    int32_t moment_set, storage;   /* as in orc_grid */
+    double trig_zone;
 } orc_amr;
 
 /* Alg. 3 core: the moment-bound absorbance fraction A(z0) in [0,1] for raw
@@ -58,12 +63,34 @@ typedef struct {
 double orc_mboit_bound(const double m[5], double z0, double moment_bias,
                        const double bias_vector[4], double overestimation, int* flags);
 
+/* Trigonometric moments (n = 3 or 4 complex moments, "6 / 8 trigonometric
+ * moments" of Sec. 4.3 / Fig. 3): warped depth z -> angle phi = z (1 - zeta) pi,
+ * moments t_j = sum a e^{i j phi}.  m = (b0, Re t1, Im t1, ..., Re tn, Im tn).
+ * The bound mixes the normalised moments with the uniform measure
+ * (tau'_j = (1 - beta) t_j / b0), takes the canonical representation through
+ * u0 = e^{i phi0} (nodes: u0 and the roots of K(., u0), K the reproducing
+ * kernel of the Toeplitz matrix; weights 1 / K(u_i, u_i)) and returns
+ * w0 rho0 + the weights of the nodes at angles (in (-pi, pi]) below phi0.
+ * *status (optional): 0 ok, -1 Toeplitz matrix not positive definite,
+ * -2 root iteration did not converge. */
+double orc_trig_bound(const double* m, int n, double phi0, double moment_bias, double overestimation,
+                      int* status, double* weights_sum);
+
+/* The canonical representation itself: nodes[2 (n+1)] (re, im; node 0 is
+ * u0) and weights[n + 1].  Returns the status of orc_trig_bound. */
+int orc_trig_nodes(const double* m, int n, double phi0, double moment_bias, double* nodes, double* weights);
+
+/* Storage rounding of one normalised trigonometric moment: float64 ->
+ * float32 -> float16 (storage 1) or bfloat16 (storage 2), nearest-even. */
+double orc_store_round(double x, int storage);
+
 /* Logarithmic depth warp of Alg. 2/3: [near, far] -> [-1, 1], clamped. */
 double orc_log_warp(double t, double znear, double zfar);
 
 /* Renders the listed pixels (index y*width + x) of one view.  Every output
- * pointer may be NULL.  Per pixel: moments = summed global moments [5];
- * piece_moments [K][5]; piece_color [K][4] (stage 2 partial images);
+ * pointer may be NULL.  Per pixel: moments = summed global moments [NM]
+ * (NM = 5 for power moments: b0..b4; 1 + 2n for n trigonometric moments:
+ * b0, Re t1, Im t1, ...); piece_moments [K][NM]; piece_color [K][4];
  * mboit_rgba = renormalised resolve; raw_rgba = sum of T*alpha*(c,1);
  * exact_rgba = front-to-back blend of the same samples; sortlast_rgba =
  * per-piece segments sorted and blended; nsamples = owned samples.

@@ -391,3 +391,91 @@ def test_amr_leaf_lookup_brute_force():
             np.testing.assert_allclose(r["moments"][idx, :2], [m0, m1], rtol=2e-6, atol=1e-9)
             hit += len(S) > 0
     assert hit > 30
+
+
+# --------------------------------------------------------------------------
+# trigonometric moments (Sec. 4.3, Fig. 3: "different moments")
+
+
+def trig_moments(phis, a, n):
+    t = [np.sum(a * np.exp(1j * j * np.asarray(phis))) for j in range(n + 1)]
+    return np.array([t[0].real] + sum([[t[j].real, t[j].imag] for j in range(1, n + 1)], []))
+
+
+@pytest.mark.parametrize("n", [3, 4])
+def test_trig_n_plus_one_atoms_canonical(n):
+    """n+1 atoms on the circle are their own Szego representation through
+    each atom: A(phi_j) = (sum_{phi_i < phi_j} a_i + w0 a_j) / sum a."""
+    rng = np.random.default_rng(10 + n)
+    done = 0
+    while done < 200:
+        phis = np.sort(rng.uniform(-0.9 * np.pi, 0.9 * np.pi, n + 1))
+        if np.diff(phis).min() < 0.25:
+            continue
+        a = rng.uniform(0.1, 2.0, n + 1)
+        w0 = rng.uniform(0, 1)
+        m = trig_moments(phis, a, n)
+        for j in range(n + 1):
+            A, st, ws = oracle.trig_bound(m, n, phis[j], 0.0, w0)
+            assert st == 0
+            assert ws == pytest.approx(1.0, abs=1e-11)
+            assert A == pytest.approx((a[phis < phis[j]].sum() + w0 * a[j]) / a.sum(), abs=1e-10)
+        done += 1
+
+
+@pytest.mark.parametrize("n", [3, 4])
+def test_trig_full_bias_is_uniform_measure(n):
+    """Mix amount 1 leaves the uniform measure: the nodes through u0 are the
+    (n+1)-th roots of unity times u0, each of weight 1/(n+1)."""
+    m = trig_moments([0.4, -1.1], np.array([1.0, 0.5]), n)
+    for phi0 in np.linspace(-2.8, 2.8, 9):
+        nodes = np.angle(np.exp(1j * (phi0 + 2 * np.pi * np.arange(1, n + 1) / (n + 1))))
+        A, st, ws = oracle.trig_bound(m, n, phi0, 1.0, 0.3)
+        assert A == pytest.approx((0.3 + np.sum(nodes < phi0)) / (n + 1), abs=1e-12)
+
+
+@pytest.mark.parametrize("n", [3, 4])
+def test_trig_representation_reproduces_moments(n):
+    """For any biased moments and any u0 the representation is exact: its
+    nodes lie on the circle, its weights are positive and sum to 1, and
+    sum_i rho_i u_i^j equals the biased normalised moment tau'_j; the bound
+    lies in [0, 1]."""
+    rng = np.random.default_rng(20 + n)
+    for _ in range(60):
+        k = rng.integers(1, 15)
+        m = trig_moments(rng.uniform(-0.9 * np.pi, 0.9 * np.pi, k), rng.uniform(0.05, 2, k), n)
+        beta = 10 ** rng.uniform(-4, -1)
+        tau = (1 - beta) * (m[1::2] + 1j * m[2::2]) / m[0]
+        for phi0 in rng.uniform(-0.9 * np.pi, 0.9 * np.pi, 5):
+            u, w, st = oracle.trig_nodes(m, n, phi0, beta)
+            assert st == 0
+            np.testing.assert_allclose(np.abs(u), 1.0, atol=1e-12)
+            assert np.all(w > 0) and w.sum() == pytest.approx(1.0, abs=1e-10)
+            for j in range(1, n + 1):
+                assert np.sum(w * u ** j) == pytest.approx(tau[j - 1], abs=1e-9)
+            A = oracle.trig_bound(m, n, phi0, beta, 0.3)[0]
+            assert -1e-12 <= A <= 1 + 1e-12
+
+
+def test_trig_storage_rounding_matches_numpy():
+    rng = np.random.default_rng(5)
+    xs = np.concatenate([rng.uniform(-1, 1, 2000), rng.uniform(-1e-3, 1e-3, 500), [0.0, 1.0, -1.0, 0.1]])
+    for x in xs:
+        assert oracle.store_round(x, "f16") == float(np.float16(np.float32(x)))
+        u = np.array([np.float32(x)]).view(np.uint32).astype(np.uint64)
+        u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+        assert oracle.store_round(x, "bf16") == float(u.view(np.float32)[0])
+
+
+def test_trig_render_quantised_storage_changes_little():
+    """The 16-bit stored moments give images close to the float64 ones."""
+    import copy
+    sc = scenes.blobs64(width=48, height=48)
+    out = {}
+    for st, beta in (("f32", 1e-5), ("f16", 2e-3), ("bf16", 2e-2)):
+        s2 = copy.copy(sc)
+        s2.moment_set, s2.storage, s2.moment_bias = "trig6", st, beta
+        out[st] = oracle.render_grid(s2, want=("mboit", "exact"))
+    for st in ("f16", "bf16"):
+        assert np.abs(out[st]["mboit"] - out["f32"]["mboit"]).max() < 0.1
+    assert np.sqrt(((out["f32"]["mboit"] - out["f32"]["exact"]) ** 2).mean()) < 0.02
