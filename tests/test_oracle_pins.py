@@ -479,3 +479,20 @@ def test_trig_render_quantised_storage_changes_little():
     for st in ("f16", "bf16"):
         assert np.abs(out[st]["mboit"] - out["f32"]["mboit"]).max() < 0.1
     assert np.sqrt(((out["f32"]["mboit"] - out["f32"]["exact"]) ** 2).mean()) < 0.02
+
+
+@pytest.mark.parametrize("n", [3, 4])
+def test_trig_node_just_behind_is_not_counted(n):
+    """Two atoms 0.03 rad apart among n+1: at the front one, the one just
+    behind must not count (and at the back one, the front one must)."""
+    rng = np.random.default_rng(30 + n)
+    for _ in range(50):
+        base = np.sort(rng.uniform(-0.8 * np.pi, 0.7 * np.pi, n))
+        if np.diff(base).min() < 0.3:
+            continue
+        phis = np.sort(np.concatenate([base, [base[0] + 0.03]]))
+        a = rng.uniform(0.2, 2.0, n + 1)
+        m = trig_moments(phis, a, n)
+        for j in range(n + 1):
+            A = oracle.trig_bound(m, n, phis[j], 0.0, 0.5)[0]
+            assert A == pytest.approx((a[phis < phis[j]].sum() + 0.5 * a[j]) / a.sum(), abs=1e-6)
