@@ -30,10 +30,12 @@
  *     inside kernels (a wait limit or an index check) are reported by
  *     mboit_synchronize().
  *   - Images are row-major, pixel index y * width + x, x to the right.
- *   - Moment images: per (view[, piece]) one slab of 20 * P bytes, P = width *
- *     height rounded up to a multiple of 4: b0 as P float32, then (b1, b2,
- *     b3, b4) as P float4 (16-byte aligned).  mboit_moment_image_bytes()
- *     gives the slab size.
+ *   - Moment images: per (view[, piece]) one slab, P = width * height rounded
+ *     up to a multiple of 4.  Power moments: b0 as P float32, then (b1, b2,
+ *     b3, b4) as P float4 (20 * P bytes).  Trigonometric moments: b0 as P
+ *     float32, then for j = 1..n a plane of P 16-bit pairs (Re, Im of
+ *     t_j / b0) ((4 + 4 n) * P bytes).  mboit_moment_image_bytes() gives the
+ *     slab size.
  *   - Colour images: float32 RGBA [height][width][4] per (view[, piece]),
  *     premultiplied (sum of T * alpha * (r, g, b) and sum of T * alpha).
  */
@@ -65,8 +67,13 @@ typedef enum {
 } mboit_status;
 
 typedef enum { MBOIT_GRID = 0, MBOIT_AMR = 1, MBOIT_TET = 2 } mboit_volume_kind;
-typedef enum { MBOIT_POWER4 = 0 } mboit_moment_set;
-typedef enum { MBOIT_STORE_F32 = 0 } mboit_storage;
+/* Moment sets (Sec. 4.3, Fig. 3): 4 power moments of the warped depth, or 3 / 4
+ * complex trigonometric moments ("6 / 8 trigonometric moments") of the angle
+ * phi = z (1 - 0.1) pi (a wrapping zone of 0.2 pi separates far from near). */
+typedef enum { MBOIT_POWER4 = 0, MBOIT_TRIG6 = 1, MBOIT_TRIG8 = 2 } mboit_moment_set;
+/* Moment storage: power moments in float32; trigonometric moments normalised
+ * by b0 (kept in float32) in float16 or bfloat16 (nearest-even rounding). */
+typedef enum { MBOIT_STORE_F32 = 0, MBOIT_STORE_F16 = 1, MBOIT_STORE_BF16 = 2 } mboit_storage;
 typedef enum { MBOIT_ORTHO = 0, MBOIT_PERSPECTIVE = 1 } mboit_projection;
 
 /* pass-1 output layout */
@@ -114,7 +121,9 @@ typedef struct {
     float step;                 /* sample spacing in voxels, a power of two (Sec. 5.3: fixed step);
                                  * lattice point k sits at t = (k + 1/2) step from the eye, and only
                                  * k < 2^22 is sampled (t exact in float32) */
-    float moment_bias;          /* mix amount of the bias vector (Alg. 3 "mix"), in [0, 1) */
+    float moment_bias;          /* mix amount of the bias vector (Alg. 3 "mix"), in [0, 1); for
+                                 * trigonometric moments the mix is with the uniform measure and
+                                 * must be >= 2e-3 (float16) / 2e-2 (bfloat16) */
     float overestimation;       /* weight of the sample's own depth (Alg. 3), paper: 0.3 */
     float absorbance_max;       /* ABSORBANCE_MAX_VALUE of Alg. 2, > 0 */
     /* MBOIT_AMR (brick octree) only; `field` is then unused.  dims = finest

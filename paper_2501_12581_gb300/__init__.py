@@ -22,8 +22,10 @@ MBOIT_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "UNSUPPORTED", 5: "STATE",
                 6: "TIMEOUT", 7: "DEVICE_ASSERT"}
 MBOIT_GRID, MBOIT_AMR, MBOIT_TET = 0, 1, 2
-MBOIT_POWER4 = 0
-MBOIT_STORE_F32 = 0
+MBOIT_POWER4, MBOIT_TRIG6, MBOIT_TRIG8 = 0, 1, 2
+MBOIT_STORE_F32, MBOIT_STORE_F16, MBOIT_STORE_BF16 = 0, 1, 2
+MOMENT_SET_IDS = {"power4": MBOIT_POWER4, "trig6": MBOIT_TRIG6, "trig8": MBOIT_TRIG8}
+STORAGE_IDS = {"f32": MBOIT_STORE_F32, "f16": MBOIT_STORE_F16, "bf16": MBOIT_STORE_BF16}
 MBOIT_ORTHO, MBOIT_PERSPECTIVE = 0, 1
 MBOIT_MOMENTS_PER_PIECE, MBOIT_MOMENTS_REDUCED = 0, 1
 MBOIT_COLOR_PER_PIECE, MBOIT_COLOR_REDUCED, MBOIT_COLOR_RESOLVED = 0, 1, 2
@@ -295,7 +297,9 @@ class Volume:
         tf = np.ascontiguousarray(scene.tf, dtype=np.float32)
         d = mboit_volume_desc()
         d.kind = MBOIT_AMR if amr else MBOIT_GRID
-        d.moment_set, d.storage, d.flags = MBOIT_POWER4, MBOIT_STORE_F32, flags
+        self.moment_set = MOMENT_SET_IDS[getattr(scene, "moment_set", "power4")]
+        self.storage = STORAGE_IDS[getattr(scene, "storage", "f32")]
+        d.moment_set, d.storage, d.flags = self.moment_set, self.storage, flags
         if amr:
             table = np.ascontiguousarray(scene.leaves, dtype=np.int32)
             d.leaf_values, d.leaf_table = self.field.data_ptr(), table.ctypes.data
@@ -327,10 +331,15 @@ class Volume:
             pass
 
     @staticmethod
-    def moment_buffer(views, n_slots=1):
+    def moment_buffer(views, n_slots=1, moment_set=MBOIT_POWER4, storage=MBOIT_STORE_F32):
+        """Zeroed device buffer (float32 words) for n_slots moment slabs per view."""
         import torch
-        total = sum(mboit_moment_image_bytes(v.width, v.height) for v in views) * n_slots
+        total = sum(mboit_moment_image_bytes(v.width, v.height, moment_set, storage) for v in views) * n_slots
         return torch.zeros(total // 4, dtype=torch.float32, device="cuda")
+
+    def moments_for(self, views, n_slots=1):
+        """moment_buffer in this volume's moment format."""
+        return Volume.moment_buffer(views, n_slots, self.moment_set, self.storage)
 
     @staticmethod
     def color_buffer(views, n_slots=1):

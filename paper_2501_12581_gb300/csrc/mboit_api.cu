@@ -92,6 +92,42 @@ struct mboit_volume_s {
 
 namespace {
 
+constexpr double kTrigZone = 0.1;  // wrapping zone: phi = z (1 - zeta) pi
+
+// Angle map and the coefficients of s^m in (s + i)^k (s - i)^(n-k).
+void fill_trig(mb::TrigTables& T, int32_t moment_set, int32_t storage, float beta) {
+    std::memset(&T, 0, sizeof T);
+    T.n = moment_set == MBOIT_TRIG6 ? 3 : moment_set == MBOIT_TRIG8 ? 4 : 0;
+    T.storage = storage;
+    T.beta = beta;
+    T.zone_scale = (float)((1.0 - kTrigZone) * 3.14159265358979323846);
+    for (int k = 0; k <= T.n; ++k) {
+        double cr[6] = {1, 0, 0, 0, 0, 0}, ci[6] = {0, 0, 0, 0, 0, 0};
+        for (int f = 0; f < T.n; ++f) {
+            const double rim = f < k ? 1.0 : -1.0;  // factor (s + i) or (s - i)
+            double nr[6] = {0, 0, 0, 0, 0, 0}, ni[6] = {0, 0, 0, 0, 0, 0};
+            for (int m = 0; m <= f; ++m) {
+                nr[m + 1] += cr[m];
+                ni[m + 1] += ci[m];
+                nr[m] += -ci[m] * rim;  // c * (i * rim)
+                ni[m] += cr[m] * rim;
+            }
+            for (int m = 0; m <= f + 1; ++m) {
+                cr[m] = nr[m];
+                ci[m] = ni[m];
+            }
+        }
+        for (int m = 0; m <= T.n; ++m) {
+            T.er[k][m] = (float)cr[m];
+            T.ei[k][m] = (float)ci[m];
+        }
+    }
+}
+
+int64_t slab_bytes_per_px(int32_t moment_set) {
+    return moment_set == MBOIT_TRIG6 ? 16 : moment_set == MBOIT_TRIG8 ? 20 : 20;
+}
+
 template <class T>
 cudaError_t ensure_capacity(T*& p, size_t& cap, size_t n) {
     if (n <= cap) return cudaSuccess;
@@ -116,7 +152,7 @@ mboit_status check_volume(mboit_volume v) {
 }
 
 // Validates views and lays out tiles and output offsets.
-mboit_status build_views(const mboit_view* views, int32_t n_views, mb::ViewTable& vt) {
+mboit_status build_views(const mboit_view* views, int32_t n_views, mb::ViewTable& vt, int64_t bpp = 20) {
     if (!views) return fail(MBOIT_ERR_INVALID_ARG, "views is NULL");
     if (n_views < 1 || n_views > mb::kMaxViews)
         return fail(MBOIT_ERR_INVALID_ARG, "n_views must be in [1, " + std::to_string(mb::kMaxViews) + "]");
@@ -160,7 +196,7 @@ mboit_status build_views(const mboit_view* views, int32_t n_views, mb::ViewTable
         S.plane = (int32_t)((((int64_t)V.width * V.height) + 3) / 4 * 4);
         S.moment_off = moff;
         S.color_off = coff;
-        moff += (int64_t)20 * S.plane;
+        moff += bpp * S.plane;
         coff += (int64_t)4 * V.width * V.height;
     }
     if (tiles >= (int64_t)1 << 31) return fail(MBOIT_ERR_INVALID_ARG, "too many pixels in one call");
@@ -169,7 +205,7 @@ mboit_status build_views(const mboit_view* views, int32_t n_views, mb::ViewTable
 }
 
 // Image-only table for the composite op (offsets of n_views equal images).
-mboit_status build_images(int32_t width, int32_t height, int32_t n_views, mb::ViewTable& vt) {
+mboit_status build_images(int32_t width, int32_t height, int32_t n_views, mb::ViewTable& vt, int64_t bpp = 20) {
     if (n_views < 1 || n_views > mb::kMaxViews) return fail(MBOIT_ERR_INVALID_ARG, "n_views out of range");
     if (width < 1 || height < 1 || width > 32768 || height > 32768)
         return fail(MBOIT_ERR_INVALID_ARG, "width and height must be in [1, 32768]");
@@ -180,7 +216,7 @@ mboit_status build_images(int32_t width, int32_t height, int32_t n_views, mb::Vi
         S.v.width = width;
         S.v.height = height;
         S.plane = (int32_t)((((int64_t)width * height) + 3) / 4 * 4);
-        S.moment_off = (int64_t)i * 20 * S.plane;
+        S.moment_off = (int64_t)i * bpp * S.plane;
         S.color_off = (int64_t)i * 4 * width * height;
     }
     return MBOIT_OK;
@@ -230,9 +266,13 @@ extern "C" {
 const char* mboit_last_error(void) { return g_err.c_str(); }
 
 size_t mboit_moment_image_bytes(int32_t width, int32_t height, int32_t moment_set, int32_t storage) {
-    if (width < 1 || height < 1 || moment_set != MBOIT_POWER4 || storage != MBOIT_STORE_F32) return 0;
+    if (width < 1 || height < 1) return 0;
+    const bool power = moment_set == MBOIT_POWER4 && storage == MBOIT_STORE_F32;
+    const bool trig = (moment_set == MBOIT_TRIG6 || moment_set == MBOIT_TRIG8) &&
+                      (storage == MBOIT_STORE_F16 || storage == MBOIT_STORE_BF16);
+    if (!power && !trig) return 0;
     const size_t P = (((size_t)width * (size_t)height) + 3) / 4 * 4;
-    return 20 * P;
+    return (size_t)slab_bytes_per_px(moment_set) * P;
 }
 
 mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) {
@@ -241,8 +281,15 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
     if (d->kind != MBOIT_GRID && d->kind != MBOIT_AMR)
         return fail(MBOIT_ERR_UNSUPPORTED, "only MBOIT_GRID and MBOIT_AMR volumes are implemented");
     const bool is_amr = d->kind == MBOIT_AMR;
-    if (d->moment_set != MBOIT_POWER4) return fail(MBOIT_ERR_UNSUPPORTED, "only MBOIT_POWER4 moments are implemented");
-    if (d->storage != MBOIT_STORE_F32) return fail(MBOIT_ERR_UNSUPPORTED, "only float32 moment storage is implemented");
+    if (d->moment_set < MBOIT_POWER4 || d->moment_set > MBOIT_TRIG8) return fail(MBOIT_ERR_UNSUPPORTED, "unknown moment set");
+    if (d->moment_set == MBOIT_POWER4 && d->storage != MBOIT_STORE_F32)
+        return fail(MBOIT_ERR_UNSUPPORTED, "power moments are stored in float32");
+    if (d->moment_set != MBOIT_POWER4 && d->storage != MBOIT_STORE_F16 && d->storage != MBOIT_STORE_BF16)
+        return fail(MBOIT_ERR_UNSUPPORTED, "trigonometric moments are stored in float16 or bfloat16");
+    if (d->moment_set != MBOIT_POWER4 &&
+        !(d->moment_bias >= (d->storage == MBOIT_STORE_F16 ? 2e-3f : 2e-2f)))
+        return fail(MBOIT_ERR_INVALID_ARG, "trigonometric moments in 16 bits need moment_bias >= 2e-3 (float16) or "
+                                           ">= 2e-2 (bfloat16) to keep the stored Toeplitz matrices positive definite");
     if (d->flags & ~(MBOIT_FLAG_RAW_SUM | MBOIT_FLAG_DETERMINISTIC)) return fail(MBOIT_ERR_INVALID_ARG, "unknown flag bits");
     if (!is_amr && !d->field) return fail(MBOIT_ERR_INVALID_ARG, "field is NULL");
     if (is_amr) {
@@ -348,6 +395,7 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
     g.bias_vector[2] = 0.0f;
     g.bias_vector[3] = 0.375f;
     g.flags = d->flags;
+    fill_trig(g.trig, d->moment_set, d->storage, d->moment_bias);
     v->nbricks = (int64_t)g.nbx * g.nby * g.nbz;
     v->field_bytes = (size_t)g.nx * g.ny * g.nz * sizeof(float);
     v->kind = d->kind;
@@ -502,7 +550,7 @@ mboit_status mboit_render_moments(mboit_volume v, const mboit_view* views, int32
     std::lock_guard<std::mutex> lk(v->mu);
     DeviceGuard dg(v->device);
     mb::ViewTable vt;
-    if ((st = build_views(views, n_views, vt)) != MBOIT_OK) return st;
+    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set))) != MBOIT_OK) return st;
     std::vector<int32_t> list;
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, pieces, n_pieces, list, &mask)) != MBOIT_OK) return st;
@@ -540,7 +588,7 @@ mboit_status mboit_reconstruct_blend(mboit_volume v, const mboit_view* views, in
     std::lock_guard<std::mutex> lk(v->mu);
     DeviceGuard dg(v->device);
     mb::ViewTable vt;
-    if ((st = build_views(views, n_views, vt)) != MBOIT_OK) return st;
+    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set))) != MBOIT_OK) return st;
     std::vector<int32_t> list;
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, pieces, n_pieces, list, &mask)) != MBOIT_OK) return st;
@@ -587,11 +635,11 @@ mboit_status mboit_composite(mboit_volume v, int32_t op, int32_t width, int32_t 
     std::lock_guard<std::mutex> lk(v->mu);
     DeviceGuard dg(v->device);
     mb::ViewTable vt;
-    mboit_status st = build_images(width, height, n_views, vt);
+    mboit_status st = build_images(width, height, n_views, vt, slab_bytes_per_px(v->desc.moment_set));
     if (st != MBOIT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (op == MBOIT_OP_MOMENTS_SUM) {
-        MB_CUDA(mb::launch_moments_sum(vt, n_inputs, in, out, s));
+        MB_CUDA(mb::launch_moments_sum(v->kind == MBOIT_AMR ? v->amr.g : v->grid, vt, n_inputs, in, out, s));
     } else {
         MB_CUDA(mb::launch_color_resolve(vt, n_inputs, static_cast<const float*>(in), static_cast<float*>(out),
                                          global_moments, b, raw ? 1 : 0, s));
@@ -608,7 +656,7 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
     std::lock_guard<std::mutex> lk(v->mu);
     DeviceGuard dg(v->device);
     mb::ViewTable vt;
-    if ((st = build_views(views, n_views, vt)) != MBOIT_OK) return st;
+    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set))) != MBOIT_OK) return st;
     std::vector<int32_t> list;
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, nullptr, 0, list, &mask)) != MBOIT_OK) return st;
@@ -657,7 +705,7 @@ mboit_status mboit_render_frame_host(mboit_volume v, const float* field_host, co
     if (st != MBOIT_OK) return st;
     if (!field_host || !rgba_host || !rgba_device) return fail(MBOIT_ERR_INVALID_ARG, "NULL buffer");
     mb::ViewTable vt;
-    if ((st = build_views(views, n_views, vt)) != MBOIT_OK) return st;
+    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set))) != MBOIT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     {
         DeviceGuard dg(v->device);
@@ -715,7 +763,7 @@ mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int3
     std::lock_guard<std::mutex> lk(v->mu);
     DeviceGuard dg(v->device);
     mb::ViewTable vt;
-    if ((st = build_views(views, n_views, vt)) != MBOIT_OK) return st;
+    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set))) != MBOIT_OK) return st;
     int64_t total_px = 0;
     for (int i = 0; i < n_views; ++i) total_px += (int64_t)views[i].width * views[i].height;
     const int32_t K = (int32_t)v->boxes.size();
@@ -784,7 +832,7 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
     std::lock_guard<std::mutex> lk(v->mu);
     DeviceGuard dg(v->device);
     mb::ViewTable vt;
-    if ((st = build_views(views, n_views, vt)) != MBOIT_OK) return st;
+    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set))) != MBOIT_OK) return st;
     std::vector<int32_t> list;
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, nullptr, 0, list, &mask)) != MBOIT_OK) return st;

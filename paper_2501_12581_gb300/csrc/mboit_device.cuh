@@ -123,6 +123,16 @@ struct ViewD {
     float warp_a, warp_b;  // warped depth z = clamp(warp_a * log2(t) + warp_b, -1, 1)
 };
 
+// Trigonometric moments: coefficients of s^m in (s + i)^k (s - i)^(n-k)
+// (k, m = 0..n, filled on the host) and the angle mapping.
+struct TrigTables {
+    float er[5][5], ei[5][5];
+    float zone_scale;     // phi = z * zone_scale = z (1 - zeta) pi
+    float beta;
+    int32_t n;            // 3 or 4 complex moments (0: power moments)
+    int32_t storage;      // 1 float16, 2 bfloat16
+};
+
 struct GridD {
     const float* field;           // [nz][ny][nx]
     int32_t nx, ny, nz;
@@ -134,6 +144,7 @@ struct GridD {
     float moment_bias, overestimation;
     float bias_vector[4];
     uint32_t flags;
+    TrigTables trig;
 };
 
 // ---------------------------------------------------------------------------

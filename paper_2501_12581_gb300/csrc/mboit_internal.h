@@ -108,7 +108,8 @@ cudaError_t launch_sortlast_march(bool fill, const AmrD& a, const float4* tf, co
                                   int32_t n_slots, int32_t* counts, const int64_t* starts, int32_t* seg_key,
                                   float4* seg_col, cudaStream_t s);
 // Image-space reductions.
-cudaError_t launch_moments_sum(const ViewTable& vt, int32_t n_inputs, const void* in, void* out, cudaStream_t s);
+cudaError_t launch_moments_sum(const GridD& g, const ViewTable& vt, int32_t n_inputs, const void* in, void* out,
+                               cudaStream_t s);
 cudaError_t launch_color_resolve(const ViewTable& vt, int32_t n_inputs, const float* in, float* out,
                                  const void* moments, float4 bg, int32_t raw_sum, cudaStream_t s);
 

@@ -26,7 +26,11 @@
 #include <mutex>
 #include <utility>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "mboit_internal.h"
+#include "mboit_trig.cuh"
 
 namespace mb {
 
@@ -300,6 +304,9 @@ struct MomentBody {
         m4 = ffma(az2 * z, z, m4);
         ++n;
     }
+    __device__ __forceinline__ void store(const GridD&, char* base, const ViewSlot& S, int64_t off, int pix) {
+        store_moments(base, S, off, pix, m0, m1, m2, m3, m4);
+    }
 };
 
 // Alg. 1 loop 2 per sample: colour += T(z) * alpha * (r, g, b, 1).
@@ -307,6 +314,7 @@ struct BlendBody {
     const float4* s_tf;   // [2*i] = entry i (r, g, b, sigma*step), [2*i+1] = entry i+1 minus entry i
     Frame F;
     float tf_scale, tf_bias, amax, wa, wb, w0;
+    float b0;
     float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     unsigned n = 0;
     __device__ __forceinline__ void operator()(float t, float val) {
@@ -324,7 +332,172 @@ struct BlendBody {
         C.w += wgt;
         ++n;
     }
+    __device__ __forceinline__ bool singular() const { return F.kind == kFrameOneAtom || F.kind == kFrameTwoAtoms; }
 };
+
+// Bytes of one moment slab of P pixels in the volume's format.
+__device__ __forceinline__ int64_t slab_bytes(const GridD& g, int plane) {
+    return g.trig.n ? (int64_t)(4 + 4 * g.trig.n) * plane : (int64_t)20 * plane;
+}
+
+__device__ __forceinline__ uint32_t pack16(const GridD& g, float x, float y) {
+    if (g.trig.storage == 2) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+    const __half2 h = __floats2half2_rn(x, y);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__device__ __forceinline__ cf unpack16(const GridD& g, uint32_t bits) {
+    if (g.trig.storage == 2) {
+        const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&bits);
+        return {__low2float(h), __high2float(h)};
+    }
+    const __half2 h = *reinterpret_cast<const __half2*>(&bits);
+    return {__low2float(h), __high2float(h)};
+}
+
+// Trigonometric moment slab: b0 plane (float), then plane j of tau_j = t_j / b0
+// as a 16-bit pair.
+__device__ __forceinline__ void store_trig(const GridD& g, char* base, const ViewSlot& S, int64_t slab_off, int pix,
+                                           float m0, const cf* t, int n) {
+    char* slab = base + slab_off;
+    reinterpret_cast<float*>(slab)[pix] = m0;
+    const float inv = m0 > 0.0f ? 1.0f / m0 : 0.0f;
+    for (int j = 0; j < n; ++j)
+        reinterpret_cast<uint32_t*>(slab + (size_t)4 * S.plane * (1 + j))[pix] = pack16(g, t[j].x * inv, t[j].y * inv);
+}
+
+__device__ __forceinline__ float load_trig(const GridD& g, const char* base, const ViewSlot& S, int64_t slab_off,
+                                           int pix, cf* tau, int n) {
+    const char* slab = base + slab_off;
+    for (int j = 0; j < n; ++j)
+        tau[j] = unpack16(g, __ldg(reinterpret_cast<const uint32_t*>(slab + (size_t)4 * S.plane * (1 + j)) + pix));
+    return __ldg(reinterpret_cast<const float*>(slab) + pix);
+}
+
+// Pass 1 with trigonometric moments: b0 += a, t_j += a e^{i j phi}.
+template <int N>
+struct TrigMomentBody {
+    const float2* s_sig;
+    float tf_scale, tf_bias, amax, wa, wb, zs;
+    float m0 = 0.0f;
+    cf t[N];
+    unsigned n = 0;
+    __device__ __forceinline__ void operator()(float tt, float val) {
+        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+        const int i = (int)xt;
+        const float f = xt - (float)i;
+        const float2 s = s_sig[i];
+        const float a = fmin_(ffma(f, s.y, s.x), amax);
+        const float phi = warp_depth(tt, wa, wb) * zs;
+        float sn, cs;
+        __sincosf(phi, &sn, &cs);
+        const cf u = {cs, sn};
+        cf p = u;
+        m0 += a;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            if (j > 0) p = cmul(p, u);
+            t[j].x = ffma(a, p.x, t[j].x);
+            t[j].y = ffma(a, p.y, t[j].y);
+        }
+        ++n;
+    }
+    __device__ __forceinline__ void store(const GridD& g, char* base, const ViewSlot& S, int64_t off, int pix) {
+        store_trig(g, base, S, off, pix, m0, t, N);
+    }
+};
+
+// Pass 2 with trigonometric moments.
+template <int N>
+struct TrigBlendBody {
+    const float4* s_tf;
+    const TrigTables* T;
+    TrigFrame F;
+    float tf_scale, tf_bias, amax, wa, wb, w0;
+    float b0;
+    float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    unsigned n = 0;
+    __device__ __forceinline__ void operator()(float t, float val) {
+        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+        const int i = (int)xt;
+        const float f = xt - (float)i;
+        const float4 e0 = s_tf[2 * i], de = s_tf[2 * i + 1];
+        const float a = fmin_(ffma(f, de.w, e0.w), amax);
+        const float alpha = one_minus_exp_neg(a);
+        const float z = warp_depth(t, wa, wb);
+        const float A = trig_fraction<N>(F, *T, z, w0);
+        const float wgt = fclamp(fexp2(-F.m0_log2e * A), 0.0f, 1.0f) * alpha;
+        C.x = ffma(wgt, ffma(f, de.x, e0.x), C.x);
+        C.y = ffma(wgt, ffma(f, de.y, e0.y), C.y);
+        C.z = ffma(wgt, ffma(f, de.z, e0.z), C.z);
+        C.w += wgt;
+        ++n;
+    }
+    __device__ __forceinline__ bool singular() const { return b0 > 0.0f && F.n == 0; }
+};
+
+template <int MS> struct Bodies;
+template <> struct Bodies<0> {
+    using Moment = MomentBody;
+    using Blend = BlendBody;
+};
+template <> struct Bodies<3> {
+    using Moment = TrigMomentBody<3>;
+    using Blend = TrigBlendBody<3>;
+};
+template <> struct Bodies<4> {
+    using Moment = TrigMomentBody<4>;
+    using Blend = TrigBlendBody<4>;
+};
+
+template <int MS>
+__device__ __forceinline__ typename Bodies<MS>::Moment make_moment_body(const float2* s_sig, const GridD& g,
+                                                                        const ViewD& v) {
+    typename Bodies<MS>::Moment b;
+    b.s_sig = s_sig;
+    b.tf_scale = g.tf_scale;
+    b.tf_bias = g.tf_bias;
+    b.amax = g.absorbance_max;
+    b.wa = v.warp_a;
+    b.wb = v.warp_b;
+    if constexpr (MS != 0) {
+        b.zs = g.trig.zone_scale;
+        for (int j = 0; j < MS; ++j) b.t[j] = {0.0f, 0.0f};
+    }
+    return b;
+}
+
+// Loads the pixel's global moments (if `valid`) and builds the reconstruction.
+template <int MS>
+__device__ __forceinline__ typename Bodies<MS>::Blend make_blend_body(const float4* s_tf, const GridD& g, const ViewSlot& S,
+                                                                      const char* moments, int64_t off, int pix,
+                                                                      bool valid) {
+    typename Bodies<MS>::Blend b;
+    b.s_tf = s_tf;
+    b.tf_scale = g.tf_scale;
+    b.tf_bias = g.tf_bias;
+    b.amax = g.absorbance_max;
+    b.wa = S.v.warp_a;
+    b.wb = S.v.warp_b;
+    b.w0 = g.overestimation;
+    if constexpr (MS == 0) {
+        float m[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (valid) load_moments(moments, S, off, pix, m);
+        b.F = make_frame(m, g.moment_bias, g.bias_vector);
+        b.b0 = m[0];
+    } else {
+        cf tau[MS];
+        for (int j = 0; j < MS; ++j) tau[j] = {0.0f, 0.0f};
+        b.b0 = valid ? load_trig(g, moments, S, off, pix, tau, MS) : 0.0f;
+        b.T = &g.trig;
+        b.F = make_trig_frame(b.b0, tau, MS, g.trig.beta);
+    }
+    return b;
+}
+
 
 // Pops the next 8x4 ray tile of the work queue; returns false when empty.
 __device__ __forceinline__ bool next_tile(const ViewTable& vt, int32_t* head, int& vi, int& px, int& py) {
@@ -371,7 +544,7 @@ __device__ __forceinline__ void ray_range(const GridD& g, const ViewD& V, bool v
     }
 }
 
-template <bool kSel, class Cfg>
+template <bool kSel, class Cfg, int MS>
 __global__ void __launch_bounds__(256) k_pass1_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
                                                      const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                      char* __restrict__ moments, Counters* __restrict__ ctr) {
@@ -390,15 +563,14 @@ __global__ void __launch_bounds__(256) k_pass1_fused(const __grid_constant__ Gri
         float o[3], d[3];
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
-        MomentBody body{s_sig, g.tf_scale, g.tf_bias, g.absorbance_max, S.v.warp_a, S.v.warp_b};
+        auto body = make_moment_body<MS>(s_sig, g, S.v);
         march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
-        if (valid)
-            store_moments(moments, S, S.moment_off, py * S.v.width + px, body.m0, body.m1, body.m2, body.m3, body.m4);
+        if (valid) body.store(g, moments, S, S.moment_off, py * S.v.width + px);
         warp_add_u64(&ctr->samples[0], body.n);
     }
 }
 
-template <bool kSel, class Cfg>
+template <bool kSel, class Cfg, int MS>
 __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
                                                      const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                      const char* __restrict__ moments, float* __restrict__ color,
@@ -418,11 +590,8 @@ __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ Gri
         const ViewSlot& S = vt.s[vi];
         const bool valid = px < S.v.width && py < S.v.height;
         const int pix = valid ? py * S.v.width + px : 0;
-        float m[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        if (valid) load_moments(moments, S, S.moment_off, pix, m);
-        BlendBody body{s_tf, make_frame(m, g.moment_bias, g.bias_vector), g.tf_scale, g.tf_bias, g.absorbance_max,
-                       S.v.warp_a, S.v.warp_b, g.overestimation};
-        if (valid && (body.F.kind == kFrameOneAtom || body.F.kind == kFrameTwoAtoms)) atomicAdd(&ctr->singular, 1ull);
+        auto body = make_blend_body<MS>(s_tf, g, S, moments, S.moment_off, pix, valid);
+        if (valid && body.singular()) atomicAdd(&ctr->singular, 1ull);
         float o[3], d[3];
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
@@ -430,7 +599,7 @@ __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ Gri
         if (valid) {
             float4* out = reinterpret_cast<float4*>(color + S.color_off) + pix;
             if (mode == kColorResolved)
-                *out = resolve_pixel(body.C, m[0], make_float4(0.0f, 0.0f, 0.0f, 0.0f), raw);
+                *out = resolve_pixel(body.C, body.b0, make_float4(0.0f, 0.0f, 0.0f, 0.0f), raw);
             else
                 *out = body.C;
         }
@@ -536,14 +705,18 @@ __device__ __forceinline__ bool piece_sample(const V& vol, const int32_t* __rest
     return true;
 }
 
-template <class V>
+template <class V, int MS>
 __global__ void __launch_bounds__(128) k_pass1_piece(const __grid_constant__ V vol, const float4* __restrict__ tf,
-                                                     const int32_t* __restrict__ pob, int piece, const __grid_constant__ PieceBox box,
+                                                     const int32_t* __restrict__ pob, int piece,
+                                                     const __grid_constant__ PieceBox box,
                                                      const __grid_constant__ ViewTable vt, int slot, int n_slots,
                                                      char* __restrict__ moments, Counters* __restrict__ ctr) {
     const GridD& g = common(vol);
-    __shared__ float s_sig[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_sig[i] = tf[i].w;
+    __shared__ float2 s_sig[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const float s0 = tf[i].w;
+        s_sig[i] = make_float2(s0, i < 255 ? tf[i + 1].w - s0 : 0.0f);
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -555,53 +728,40 @@ __global__ void __launch_bounds__(128) k_pass1_piece(const __grid_constant__ V v
     const int py = (lt / S.ntx) * kTileH + (lane >> 3);
     unsigned n = 0;
     if (px < S.v.width && py < S.v.height) {
-        float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f;
+        auto body = make_moment_body<MS>(s_sig, g, S.v);
         float o[3], d[3];
         make_ray(S.v, px, py, o, d);
         int k0, k1;
         if (lattice_range(o, d, box.lo, box.hi, g.step, &k0, &k1)) {
-            const float wa = S.v.warp_a, wb = S.v.warp_b;
             for (int k = k0; k <= k1;) {
                 const float t = lattice_t(k, g.step);
                 float val;
                 int kn;
-                if (!piece_sample(vol, pob, piece, t, o, d, k, val, kn)) {
-                    k = kn;
-                    continue;
-                }
+                const bool owned = piece_sample(vol, pob, piece, t, o, d, k, val, kn);
                 k = kn;
-                int i;
-                const float f = tf_coord(g, val, i);
-                const float s0 = s_sig[i], s1 = s_sig[i + 1];
-                const float a = fmin_(ffma(f, s1 - s0, s0), g.absorbance_max);
-                const float z = warp_depth(t, wa, wb);
-                m0 += a;
-                float az = a * z;
-                m1 += az;
-                az *= z;
-                m2 += az;
-                az *= z;
-                m3 += az;
-                az *= z;
-                m4 += az;
-                ++n;
+                if (owned) body(t, val);
             }
         }
-        const int64_t slab = (int64_t)20 * S.plane;
-        store_moments(moments, S, S.moment_off * n_slots + slot * slab, py * S.v.width + px, m0, m1, m2, m3, m4);
+        n = body.n;
+        body.store(g, moments, S, S.moment_off * n_slots + slot * slab_bytes(g, S.plane), py * S.v.width + px);
     }
     warp_add_u64(&ctr->samples[0], n);
 }
 
-template <class V>
+template <class V, int MS>
 __global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ V vol, const float4* __restrict__ tf,
-                                                     const int32_t* __restrict__ pob, int piece, const __grid_constant__ PieceBox box,
+                                                     const int32_t* __restrict__ pob, int piece,
+                                                     const __grid_constant__ PieceBox box,
                                                      const __grid_constant__ ViewTable vt, int slot, int n_slots,
                                                      const char* __restrict__ moments, float* __restrict__ color,
                                                      Counters* __restrict__ ctr) {
     const GridD& g = common(vol);
-    __shared__ float4 s_tf[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = tf[i];
+    __shared__ float4 s_tf[512];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const float4 e0 = tf[i], e1 = i < 255 ? tf[i + 1] : tf[i];
+        s_tf[2 * i] = e0;
+        s_tf[2 * i + 1] = make_float4(e1.x - e0.x, e1.y - e0.y, e1.z - e0.z, e1.w - e0.w);
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -611,7 +771,6 @@ __global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ V v
     const int lt = tile - S.tile_base;
     const int px = (lt % S.ntx) * kTileW + (lane & 7);
     const int py = (lt / S.ntx) * kTileH + (lane >> 3);
-    const float w0 = g.overestimation;
     unsigned n = 0;
     if (px < S.v.width && py < S.v.height) {
         const int pix = py * S.v.width + px;
@@ -620,32 +779,17 @@ __global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ V v
         make_ray(S.v, px, py, o, d);
         int k0, k1;
         if (lattice_range(o, d, box.lo, box.hi, g.step, &k0, &k1)) {
-            float m[5];
-            load_moments(moments, S, S.moment_off, pix, m);
-            const Frame F = make_frame(m, g.moment_bias, g.bias_vector);
-            const float wa = S.v.warp_a, wb = S.v.warp_b;
+            auto body = make_blend_body<MS>(s_tf, g, S, moments, S.moment_off, pix, true);
             for (int k = k0; k <= k1;) {
                 const float t = lattice_t(k, g.step);
                 float val;
                 int kn;
-                if (!piece_sample(vol, pob, piece, t, o, d, k, val, kn)) {
-                    k = kn;
-                    continue;
-                }
+                const bool owned = piece_sample(vol, pob, piece, t, o, d, k, val, kn);
                 k = kn;
-                int i;
-                const float f = tf_coord(g, val, i);
-                const float4 e0 = s_tf[i], e1 = s_tf[i + 1];
-                const float a = fmin_(ffma(f, e1.w - e0.w, e0.w), g.absorbance_max);
-                const float alpha = one_minus_exp_neg(a);
-                const float z = warp_depth(t, wa, wb);
-                const float wgt = transmittance(F, z, w0) * alpha;
-                C.x = ffma(wgt, ffma(f, e1.x - e0.x, e0.x), C.x);
-                C.y = ffma(wgt, ffma(f, e1.y - e0.y, e0.y), C.y);
-                C.z = ffma(wgt, ffma(f, e1.z - e0.z, e0.z), C.z);
-                C.w += wgt;
-                ++n;
+                if (owned) body(t, val);
             }
+            C = body.C;
+            n = body.n;
         }
         const int64_t img = (int64_t)4 * S.v.width * S.v.height;
         reinterpret_cast<float4*>(color + S.color_off * n_slots + slot * img)[pix] = C;
@@ -673,7 +817,7 @@ __device__ __forceinline__ void march_amr(const AmrD& a, const uint8_t* __restri
     }
 }
 
-template <bool kSel>
+template <bool kSel, int MS>
 __global__ void __launch_bounds__(256) k_pass1_amr(const __grid_constant__ AmrD a, const float4* __restrict__ tf,
                                                    const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                    char* __restrict__ moments, Counters* __restrict__ ctr) {
@@ -691,15 +835,14 @@ __global__ void __launch_bounds__(256) k_pass1_amr(const __grid_constant__ AmrD 
         float o[3], d[3];
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
-        MomentBody body{s_sig, g.tf_scale, g.tf_bias, g.absorbance_max, S.v.warp_a, S.v.warp_b};
+        auto body = make_moment_body<MS>(s_sig, g, S.v);
         march_amr<kSel>(a, sel, o, d, k0, k1, body);
-        if (valid)
-            store_moments(moments, S, S.moment_off, py * S.v.width + px, body.m0, body.m1, body.m2, body.m3, body.m4);
+        if (valid) body.store(g, moments, S, S.moment_off, py * S.v.width + px);
         warp_add_u64(&ctr->samples[0], body.n);
     }
 }
 
-template <bool kSel>
+template <bool kSel, int MS>
 __global__ void __launch_bounds__(256) k_pass2_amr(const __grid_constant__ AmrD a, const float4* __restrict__ tf,
                                                    const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                    const char* __restrict__ moments, float* __restrict__ color, int mode,
@@ -718,18 +861,15 @@ __global__ void __launch_bounds__(256) k_pass2_amr(const __grid_constant__ AmrD 
         const ViewSlot& S = vt.s[vi];
         const bool valid = px < S.v.width && py < S.v.height;
         const int pix = valid ? py * S.v.width + px : 0;
-        float m[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        if (valid) load_moments(moments, S, S.moment_off, pix, m);
-        BlendBody body{s_tf, make_frame(m, g.moment_bias, g.bias_vector), g.tf_scale, g.tf_bias, g.absorbance_max,
-                       S.v.warp_a, S.v.warp_b, g.overestimation};
-        if (valid && (body.F.kind == kFrameOneAtom || body.F.kind == kFrameTwoAtoms)) atomicAdd(&ctr->singular, 1ull);
+        auto body = make_blend_body<MS>(s_tf, g, S, moments, S.moment_off, pix, valid);
+        if (valid && body.singular()) atomicAdd(&ctr->singular, 1ull);
         float o[3], d[3];
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
         march_amr<kSel>(a, sel, o, d, k0, k1, body);
         if (valid) {
             float4* out = reinterpret_cast<float4*>(color + S.color_off) + pix;
-            *out = mode == kColorResolved ? resolve_pixel(body.C, m[0], make_float4(0.0f, 0.0f, 0.0f, 0.0f), raw)
+            *out = mode == kColorResolved ? resolve_pixel(body.C, body.b0, make_float4(0.0f, 0.0f, 0.0f, 0.0f), raw)
                                           : body.C;
         }
         warp_add_u64(&ctr->samples[1], body.n);
@@ -1013,6 +1153,33 @@ __global__ void k_moments_sum(const float4* __restrict__ in, float4* __restrict_
     }
 }
 
+// Trigonometric slabs: per pixel sum b0 and b0 * tau_j over the inputs
+// (compensated), then renormalise and round to the storage format again.
+template <int N>
+__global__ void k_moments_sum_trig(const __grid_constant__ GridD g, const char* __restrict__ in, char* __restrict__ out,
+                                   int64_t plane, int64_t npix, int n_inputs) {
+    const int64_t slab = (int64_t)(4 + 4 * N) * plane;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
+        Neumaier b0;
+        Neumaier tr[N], ti[N];
+        for (int j = 0; j < n_inputs; ++j) {
+            const char* sl = in + j * slab;
+            const float m0 = __ldg(reinterpret_cast<const float*>(sl) + i);
+            b0.add(m0);
+            for (int k = 0; k < N; ++k) {
+                const cf t = unpack16(g, __ldg(reinterpret_cast<const uint32_t*>(sl + 4 * plane * (1 + k)) + i));
+                tr[k].add(t.x * m0);
+                ti[k].add(t.y * m0);
+            }
+        }
+        const float m0 = b0.get();
+        const float inv = m0 > 0.0f ? 1.0f / m0 : 0.0f;
+        reinterpret_cast<float*>(out)[i] = m0;
+        for (int k = 0; k < N; ++k)
+            reinterpret_cast<uint32_t*>(out + 4 * plane * (1 + k))[i] = pack16(g, tr[k].get() * inv, ti[k].get() * inv);
+    }
+}
+
 __global__ void k_color_resolve(const float4* __restrict__ in, float4* __restrict__ out, const float* __restrict__ b0,
                                 int64_t npix, int n_inputs, float4 bg, int raw) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1046,26 +1213,49 @@ int persistent_blocks(const void* fn, int threads, size_t smem) {
     return nb;
 }
 
-const void* pass1_fn(int cfg, bool sel) {
-    if (sel) return (const void*)k_pass1_fused<true, Stage0>;
+template <int MS>
+const void* pass1_fn_ms(int cfg, bool sel) {
+    if (sel) return (const void*)k_pass1_fused<true, Stage0, MS>;
+    if constexpr (MS != 0) return cfg == 3 ? (const void*)k_pass1_fused<false, Stage3, MS>
+                                           : (const void*)k_pass1_fused<false, Stage0, MS>;
     switch (cfg) {
-        case 1: return (const void*)k_pass1_fused<false, Stage1>;
-        case 2: return (const void*)k_pass1_fused<false, Stage2>;
-        case 3: return (const void*)k_pass1_fused<false, Stage3>;
-        case 4: return (const void*)k_pass1_fused<false, Stage4>;
-        default: return (const void*)k_pass1_fused<false, Stage0>;
+        case 1: return (const void*)k_pass1_fused<false, Stage1, MS>;
+        case 2: return (const void*)k_pass1_fused<false, Stage2, MS>;
+        case 3: return (const void*)k_pass1_fused<false, Stage3, MS>;
+        case 4: return (const void*)k_pass1_fused<false, Stage4, MS>;
+        default: return (const void*)k_pass1_fused<false, Stage0, MS>;
     }
 }
 
-const void* pass2_fn(int cfg, bool sel) {
-    if (sel) return (const void*)k_pass2_fused<true, Stage0>;
+template <int MS>
+const void* pass2_fn_ms(int cfg, bool sel) {
+    if (sel) return (const void*)k_pass2_fused<true, Stage0, MS>;
+    if constexpr (MS != 0) return cfg == 3 ? (const void*)k_pass2_fused<false, Stage3, MS>
+                                           : (const void*)k_pass2_fused<false, Stage0, MS>;
     switch (cfg) {
-        case 1: return (const void*)k_pass2_fused<false, Stage1>;
-        case 2: return (const void*)k_pass2_fused<false, Stage2>;
-        case 3: return (const void*)k_pass2_fused<false, Stage3>;
-        case 4: return (const void*)k_pass2_fused<false, Stage4>;
-        default: return (const void*)k_pass2_fused<false, Stage0>;
+        case 1: return (const void*)k_pass2_fused<false, Stage1, MS>;
+        case 2: return (const void*)k_pass2_fused<false, Stage2, MS>;
+        case 3: return (const void*)k_pass2_fused<false, Stage3, MS>;
+        case 4: return (const void*)k_pass2_fused<false, Stage4, MS>;
+        default: return (const void*)k_pass2_fused<false, Stage0, MS>;
     }
+}
+
+const void* pass1_fn(int cfg, bool sel, int ms) {
+    return ms == 3 ? pass1_fn_ms<3>(cfg, sel) : ms == 4 ? pass1_fn_ms<4>(cfg, sel) : pass1_fn_ms<0>(cfg, sel);
+}
+const void* pass2_fn(int cfg, bool sel, int ms) {
+    return ms == 3 ? pass2_fn_ms<3>(cfg, sel) : ms == 4 ? pass2_fn_ms<4>(cfg, sel) : pass2_fn_ms<0>(cfg, sel);
+}
+const void* amr1_fn(bool sel, int ms) {
+    if (ms == 3) return sel ? (const void*)k_pass1_amr<true, 3> : (const void*)k_pass1_amr<false, 3>;
+    if (ms == 4) return sel ? (const void*)k_pass1_amr<true, 4> : (const void*)k_pass1_amr<false, 4>;
+    return sel ? (const void*)k_pass1_amr<true, 0> : (const void*)k_pass1_amr<false, 0>;
+}
+const void* amr2_fn(bool sel, int ms) {
+    if (ms == 3) return sel ? (const void*)k_pass2_amr<true, 3> : (const void*)k_pass2_amr<false, 3>;
+    if (ms == 4) return sel ? (const void*)k_pass2_amr<true, 4> : (const void*)k_pass2_amr<false, 4>;
+    return sel ? (const void*)k_pass2_amr<true, 0> : (const void*)k_pass2_amr<false, 0>;
 }
 
 bool vec_config(int cfg) { return cfg == 2 || cfg == 3 || cfg == 4; }
@@ -1074,6 +1264,7 @@ bool vec_config(int cfg) { return cfg == 2 || cfg == 3 || cfg == 4; }
 
 bool stage_config_eligible(const GridD& g, int cfg) {
     if (cfg < 0 || cfg >= kNumStageConfigs) return false;
+    if (g.trig.n != 0 && cfg != 0 && cfg != 3) return false;
     if (!vec_config(cfg)) return true;
     return g.nx % 4 == 0 && g.nx >= 4 && (reinterpret_cast<uintptr_t>(g.field) & 15u) == 0;
 }
@@ -1081,10 +1272,13 @@ bool stage_config_eligible(const GridD& g, int cfg) {
 cudaError_t prepare_kernels() {
     // Loads every kernel and fills the occupancy cache, so that no module
     // loading happens later inside a stream capture.
-    const void* fns[] = {(const void*)k_pass1_piece<GridD>, (const void*)k_pass2_piece<GridD>,
-                         (const void*)k_pass1_piece<AmrD>, (const void*)k_pass2_piece<AmrD>,
-                         (const void*)k_pass1_amr<true>, (const void*)k_pass1_amr<false>,
-                         (const void*)k_pass2_amr<true>, (const void*)k_pass2_amr<false>,
+    const void* fns[] = {(const void*)k_pass1_piece<GridD, 0>, (const void*)k_pass2_piece<GridD, 0>,
+                         (const void*)k_pass1_piece<GridD, 3>, (const void*)k_pass2_piece<GridD, 3>,
+                         (const void*)k_pass1_piece<GridD, 4>, (const void*)k_pass2_piece<GridD, 4>,
+                         (const void*)k_pass1_piece<AmrD, 0>, (const void*)k_pass2_piece<AmrD, 0>,
+                         (const void*)k_pass1_piece<AmrD, 3>, (const void*)k_pass2_piece<AmrD, 3>,
+                         (const void*)k_pass1_piece<AmrD, 4>, (const void*)k_pass2_piece<AmrD, 4>,
+                         (const void*)k_moments_sum_trig<3>, (const void*)k_moments_sum_trig<4>,
                          (const void*)k_moments_sum,        (const void*)k_color_resolve,
                          (const void*)k_sortlast_piece<GridD, true>, (const void*)k_sortlast_piece<GridD, false>,
                          (const void*)k_sortlast_piece<AmrD, true>, (const void*)k_sortlast_piece<AmrD, false>,
@@ -1096,19 +1290,24 @@ cudaError_t prepare_kernels() {
         const cudaError_t e = cudaFuncGetAttributes(&a, f);
         if (e != cudaSuccess) return e;
     }
-    for (int cfg = 0; cfg < kNumStageConfigs; ++cfg)
+    const int sets[3] = {0, 3, 4};
+    for (int ms : sets)
+        for (int cfg = 0; cfg < kNumStageConfigs; ++cfg)
+            for (int sel = 0; sel < 2; ++sel) {
+                const void* f1 = pass1_fn(cfg, sel, ms);
+                const void* f2 = pass2_fn(cfg, sel, ms);
+                cudaFuncAttributes a;
+                cudaError_t e = cudaFuncGetAttributes(&a, f1);
+                if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, f2);
+                if (e != cudaSuccess) return e;
+                persistent_blocks(f1, 256, 0);
+                persistent_blocks(f2, 256, 0);
+            }
+    for (int ms : sets)
         for (int sel = 0; sel < 2; ++sel) {
-            cudaFuncAttributes a;
-            cudaError_t e = cudaFuncGetAttributes(&a, pass1_fn(cfg, sel));
-            if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, pass2_fn(cfg, sel));
-            if (e != cudaSuccess) return e;
-            persistent_blocks(pass1_fn(cfg, sel), 256, 0);
-            persistent_blocks(pass2_fn(cfg, sel), 256, 0);
+            persistent_blocks(amr1_fn(sel, ms), 256, 0);
+            persistent_blocks(amr2_fn(sel, ms), 256, 0);
         }
-    persistent_blocks((const void*)k_pass1_amr<true>, 256, 0);
-    persistent_blocks((const void*)k_pass1_amr<false>, 256, 0);
-    persistent_blocks((const void*)k_pass2_amr<true>, 256, 0);
-    persistent_blocks((const void*)k_pass2_amr<false>, 256, 0);
     return cudaGetLastError();
 }
 
@@ -1117,7 +1316,7 @@ cudaError_t launch_pass1_fused(const GridD& g, const float4* tf, const uint8_t* 
     if (!stage_config_eligible(g, cfg)) cfg = 0;
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const void* fn = pass1_fn(cfg, brick_sel != nullptr);
+    const void* fn = pass1_fn(cfg, brick_sel != nullptr, g.trig.n);
     char* m = static_cast<char*>(moments);
     void* args[] = {(void*)&g, (void*)&tf, (void*)&brick_sel, (void*)&vt, (void*)&m, (void*)&ctr};
     return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
@@ -1129,7 +1328,7 @@ cudaError_t launch_pass2_fused(const GridD& g, const float4* tf, const uint8_t* 
     if (!stage_config_eligible(g, cfg)) cfg = 0;
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[1], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const void* fn = pass2_fn(cfg, brick_sel != nullptr);
+    const void* fn = pass2_fn(cfg, brick_sel != nullptr, g.trig.n);
     const char* m = static_cast<const char*>(moments);
     int md = mode;
     void* args[] = {(void*)&g, (void*)&tf, (void*)&brick_sel, (void*)&vt, (void*)&m, (void*)&color, (void*)&md,
@@ -1141,7 +1340,10 @@ cudaError_t launch_pass1_piece(const GridD& g, const float4* tf, const int32_t* 
                                const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
                                void* moments, Counters* ctr, cudaStream_t s) {
     const int blocks = (vt.total_tiles + 3) / 4;
-    k_pass1_piece<GridD><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, static_cast<char*>(moments), ctr);
+    char* m = static_cast<char*>(moments);
+    if (g.trig.n == 3) k_pass1_piece<GridD, 3><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, m, ctr);
+    else if (g.trig.n == 4) k_pass1_piece<GridD, 4><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, m, ctr);
+    else k_pass1_piece<GridD, 0><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, m, ctr);
     return cudaGetLastError();
 }
 
@@ -1149,14 +1351,28 @@ cudaError_t launch_pass2_piece(const GridD& g, const float4* tf, const int32_t* 
                                const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
                                const void* moments, float* color, Counters* ctr, cudaStream_t s) {
     const int blocks = (vt.total_tiles + 3) / 4;
-    k_pass2_piece<GridD><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots,
-                                         static_cast<const char*>(moments), color, ctr);
+    const char* m = static_cast<const char*>(moments);
+    if (g.trig.n == 3) k_pass2_piece<GridD, 3><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, m, color, ctr);
+    else if (g.trig.n == 4) k_pass2_piece<GridD, 4><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, m, color, ctr);
+    else k_pass2_piece<GridD, 0><<<blocks, 128, 0, s>>>(g, tf, pob, piece, box, vt, slot, n_slots, m, color, ctr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments_sum(const ViewTable& vt, int32_t n_inputs, const void* in, void* out, cudaStream_t s) {
+cudaError_t launch_moments_sum(const GridD& g, const ViewTable& vt, int32_t n_inputs, const void* in, void* out,
+                               cudaStream_t s) {
     for (int v = 0; v < vt.n; ++v) {
         const ViewSlot& S = vt.s[v];
+        if (g.trig.n) {
+            const int64_t npix = (int64_t)S.v.width * S.v.height;
+            const char* src = static_cast<const char*>(in) + S.moment_off * n_inputs;
+            char* dst = static_cast<char*>(out) + S.moment_off;
+            const int blocks = (int)((npix + 255) / 256 < 4096 ? (npix + 255) / 256 : 4096);
+            if (g.trig.n == 3)
+                k_moments_sum_trig<3><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(g, src, dst, S.plane, npix, n_inputs);
+            else
+                k_moments_sum_trig<4><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(g, src, dst, S.plane, npix, n_inputs);
+            continue;
+        }
         const int64_t n4 = (int64_t)5 * S.plane / 4;
         const float4* src = reinterpret_cast<const float4*>(static_cast<const char*>(in) + S.moment_off * n_inputs);
         float4* dst = reinterpret_cast<float4*>(static_cast<char*>(out) + S.moment_off);
@@ -1218,7 +1434,7 @@ cudaError_t launch_pass1_amr(const AmrD& a, const float4* tf, const uint8_t* uni
                              void* moments, Counters* ctr, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const void* fn = unit_sel ? (const void*)k_pass1_amr<true> : (const void*)k_pass1_amr<false>;
+    const void* fn = amr1_fn(unit_sel != nullptr, a.g.trig.n);
     char* m = static_cast<char*>(moments);
     void* args[] = {(void*)&a, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&m, (void*)&ctr};
     return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
@@ -1228,7 +1444,7 @@ cudaError_t launch_pass2_amr(const AmrD& a, const float4* tf, const uint8_t* uni
                              const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[1], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const void* fn = unit_sel ? (const void*)k_pass2_amr<true> : (const void*)k_pass2_amr<false>;
+    const void* fn = amr2_fn(unit_sel != nullptr, a.g.trig.n);
     const char* m = static_cast<const char*>(moments);
     int md = mode;
     void* args[] = {(void*)&a, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&m, (void*)&color, (void*)&md,
@@ -1240,8 +1456,10 @@ cudaError_t launch_pass1_piece(const AmrD& a, const float4* tf, const int32_t* p
                                const ViewTable& vt, int32_t slot, int32_t n_slots, void* moments, Counters* ctr,
                                cudaStream_t s) {
     const int blocks = (vt.total_tiles + 3) / 4;
-    k_pass1_piece<AmrD><<<blocks, 128, 0, s>>>(a, tf, pou, piece, box, vt, slot, n_slots, static_cast<char*>(moments),
-                                               ctr);
+    char* m = static_cast<char*>(moments);
+    if (a.g.trig.n == 3) k_pass1_piece<AmrD, 3><<<blocks, 128, 0, s>>>(a, tf, pou, piece, box, vt, slot, n_slots, m, ctr);
+    else if (a.g.trig.n == 4) k_pass1_piece<AmrD, 4><<<blocks, 128, 0, s>>>(a, tf, pou, piece, box, vt, slot, n_slots, m, ctr);
+    else k_pass1_piece<AmrD, 0><<<blocks, 128, 0, s>>>(a, tf, pou, piece, box, vt, slot, n_slots, m, ctr);
     return cudaGetLastError();
 }
 
@@ -1249,8 +1467,10 @@ cudaError_t launch_pass2_piece(const AmrD& a, const float4* tf, const int32_t* p
                                const ViewTable& vt, int32_t slot, int32_t n_slots, const void* moments, float* color,
                                Counters* ctr, cudaStream_t s) {
     const int blocks = (vt.total_tiles + 3) / 4;
-    k_pass2_piece<AmrD><<<blocks, 128, 0, s>>>(a, tf, pou, piece, box, vt, slot, n_slots,
-                                               static_cast<const char*>(moments), color, ctr);
+    const char* m = static_cast<const char*>(moments);
+    if (a.g.trig.n == 3) k_pass2_piece<AmrD, 3><<<blocks, 128, 0, s>>>(a, tf, pou, piece, box, vt, slot, n_slots, m, color, ctr);
+    else if (a.g.trig.n == 4) k_pass2_piece<AmrD, 4><<<blocks, 128, 0, s>>>(a, tf, pou, piece, box, vt, slot, n_slots, m, color, ctr);
+    else k_pass2_piece<AmrD, 0><<<blocks, 128, 0, s>>>(a, tf, pou, piece, box, vt, slot, n_slots, m, color, ctr);
     return cudaGetLastError();
 }
 
