@@ -194,6 +194,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="blobs512", choices=["blobs512", "blobs64", "amr"])
     ap.add_argument("--no-amr", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-piece", action="store_true")
     ap.add_argument("--no-sortlast", action="store_true")
@@ -358,6 +359,48 @@ def main():
         del avol, amom, argba
         torch.cuda.empty_cache()
 
+    # precision sweep on the octree field with the 2048^2 view: moment sets and storages
+    sweep = None
+    if args.workload == "blobs512" and not args.no_sweep:
+        import copy
+        import scenes as _scenes
+        import oracle as _oracle
+        base = workload("amr")
+        base.views = [_scenes.perspective_view(base.dims, (0.57, 0.49, 0.66), 2048, 2048)]
+        spix = sample_pixels(2048, 2048, 64, 32)
+        sweep = []
+        exact_ref = None
+        for ms, st, beta in (("power4", "f32", 5e-5), ("trig6", "f16", 2e-3), ("trig6", "bf16", 2e-2),
+                             ("trig8", "f16", 2e-3), ("trig8", "bf16", 2e-2)):
+            sc2 = copy.copy(base)
+            sc2.moment_set, sc2.storage, sc2.moment_bias = ms, st, beta
+            svol = pkg.Volume(sc2)
+            sv = sc2.views
+            smom, srgba = svol.moments_for(sv), pkg.Volume.color_buffer(sv)
+            sframe = lambda: svol.render_frame(sv, smom, srgba)  # noqa: E731
+            for _ in range(2):
+                sframe()
+            ms_s = timed(sframe, 3)
+            svol.synchronize()
+            ns = svol.stats()["samples_pass1"]
+            row = {"moments": ms, "storage": st, "moment_bias": beta,
+                   "moment_bytes_per_pixel": pkg.mboit_moment_image_bytes(4, 1, svol.moment_set, svol.storage) // 4,
+                   "ms_per_frame": ms_s, "gsamples_per_s": ns / (ms_s * 1e-3) / 1e9}
+            if rank == 0 and not args.no_cpu_baseline:
+                ref = _oracle.render_amr(sc2, pixels=spix, want=("mboit", "exact") if exact_ref is None else ("mboit",))
+                if exact_ref is None:
+                    exact_ref = ref["exact"]
+                got = srgba.view(-1, 4)[torch.from_numpy(spix).cuda()].double().cpu().numpy()
+                row.update({"max_abs_vs_oracle": float(np.abs(got - ref["mboit"]).max()),
+                            "rmse_vs_oracle": float(np.sqrt(((got - ref["mboit"]) ** 2).mean())),
+                            "rmse_vs_exact": float(np.sqrt(((got - exact_ref) ** 2).mean())),
+                            "max_abs_vs_exact": float(np.abs(got - exact_ref).max()),
+                            "pixels": int(spix.size)})
+            sweep.append(row)
+            svol.close()
+            del svol, smom, srgba
+            torch.cuda.empty_cache()
+
     # end to end through the host API: field upload, frame, image download
     field_host = torch.from_numpy(np.ascontiguousarray(sc.values if hasattr(sc, "leaves") else sc.field)).pin_memory()
     rgba_host = torch.empty(rgba.numel(), dtype=torch.float32).pin_memory()
@@ -397,7 +440,7 @@ def main():
                           form="batched: 2 persistent kernels per frame, CUDA graph",
                           tuning={"pass1": tuning[0], "pass2": tuning[1]}),
            "samples_per_frame": samples, "ms_per_frame": ms_max, "per_piece_fp32": per_piece,
-           "sortlast_gpu": sortlast, "amr_72_pieces": amr,
+           "sortlast_gpu": sortlast, "amr_72_pieces": amr, "precision_sweep_amr_2048": sweep,
            "quality": quality, "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
            "gpu_launches": 2 * args.steps, "clocks": clk.summary()}
     vol.close()
