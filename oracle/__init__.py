@@ -54,6 +54,17 @@ class _Amr(ctypes.Structure):
                 ("bias_vector", ctypes.c_double * 4), ("moment_set", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("trig_zone", ctypes.c_double)]
 
+class _Tet(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("tets", ctypes.c_void_p), ("n_verts", ctypes.c_int64),
+                ("n_tets", ctypes.c_int64), ("box", ctypes.c_double * 3), ("quantum_log2", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("piece_of_tet", ctypes.c_void_p), ("n_pieces", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32), ("piece_selected", ctypes.c_void_p), ("tf", ctypes.c_void_p),
+                ("vmin", ctypes.c_double), ("vmax", ctypes.c_double), ("step", ctypes.c_double),
+                ("moment_bias", ctypes.c_double), ("overestimation", ctypes.c_double),
+                ("absorbance_max", ctypes.c_double), ("bias_vector", ctypes.c_double * 4),
+                ("moment_set", ctypes.c_int32), ("storage", ctypes.c_int32), ("trig_zone", ctypes.c_double)]
+
+
 MOMENT_SETS = {"power4": 0, "trig6": 3, "trig8": 4}
 STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
 TRIG_ZONE = 0.1
@@ -107,6 +118,12 @@ def _load():
             lib.orc_render_amr.restype = ctypes.c_int
             lib.orc_render_amr.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64] + \
                 [ctypes.c_void_p] * 9
+            lib.orc_render_tet.restype = ctypes.c_int
+            lib.orc_render_tet.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64] + \
+                [ctypes.c_void_p] * 9
+            lib.orc_tet_locate.restype = ctypes.c_int
+            lib.orc_tet_locate.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
             lib.orc_render_grid_segments.restype = ctypes.c_int
             lib.orc_render_grid_segments.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
@@ -223,13 +240,59 @@ def _amr_struct(scene, pieces):
     return a, keep
 
 
+def _tet_struct(scene, pieces):
+    K = scene.n_pieces
+    keep = dict(verts=np.ascontiguousarray(scene.verts, dtype=np.float32),
+                tets=np.ascontiguousarray(scene.tets, dtype=np.int32),
+                pot=np.ascontiguousarray(scene.piece_of_tet, dtype=np.int32),
+                tf=np.ascontiguousarray(scene.tf, dtype=np.float32), sel=None)
+    if pieces is not None:
+        keep["sel"] = np.zeros(K, dtype=np.uint8)
+        keep["sel"][np.asarray(list(pieces), dtype=np.int64)] = 1
+    m = _Tet()
+    m.verts, m.tets = keep["verts"].ctypes.data, keep["tets"].ctypes.data
+    m.n_verts, m.n_tets = keep["verts"].shape[0], keep["tets"].shape[0]
+    m.box[:] = [float(b) for b in scene.box]
+    m.quantum_log2 = int(scene.quantum_log2)
+    m.piece_of_tet, m.n_pieces = keep["pot"].ctypes.data, K
+    m.piece_selected = _ptr(keep["sel"])
+    m.tf = keep["tf"].ctypes.data
+    m.vmin, m.vmax = float(scene.tf_range[0]), float(scene.tf_range[1])
+    m.step = float(scene.step)
+    m.moment_bias, m.overestimation = float(scene.moment_bias), float(scene.overestimation)
+    m.absorbance_max = float(scene.absorbance_max)
+    m.bias_vector[:] = list(getattr(scene, "bias_vector", BIAS_VECTOR_POWER4))
+    _set_moment_fields(m, scene)
+    return m, keep
+
+
 def _is_amr(scene):
     return hasattr(scene, "leaves")
 
 
+def _is_tet(scene):
+    return hasattr(scene, "tets")
+
+
+def tet_locate(scene, points, brute_force=False):
+    """Exact point location in a tetrahedral scene: (owner tet [n] int32, -1
+    none; tets passing the test [n] int32; interpolated value [n] float64)."""
+    lib = _load()
+    pts = np.ascontiguousarray(points, dtype=np.float32).reshape(-1, 3)
+    n = pts.shape[0]
+    owner = np.zeros(n, np.int32)
+    npass = np.zeros(n, np.int32)
+    val = np.zeros(n)
+    m, keep = _tet_struct(scene, None)
+    if lib.orc_tet_locate(ctypes.byref(m), pts.ctypes.data, n, owner.ctypes.data, npass.ctypes.data,
+                          val.ctypes.data, int(bool(brute_force))) != 0:
+        raise ValueError("oracle rejected the mesh (orientation, box or quantum)")
+    return owner, npass, val
+
+
 def render_amr(scene, view=0, pixels=None, pieces=None, want=("mboit",)):
-    """render_grid for a brick-octree scene (`scenes.AmrScene`); `want` may
-    also name "nsegments"."""
+    """render_grid for a brick-octree scene (`scenes.AmrScene`) or a
+    tetrahedral scene (`scenes.TetScene`); `want` may also name "nsegments"."""
     lib = _load()
     v = scene.views[view] if isinstance(view, int) else view
     pix = np.arange(v.width * v.height, dtype=np.int64) if pixels is None else \
@@ -243,26 +306,31 @@ def render_amr(scene, view=0, pixels=None, pieces=None, want=("mboit",)):
             out[k] = np.zeros(n, dtype=np.int64)
     if "nsegments" in out and "sortlast" not in out:
         out["sortlast"] = np.zeros((n, 4))
-    a, keep = _amr_struct(scene, pieces)
+    if _is_tet(scene):
+        a, keep = _tet_struct(scene, pieces)
+        fn = lib.orc_render_tet
+    else:
+        a, keep = _amr_struct(scene, pieces)
+        fn = lib.orc_render_amr
     vs = _view_struct(v)
-    rc = lib.orc_render_amr(ctypes.byref(a), ctypes.byref(vs), pix.ctypes.data, n,
+    rc = fn(ctypes.byref(a), ctypes.byref(vs), pix.ctypes.data, n,
                             _ptr(out.get("moments")), _ptr(out.get("piece_moments")), _ptr(out.get("piece_color")),
                             _ptr(out.get("mboit")), _ptr(out.get("raw")), _ptr(out.get("exact")),
                             _ptr(out.get("sortlast")), _ptr(out.get("nsamples")), _ptr(out.get("nsegments")))
     if rc != 0:
-        raise ValueError("oracle rejected its arguments (bad or overlapping leaves?)")
+        raise ValueError("oracle rejected its arguments (bad or overlapping leaves or tets?)")
     return out
 
 
 def render(scene, view=0, pixels=None, pieces=None, want=("mboit",)):
     """render_grid or render_amr, by scene type."""
-    f = render_amr if _is_amr(scene) else render_grid
+    f = render_amr if (_is_amr(scene) or _is_tet(scene)) else render_grid
     return f(scene, view=view, pixels=pixels, pieces=pieces, want=want)
 
 
 def render_segments(scene, view=0, pixels=None, pieces=None):
     """Sort-last route only: (rgba [n][4] float64, segments per pixel [n] int64)."""
-    if _is_amr(scene):
+    if _is_amr(scene) or _is_tet(scene):
         r = render_amr(scene, view=view, pixels=pixels, pieces=pieces, want=("sortlast", "nsegments"))
         return r["sortlast"], r["nsegments"]
     lib = _load()

@@ -171,11 +171,16 @@ double orc_mboit_bound(const double m[5], double z0, double moment_bias,
 /* the volume being rendered: a regular grid or a brick octree               */
 
 typedef struct {
-    int kind;                      /* 0 grid, 1 brick octree */
+    int kind;                      /* 0 grid, 1 brick octree, 2 tetrahedral mesh */
     const orc_grid* g;
     const orc_amr* a;
     int32_t* fmap;                 /* octree: finest brick -> leaf (-1 none) */
     int64_t fdim;                  /* finest bricks per axis */
+    const orc_tet* m;
+    int64_t* vq;                   /* tets: snapped vertex coordinates [n_verts][3] */
+    int32_t *bin_start, *bin_tets; /* tets: unit bins -> tets whose box meets the bin */
+    int64_t bdim[3];
+    int overlap;                   /* tets: set when two tets claim one point */
     double hi[3];                  /* the domain is [0, hi) per axis */
     int n_pieces;
     const uint8_t* piece_selected;
@@ -533,6 +538,200 @@ static int locate_amr(const vol_t* vol, const float p[3], double* val)
     return piece;
 }
 
+/* ------------------------------------------------------------------------ */
+/* tetrahedral mesh: exact point location                                    */
+
+__extension__ typedef __int128 i128;
+
+/* Snap one coordinate to the lattice 2^-s (nearest-even). */
+static int64_t snap(double x, int s) { return (int64_t)nearbyint(ldexp(x, s)); }
+
+/* det[P1 - P0, P2 - P0, P3 - P0]: six times the signed volume of P0..P3. */
+static i128 orient4(const int64_t P[4][3])
+{
+    i128 a[3], b[3], c[3];
+    for (int k = 0; k < 3; ++k) {
+        a[k] = P[1][k] - P[0][k];
+        b[k] = P[2][k] - P[0][k];
+        c[k] = P[3][k] - P[0][k];
+    }
+    return a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
+}
+
+static void tet_corners(const vol_t* v, int64_t t, int64_t P[4][3])
+{
+    const int32_t* T = v->m->tets + 4 * t;
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 3; ++k) P[i][k] = v->vq[3 * (int64_t)T[i] + k];
+}
+
+/* D_i(q): the orientation with corner i replaced by q (q's barycentric
+ * coordinate times six volumes).  Returns 1 if q + (e, e^2, e^3) is strictly
+ * on the inner side of every face, and D_0..D_3 at q itself in D. */
+static int tet_contains(const vol_t* v, int64_t t, const int64_t q[3], i128 D[4])
+{
+    int64_t P[4][3];
+    tet_corners(v, t, P);
+    int inside = 1;
+    for (int i = 0; i < 4; ++i) {
+        int64_t R[4][3];
+        memcpy(R, P, sizeof R);
+        for (int k = 0; k < 3; ++k) R[i][k] = q[k];
+        D[i] = orient4(R);
+        /* D_i is affine in q: its partial derivatives are exact differences */
+        i128 sgn = D[i];
+        for (int k = 0; k < 3 && sgn == 0; ++k) {
+            R[i][k] = q[k] + 1;
+            sgn = orient4(R) - D[i];
+            R[i][k] = q[k];
+        }
+        if (sgn <= 0) inside = 0;
+    }
+    return inside;
+}
+
+static double tet_value(const vol_t* v, int64_t t, const i128 D[4])
+{
+    const int32_t* T = v->m->tets + 4 * t;
+    double tot = (double)(D[0] + D[1] + D[2] + D[3]), val = 0.0;
+    for (int i = 0; i < 4; ++i) val += (double)D[i] / tot * (double)v->m->verts[4 * (int64_t)T[i] + 3];
+    return val;
+}
+
+/* The owning tet of the snapped point q (-1 if none); *n_pass = how many
+ * tets passed (more than one only for an overlapping mesh). */
+static int64_t tet_find(const vol_t* v, const int64_t q[3], int brute, int* n_pass, double* val)
+{
+    int64_t owner = -1, lo = 0, hi = v->m->n_tets;
+    const int32_t* list = NULL;
+    if (!brute) {
+        int64_t b[3];
+        for (int k = 0; k < 3; ++k) {
+            b[k] = q[k] >> v->m->quantum_log2;
+            if (b[k] < 0) b[k] = 0;
+            if (b[k] > v->bdim[k] - 1) b[k] = v->bdim[k] - 1;
+        }
+        int64_t bin = (b[2] * v->bdim[1] + b[1]) * v->bdim[0] + b[0];
+        lo = v->bin_start[bin];
+        hi = v->bin_start[bin + 1];
+        list = v->bin_tets;
+    }
+    *n_pass = 0;
+    for (int64_t j = lo; j < hi; ++j) {
+        int64_t t = list ? list[j] : j;
+        i128 D[4];
+        if (tet_contains(v, t, q, D)) {
+            if (*n_pass == 0) {
+                owner = t;
+                if (val) *val = tet_value(v, t, D);
+            }
+            ++*n_pass;
+        }
+    }
+    return owner;
+}
+
+static int locate_tet_piece(const vol_t* vol, const float p[3], double* val)
+{
+    int64_t q[3];
+    for (int k = 0; k < 3; ++k) q[k] = snap((double)p[k], vol->m->quantum_log2);
+    int n_pass;
+    int64_t t = tet_find(vol, q, 0, &n_pass, val);
+    if (n_pass > 1) ((vol_t*)vol)->overlap = 1;
+    if (t < 0) return -1;
+    return vol->m->piece_of_tet[t];
+}
+
+static void tet_free(vol_t* v)
+{
+    free(v->vq);
+    free(v->bin_start);
+    free(v->bin_tets);
+}
+
+/* Snaps the vertices, checks boxes and orientation, bins the tets by their
+ * snapped bounding boxes (bins of one unit). */
+static int tet_vol(const orc_tet* m, vol_t* v)
+{
+    memset(v, 0, sizeof *v);
+    if (!m || !m->verts || !m->tets || !m->piece_of_tet || !m->tf || m->n_tets <= 0 || m->n_verts <= 0 ||
+        m->n_pieces <= 0 || m->quantum_log2 < 0 || m->quantum_log2 > 24)
+        return -1;
+    if ((m->moment_set != 0 && m->moment_set != 3 && m->moment_set != 4) || m->storage < 0 || m->storage > 2 ||
+        (m->storage && !m->moment_set))
+        return -1;
+    const int s = m->quantum_log2;
+    v->kind = 2;
+    v->m = m;
+    v->vq = (int64_t*)malloc((size_t)m->n_verts * 3 * sizeof(int64_t));
+    for (int k = 0; k < 3; ++k) v->bdim[k] = (snap(m->box[k], s) >> s) + 1;
+    int64_t nbins = v->bdim[0] * v->bdim[1] * v->bdim[2];
+    v->bin_start = (int32_t*)calloc((size_t)nbins + 1, sizeof(int32_t));
+    if (!v->vq || !v->bin_start) { tet_free(v); return -1; }
+    for (int64_t i = 0; i < m->n_verts; ++i)
+        for (int k = 0; k < 3; ++k) {
+            double x = m->verts[4 * i + k];
+            if (!(x >= 0.0 && x <= m->box[k])) { tet_free(v); return -1; }
+            v->vq[3 * i + k] = snap(x, s);
+        }
+    /* two sweeps over the tets: count bin entries, then fill them */
+    for (int sweep = 0; sweep < 2; ++sweep) {
+        if (sweep == 1) {
+            for (int64_t b = 0; b < nbins; ++b) v->bin_start[b + 1] += v->bin_start[b];
+            v->bin_tets = (int32_t*)malloc((size_t)(v->bin_start[nbins] > 0 ? v->bin_start[nbins] : 1) * sizeof(int32_t));
+            if (!v->bin_tets) { tet_free(v); return -1; }
+        }
+        int64_t* fill = NULL;
+        if (sweep == 1) {
+            fill = (int64_t*)malloc((size_t)nbins * sizeof(int64_t));
+            if (!fill) { tet_free(v); return -1; }
+            for (int64_t b = 0; b < nbins; ++b) fill[b] = v->bin_start[b];
+        }
+        for (int64_t t = 0; t < m->n_tets; ++t) {
+            int64_t P[4][3], lo[3], hi[3];
+            for (int i = 0; i < 4; ++i)
+                if (m->tets[4 * t + i] < 0 || m->tets[4 * t + i] >= m->n_verts) { free(fill); tet_free(v); return -1; }
+            tet_corners(v, t, P);
+            if (sweep == 0 && orient4(P) <= 0) { tet_free(v); return -1; }
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = hi[k] = P[0][k];
+                for (int i = 1; i < 4; ++i) {
+                    if (P[i][k] < lo[k]) lo[k] = P[i][k];
+                    if (P[i][k] > hi[k]) hi[k] = P[i][k];
+                }
+                lo[k] >>= s;
+                hi[k] >>= s;
+                if (hi[k] > v->bdim[k] - 1) hi[k] = v->bdim[k] - 1;
+            }
+            for (int64_t z = lo[2]; z <= hi[2]; ++z)
+                for (int64_t y = lo[1]; y <= hi[1]; ++y)
+                    for (int64_t x = lo[0]; x <= hi[0]; ++x) {
+                        int64_t b = (z * v->bdim[1] + y) * v->bdim[0] + x;
+                        if (sweep == 0) ++v->bin_start[b + 1];
+                        else v->bin_tets[fill[b]++] = (int32_t)t;
+                    }
+        }
+        free(fill);
+    }
+    v->hi[0] = m->box[0];
+    v->hi[1] = m->box[1];
+    v->hi[2] = m->box[2];
+    v->n_pieces = m->n_pieces;
+    v->piece_selected = m->piece_selected;
+    v->tf = m->tf;
+    v->vmin = m->vmin;
+    v->vmax = m->vmax;
+    v->step = m->step;
+    v->moment_bias = m->moment_bias;
+    v->overestimation = m->overestimation;
+    v->absorbance_max = m->absorbance_max;
+    v->bias_vector = m->bias_vector;
+    v->n_trig = m->moment_set;
+    v->storage = m->storage;
+    v->trig_zone = m->trig_zone;
+    return 0;
+}
+
 /* Classifies lattice point k; returns 1 and fills s if it is inside the
  * domain and owned by a selected piece. */
 static int take_sample(const vol_t* g, const orc_view* V, const float o[3], const float d[3],
@@ -544,7 +743,8 @@ static int take_sample(const vol_t* g, const orc_view* V, const float o[3], cons
     for (int c = 0; c < 3; ++c)
         if (!(p[c] >= 0.0f && p[c] < (float)g->hi[c])) return 0;
     double val;
-    int piece = (g->kind == 0) ? locate_grid(g->g, p, &val) : locate_amr(g, p, &val);
+    int piece = (g->kind == 0) ? locate_grid(g->g, p, &val) : (g->kind == 1) ? locate_amr(g, p, &val)
+                                                                             : locate_tet_piece(g, p, &val);
     if (piece < 0) return 0;
     if (g->piece_selected && !g->piece_selected[piece]) return 0;
 
@@ -864,5 +1064,39 @@ static int render_impl(const vol_t* g, const orc_view* V,
     free(S);
     free(mP);
     free(cP);
+    return 0;
+}
+
+int orc_render_tet(const orc_tet* m, const orc_view* V,
+                   const int64_t* pixels, int64_t n_pixels,
+                   double* moments, double* piece_moments, double* piece_color,
+                   double* mboit_rgba, double* raw_rgba, double* exact_rgba,
+                   double* sortlast_rgba, int64_t* nsamples, int64_t* nsegments)
+{
+    vol_t v;
+    if (tet_vol(m, &v) != 0) return -1;
+    int rc = render_impl(&v, V, pixels, n_pixels, moments, piece_moments, piece_color, mboit_rgba, raw_rgba,
+                         exact_rgba, sortlast_rgba, nsamples, nsegments);
+    if (v.overlap) rc = -1;
+    tet_free(&v);
+    return rc;
+}
+
+int orc_tet_locate(const orc_tet* m, const float* points, int64_t n, int32_t* tet_out, int32_t* n_pass_out,
+                   double* value_out, int32_t brute_force)
+{
+    vol_t v;
+    if (!points || n < 0 || tet_vol(m, &v) != 0) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t q[3];
+        for (int k = 0; k < 3; ++k) q[k] = snap((double)points[3 * i + k], m->quantum_log2);
+        int n_pass;
+        double val = NAN;
+        int64_t t = tet_find(&v, q, brute_force, &n_pass, &val);
+        if (tet_out) tet_out[i] = (int32_t)t;
+        if (n_pass_out) n_pass_out[i] = n_pass;
+        if (value_out) value_out[i] = t >= 0 ? val : NAN;
+    }
+    tet_free(&v);
     return 0;
 }

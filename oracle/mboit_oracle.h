@@ -117,6 +117,47 @@ int orc_render_amr(const orc_amr* a, const orc_view* view,
                    double* mboit_rgba, double* raw_rgba, double* exact_rgba,
                    double* sortlast_rgba, int64_t* nsamples, int64_t* nsegments);
 
+/* Tetrahedral mesh (Sec. 5: unstructured pieces; a piece is a set of tets).
+ * Point location is exact: positions and vertices snap to the lattice of
+ * multiples of 2^-quantum_log2 (nearest-even), and a snapped point q belongs
+ * to the one tet containing q + (e, e^2, e^3) for an infinitesimal e > 0
+ * (symbolic perturbation), so that the tets of a conforming mesh partition
+ * the box exactly with no gaps or double counts on faces, edges and
+ * vertices.  The value is the barycentric (linear) interpolation of the four
+ * vertex values at q. */
+typedef struct {
+    const float* verts;            /* [n_verts][4]: x, y, z, value */
+    const int32_t* tets;           /* [n_tets][4]: vertex ids, positively oriented */
+    int64_t n_verts, n_tets;
+    double box[3];                 /* the domain is [0, box) per axis; vertices lie in [0, box] */
+    int32_t quantum_log2;
+    int32_t reserved;
+    const int32_t* piece_of_tet;   /* [n_tets] */
+    int32_t n_pieces, reserved2;
+    const uint8_t* piece_selected; /* [n_pieces], NULL = every piece */
+    const float* tf;
+    double vmin, vmax, step, moment_bias, overestimation, absorbance_max;
+    double bias_vector[4];
+    int32_t moment_set, storage;   /* as in orc_grid */
+    double trig_zone;
+} orc_tet;
+
+/* The render outputs of orc_render_amr for a tetrahedral mesh.  Returns -1
+ * also for a tet that is not positively oriented after snapping, a vertex
+ * outside the box, or a point that two tets claim (a mesh that overlaps). */
+int orc_render_tet(const orc_tet* m, const orc_view* view,
+                   const int64_t* pixels, int64_t n_pixels,
+                   double* moments, double* piece_moments, double* piece_color,
+                   double* mboit_rgba, double* raw_rgba, double* exact_rgba,
+                   double* sortlast_rgba, int64_t* nsamples, int64_t* nsegments);
+
+/* Point location alone: for n float32 points (x, y, z), the owning tet
+ * (-1: none), the number of tets that pass the test (0 or 1 for a valid
+ * mesh) and the interpolated value (NaN if none).  brute_force = 1 tests
+ * every tet instead of the candidates of the point's bin.  Returns 0 / -1. */
+int orc_tet_locate(const orc_tet* m, const float* points, int64_t n, int32_t* tet_out, int32_t* n_pass_out,
+                   double* value_out, int32_t brute_force);
+
 #ifdef __cplusplus
 }
 #endif

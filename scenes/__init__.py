@@ -474,3 +474,135 @@ def morton_pieces_linear(n, n_pieces, weights, stream, jitter=0.0):
     for p in range(n_pieces):
         piece[splits[p]:splits[p + 1]] = p
     return piece
+
+
+# ---------------------------------------------------------------------------
+# tetrahedral mesh
+
+@dataclass
+class TetScene:
+    """Conforming tetrahedral mesh of the box [0, n]^3: vertices (x, y, z,
+    value) float32, tets (4 vertex ids, positively oriented), neighbours
+    (the tet across the face opposite vertex i, -1 on the boundary)."""
+    name: str
+    verts: np.ndarray           # float32 [nv][4]
+    tets: np.ndarray            # int32 [nt][4]
+    neighbors: np.ndarray       # int32 [nt][4]
+    box: tuple                  # the domain is [0, box) per axis
+    quantum_log2: int           # positions snap to multiples of 2^-quantum_log2
+    piece_of_tet: np.ndarray    # int32 [nt]
+    n_pieces: int
+    tf: np.ndarray
+    tf_range: tuple
+    step: float
+    views: List[View] = dc_field(default_factory=list)
+    moment_bias: float = 5e-5
+    overestimation: float = 0.3
+    absorbance_max: float = 10.0
+
+    @property
+    def dims(self):
+        return tuple(int(b) + 1 for b in self.box)
+
+
+# corner indices (dx, dy, dz) of the 5-tet split; even hexes use the first
+# set, odd hexes its mirror, so neighbouring hexes split shared faces alike
+_TET5_EVEN = [((0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)), ((1, 1, 0), (0, 1, 0), (1, 0, 0), (1, 1, 1)),
+              ((1, 0, 1), (0, 0, 1), (1, 1, 1), (1, 0, 0)), ((0, 1, 1), (1, 1, 1), (0, 0, 1), (0, 1, 0)),
+              ((1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 1))]
+_TET5_ODD = [tuple((1 - a, b, c) for a, b, c in t) for t in _TET5_EVEN]
+
+
+def tet_neighbors(tets):
+    """Tet across each face (face i is opposite vertex i); -1 on the boundary."""
+    nt = tets.shape[0]
+    faces = np.stack([np.delete(tets, i, axis=1) for i in range(4)], axis=1).reshape(-1, 3)
+    faces = np.sort(faces, axis=1).astype(np.int64)
+    key = (faces[:, 0] << 42) | (faces[:, 1] << 21) | faces[:, 2]
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    same = np.nonzero(ks[1:] == ks[:-1])[0]
+    nb = np.full(nt * 4, -1, np.int64)
+    a, b = order[same], order[same + 1]
+    nb[a] = b // 4
+    nb[b] = a // 4
+    return nb.reshape(nt, 4).astype(np.int32)
+
+
+def tet_orient(P, tets):
+    """Six signed volumes of the tets, exact for coordinates on the 2^-16 lattice."""
+    Q = np.rint(np.asarray(P, np.float64) * 65536.0).astype(np.int64)
+    a, b, c, d = (Q[tets[:, i]] for i in range(4))
+    u, v, w = b - a, c - a, d - a
+    return (u[:, 0] * (v[:, 1] * w[:, 2] - v[:, 2] * w[:, 1]) - u[:, 1] * (v[:, 0] * w[:, 2] - v[:, 2] * w[:, 0])
+            + u[:, 2] * (v[:, 0] * w[:, 1] - v[:, 1] * w[:, 0]))
+
+
+def hex_tets(n):
+    """Vertex ids of the 5-tet split of an n^3 hex grid ((n+1)^3 vertices,
+    x fastest), 5 tets per hex in hex order (parity-alternating split)."""
+    nv1 = n + 1
+    hz, hy, hx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    hx, hy, hz = hx.ravel(), hy.ravel(), hz.ravel()
+    even = ((hx + hy + hz) % 2) == 0
+    tets = np.empty((n ** 3, 5, 4), np.int64)
+    for t in range(5):
+        for corner in range(4):
+            e, o = _TET5_EVEN[t][corner], _TET5_ODD[t][corner]
+            tets[:, t, corner] = np.where(even, ((hz + e[2]) * nv1 + (hy + e[1])) * nv1 + (hx + e[0]),
+                                          ((hz + o[2]) * nv1 + (hy + o[1])) * nv1 + (hx + o[0]))
+    return tets.reshape(-1, 4)
+
+
+def tet_mesh(n=96, jitter=0.3, n_pieces=72, width=1024, height=1024, seed=1004, alpha_max=None):
+    """Jittered n^3 hex grid, 5 tets per hex, the scalar of the 64^3 blob
+    workload (8 blobs, scaled to n) at the vertices, 72 pieces in equal-count
+    ranges of the Morton order of tet centroids, a perspective view, step 0.5.
+
+    Vertices move by U[-jitter, jitter] cells per axis (boundary vertices only
+    along the box faces, so the mesh fills the box exactly); a vertex whose
+    move would leave a tet with under 5% of its unjittered volume has its
+    move halved until none does; positions are then rounded to multiples of
+    2^-16 (the lattice the exact point location snaps to)."""
+    s = Stream(seed)
+    nv1 = n + 1
+    g = np.arange(nv1, dtype=np.float64)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    P0 = np.stack([X, Y, Z], -1).reshape(-1, 3)
+    J = s.uniform(P0.size).reshape(-1, 3) * (2 * jitter) - jitter
+    J[(P0 == 0) | (P0 == n)] = 0.0
+    tets = hex_tets(n)
+    v0 = tet_orient(P0, tets)
+    flip = v0 < 0
+    tets[flip, 2], tets[flip, 3] = tets[flip, 3].copy(), tets[flip, 2].copy()
+    v0 = np.abs(v0)
+    while True:
+        P = np.rint((P0 + J) * 65536.0) / 65536.0
+        bad = tet_orient(P, tets) < 0.05 * v0
+        if not bad.any():
+            break
+        J[np.unique(tets[bad].ravel())] *= 0.5
+    # value: 8 blobs as in the 64^3 workload, scaled to n
+    k = n / 64.0
+    c = s.uniform(24).reshape(8, 3) * n
+    sg = s.uniform(8, 4.0 * k, 12.0 * k)
+    am = s.uniform(8, 0.3, 1.0)
+    val = np.zeros(len(P))
+    for i in range(8):
+        val += am[i] * np.exp(-((P - c[i]) ** 2).sum(1) / (2 * sg[i] ** 2))
+    verts = np.concatenate([P, val[:, None]], 1).astype(np.float32)
+    tets = tets.astype(np.int32)
+    nb = tet_neighbors(tets)
+    cen = P[tets].mean(axis=1)
+    q = np.clip((cen / n * 1023).astype(np.int64), 0, 1023)
+    order = np.argsort(morton3(q[:, 0], q[:, 1], q[:, 2], 10), kind="stable")
+    piece = np.empty(len(tets), np.int32)
+    bounds = np.linspace(0, len(tets), n_pieces + 1).round().astype(np.int64)
+    for p in range(n_pieces):
+        piece[order[bounds[p]:bounds[p + 1]]] = p
+    tf = tf_table(Stream(seed + 7), alpha_max if alpha_max is not None else min(0.13 * 64.0 / n, 0.4))
+    dims = (n + 1,) * 3
+    view = perspective_view(dims, (0.57, 0.49, 0.66), width, height)
+    vf = verts[:, 3]
+    return TetScene("tets" if n == 96 else f"tets{n}", verts, tets, nb, (float(n),) * 3, 16, piece, n_pieces, tf,
+                    (np.float32(vf.min()), np.float32(vf.max())), 0.5, [view])

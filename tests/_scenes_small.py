@@ -113,3 +113,23 @@ def linear_amr(base=3, max_level=2, refine=((0, 0, 0), (1, 2, 1))):
                           (vmin, vmax), 0.5, [])
     grid = scenes.GridScene("linear_grid", field, 3, np.zeros(((D + 7) // 8) ** 3, np.int32), 1, tf, (vmin, vmax), 0.5, [])
     return amr, grid
+
+
+def linear_tets(n=6, n_pieces=3, seed=21):
+    """Jittered n^3 tetrahedral mesh with the dyadic linear field of
+    linear_amr at its vertices (barycentric interpolation reproduces it), and
+    the (n+1)^3 regular grid holding the same field."""
+    lin = lambda x, y, z: 0.25 + x / 16.0 + y / 32.0 + z / 8.0  # noqa: E731
+    sc = scenes.tet_mesh(n=n, n_pieces=n_pieces, width=4, height=4, seed=seed)
+    P = sc.verts[:, :3].astype(np.float64)
+    sc.verts[:, 3] = lin(P[:, 0], P[:, 1], P[:, 2])
+    g = np.arange(n + 1.0)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    field = lin(X, Y, Z).astype(np.float32)
+    vmin, vmax = np.float32(field.min()), np.float32(field.max())
+    tf = linear_tf(0.05, 0.3)
+    sc.tf, sc.tf_range = tf, (vmin, vmax)
+    B = 2
+    nb = (n + B - 1) // B
+    grid = scenes.GridScene("linear_grid", field, 1, np.zeros(nb ** 3, np.int32), 1, tf, (vmin, vmax), 0.5, [])
+    return sc, grid

@@ -496,3 +496,115 @@ def test_trig_node_just_behind_is_not_counted(n):
         for j in range(n + 1):
             A = oracle.trig_bound(m, n, phis[j], 0.0, 0.5)[0]
             assert A == pytest.approx((a[phis < phis[j]].sum() + 0.5 * a[j]) / a.sum(), abs=1e-6)
+
+
+# --------------------------------------------------------------------------
+# tetrahedral meshes (Sec. 5: unstructured pieces)
+
+
+def _special_points(sc):
+    """Vertices, edge midpoints and face centroids of every tet."""
+    V = sc.verts[:, :3].astype(np.float64)
+    T = sc.tets
+    e = [(V[T[:, i]] + V[T[:, j]]) / 2 for i in range(4) for j in range(i + 1, 4)]
+    f = [(V[T[:, a]] + V[T[:, b]] + V[T[:, c]]) / 3 for a, b, c in ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3))]
+    return np.concatenate([V] + e + f).astype(np.float32)
+
+
+def test_tet_mesh_is_conforming_and_oriented():
+    sc = scenes.tet_mesh(n=5, n_pieces=3, width=4, height=4)
+    assert sc.tets.shape == (5 * 125, 4)
+    assert np.all(scenes.tet_orient(sc.verts[:, :3], sc.tets) > 0)
+    # every interior face is shared by exactly two tets: 2 n^2 boundary triangles per box face
+    assert (sc.neighbors < 0).sum() == 2 * 6 * 25
+    for t in range(0, len(sc.tets), 7):
+        for i in range(4):
+            u = sc.neighbors[t, i]
+            if u >= 0:
+                assert t in sc.neighbors[u]
+                assert set(np.delete(sc.tets[t], i)) <= set(sc.tets[u])
+
+
+def test_tet_location_partitions_the_box():
+    """Exactly one tet owns every point of [0, n)^3, on faces, edges and
+    vertices included (the symbolic perturbation), none owns a point outside;
+    the owner's barycentric coordinates (solved independently in numpy) are
+    all >= 0, and the binned search equals testing every tet."""
+    n = 5
+    sc = scenes.tet_mesh(n=n, n_pieces=3, width=4, height=4, seed=5)
+    rng = np.random.default_rng(1)
+    pts = np.concatenate([(rng.random((3000, 3)) * n).astype(np.float32), _special_points(sc)])
+    inside = np.all((pts >= 0) & (pts < n), axis=1)
+    owner, npass, val = oracle.tet_locate(sc, pts)
+    np.testing.assert_array_equal(npass[inside], 1)
+    assert np.all(owner[~inside] < 0) or np.all(npass[~inside] <= 1)
+    ob, npb, _ = oracle.tet_locate(sc, pts, brute_force=True)
+    np.testing.assert_array_equal(ob, owner)
+    np.testing.assert_array_equal(npb, npass)
+    V = sc.verts[:, :3].astype(np.float64)
+    q = np.rint(pts[inside].astype(np.float64) * 65536.0) / 65536.0
+    T = sc.tets[owner[inside]]
+    A = np.stack([V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]], V[T[:, 3]] - V[T[:, 0]]], axis=2)
+    lam = np.linalg.solve(A, (q - V[T[:, 0]])[:, :, None])[:, :, 0]
+    bary = np.concatenate([1 - lam.sum(1, keepdims=True), lam], 1)
+    assert bary.min() > -1e-9
+    # points on the upper box faces belong to no tet (the box is half-open)
+    top = np.array([[n, 1.5, 2.5], [2.25, n, 0.5], [0.5, 0.5, n], [0.0, 0.0, 0.0]], np.float32)
+    o2, n2, _ = oracle.tet_locate(sc, top)
+    np.testing.assert_array_equal(n2, [0, 0, 0, 1])
+
+
+def test_tet_point_inside_known_tet():
+    """Points built from barycentric coordinates >= 1/20 are owned by the
+    tet they were built in, with the linear value of that combination."""
+    sc = scenes.tet_mesh(n=4, n_pieces=2, width=4, height=4, seed=9)
+    rng = np.random.default_rng(3)
+    ts = rng.integers(0, len(sc.tets), 400)
+    lam = rng.random((400, 4)) + 0.2
+    lam /= lam.sum(1, keepdims=True)
+    V = sc.verts[:, :3].astype(np.float64)
+    P = np.einsum("ni,nik->nk", lam, V[sc.tets[ts]])
+    P = (np.rint(P * 65536.0) / 65536.0).astype(np.float32)
+    owner, npass, val = oracle.tet_locate(sc, P)
+    np.testing.assert_array_equal(owner, ts)
+    want = np.einsum("ni,ni->n", lam, sc.verts[sc.tets[ts], 3].astype(np.float64))
+    np.testing.assert_allclose(val, want, atol=2e-5)
+
+
+def test_tet_linear_field_equals_grid():
+    """Barycentric interpolation reproduces a linear field on any mesh, so a
+    tet render equals the regular grid's up to the 2^-16 position snap."""
+    sc, grid = small.linear_tets()
+    P = sc.verts[:, :3].astype(np.float64)
+    owner, npass, val = oracle.tet_locate(sc, (np.random.default_rng(2).random((500, 3)) * 6).astype(np.float32))
+    views = [scenes.ortho_view(sc.dims, (0.4, 0.5, 0.77), 20, 18),
+             scenes.perspective_view(sc.dims, (-0.6, 0.45, 0.66), 16, 14, fov_deg=35.0)]
+    for v in views:
+        a = oracle.render(sc, view=v, want=("moments", "mboit", "exact", "nsamples"))
+        g = oracle.render_grid(grid, view=v, want=("moments", "mboit", "exact", "nsamples"))
+        assert np.abs(a["nsamples"] - g["nsamples"]).max() <= 1
+        assert (a["nsamples"] == g["nsamples"]).mean() > 0.95
+        same = a["nsamples"] == g["nsamples"]
+        np.testing.assert_allclose(a["moments"][same], g["moments"][same], rtol=1e-5, atol=1e-6)
+        np.testing.assert_allclose(a["mboit"][same], g["mboit"][same], atol=1e-5)
+        np.testing.assert_allclose(a["exact"], g["exact"], atol=0.05)
+        assert a["nsamples"].sum() > 100
+
+
+def test_tet_pieces_sum_and_sortlast():
+    sc = scenes.tet_mesh(n=6, n_pieces=4, width=20, height=18, seed=13)
+    r = oracle.render(sc, want=("piece_moments", "moments", "exact", "sortlast", "mboit", "nsamples"))
+    np.testing.assert_allclose(r["piece_moments"].sum(axis=1), r["moments"], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(r["sortlast"], r["exact"], atol=1e-12)
+    assert np.abs(r["mboit"] - r["exact"]).max() > 1e-4
+    assert (r["moments"][:, 0] > 0).mean() > 0.3
+    sub = oracle.render(sc, pieces=[1, 3], want=("moments",))
+    pm = r["piece_moments"][:, [1, 3]].sum(axis=1)
+    np.testing.assert_allclose(sub["moments"], pm, rtol=1e-12, atol=1e-14)
+
+
+def test_tet_inverted_mesh_rejected():
+    sc = scenes.tet_mesh(n=3, n_pieces=2, width=4, height=4)
+    sc.tets[5, [2, 3]] = sc.tets[5, [3, 2]]
+    with pytest.raises(ValueError):
+        oracle.tet_locate(sc, np.zeros((1, 3), np.float32))
