@@ -101,7 +101,7 @@ typedef enum {
 typedef struct mboit_volume_s* mboit_volume;
 
 typedef struct {
-    int32_t kind;               /* mboit_volume_kind; MBOIT_GRID and MBOIT_AMR are implemented */
+    int32_t kind;               /* mboit_volume_kind */
     int32_t moment_set;         /* mboit_moment_set */
     int32_t storage;            /* mboit_storage */
     uint32_t flags;             /* MBOIT_FLAG_* */
@@ -137,6 +137,28 @@ typedef struct {
     const int32_t* leaf_table;  /* HOST int32 [n_leaves][4]: origin x, y, z (finest cells), level; copied */
     int32_t n_leaves;
     int32_t max_level;          /* 0..10 */
+    /* MBOIT_TET (tetrahedral mesh, Sec. 5's unstructured pieces) only;
+     * field, dims and brick_log2 are then unused.  The mesh must be a
+     * conforming tetrahedralisation lying in the box [0, tet_box] (the
+     * sampled domain is [0, tet_box) per axis).  Point location is exact:
+     * vertex and sample positions snap to multiples of 2^-quantum_log2
+     * (nearest-even), and a snapped point q belongs to the one tet that
+     * contains q + (e, e^2, e^3) for an infinitesimal e > 0, so faces, edges
+     * and vertices are owned exactly once.  A sample takes the linear
+     * (barycentric) interpolation of its tet's four vertex values.  Pieces
+     * are lists of tet ids.  Checked: ids in range, every tet positively
+     * oriented after snapping, vertices inside the box, neighbours
+     * reciprocal, and the snapped coordinates small enough for exact 64-bit
+     * predicates (6 E^2 Q < 2^62 with E the largest tet extent and Q the box,
+     * both in quanta). */
+    const float* tet_verts;     /* HOST float32 [n_verts][4]: x, y, z, value; copied */
+    const int32_t* tet_cells;   /* HOST int32 [n_tets][4]: vertex ids; copied */
+    const int32_t* tet_neighbors; /* HOST int32 [n_tets][4]: the tet across the face opposite corner i,
+                                   * -1 on the boundary; copied */
+    int64_t n_verts;
+    int64_t n_tets;             /* 1 .. 2^31 - 1 */
+    float tet_box[3];
+    int32_t quantum_log2;       /* 0 .. 24; 2^quantum_log2 * tet_box < 2^30 */
 } mboit_volume_desc;
 
 typedef struct {
@@ -188,7 +210,7 @@ MBOIT_API mboit_status mboit_create_volume(const mboit_volume_desc* desc, mboit_
 MBOIT_API mboit_status mboit_destroy_volume(mboit_volume v);
 
 /* Adds one piece: `ids` lists brick ids ((bz*nby + by)*nbx + bx) of the
- * piece; copied.  `ids_on_device` = 1 if ids is a device pointer.  Pieces
+ * piece (leaf ids of an octree, tet ids of a mesh); copied.  `ids_on_device` = 1 if ids is a device pointer.  Pieces
  * must not overlap (Sec. 6: reconstruction requires non-overlapping
  * volumes); a brick already owned -> MBOIT_ERR_INVALID_ARG and the volume is
  * unchanged.  Piece ids are 0, 1, ... in call order.  Bricks that belong to
@@ -236,7 +258,8 @@ MBOIT_API mboit_status mboit_render_frame(mboit_volume v, const mboit_view* view
                                 float* rgba, void* stream);
 
 /* End-to-end frame from HOST memory: copies `field_host` (nx*ny*nz
- * float32, preferably pinned) into the volume's borrowed device field,
+ * float32 for a grid, the leaf values for an octree, n_verts vertex values
+ * for a tet mesh; preferably pinned) into the volume's device values,
  * renders the frame as mboit_render_frame, and copies the RGBA images to
  * `rgba_host` (n_views * width * height * 4 float32).  Returns after the
  * image has arrived on the host. */

@@ -58,7 +58,9 @@ class mboit_volume_desc(ctypes.Structure):
                 ("brick_log2", ctypes.c_int32), ("tf_rgba", ctypes.c_void_p), ("tf_range", ctypes.c_float * 2),
                 ("step", ctypes.c_float), ("moment_bias", ctypes.c_float), ("overestimation", ctypes.c_float),
                 ("absorbance_max", ctypes.c_float), ("leaf_values", ctypes.c_void_p), ("leaf_table", ctypes.c_void_p),
-                ("n_leaves", ctypes.c_int32), ("max_level", ctypes.c_int32)]
+                ("n_leaves", ctypes.c_int32), ("max_level", ctypes.c_int32), ("tet_verts", ctypes.c_void_p),
+                ("tet_cells", ctypes.c_void_p), ("tet_neighbors", ctypes.c_void_p), ("n_verts", ctypes.c_int64),
+                ("n_tets", ctypes.c_int64), ("tet_box", ctypes.c_float * 3), ("quantum_log2", ctypes.c_int32)]
 
 
 class mboit_stats(ctypes.Structure):
@@ -282,25 +284,39 @@ def mboit_render_moments_noalloc(desc, views, moments, brick_selected=None, stre
 
 class Volume:
     """A volume on the current CUDA device built from a scene: a regular grid
-    (``field``, ``brick_log2``, ``piece_of_brick``) or a brick octree
-    (``leaves``, ``values``, ``max_level``, ``piece_of_leaf``), plus
-    ``n_pieces``, ``tf``, ``tf_range``, ``step``, ``moment_bias``,
-    ``overestimation``, ``absorbance_max``.  Keeps the device data alive."""
+    (``field``, ``brick_log2``, ``piece_of_brick``), a brick octree
+    (``leaves``, ``values``, ``max_level``, ``piece_of_leaf``) or a
+    tetrahedral mesh (``verts``, ``tets``, ``neighbors``, ``box``,
+    ``quantum_log2``, ``piece_of_tet``), plus ``n_pieces``, ``tf``,
+    ``tf_range``, ``step``, ``moment_bias``, ``overestimation``,
+    ``absorbance_max``.  Keeps the device data alive."""
 
     def __init__(self, scene, field=None, flags=0):
         import torch
         load_library()
         self.scene = scene
         amr = hasattr(scene, "leaves")
-        data = scene.values if amr else scene.field
-        self.field = field if field is not None else torch.from_numpy(np.ascontiguousarray(data)).cuda()
+        tet = hasattr(scene, "tets")
+        if tet:
+            self.field = None
+        else:
+            data = scene.values if amr else scene.field
+            self.field = field if field is not None else torch.from_numpy(np.ascontiguousarray(data)).cuda()
         tf = np.ascontiguousarray(scene.tf, dtype=np.float32)
         d = mboit_volume_desc()
-        d.kind = MBOIT_AMR if amr else MBOIT_GRID
+        d.kind = MBOIT_TET if tet else MBOIT_AMR if amr else MBOIT_GRID
         self.moment_set = MOMENT_SET_IDS[getattr(scene, "moment_set", "power4")]
         self.storage = STORAGE_IDS[getattr(scene, "storage", "f32")]
         d.moment_set, d.storage, d.flags = self.moment_set, self.storage, flags
-        if amr:
+        if tet:
+            verts = np.ascontiguousarray(scene.verts, dtype=np.float32)
+            cells = np.ascontiguousarray(scene.tets, dtype=np.int32)
+            nbrs = np.ascontiguousarray(scene.neighbors, dtype=np.int32)
+            d.tet_verts, d.tet_cells, d.tet_neighbors = verts.ctypes.data, cells.ctypes.data, nbrs.ctypes.data
+            d.n_verts, d.n_tets = verts.shape[0], cells.shape[0]
+            d.tet_box[:] = [float(b) for b in scene.box]
+            d.quantum_log2 = int(scene.quantum_log2)
+        elif amr:
             table = np.ascontiguousarray(scene.leaves, dtype=np.int32)
             d.leaf_values, d.leaf_table = self.field.data_ptr(), table.ctypes.data
             d.n_leaves, d.max_level = table.shape[0], scene.max_level
@@ -309,13 +325,13 @@ class Volume:
             d.field = self.field.data_ptr()
             nz, ny, nx = scene.field.shape
             d.dims[:] = [nx, ny, nz]
-        d.brick_log2 = scene.brick_log2
+        d.brick_log2 = 0 if tet else scene.brick_log2
         d.tf_rgba = tf.ctypes.data
         d.tf_range[:] = [float(scene.tf_range[0]), float(scene.tf_range[1])]
         d.step, d.moment_bias = float(scene.step), float(scene.moment_bias)
         d.overestimation, d.absorbance_max = float(scene.overestimation), float(scene.absorbance_max)
         self.handle = mboit_create_volume(d)
-        pob = np.asarray(scene.piece_of_leaf if amr else scene.piece_of_brick)
+        pob = np.asarray(scene.piece_of_tet if tet else scene.piece_of_leaf if amr else scene.piece_of_brick)
         for p in range(scene.n_pieces):
             mboit_add_piece(self.handle, np.nonzero(pob == p)[0].astype(np.int32))
 

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "mboit.h"
@@ -63,6 +64,15 @@ struct mboit_volume_s {
     int4* d_leaves = nullptr;
     int32_t* d_fmap = nullptr;
     std::vector<int32_t> leaf_table;
+    mb::TetD tet{};             // tetrahedral meshes: amr-like parameters plus the device tables below
+    int4* d_tverts = nullptr;
+    int4* d_tcells = nullptr;
+    int4* d_tnbrs = nullptr;
+    int32_t* d_bin_start = nullptr;
+    int32_t* d_bin_tets = nullptr;
+    float* d_tvals = nullptr;   // staging of host vertex values (mboit_render_frame_host)
+    std::vector<int32_t> tet_cells;
+    std::vector<float> tet_xyz;
     int64_t nbricks = 0;
     size_t field_bytes = 0;
     float4* d_tf = nullptr;
@@ -259,6 +269,163 @@ mboit_status select_pieces(mboit_volume v, const int32_t* pieces, int32_t n_piec
     return MBOIT_OK;
 }
 
+// Host tables of a tetrahedral mesh: snapped vertex records, cells,
+// neighbours and the bin lists, after checking everything the exact
+// predicates rely on.
+struct TetHost {
+    std::vector<int4> verts, cells, nbrs;
+    std::vector<int32_t> bin_start, bin_tets;
+    int32_t bdim[3] = {0, 0, 0};
+    int32_t bin_shift = 0;
+};
+
+mboit_status prepare_tets(const mboit_volume_desc* d, TetHost& h) {
+    if (!d->tet_verts || !d->tet_cells || !d->tet_neighbors)
+        return fail(MBOIT_ERR_INVALID_ARG, "tet_verts, tet_cells and tet_neighbors are required");
+    if (d->n_verts < 4 || d->n_verts > INT32_MAX) return fail(MBOIT_ERR_INVALID_ARG, "n_verts must be in [4, 2^31)");
+    if (d->n_tets < 1 || d->n_tets > INT32_MAX) return fail(MBOIT_ERR_INVALID_ARG, "n_tets must be in [1, 2^31)");
+    if (d->quantum_log2 < 0 || d->quantum_log2 > 24) return fail(MBOIT_ERR_INVALID_ARG, "quantum_log2 must be in [0, 24]");
+    const int s = d->quantum_log2;
+    double qmax = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        if (!(d->tet_box[c] > 0.0f) || !std::isfinite(d->tet_box[c]))
+            return fail(MBOIT_ERR_INVALID_ARG, "tet_box must be positive and finite");
+        qmax = std::max(qmax, std::ldexp((double)d->tet_box[c], s));
+    }
+    if (qmax >= 1073741824.0) return fail(MBOIT_ERR_INVALID_ARG, "tet_box * 2^quantum_log2 must be below 2^30");
+    const int64_t nv = d->n_verts, nt = d->n_tets;
+    h.verts.resize((size_t)nv);
+    for (int64_t i = 0; i < nv; ++i) {
+        const float* P = d->tet_verts + 4 * i;
+        int q[3];
+        for (int c = 0; c < 3; ++c) {
+            if (!(P[c] >= 0.0f && P[c] <= d->tet_box[c]))
+                return fail(MBOIT_ERR_INVALID_ARG, "vertex " + std::to_string(i) + " lies outside [0, tet_box]");
+            q[c] = (int)std::nearbyint(std::ldexp((double)P[c], s));
+        }
+        if (!std::isfinite(P[3])) return fail(MBOIT_ERR_INVALID_ARG, "vertex " + std::to_string(i) + ": non-finite value");
+        int w;
+        std::memcpy(&w, &P[3], sizeof w);
+        h.verts[i] = make_int4(q[0], q[1], q[2], w);
+    }
+    h.cells.resize((size_t)nt);
+    h.nbrs.resize((size_t)nt);
+    int64_t emax = 0;
+    double esum = 0.0;
+    for (int64_t t = 0; t < nt; ++t) {
+        const int32_t* C = d->tet_cells + 4 * t;
+        const int32_t* N = d->tet_neighbors + 4 * t;
+        for (int i = 0; i < 4; ++i) {
+            if (C[i] < 0 || C[i] >= nv) return fail(MBOIT_ERR_INVALID_ARG, "tet " + std::to_string(t) + ": vertex id out of range");
+            if (N[i] < -1 || N[i] >= nt) return fail(MBOIT_ERR_INVALID_ARG, "tet " + std::to_string(t) + ": neighbour id out of range");
+        }
+        h.cells[t] = make_int4(C[0], C[1], C[2], C[3]);
+        h.nbrs[t] = make_int4(N[0], N[1], N[2], N[3]);
+        int64_t ext = 0;
+        for (int c = 0; c < 3; ++c) {
+            int lo = INT32_MAX, hi = INT32_MIN;
+            for (int i = 0; i < 4; ++i) {
+                const int4& V = h.verts[C[i]];
+                const int x = c == 0 ? V.x : c == 1 ? V.y : V.z;
+                lo = std::min(lo, x);
+                hi = std::max(hi, x);
+            }
+            ext = std::max(ext, (int64_t)hi - lo);
+        }
+        emax = std::max(emax, ext);
+        esum += (double)ext;
+    }
+    // |n_i| <= 2 E^2 per component and |q - b| <= Q: every D_i fits in 64 bits
+    if (6.0 * (double)emax * (double)emax * (qmax + 2.0) >= 4.6e18)
+        return fail(MBOIT_ERR_INVALID_ARG, "tets too large for exact 64-bit predicates at this quantum_log2 "
+                                           "(use a smaller quantum_log2)");
+    for (int64_t t = 0; t < nt; ++t) {
+        const int4 c = h.cells[t];
+        const int4 a = h.verts[c.x], b = h.verts[c.y], e = h.verts[c.z], f = h.verts[c.w];
+        const long long ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+        const long long vx = e.x - a.x, vy = e.y - a.y, vz = e.z - a.z;
+        const long long nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+        if (nx * (f.x - a.x) + ny * (f.y - a.y) + nz * (f.z - a.z) <= 0)
+            return fail(MBOIT_ERR_INVALID_ARG, "tet " + std::to_string(t) + " is not positively oriented after snapping");
+        const int32_t* C = d->tet_cells + 4 * t;
+        const int32_t* N = d->tet_neighbors + 4 * t;
+        for (int i = 0; i < 4; ++i) {
+            const int32_t u = N[i];
+            if (u < 0) continue;
+            const int32_t* CU = d->tet_cells + 4 * (int64_t)u;
+            const int32_t* NU = d->tet_neighbors + 4 * (int64_t)u;
+            int j = 0;
+            while (j < 4 && NU[j] != t) ++j;
+            bool ok = j < 4;
+            for (int k = 0; ok && k < 4; ++k) {
+                if (k == i) continue;
+                bool found = false;
+                for (int l = 0; l < 4; ++l) found = found || (l != j && CU[l] == C[k]);
+                ok = found;
+            }
+            if (!ok)
+                return fail(MBOIT_ERR_INVALID_ARG, "tets " + std::to_string(t) + " and " + std::to_string(u) +
+                                                       ": neighbours not reciprocal or not sharing the face");
+        }
+    }
+    // bins: a power of two no smaller than the mean tet extent, at most ~4 per tet
+    const double eavg = std::max(1.0, esum / (double)nt);
+    int bs = 0;
+    while (bs < 30 && std::ldexp(1.0, bs) < eavg) ++bs;
+    for (;; ++bs) {
+        int64_t nb = 1;
+        for (int c = 0; c < 3; ++c) nb *= ((int64_t)std::nearbyint(std::ldexp((double)d->tet_box[c], s)) >> bs) + 1;
+        if (nb <= 4 * nt + 64 && nb <= (int64_t(1) << 26)) break;
+    }
+    h.bin_shift = bs;
+    for (int c = 0; c < 3; ++c) h.bdim[c] = (int32_t)(((int64_t)std::nearbyint(std::ldexp((double)d->tet_box[c], s)) >> bs) + 1);
+    const int64_t nbins = (int64_t)h.bdim[0] * h.bdim[1] * h.bdim[2];
+    std::vector<int64_t> start((size_t)nbins + 1, 0);
+    for (int sweep = 0; sweep < 2; ++sweep) {
+        if (sweep == 1) {
+            for (int64_t b = 0; b < nbins; ++b) start[b + 1] += start[b];
+            if (start[nbins] > INT32_MAX) return fail(MBOIT_ERR_INVALID_ARG, "mesh too large for the bin lists");
+            h.bin_tets.resize((size_t)start[nbins]);
+        }
+        std::vector<int64_t> fill;
+        if (sweep == 1) fill.assign(start.begin(), start.end() - 1);
+        for (int64_t t = 0; t < nt; ++t) {
+            const int4 c = h.cells[t];
+            const int4 V[4] = {h.verts[c.x], h.verts[c.y], h.verts[c.z], h.verts[c.w]};
+            int lo[3], hi[3];
+            lo[0] = std::min(std::min(V[0].x, V[1].x), std::min(V[2].x, V[3].x)) >> bs;
+            lo[1] = std::min(std::min(V[0].y, V[1].y), std::min(V[2].y, V[3].y)) >> bs;
+            lo[2] = std::min(std::min(V[0].z, V[1].z), std::min(V[2].z, V[3].z)) >> bs;
+            hi[0] = std::max(std::max(V[0].x, V[1].x), std::max(V[2].x, V[3].x)) >> bs;
+            hi[1] = std::max(std::max(V[0].y, V[1].y), std::max(V[2].y, V[3].y)) >> bs;
+            hi[2] = std::max(std::max(V[0].z, V[1].z), std::max(V[2].z, V[3].z)) >> bs;
+            for (int z = lo[2]; z <= hi[2]; ++z)
+                for (int y = lo[1]; y <= hi[1]; ++y)
+                    for (int x = lo[0]; x <= hi[0]; ++x) {
+                        const int64_t b = ((int64_t)z * h.bdim[1] + y) * h.bdim[0] + x;
+                        if (sweep == 0) ++start[b + 1];
+                        else h.bin_tets[(size_t)fill[b]++] = (int32_t)t;
+                    }
+        }
+    }
+    h.bin_start.assign(start.begin(), start.end());
+    return MBOIT_OK;
+}
+
+// The batched (fused, persistent) passes of the volume's kind.
+cudaError_t pass1_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, void* moments, cudaStream_t s) {
+    if (v->kind == MBOIT_AMR) return mb::launch_pass1_amr(v->amr, v->d_tf, mask, vt, moments, v->d_ctr, s);
+    if (v->kind == MBOIT_TET) return mb::launch_pass1_tet(v->tet, v->d_tf, mask, vt, moments, v->d_ctr, s);
+    return mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1);
+}
+
+cudaError_t pass2_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, const void* moments,
+                          float* color, int32_t mode, cudaStream_t s) {
+    if (v->kind == MBOIT_AMR) return mb::launch_pass2_amr(v->amr, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s);
+    if (v->kind == MBOIT_TET) return mb::launch_pass2_tet(v->tet, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s);
+    return mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s, v->tune2);
+}
+
 }  // namespace
 
 extern "C" {
@@ -278,9 +445,10 @@ size_t mboit_moment_image_bytes(int32_t width, int32_t height, int32_t moment_se
 mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) {
     g_err.clear();
     if (!d || !out) return fail(MBOIT_ERR_INVALID_ARG, "desc and out must be non-NULL");
-    if (d->kind != MBOIT_GRID && d->kind != MBOIT_AMR)
-        return fail(MBOIT_ERR_UNSUPPORTED, "only MBOIT_GRID and MBOIT_AMR volumes are implemented");
+    if (d->kind != MBOIT_GRID && d->kind != MBOIT_AMR && d->kind != MBOIT_TET)
+        return fail(MBOIT_ERR_UNSUPPORTED, "unknown volume kind");
     const bool is_amr = d->kind == MBOIT_AMR;
+    const bool is_tet = d->kind == MBOIT_TET;
     if (d->moment_set < MBOIT_POWER4 || d->moment_set > MBOIT_TRIG8) return fail(MBOIT_ERR_UNSUPPORTED, "unknown moment set");
     if (d->moment_set == MBOIT_POWER4 && d->storage != MBOIT_STORE_F32)
         return fail(MBOIT_ERR_UNSUPPORTED, "power moments are stored in float32");
@@ -291,7 +459,7 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
         return fail(MBOIT_ERR_INVALID_ARG, "trigonometric moments in 16 bits need moment_bias >= 2e-3 (float16) or "
                                            ">= 2e-2 (bfloat16) to keep the stored Toeplitz matrices positive definite");
     if (d->flags & ~(MBOIT_FLAG_RAW_SUM | MBOIT_FLAG_DETERMINISTIC)) return fail(MBOIT_ERR_INVALID_ARG, "unknown flag bits");
-    if (!is_amr && !d->field) return fail(MBOIT_ERR_INVALID_ARG, "field is NULL");
+    if (!is_amr && !is_tet && !d->field) return fail(MBOIT_ERR_INVALID_ARG, "field is NULL");
     if (is_amr) {
         if (!d->leaf_values || !d->leaf_table) return fail(MBOIT_ERR_INVALID_ARG, "leaf_values and leaf_table are required");
         if (d->n_leaves < 1) return fail(MBOIT_ERR_INVALID_ARG, "n_leaves must be >= 1");
@@ -299,9 +467,11 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
         if (d->dims[0] != d->dims[1] || d->dims[0] != d->dims[2])
             return fail(MBOIT_ERR_INVALID_ARG, "octree domains are cubes: dims must be equal");
     }
-    for (int c = 0; c < 3; ++c)
-        if (d->dims[c] < 2 || d->dims[c] > (1 << 20)) return fail(MBOIT_ERR_INVALID_ARG, "dims must be in [2, 2^20]");
-    if (d->brick_log2 < 0 || d->brick_log2 > 7) return fail(MBOIT_ERR_INVALID_ARG, "brick_log2 must be in [0, 7]");
+    if (!is_tet) {
+        for (int c = 0; c < 3; ++c)
+            if (d->dims[c] < 2 || d->dims[c] > (1 << 20)) return fail(MBOIT_ERR_INVALID_ARG, "dims must be in [2, 2^20]");
+        if (d->brick_log2 < 0 || d->brick_log2 > 7) return fail(MBOIT_ERR_INVALID_ARG, "brick_log2 must be in [0, 7]");
+    }
     if (!d->tf_rgba) return fail(MBOIT_ERR_INVALID_ARG, "tf_rgba is NULL");
     if (!std::isfinite(d->tf_range[0]) || !std::isfinite(d->tf_range[1]) || !(d->tf_range[1] > d->tf_range[0]))
         return fail(MBOIT_ERR_INVALID_ARG, "tf_range must be finite with tf_range[1] > tf_range[0]");
@@ -355,16 +525,24 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
                     }
         }
     }
+    TetHost th;
+    if (is_tet) {
+        const mboit_status ts = prepare_tets(d, th);
+        if (ts != MBOIT_OK) return ts;
+    }
     int dev = 0;
     MB_CUDA(cudaGetDevice(&dev));
-    cudaPointerAttributes attr{};
-    const void* data_ptr = is_amr ? (const void*)d->leaf_values : (const void*)d->field;
-    if (cudaPointerGetAttributes(&attr, data_ptr) != cudaSuccess ||
-        (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
-        cudaGetLastError();
-        return fail(MBOIT_ERR_INVALID_ARG, is_amr ? "leaf_values must be a device pointer" : "field must be a device pointer");
+    if (!is_tet) {
+        cudaPointerAttributes attr{};
+        const void* data_ptr = is_amr ? (const void*)d->leaf_values : (const void*)d->field;
+        if (cudaPointerGetAttributes(&attr, data_ptr) != cudaSuccess ||
+            (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return fail(MBOIT_ERR_INVALID_ARG,
+                        is_amr ? "leaf_values must be a device pointer" : "field must be a device pointer");
+        }
+        if (attr.device != dev) return fail(MBOIT_ERR_INVALID_ARG, "volume data lives on another device than the current one");
     }
-    if (attr.device != dev) return fail(MBOIT_ERR_INVALID_ARG, "volume data lives on another device than the current one");
 
     mboit_volume v = new (std::nothrow) mboit_volume_s();
     if (!v) return fail(MBOIT_ERR_OUT_OF_MEMORY, "host allocation failed");
@@ -407,6 +585,23 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
         v->leaf_table.assign(d->leaf_table, d->leaf_table + 4 * (size_t)d->n_leaves);
         v->desc.leaf_table = nullptr;
     }
+    if (is_tet) {
+        g.field = nullptr;
+        g.nx = g.ny = g.nz = 0;
+        g.nbx = g.nby = g.nbz = 0;
+        g.hx = d->tet_box[0];
+        g.hy = d->tet_box[1];
+        g.hz = d->tet_box[2];
+        v->nbricks = d->n_tets;  // the units of a mesh are its tets
+        v->field_bytes = (size_t)d->n_verts * sizeof(float);
+        v->tet_cells.assign(d->tet_cells, d->tet_cells + 4 * (size_t)d->n_tets);
+        v->tet_xyz.resize(3 * (size_t)d->n_verts);
+        for (int64_t i = 0; i < d->n_verts; ++i)
+            for (int c = 0; c < 3; ++c) v->tet_xyz[3 * i + c] = d->tet_verts[4 * i + c];
+        v->desc.tet_verts = nullptr;
+        v->desc.tet_cells = nullptr;
+        v->desc.tet_neighbors = nullptr;
+    }
     v->pob.assign((size_t)v->nbricks, -1);
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&v->d_tf, 256 * sizeof(float4));
@@ -430,6 +625,32 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
         v->amr.fdim = (int32_t)fdim;
         v->amr.nv = (1 << d->brick_log2) + 1;
         v->amr.max_level = d->max_level;
+    }
+    if (e == cudaSuccess && is_tet) {
+        auto up = [&](auto*& dst, const auto& src) {
+            using T = typename std::remove_reference<decltype(src)>::type::value_type;
+            cudaError_t r = cudaMalloc(&dst, std::max<size_t>(src.size(), 1) * sizeof(T));
+            if (r == cudaSuccess && !src.empty())
+                r = cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+            return r;
+        };
+        e = up(v->d_tverts, th.verts);
+        if (e == cudaSuccess) e = up(v->d_tcells, th.cells);
+        if (e == cudaSuccess) e = up(v->d_tnbrs, th.nbrs);
+        if (e == cudaSuccess) e = up(v->d_bin_start, th.bin_start);
+        if (e == cudaSuccess) e = up(v->d_bin_tets, th.bin_tets);
+        if (e == cudaSuccess) e = cudaMalloc(&v->d_tvals, v->field_bytes);
+        mb::TetD& m = v->tet;
+        m.g = g;
+        m.verts = v->d_tverts;
+        m.cells = v->d_tcells;
+        m.nbrs = v->d_tnbrs;
+        m.bin_start = v->d_bin_start;
+        m.bin_tets = v->d_bin_tets;
+        for (int c = 0; c < 3; ++c) m.bdim[c] = th.bdim[c];
+        m.bin_shift = th.bin_shift;
+        m.qscale = std::ldexp(1.0f, d->quantum_log2);
+        m.max_walk = 64;
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&v->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = mb::prepare_kernels();
@@ -455,6 +676,12 @@ mboit_status mboit_destroy_volume(mboit_volume v) {
         cudaFree(v->d_tf);
         cudaFree(v->d_leaves);
         cudaFree(v->d_fmap);
+        cudaFree(v->d_tverts);
+        cudaFree(v->d_tcells);
+        cudaFree(v->d_tnbrs);
+        cudaFree(v->d_bin_start);
+        cudaFree(v->d_bin_tets);
+        cudaFree(v->d_tvals);
         cudaFree(v->d_pob);
         cudaFree(v->d_sel);
         cudaFree(v->d_ctr);
@@ -496,6 +723,7 @@ mboit_status mboit_add_piece(mboit_volume v, const int32_t* ids, int64_t n, int3
             return fail(MBOIT_ERR_INVALID_ARG, "brick " + std::to_string(b) + " already belongs to piece " +
                                                    std::to_string(v->pob[b]) + " (pieces must not overlap)");
         seen[b] = 1;
+        if (v->kind != MBOIT_GRID) continue;
         const int bc[3] = {b % g.nbx, (b / g.nbx) % g.nby, b / (g.nbx * g.nby)};
         for (int c = 0; c < 3; ++c) {
             bmin[c] = bc[c] < bmin[c] ? bc[c] : bmin[c];
@@ -511,7 +739,26 @@ mboit_status mboit_add_piece(mboit_volume v, const int32_t* ids, int64_t n, int3
     const int B = 1 << g.brick_log2;
     const float hi[3] = {g.hx, g.hy, g.hz};
     mb::PieceBox box;
-    if (v->kind == MBOIT_AMR) {
+    if (v->kind == MBOIT_TET) {
+        // union of the tets' boxes, padded by one quantum (a sample snaps by up to half of one)
+        const float pad = std::ldexp(1.0f, -v->desc.quantum_log2);
+        for (int c = 0; c < 3; ++c) {
+            box.lo[c] = 3.0e38f;
+            box.hi[c] = -3.0e38f;
+        }
+        for (int64_t i = 0; i < n; ++i)
+            for (int k = 0; k < 4; ++k) {
+                const float* P = &v->tet_xyz[3 * (size_t)v->tet_cells[4 * (size_t)h[i] + k]];
+                for (int c = 0; c < 3; ++c) {
+                    box.lo[c] = std::min(box.lo[c], P[c]);
+                    box.hi[c] = std::max(box.hi[c], P[c]);
+                }
+            }
+        for (int c = 0; c < 3; ++c) {
+            box.lo[c] = std::max(box.lo[c] - pad, 0.0f);
+            box.hi[c] = std::min(box.hi[c] + pad, hi[c]);
+        }
+    } else if (v->kind == MBOIT_AMR) {
         // union of the leaves' boxes
         for (int c = 0; c < 3; ++c) {
             box.lo[c] = 3.0e38f;
@@ -556,21 +803,18 @@ mboit_status mboit_render_moments(mboit_volume v, const mboit_view* views, int32
     if ((st = select_pieces(v, pieces, n_pieces, list, &mask)) != MBOIT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->samples[0], 0, sizeof(unsigned long long), s));
-    const bool amr = v->kind == MBOIT_AMR;
     if (mode == MBOIT_MOMENTS_REDUCED) {
-        if (amr)
-            MB_CUDA(mb::launch_pass1_amr(v->amr, v->d_tf, mask, vt, moments, v->d_ctr, s));
-        else
-            MB_CUDA(mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1));
+        MB_CUDA(pass1_batched(v, mask, vt, moments, s));
     } else {
         const int32_t slots = (int32_t)list.size();
         for (int32_t j = 0; j < slots; ++j) {
-            if (amr)
-                MB_CUDA(mb::launch_pass1_piece(v->amr, v->d_tf, v->d_pob, list[j], v->boxes[list[j]], vt, j, slots,
-                                               moments, v->d_ctr, s));
+            const mb::PieceBox& box = v->boxes[list[j]];
+            if (v->kind == MBOIT_AMR)
+                MB_CUDA(mb::launch_pass1_piece(v->amr, v->d_tf, v->d_pob, list[j], box, vt, j, slots, moments, v->d_ctr, s));
+            else if (v->kind == MBOIT_TET)
+                MB_CUDA(mb::launch_pass1_piece(v->tet, v->d_tf, v->d_pob, list[j], box, vt, j, slots, moments, v->d_ctr, s));
             else
-                MB_CUDA(mb::launch_pass1_piece(v->grid, v->d_tf, v->d_pob, list[j], v->boxes[list[j]], vt, j, slots,
-                                               moments, v->d_ctr, s));
+                MB_CUDA(mb::launch_pass1_piece(v->grid, v->d_tf, v->d_pob, list[j], box, vt, j, slots, moments, v->d_ctr, s));
         }
     }
     return MBOIT_OK;
@@ -594,23 +838,23 @@ mboit_status mboit_reconstruct_blend(mboit_volume v, const mboit_view* views, in
     if ((st = select_pieces(v, pieces, n_pieces, list, &mask)) != MBOIT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->samples[1], 0, 2 * sizeof(unsigned long long), s));
-    const bool amr = v->kind == MBOIT_AMR;
     if (mode == MBOIT_COLOR_PER_PIECE) {
         const int32_t slots = (int32_t)list.size();
         for (int32_t j = 0; j < slots; ++j) {
-            if (amr)
-                MB_CUDA(mb::launch_pass2_piece(v->amr, v->d_tf, v->d_pob, list[j], v->boxes[list[j]], vt, j, slots,
-                                               global_moments, color, v->d_ctr, s));
+            const mb::PieceBox& box = v->boxes[list[j]];
+            if (v->kind == MBOIT_AMR)
+                MB_CUDA(mb::launch_pass2_piece(v->amr, v->d_tf, v->d_pob, list[j], box, vt, j, slots, global_moments,
+                                               color, v->d_ctr, s));
+            else if (v->kind == MBOIT_TET)
+                MB_CUDA(mb::launch_pass2_piece(v->tet, v->d_tf, v->d_pob, list[j], box, vt, j, slots, global_moments,
+                                               color, v->d_ctr, s));
             else
-                MB_CUDA(mb::launch_pass2_piece(v->grid, v->d_tf, v->d_pob, list[j], v->boxes[list[j]], vt, j, slots,
-                                               global_moments, color, v->d_ctr, s));
+                MB_CUDA(mb::launch_pass2_piece(v->grid, v->d_tf, v->d_pob, list[j], box, vt, j, slots, global_moments,
+                                               color, v->d_ctr, s));
         }
     } else {
         const int32_t md = mode == MBOIT_COLOR_RESOLVED ? mb::kColorResolved : mb::kColorReduced;
-        if (amr)
-            MB_CUDA(mb::launch_pass2_amr(v->amr, v->d_tf, mask, vt, global_moments, color, md, v->d_ctr, s));
-        else
-            MB_CUDA(mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, global_moments, color, md, v->d_ctr, s, v->tune2));
+        MB_CUDA(pass2_batched(v, mask, vt, global_moments, color, md, s));
     }
     return MBOIT_OK;
 }
@@ -639,7 +883,7 @@ mboit_status mboit_composite(mboit_volume v, int32_t op, int32_t width, int32_t 
     if (st != MBOIT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (op == MBOIT_OP_MOMENTS_SUM) {
-        MB_CUDA(mb::launch_moments_sum(v->kind == MBOIT_AMR ? v->amr.g : v->grid, vt, n_inputs, in, out, s));
+        MB_CUDA(mb::launch_moments_sum(v->grid, vt, n_inputs, in, out, s));
     } else {
         MB_CUDA(mb::launch_color_resolve(vt, n_inputs, static_cast<const float*>(in), static_cast<float*>(out),
                                          global_moments, b, raw ? 1 : 0, s));
@@ -672,15 +916,8 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
         cudaStream_t cs = v->cap_stream;
         MB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemsetAsync(&v->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), cs);
-        const bool amr = v->kind == MBOIT_AMR;
-        if (e == cudaSuccess)
-            e = amr ? mb::launch_pass1_amr(v->amr, v->d_tf, mask, vt, moments_scratch, v->d_ctr, cs)
-                    : mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, cs, v->tune1);
-        if (e == cudaSuccess)
-            e = amr ? mb::launch_pass2_amr(v->amr, v->d_tf, mask, vt, moments_scratch, rgba, mb::kColorResolved,
-                                           v->d_ctr, cs)
-                    : mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba, mb::kColorResolved,
-                                             v->d_ctr, cs, v->tune2);
+        if (e == cudaSuccess) e = pass1_batched(v, mask, vt, moments_scratch, cs);
+        if (e == cudaSuccess) e = pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved, cs);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -709,8 +946,14 @@ mboit_status mboit_render_frame_host(mboit_volume v, const float* field_host, co
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     {
         DeviceGuard dg(v->device);
-        float* dst = const_cast<float*>(v->kind == MBOIT_AMR ? v->amr.values : v->grid.field);
-        MB_CUDA(cudaMemcpyAsync(dst, field_host, v->field_bytes, cudaMemcpyHostToDevice, s));
+        if (v->kind == MBOIT_TET) {
+            // vertex values live in the vertex records: stage, then scatter
+            MB_CUDA(cudaMemcpyAsync(v->d_tvals, field_host, v->field_bytes, cudaMemcpyHostToDevice, s));
+            MB_CUDA(mb::launch_tet_values(v->d_tverts, v->d_tvals, (int64_t)(v->field_bytes / sizeof(float)), s));
+        } else {
+            float* dst = const_cast<float*>(v->kind == MBOIT_AMR ? v->amr.values : v->grid.field);
+            MB_CUDA(cudaMemcpyAsync(dst, field_host, v->field_bytes, cudaMemcpyHostToDevice, s));
+        }
     }
     if ((st = mboit_render_frame(v, views, n_views, moments_scratch, rgba_device, stream)) != MBOIT_OK) return st;
     int64_t floats = 0;
@@ -776,15 +1019,20 @@ mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int3
     MB_CUDA(ensure_capacity(v->sl_bsum, v->cap_bsum, nb));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->segments, 0, sizeof(unsigned long long) + sizeof(int32_t), s));
-    const bool amr = v->kind == MBOIT_AMR;
-    for (int32_t p = 0; p < K; ++p) {
-        if (amr)
-            MB_CUDA(mb::launch_sortlast_march(false, v->amr, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts,
-                                              nullptr, nullptr, nullptr, s));
-        else
-            MB_CUDA(mb::launch_sortlast_march(false, v->grid, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts,
-                                              nullptr, nullptr, nullptr, s));
-    }
+    auto march = [&](bool fill, int32_t p) {
+        const int64_t* st = fill ? v->sl_starts : nullptr;
+        int32_t* key = fill ? v->sl_key : nullptr;
+        float4* col = fill ? v->sl_col : nullptr;
+        if (v->kind == MBOIT_AMR)
+            return mb::launch_sortlast_march(fill, v->amr, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts, st,
+                                             key, col, s);
+        if (v->kind == MBOIT_TET)
+            return mb::launch_sortlast_march(fill, v->tet, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts, st,
+                                             key, col, s);
+        return mb::launch_sortlast_march(fill, v->grid, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts, st,
+                                         key, col, s);
+    };
+    for (int32_t p = 0; p < K; ++p) MB_CUDA(march(false, p));
     MB_CUDA(mb::launch_sortlast_offsets(vt, K, v->sl_counts, v->sl_totals, v->sl_base, v->sl_bsum, v->sl_starts,
                                         total_px, s));
     int64_t total = 0;
@@ -792,14 +1040,7 @@ mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int3
     MB_CUDA(cudaStreamSynchronize(s));
     MB_CUDA(ensure_capacity(v->sl_key, v->cap_seg, (size_t)total));
     MB_CUDA(ensure_capacity(v->sl_col, v->cap_col, (size_t)total));
-    for (int32_t p = 0; p < K; ++p) {
-        if (amr)
-            MB_CUDA(mb::launch_sortlast_march(true, v->amr, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts,
-                                              v->sl_starts, v->sl_key, v->sl_col, s));
-        else
-            MB_CUDA(mb::launch_sortlast_march(true, v->grid, v->d_tf, v->d_pob, p, v->boxes[p], vt, p, K, v->sl_counts,
-                                              v->sl_starts, v->sl_key, v->sl_col, s));
-    }
+    for (int32_t p = 0; p < K; ++p) MB_CUDA(march(true, p));
     MB_CUDA(mb::launch_sortlast_blend(v->sl_base, v->sl_key, v->sl_col, rgba, total_px, v->d_ctr, s));
     if (segments_per_pixel)
         MB_CUDA(cudaMemcpyAsync(segments_per_pixel, v->sl_totals, (size_t)total_px * sizeof(int32_t),
@@ -811,8 +1052,8 @@ mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int3
 mboit_status mboit_set_tuning(mboit_volume v, int32_t pass1, int32_t pass2) {
     g_err.clear();
     if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
-    if (v->kind == MBOIT_AMR && (pass1 != 0 || pass2 != 0))
-        return fail(MBOIT_ERR_INVALID_ARG, "octree volumes have one configuration (0)");
+    if (v->kind != MBOIT_GRID && (pass1 != 0 || pass2 != 0))
+        return fail(MBOIT_ERR_INVALID_ARG, "octree and mesh volumes have one configuration (0)");
     if (!mb::stage_config_eligible(v->grid, pass1) || !mb::stage_config_eligible(v->grid, pass2))
         return fail(MBOIT_ERR_INVALID_ARG, "tuning must be in [0, " + std::to_string(mb::kNumStageConfigs - 1) +
                                                "]; 2-4 need dims[0] % 4 == 0 and a 16-byte aligned field");
@@ -836,7 +1077,7 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
     std::vector<int32_t> list;
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, nullptr, 0, list, &mask)) != MBOIT_OK) return st;
-    if (v->kind == MBOIT_AMR) {  // one configuration only
+    if (v->kind != MBOIT_GRID) {  // one configuration only
         if (chosen) chosen[0] = chosen[1] = 0;
         return MBOIT_OK;
     }

@@ -57,6 +57,24 @@ struct AmrD {
     int32_t fdim, nv, max_level, pad;
 };
 
+// Tetrahedral mesh as the kernels see it.  `g` carries the box
+// [0, hx) x [0, hy) x [0, hz) and every sampling and transfer-function
+// parameter (its field/brick members are unused).  Coordinates are integers
+// in quanta of 2^-quantum_log2; a point snaps by nearest-even rounding of
+// p * qscale.
+struct TetD {
+    GridD g;
+    const int4* verts;         // snapped x, y, z and the value's float32 bits
+    const int4* cells;         // corner vertex ids, positively oriented
+    const int4* nbrs;          // tet across the face opposite corner i, -1 on the boundary
+    const int32_t* bin_start;  // [nbins + 1]: bins of 2^bin_shift quanta, CSR over
+    const int32_t* bin_tets;   //   the tets whose snapped bounding box meets the bin
+    int32_t bdim[3];
+    int32_t bin_shift;
+    float qscale;              // 2^quantum_log2
+    int32_t max_walk;          // walk steps before a bin search takes over
+};
+
 // Number of shared-memory window configurations of the fused passes (the
 // autotuner's choices).  Configurations 2-4 use 16-byte loads and need
 // nx % 4 == 0 and a 16-byte aligned field; 0 and 1 work everywhere.
@@ -107,6 +125,24 @@ cudaError_t launch_sortlast_march(bool fill, const AmrD& a, const float4* tf, co
                                   int32_t piece, const PieceBox& box, const ViewTable& vt, int32_t slot,
                                   int32_t n_slots, int32_t* counts, const int64_t* starts, int32_t* seg_key,
                                   float4* seg_col, cudaStream_t s);
+// Tetrahedral-mesh versions (walks between face neighbours; same layouts).
+cudaError_t launch_pass1_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
+                             void* moments, Counters* ctr, cudaStream_t s);
+cudaError_t launch_pass2_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
+                             const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s);
+cudaError_t launch_pass1_piece(const TetD& m, const float4* tf, const int32_t* piece_of_unit, int32_t piece,
+                               const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
+                               void* moments, Counters* ctr, cudaStream_t s);
+cudaError_t launch_pass2_piece(const TetD& m, const float4* tf, const int32_t* piece_of_unit, int32_t piece,
+                               const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
+                               const void* moments, float* color, Counters* ctr, cudaStream_t s);
+cudaError_t launch_sortlast_march(bool fill, const TetD& m, const float4* tf, const int32_t* piece_of_unit,
+                                  int32_t piece, const PieceBox& box, const ViewTable& vt, int32_t slot,
+                                  int32_t n_slots, int32_t* counts, const int64_t* starts, int32_t* seg_key,
+                                  float4* seg_col, cudaStream_t s);
+// Writes n vertex values into the .w words of the mesh's vertex records.
+cudaError_t launch_tet_values(int4* verts, const float* values, int64_t n, cudaStream_t s);
+
 // Image-space reductions.
 cudaError_t launch_moments_sum(const GridD& g, const ViewTable& vt, int32_t n_inputs, const void* in, void* out,
                                cudaStream_t s);

@@ -615,6 +615,7 @@ __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ Gri
 // and the unit's box (for skipping units a piece does not own).
 __device__ __forceinline__ const GridD& common(const GridD& g) { return g; }
 __device__ __forceinline__ const GridD& common(const AmrD& a) { return a.g; }
+__device__ __forceinline__ const GridD& common(const TetD& m) { return m.g; }
 
 __device__ __forceinline__ int unit_of(const GridD& g, const float p[3]) {
     const int ix = (int)p[0], iy = (int)p[1], iz = (int)p[2];
@@ -687,10 +688,21 @@ __device__ __forceinline__ int skip_unit(const V& vol, int unit, const float o[3
     return kn > 4194303.0f ? 4194304 : (int)kn;
 }
 
+// Per-ray state of a sampler: none for grids and octrees (a point's unit is
+// a table lookup), the current tet for meshes (the walk starts there).
+struct NoWalk {};
+struct TetWalk {
+    int T = -1;
+    int4 v[4];
+};
+template <class V> struct WalkOf { using type = NoWalk; };
+template <> struct WalkOf<TetD> { using type = TetWalk; };
+
 // One owned sample of `piece` at lattice index k, or the next index to try.
 template <class V>
 __device__ __forceinline__ bool piece_sample(const V& vol, const int32_t* __restrict__ pou, int piece, float t,
-                                             const float o[3], const float d[3], int k, float& val, int& k_next) {
+                                             const float o[3], const float d[3], int k, float& val, int& k_next,
+                                             NoWalk&) {
     const GridD& g = common(vol);
     k_next = k + 1;
     const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
@@ -733,11 +745,12 @@ __global__ void __launch_bounds__(128) k_pass1_piece(const __grid_constant__ V v
         make_ray(S.v, px, py, o, d);
         int k0, k1;
         if (lattice_range(o, d, box.lo, box.hi, g.step, &k0, &k1)) {
+            typename WalkOf<V>::type walk;
             for (int k = k0; k <= k1;) {
                 const float t = lattice_t(k, g.step);
                 float val;
                 int kn;
-                const bool owned = piece_sample(vol, pob, piece, t, o, d, k, val, kn);
+                const bool owned = piece_sample(vol, pob, piece, t, o, d, k, val, kn, walk);
                 k = kn;
                 if (owned) body(t, val);
             }
@@ -780,11 +793,12 @@ __global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ V v
         int k0, k1;
         if (lattice_range(o, d, box.lo, box.hi, g.step, &k0, &k1)) {
             auto body = make_blend_body<MS>(s_tf, g, S, moments, S.moment_off, pix, true);
+            typename WalkOf<V>::type walk;
             for (int k = k0; k <= k1;) {
                 const float t = lattice_t(k, g.step);
                 float val;
                 int kn;
-                const bool owned = piece_sample(vol, pob, piece, t, o, d, k, val, kn);
+                const bool owned = piece_sample(vol, pob, piece, t, o, d, k, val, kn, walk);
                 k = kn;
                 if (owned) body(t, val);
             }
@@ -798,13 +812,158 @@ __global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ V v
 }
 
 // ------------------------------------------------------------------------
-// fused, persistent passes over a brick octree (direct gathers): the leaf of
-// each lattice point comes from the finest-brick map, its value from the
-// leaf's own vertex block
+// tetrahedral meshes: exact point location.  A point snaps to integer
+// quanta; D_i(q), six times the signed volume of the tet with corner i
+// replaced by q, is n_i . (q - b_i) with n_i the cross product of two edges
+// of face i and b_i a corner of it.  All of it is exact in 64-bit integers
+// (the volume checks the coordinate range), so the two tets of a face see
+// exactly opposite signs; a zero is decided by the symbolic perturbation
+// q + (e, e^2, e^3): the sign of n_i.x, then n_i.y, then n_i.z.
+
+__device__ __forceinline__ void snap_point(const TetD& m, const float p[3], int q[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) q[c] = __float2int_rn(fmul(p[c], m.qscale));
+}
+
+__device__ __forceinline__ bool face_positive(const int4 a, const int4 b, const int4 base, const int q[3],
+                                              long long& D) {
+    const int ax = a.x - base.x, ay = a.y - base.y, az = a.z - base.z;
+    const int bx = b.x - base.x, by = b.y - base.y, bz = b.z - base.z;
+    const long long nx = (long long)ay * bz - (long long)az * by;
+    const long long ny = (long long)az * bx - (long long)ax * bz;
+    const long long nz = (long long)ax * by - (long long)ay * bx;
+    D = nx * (long long)(q[0] - base.x) + ny * (long long)(q[1] - base.y) + nz * (long long)(q[2] - base.z);
+    if (D != 0) return D > 0;
+    if (nx != 0) return nx > 0;
+    if (ny != 0) return ny > 0;
+    return nz > 0;
+}
+
+// D_0..D_3 of q; returns -1 if q is inside, else a face that q lies
+// strictly outside of (the first one from `rot`, so that walks do not
+// always prefer one face).
+__device__ __forceinline__ int tet_exit_face(const int4 v[4], const int q[3], long long D[4], int rot) {
+    bool in[4];
+    in[0] = face_positive(v[2], v[1], v[3], q, D[0]);
+    in[1] = face_positive(v[2], v[3], v[0], q, D[1]);
+    in[2] = face_positive(v[3], v[1], v[0], q, D[2]);
+    in[3] = face_positive(v[1], v[2], v[0], q, D[3]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int f = (rot + j) & 3;
+        if (!in[f]) return f;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ void load_tet(const TetD& m, int T, int4 v[4]) {
+    const int4 c = __ldg(m.cells + T);
+    v[0] = __ldg(m.verts + c.x);
+    v[1] = __ldg(m.verts + c.y);
+    v[2] = __ldg(m.verts + c.z);
+    v[3] = __ldg(m.verts + c.w);
+}
+
+__device__ __forceinline__ int bin_of(const TetD& m, const int q[3]) {
+    int b[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) b[c] = min(max(q[c] >> m.bin_shift, 0), m.bdim[c] - 1);
+    return (b[2] * m.bdim[1] + b[1]) * m.bdim[0] + b[0];
+}
+
+// Finds the tet owning q.  The walk starts at T (the tet of the previous
+// sample; -1: the first tet listed in q's bin) and crosses a face that q is
+// outside of, at most max_walk times.  If it leaves the mesh or runs long,
+// the tets listed in q's bin are tested one by one.  On success T is the
+// owner, v its corners and D its four volumes at q; on failure (no tet
+// owns q) T and v still name one tet near q.
+__device__ __forceinline__ bool tet_walk(const TetD& m, int& T, int4 v[4], const int q[3], long long D[4]) {
+    if (T < 0) {
+        const int b = bin_of(m, q);
+        const int j0 = __ldg(m.bin_start + b);
+        if (j0 == __ldg(m.bin_start + b + 1)) return false;  // no tet comes near q
+        T = __ldg(m.bin_tets + j0);
+        load_tet(m, T, v);
+    }
+    for (int step = 0;; ++step) {
+        const int f = tet_exit_face(v, q, D, step);
+        if (f < 0) return true;
+        if (step + 1 >= m.max_walk) break;
+        const int4 nb = __ldg(m.nbrs + T);
+        const int nt = f == 0 ? nb.x : f == 1 ? nb.y : f == 2 ? nb.z : nb.w;
+        if (nt < 0) break;
+        T = nt;
+        load_tet(m, T, v);
+    }
+    const int b = bin_of(m, q);
+    const int j1 = __ldg(m.bin_start + b + 1);
+    for (int j = __ldg(m.bin_start + b); j < j1; ++j) {
+        const int t = __ldg(m.bin_tets + j);
+        int4 w[4];
+        load_tet(m, t, w);
+        if (tet_exit_face(w, q, D, 0) < 0) {
+            T = t;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = w[i];
+            return true;
+        }
+    }
+    return false;
+}
+
+// Barycentric interpolation of the corner values: lambda_i = D_i / sum D.
+__device__ __forceinline__ float tet_value(const long long D[4], const int4 v[4]) {
+    const float inv = 1.0f / __ll2float_rn(D[0] + D[1] + D[2] + D[3]);
+    float s = __ll2float_rn(D[0]) * __int_as_float(v[0].w);
+    s = ffma(__ll2float_rn(D[1]), __int_as_float(v[1].w), s);
+    s = ffma(__ll2float_rn(D[2]), __int_as_float(v[2].w), s);
+    s = ffma(__ll2float_rn(D[3]), __int_as_float(v[3].w), s);
+    return s * inv;
+}
+
+__device__ __forceinline__ bool piece_sample(const TetD& m, const int32_t* __restrict__ pou, int piece, float t,
+                                             const float o[3], const float d[3], int k, float& val, int& k_next,
+                                             TetWalk& w) {
+    const GridD& g = m.g;
+    k_next = k + 1;
+    const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+    if (!(p[0] >= 0.0f && p[0] < g.hx && p[1] >= 0.0f && p[1] < g.hy && p[2] >= 0.0f && p[2] < g.hz)) return false;
+    int q[3];
+    snap_point(m, p, q);
+    long long D[4];
+    if (!tet_walk(m, w.T, w.v, q, D)) return false;
+    if (__ldg(pou + w.T) != piece) return false;
+    val = tet_value(D, w.v);
+    return true;
+}
+
+// ------------------------------------------------------------------------
+// fused, persistent passes over a brick octree or a tetrahedral mesh
+// (direct gathers).  Octree: the leaf of each lattice point comes from the
+// finest-brick map, its value from the leaf's own vertex block.  Mesh: the
+// tet comes from a walk that starts at the previous sample's tet.
 
 template <bool kSel, class Body>
-__device__ __forceinline__ void march_amr(const AmrD& a, const uint8_t* __restrict__ sel, const float o[3],
-                                          const float d[3], int k0, int k1, Body& body) {
+__device__ __forceinline__ void march_unit(const TetD& m, const uint8_t* __restrict__ sel, const float o[3],
+                                           const float d[3], int k0, int k1, Body& body) {
+    const GridD& g = m.g;
+    if (k0 > k1) return;
+    TetWalk w;
+    const float tz = lattice_t(k1, g.step);
+    for (float t = lattice_t(k0, g.step); t <= tz; t += g.step) {
+        const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+        int q[3];
+        snap_point(m, p, q);
+        long long D[4];
+        if (!tet_walk(m, w.T, w.v, q, D)) continue;
+        if (kSel && !__ldg(sel + w.T)) continue;
+        body(t, tet_value(D, w.v));
+    }
+}
+
+template <bool kSel, class Body>
+__device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restrict__ sel, const float o[3],
+                                           const float d[3], int k0, int k1, Body& body) {
     const GridD& g = a.g;
     if (k0 > k1) return;
     const float tz = lattice_t(k1, g.step);
@@ -817,10 +976,10 @@ __device__ __forceinline__ void march_amr(const AmrD& a, const uint8_t* __restri
     }
 }
 
-template <bool kSel, int MS>
-__global__ void __launch_bounds__(256) k_pass1_amr(const __grid_constant__ AmrD a, const float4* __restrict__ tf,
-                                                   const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
-                                                   char* __restrict__ moments, Counters* __restrict__ ctr) {
+template <class V, bool kSel, int MS>
+__global__ void __launch_bounds__(256) k_pass1_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
+                                                    const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
+                                                    char* __restrict__ moments, Counters* __restrict__ ctr) {
     __shared__ float2 s_sig[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float s0 = tf[i].w;
@@ -836,17 +995,17 @@ __global__ void __launch_bounds__(256) k_pass1_amr(const __grid_constant__ AmrD 
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
         auto body = make_moment_body<MS>(s_sig, g, S.v);
-        march_amr<kSel>(a, sel, o, d, k0, k1, body);
+        march_unit<kSel>(a, sel, o, d, k0, k1, body);
         if (valid) body.store(g, moments, S, S.moment_off, py * S.v.width + px);
         warp_add_u64(&ctr->samples[0], body.n);
     }
 }
 
-template <bool kSel, int MS>
-__global__ void __launch_bounds__(256) k_pass2_amr(const __grid_constant__ AmrD a, const float4* __restrict__ tf,
-                                                   const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
-                                                   const char* __restrict__ moments, float* __restrict__ color, int mode,
-                                                   Counters* __restrict__ ctr) {
+template <class V, bool kSel, int MS>
+__global__ void __launch_bounds__(256) k_pass2_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
+                                                    const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
+                                                    const char* __restrict__ moments, float* __restrict__ color, int mode,
+                                                    Counters* __restrict__ ctr) {
     __shared__ float4 s_tf[512];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float4 e0 = tf[i], e1 = i < 255 ? tf[i + 1] : tf[i];
@@ -866,7 +1025,7 @@ __global__ void __launch_bounds__(256) k_pass2_amr(const __grid_constant__ AmrD 
         float o[3], d[3];
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
-        march_amr<kSel>(a, sel, o, d, k0, k1, body);
+        march_unit<kSel>(a, sel, o, d, k0, k1, body);
         if (valid) {
             float4* out = reinterpret_cast<float4*>(color + S.color_off) + pix;
             *out = mode == kColorResolved ? resolve_pixel(body.C, body.b0, make_float4(0.0f, 0.0f, 0.0f, 0.0f), raw)
@@ -919,11 +1078,12 @@ __global__ void __launch_bounds__(128) k_sortlast_piece(const __grid_constant__ 
         int prev = -2, key = 0;
         float4 cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         float tr = 1.0f;
+        typename WalkOf<V>::type walk;
         for (int k = k0; k <= k1;) {
             const float t = lattice_t(k, g.step);
             float val;
             int kn;
-            if (!piece_sample(vol, pob, piece, t, o, d, k, val, kn)) {
+            if (!piece_sample(vol, pob, piece, t, o, d, k, val, kn, walk)) {
                 k = kn;
                 continue;
             }
@@ -1247,15 +1407,22 @@ const void* pass1_fn(int cfg, bool sel, int ms) {
 const void* pass2_fn(int cfg, bool sel, int ms) {
     return ms == 3 ? pass2_fn_ms<3>(cfg, sel) : ms == 4 ? pass2_fn_ms<4>(cfg, sel) : pass2_fn_ms<0>(cfg, sel);
 }
-const void* amr1_fn(bool sel, int ms) {
-    if (ms == 3) return sel ? (const void*)k_pass1_amr<true, 3> : (const void*)k_pass1_amr<false, 3>;
-    if (ms == 4) return sel ? (const void*)k_pass1_amr<true, 4> : (const void*)k_pass1_amr<false, 4>;
-    return sel ? (const void*)k_pass1_amr<true, 0> : (const void*)k_pass1_amr<false, 0>;
+template <class V>
+const void* unit1_fn(bool sel, int ms) {
+    if (ms == 3) return sel ? (const void*)k_pass1_unit<V, true, 3> : (const void*)k_pass1_unit<V, false, 3>;
+    if (ms == 4) return sel ? (const void*)k_pass1_unit<V, true, 4> : (const void*)k_pass1_unit<V, false, 4>;
+    return sel ? (const void*)k_pass1_unit<V, true, 0> : (const void*)k_pass1_unit<V, false, 0>;
 }
-const void* amr2_fn(bool sel, int ms) {
-    if (ms == 3) return sel ? (const void*)k_pass2_amr<true, 3> : (const void*)k_pass2_amr<false, 3>;
-    if (ms == 4) return sel ? (const void*)k_pass2_amr<true, 4> : (const void*)k_pass2_amr<false, 4>;
-    return sel ? (const void*)k_pass2_amr<true, 0> : (const void*)k_pass2_amr<false, 0>;
+template <class V>
+const void* unit2_fn(bool sel, int ms) {
+    if (ms == 3) return sel ? (const void*)k_pass2_unit<V, true, 3> : (const void*)k_pass2_unit<V, false, 3>;
+    if (ms == 4) return sel ? (const void*)k_pass2_unit<V, true, 4> : (const void*)k_pass2_unit<V, false, 4>;
+    return sel ? (const void*)k_pass2_unit<V, true, 0> : (const void*)k_pass2_unit<V, false, 0>;
+}
+
+__global__ void k_tet_values(int4* __restrict__ verts, const float* __restrict__ values, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        verts[i].w = __float_as_int(values[i]);
 }
 
 bool vec_config(int cfg) { return cfg == 2 || cfg == 3 || cfg == 4; }
@@ -1282,6 +1449,11 @@ cudaError_t prepare_kernels() {
                          (const void*)k_moments_sum,        (const void*)k_color_resolve,
                          (const void*)k_sortlast_piece<GridD, true>, (const void*)k_sortlast_piece<GridD, false>,
                          (const void*)k_sortlast_piece<AmrD, true>, (const void*)k_sortlast_piece<AmrD, false>,
+                         (const void*)k_pass1_piece<TetD, 0>, (const void*)k_pass2_piece<TetD, 0>,
+                         (const void*)k_pass1_piece<TetD, 3>, (const void*)k_pass2_piece<TetD, 3>,
+                         (const void*)k_pass1_piece<TetD, 4>, (const void*)k_pass2_piece<TetD, 4>,
+                         (const void*)k_sortlast_piece<TetD, true>, (const void*)k_sortlast_piece<TetD, false>,
+                         (const void*)k_tet_values,
                          (const void*)k_sortlast_totals,    (const void*)k_sortlast_starts,
                          (const void*)k_scan_blocks,        (const void*)k_scan_sums,
                          (const void*)k_scan_add,           (const void*)k_sortlast_blend};
@@ -1305,8 +1477,10 @@ cudaError_t prepare_kernels() {
             }
     for (int ms : sets)
         for (int sel = 0; sel < 2; ++sel) {
-            persistent_blocks(amr1_fn(sel, ms), 256, 0);
-            persistent_blocks(amr2_fn(sel, ms), 256, 0);
+            persistent_blocks(unit1_fn<AmrD>(sel, ms), 256, 0);
+            persistent_blocks(unit2_fn<AmrD>(sel, ms), 256, 0);
+            persistent_blocks(unit1_fn<TetD>(sel, ms), 256, 0);
+            persistent_blocks(unit2_fn<TetD>(sel, ms), 256, 0);
         }
     return cudaGetLastError();
 }
@@ -1434,7 +1608,7 @@ cudaError_t launch_pass1_amr(const AmrD& a, const float4* tf, const uint8_t* uni
                              void* moments, Counters* ctr, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const void* fn = amr1_fn(unit_sel != nullptr, a.g.trig.n);
+    const void* fn = unit1_fn<AmrD>(unit_sel != nullptr, a.g.trig.n);
     char* m = static_cast<char*>(moments);
     void* args[] = {(void*)&a, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&m, (void*)&ctr};
     return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
@@ -1444,7 +1618,7 @@ cudaError_t launch_pass2_amr(const AmrD& a, const float4* tf, const uint8_t* uni
                              const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[1], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const void* fn = amr2_fn(unit_sel != nullptr, a.g.trig.n);
+    const void* fn = unit2_fn<AmrD>(unit_sel != nullptr, a.g.trig.n);
     const char* m = static_cast<const char*>(moments);
     int md = mode;
     void* args[] = {(void*)&a, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&m, (void*)&color, (void*)&md,
@@ -1485,6 +1659,70 @@ cudaError_t launch_sortlast_march(bool fill, const AmrD& a, const float4* tf, co
     else
         k_sortlast_piece<AmrD, false><<<blocks, 128, 0, s>>>(a, tf, pou, piece, box, vt, slot, n_slots, counts, starts,
                                                              seg_key, seg_col);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass1_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
+                             void* moments, Counters* ctr, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const void* fn = unit1_fn<TetD>(unit_sel != nullptr, m.g.trig.n);
+    char* mo = static_cast<char*>(moments);
+    void* args[] = {(void*)&m, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&mo, (void*)&ctr};
+    return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
+}
+
+cudaError_t launch_pass2_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
+                             const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&ctr->tile_next[1], 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const void* fn = unit2_fn<TetD>(unit_sel != nullptr, m.g.trig.n);
+    const char* mo = static_cast<const char*>(moments);
+    int md = mode;
+    void* args[] = {(void*)&m, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&mo, (void*)&color, (void*)&md,
+                    (void*)&ctr};
+    return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
+}
+
+cudaError_t launch_pass1_piece(const TetD& m, const float4* tf, const int32_t* pou, int32_t piece, const PieceBox& box,
+                               const ViewTable& vt, int32_t slot, int32_t n_slots, void* moments, Counters* ctr,
+                               cudaStream_t s) {
+    const int blocks = (vt.total_tiles + 3) / 4;
+    char* mo = static_cast<char*>(moments);
+    if (m.g.trig.n == 3) k_pass1_piece<TetD, 3><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, ctr);
+    else if (m.g.trig.n == 4) k_pass1_piece<TetD, 4><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, ctr);
+    else k_pass1_piece<TetD, 0><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass2_piece(const TetD& m, const float4* tf, const int32_t* pou, int32_t piece, const PieceBox& box,
+                               const ViewTable& vt, int32_t slot, int32_t n_slots, const void* moments, float* color,
+                               Counters* ctr, cudaStream_t s) {
+    const int blocks = (vt.total_tiles + 3) / 4;
+    const char* mo = static_cast<const char*>(moments);
+    if (m.g.trig.n == 3) k_pass2_piece<TetD, 3><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, color, ctr);
+    else if (m.g.trig.n == 4) k_pass2_piece<TetD, 4><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, color, ctr);
+    else k_pass2_piece<TetD, 0><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, color, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sortlast_march(bool fill, const TetD& m, const float4* tf, const int32_t* pou, int32_t piece,
+                                  const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
+                                  int32_t* counts, const int64_t* starts, int32_t* seg_key, float4* seg_col,
+                                  cudaStream_t s) {
+    const int blocks = (vt.total_tiles + 3) / 4;
+    if (fill)
+        k_sortlast_piece<TetD, true><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, counts, starts,
+                                                            seg_key, seg_col);
+    else
+        k_sortlast_piece<TetD, false><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, counts, starts,
+                                                             seg_key, seg_col);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tet_values(int4* verts, const float* values, int64_t n, cudaStream_t s) {
+    const int64_t nb = (n + 255) / 256;
+    k_tet_values<<<(unsigned)(nb < 4096 ? (nb > 0 ? nb : 1) : 4096), 256, 0, s>>>(verts, values, n);
     return cudaGetLastError();
 }
 

@@ -64,7 +64,7 @@ def _desc(**kw):
 
 
 @pytest.mark.parametrize("bad, status", [
-    (dict(kind=pkg.MBOIT_TET), 4),
+    (dict(kind=7), 4),
     (dict(moment_set=3), 4),
     (dict(field=None), 1),
     (dict(brick_log2=9), 1),
@@ -147,4 +147,58 @@ def test_amr_needs_cubic_domain_and_tables(lib):
     assert lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h)) == 1
     d = _amr_desc([[0, 0, 0, 0]])
     d.leaf_table = None
+    assert lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h)) == 1
+
+
+def _tet_desc(sc, **kw):
+    d = _desc(kind=pkg.MBOIT_TET, field=None)
+    d.dims[:] = [0, 0, 0]
+    d.brick_log2 = 0
+    keep = {k: np.ascontiguousarray(getattr(sc, k)) for k in ("verts", "tets", "neighbors")}
+    for k, v in kw.items():
+        keep[k] = v
+    d._keep = keep
+    d.tet_verts, d.tet_cells, d.tet_neighbors = (keep[k].ctypes.data for k in ("verts", "tets", "neighbors"))
+    d.n_verts, d.n_tets = keep["verts"].shape[0], keep["tets"].shape[0]
+    d.tet_box[:] = list(sc.box)
+    d.quantum_log2 = sc.quantum_log2
+    return d
+
+
+def _tet_scene():
+    import scenes
+    return scenes.tet_mesh(n=3, n_pieces=2, width=4, height=4)
+
+
+@pytest.mark.parametrize("mutate, word", [
+    (lambda sc: (sc.tets.__setitem__((4, slice(2, 4)), sc.tets[4, [3, 2]]),
+                 sc.neighbors.__setitem__((4, slice(2, 4)), sc.neighbors[4, [3, 2]])), "oriented"),
+    (lambda sc: sc.tets.__setitem__((2, 1), len(sc.verts)), "vertex id"),
+    (lambda sc: sc.neighbors.__setitem__((7, 0), len(sc.tets)), "neighbour id"),
+    (lambda sc: sc.verts.__setitem__((5, 0), -0.25), "outside"),
+    (lambda sc: sc.neighbors.__setitem__((int(np.nonzero(sc.neighbors[:, 0] >= 0)[0][0]), 0), -1), "reciprocal"),
+])
+def test_tet_descriptor_validation(lib, mutate, word):
+    sc = _tet_scene()
+    mutate(sc)
+    d = _tet_desc(sc)
+    h = ctypes.c_void_p()
+    assert lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert word in pkg.mboit_last_error()
+    assert h.value is None
+
+
+def test_tet_quantum_range_checked(lib):
+    sc = _tet_scene()
+    h = ctypes.c_void_p()
+    d = _tet_desc(sc)
+    d.quantum_log2 = 25
+    assert lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h)) == 1
+    d = _tet_desc(sc)
+    d.quantum_log2 = 24          # 3 * 2^24 quanta would pass the box check, the predicate bound fails
+    d.tet_box[:] = [3.0, 3.0, 3.0]
+    assert lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert "64-bit" in pkg.mboit_last_error() or "2^30" in pkg.mboit_last_error()
+    d = _tet_desc(sc)
+    d.tet_cells = None
     assert lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h)) == 1
