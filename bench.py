@@ -142,11 +142,21 @@ def workload(name):
         return scenes.blobs64()
     if name == "amr":
         return scenes.amr_blobs()
+    if name == "tets":
+        return scenes.tet_mesh()
     raise SystemExit(f"unknown workload {name}")
 
 
 def config_of(sc, name):
     v = sc.views[0]
+    if hasattr(sc, "tets"):
+        return {"workload": name,
+                "field": (f"tetrahedral mesh, {sc.tets.shape[0]} tets ({sc.verts.shape[0]} vertices, jittered "
+                          f"{int(sc.box[0])}^3 hex grid, 5 tets per hex), float32 vertex values"),
+                "pieces": sc.n_pieces, "image": f"{v.width}x{v.height}",
+                "projection": "perspective" if v.projection else "orthographic", "step_voxels": sc.step,
+                "moments": "4 power, float32", "moment_bias": sc.moment_bias, "overestimation": sc.overestimation,
+                "l2": "mesh tables (~330 MB) larger than L2, re-read every frame"}
     if hasattr(sc, "leaves"):
         lv = np.bincount(sc.leaves[:, 3])
         field = (f"brick octree, {sc.leaves.shape[0]} leaves of 8^3 cells (per level {lv.tolist()}), "
@@ -194,6 +204,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="blobs512", choices=["blobs512", "blobs64", "amr"])
     ap.add_argument("--no-amr", action="store_true")
+    ap.add_argument("--no-tets", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-piece", action="store_true")
@@ -318,46 +329,50 @@ def main():
         del exact
         torch.cuda.empty_cache()
 
-    # the 72-piece brick-octree workload (2560x2560) as a second line of results
-    amr = None
-    if args.workload == "blobs512" and not args.no_amr:
-        asc = workload("amr")
-        avol = pkg.Volume(asc)
-        av = asc.views
-        amom, argba = pkg.Volume.moment_buffer(av), pkg.Volume.color_buffer(av)
-        aframe = lambda: avol.render_frame(av, amom, argba)  # noqa: E731
+    # the 72-piece brick-octree workload (2560x2560) and the 72-piece
+    # tetrahedral workload (1024x1024) as further lines of results
+    def unit_block(name):
+        usc = workload(name)
+        uvol = pkg.Volume(usc)
+        uv = usc.views
+        umom, urgba = pkg.Volume.moment_buffer(uv), pkg.Volume.color_buffer(uv)
+        uframe = lambda: uvol.render_frame(uv, umom, urgba)  # noqa: E731
         for _ in range(3):
-            aframe()
-        ms_a = timed(aframe, max(3, args.steps // 3))
-        avol.synchronize()
-        sa = avol.stats()["samples_pass1"]
-        K = asc.n_pieces
-        pm, pc, gm = pkg.Volume.moment_buffer(av, K), pkg.Volume.color_buffer(av, K), pkg.Volume.moment_buffer(av)
-        aw, ah = av[0].width, av[0].height
+            uframe()
+        ms_u = timed(uframe, max(3, args.steps // 3))
+        uvol.synchronize()
+        su = uvol.stats()["samples_pass1"]
+        K = usc.n_pieces
+        pm, pc, gm = pkg.Volume.moment_buffer(uv, K), pkg.Volume.color_buffer(uv, K), pkg.Volume.moment_buffer(uv)
+        uw, uh = uv[0].width, uv[0].height
 
-        def aplain():
-            avol.render_moments(av, pm, mode=pkg.MBOIT_MOMENTS_PER_PIECE)
-            avol.composite(pkg.MBOIT_OP_MOMENTS_SUM, aw, ah, 1, K, pm, gm)
-            avol.reconstruct_blend(av, gm, pc, mode=pkg.MBOIT_COLOR_PER_PIECE)
-            avol.composite(pkg.MBOIT_OP_COLOR_SUM_RESOLVE, aw, ah, 1, K, pc, argba, gm)
-        aplain()
-        ms_ap = timed(aplain, 3)
+        def uplain():
+            uvol.render_moments(uv, pm, mode=pkg.MBOIT_MOMENTS_PER_PIECE)
+            uvol.composite(pkg.MBOIT_OP_MOMENTS_SUM, uw, uh, 1, K, pm, gm)
+            uvol.reconstruct_blend(uv, gm, pc, mode=pkg.MBOIT_COLOR_PER_PIECE)
+            uvol.composite(pkg.MBOIT_OP_COLOR_SUM_RESOLVE, uw, uh, 1, K, pc, urgba, gm)
+        uplain()
+        ms_up = timed(uplain, 3)
         del pm, pc, gm
         torch.cuda.empty_cache()
-        aframe()
-        avol.synchronize()
-        amr = {"config": config_of(asc, "amr"), "samples_per_frame": sa, "ms_per_frame": ms_a,
-               "gsamples_per_s": sa / (ms_a * 1e-3) / 1e9, "per_piece_fp32_ms_per_frame": ms_ap,
-               "speedup_of_batched": ms_ap / ms_a}
+        uframe()
+        uvol.synchronize()
+        out_u = {"config": config_of(usc, name), "samples_per_frame": su, "ms_per_frame": ms_u,
+                 "gsamples_per_s": su / (ms_u * 1e-3) / 1e9, "per_piece_fp32_ms_per_frame": ms_up,
+                 "speedup_of_batched": ms_up / ms_u}
         if rank == 0 and not args.no_cpu_baseline:
-            apix = sample_pixels(aw, ah, 64, 32)
-            ref = __import__("oracle").render_amr(asc, pixels=apix, want=("mboit",))["mboit"]
-            got = argba.view(-1, 4)[torch.from_numpy(apix).cuda()].double().cpu().numpy()
-            amr["quality"] = {"pixels": int(apix.size), "max_abs_vs_oracle": float(np.abs(got - ref).max()),
-                              "rmse_vs_oracle": float(np.sqrt(((got - ref) ** 2).mean()))}
-        avol.close()
-        del avol, amom, argba
+            upix = sample_pixels(uw, uh, 64, 32)
+            ref = __import__("oracle").render(usc, pixels=upix, want=("mboit",))["mboit"]
+            got = urgba.view(-1, 4)[torch.from_numpy(upix).cuda()].double().cpu().numpy()
+            out_u["quality"] = {"pixels": int(upix.size), "max_abs_vs_oracle": float(np.abs(got - ref).max()),
+                                "rmse_vs_oracle": float(np.sqrt(((got - ref) ** 2).mean()))}
+        uvol.close()
+        del uvol, umom, urgba
         torch.cuda.empty_cache()
+        return out_u
+
+    amr = unit_block("amr") if args.workload == "blobs512" and not args.no_amr else None
+    tets = unit_block("tets") if args.workload == "blobs512" and not args.no_tets else None
 
     # precision sweep on the octree field with the 2048^2 view: moment sets and storages
     sweep = None
@@ -440,7 +455,8 @@ def main():
                           form="batched: 2 persistent kernels per frame, CUDA graph",
                           tuning={"pass1": tuning[0], "pass2": tuning[1]}),
            "samples_per_frame": samples, "ms_per_frame": ms_max, "per_piece_fp32": per_piece,
-           "sortlast_gpu": sortlast, "amr_72_pieces": amr, "precision_sweep_amr_2048": sweep,
+           "sortlast_gpu": sortlast, "amr_72_pieces": amr, "tets_72_pieces": tets,
+           "precision_sweep_amr_2048": sweep,
            "quality": quality, "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
            "gpu_launches": 2 * args.steps, "clocks": clk.summary()}
     vol.close()

@@ -65,9 +65,11 @@ struct mboit_volume_s {
     int32_t* d_fmap = nullptr;
     std::vector<int32_t> leaf_table;
     mb::TetD tet{};             // tetrahedral meshes: amr-like parameters plus the device tables below
-    int4* d_tverts = nullptr;
-    int4* d_tcells = nullptr;
+    int4* d_tcorners = nullptr;
     int4* d_tnbrs = nullptr;
+    int4* d_tcells = nullptr;
+    float* d_scache = nullptr;  // sample values of the batched frame (grow only)
+    size_t cap_scache = 0;
     int32_t* d_bin_start = nullptr;
     int32_t* d_bin_tets = nullptr;
     float* d_tvals = nullptr;   // staging of host vertex values (mboit_render_frame_host)
@@ -273,7 +275,8 @@ mboit_status select_pieces(mboit_volume v, const int32_t* pieces, int32_t n_piec
 // neighbours and the bin lists, after checking everything the exact
 // predicates rely on.
 struct TetHost {
-    std::vector<int4> verts, cells, nbrs;
+    std::vector<int4> verts, cells, nbrs, corners;
+    bool narrow = false;
     std::vector<int32_t> bin_start, bin_tets;
     int32_t bdim[3] = {0, 0, 0};
     int32_t bin_shift = 0;
@@ -335,6 +338,7 @@ mboit_status prepare_tets(const mboit_volume_desc* d, TetHost& h) {
         emax = std::max(emax, ext);
         esum += (double)ext;
     }
+    h.narrow = emax <= 32767;  // 2 E^2 < 2^31: normals fit in 32 bits
     // |n_i| <= 2 E^2 per component and |q - b| <= Q: every D_i fits in 64 bits
     if (6.0 * (double)emax * (double)emax * (qmax + 2.0) >= 4.6e18)
         return fail(MBOIT_ERR_INVALID_ARG, "tets too large for exact 64-bit predicates at this quantum_log2 "
@@ -409,21 +413,51 @@ mboit_status prepare_tets(const mboit_volume_desc* d, TetHost& h) {
         }
     }
     h.bin_start.assign(start.begin(), start.end());
+    h.corners.resize(4 * (size_t)nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        const int4 c = h.cells[t];
+        h.corners[4 * t] = h.verts[c.x];
+        h.corners[4 * t + 1] = h.verts[c.y];
+        h.corners[4 * t + 2] = h.verts[c.z];
+        h.corners[4 * t + 3] = h.verts[c.w];
+    }
     return MBOIT_OK;
 }
 
-// The batched (fused, persistent) passes of the volume's kind.
-cudaError_t pass1_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, void* moments, cudaStream_t s) {
+// The batched (fused, persistent) passes of the volume's kind.  `cache`:
+// mesh sample values shared by the two passes of one frame.
+cudaError_t pass1_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, void* moments, cudaStream_t s,
+                          mb::SampleCache cache = mb::SampleCache{}) {
     if (v->kind == MBOIT_AMR) return mb::launch_pass1_amr(v->amr, v->d_tf, mask, vt, moments, v->d_ctr, s);
-    if (v->kind == MBOIT_TET) return mb::launch_pass1_tet(v->tet, v->d_tf, mask, vt, moments, v->d_ctr, s);
+    if (v->kind == MBOIT_TET) return mb::launch_pass1_tet(v->tet, v->d_tf, mask, vt, moments, v->d_ctr, s, cache);
     return mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1);
 }
 
 cudaError_t pass2_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, const void* moments,
-                          float* color, int32_t mode, cudaStream_t s) {
+                          float* color, int32_t mode, cudaStream_t s, mb::SampleCache cache = mb::SampleCache{}) {
     if (v->kind == MBOIT_AMR) return mb::launch_pass2_amr(v->amr, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s);
-    if (v->kind == MBOIT_TET) return mb::launch_pass2_tet(v->tet, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s);
+    if (v->kind == MBOIT_TET)
+        return mb::launch_pass2_tet(v->tet, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s, cache);
     return mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s, v->tune2);
+}
+
+// The mesh frame's sample cache: L lattice points per ray bound the chord of
+// the box (plus rounding slack), one float per point and pixel.
+mboit_status tet_cache(mboit_volume v, const mb::ViewTable& vt, mb::SampleCache& c) {
+    c = mb::SampleCache{};
+    if (v->kind != MBOIT_TET) return MBOIT_OK;
+    const mb::GridD& g = v->grid;
+    const double diag = std::sqrt((double)g.hx * g.hx + (double)g.hy * g.hy + (double)g.hz * g.hz);
+    const int64_t L = (int64_t)std::ceil(diag / (double)g.step) + 4;
+    int64_t px = 0;
+    for (int i = 0; i < vt.n; ++i) px += (int64_t)vt.s[i].v.width * vt.s[i].v.height;
+    if (L > INT32_MAX) return fail(MBOIT_ERR_INVALID_ARG, "mesh box too long for the sample cache");
+    float* before = v->d_scache;
+    MB_CUDA(ensure_capacity(v->d_scache, v->cap_scache, (size_t)(L * px)));
+    if (v->d_scache != before) drop_graphs(v);
+    c.vals = v->d_scache;
+    c.L = (int32_t)L;
+    return MBOIT_OK;
 }
 
 }  // namespace
@@ -634,17 +668,17 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
                 r = cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
             return r;
         };
-        e = up(v->d_tverts, th.verts);
-        if (e == cudaSuccess) e = up(v->d_tcells, th.cells);
+        e = up(v->d_tcorners, th.corners);
         if (e == cudaSuccess) e = up(v->d_tnbrs, th.nbrs);
+        if (e == cudaSuccess) e = up(v->d_tcells, th.cells);
         if (e == cudaSuccess) e = up(v->d_bin_start, th.bin_start);
         if (e == cudaSuccess) e = up(v->d_bin_tets, th.bin_tets);
         if (e == cudaSuccess) e = cudaMalloc(&v->d_tvals, v->field_bytes);
         mb::TetD& m = v->tet;
         m.g = g;
-        m.verts = v->d_tverts;
-        m.cells = v->d_tcells;
+        m.corners = v->d_tcorners;
         m.nbrs = v->d_tnbrs;
+        m.narrow = th.narrow ? 1 : 0;
         m.bin_start = v->d_bin_start;
         m.bin_tets = v->d_bin_tets;
         for (int c = 0; c < 3; ++c) m.bdim[c] = th.bdim[c];
@@ -676,9 +710,10 @@ mboit_status mboit_destroy_volume(mboit_volume v) {
         cudaFree(v->d_tf);
         cudaFree(v->d_leaves);
         cudaFree(v->d_fmap);
-        cudaFree(v->d_tverts);
-        cudaFree(v->d_tcells);
+        cudaFree(v->d_tcorners);
         cudaFree(v->d_tnbrs);
+        cudaFree(v->d_tcells);
+        cudaFree(v->d_scache);
         cudaFree(v->d_bin_start);
         cudaFree(v->d_bin_tets);
         cudaFree(v->d_tvals);
@@ -909,6 +944,8 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
     std::memcpy(key.data(), &vt, sizeof vt);
     std::memcpy(key.data() + sizeof vt, &moments_scratch, sizeof(void*));
     std::memcpy(key.data() + sizeof vt + sizeof(void*), &rgba, sizeof(void*));
+    mb::SampleCache cache;
+    if ((st = tet_cache(v, vt, cache)) != MBOIT_OK) return st;
     cudaGraphExec_t exec = nullptr;
     for (auto& ge : v->graphs)
         if (ge.key == key) exec = ge.exec;
@@ -916,8 +953,8 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
         cudaStream_t cs = v->cap_stream;
         MB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemsetAsync(&v->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), cs);
-        if (e == cudaSuccess) e = pass1_batched(v, mask, vt, moments_scratch, cs);
-        if (e == cudaSuccess) e = pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved, cs);
+        if (e == cudaSuccess) e = pass1_batched(v, mask, vt, moments_scratch, cs, cache);
+        if (e == cudaSuccess) e = pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved, cs, cache);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -949,7 +986,7 @@ mboit_status mboit_render_frame_host(mboit_volume v, const float* field_host, co
         if (v->kind == MBOIT_TET) {
             // vertex values live in the vertex records: stage, then scatter
             MB_CUDA(cudaMemcpyAsync(v->d_tvals, field_host, v->field_bytes, cudaMemcpyHostToDevice, s));
-            MB_CUDA(mb::launch_tet_values(v->d_tverts, v->d_tvals, (int64_t)(v->field_bytes / sizeof(float)), s));
+            MB_CUDA(mb::launch_tet_values(v->d_tcorners, v->d_tcells, v->desc.n_tets, v->d_tvals, s));
         } else {
             float* dst = const_cast<float*>(v->kind == MBOIT_AMR ? v->amr.values : v->grid.field);
             MB_CUDA(cudaMemcpyAsync(dst, field_host, v->field_bytes, cudaMemcpyHostToDevice, s));

@@ -64,15 +64,31 @@ struct AmrD {
 // p * qscale.
 struct TetD {
     GridD g;
-    const int4* verts;         // snapped x, y, z and the value's float32 bits
-    const int4* cells;         // corner vertex ids, positively oriented
-    const int4* nbrs;          // tet across the face opposite corner i, -1 on the boundary
+    const int4* corners;       // per tet its 4 corners (positively oriented): snapped x, y, z and the
+                               //   value's float32 bits
+    const int4* nbrs;          // per tet: the tet across the face opposite each corner (-1 on the boundary)
     const int32_t* bin_start;  // [nbins + 1]: bins of 2^bin_shift quanta, CSR over
     const int32_t* bin_tets;   //   the tets whose snapped bounding box meets the bin
     int32_t bdim[3];
     int32_t bin_shift;
     float qscale;              // 2^quantum_log2
     int32_t max_walk;          // walk steps before a bin search takes over
+    int32_t narrow;            // 1: every tet spans < 2^15 quanta, so face normals fit in 32 bits
+    int32_t pad;
+};
+
+// The kernels' view of a mesh, with the normal width as a type.
+template <bool kNarrow>
+struct TetT : TetD {};
+
+// Sample values of the batched frame: pass 1 stores the value of every
+// lattice point j = k - k0 of every ray (NaN: not sampled), pass 2 reads
+// them instead of locating the points again.  Slot of (view, pixel, j):
+// (color_off / 4) * L + j * width * height + pixel.
+struct SampleCache {
+    float* vals;
+    int32_t L;                 // lattice points per ray, at most
+    int32_t pad;
 };
 
 // Number of shared-memory window configurations of the fused passes (the
@@ -126,10 +142,12 @@ cudaError_t launch_sortlast_march(bool fill, const AmrD& a, const float4* tf, co
                                   int32_t n_slots, int32_t* counts, const int64_t* starts, int32_t* seg_key,
                                   float4* seg_col, cudaStream_t s);
 // Tetrahedral-mesh versions (walks between face neighbours; same layouts).
+// `cache` (vals NULL: none): pass 1 stores the sample values, pass 2 reads them.
 cudaError_t launch_pass1_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
-                             void* moments, Counters* ctr, cudaStream_t s);
+                             void* moments, Counters* ctr, cudaStream_t s, SampleCache cache = SampleCache{});
 cudaError_t launch_pass2_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
-                             const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s);
+                             const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
+                             SampleCache cache = SampleCache{});
 cudaError_t launch_pass1_piece(const TetD& m, const float4* tf, const int32_t* piece_of_unit, int32_t piece,
                                const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
                                void* moments, Counters* ctr, cudaStream_t s);
@@ -140,8 +158,9 @@ cudaError_t launch_sortlast_march(bool fill, const TetD& m, const float4* tf, co
                                   int32_t piece, const PieceBox& box, const ViewTable& vt, int32_t slot,
                                   int32_t n_slots, int32_t* counts, const int64_t* starts, int32_t* seg_key,
                                   float4* seg_col, cudaStream_t s);
-// Writes n vertex values into the .w words of the mesh's vertex records.
-cudaError_t launch_tet_values(int4* verts, const float* values, int64_t n, cudaStream_t s);
+// Writes vertex values (values[vertex id]) into the .w words of the tets'
+// corner records.
+cudaError_t launch_tet_values(int4* corners, const int4* cells, int64_t n_tets, const float* values, cudaStream_t s);
 
 // Image-space reductions.
 cudaError_t launch_moments_sum(const GridD& g, const ViewTable& vt, int32_t n_inputs, const void* in, void* out,

@@ -691,12 +691,9 @@ __device__ __forceinline__ int skip_unit(const V& vol, int unit, const float o[3
 // Per-ray state of a sampler: none for grids and octrees (a point's unit is
 // a table lookup), the current tet for meshes (the walk starts there).
 struct NoWalk {};
-struct TetWalk {
-    int T = -1;
-    int4 v[4];
-};
+struct TetWalk;
 template <class V> struct WalkOf { using type = NoWalk; };
-template <> struct WalkOf<TetD> { using type = TetWalk; };
+template <bool kNarrow> struct WalkOf<TetT<kNarrow>> { using type = TetWalk; };
 
 // One owned sample of `piece` at lattice index k, or the next index to try.
 template <class V>
@@ -825,14 +822,28 @@ __device__ __forceinline__ void snap_point(const TetD& m, const float p[3], int 
     for (int c = 0; c < 3; ++c) q[c] = __float2int_rn(fmul(p[c], m.qscale));
 }
 
+// Sign of D for face (a, b) around `base` at q, D itself in D.  Narrow:
+// edges below 2^15 quanta, so the normal's components fit in 32 bits and D
+// is three 32 x 32 -> 64-bit multiply-adds.
+template <bool kNarrow>
 __device__ __forceinline__ bool face_positive(const int4 a, const int4 b, const int4 base, const int q[3],
                                               long long& D) {
     const int ax = a.x - base.x, ay = a.y - base.y, az = a.z - base.z;
     const int bx = b.x - base.x, by = b.y - base.y, bz = b.z - base.z;
-    const long long nx = (long long)ay * bz - (long long)az * by;
-    const long long ny = (long long)az * bx - (long long)ax * bz;
-    const long long nz = (long long)ax * by - (long long)ay * bx;
-    D = nx * (long long)(q[0] - base.x) + ny * (long long)(q[1] - base.y) + nz * (long long)(q[2] - base.z);
+    const int dx = q[0] - base.x, dy = q[1] - base.y, dz = q[2] - base.z;
+    long long nx, ny, nz;
+    if (kNarrow) {
+        const int n0 = ay * bz - az * by, n1 = az * bx - ax * bz, n2 = ax * by - ay * bx;
+        D = (long long)n0 * dx + (long long)n1 * dy + (long long)n2 * dz;
+        nx = n0;
+        ny = n1;
+        nz = n2;
+    } else {
+        nx = (long long)ay * bz - (long long)az * by;
+        ny = (long long)az * bx - (long long)ax * bz;
+        nz = (long long)ax * by - (long long)ay * bx;
+        D = nx * dx + ny * dy + nz * dz;
+    }
     if (D != 0) return D > 0;
     if (nx != 0) return nx > 0;
     if (ny != 0) return ny > 0;
@@ -841,28 +852,22 @@ __device__ __forceinline__ bool face_positive(const int4 a, const int4 b, const 
 
 // D_0..D_3 of q; returns -1 if q is inside, else a face that q lies
 // strictly outside of (the first one from `rot`, so that walks do not
-// always prefer one face).
-__device__ __forceinline__ int tet_exit_face(const int4 v[4], const int q[3], long long D[4], int rot) {
-    bool in[4];
-    in[0] = face_positive(v[2], v[1], v[3], q, D[0]);
-    in[1] = face_positive(v[2], v[3], v[0], q, D[1]);
-    in[2] = face_positive(v[3], v[1], v[0], q, D[2]);
-    in[3] = face_positive(v[1], v[2], v[0], q, D[3]);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int f = (rot + j) & 3;
-        if (!in[f]) return f;
-    }
-    return -1;
+// always prefer one face).  Face `skip` (-1: none) is known to pass, its D
+// already in D[skip].
+template <bool kNarrow>
+__device__ __forceinline__ int tet_exit_face(const int4 v[4], const int q[3], long long D[4], int rot, int skip) {
+    unsigned out = 0;  // bit i: q is outside face i
+    if (skip != 0 && !face_positive<kNarrow>(v[2], v[1], v[3], q, D[0])) out |= 1u;
+    if (skip != 1 && !face_positive<kNarrow>(v[2], v[3], v[0], q, D[1])) out |= 2u;
+    if (skip != 2 && !face_positive<kNarrow>(v[3], v[1], v[0], q, D[2])) out |= 4u;
+    if (skip != 3 && !face_positive<kNarrow>(v[1], v[2], v[0], q, D[3])) out |= 8u;
+    if (!out) return -1;
+    rot &= 3;
+    const unsigned r = ((out >> rot) | (out << (4 - rot))) & 15u;
+    return (rot + __ffs(r) - 1) & 3;
 }
 
-__device__ __forceinline__ void load_tet(const TetD& m, int T, int4 v[4]) {
-    const int4 c = __ldg(m.cells + T);
-    v[0] = __ldg(m.verts + c.x);
-    v[1] = __ldg(m.verts + c.y);
-    v[2] = __ldg(m.verts + c.z);
-    v[3] = __ldg(m.verts + c.w);
-}
+__device__ __forceinline__ int pick(const int4 a, int i) { return i == 0 ? a.x : i == 1 ? a.y : i == 2 ? a.z : a.w; }
 
 __device__ __forceinline__ int bin_of(const TetD& m, const int q[3]) {
     int b[3];
@@ -871,40 +876,61 @@ __device__ __forceinline__ int bin_of(const TetD& m, const int q[3]) {
     return (b[2] * m.bdim[1] + b[1]) * m.bdim[0] + b[0];
 }
 
-// Finds the tet owning q.  The walk starts at T (the tet of the previous
+// Per-ray walk state: the current tet, its neighbours and its corners
+// (snapped x, y, z, value bits).
+struct TetWalk {
+    int T = -1;
+    int4 nb;
+    int4 v[4];
+};
+
+__device__ __forceinline__ void load_tet(const TetD& m, int T, TetWalk& w) {
+    w.T = T;
+    w.nb = __ldg(m.nbrs + T);
+    const int4* c = m.corners + 4 * (size_t)T;
+    w.v[0] = __ldg(c);
+    w.v[1] = __ldg(c + 1);
+    w.v[2] = __ldg(c + 2);
+    w.v[3] = __ldg(c + 3);
+}
+
+// Finds the tet owning q.  The walk starts at w.T (the tet of the previous
 // sample; -1: the first tet listed in q's bin) and crosses a face that q is
-// outside of, at most max_walk times.  If it leaves the mesh or runs long,
-// the tets listed in q's bin are tested one by one.  On success T is the
-// owner, v its corners and D its four volumes at q; on failure (no tet
-// owns q) T and v still name one tet near q.
-__device__ __forceinline__ bool tet_walk(const TetD& m, int& T, int4 v[4], const int q[3], long long D[4]) {
-    if (T < 0) {
+// outside of, at most max_walk times; after a crossing the entry face is
+// known to pass (its D is the exact negative of the exit face's).  If the
+// walk leaves the mesh or runs long, the tets listed in q's bin are tested
+// one by one.  On success w holds the owner and D its four volumes at q; on
+// failure (no tet owns q) w still holds one tet near q.
+template <bool kNarrow>
+__device__ __forceinline__ bool tet_walk(const TetD& m, TetWalk& w, const int q[3], long long D[4]) {
+    if (w.T < 0) {
         const int b = bin_of(m, q);
         const int j0 = __ldg(m.bin_start + b);
         if (j0 == __ldg(m.bin_start + b + 1)) return false;  // no tet comes near q
-        T = __ldg(m.bin_tets + j0);
-        load_tet(m, T, v);
+        load_tet(m, __ldg(m.bin_tets + j0), w);
     }
+    int skip = -1;
     for (int step = 0;; ++step) {
-        const int f = tet_exit_face(v, q, D, step);
+        const int f = tet_exit_face<kNarrow>(w.v, q, D, step, skip);
         if (f < 0) return true;
         if (step + 1 >= m.max_walk) break;
-        const int4 nb = __ldg(m.nbrs + T);
-        const int nt = f == 0 ? nb.x : f == 1 ? nb.y : f == 2 ? nb.z : nb.w;
+        const int nt = pick(w.nb, f);
         if (nt < 0) break;
-        T = nt;
-        load_tet(m, T, v);
+        const int from = w.T;
+        const long long Df = f == 0 ? D[0] : f == 1 ? D[1] : f == 2 ? D[2] : D[3];
+        load_tet(m, nt, w);
+        skip = w.nb.x == from ? 0 : w.nb.y == from ? 1 : w.nb.z == from ? 2 : 3;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (skip == i) D[i] = -Df;
     }
     const int b = bin_of(m, q);
     const int j1 = __ldg(m.bin_start + b + 1);
     for (int j = __ldg(m.bin_start + b); j < j1; ++j) {
-        const int t = __ldg(m.bin_tets + j);
-        int4 w[4];
-        load_tet(m, t, w);
-        if (tet_exit_face(w, q, D, 0) < 0) {
-            T = t;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) v[i] = w[i];
+        TetWalk u;
+        load_tet(m, __ldg(m.bin_tets + j), u);
+        if (tet_exit_face<kNarrow>(u.v, q, D, 0, -1) < 0) {
+            w = u;
             return true;
         }
     }
@@ -921,9 +947,10 @@ __device__ __forceinline__ float tet_value(const long long D[4], const int4 v[4]
     return s * inv;
 }
 
-__device__ __forceinline__ bool piece_sample(const TetD& m, const int32_t* __restrict__ pou, int piece, float t,
-                                             const float o[3], const float d[3], int k, float& val, int& k_next,
-                                             TetWalk& w) {
+template <bool kNarrow>
+__device__ __forceinline__ bool piece_sample(const TetT<kNarrow>& m, const int32_t* __restrict__ pou, int piece,
+                                             float t, const float o[3], const float d[3], int k, float& val,
+                                             int& k_next, TetWalk& w) {
     const GridD& g = m.g;
     k_next = k + 1;
     const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
@@ -931,7 +958,7 @@ __device__ __forceinline__ bool piece_sample(const TetD& m, const int32_t* __res
     int q[3];
     snap_point(m, p, q);
     long long D[4];
-    if (!tet_walk(m, w.T, w.v, q, D)) return false;
+    if (!tet_walk<kNarrow>(m, w, q, D)) return false;
     if (__ldg(pou + w.T) != piece) return false;
     val = tet_value(D, w.v);
     return true;
@@ -943,8 +970,8 @@ __device__ __forceinline__ bool piece_sample(const TetD& m, const int32_t* __res
 // finest-brick map, its value from the leaf's own vertex block.  Mesh: the
 // tet comes from a walk that starts at the previous sample's tet.
 
-template <bool kSel, class Body>
-__device__ __forceinline__ void march_unit(const TetD& m, const uint8_t* __restrict__ sel, const float o[3],
+template <bool kSel, class Body, bool kNarrow>
+__device__ __forceinline__ void march_unit(const TetT<kNarrow>& m, const uint8_t* __restrict__ sel, const float o[3],
                                            const float d[3], int k0, int k1, Body& body) {
     const GridD& g = m.g;
     if (k0 > k1) return;
@@ -955,10 +982,59 @@ __device__ __forceinline__ void march_unit(const TetD& m, const uint8_t* __restr
         int q[3];
         snap_point(m, p, q);
         long long D[4];
-        if (!tet_walk(m, w.T, w.v, q, D)) continue;
+        if (!tet_walk<kNarrow>(m, w, q, D)) continue;
         if (kSel && !__ldg(sel + w.T)) continue;
         body(t, tet_value(D, w.v));
     }
+}
+
+// The same march storing every lattice point's value (NaN: not sampled)
+// at cache[j * stride], j = k - k0.
+template <bool kSel, class Body, bool kNarrow>
+__device__ __forceinline__ void march_unit_store(const TetT<kNarrow>& m, const uint8_t* __restrict__ sel,
+                                                 const float o[3], const float d[3], int k0, int k1, Body& body,
+                                                 float* __restrict__ cache, int64_t stride) {
+    const GridD& g = m.g;
+    if (k0 > k1) return;
+    TetWalk w;
+    const float tz = lattice_t(k1, g.step);
+    int64_t j = 0;
+    for (float t = lattice_t(k0, g.step); t <= tz; t += g.step, j += stride) {
+        const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+        int q[3];
+        snap_point(m, p, q);
+        long long D[4];
+        float val = __int_as_float(0x7fc00000);
+        if (tet_walk<kNarrow>(m, w, q, D) && (!kSel || __ldg(sel + w.T))) {
+            val = tet_value(D, w.v);
+            body(t, val);
+        }
+        cache[j] = val;
+    }
+}
+
+// Pass 2 of the batched frame: the values pass 1 stored.
+template <class Body>
+__device__ __forceinline__ void march_cached(const GridD& g, int k0, int k1, const float* __restrict__ cache,
+                                             int64_t stride, Body& body) {
+    if (k0 > k1) return;
+    const float tz = lattice_t(k1, g.step);
+    int64_t j = 0;
+    for (float t = lattice_t(k0, g.step); t <= tz; t += g.step, j += stride) {
+        const float val = __ldg(cache + j);
+        if (val == val) body(t, val);
+    }
+}
+
+// Ray slot of the sample cache; clamps k1 to the cache's L lattice points
+// (flagging an error if that cuts the ray, which the box bound excludes).
+__device__ __forceinline__ int64_t cache_slot(const SampleCache& c, const ViewSlot& S, int pix, int k0, int& k1,
+                                              Counters* ctr) {
+    if (k1 - k0 + 1 > c.L) {
+        k1 = k0 + c.L - 1;
+        atomicExch(&ctr->error, 3);
+    }
+    return (S.color_off / 4) * (int64_t)c.L + pix;
 }
 
 template <bool kSel, class Body>
@@ -976,10 +1052,19 @@ __device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restr
     }
 }
 
-template <class V, bool kSel, int MS>
-__global__ void __launch_bounds__(256) k_pass1_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
+// Resident 256-thread blocks per SM the unit kernels are compiled for (the
+// mesh walk is latency-bound: more warps hide more of it).
+#ifndef MB_TET_MIN_BLOCKS
+#define MB_TET_MIN_BLOCKS 4
+#endif
+template <class V> struct MinBlocks { static constexpr int value = 1; };
+template <bool k> struct MinBlocks<TetT<k>> { static constexpr int value = MB_TET_MIN_BLOCKS; };
+
+template <class V, bool kSel, int MS, bool kCache = false>
+__global__ void __launch_bounds__(256, MinBlocks<V>::value) k_pass1_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
                                                     const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
-                                                    char* __restrict__ moments, Counters* __restrict__ ctr) {
+                                                    char* __restrict__ moments, Counters* __restrict__ ctr,
+                                                    const SampleCache cache) {
     __shared__ float2 s_sig[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float s0 = tf[i].w;
@@ -995,17 +1080,23 @@ __global__ void __launch_bounds__(256) k_pass1_unit(const __grid_constant__ V a,
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
         auto body = make_moment_body<MS>(s_sig, g, S.v);
-        march_unit<kSel>(a, sel, o, d, k0, k1, body);
+        if constexpr (kCache) {
+            const int pix = valid ? py * S.v.width + px : 0;
+            const int64_t slot = cache_slot(cache, S, pix, k0, k1, ctr);
+            march_unit_store<kSel>(a, sel, o, d, k0, k1, body, cache.vals + slot, (int64_t)S.v.width * S.v.height);
+        } else {
+            march_unit<kSel>(a, sel, o, d, k0, k1, body);
+        }
         if (valid) body.store(g, moments, S, S.moment_off, py * S.v.width + px);
         warp_add_u64(&ctr->samples[0], body.n);
     }
 }
 
-template <class V, bool kSel, int MS>
-__global__ void __launch_bounds__(256) k_pass2_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
+template <class V, bool kSel, int MS, bool kCache = false>
+__global__ void __launch_bounds__(256, MinBlocks<V>::value) k_pass2_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
                                                     const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                     const char* __restrict__ moments, float* __restrict__ color, int mode,
-                                                    Counters* __restrict__ ctr) {
+                                                    Counters* __restrict__ ctr, const SampleCache cache) {
     __shared__ float4 s_tf[512];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float4 e0 = tf[i], e1 = i < 255 ? tf[i + 1] : tf[i];
@@ -1025,7 +1116,12 @@ __global__ void __launch_bounds__(256) k_pass2_unit(const __grid_constant__ V a,
         float o[3], d[3];
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
-        march_unit<kSel>(a, sel, o, d, k0, k1, body);
+        if constexpr (kCache) {
+            const int64_t slot = cache_slot(cache, S, pix, k0, k1, ctr);
+            march_cached(g, k0, k1, cache.vals + slot, (int64_t)S.v.width * S.v.height, body);
+        } else {
+            march_unit<kSel>(a, sel, o, d, k0, k1, body);
+        }
         if (valid) {
             float4* out = reinterpret_cast<float4*>(color + S.color_off) + pix;
             *out = mode == kColorResolved ? resolve_pixel(body.C, body.b0, make_float4(0.0f, 0.0f, 0.0f, 0.0f), raw)
@@ -1407,22 +1503,28 @@ const void* pass1_fn(int cfg, bool sel, int ms) {
 const void* pass2_fn(int cfg, bool sel, int ms) {
     return ms == 3 ? pass2_fn_ms<3>(cfg, sel) : ms == 4 ? pass2_fn_ms<4>(cfg, sel) : pass2_fn_ms<0>(cfg, sel);
 }
-template <class V>
+template <class V, bool kC = false>
 const void* unit1_fn(bool sel, int ms) {
-    if (ms == 3) return sel ? (const void*)k_pass1_unit<V, true, 3> : (const void*)k_pass1_unit<V, false, 3>;
-    if (ms == 4) return sel ? (const void*)k_pass1_unit<V, true, 4> : (const void*)k_pass1_unit<V, false, 4>;
-    return sel ? (const void*)k_pass1_unit<V, true, 0> : (const void*)k_pass1_unit<V, false, 0>;
+    if (ms == 3) return sel ? (const void*)k_pass1_unit<V, true, 3, kC> : (const void*)k_pass1_unit<V, false, 3, kC>;
+    if (ms == 4) return sel ? (const void*)k_pass1_unit<V, true, 4, kC> : (const void*)k_pass1_unit<V, false, 4, kC>;
+    return sel ? (const void*)k_pass1_unit<V, true, 0, kC> : (const void*)k_pass1_unit<V, false, 0, kC>;
 }
-template <class V>
+template <class V, bool kC = false>
 const void* unit2_fn(bool sel, int ms) {
-    if (ms == 3) return sel ? (const void*)k_pass2_unit<V, true, 3> : (const void*)k_pass2_unit<V, false, 3>;
-    if (ms == 4) return sel ? (const void*)k_pass2_unit<V, true, 4> : (const void*)k_pass2_unit<V, false, 4>;
-    return sel ? (const void*)k_pass2_unit<V, true, 0> : (const void*)k_pass2_unit<V, false, 0>;
+    if (ms == 3) return sel ? (const void*)k_pass2_unit<V, true, 3, kC> : (const void*)k_pass2_unit<V, false, 3, kC>;
+    if (ms == 4) return sel ? (const void*)k_pass2_unit<V, true, 4, kC> : (const void*)k_pass2_unit<V, false, 4, kC>;
+    return sel ? (const void*)k_pass2_unit<V, true, 0, kC> : (const void*)k_pass2_unit<V, false, 0, kC>;
 }
 
-__global__ void k_tet_values(int4* __restrict__ verts, const float* __restrict__ values, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        verts[i].w = __float_as_int(values[i]);
+__global__ void k_tet_values(int4* __restrict__ corners, const int4* __restrict__ cells, int64_t n_tets,
+                             const float* __restrict__ values) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tets; t += (int64_t)gridDim.x * blockDim.x) {
+        const int4 c = cells[t];
+        corners[4 * t].w = __float_as_int(values[c.x]);
+        corners[4 * t + 1].w = __float_as_int(values[c.y]);
+        corners[4 * t + 2].w = __float_as_int(values[c.z]);
+        corners[4 * t + 3].w = __float_as_int(values[c.w]);
+    }
 }
 
 bool vec_config(int cfg) { return cfg == 2 || cfg == 3 || cfg == 4; }
@@ -1449,10 +1551,14 @@ cudaError_t prepare_kernels() {
                          (const void*)k_moments_sum,        (const void*)k_color_resolve,
                          (const void*)k_sortlast_piece<GridD, true>, (const void*)k_sortlast_piece<GridD, false>,
                          (const void*)k_sortlast_piece<AmrD, true>, (const void*)k_sortlast_piece<AmrD, false>,
-                         (const void*)k_pass1_piece<TetD, 0>, (const void*)k_pass2_piece<TetD, 0>,
-                         (const void*)k_pass1_piece<TetD, 3>, (const void*)k_pass2_piece<TetD, 3>,
-                         (const void*)k_pass1_piece<TetD, 4>, (const void*)k_pass2_piece<TetD, 4>,
-                         (const void*)k_sortlast_piece<TetD, true>, (const void*)k_sortlast_piece<TetD, false>,
+                         (const void*)k_pass1_piece<TetT<true>, 0>, (const void*)k_pass2_piece<TetT<true>, 0>,
+                         (const void*)k_pass1_piece<TetT<true>, 3>, (const void*)k_pass2_piece<TetT<true>, 3>,
+                         (const void*)k_pass1_piece<TetT<true>, 4>, (const void*)k_pass2_piece<TetT<true>, 4>,
+                         (const void*)k_sortlast_piece<TetT<true>, true>, (const void*)k_sortlast_piece<TetT<true>, false>,
+                         (const void*)k_pass1_piece<TetT<false>, 0>, (const void*)k_pass2_piece<TetT<false>, 0>,
+                         (const void*)k_pass1_piece<TetT<false>, 3>, (const void*)k_pass2_piece<TetT<false>, 3>,
+                         (const void*)k_pass1_piece<TetT<false>, 4>, (const void*)k_pass2_piece<TetT<false>, 4>,
+                         (const void*)k_sortlast_piece<TetT<false>, true>, (const void*)k_sortlast_piece<TetT<false>, false>,
                          (const void*)k_tet_values,
                          (const void*)k_sortlast_totals,    (const void*)k_sortlast_starts,
                          (const void*)k_scan_blocks,        (const void*)k_scan_sums,
@@ -1479,8 +1585,14 @@ cudaError_t prepare_kernels() {
         for (int sel = 0; sel < 2; ++sel) {
             persistent_blocks(unit1_fn<AmrD>(sel, ms), 256, 0);
             persistent_blocks(unit2_fn<AmrD>(sel, ms), 256, 0);
-            persistent_blocks(unit1_fn<TetD>(sel, ms), 256, 0);
-            persistent_blocks(unit2_fn<TetD>(sel, ms), 256, 0);
+            persistent_blocks(unit1_fn<TetT<true>>(sel, ms), 256, 0);
+            persistent_blocks(unit2_fn<TetT<true>>(sel, ms), 256, 0);
+            persistent_blocks(unit1_fn<TetT<false>>(sel, ms), 256, 0);
+            persistent_blocks(unit2_fn<TetT<false>>(sel, ms), 256, 0);
+            persistent_blocks(unit1_fn<TetT<true>, true>(sel, ms), 256, 0);
+            persistent_blocks(unit2_fn<TetT<true>, true>(sel, ms), 256, 0);
+            persistent_blocks(unit1_fn<TetT<false>, true>(sel, ms), 256, 0);
+            persistent_blocks(unit2_fn<TetT<false>, true>(sel, ms), 256, 0);
         }
     return cudaGetLastError();
 }
@@ -1610,7 +1722,8 @@ cudaError_t launch_pass1_amr(const AmrD& a, const float4* tf, const uint8_t* uni
     if (e != cudaSuccess) return e;
     const void* fn = unit1_fn<AmrD>(unit_sel != nullptr, a.g.trig.n);
     char* m = static_cast<char*>(moments);
-    void* args[] = {(void*)&a, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&m, (void*)&ctr};
+    SampleCache none{};
+    void* args[] = {(void*)&a, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&m, (void*)&ctr, (void*)&none};
     return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
 }
 
@@ -1621,8 +1734,9 @@ cudaError_t launch_pass2_amr(const AmrD& a, const float4* tf, const uint8_t* uni
     const void* fn = unit2_fn<AmrD>(unit_sel != nullptr, a.g.trig.n);
     const char* m = static_cast<const char*>(moments);
     int md = mode;
+    SampleCache none{};
     void* args[] = {(void*)&a, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&m, (void*)&color, (void*)&md,
-                    (void*)&ctr};
+                    (void*)&ctr, (void*)&none};
     return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
 }
 
@@ -1662,67 +1776,122 @@ cudaError_t launch_sortlast_march(bool fill, const AmrD& a, const float4* tf, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_pass1_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
-                             void* moments, Counters* ctr, cudaStream_t s) {
+namespace {
+
+template <bool kN>
+TetT<kN> as_tet(const TetD& m) {
+    TetT<kN> t;
+    static_cast<TetD&>(t) = m;
+    return t;
+}
+
+template <class V>
+cudaError_t launch_unit1(const V& vol, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt, void* moments,
+                         Counters* ctr, cudaStream_t s, SampleCache cache) {
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const void* fn = unit1_fn<TetD>(unit_sel != nullptr, m.g.trig.n);
+    const bool sel = unit_sel != nullptr;
+    const void* fn = cache.vals ? unit1_fn<V, true>(sel, vol.g.trig.n) : unit1_fn<V>(sel, vol.g.trig.n);
     char* mo = static_cast<char*>(moments);
-    void* args[] = {(void*)&m, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&mo, (void*)&ctr};
+    void* args[] = {(void*)&vol, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&mo, (void*)&ctr, (void*)&cache};
     return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
 }
 
-cudaError_t launch_pass2_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
-                             const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s) {
+template <class V>
+cudaError_t launch_unit2(const V& vol, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
+                         const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
+                         SampleCache cache) {
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[1], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const void* fn = unit2_fn<TetD>(unit_sel != nullptr, m.g.trig.n);
+    const bool sel = unit_sel != nullptr;
+    const void* fn = cache.vals ? unit2_fn<V, true>(sel, vol.g.trig.n) : unit2_fn<V>(sel, vol.g.trig.n);
     const char* mo = static_cast<const char*>(moments);
     int md = mode;
-    void* args[] = {(void*)&m, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&mo, (void*)&color, (void*)&md,
-                    (void*)&ctr};
+    void* args[] = {(void*)&vol, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&mo, (void*)&color, (void*)&md,
+                    (void*)&ctr, (void*)&cache};
     return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
+}
+
+template <class V>
+cudaError_t launch_piece1(const V& m, const float4* tf, const int32_t* pou, int32_t piece, const PieceBox& box,
+                          const ViewTable& vt, int32_t slot, int32_t n_slots, void* moments, Counters* ctr,
+                          cudaStream_t s) {
+    const int blocks = (vt.total_tiles + 3) / 4;
+    char* mo = static_cast<char*>(moments);
+    if (m.g.trig.n == 3) k_pass1_piece<V, 3><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, ctr);
+    else if (m.g.trig.n == 4) k_pass1_piece<V, 4><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, ctr);
+    else k_pass1_piece<V, 0><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, ctr);
+    return cudaGetLastError();
+}
+
+template <class V>
+cudaError_t launch_piece2(const V& m, const float4* tf, const int32_t* pou, int32_t piece, const PieceBox& box,
+                          const ViewTable& vt, int32_t slot, int32_t n_slots, const void* moments, float* color,
+                          Counters* ctr, cudaStream_t s) {
+    const int blocks = (vt.total_tiles + 3) / 4;
+    const char* mo = static_cast<const char*>(moments);
+    if (m.g.trig.n == 3) k_pass2_piece<V, 3><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, color, ctr);
+    else if (m.g.trig.n == 4) k_pass2_piece<V, 4><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, color, ctr);
+    else k_pass2_piece<V, 0><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, color, ctr);
+    return cudaGetLastError();
+}
+
+template <class V>
+cudaError_t launch_sortlast(bool fill, const V& m, const float4* tf, const int32_t* pou, int32_t piece,
+                            const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots, int32_t* counts,
+                            const int64_t* starts, int32_t* seg_key, float4* seg_col, cudaStream_t s) {
+    const int blocks = (vt.total_tiles + 3) / 4;
+    if (fill)
+        k_sortlast_piece<V, true><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, counts, starts,
+                                                         seg_key, seg_col);
+    else
+        k_sortlast_piece<V, false><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, counts, starts,
+                                                          seg_key, seg_col);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_pass1_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
+                             void* moments, Counters* ctr, cudaStream_t s, SampleCache cache) {
+    return m.narrow ? launch_unit1(as_tet<true>(m), tf, unit_sel, vt, moments, ctr, s, cache)
+                    : launch_unit1(as_tet<false>(m), tf, unit_sel, vt, moments, ctr, s, cache);
+}
+
+cudaError_t launch_pass2_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
+                             const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
+                             SampleCache cache) {
+    return m.narrow ? launch_unit2(as_tet<true>(m), tf, unit_sel, vt, moments, color, mode, ctr, s, cache)
+                    : launch_unit2(as_tet<false>(m), tf, unit_sel, vt, moments, color, mode, ctr, s, cache);
 }
 
 cudaError_t launch_pass1_piece(const TetD& m, const float4* tf, const int32_t* pou, int32_t piece, const PieceBox& box,
                                const ViewTable& vt, int32_t slot, int32_t n_slots, void* moments, Counters* ctr,
                                cudaStream_t s) {
-    const int blocks = (vt.total_tiles + 3) / 4;
-    char* mo = static_cast<char*>(moments);
-    if (m.g.trig.n == 3) k_pass1_piece<TetD, 3><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, ctr);
-    else if (m.g.trig.n == 4) k_pass1_piece<TetD, 4><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, ctr);
-    else k_pass1_piece<TetD, 0><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, ctr);
-    return cudaGetLastError();
+    return m.narrow ? launch_piece1(as_tet<true>(m), tf, pou, piece, box, vt, slot, n_slots, moments, ctr, s)
+                    : launch_piece1(as_tet<false>(m), tf, pou, piece, box, vt, slot, n_slots, moments, ctr, s);
 }
 
 cudaError_t launch_pass2_piece(const TetD& m, const float4* tf, const int32_t* pou, int32_t piece, const PieceBox& box,
                                const ViewTable& vt, int32_t slot, int32_t n_slots, const void* moments, float* color,
                                Counters* ctr, cudaStream_t s) {
-    const int blocks = (vt.total_tiles + 3) / 4;
-    const char* mo = static_cast<const char*>(moments);
-    if (m.g.trig.n == 3) k_pass2_piece<TetD, 3><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, color, ctr);
-    else if (m.g.trig.n == 4) k_pass2_piece<TetD, 4><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, color, ctr);
-    else k_pass2_piece<TetD, 0><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, mo, color, ctr);
-    return cudaGetLastError();
+    return m.narrow ? launch_piece2(as_tet<true>(m), tf, pou, piece, box, vt, slot, n_slots, moments, color, ctr, s)
+                    : launch_piece2(as_tet<false>(m), tf, pou, piece, box, vt, slot, n_slots, moments, color, ctr, s);
 }
 
 cudaError_t launch_sortlast_march(bool fill, const TetD& m, const float4* tf, const int32_t* pou, int32_t piece,
                                   const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
                                   int32_t* counts, const int64_t* starts, int32_t* seg_key, float4* seg_col,
                                   cudaStream_t s) {
-    const int blocks = (vt.total_tiles + 3) / 4;
-    if (fill)
-        k_sortlast_piece<TetD, true><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, counts, starts,
-                                                            seg_key, seg_col);
-    else
-        k_sortlast_piece<TetD, false><<<blocks, 128, 0, s>>>(m, tf, pou, piece, box, vt, slot, n_slots, counts, starts,
-                                                             seg_key, seg_col);
-    return cudaGetLastError();
+    return m.narrow ? launch_sortlast(fill, as_tet<true>(m), tf, pou, piece, box, vt, slot, n_slots, counts, starts,
+                                      seg_key, seg_col, s)
+                    : launch_sortlast(fill, as_tet<false>(m), tf, pou, piece, box, vt, slot, n_slots, counts, starts,
+                                      seg_key, seg_col, s);
 }
 
-cudaError_t launch_tet_values(int4* verts, const float* values, int64_t n, cudaStream_t s) {
-    const int64_t nb = (n + 255) / 256;
-    k_tet_values<<<(unsigned)(nb < 4096 ? (nb > 0 ? nb : 1) : 4096), 256, 0, s>>>(verts, values, n);
+cudaError_t launch_tet_values(int4* corners, const int4* cells, int64_t n_tets, const float* values, cudaStream_t s) {
+    const int64_t nb = (n_tets + 255) / 256;
+    k_tet_values<<<(unsigned)(nb < 4096 ? (nb > 0 ? nb : 1) : 4096), 256, 0, s>>>(corners, cells, n_tets, values);
     return cudaGetLastError();
 }
 

@@ -530,7 +530,7 @@ def tet_neighbors(tets):
 
 
 def tet_orient(P, tets):
-    """Six signed volumes of the tets, exact for coordinates on the 2^-16 lattice."""
+    """Six signed volumes of the tets, exact for coordinates on the 2^-16 lattice (or a coarser one)."""
     Q = np.rint(np.asarray(P, np.float64) * 65536.0).astype(np.int64)
     a, b, c, d = (Q[tets[:, i]] for i in range(4))
     u, v, w = b - a, c - a, d - a
@@ -563,7 +563,7 @@ def tet_mesh(n=96, jitter=0.3, n_pieces=72, width=1024, height=1024, seed=1004, 
     along the box faces, so the mesh fills the box exactly); a vertex whose
     move would leave a tet with under 5% of its unjittered volume has its
     move halved until none does; positions are then rounded to multiples of
-    2^-16 (the lattice the exact point location snaps to)."""
+    2^-14 (the lattice the exact point location snaps to)."""
     s = Stream(seed)
     nv1 = n + 1
     g = np.arange(nv1, dtype=np.float64)
@@ -577,7 +577,7 @@ def tet_mesh(n=96, jitter=0.3, n_pieces=72, width=1024, height=1024, seed=1004, 
     tets[flip, 2], tets[flip, 3] = tets[flip, 3].copy(), tets[flip, 2].copy()
     v0 = np.abs(v0)
     while True:
-        P = np.rint((P0 + J) * 65536.0) / 65536.0
+        P = np.rint((P0 + J) * 16384.0) / 16384.0
         bad = tet_orient(P, tets) < 0.05 * v0
         if not bad.any():
             break
@@ -604,5 +604,5 @@ def tet_mesh(n=96, jitter=0.3, n_pieces=72, width=1024, height=1024, seed=1004, 
     dims = (n + 1,) * 3
     view = perspective_view(dims, (0.57, 0.49, 0.66), width, height)
     vf = verts[:, 3]
-    return TetScene("tets" if n == 96 else f"tets{n}", verts, tets, nb, (float(n),) * 3, 16, piece, n_pieces, tf,
+    return TetScene("tets" if n == 96 else f"tets{n}", verts, tets, nb, (float(n),) * 3, 14, piece, n_pieces, tf,
                     (np.float32(vf.min()), np.float32(vf.max())), 0.5, [view])

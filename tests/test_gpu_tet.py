@@ -49,6 +49,14 @@ def test_tet_fused_frame(pkg, small_tet):
     assert_rgba_close(unpack_color(col, v)[0][0], ref["mboit"])
     st = vol.stats()
     assert st["samples_pass1"] == st["samples_pass2"] == int(ref["nsamples"].sum()) > 10000
+    # the frame's pass 2 reads the values pass 1 stored; the split calls walk
+    # the mesh twice: the same bits either way
+    mom2 = pkg.Volume.moment_buffer(v)
+    col2 = pkg.Volume.color_buffer(v)
+    vol.render_moments(v, mom2)
+    vol.reconstruct_blend(v, mom2, col2)
+    torch.cuda.synchronize()
+    assert torch.equal(mom, mom2) and torch.equal(col, col2)
 
 
 def test_tet_per_piece_and_composites(pkg, small_tet):

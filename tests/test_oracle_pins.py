@@ -542,7 +542,8 @@ def test_tet_location_partitions_the_box():
     np.testing.assert_array_equal(ob, owner)
     np.testing.assert_array_equal(npb, npass)
     V = sc.verts[:, :3].astype(np.float64)
-    q = np.rint(pts[inside].astype(np.float64) * 65536.0) / 65536.0
+    Qs = 2.0 ** sc.quantum_log2
+    q = np.rint(pts[inside].astype(np.float64) * Qs) / Qs
     T = sc.tets[owner[inside]]
     A = np.stack([V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]], V[T[:, 3]] - V[T[:, 0]]], axis=2)
     lam = np.linalg.solve(A, (q - V[T[:, 0]])[:, :, None])[:, :, 0]
@@ -564,16 +565,22 @@ def test_tet_point_inside_known_tet():
     lam /= lam.sum(1, keepdims=True)
     V = sc.verts[:, :3].astype(np.float64)
     P = np.einsum("ni,nik->nk", lam, V[sc.tets[ts]])
-    P = (np.rint(P * 65536.0) / 65536.0).astype(np.float32)
+    P = (np.rint(P * 2.0 ** sc.quantum_log2) / 2.0 ** sc.quantum_log2).astype(np.float32)
     owner, npass, val = oracle.tet_locate(sc, P)
     np.testing.assert_array_equal(owner, ts)
-    want = np.einsum("ni,ni->n", lam, sc.verts[sc.tets[ts], 3].astype(np.float64))
-    np.testing.assert_allclose(val, want, atol=2e-5)
+    # the value is linear in the snapped point: re-solve its barycentric coordinates
+    T = sc.tets[ts]
+    A = np.stack([V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]], V[T[:, 3]] - V[T[:, 0]]], axis=2)
+    mu = np.linalg.solve(A, (P.astype(np.float64) - V[T[:, 0]])[:, :, None])[:, :, 0]
+    bary = np.concatenate([1 - mu.sum(1, keepdims=True), mu], 1)
+    assert np.abs(bary - lam).max() < 1e-3
+    want = np.einsum("ni,ni->n", bary, sc.verts[T, 3].astype(np.float64))
+    np.testing.assert_allclose(val, want, rtol=1e-12, atol=1e-13)
 
 
 def test_tet_linear_field_equals_grid():
     """Barycentric interpolation reproduces a linear field on any mesh, so a
-    tet render equals the regular grid's up to the 2^-16 position snap."""
+    tet render equals the regular grid's up to the 2^-14 position snap."""
     sc, grid = small.linear_tets()
     P = sc.verts[:, :3].astype(np.float64)
     owner, npass, val = oracle.tet_locate(sc, (np.random.default_rng(2).random((500, 3)) * 6).astype(np.float32))
