@@ -894,6 +894,23 @@ __device__ __forceinline__ void load_tet(const TetD& m, int T, TetWalk& w) {
     w.v[3] = __ldg(c + 3);
 }
 
+// Tests the tets listed in q's bin one by one (the walk's fallback); on
+// success w holds the owner and D its volumes, else w is unchanged.
+template <bool kNarrow>
+__device__ __forceinline__ bool tet_search(const TetD& m, TetWalk& w, const int q[3], long long D[4]) {
+    const int b = bin_of(m, q);
+    const int j1 = __ldg(m.bin_start + b + 1);
+    for (int j = __ldg(m.bin_start + b); j < j1; ++j) {
+        TetWalk u;
+        load_tet(m, __ldg(m.bin_tets + j), u);
+        if (tet_exit_face<kNarrow>(u.v, q, D, 0, -1) < 0) {
+            w = u;
+            return true;
+        }
+    }
+    return false;
+}
+
 // Finds the tet owning q.  The walk starts at w.T (the tet of the previous
 // sample; -1: the first tet listed in q's bin) and crosses a face that q is
 // outside of, at most max_walk times; after a crossing the entry face is
@@ -924,17 +941,7 @@ __device__ __forceinline__ bool tet_walk(const TetD& m, TetWalk& w, const int q[
         for (int i = 0; i < 4; ++i)
             if (skip == i) D[i] = -Df;
     }
-    const int b = bin_of(m, q);
-    const int j1 = __ldg(m.bin_start + b + 1);
-    for (int j = __ldg(m.bin_start + b); j < j1; ++j) {
-        TetWalk u;
-        load_tet(m, __ldg(m.bin_tets + j), u);
-        if (tet_exit_face<kNarrow>(u.v, q, D, 0, -1) < 0) {
-            w = u;
-            return true;
-        }
-    }
-    return false;
+    return tet_search<kNarrow>(m, w, q, D);
 }
 
 // Barycentric interpolation of the corner values: lambda_i = D_i / sum D.
@@ -970,47 +977,78 @@ __device__ __forceinline__ bool piece_sample(const TetT<kNarrow>& m, const int32
 // finest-brick map, its value from the leaf's own vertex block.  Mesh: the
 // tet comes from a walk that starts at the previous sample's tet.
 
-template <bool kSel, class Body, bool kNarrow>
-__device__ __forceinline__ void march_unit(const TetT<kNarrow>& m, const uint8_t* __restrict__ sel, const float o[3],
-                                           const float d[3], int k0, int k1, Body& body) {
+// Batched march over a mesh.  One iteration is one tet test for every lane
+// of the warp: it either places the current lattice point (the sample is
+// taken, the next point comes up) or crosses a face towards it, so the
+// lanes stay together in the test and part only for the sample or the
+// crossing.  The owners are those of tet_walk: the same walk, the same
+// fallback.  kStore: every lattice point's value (NaN: not sampled) goes to
+// cache[j * stride], j = k - k0.
+template <bool kSel, bool kStore, class Body, bool kNarrow>
+__device__ __forceinline__ void march_tet(const TetT<kNarrow>& m, const uint8_t* __restrict__ sel, const float o[3],
+                                          const float d[3], int k0, int k1, Body& body, float* __restrict__ cache,
+                                          int64_t stride) {
     const GridD& g = m.g;
     if (k0 > k1) return;
-    TetWalk w;
     const float tz = lattice_t(k1, g.step);
-    for (float t = lattice_t(k0, g.step); t <= tz; t += g.step) {
+    float t = lattice_t(k0, g.step);
+    int q[3];
+    {
         const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
-        int q[3];
         snap_point(m, p, q);
-        long long D[4];
-        if (!tet_walk<kNarrow>(m, w, q, D)) continue;
-        if (kSel && !__ldg(sel + w.T)) continue;
-        body(t, tet_value(D, w.v));
+    }
+    TetWalk w;
+    {
+        const int b = bin_of(m, q);
+        const int j0 = __ldg(m.bin_start + b);
+        if (j0 < __ldg(m.bin_start + b + 1)) load_tet(m, __ldg(m.bin_tets + j0), w);
+    }
+    long long D[4];
+    int64_t j = 0;
+    int skip = -1, steps = 0;
+    while (t <= tz) {
+        const int f = w.T >= 0 ? tet_exit_face<kNarrow>(w.v, q, D, steps, skip) : -2;
+        if (f >= 0) {
+            const int nt = pick(w.nb, f);
+            if (nt >= 0 && steps + 1 < m.max_walk) {
+                const int from = w.T;
+                const long long Df = f == 0 ? D[0] : f == 1 ? D[1] : f == 2 ? D[2] : D[3];
+                load_tet(m, nt, w);
+                skip = w.nb.x == from ? 0 : w.nb.y == from ? 1 : w.nb.z == from ? 2 : 3;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (skip == i) D[i] = -Df;
+                ++steps;
+                continue;
+            }
+        }
+        const bool found = f == -1 || tet_search<kNarrow>(m, w, q, D);
+        float val = __int_as_float(0x7fc00000);
+        if (found && (!kSel || __ldg(sel + w.T))) {
+            val = tet_value(D, w.v);
+            body(t, val);
+        }
+        if (kStore) cache[j] = val;
+        t += g.step;
+        j += stride;
+        const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+        snap_point(m, p, q);
+        skip = -1;
+        steps = 0;
     }
 }
 
-// The same march storing every lattice point's value (NaN: not sampled)
-// at cache[j * stride], j = k - k0.
+template <bool kSel, class Body, bool kNarrow>
+__device__ __forceinline__ void march_unit(const TetT<kNarrow>& m, const uint8_t* __restrict__ sel, const float o[3],
+                                           const float d[3], int k0, int k1, Body& body) {
+    march_tet<kSel, false>(m, sel, o, d, k0, k1, body, nullptr, 0);
+}
+
 template <bool kSel, class Body, bool kNarrow>
 __device__ __forceinline__ void march_unit_store(const TetT<kNarrow>& m, const uint8_t* __restrict__ sel,
                                                  const float o[3], const float d[3], int k0, int k1, Body& body,
                                                  float* __restrict__ cache, int64_t stride) {
-    const GridD& g = m.g;
-    if (k0 > k1) return;
-    TetWalk w;
-    const float tz = lattice_t(k1, g.step);
-    int64_t j = 0;
-    for (float t = lattice_t(k0, g.step); t <= tz; t += g.step, j += stride) {
-        const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
-        int q[3];
-        snap_point(m, p, q);
-        long long D[4];
-        float val = __int_as_float(0x7fc00000);
-        if (tet_walk<kNarrow>(m, w, q, D) && (!kSel || __ldg(sel + w.T))) {
-            val = tet_value(D, w.v);
-            body(t, val);
-        }
-        cache[j] = val;
-    }
+    march_tet<kSel, true>(m, sel, o, d, k0, k1, body, cache, stride);
 }
 
 // Pass 2 of the batched frame: the values pass 1 stored.
@@ -1055,7 +1093,7 @@ __device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restr
 // Resident 256-thread blocks per SM the unit kernels are compiled for (the
 // mesh walk is latency-bound: more warps hide more of it).
 #ifndef MB_TET_MIN_BLOCKS
-#define MB_TET_MIN_BLOCKS 4
+#define MB_TET_MIN_BLOCKS 3
 #endif
 template <class V> struct MinBlocks { static constexpr int value = 1; };
 template <bool k> struct MinBlocks<TetT<k>> { static constexpr int value = MB_TET_MIN_BLOCKS; };
