@@ -944,13 +944,23 @@ __device__ __forceinline__ bool tet_walk(const TetD& m, TetWalk& w, const int q[
     return tet_search<kNarrow>(m, w, q, D);
 }
 
+// 0 <= x < 2^23 as float, exactly: x is the mantissa of 2^23 + x.
+__device__ __forceinline__ float small_to_float(long long x) {
+    return __int_as_float(0x4b000000 | (int)x) - 8388608.0f;
+}
+
 // Barycentric interpolation of the corner values: lambda_i = D_i / sum D.
+// Inside a tet every D_i >= 0; all four are shifted right together until
+// the sum fits in 23 bits, so each weight is off by at most 2^-23 and no
+// 64-bit conversion (a double-precision-pipe instruction) is needed.
 __device__ __forceinline__ float tet_value(const long long D[4], const int4 v[4]) {
-    const float inv = 1.0f / __ll2float_rn(D[0] + D[1] + D[2] + D[3]);
-    float s = __ll2float_rn(D[0]) * __int_as_float(v[0].w);
-    s = ffma(__ll2float_rn(D[1]), __int_as_float(v[1].w), s);
-    s = ffma(__ll2float_rn(D[2]), __int_as_float(v[2].w), s);
-    s = ffma(__ll2float_rn(D[3]), __int_as_float(v[3].w), s);
+    const long long tot = D[0] + D[1] + D[2] + D[3];
+    const int sh = max(0, 41 - __clzll(tot));
+    const float inv = 1.0f / small_to_float(tot >> sh);
+    float s = small_to_float(D[0] >> sh) * __int_as_float(v[0].w);
+    s = ffma(small_to_float(D[1] >> sh), __int_as_float(v[1].w), s);
+    s = ffma(small_to_float(D[2] >> sh), __int_as_float(v[2].w), s);
+    s = ffma(small_to_float(D[3] >> sh), __int_as_float(v[3].w), s);
     return s * inv;
 }
 
