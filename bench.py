@@ -355,11 +355,25 @@ def main():
         ms_up = timed(uplain, 3)
         del pm, pc, gm
         torch.cuda.empty_cache()
+        usl = None
+        if not args.no_sortlast:
+            uexact = pkg.Volume.color_buffer(uv)
+            uvol.render_sortlast(uv, uexact)
+            ms_usl = timed(lambda: uvol.render_sortlast(uv, uexact), 3)
+            uframe()
+            uvol.synchronize()
+            dd = (urgba - uexact).view(-1, 4).double()
+            stu = uvol.stats()
+            usl = {"ms_per_frame": ms_usl, "segments": stu["sortlast_segments"],
+                   "max_segments_per_pixel": stu["sortlast_max_segments"], "speedup_of_batched_mboit": ms_usl / ms_u,
+                   "mboit_vs_exact_rmse": float(dd.pow(2).mean().sqrt()), "mboit_vs_exact_max": float(dd.abs().max())}
+            del uexact, dd
+            torch.cuda.empty_cache()
         uframe()
         uvol.synchronize()
         out_u = {"config": config_of(usc, name), "samples_per_frame": su, "ms_per_frame": ms_u,
                  "gsamples_per_s": su / (ms_u * 1e-3) / 1e9, "per_piece_fp32_ms_per_frame": ms_up,
-                 "speedup_of_batched": ms_up / ms_u}
+                 "speedup_of_batched": ms_up / ms_u, "sortlast_gpu": usl}
         if rank == 0 and not args.no_cpu_baseline:
             upix = sample_pixels(uw, uh, 64, 32)
             ref = __import__("oracle").render(usc, pixels=upix, want=("mboit",))["mboit"]

@@ -99,6 +99,13 @@ MB_HD float fsqrt_fast(float x) {
     return sqrtf(x);
 #endif
 }
+MB_HD float frsqrt_fast(float x) {
+#if defined(__CUDA_ARCH__)
+    return rsqrtf(x);  // one MUFU op
+#else
+    return 1.0f / sqrtf(x);
+#endif
+}
 MB_HD float fdiv_fast(float a, float b) {
 #if defined(__CUDA_ARCH__)
     return __fdividef(a, b);  // 2 ulp for |b| < 2^126; every divisor here is far below
@@ -289,22 +296,21 @@ MB_HD float bound_fraction(const Frame& F, float z0, float w0) {
         float y3 = ffma(x0, x0 - g, -1.0f);
         float e = y3 * inv_d;                         // leading coefficient of K(., x0)
         float rho0 = frcp(ffma(y3, e, ffma(x0, x0, 1.0f)));
-        if (y3 < 0.0f) {
-            // x1 < x0 < x2: need the weight of the smaller root x1
-            float c1 = ffma(-g, e, x0);
-            float c0 = 1.0f - e;
-            float disc = fmax_(ffma(c1, c1, -4.0f * e * c0), 0.0f);
-            float sq = fsqrt_fast(disc);
-            float h = -0.5f * (c1 + (c1 >= 0.0f ? sq : -sq));
-            float ra = fdiv_fast(h, e), rb = fdiv_fast(c0, h);
-            float x1 = fmin_(ra, rb);
-            float y31 = ffma(x1, x1 - g, -1.0f);
-            float rho1 = frcp(ffma(y31 * inv_d, y31, ffma(x1, x1, 1.0f)));
-            return ffma(w0, rho0, rho1);
-        }
         // x0 outside [x1, x2]: left of both iff K'(x0) < 0
         float slope = ffma(ffma(2.0f, x0, -g), e, x0);
-        return slope < 0.0f ? w0 * rho0 : ffma(w0 - 1.0f, rho0, 1.0f);
+        float A_out = slope < 0.0f ? w0 * rho0 : ffma(w0 - 1.0f, rho0, 1.0f);
+        // x1 < x0 < x2 (y3 < 0, so e < 0): the weight rho1 of the smaller root
+        // from the representation's moments of order 0 and 1 (rho0 + rho1 +
+        // rho2 = 1, rho0 x0 + rho1 x1 + rho2 x2 = 0) and the roots' sum and
+        // spread (-c1/e, sqrt(c1^2 - 4 e c0)/|e|):
+        //   rho1 = R/2 + (R c1/2 - rho0 x0 e) / sqrt(c1^2 - 4 e c0),  R = 1 - rho0
+        float c1 = ffma(-g, e, x0);
+        float c0 = 1.0f - e;
+        float disc = fmax_(ffma(c1, c1, -4.0f * e * c0), 1e-30f);
+        float R = 1.0f - rho0;
+        float rho1 = ffma(ffma(0.5f * R, c1, -rho0 * x0 * e), frsqrt_fast(disc), 0.5f * R);
+        rho1 = fclamp(rho1, 0.0f, R);
+        return y3 < 0.0f ? ffma(w0, rho0, rho1) : A_out;
     }
     if (F.kind == kFrameOneAtom) return step_weight(F.p0, z0, w0);
     if (F.kind == kFrameTwoAtoms) return F.p2 * step_weight(F.p0, z0, w0) + F.p3 * step_weight(F.p1, z0, w0);
