@@ -69,6 +69,10 @@ struct mboit_volume_s {
     int4* d_tnbrs = nullptr;
     int4* d_tcells = nullptr;
     float* d_scache = nullptr;  // sample values of the batched frame (grow only)
+    float* d_tcvals = nullptr;  // grid frames: tile-row sample cache (grow only)
+    long long* d_tile_base = nullptr;
+    unsigned long long* d_rows = nullptr;
+    size_t cap_tcvals = 0, cap_tile_base = 0;
     size_t cap_scache = 0;
     int32_t* d_bin_start = nullptr;
     int32_t* d_bin_tets = nullptr;
@@ -427,18 +431,50 @@ mboit_status prepare_tets(const mboit_volume_desc* d, TetHost& h) {
 // The batched (fused, persistent) passes of the volume's kind.  `cache`:
 // mesh sample values shared by the two passes of one frame.
 cudaError_t pass1_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, void* moments, cudaStream_t s,
-                          mb::SampleCache cache = mb::SampleCache{}) {
+                          mb::SampleCache cache = mb::SampleCache{}, mb::TileCache tc = mb::TileCache{}) {
     if (v->kind == MBOIT_AMR) return mb::launch_pass1_amr(v->amr, v->d_tf, mask, vt, moments, v->d_ctr, s);
     if (v->kind == MBOIT_TET) return mb::launch_pass1_tet(v->tet, v->d_tf, mask, vt, moments, v->d_ctr, s, cache);
-    return mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1);
+    return mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1, tc);
 }
 
 cudaError_t pass2_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, const void* moments,
-                          float* color, int32_t mode, cudaStream_t s, mb::SampleCache cache = mb::SampleCache{}) {
+                          float* color, int32_t mode, cudaStream_t s, mb::SampleCache cache = mb::SampleCache{},
+                          mb::TileCache tc = mb::TileCache{}) {
     if (v->kind == MBOIT_AMR) return mb::launch_pass2_amr(v->amr, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s);
     if (v->kind == MBOIT_TET)
         return mb::launch_pass2_tet(v->tet, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s, cache);
-    return mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s, v->tune2);
+    return mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s, v->tune2, tc);
+}
+
+// The tile-row sample cache of a grid frame: its exact row count for these
+// views (one small kernel, synchronous; done once per recorded frame graph),
+// then grow-only buffers.  Left off (c.vals NULL, pass 2 marches again) when
+// the device lacks the memory with 1 GiB to spare.
+mboit_status tile_cache(mboit_volume v, const mb::ViewTable& vt, mb::TileCache& c) {
+    c = mb::TileCache{};
+    if (v->kind != MBOIT_GRID) return MBOIT_OK;
+    cudaStream_t cs = v->cap_stream;
+    if (!v->d_rows) MB_CUDA(cudaMalloc(&v->d_rows, sizeof(unsigned long long)));
+    MB_CUDA(cudaMemsetAsync(v->d_rows, 0, sizeof(unsigned long long), cs));
+    MB_CUDA(mb::launch_tile_rows(v->grid, vt, v->d_rows, cs));
+    unsigned long long rows = 0;
+    MB_CUDA(cudaMemcpyAsync(&rows, v->d_rows, sizeof rows, cudaMemcpyDeviceToHost, cs));
+    MB_CUDA(cudaStreamSynchronize(cs));
+    const size_t nvals = (size_t)rows * 32, ntiles = (size_t)std::max(vt.total_tiles, 1);
+    size_t free_b = 0, total_b = 0;
+    MB_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t grow = (nvals > v->cap_tcvals ? nvals * sizeof(float) : 0) +
+                        (ntiles > v->cap_tile_base ? ntiles * sizeof(long long) : 0);
+    if (grow + (size_t(1) << 30) > free_b) return MBOIT_OK;
+    float* b1 = v->d_tcvals;
+    long long* b2 = v->d_tile_base;
+    MB_CUDA(ensure_capacity(v->d_tcvals, v->cap_tcvals, std::max<size_t>(nvals, 32)));
+    MB_CUDA(ensure_capacity(v->d_tile_base, v->cap_tile_base, ntiles));
+    if (v->d_tcvals != b1 || v->d_tile_base != b2) drop_graphs(v);
+    c.vals = v->d_tcvals;
+    c.tile_base = v->d_tile_base;
+    c.rows_cap = (long long)(v->cap_tcvals / 32);
+    return MBOIT_OK;
 }
 
 // The mesh frame's sample cache: L lattice points per ray bound the chord of
@@ -714,6 +750,9 @@ mboit_status mboit_destroy_volume(mboit_volume v) {
         cudaFree(v->d_tnbrs);
         cudaFree(v->d_tcells);
         cudaFree(v->d_scache);
+        cudaFree(v->d_tcvals);
+        cudaFree(v->d_tile_base);
+        cudaFree(v->d_rows);
         cudaFree(v->d_bin_start);
         cudaFree(v->d_bin_tets);
         cudaFree(v->d_tvals);
@@ -950,11 +989,13 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
     for (auto& ge : v->graphs)
         if (ge.key == key) exec = ge.exec;
     if (!exec) {
+        mb::TileCache tc;
+        if ((st = tile_cache(v, vt, tc)) != MBOIT_OK) return st;
         cudaStream_t cs = v->cap_stream;
         MB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemsetAsync(&v->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), cs);
-        if (e == cudaSuccess) e = pass1_batched(v, mask, vt, moments_scratch, cs, cache);
-        if (e == cudaSuccess) e = pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved, cs, cache);
+        if (e == cudaSuccess) e = pass1_batched(v, mask, vt, moments_scratch, cs, cache, tc);
+        if (e == cudaSuccess) e = pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved, cs, cache, tc);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {

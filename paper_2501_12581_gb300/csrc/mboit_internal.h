@@ -38,6 +38,7 @@ struct Counters {
     unsigned long long segments;     // sort-last segments of the last baseline frame
     int32_t max_segments;            // most segments on one pixel
     int32_t pad2;
+    unsigned long long cache_rows;   // rows of the frame's sample cache handed out so far
 };
 
 struct PieceBox {
@@ -91,6 +92,18 @@ struct SampleCache {
     int32_t pad;
 };
 
+// Sample values of one batched frame, shared by its two passes.  A warp's
+// 8 x 4 ray tile owns rows kmin..kmax (its lattice indices); row r holds 32
+// floats, one per lane, at vals[(tile_base[tile] + r - kmin) * 32 + lane]
+// (NaN: not sampled).  Pass 1 takes the tile's rows from ctr->cache_rows and
+// stores; pass 2 reads.  A tile that found no room (tile_base -1) is marched
+// again in pass 2.  vals NULL: no cache.
+struct TileCache {
+    float* vals;
+    long long* tile_base;
+    long long rows_cap;
+};
+
 // Number of shared-memory window configurations of the fused passes (the
 // autotuner's choices).  Configurations 2-4 use 16-byte loads and need
 // nx % 4 == 0 and a 16-byte aligned field; 0 and 1 work everywhere.
@@ -102,11 +115,15 @@ cudaError_t prepare_kernels();
 // Fused pass 1 over all selected pieces, REDUCED output.  `brick_sel` NULL
 // means every brick is sampled.  An ineligible `cfg` falls back to 0.
 cudaError_t launch_pass1_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
-                               void* moments, Counters* ctr, cudaStream_t s, int cfg = 0);
+                               void* moments, Counters* ctr, cudaStream_t s, int cfg = 0,
+                               TileCache cache = TileCache{});
 // Fused pass 2 over all selected pieces, REDUCED or RESOLVED output.
 cudaError_t launch_pass2_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
                                const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
-                               int cfg = 0);
+                               int cfg = 0, TileCache cache = TileCache{});
+// Rows a frame's tile cache needs over the domain box of `g` (sum over the
+// ray tiles of kmax - kmin + 1), added to *rows.
+cudaError_t launch_tile_rows(const GridD& g, const ViewTable& vt, unsigned long long* rows, cudaStream_t s);
 // Plain per-piece passes: one launch = one piece, its own slab.
 cudaError_t launch_pass1_piece(const GridD& g, const float4* tf, const int32_t* piece_of_brick, int32_t piece,
                                const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,

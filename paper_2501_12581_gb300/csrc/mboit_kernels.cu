@@ -194,9 +194,26 @@ __device__ __forceinline__ bool window_box(const GridD& g, const float o[3], con
 // Marches the lattice indices [k0, k1] of this lane's ray (exactly the
 // in-domain points; k0 > k1: none), calling body(t, value) for every owned
 // sample in depth order.  All 32 lanes of the warp call it together.
-template <class Cfg, bool kSel, class Body>
+// Where a march puts every lattice point's value: nowhere, or a tile-cache
+// row (the lane's slot of row k; NaN for a point no selected piece owns).
+struct NoStore {
+    __device__ __forceinline__ void seek(int) {}
+    __device__ __forceinline__ void put(float) {}
+};
+struct RowStore {
+    float* base;  // slot of row 0: vals + (tile_base - kmin) * 32 + lane; NULL: off
+    float* at = nullptr;
+    __device__ __forceinline__ void seek(int k) { at = base + (int64_t)k * 32; }
+    __device__ __forceinline__ void put(float v) {
+        if (base) __stcs(at, v);  // streaming store: read once by pass 2, keep the field in L2
+        at += 32;
+    }
+};
+
+template <class Cfg, bool kSel, class Body, class Store = NoStore>
 __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __restrict__ sel, float* __restrict__ win,
-                                            const float o[3], const float d[3], int k0, int k1, Body& body) {
+                                            const float o[3], const float d[3], int k0, int k1, Body& body,
+                                            Store store = Store{}) {
     const unsigned full = 0xffffffffu;
     const int kmin = __reduce_min_sync(full, k0);
     const int kmax = __reduce_max_sync(full, k1);
@@ -255,25 +272,35 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
             // t_{k+1} = t_k + step exactly (odd multiples of step/2 below 2^24), so the
             // loop runs on t itself
             const float tz = lattice_t(kz, g.step);
+            store.seek(ka);
             for (float t = lattice_t(ka, g.step); t <= tz; t += g.step) {
                 const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
                 const int ix = (int)p0, iy = (int)p1, iz = (int)p2;
                 if (kSel) {
                     const int b = ((iz >> g.brick_log2) * g.nby + (iy >> g.brick_log2)) * g.nbx + (ix >> g.brick_log2);
-                    if (!__ldg(sel + b)) continue;
+                    if (!__ldg(sel + b)) {
+                        store.put(__int_as_float(0x7fc00000));
+                        continue;
+                    }
                 }
                 const float* c = wbase + iz * Cfg::Plane + iy * Cfg::Pitch + ix;
                 const float val = trilinear8(c[0], c[1], c[Cfg::Pitch], c[Cfg::Pitch + 1], c[Cfg::Plane],
                                              c[Cfg::Plane + 1], c[Cfg::Plane + Cfg::Pitch],
                                              c[Cfg::Plane + Cfg::Pitch + 1], p0 - (float)ix, p1 - (float)iy,
                                              p2 - (float)iz);
+                store.put(val);
                 body(t, val);
             }
         } else {
             const float tz = lattice_t(kz, g.step);
+            store.seek(ka);
             for (float t = lattice_t(ka, g.step); t <= tz; t += g.step) {
                 float val;
-                if (!field_sample<kSel>(g, sel, t, o, d, val)) continue;
+                if (!field_sample<kSel>(g, sel, t, o, d, val)) {
+                    store.put(__int_as_float(0x7fc00000));
+                    continue;
+                }
+                store.put(val);
                 body(t, val);
             }
         }
@@ -500,9 +527,9 @@ __device__ __forceinline__ typename Bodies<MS>::Blend make_blend_body(const floa
 
 
 // Pops the next 8x4 ray tile of the work queue; returns false when empty.
-__device__ __forceinline__ bool next_tile(const ViewTable& vt, int32_t* head, int& vi, int& px, int& py) {
+__device__ __forceinline__ bool next_tile(const ViewTable& vt, int32_t* head, int& vi, int& px, int& py, int& tile) {
     const int lane = threadIdx.x & 31;
-    int tile = 0;
+    tile = 0;
     if (lane == 0) tile = atomicAdd(head, 1);
     tile = __shfl_sync(0xffffffffu, tile, 0);
     if (tile >= vt.total_tiles) return false;
@@ -544,39 +571,123 @@ __device__ __forceinline__ void ray_range(const GridD& g, const ViewD& V, bool v
     }
 }
 
-template <bool kSel, class Cfg, int MS>
+// Asynchronous 16-byte global -> shared copies (no register staging).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kRowChunk = 8;                    // cache rows per prefetch
+constexpr int kRowBuf = 2 * kRowChunk * 32;     // floats of a warp's double buffer
+
+// Pass 2 of the batched frame from the tile cache.  The tile's rows are
+// contiguous (rows[r * 32 + lane], r = k - kmin), so the warp copies them
+// into its shared-memory buffer 8 rows (1 KiB) at a time, one chunk ahead of
+// the one it blends, and every lane takes its own column over its own
+// [k0, k1].  buf: 16-byte aligned, kRowBuf floats, this warp's only.
+template <bool kSel, class Body>
+__device__ __forceinline__ void march_rows(const GridD& g, const float* __restrict__ rows, int kmin, int kmax, int k0,
+                                           int k1, float* __restrict__ buf, Body& body) {
+    if (kmin > kmax) return;
+    const int lane = threadIdx.x & 31;
+    const int nrows = kmax - kmin + 1;
+    const int nchunks = (nrows + kRowChunk - 1) / kRowChunk;
+    auto fetch = [&](int c) {
+        float* dst = buf + (c & 1) * kRowChunk * 32;
+#pragma unroll
+        for (int h = 0; h < kRowChunk / 4; ++h) {       // 16-byte pieces: 8 per row
+            const int piece = lane + 32 * h, r = piece >> 3, q = (piece & 7) * 4;
+            if (c * kRowChunk + r < nrows)
+                cp_async16(dst + r * 32 + q, rows + (int64_t)(c * kRowChunk + r) * 32 + q);
+        }
+        cp_async_commit();
+    };
+    fetch(0);
+    float t = lattice_t(kmin, g.step);
+    for (int c = 0; c < nchunks; ++c) {
+        if (c + 1 < nchunks) {
+            fetch(c + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
+        const float* src = buf + (c & 1) * kRowChunk * 32 + lane;
+        const int kc = kmin + c * kRowChunk;
+        const int n = min(kRowChunk, kmax - kc + 1);
+        for (int i = 0; i < n; ++i, t += g.step) {
+            const int k = kc + i;
+            if (k < k0 || k > k1) continue;
+            const float val = src[i * 32];
+            if (!kSel || val == val) body(t, val);  // every in-domain point is owned when no piece is left out
+        }
+        __syncwarp();  // every lane is done with the chunk before it is refilled
+    }
+}
+
+// Pass 1: the tile's rows of the cache (lane 0 takes them, all lanes get the
+// base; a tile that does not fit gets -1 and is marched again in pass 2).
+__device__ __forceinline__ float* tile_rows(const TileCache& c, Counters* ctr, int tile, int k0, int k1) {
+    const unsigned full = 0xffffffffu;
+    const int kmin = __reduce_min_sync(full, k0), kmax = __reduce_max_sync(full, k1);
+    long long base = -1;
+    if ((threadIdx.x & 31) == 0) {
+        if (kmax >= kmin) {
+            const long long rows = (long long)kmax - kmin + 1;
+            const long long r = (long long)atomicAdd(&ctr->cache_rows, (unsigned long long)rows);
+            if (r + rows <= c.rows_cap) base = r;
+        }
+        c.tile_base[tile] = base;
+    }
+    base = __shfl_sync(full, base, 0);
+    return base >= 0 ? c.vals + (base - kmin) * 32 + (threadIdx.x & 31) : nullptr;
+}
+
+template <bool kSel, class Cfg, int MS, bool kCache = false>
 __global__ void __launch_bounds__(256) k_pass1_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
                                                      const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
-                                                     char* __restrict__ moments, Counters* __restrict__ ctr) {
+                                                     char* __restrict__ moments, Counters* __restrict__ ctr,
+                                                     const TileCache cache) {
     __shared__ float2 s_sig[256];
-    __shared__ float s_win[kFusedWarps][Cfg::Floats];
+    __shared__ __align__(16) float s_win[kFusedWarps][Cfg::Floats];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float s0 = tf[i].w;
         s_sig[i] = make_float2(s0, i < 255 ? tf[i + 1].w - s0 : 0.0f);
     }
     __syncthreads();
     float* win = s_win[threadIdx.x >> 5];
-    int vi, px, py;
-    while (next_tile(vt, &ctr->tile_next[0], vi, px, py)) {
+    int vi, px, py, tile;
+    while (next_tile(vt, &ctr->tile_next[0], vi, px, py, tile)) {
         const ViewSlot& S = vt.s[vi];
         const bool valid = px < S.v.width && py < S.v.height;
         float o[3], d[3];
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
         auto body = make_moment_body<MS>(s_sig, g, S.v);
-        march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
+        if constexpr (kCache) {
+            RowStore st{tile_rows(cache, ctr, tile, k0, k1)};
+            march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body, st);
+        } else {
+            march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
+        }
         if (valid) body.store(g, moments, S, S.moment_off, py * S.v.width + px);
         warp_add_u64(&ctr->samples[0], body.n);
     }
 }
 
-template <bool kSel, class Cfg, int MS>
+template <bool kSel, class Cfg, int MS, bool kCache = false>
 __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
                                                      const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                      const char* __restrict__ moments, float* __restrict__ color,
-                                                     int mode, Counters* __restrict__ ctr) {
+                                                     int mode, Counters* __restrict__ ctr, const TileCache cache) {
+    static_assert(Cfg::Floats >= kRowBuf && Cfg::Floats % 4 == 0, "the window slot doubles as the row buffer");
     __shared__ float4 s_tf[512];
-    __shared__ float s_win[kFusedWarps][Cfg::Floats];
+    __shared__ __align__(16) float s_win[kFusedWarps][Cfg::Floats];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float4 e0 = tf[i], e1 = i < 255 ? tf[i + 1] : tf[i];
         s_tf[2 * i] = e0;
@@ -585,8 +696,8 @@ __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ Gri
     __syncthreads();
     float* win = s_win[threadIdx.x >> 5];
     const bool raw = (g.flags & 1u) != 0;
-    int vi, px, py;
-    while (next_tile(vt, &ctr->tile_next[1], vi, px, py)) {
+    int vi, px, py, tile;
+    while (next_tile(vt, &ctr->tile_next[1], vi, px, py, tile)) {
         const ViewSlot& S = vt.s[vi];
         const bool valid = px < S.v.width && py < S.v.height;
         const int pix = valid ? py * S.v.width + px : 0;
@@ -595,7 +706,13 @@ __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ Gri
         float o[3], d[3];
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
-        march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
+        const long long tb = kCache ? cache.tile_base[tile] : -1;
+        if (kCache && tb >= 0) {
+            const int kmin = __reduce_min_sync(0xffffffffu, k0), kmax = __reduce_max_sync(0xffffffffu, k1);
+            march_rows<kSel>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, win, body);
+        } else {
+            march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
+        }
         if (valid) {
             float4* out = reinterpret_cast<float4*>(color + S.color_off) + pix;
             if (mode == kColorResolved)
@@ -1120,8 +1237,8 @@ __global__ void __launch_bounds__(256, MinBlocks<V>::value) k_pass1_unit(const _
     }
     __syncthreads();
     const GridD& g = a.g;
-    int vi, px, py;
-    while (next_tile(vt, &ctr->tile_next[0], vi, px, py)) {
+    int vi, px, py, tile;
+    while (next_tile(vt, &ctr->tile_next[0], vi, px, py, tile)) {
         const ViewSlot& S = vt.s[vi];
         const bool valid = px < S.v.width && py < S.v.height;
         float o[3], d[3];
@@ -1154,8 +1271,8 @@ __global__ void __launch_bounds__(256, MinBlocks<V>::value) k_pass2_unit(const _
     __syncthreads();
     const GridD& g = a.g;
     const bool raw = (g.flags & 1u) != 0;
-    int vi, px, py;
-    while (next_tile(vt, &ctr->tile_next[1], vi, px, py)) {
+    int vi, px, py, tile;
+    while (next_tile(vt, &ctr->tile_next[1], vi, px, py, tile)) {
         const ViewSlot& S = vt.s[vi];
         const bool valid = px < S.v.width && py < S.v.height;
         const int pix = valid ? py * S.v.width + px : 0;
@@ -1517,39 +1634,64 @@ int persistent_blocks(const void* fn, int threads, size_t smem) {
     return nb;
 }
 
-template <int MS>
+template <int MS, bool kC>
 const void* pass1_fn_ms(int cfg, bool sel) {
-    if (sel) return (const void*)k_pass1_fused<true, Stage0, MS>;
-    if constexpr (MS != 0) return cfg == 3 ? (const void*)k_pass1_fused<false, Stage3, MS>
-                                           : (const void*)k_pass1_fused<false, Stage0, MS>;
+    if (sel) return (const void*)k_pass1_fused<true, Stage0, MS, kC>;
+    if constexpr (MS != 0) return cfg == 3 ? (const void*)k_pass1_fused<false, Stage3, MS, kC>
+                                           : (const void*)k_pass1_fused<false, Stage0, MS, kC>;
     switch (cfg) {
-        case 1: return (const void*)k_pass1_fused<false, Stage1, MS>;
-        case 2: return (const void*)k_pass1_fused<false, Stage2, MS>;
-        case 3: return (const void*)k_pass1_fused<false, Stage3, MS>;
-        case 4: return (const void*)k_pass1_fused<false, Stage4, MS>;
-        default: return (const void*)k_pass1_fused<false, Stage0, MS>;
+        case 1: return (const void*)k_pass1_fused<false, Stage1, MS, kC>;
+        case 2: return (const void*)k_pass1_fused<false, Stage2, MS, kC>;
+        case 3: return (const void*)k_pass1_fused<false, Stage3, MS, kC>;
+        case 4: return (const void*)k_pass1_fused<false, Stage4, MS, kC>;
+        default: return (const void*)k_pass1_fused<false, Stage0, MS, kC>;
     }
 }
 
-template <int MS>
+template <int MS, bool kC>
 const void* pass2_fn_ms(int cfg, bool sel) {
-    if (sel) return (const void*)k_pass2_fused<true, Stage0, MS>;
-    if constexpr (MS != 0) return cfg == 3 ? (const void*)k_pass2_fused<false, Stage3, MS>
-                                           : (const void*)k_pass2_fused<false, Stage0, MS>;
+    if (sel) return (const void*)k_pass2_fused<true, Stage0, MS, kC>;
+    if constexpr (MS != 0) return cfg == 3 ? (const void*)k_pass2_fused<false, Stage3, MS, kC>
+                                           : (const void*)k_pass2_fused<false, Stage0, MS, kC>;
     switch (cfg) {
-        case 1: return (const void*)k_pass2_fused<false, Stage1, MS>;
-        case 2: return (const void*)k_pass2_fused<false, Stage2, MS>;
-        case 3: return (const void*)k_pass2_fused<false, Stage3, MS>;
-        case 4: return (const void*)k_pass2_fused<false, Stage4, MS>;
-        default: return (const void*)k_pass2_fused<false, Stage0, MS>;
+        case 1: return (const void*)k_pass2_fused<false, Stage1, MS, kC>;
+        case 2: return (const void*)k_pass2_fused<false, Stage2, MS, kC>;
+        case 3: return (const void*)k_pass2_fused<false, Stage3, MS, kC>;
+        case 4: return (const void*)k_pass2_fused<false, Stage4, MS, kC>;
+        default: return (const void*)k_pass2_fused<false, Stage0, MS, kC>;
     }
 }
 
+template <bool kC = false>
 const void* pass1_fn(int cfg, bool sel, int ms) {
-    return ms == 3 ? pass1_fn_ms<3>(cfg, sel) : ms == 4 ? pass1_fn_ms<4>(cfg, sel) : pass1_fn_ms<0>(cfg, sel);
+    return ms == 3 ? pass1_fn_ms<3, kC>(cfg, sel) : ms == 4 ? pass1_fn_ms<4, kC>(cfg, sel) : pass1_fn_ms<0, kC>(cfg, sel);
 }
+template <bool kC = false>
 const void* pass2_fn(int cfg, bool sel, int ms) {
-    return ms == 3 ? pass2_fn_ms<3>(cfg, sel) : ms == 4 ? pass2_fn_ms<4>(cfg, sel) : pass2_fn_ms<0>(cfg, sel);
+    return ms == 3 ? pass2_fn_ms<3, kC>(cfg, sel) : ms == 4 ? pass2_fn_ms<4, kC>(cfg, sel) : pass2_fn_ms<0, kC>(cfg, sel);
+}
+
+// One warp per ray tile: adds the tile's cache rows (kmax - kmin + 1 over its
+// rays' exact in-domain intervals, as pass 1 will take them) to *rows.
+__global__ void __launch_bounds__(256) k_tile_rows(const __grid_constant__ GridD g, const __grid_constant__ ViewTable vt,
+                                                   unsigned long long* __restrict__ rows) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    unsigned long long mine = 0;
+    for (int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile < vt.total_tiles; tile += warps) {
+        const int vi = find_view(vt, tile);
+        const ViewSlot& S = vt.s[vi];
+        const int lt = tile - S.tile_base;
+        const int px = (lt % S.ntx) * kTileW + (lane & 7);
+        const int py = (lt / S.ntx) * kTileH + (lane >> 3);
+        const bool valid = px < S.v.width && py < S.v.height;
+        float o[3], d[3];
+        int k0, k1;
+        ray_range(g, S.v, valid, px, py, o, d, k0, k1);
+        const int kmin = __reduce_min_sync(0xffffffffu, k0), kmax = __reduce_max_sync(0xffffffffu, k1);
+        if (kmax >= kmin) mine += (unsigned long long)(kmax - kmin + 1);
+    }
+    if (lane == 0 && mine) atomicAdd(rows, mine);
 }
 template <class V, bool kC = false>
 const void* unit1_fn(bool sel, int ms) {
@@ -1607,7 +1749,7 @@ cudaError_t prepare_kernels() {
                          (const void*)k_pass1_piece<TetT<false>, 3>, (const void*)k_pass2_piece<TetT<false>, 3>,
                          (const void*)k_pass1_piece<TetT<false>, 4>, (const void*)k_pass2_piece<TetT<false>, 4>,
                          (const void*)k_sortlast_piece<TetT<false>, true>, (const void*)k_sortlast_piece<TetT<false>, false>,
-                         (const void*)k_tet_values,
+                         (const void*)k_tet_values,         (const void*)k_tile_rows,
                          (const void*)k_sortlast_totals,    (const void*)k_sortlast_starts,
                          (const void*)k_scan_blocks,        (const void*)k_scan_sums,
                          (const void*)k_scan_add,           (const void*)k_sortlast_blend};
@@ -1620,14 +1762,14 @@ cudaError_t prepare_kernels() {
     for (int ms : sets)
         for (int cfg = 0; cfg < kNumStageConfigs; ++cfg)
             for (int sel = 0; sel < 2; ++sel) {
-                const void* f1 = pass1_fn(cfg, sel, ms);
-                const void* f2 = pass2_fn(cfg, sel, ms);
-                cudaFuncAttributes a;
-                cudaError_t e = cudaFuncGetAttributes(&a, f1);
-                if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, f2);
-                if (e != cudaSuccess) return e;
-                persistent_blocks(f1, 256, 0);
-                persistent_blocks(f2, 256, 0);
+                const void* fs[4] = {pass1_fn(cfg, sel, ms), pass2_fn(cfg, sel, ms), pass1_fn<true>(cfg, sel, ms),
+                                     pass2_fn<true>(cfg, sel, ms)};
+                for (const void* f : fs) {
+                    cudaFuncAttributes a;
+                    const cudaError_t e = cudaFuncGetAttributes(&a, f);
+                    if (e != cudaSuccess) return e;
+                    persistent_blocks(f, 256, 0);
+                }
             }
     for (int ms : sets)
         for (int sel = 0; sel < 2; ++sel) {
@@ -1646,28 +1788,37 @@ cudaError_t prepare_kernels() {
 }
 
 cudaError_t launch_pass1_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
-                               void* moments, Counters* ctr, cudaStream_t s, int cfg) {
+                               void* moments, Counters* ctr, cudaStream_t s, int cfg, TileCache cache) {
     if (!stage_config_eligible(g, cfg)) cfg = 0;
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
+    if (e == cudaSuccess && cache.vals) e = cudaMemsetAsync(&ctr->cache_rows, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    const void* fn = pass1_fn(cfg, brick_sel != nullptr, g.trig.n);
+    const bool sel = brick_sel != nullptr;
+    const void* fn = cache.vals ? pass1_fn<true>(cfg, sel, g.trig.n) : pass1_fn(cfg, sel, g.trig.n);
     char* m = static_cast<char*>(moments);
-    void* args[] = {(void*)&g, (void*)&tf, (void*)&brick_sel, (void*)&vt, (void*)&m, (void*)&ctr};
+    void* args[] = {(void*)&g, (void*)&tf, (void*)&brick_sel, (void*)&vt, (void*)&m, (void*)&ctr, (void*)&cache};
     return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
 }
 
 cudaError_t launch_pass2_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
                                const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
-                               int cfg) {
+                               int cfg, TileCache cache) {
     if (!stage_config_eligible(g, cfg)) cfg = 0;
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[1], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const void* fn = pass2_fn(cfg, brick_sel != nullptr, g.trig.n);
+    const bool sel = brick_sel != nullptr;
+    const void* fn = cache.vals ? pass2_fn<true>(cfg, sel, g.trig.n) : pass2_fn(cfg, sel, g.trig.n);
     const char* m = static_cast<const char*>(moments);
     int md = mode;
     void* args[] = {(void*)&g, (void*)&tf, (void*)&brick_sel, (void*)&vt, (void*)&m, (void*)&color, (void*)&md,
-                    (void*)&ctr};
+                    (void*)&ctr, (void*)&cache};
     return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
+}
+
+cudaError_t launch_tile_rows(const GridD& g, const ViewTable& vt, unsigned long long* rows, cudaStream_t s) {
+    const int blocks = (vt.total_tiles + 7) / 8;
+    k_tile_rows<<<blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096, 256, 0, s>>>(g, vt, rows);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pass1_piece(const GridD& g, const float4* tf, const int32_t* pob, int32_t piece,

@@ -109,6 +109,29 @@ def test_render_frame_graph_matches_oracle_and_is_deterministic(pkg, blobs):
     assert_rgba_close(unpack_color(a, views)[0][0], ref["mboit"])
 
 
+def test_frame_sample_cache_equals_split_calls(pkg, blobs):
+    """The frame's pass 2 reads the values pass 1 stored in its tile rows; the
+    split calls march twice: the same bits, also for ragged views, several
+    views in one frame and a view that misses the domain."""
+    import torch
+    sc, _, vol = blobs
+    for views in (sc.views,
+                  [scenes.ortho_view(sc.dims, (0.3, -0.8, 0.5), 37, 23),
+                   scenes.perspective_view(sc.dims, (-0.5, 0.6, -0.62), 20, 13, fov_deg=40.0),
+                   small.axis_view(sc.dims, 9, 5, -10.0, 4.0, centre=(300.0, 300.0))]):
+        m1, c1 = pkg.Volume.moment_buffer(views), pkg.Volume.color_buffer(views)
+        vol.render_frame(views, m1, c1)
+        vol.render_frame(views, m1, c1)
+        m2, c2 = pkg.Volume.moment_buffer(views), pkg.Volume.color_buffer(views)
+        vol.render_moments(views, m2)
+        vol.reconstruct_blend(views, m2, c2)
+        vol.synchronize()
+        sync()
+        assert torch.equal(m1, m2) and torch.equal(c1, c2)
+        st = vol.stats()
+        assert st["samples_pass1"] == st["samples_pass2"]
+
+
 def test_per_piece_path_and_composites(pkg, blobs):
     sc, ref, vol = blobs
     views = sc.views
