@@ -68,12 +68,10 @@ struct mboit_volume_s {
     int4* d_tcorners = nullptr;
     int4* d_tnbrs = nullptr;
     int4* d_tcells = nullptr;
-    float* d_scache = nullptr;  // sample values of the batched frame (grow only)
-    float* d_tcvals = nullptr;  // grid frames: tile-row sample cache (grow only)
+    float* d_tcvals = nullptr;  // tile-row sample cache of the batched frame (grow only)
     long long* d_tile_base = nullptr;
     unsigned long long* d_rows = nullptr;
     size_t cap_tcvals = 0, cap_tile_base = 0;
-    size_t cap_scache = 0;
     int32_t* d_bin_start = nullptr;
     int32_t* d_bin_tets = nullptr;
     float* d_tvals = nullptr;   // staging of host vertex values (mboit_render_frame_host)
@@ -431,28 +429,27 @@ mboit_status prepare_tets(const mboit_volume_desc* d, TetHost& h) {
 // The batched (fused, persistent) passes of the volume's kind.  `cache`:
 // mesh sample values shared by the two passes of one frame.
 cudaError_t pass1_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, void* moments, cudaStream_t s,
-                          mb::SampleCache cache = mb::SampleCache{}, mb::TileCache tc = mb::TileCache{}) {
-    if (v->kind == MBOIT_AMR) return mb::launch_pass1_amr(v->amr, v->d_tf, mask, vt, moments, v->d_ctr, s);
-    if (v->kind == MBOIT_TET) return mb::launch_pass1_tet(v->tet, v->d_tf, mask, vt, moments, v->d_ctr, s, cache);
+                          mb::TileCache tc = mb::TileCache{}) {
+    if (v->kind == MBOIT_AMR) return mb::launch_pass1_amr(v->amr, v->d_tf, mask, vt, moments, v->d_ctr, s, tc);
+    if (v->kind == MBOIT_TET) return mb::launch_pass1_tet(v->tet, v->d_tf, mask, vt, moments, v->d_ctr, s, tc);
     return mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1, tc);
 }
 
 cudaError_t pass2_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, const void* moments,
-                          float* color, int32_t mode, cudaStream_t s, mb::SampleCache cache = mb::SampleCache{},
-                          mb::TileCache tc = mb::TileCache{}) {
-    if (v->kind == MBOIT_AMR) return mb::launch_pass2_amr(v->amr, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s);
+                          float* color, int32_t mode, cudaStream_t s, mb::TileCache tc = mb::TileCache{}) {
+    if (v->kind == MBOIT_AMR)
+        return mb::launch_pass2_amr(v->amr, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s, tc);
     if (v->kind == MBOIT_TET)
-        return mb::launch_pass2_tet(v->tet, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s, cache);
+        return mb::launch_pass2_tet(v->tet, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s, tc);
     return mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s, v->tune2, tc);
 }
 
-// The tile-row sample cache of a grid frame: its exact row count for these
-// views (one small kernel, synchronous; done once per recorded frame graph),
-// then grow-only buffers.  Left off (c.vals NULL, pass 2 marches again) when
-// the device lacks the memory with 1 GiB to spare.
+// The tile-row sample cache of a frame: its exact row count for these views
+// (one small kernel, synchronous; done once per recorded frame graph), then
+// grow-only buffers.  Left off (c.vals NULL, pass 2 marches again) when the
+// device lacks the memory with 1 GiB to spare.
 mboit_status tile_cache(mboit_volume v, const mb::ViewTable& vt, mb::TileCache& c) {
     c = mb::TileCache{};
-    if (v->kind != MBOIT_GRID) return MBOIT_OK;
     cudaStream_t cs = v->cap_stream;
     if (!v->d_rows) MB_CUDA(cudaMalloc(&v->d_rows, sizeof(unsigned long long)));
     MB_CUDA(cudaMemsetAsync(v->d_rows, 0, sizeof(unsigned long long), cs));
@@ -474,25 +471,6 @@ mboit_status tile_cache(mboit_volume v, const mb::ViewTable& vt, mb::TileCache& 
     c.vals = v->d_tcvals;
     c.tile_base = v->d_tile_base;
     c.rows_cap = (long long)(v->cap_tcvals / 32);
-    return MBOIT_OK;
-}
-
-// The mesh frame's sample cache: L lattice points per ray bound the chord of
-// the box (plus rounding slack), one float per point and pixel.
-mboit_status tet_cache(mboit_volume v, const mb::ViewTable& vt, mb::SampleCache& c) {
-    c = mb::SampleCache{};
-    if (v->kind != MBOIT_TET) return MBOIT_OK;
-    const mb::GridD& g = v->grid;
-    const double diag = std::sqrt((double)g.hx * g.hx + (double)g.hy * g.hy + (double)g.hz * g.hz);
-    const int64_t L = (int64_t)std::ceil(diag / (double)g.step) + 4;
-    int64_t px = 0;
-    for (int i = 0; i < vt.n; ++i) px += (int64_t)vt.s[i].v.width * vt.s[i].v.height;
-    if (L > INT32_MAX) return fail(MBOIT_ERR_INVALID_ARG, "mesh box too long for the sample cache");
-    float* before = v->d_scache;
-    MB_CUDA(ensure_capacity(v->d_scache, v->cap_scache, (size_t)(L * px)));
-    if (v->d_scache != before) drop_graphs(v);
-    c.vals = v->d_scache;
-    c.L = (int32_t)L;
     return MBOIT_OK;
 }
 
@@ -749,7 +727,6 @@ mboit_status mboit_destroy_volume(mboit_volume v) {
         cudaFree(v->d_tcorners);
         cudaFree(v->d_tnbrs);
         cudaFree(v->d_tcells);
-        cudaFree(v->d_scache);
         cudaFree(v->d_tcvals);
         cudaFree(v->d_tile_base);
         cudaFree(v->d_rows);
@@ -983,8 +960,6 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
     std::memcpy(key.data(), &vt, sizeof vt);
     std::memcpy(key.data() + sizeof vt, &moments_scratch, sizeof(void*));
     std::memcpy(key.data() + sizeof vt + sizeof(void*), &rgba, sizeof(void*));
-    mb::SampleCache cache;
-    if ((st = tet_cache(v, vt, cache)) != MBOIT_OK) return st;
     cudaGraphExec_t exec = nullptr;
     for (auto& ge : v->graphs)
         if (ge.key == key) exec = ge.exec;
@@ -994,8 +969,8 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
         cudaStream_t cs = v->cap_stream;
         MB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemsetAsync(&v->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), cs);
-        if (e == cudaSuccess) e = pass1_batched(v, mask, vt, moments_scratch, cs, cache, tc);
-        if (e == cudaSuccess) e = pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved, cs, cache, tc);
+        if (e == cudaSuccess) e = pass1_batched(v, mask, vt, moments_scratch, cs, tc);
+        if (e == cudaSuccess) e = pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved, cs, tc);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {

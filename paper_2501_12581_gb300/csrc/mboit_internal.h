@@ -82,16 +82,6 @@ struct TetD {
 template <bool kNarrow>
 struct TetT : TetD {};
 
-// Sample values of the batched frame: pass 1 stores the value of every
-// lattice point j = k - k0 of every ray (NaN: not sampled), pass 2 reads
-// them instead of locating the points again.  Slot of (view, pixel, j):
-// (color_off / 4) * L + j * width * height + pixel.
-struct SampleCache {
-    float* vals;
-    int32_t L;                 // lattice points per ray, at most
-    int32_t pad;
-};
-
 // Sample values of one batched frame, shared by its two passes.  A warp's
 // 8 x 4 ray tile owns rows kmin..kmax (its lattice indices); row r holds 32
 // floats, one per lane, at vals[(tile_base[tile] + r - kmin) * 32 + lane]
@@ -144,10 +134,12 @@ cudaError_t launch_sortlast_offsets(const ViewTable& vt, int32_t n_slots, const 
 cudaError_t launch_sortlast_blend(const int64_t* base, int32_t* seg_key, float4* seg_col, float* rgba, int64_t total_px,
                                   Counters* ctr, cudaStream_t s);
 // Octree versions of the passes (direct gathers; same output layouts).
+// `cache` (vals NULL: none): pass 1 stores the frame's samples, pass 2 reads them.
 cudaError_t launch_pass1_amr(const AmrD& a, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
-                             void* moments, Counters* ctr, cudaStream_t s);
+                             void* moments, Counters* ctr, cudaStream_t s, TileCache cache = TileCache{});
 cudaError_t launch_pass2_amr(const AmrD& a, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
-                             const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s);
+                             const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
+                             TileCache cache = TileCache{});
 cudaError_t launch_pass1_piece(const AmrD& a, const float4* tf, const int32_t* piece_of_unit, int32_t piece,
                                const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
                                void* moments, Counters* ctr, cudaStream_t s);
@@ -159,12 +151,12 @@ cudaError_t launch_sortlast_march(bool fill, const AmrD& a, const float4* tf, co
                                   int32_t n_slots, int32_t* counts, const int64_t* starts, int32_t* seg_key,
                                   float4* seg_col, cudaStream_t s);
 // Tetrahedral-mesh versions (walks between face neighbours; same layouts).
-// `cache` (vals NULL: none): pass 1 stores the sample values, pass 2 reads them.
+// `cache` (vals NULL: none): pass 1 stores the frame's samples, pass 2 reads them.
 cudaError_t launch_pass1_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
-                             void* moments, Counters* ctr, cudaStream_t s, SampleCache cache = SampleCache{});
+                             void* moments, Counters* ctr, cudaStream_t s, TileCache cache = TileCache{});
 cudaError_t launch_pass2_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
                              const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
-                             SampleCache cache = SampleCache{});
+                             TileCache cache = TileCache{});
 cudaError_t launch_pass1_piece(const TetD& m, const float4* tf, const int32_t* piece_of_unit, int32_t piece,
                                const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
                                void* moments, Counters* ctr, cudaStream_t s);

@@ -1109,14 +1109,13 @@ __device__ __forceinline__ bool piece_sample(const TetT<kNarrow>& m, const int32
 // taken, the next point comes up) or crosses a face towards it, so the
 // lanes stay together in the test and part only for the sample or the
 // crossing.  The owners are those of tet_walk: the same walk, the same
-// fallback.  kStore: every lattice point's value (NaN: not sampled) goes to
-// cache[j * stride], j = k - k0.
-template <bool kSel, bool kStore, class Body, bool kNarrow>
-__device__ __forceinline__ void march_tet(const TetT<kNarrow>& m, const uint8_t* __restrict__ sel, const float o[3],
-                                          const float d[3], int k0, int k1, Body& body, float* __restrict__ cache,
-                                          int64_t stride) {
+// fallback.  `store` gets every lattice point's value (NaN: not sampled).
+template <bool kSel, class Body, bool kNarrow, class Store = NoStore>
+__device__ __forceinline__ void march_unit(const TetT<kNarrow>& m, const uint8_t* __restrict__ sel, const float o[3],
+                                           const float d[3], int k0, int k1, Body& body, Store store = Store{}) {
     const GridD& g = m.g;
     if (k0 > k1) return;
+    store.seek(k0);
     const float tz = lattice_t(k1, g.step);
     float t = lattice_t(k0, g.step);
     int q[3];
@@ -1131,7 +1130,6 @@ __device__ __forceinline__ void march_tet(const TetT<kNarrow>& m, const uint8_t*
         if (j0 < __ldg(m.bin_start + b + 1)) load_tet(m, __ldg(m.bin_tets + j0), w);
     }
     long long D[4];
-    int64_t j = 0;
     int skip = -1, steps = 0;
     while (t <= tz) {
         const int f = w.T >= 0 ? tet_exit_face<kNarrow>(w.v, q, D, steps, skip) : -2;
@@ -1155,9 +1153,8 @@ __device__ __forceinline__ void march_tet(const TetT<kNarrow>& m, const uint8_t*
             val = tet_value(D, w.v);
             body(t, val);
         }
-        if (kStore) cache[j] = val;
+        store.put(val);
         t += g.step;
-        j += stride;
         const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
         snap_point(m, p, q);
         skip = -1;
@@ -1165,55 +1162,23 @@ __device__ __forceinline__ void march_tet(const TetT<kNarrow>& m, const uint8_t*
     }
 }
 
-template <bool kSel, class Body, bool kNarrow>
-__device__ __forceinline__ void march_unit(const TetT<kNarrow>& m, const uint8_t* __restrict__ sel, const float o[3],
-                                           const float d[3], int k0, int k1, Body& body) {
-    march_tet<kSel, false>(m, sel, o, d, k0, k1, body, nullptr, 0);
-}
-
-template <bool kSel, class Body, bool kNarrow>
-__device__ __forceinline__ void march_unit_store(const TetT<kNarrow>& m, const uint8_t* __restrict__ sel,
-                                                 const float o[3], const float d[3], int k0, int k1, Body& body,
-                                                 float* __restrict__ cache, int64_t stride) {
-    march_tet<kSel, true>(m, sel, o, d, k0, k1, body, cache, stride);
-}
-
-// Pass 2 of the batched frame: the values pass 1 stored.
-template <class Body>
-__device__ __forceinline__ void march_cached(const GridD& g, int k0, int k1, const float* __restrict__ cache,
-                                             int64_t stride, Body& body) {
-    if (k0 > k1) return;
-    const float tz = lattice_t(k1, g.step);
-    int64_t j = 0;
-    for (float t = lattice_t(k0, g.step); t <= tz; t += g.step, j += stride) {
-        const float val = __ldg(cache + j);
-        if (val == val) body(t, val);
-    }
-}
-
-// Ray slot of the sample cache; clamps k1 to the cache's L lattice points
-// (flagging an error if that cuts the ray, which the box bound excludes).
-__device__ __forceinline__ int64_t cache_slot(const SampleCache& c, const ViewSlot& S, int pix, int k0, int& k1,
-                                              Counters* ctr) {
-    if (k1 - k0 + 1 > c.L) {
-        k1 = k0 + c.L - 1;
-        atomicExch(&ctr->error, 3);
-    }
-    return (S.color_off / 4) * (int64_t)c.L + pix;
-}
-
-template <bool kSel, class Body>
+template <bool kSel, class Body, class Store = NoStore>
 __device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restrict__ sel, const float o[3],
-                                           const float d[3], int k0, int k1, Body& body) {
+                                           const float d[3], int k0, int k1, Body& body, Store store = Store{}) {
     const GridD& g = a.g;
     if (k0 > k1) return;
+    store.seek(k0);
     const float tz = lattice_t(k1, g.step);
     for (float t = lattice_t(k0, g.step); t <= tz; t += g.step) {
         const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
         const int u = unit_of(a, p);
-        if (u < 0) continue;
-        if (kSel && !__ldg(sel + u)) continue;
-        body(t, unit_value(a, p, u));
+        if (u < 0 || (kSel && !__ldg(sel + u))) {
+            store.put(__int_as_float(0x7fc00000));
+            continue;
+        }
+        const float val = unit_value(a, p, u);
+        store.put(val);
+        body(t, val);
     }
 }
 
@@ -1229,7 +1194,7 @@ template <class V, bool kSel, int MS, bool kCache = false>
 __global__ void __launch_bounds__(256, MinBlocks<V>::value) k_pass1_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
                                                     const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                     char* __restrict__ moments, Counters* __restrict__ ctr,
-                                                    const SampleCache cache) {
+                                                    const TileCache cache) {
     __shared__ float2 s_sig[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float s0 = tf[i].w;
@@ -1246,9 +1211,8 @@ __global__ void __launch_bounds__(256, MinBlocks<V>::value) k_pass1_unit(const _
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
         auto body = make_moment_body<MS>(s_sig, g, S.v);
         if constexpr (kCache) {
-            const int pix = valid ? py * S.v.width + px : 0;
-            const int64_t slot = cache_slot(cache, S, pix, k0, k1, ctr);
-            march_unit_store<kSel>(a, sel, o, d, k0, k1, body, cache.vals + slot, (int64_t)S.v.width * S.v.height);
+            RowStore st{tile_rows(cache, ctr, tile, k0, k1)};
+            march_unit<kSel>(a, sel, o, d, k0, k1, body, st);
         } else {
             march_unit<kSel>(a, sel, o, d, k0, k1, body);
         }
@@ -1261,8 +1225,9 @@ template <class V, bool kSel, int MS, bool kCache = false>
 __global__ void __launch_bounds__(256, MinBlocks<V>::value) k_pass2_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
                                                     const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                     const char* __restrict__ moments, float* __restrict__ color, int mode,
-                                                    Counters* __restrict__ ctr, const SampleCache cache) {
+                                                    Counters* __restrict__ ctr, const TileCache cache) {
     __shared__ float4 s_tf[512];
+    __shared__ __align__(16) float s_rows[kCache ? kFusedWarps : 1][kCache ? kRowBuf : 4];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float4 e0 = tf[i], e1 = i < 255 ? tf[i + 1] : tf[i];
         s_tf[2 * i] = e0;
@@ -1281,9 +1246,10 @@ __global__ void __launch_bounds__(256, MinBlocks<V>::value) k_pass2_unit(const _
         float o[3], d[3];
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
-        if constexpr (kCache) {
-            const int64_t slot = cache_slot(cache, S, pix, k0, k1, ctr);
-            march_cached(g, k0, k1, cache.vals + slot, (int64_t)S.v.width * S.v.height, body);
+        const long long tb = kCache ? cache.tile_base[tile] : -1;
+        if (kCache && tb >= 0) {
+            const int kmin = __reduce_min_sync(0xffffffffu, k0), kmax = __reduce_max_sync(0xffffffffu, k1);
+            march_rows<true>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, s_rows[kCache ? threadIdx.x >> 5 : 0], body);
         } else {
             march_unit<kSel>(a, sel, o, d, k0, k1, body);
         }
@@ -1775,6 +1741,8 @@ cudaError_t prepare_kernels() {
         for (int sel = 0; sel < 2; ++sel) {
             persistent_blocks(unit1_fn<AmrD>(sel, ms), 256, 0);
             persistent_blocks(unit2_fn<AmrD>(sel, ms), 256, 0);
+            persistent_blocks(unit1_fn<AmrD, true>(sel, ms), 256, 0);
+            persistent_blocks(unit2_fn<AmrD, true>(sel, ms), 256, 0);
             persistent_blocks(unit1_fn<TetT<true>>(sel, ms), 256, 0);
             persistent_blocks(unit2_fn<TetT<true>>(sel, ms), 256, 0);
             persistent_blocks(unit1_fn<TetT<false>>(sel, ms), 256, 0);
@@ -1916,26 +1884,28 @@ cudaError_t launch_sortlast_blend(const int64_t* base, int32_t* seg_key, float4*
 }
 
 cudaError_t launch_pass1_amr(const AmrD& a, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
-                             void* moments, Counters* ctr, cudaStream_t s) {
+                             void* moments, Counters* ctr, cudaStream_t s, TileCache cache) {
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
+    if (e == cudaSuccess && cache.vals) e = cudaMemsetAsync(&ctr->cache_rows, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    const void* fn = unit1_fn<AmrD>(unit_sel != nullptr, a.g.trig.n);
+    const bool sel = unit_sel != nullptr;
+    const void* fn = cache.vals ? unit1_fn<AmrD, true>(sel, a.g.trig.n) : unit1_fn<AmrD>(sel, a.g.trig.n);
     char* m = static_cast<char*>(moments);
-    SampleCache none{};
-    void* args[] = {(void*)&a, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&m, (void*)&ctr, (void*)&none};
+    void* args[] = {(void*)&a, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&m, (void*)&ctr, (void*)&cache};
     return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
 }
 
 cudaError_t launch_pass2_amr(const AmrD& a, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
-                             const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s) {
+                             const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
+                             TileCache cache) {
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[1], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const void* fn = unit2_fn<AmrD>(unit_sel != nullptr, a.g.trig.n);
+    const bool sel = unit_sel != nullptr;
+    const void* fn = cache.vals ? unit2_fn<AmrD, true>(sel, a.g.trig.n) : unit2_fn<AmrD>(sel, a.g.trig.n);
     const char* m = static_cast<const char*>(moments);
     int md = mode;
-    SampleCache none{};
     void* args[] = {(void*)&a, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&m, (void*)&color, (void*)&md,
-                    (void*)&ctr, (void*)&none};
+                    (void*)&ctr, (void*)&cache};
     return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
 }
 
@@ -1986,8 +1956,9 @@ TetT<kN> as_tet(const TetD& m) {
 
 template <class V>
 cudaError_t launch_unit1(const V& vol, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt, void* moments,
-                         Counters* ctr, cudaStream_t s, SampleCache cache) {
+                         Counters* ctr, cudaStream_t s, TileCache cache) {
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
+    if (e == cudaSuccess && cache.vals) e = cudaMemsetAsync(&ctr->cache_rows, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const bool sel = unit_sel != nullptr;
     const void* fn = cache.vals ? unit1_fn<V, true>(sel, vol.g.trig.n) : unit1_fn<V>(sel, vol.g.trig.n);
@@ -1999,7 +1970,7 @@ cudaError_t launch_unit1(const V& vol, const float4* tf, const uint8_t* unit_sel
 template <class V>
 cudaError_t launch_unit2(const V& vol, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
                          const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
-                         SampleCache cache) {
+                         TileCache cache) {
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[1], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     const bool sel = unit_sel != nullptr;
@@ -2052,14 +2023,14 @@ cudaError_t launch_sortlast(bool fill, const V& m, const float4* tf, const int32
 }  // namespace
 
 cudaError_t launch_pass1_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
-                             void* moments, Counters* ctr, cudaStream_t s, SampleCache cache) {
+                             void* moments, Counters* ctr, cudaStream_t s, TileCache cache) {
     return m.narrow ? launch_unit1(as_tet<true>(m), tf, unit_sel, vt, moments, ctr, s, cache)
                     : launch_unit1(as_tet<false>(m), tf, unit_sel, vt, moments, ctr, s, cache);
 }
 
 cudaError_t launch_pass2_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
                              const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
-                             SampleCache cache) {
+                             TileCache cache) {
     return m.narrow ? launch_unit2(as_tet<true>(m), tf, unit_sel, vt, moments, color, mode, ctr, s, cache)
                     : launch_unit2(as_tet<false>(m), tf, unit_sel, vt, moments, color, mode, ctr, s, cache);
 }
