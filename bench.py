@@ -42,7 +42,8 @@ FLOP_PASS2 = 76
 # FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x
 # 2 FLOP x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-KERNEL_SOURCES = ["paper_2501_12581_gb300/csrc/mboit_kernels.cu", "paper_2501_12581_gb300/csrc/mboit_device.cuh"]
+KERNEL_SOURCES = ["paper_2501_12581_gb300/csrc/mboit_grid.cu", "paper_2501_12581_gb300/csrc/mboit_common.cuh",
+                  "paper_2501_12581_gb300/csrc/mboit_device.cuh", "paper_2501_12581_gb300/csrc/mboit_trig.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pass2_fused_blobs512_traffic.txt")
 
 

@@ -3,7 +3,7 @@
 // Host side only: argument validation, the volume registry (transfer
 // function, brick ownership, piece boxes), view tables, CUDA-graph capture of
 // the batched frame, and error reporting.  Every step of the render runs in
-// the kernels of mboit_kernels.cu.
+// the kernels of mboit_grid.cu, mboit_units.cu and mboit_kernels.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>

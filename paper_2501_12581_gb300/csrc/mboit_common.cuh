@@ -1,0 +1,476 @@
+// Device code shared by the kernel translation units of the MBOIT
+// puzzle-piece render (sm_103a): transfer-function and moment-image helpers,
+// the per-sample bodies of pass 1 (Alg. 2) and pass 2 (Alg. 1 loop 2, Alg. 3),
+// the work queue of 8 x 4 ray tiles, exact in-domain ray intervals, and the
+// frame's tile-row sample cache (pass 1 stores, pass 2 prefetches and reads).
+// Everything here is internal (an unnamed namespace per translation unit).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "mboit_internal.h"
+#include "mboit_trig.cuh"
+
+namespace mb {
+
+// Resident CTAs per SM x SMs for a persistent kernel, cached per function.
+int persistent_blocks(const void* fn, int threads, size_t smem);
+
+namespace {
+
+constexpr int kFusedWarps = 8;  // 256 threads per CTA
+
+__device__ __forceinline__ float one_minus_exp_neg(float a) {
+    // 1 - e^-a without cancellation: Taylor series a * sum_{n>=0} (-a)^n / (n+1)!
+    // truncated after (-a)^5/6! for a < 1/4 (relative error < 5e-8); the
+    // direct form above, where cancellation costs at most a few ulp.
+    if (a < 0.25f) {
+        float p = ffma(a, -1.0f / 720.0f, 1.0f / 120.0f);
+        p = ffma(a, p, -1.0f / 24.0f);
+        p = ffma(a, p, 1.0f / 6.0f);
+        p = ffma(a, p, -0.5f);
+        p = ffma(a, p, 1.0f);
+        return a * p;
+    }
+    return 1.0f - fexp2(-a * kLog2e);
+}
+
+// Position of lattice point t on the ray, domain test, optional brick
+// selection, trilinear value.  Cells are half-open, so a point inside
+// [0, n-1) has all 8 corner vertices in range.
+template <bool kSel>
+__device__ __forceinline__ bool field_sample(const GridD& g, const uint8_t* __restrict__ sel, float t,
+                                             const float o[3], const float d[3], float& val) {
+    const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
+    if (!(p0 >= 0.0f && p0 < g.hx && p1 >= 0.0f && p1 < g.hy && p2 >= 0.0f && p2 < g.hz)) return false;
+    const int ix = (int)p0, iy = (int)p1, iz = (int)p2;
+    if (kSel) {
+        const int b = ((iz >> g.brick_log2) * g.nby + (iy >> g.brick_log2)) * g.nbx + (ix >> g.brick_log2);
+        if (!__ldg(sel + b)) return false;
+    }
+    const float fx = p0 - (float)ix, fy = p1 - (float)iy, fz = p2 - (float)iz;
+    const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * (size_t)g.ny;
+    const float* __restrict__ c = g.field + (size_t)iz * sz + (size_t)iy * sy + (size_t)ix;
+    const float v000 = __ldg(c), v100 = __ldg(c + 1);
+    const float v010 = __ldg(c + sy), v110 = __ldg(c + sy + 1);
+    const float v001 = __ldg(c + sz), v101 = __ldg(c + sz + 1);
+    const float v011 = __ldg(c + sz + sy), v111 = __ldg(c + sz + sy + 1);
+    const float a00 = ffma(fx, v100 - v000, v000), a10 = ffma(fx, v110 - v010, v010);
+    const float a01 = ffma(fx, v101 - v001, v001), a11 = ffma(fx, v111 - v011, v011);
+    const float b0 = ffma(fy, a10 - a00, a00), b1 = ffma(fy, a11 - a01, a01);
+    val = ffma(fz, b1 - b0, b0);
+    return true;
+}
+
+__device__ __forceinline__ float tf_coord(const GridD& g, float v, int& i) {
+    const float xt = fclamp(ffma(v, g.tf_scale, g.tf_bias), 0.0f, 255.0f);
+    i = min((int)xt, 254);
+    return xt - (float)i;
+}
+
+__device__ __forceinline__ int find_view(const ViewTable& vt, int tile) {
+    int vi = 0;
+    while (vi + 1 < vt.n && tile >= vt.s[vi + 1].tile_base) ++vi;
+    return vi;
+}
+
+__device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned n) {
+    unsigned long long v = n;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+__device__ __forceinline__ void store_moments(char* base, const ViewSlot& S, int64_t slab_off, int pix,
+                                              float m0, float m1, float m2, float m3, float m4) {
+    char* slab = base + slab_off;
+    reinterpret_cast<float*>(slab)[pix] = m0;
+    reinterpret_cast<float4*>(slab + (size_t)4 * S.plane)[pix] = make_float4(m1, m2, m3, m4);
+}
+
+__device__ __forceinline__ void load_moments(const char* base, const ViewSlot& S, int64_t slab_off, int pix,
+                                             float m[5]) {
+    const char* slab = base + slab_off;
+    m[0] = __ldg(reinterpret_cast<const float*>(slab) + pix);
+    const float4 q = __ldg(reinterpret_cast<const float4*>(slab + (size_t)4 * S.plane) + pix);
+    m[1] = q.x; m[2] = q.y; m[3] = q.z; m[4] = q.w;
+}
+
+__device__ __forceinline__ float4 resolve_pixel(float4 C, float m0, float4 bg, bool raw) {
+    if (raw) return C;
+    const float A = -expm1f(-m0);
+    const float T = 1.0f - A;
+    const float k = C.w > 0.0f ? A / C.w : 0.0f;
+    return make_float4(ffma(C.x, k, T * bg.x), ffma(C.y, k, T * bg.y), ffma(C.z, k, T * bg.z), A + T * bg.w);
+}
+
+__device__ __forceinline__ float trilinear8(float v000, float v100, float v010, float v110, float v001, float v101,
+                                            float v011, float v111, float fx, float fy, float fz) {
+    const float a00 = ffma(fx, v100 - v000, v000), a10 = ffma(fx, v110 - v010, v010);
+    const float a01 = ffma(fx, v101 - v001, v001), a11 = ffma(fx, v111 - v011, v011);
+    const float b0 = ffma(fy, a10 - a00, a00), b1 = ffma(fy, a11 - a01, a01);
+    return ffma(fz, b1 - b0, b0);
+}
+
+// Where a march puts every lattice point's value: nowhere, or a tile-cache
+// row (the lane's slot of row k; NaN for a point no selected piece owns).
+struct NoStore {
+    __device__ __forceinline__ void seek(int) {}
+    __device__ __forceinline__ void put(float) {}
+};
+struct RowStore {
+    float* base;  // slot of row 0: vals + (tile_base - kmin) * 32 + lane; NULL: off
+    float* at = nullptr;
+    __device__ __forceinline__ void seek(int k) { at = base + (int64_t)k * 32; }
+    __device__ __forceinline__ void put(float v) {
+        if (base) __stcs(at, v);  // streaming store: read once by pass 2, keep the field in L2
+        at += 32;
+    }
+};
+
+struct MomentBody {
+    const float2* s_sig;  // (sigma*step of entry i, of entry i+1 minus entry i)
+    float tf_scale, tf_bias, amax, wa, wb;
+    float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f;
+    unsigned n = 0;
+    __device__ __forceinline__ void operator()(float t, float val) {
+        // entry 255 has a zero delta, so xt = 255 needs no special index
+        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+        const int i = (int)xt;
+        const float f = xt - (float)i;
+        const float2 s = s_sig[i];
+        const float a = fmin_(ffma(f, s.y, s.x), amax);
+        const float z = warp_depth(t, wa, wb);
+        m0 += a;
+        m1 = ffma(a, z, m1);
+        const float az = a * z;
+        m2 = ffma(az, z, m2);
+        const float az2 = az * z;
+        m3 = ffma(az2, z, m3);
+        m4 = ffma(az2 * z, z, m4);
+        ++n;
+    }
+    __device__ __forceinline__ void store(const GridD&, char* base, const ViewSlot& S, int64_t off, int pix) {
+        store_moments(base, S, off, pix, m0, m1, m2, m3, m4);
+    }
+};
+
+// Alg. 1 loop 2 per sample: colour += T(z) * alpha * (r, g, b, 1).
+struct BlendBody {
+    const float4* s_tf;   // [2*i] = entry i (r, g, b, sigma*step), [2*i+1] = entry i+1 minus entry i
+    Frame F;
+    float tf_scale, tf_bias, amax, wa, wb, w0;
+    float b0;
+    float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    unsigned n = 0;
+    __device__ __forceinline__ void operator()(float t, float val) {
+        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+        const int i = (int)xt;
+        const float f = xt - (float)i;
+        const float4 e0 = s_tf[2 * i], de = s_tf[2 * i + 1];
+        const float a = fmin_(ffma(f, de.w, e0.w), amax);
+        const float alpha = one_minus_exp_neg(a);
+        const float z = warp_depth(t, wa, wb);
+        const float wgt = transmittance(F, z, w0) * alpha;
+        C.x = ffma(wgt, ffma(f, de.x, e0.x), C.x);
+        C.y = ffma(wgt, ffma(f, de.y, e0.y), C.y);
+        C.z = ffma(wgt, ffma(f, de.z, e0.z), C.z);
+        C.w += wgt;
+        ++n;
+    }
+    __device__ __forceinline__ bool singular() const { return F.kind == kFrameOneAtom || F.kind == kFrameTwoAtoms; }
+};
+
+// Bytes of one moment slab of P pixels in the volume's format.
+__device__ __forceinline__ int64_t slab_bytes(const GridD& g, int plane) {
+    return g.trig.n ? (int64_t)(4 + 4 * g.trig.n) * plane : (int64_t)20 * plane;
+}
+
+__device__ __forceinline__ uint32_t pack16(const GridD& g, float x, float y) {
+    if (g.trig.storage == 2) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+    const __half2 h = __floats2half2_rn(x, y);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__device__ __forceinline__ cf unpack16(const GridD& g, uint32_t bits) {
+    if (g.trig.storage == 2) {
+        const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&bits);
+        return {__low2float(h), __high2float(h)};
+    }
+    const __half2 h = *reinterpret_cast<const __half2*>(&bits);
+    return {__low2float(h), __high2float(h)};
+}
+
+// Trigonometric moment slab: b0 plane (float), then plane j of tau_j = t_j / b0
+// as a 16-bit pair.
+__device__ __forceinline__ void store_trig(const GridD& g, char* base, const ViewSlot& S, int64_t slab_off, int pix,
+                                           float m0, const cf* t, int n) {
+    char* slab = base + slab_off;
+    reinterpret_cast<float*>(slab)[pix] = m0;
+    const float inv = m0 > 0.0f ? 1.0f / m0 : 0.0f;
+    for (int j = 0; j < n; ++j)
+        reinterpret_cast<uint32_t*>(slab + (size_t)4 * S.plane * (1 + j))[pix] = pack16(g, t[j].x * inv, t[j].y * inv);
+}
+
+__device__ __forceinline__ float load_trig(const GridD& g, const char* base, const ViewSlot& S, int64_t slab_off,
+                                           int pix, cf* tau, int n) {
+    const char* slab = base + slab_off;
+    for (int j = 0; j < n; ++j)
+        tau[j] = unpack16(g, __ldg(reinterpret_cast<const uint32_t*>(slab + (size_t)4 * S.plane * (1 + j)) + pix));
+    return __ldg(reinterpret_cast<const float*>(slab) + pix);
+}
+
+// Pass 1 with trigonometric moments: b0 += a, t_j += a e^{i j phi}.
+template <int N>
+struct TrigMomentBody {
+    const float2* s_sig;
+    float tf_scale, tf_bias, amax, wa, wb, zs;
+    float m0 = 0.0f;
+    cf t[N];
+    unsigned n = 0;
+    __device__ __forceinline__ void operator()(float tt, float val) {
+        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+        const int i = (int)xt;
+        const float f = xt - (float)i;
+        const float2 s = s_sig[i];
+        const float a = fmin_(ffma(f, s.y, s.x), amax);
+        const float phi = warp_depth(tt, wa, wb) * zs;
+        float sn, cs;
+        __sincosf(phi, &sn, &cs);
+        const cf u = {cs, sn};
+        cf p = u;
+        m0 += a;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            if (j > 0) p = cmul(p, u);
+            t[j].x = ffma(a, p.x, t[j].x);
+            t[j].y = ffma(a, p.y, t[j].y);
+        }
+        ++n;
+    }
+    __device__ __forceinline__ void store(const GridD& g, char* base, const ViewSlot& S, int64_t off, int pix) {
+        store_trig(g, base, S, off, pix, m0, t, N);
+    }
+};
+
+// Pass 2 with trigonometric moments.
+template <int N>
+struct TrigBlendBody {
+    const float4* s_tf;
+    const TrigTables* T;
+    TrigFrame F;
+    float tf_scale, tf_bias, amax, wa, wb, w0;
+    float b0;
+    float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    unsigned n = 0;
+    __device__ __forceinline__ void operator()(float t, float val) {
+        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+        const int i = (int)xt;
+        const float f = xt - (float)i;
+        const float4 e0 = s_tf[2 * i], de = s_tf[2 * i + 1];
+        const float a = fmin_(ffma(f, de.w, e0.w), amax);
+        const float alpha = one_minus_exp_neg(a);
+        const float z = warp_depth(t, wa, wb);
+        const float A = trig_fraction<N>(F, *T, z, w0);
+        const float wgt = fclamp(fexp2(-F.m0_log2e * A), 0.0f, 1.0f) * alpha;
+        C.x = ffma(wgt, ffma(f, de.x, e0.x), C.x);
+        C.y = ffma(wgt, ffma(f, de.y, e0.y), C.y);
+        C.z = ffma(wgt, ffma(f, de.z, e0.z), C.z);
+        C.w += wgt;
+        ++n;
+    }
+    __device__ __forceinline__ bool singular() const { return b0 > 0.0f && F.n == 0; }
+};
+
+template <int MS> struct Bodies;
+template <> struct Bodies<0> {
+    using Moment = MomentBody;
+    using Blend = BlendBody;
+};
+template <> struct Bodies<3> {
+    using Moment = TrigMomentBody<3>;
+    using Blend = TrigBlendBody<3>;
+};
+template <> struct Bodies<4> {
+    using Moment = TrigMomentBody<4>;
+    using Blend = TrigBlendBody<4>;
+};
+
+template <int MS>
+__device__ __forceinline__ typename Bodies<MS>::Moment make_moment_body(const float2* s_sig, const GridD& g,
+                                                                        const ViewD& v) {
+    typename Bodies<MS>::Moment b;
+    b.s_sig = s_sig;
+    b.tf_scale = g.tf_scale;
+    b.tf_bias = g.tf_bias;
+    b.amax = g.absorbance_max;
+    b.wa = v.warp_a;
+    b.wb = v.warp_b;
+    if constexpr (MS != 0) {
+        b.zs = g.trig.zone_scale;
+        for (int j = 0; j < MS; ++j) b.t[j] = {0.0f, 0.0f};
+    }
+    return b;
+}
+
+// Loads the pixel's global moments (if `valid`) and builds the reconstruction.
+template <int MS>
+__device__ __forceinline__ typename Bodies<MS>::Blend make_blend_body(const float4* s_tf, const GridD& g, const ViewSlot& S,
+                                                                      const char* moments, int64_t off, int pix,
+                                                                      bool valid) {
+    typename Bodies<MS>::Blend b;
+    b.s_tf = s_tf;
+    b.tf_scale = g.tf_scale;
+    b.tf_bias = g.tf_bias;
+    b.amax = g.absorbance_max;
+    b.wa = S.v.warp_a;
+    b.wb = S.v.warp_b;
+    b.w0 = g.overestimation;
+    if constexpr (MS == 0) {
+        float m[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (valid) load_moments(moments, S, off, pix, m);
+        b.F = make_frame(m, g.moment_bias, g.bias_vector);
+        b.b0 = m[0];
+    } else {
+        cf tau[MS];
+        for (int j = 0; j < MS; ++j) tau[j] = {0.0f, 0.0f};
+        b.b0 = valid ? load_trig(g, moments, S, off, pix, tau, MS) : 0.0f;
+        b.T = &g.trig;
+        b.F = make_trig_frame(b.b0, tau, MS, g.trig.beta);
+    }
+    return b;
+}
+
+
+// Pops the next 8x4 ray tile of the work queue; returns false when empty.
+__device__ __forceinline__ bool next_tile(const ViewTable& vt, int32_t* head, int& vi, int& px, int& py, int& tile) {
+    const int lane = threadIdx.x & 31;
+    tile = 0;
+    if (lane == 0) tile = atomicAdd(head, 1);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= vt.total_tiles) return false;
+    vi = find_view(vt, tile);
+    const ViewSlot& S = vt.s[vi];
+    const int lt = tile - S.tile_base;
+    px = (lt % S.ntx) * kTileW + (lane & 7);
+    py = (lt / S.ntx) * kTileH + (lane >> 3);
+    return true;
+}
+
+__device__ __forceinline__ bool inside_domain(const GridD& g, const float o[3], const float d[3], int k) {
+    const float t = lattice_t(k, g.step);
+    const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
+    return p0 >= 0.0f && p0 < g.hx && p1 >= 0.0f && p1 < g.hy && p2 >= 0.0f && p2 < g.hz;
+}
+
+// Ray of pixel (px, py) and the exact interval [k0, k1] of lattice indices
+// whose float32 positions lie inside the domain (k0 > k1 if none).  Each
+// coordinate of fma(t, d, o) is monotone in t, so the inside set of a box is
+// one interval: it is found by shrinking the conservative range.
+__device__ __forceinline__ void ray_range(const GridD& g, const ViewD& V, bool valid, int px, int py, float o[3],
+                                          float d[3], int& k0, int& k1) {
+    k0 = 0x7fffffff;
+    k1 = -1;
+    o[0] = o[1] = o[2] = 0.0f;
+    d[0] = d[1] = d[2] = 0.0f;
+    if (!valid) return;
+    make_ray(V, px, py, o, d);
+    const float lo[3] = {0.0f, 0.0f, 0.0f};
+    const float hi[3] = {g.hx, g.hy, g.hz};
+    int a, b;
+    if (!lattice_range(o, d, lo, hi, g.step, &a, &b)) return;
+    while (a <= b && !inside_domain(g, o, d, a)) ++a;
+    while (b >= a && !inside_domain(g, o, d, b)) --b;
+    if (a <= b) {
+        k0 = a;
+        k1 = b;
+    }
+}
+
+// Asynchronous 16-byte global -> shared copies (no register staging).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kRowChunk = 8;                    // cache rows per prefetch
+constexpr int kRowBuf = 2 * kRowChunk * 32;     // floats of a warp's double buffer
+
+// Pass 2 of the batched frame from the tile cache.  The tile's rows are
+// contiguous (rows[r * 32 + lane], r = k - kmin), so the warp copies them
+// into its shared-memory buffer 8 rows (1 KiB) at a time, one chunk ahead of
+// the one it blends, and every lane takes its own column over its own
+// [k0, k1].  buf: 16-byte aligned, kRowBuf floats, this warp's only.
+template <bool kSel, class Body>
+__device__ __forceinline__ void march_rows(const GridD& g, const float* __restrict__ rows, int kmin, int kmax, int k0,
+                                           int k1, float* __restrict__ buf, Body& body) {
+    if (kmin > kmax) return;
+    const int lane = threadIdx.x & 31;
+    const int nrows = kmax - kmin + 1;
+    const int nchunks = (nrows + kRowChunk - 1) / kRowChunk;
+    auto fetch = [&](int c) {
+        float* dst = buf + (c & 1) * kRowChunk * 32;
+#pragma unroll
+        for (int h = 0; h < kRowChunk / 4; ++h) {       // 16-byte pieces: 8 per row
+            const int piece = lane + 32 * h, r = piece >> 3, q = (piece & 7) * 4;
+            if (c * kRowChunk + r < nrows)
+                cp_async16(dst + r * 32 + q, rows + (int64_t)(c * kRowChunk + r) * 32 + q);
+        }
+        cp_async_commit();
+    };
+    fetch(0);
+    float t = lattice_t(kmin, g.step);
+    for (int c = 0; c < nchunks; ++c) {
+        if (c + 1 < nchunks) {
+            fetch(c + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
+        const float* src = buf + (c & 1) * kRowChunk * 32 + lane;
+        const int kc = kmin + c * kRowChunk;
+        const int n = min(kRowChunk, kmax - kc + 1);
+        for (int i = 0; i < n; ++i, t += g.step) {
+            const int k = kc + i;
+            if (k < k0 || k > k1) continue;
+            const float val = src[i * 32];
+            if (!kSel || val == val) body(t, val);  // every in-domain point is owned when no piece is left out
+        }
+        __syncwarp();  // every lane is done with the chunk before it is refilled
+    }
+}
+
+// Pass 1: the tile's rows of the cache (lane 0 takes them, all lanes get the
+// base; a tile that does not fit gets -1 and is marched again in pass 2).
+__device__ __forceinline__ float* tile_rows(const TileCache& c, Counters* ctr, int tile, int k0, int k1) {
+    const unsigned full = 0xffffffffu;
+    const int kmin = __reduce_min_sync(full, k0), kmax = __reduce_max_sync(full, k1);
+    long long base = -1;
+    if ((threadIdx.x & 31) == 0) {
+        if (kmax >= kmin) {
+            const long long rows = (long long)kmax - kmin + 1;
+            const long long r = (long long)atomicAdd(&ctr->cache_rows, (unsigned long long)rows);
+            if (r + rows <= c.rows_cap) base = r;
+        }
+        c.tile_base[tile] = base;
+    }
+    base = __shfl_sync(full, base, 0);
+    return base >= 0 ? c.vals + (base - kmin) * 32 + (threadIdx.x & 31) : nullptr;
+}
+
+
+}  // namespace
+}  // namespace mb

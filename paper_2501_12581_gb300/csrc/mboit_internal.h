@@ -1,5 +1,6 @@
 // Internal launch interface between the C ABI (mboit_api.cu) and the
-// kernels (mboit_kernels.cu).  Not part of the public ABI.
+// kernels (mboit_grid.cu, mboit_units.cu, mboit_kernels.cu).  Not part of
+// the public ABI.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
