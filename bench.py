@@ -36,15 +36,29 @@ UNIT = "Gsamples/s"
 # (position 6, trilinear 21, table coordinate 2, extinction lerp 3, warp 2,
 # moment update 9 for pass 1; pass 2 replaces the moment update by opacity 2,
 # colour lerps 9, moment-bound reconstruction 20 (outside case) and the
-# colour accumulation 9).  FMA = 2 FLOPs.
+# colour accumulation 9).  FMA = 2 FLOPs.  In the batched frame pass 2 reads
+# the values pass 1 stored, so it skips the position and the trilinear
+# interpolation; pass 1 stores 4 bytes per lattice point, pass 2 reads them.
 FLOP_PASS1 = 43
 FLOP_PASS2 = 76
+FLOP_PASS2_FRAME = FLOP_PASS2 - 6 - 21
+CACHE_BYTES_PER_SAMPLE = 4
 # FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x
 # 2 FLOP x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 KERNEL_SOURCES = ["paper_2501_12581_gb300/csrc/mboit_grid.cu", "paper_2501_12581_gb300/csrc/mboit_common.cuh",
                   "paper_2501_12581_gb300/csrc/mboit_device.cuh", "paper_2501_12581_gb300/csrc/mboit_trig.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pass2_fused_blobs512_traffic.txt")
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+MEASURED = _measured_peaks()
 
 
 def kernel_hash():
@@ -54,12 +68,12 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
-    """DRAM bytes per pass-2 launch from the committed ncu summary, or None
-    when the kernel sources changed since it was captured."""
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when it covers another kernel or the sources changed since."""
     try:
         kv = dict(tok.split("=", 1) for tok in open(TRAFFIC_FILE).read().split() if "=" in tok)
-        if kv.get("kernel_sha") == kernel_hash():
+        if kv.get("kernel") == kernel and kv.get("kernel_sha") == kernel_hash():
             return int(kv["dram_bytes_per_launch"])
     except (OSError, ValueError, KeyError):
         pass
@@ -274,7 +288,16 @@ def main():
     ms_max = max_over_ranks(ms)
     value = samples * world / (ms_max * 1e-3) / 1e9
 
-    # the two kernels of the frame, each timed alone on the launching stream
+    # the two kernels of the frame: CUDA events recorded inside its graph, on
+    # the launching stream, averaged over a few frames
+    p1 = p2 = 0.0
+    nf = max(5, args.steps // 2)
+    for _ in range(nf):
+        frame()
+        stf = vol.stats()
+        p1 += stf["frame_pass1_ms"] / nf
+        p2 += stf["frame_pass2_ms"] / nf
+    # the same passes as separate calls (pass 2 marches the field again)
     for _ in range(3):
         vol.render_moments(views, mom)
         vol.reconstruct_blend(views, mom, rgba, mode=pkg.MBOIT_COLOR_RESOLVED)
@@ -282,14 +305,29 @@ def main():
     ms_p1 = timed(lambda: vol.render_moments(views, mom), k)
     ms_p2 = timed(lambda: vol.reconstruct_blend(views, mom, rgba, mode=pkg.MBOIT_COLOR_RESOLVED), k)
     vol.synchronize()
-    achieved = FLOP_PASS2 * samples / (ms_p2 * 1e-3) / 1e12
-    traffic = measured_traffic()
-    roofline = {"bound": "alu", "kernel": "k_pass2_fused (pass 2: reconstruct + blend + resolve)",
-                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": traffic, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "flop_per_sample": FLOP_PASS2, "launch_ms": ms_p2,
-                "pass1": {"launch_ms": ms_p1, "flop_per_sample": FLOP_PASS1,
-                          "achieved_tflops": FLOP_PASS1 * samples / (ms_p1 * 1e-3) / 1e12}}
+    frame()
+    vol.synchronize()
+    hbm = MEASURED.get("hbm_gbs")
+
+    def kstats(ms_k, flop, cache_bytes):
+        d = {"launch_ms": ms_k, "flop_per_sample": flop, "achieved_tflops": flop * samples / (ms_k * 1e-3) / 1e12,
+             "cache_bytes_per_sample": cache_bytes, "cache_gbs": cache_bytes * samples / (ms_k * 1e-3) / 1e9}
+        d["alu_frac"] = d["achieved_tflops"] / FP32_PEAK_TFLOPS
+        if hbm:
+            d["hbm_frac_of_measured"] = d["cache_gbs"] / hbm
+        return d
+    k1s = kstats(p1, FLOP_PASS1, CACHE_BYTES_PER_SAMPLE)
+    k2s = kstats(p2, FLOP_PASS2_FRAME, CACHE_BYTES_PER_SAMPLE)
+    dom, dname, dflop = (k2s, "k_pass2_fused, frame form (reads the cached samples; reconstruct + blend + resolve)",
+                         FLOP_PASS2_FRAME) if p2 >= p1 else \
+        (k1s, "k_pass1_fused, frame form (march + moments + sample store)", FLOP_PASS1)
+    traffic = measured_traffic("k_pass2_fused_frame" if p2 >= p1 else "k_pass1_fused_frame")
+    roofline = {"bound": "alu", "kernel": dname, "achieved": dom["achieved_tflops"], "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": dom["achieved_tflops"] / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "flop_per_sample": dflop,
+                "launch_ms": dom["launch_ms"], "frame_pass1": k1s, "frame_pass2": k2s,
+                "split_calls": {"pass1_ms": ms_p1, "pass2_ms": ms_p2, "pass2_flop_per_sample": FLOP_PASS2,
+                                "pass2_achieved_tflops": FLOP_PASS2 * samples / (ms_p2 * 1e-3) / 1e12}}
 
     # the plain per-piece FP32 form (one launch per piece and pass, K images summed)
     per_piece = None

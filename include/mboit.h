@@ -185,6 +185,9 @@ typedef struct {
     int64_t sortlast_segments;  /* segments of the last mboit_render_sortlast */
     int32_t sortlast_max_segments; /* most segments on one pixel in it */
     int32_t reserved;
+    float frame_pass1_ms;       /* device time of pass 1 in the last mboit_render_frame (CUDA events
+                                 * recorded in its graph); -1 before the first frame */
+    float frame_pass2_ms;       /* the same for pass 2 */
 } mboit_stats;
 
 /* Number of window configurations of the fused passes.  Each fused kernel
@@ -253,7 +256,13 @@ MBOIT_API mboit_status mboit_composite(mboit_volume v, int32_t op, int32_t width
  * and all views, recorded once into a CUDA graph per (views, stream kind)
  * and replayed.  moments_scratch: DEVICE buffer of n_views moment slabs
  * (kept, so the caller can inspect the global moments); rgba: DEVICE
- * float32 RGBA n_views images. */
+ * float32 RGBA n_views images.  Pass 1 also stores every lattice point's
+ * sample value in a library-owned cache (4 bytes per lattice point inside
+ * the domain, sized exactly when a graph is recorded, e.g. 6.4 GB for 1.6 G
+ * points) and pass 2 reads it instead of sampling the volume again (the
+ * same values: images are bit-identical to the separate pass calls).  If
+ * the device lacks that memory with 1 GiB to spare, pass 2 samples again.
+ * The first call for a set of views synchronises once to size the cache. */
 MBOIT_API mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch,
                                 float* rgba, void* stream);
 

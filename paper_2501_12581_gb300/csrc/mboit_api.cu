@@ -89,6 +89,8 @@ struct mboit_volume_s {
     std::vector<uint8_t> sel_host;
     bool sel_uploaded = false;
     cudaStream_t cap_stream = nullptr;
+    cudaEvent_t frame_ev[3] = {nullptr, nullptr, nullptr};  // recorded around the passes of every frame graph
+    bool frame_timed = false;
     std::vector<GraphEntry> graphs;
     int32_t tune1 = 0, tune2 = 0;
     // sort-last baseline buffers (grow only)
@@ -701,6 +703,7 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
         m.max_walk = 64;
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&v->cap_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&v->frame_ev[i]);
     if (e == cudaSuccess) e = mb::prepare_kernels();
     if (e != cudaSuccess) {
         const mboit_status s = (e == cudaErrorMemoryAllocation) ? MBOIT_ERR_OUT_OF_MEMORY : MBOIT_ERR_CUDA;
@@ -721,6 +724,8 @@ mboit_status mboit_destroy_volume(mboit_volume v) {
         cudaDeviceSynchronize();
         drop_graphs(v);
         if (v->cap_stream) cudaStreamDestroy(v->cap_stream);
+        for (cudaEvent_t ev : v->frame_ev)
+            if (ev) cudaEventDestroy(ev);
         cudaFree(v->d_tf);
         cudaFree(v->d_leaves);
         cudaFree(v->d_fmap);
@@ -969,8 +974,12 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
         cudaStream_t cs = v->cap_stream;
         MB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemsetAsync(&v->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), cs);
+        // external record nodes: the events are recorded each time the graph runs
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(v->frame_ev[0], cs, cudaEventRecordExternal);
         if (e == cudaSuccess) e = pass1_batched(v, mask, vt, moments_scratch, cs, tc);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(v->frame_ev[1], cs, cudaEventRecordExternal);
         if (e == cudaSuccess) e = pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved, cs, tc);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(v->frame_ev[2], cs, cudaEventRecordExternal);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -985,6 +994,7 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
         v->graphs.push_back(GraphEntry{key, exec});
     }
     MB_CUDA(cudaGraphLaunch(exec, static_cast<cudaStream_t>(stream)));
+    v->frame_timed = true;
     return MBOIT_OK;
 }
 
@@ -1047,6 +1057,12 @@ mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out) {
     out->sortlast_segments = v->sl_segments;
     out->sortlast_max_segments = c.max_segments;
     out->reserved = 0;
+    out->frame_pass1_ms = out->frame_pass2_ms = -1.0f;
+    if (v->frame_timed && (cudaEventElapsedTime(&out->frame_pass1_ms, v->frame_ev[0], v->frame_ev[1]) != cudaSuccess ||
+                           cudaEventElapsedTime(&out->frame_pass2_ms, v->frame_ev[1], v->frame_ev[2]) != cudaSuccess)) {
+        cudaGetLastError();
+        out->frame_pass1_ms = out->frame_pass2_ms = -1.0f;
+    }
     return MBOIT_OK;
 }
 

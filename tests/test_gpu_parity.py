@@ -130,6 +130,10 @@ def test_frame_sample_cache_equals_split_calls(pkg, blobs):
         assert torch.equal(m1, m2) and torch.equal(c1, c2)
         st = vol.stats()
         assert st["samples_pass1"] == st["samples_pass2"]
+    m3, c3 = pkg.Volume.moment_buffer(sc.views), pkg.Volume.color_buffer(sc.views)
+    vol.render_frame(sc.views, m3, c3)
+    st = vol.stats()
+    assert st["frame_pass1_ms"] > 0 and st["frame_pass2_ms"] > 0
 
 
 def test_per_piece_path_and_composites(pkg, blobs):
