@@ -443,11 +443,17 @@ __device__ __forceinline__ void march_rows(const GridD& g, const float* __restri
         const float* src = buf + (c & 1) * kRowChunk * 32 + lane;
         const int kc = kmin + c * kRowChunk;
         const int n = min(kRowChunk, kmax - kc + 1);
-        for (int i = 0; i < n; ++i, t += g.step) {
-            const int k = kc + i;
-            if (k < k0 || k > k1) continue;
-            const float val = src[i * 32];
-            if (!kSel || val == val) body(t, val);  // every in-domain point is owned when no piece is left out
+        if (!kSel && kc >= k0 && kc + kRowChunk - 1 <= k1) {
+            // the whole chunk lies in this lane's interval: every point is owned
+#pragma unroll
+            for (int i = 0; i < kRowChunk; ++i, t += g.step) body(t, src[i * 32]);
+        } else {
+            for (int i = 0; i < n; ++i, t += g.step) {
+                const int k = kc + i;
+                if (k < k0 || k > k1) continue;
+                const float val = src[i * 32];
+                if (!kSel || val == val) body(t, val);  // every in-domain point is owned when no piece is left out
+            }
         }
         __syncwarp();  // every lane is done with the chunk before it is refilled
     }
