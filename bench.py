@@ -48,7 +48,7 @@ CACHE_BYTES_PER_SAMPLE = 4
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 KERNEL_SOURCES = ["paper_2501_12581_gb300/csrc/mboit_grid.cu", "paper_2501_12581_gb300/csrc/mboit_common.cuh",
                   "paper_2501_12581_gb300/csrc/mboit_device.cuh", "paper_2501_12581_gb300/csrc/mboit_trig.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pass2_fused_blobs512_traffic.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "frame_fused_blobs512_traffic.txt")
 
 
 def _measured_peaks():
@@ -211,6 +211,25 @@ def run_reference(args, rank):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def pin_to_gpu_cpus(device):
+    """Runs this process on the host cores next to the GPU (its PCI device's
+    local CPU list), so that pinned host buffers land in the nearby memory;
+    best effort, a no-op where the topology is not exposed."""
+    try:
+        bus = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader", "-i", str(device)],
+                             capture_output=True, text=True, timeout=20).stdout.strip().lower()
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{dom[-4:]}:{rest}/local_cpulist"
+        cpus = set()
+        for part in open(path).read().strip().split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+    except (OSError, ValueError, subprocess.SubprocessError):
+        pass
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -240,6 +259,7 @@ def main():
     import paper_2501_12581_gb300 as pkg
 
     torch.cuda.set_device(local)
+    pin_to_gpu_cpus(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     __graft_entry__.build()
@@ -328,6 +348,20 @@ def main():
                 "launch_ms": dom["launch_ms"], "frame_pass1": k1s, "frame_pass2": k2s,
                 "split_calls": {"pass1_ms": ms_p1, "pass2_ms": ms_p2, "pass2_flop_per_sample": FLOP_PASS2,
                                 "pass2_achieved_tflops": FLOP_PASS2 * samples / (ms_p2 * 1e-3) / 1e12}}
+
+    # end to end through the host API: field upload, frame, image download
+    field_host = torch.from_numpy(np.ascontiguousarray(sc.values if hasattr(sc, "leaves") else sc.field)).pin_memory()
+    rgba_host = torch.empty(rgba.numel(), dtype=torch.float32).pin_memory()
+    e2e_step = lambda: pkg.mboit_render_frame_host(vol.handle, field_host, views, mom, rgba, rgba_host)  # noqa: E731
+    e2e_step()
+    t0 = time.perf_counter()
+    barrier()
+    for _ in range(max(3, args.steps // 3)):
+        e2e_step()
+    barrier()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / max(3, args.steps // 3))
+    e2e = {"value": samples * world / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": int(field_host.numel() * 4), "d2h_bytes_per_step": int(rgba_host.numel() * 4)}
 
     # the plain per-piece FP32 form (one launch per piece and pass, K images summed)
     per_piece = None
@@ -469,19 +503,6 @@ def main():
             del svol, smom, srgba
             torch.cuda.empty_cache()
 
-    # end to end through the host API: field upload, frame, image download
-    field_host = torch.from_numpy(np.ascontiguousarray(sc.values if hasattr(sc, "leaves") else sc.field)).pin_memory()
-    rgba_host = torch.empty(rgba.numel(), dtype=torch.float32).pin_memory()
-    e2e_step = lambda: pkg.mboit_render_frame_host(vol.handle, field_host, views, mom, rgba, rgba_host)  # noqa: E731
-    e2e_step()
-    t0 = time.perf_counter()
-    barrier()
-    for _ in range(max(3, args.steps // 3)):
-        e2e_step()
-    barrier()
-    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / max(3, args.steps // 3))
-    e2e = {"value": samples * world / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
-           "h2d_bytes_per_step": int(field_host.numel() * 4), "d2h_bytes_per_step": int(rgba_host.numel() * 4)}
 
     # parity on a pixel sample and the oracle's own speed (rank 0, one GPU)
     cpu_baseline, quality = None, None
