@@ -528,7 +528,7 @@ def main():
            "config": dict(config_of(sc, args.workload), parallelism="replicas" if world > 1 else "single",
                           form="batched: 2 persistent kernels per frame, CUDA graph",
                           tuning={"pass1": tuning[0], "pass2": tuning[1]}),
-           "samples_per_frame": samples, "ms_per_frame": ms_max, "per_piece_fp32": per_piece,
+           "samples_per_frame": samples, "ms_per_frame": ms_max, "singular_pixels": st["singular_pixels"], "per_piece_fp32": per_piece,
            "sortlast_gpu": sortlast, "amr_72_pieces": amr, "tets_72_pieces": tets,
            "precision_sweep_amr_2048": sweep,
            "quality": quality, "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,

@@ -443,10 +443,14 @@ __device__ __forceinline__ void march_rows(const GridD& g, const float* __restri
         const float* src = buf + (c & 1) * kRowChunk * 32 + lane;
         const int kc = kmin + c * kRowChunk;
         const int n = min(kRowChunk, kmax - kc + 1);
-        if (!kSel && kc >= k0 && kc + kRowChunk - 1 <= k1) {
-            // the whole chunk lies in this lane's interval: every point is owned
+        if (kc >= k0 && kc + kRowChunk - 1 <= k1) {
+            // the whole chunk lies in this lane's interval (and, without a
+            // selection, every point of it is owned)
 #pragma unroll
-            for (int i = 0; i < kRowChunk; ++i, t += g.step) body(t, src[i * 32]);
+            for (int i = 0; i < kRowChunk; ++i, t += g.step) {
+                const float val = src[i * 32];
+                if (!kSel || val == val) body(t, val);
+            }
         } else {
             for (int i = 0; i < n; ++i, t += g.step) {
                 const int k = kc + i;

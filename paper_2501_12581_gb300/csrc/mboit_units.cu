@@ -471,15 +471,16 @@ __device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restr
 }
 
 // Resident 256-thread blocks per SM the unit kernels are compiled for (the
-// mesh walk is latency-bound: more warps hide more of it).
+// walks and gathers are latency-bound: more warps hide more of it); the
+// trigonometric bodies get 2, so that they keep their registers.
 #ifndef MB_TET_MIN_BLOCKS
 #define MB_TET_MIN_BLOCKS 3
 #endif
-template <class V> struct MinBlocks { static constexpr int value = 1; };
-template <bool k> struct MinBlocks<TetT<k>> { static constexpr int value = MB_TET_MIN_BLOCKS; };
+template <class V, int kPass> struct MinBlocks { static constexpr int value = kPass == 2 ? 4 : 1; };
+template <bool k, int kPass> struct MinBlocks<TetT<k>, kPass> { static constexpr int value = MB_TET_MIN_BLOCKS; };
 
 template <class V, bool kSel, int MS, bool kCache = false>
-__global__ void __launch_bounds__(256, MinBlocks<V>::value) k_pass1_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
+__global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 1>::value : 2) k_pass1_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
                                                     const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                     char* __restrict__ moments, Counters* __restrict__ ctr,
                                                     const TileCache cache) {
@@ -510,7 +511,7 @@ __global__ void __launch_bounds__(256, MinBlocks<V>::value) k_pass1_unit(const _
 }
 
 template <class V, bool kSel, int MS, bool kCache = false>
-__global__ void __launch_bounds__(256, MinBlocks<V>::value) k_pass2_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
+__global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 2>::value : 2) k_pass2_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
                                                     const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                     const char* __restrict__ moments, float* __restrict__ color, int mode,
                                                     Counters* __restrict__ ctr, const TileCache cache) {
