@@ -144,7 +144,7 @@ def sample_pixels(width, height, row_stride, col_stride):
 def time_oracle(sc, pixels):
     import oracle
     t0 = time.perf_counter()
-    r = oracle.render_grid(sc, pixels=pixels, want=("mboit", "exact", "nsamples"))
+    r = oracle.render(sc, pixels=pixels, want=("mboit", "exact", "nsamples"))
     dt = time.perf_counter() - t0
     return r, dt
 
@@ -236,7 +236,8 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="blobs512", choices=["blobs512", "blobs64", "amr"])
+    ap.add_argument("--workload", default="blobs512", choices=["blobs512", "blobs64", "amr", "tets"])
+    ap.add_argument("--image", type=int, default=0, help="square image size for the main workload (profiling)")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-tets", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
@@ -276,6 +277,10 @@ def main():
         return float(t.item())
 
     sc = workload(args.workload)
+    if args.image:
+        for vw in sc.views:
+            assert vw.width == vw.height, "--image rescales square views only"
+            vw.width = vw.height = args.image
     vol = pkg.Volume(sc)
     views = sc.views
     v = views[0]
@@ -338,9 +343,10 @@ def main():
         return d
     k1s = kstats(p1, FLOP_PASS1, CACHE_BYTES_PER_SAMPLE)
     k2s = kstats(p2, FLOP_PASS2_FRAME, CACHE_BYTES_PER_SAMPLE)
-    dom, dname, dflop = (k2s, "k_pass2_fused, frame form (reads the cached samples; reconstruct + blend + resolve)",
+    kname = "k_pass{}_fused" if not (hasattr(sc, "leaves") or hasattr(sc, "tets")) else "k_pass{}_unit"
+    dom, dname, dflop = (k2s, kname.format(2) + ", frame form (reads the cached samples; reconstruct + blend + resolve)",
                          FLOP_PASS2_FRAME) if p2 >= p1 else \
-        (k1s, "k_pass1_fused, frame form (march + moments + sample store)", FLOP_PASS1)
+        (k1s, kname.format(1) + ", frame form (march + moments + sample store)", FLOP_PASS1)
     traffic = measured_traffic("k_pass2_fused_frame" if p2 >= p1 else "k_pass1_fused_frame")
     roofline = {"bound": "alu", "kernel": dname, "achieved": dom["achieved_tflops"], "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": dom["achieved_tflops"] / FP32_PEAK_TFLOPS, "traffic": traffic,
@@ -350,7 +356,8 @@ def main():
                                 "pass2_achieved_tflops": FLOP_PASS2 * samples / (ms_p2 * 1e-3) / 1e12}}
 
     # end to end through the host API: field upload, frame, image download
-    field_host = torch.from_numpy(np.ascontiguousarray(sc.values if hasattr(sc, "leaves") else sc.field)).pin_memory()
+    host_values = sc.values if hasattr(sc, "leaves") else sc.verts[:, 3] if hasattr(sc, "tets") else sc.field
+    field_host = torch.from_numpy(np.ascontiguousarray(host_values, dtype=np.float32)).pin_memory()
     rgba_host = torch.empty(rgba.numel(), dtype=torch.float32).pin_memory()
     e2e_step = lambda: pkg.mboit_render_frame_host(vol.handle, field_host, views, mom, rgba, rgba_host)  # noqa: E731
     e2e_step()

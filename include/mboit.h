@@ -261,7 +261,9 @@ MBOIT_API mboit_status mboit_composite(mboit_volume v, int32_t op, int32_t width
  * the domain, sized exactly when a graph is recorded, e.g. 6.4 GB for 1.6 G
  * points) and pass 2 reads it instead of sampling the volume again (the
  * same values: images are bit-identical to the separate pass calls).  If
- * the device lacks that memory with 1 GiB to spare, pass 2 samples again.
+ * the device lacks that memory with 1 GiB to spare, pass 2 samples again
+ * (so does every ray tile past the row count in the environment variable
+ * MBOIT_FRAME_CACHE_ROWS, read when a graph is recorded, if it is set).
  * The first call for a set of views synchronises once to size the cache. */
 MBOIT_API mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch,
                                 float* rgba, void* stream);

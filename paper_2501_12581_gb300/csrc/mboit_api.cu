@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -473,6 +474,9 @@ mboit_status tile_cache(mboit_volume v, const mb::ViewTable& vt, mb::TileCache& 
     c.vals = v->d_tcvals;
     c.tile_base = v->d_tile_base;
     c.rows_cap = (long long)(v->cap_tcvals / 32);
+    // MBOIT_FRAME_CACHE_ROWS caps the rows handed out (0: every tile marches
+    // again in pass 2), to exercise and measure the fallback
+    if (const char* cap = std::getenv("MBOIT_FRAME_CACHE_ROWS")) c.rows_cap = std::min(c.rows_cap, std::atoll(cap));
     return MBOIT_OK;
 }
 

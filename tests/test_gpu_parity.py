@@ -136,6 +136,32 @@ def test_frame_sample_cache_equals_split_calls(pkg, blobs):
     assert st["frame_pass1_ms"] > 0 and st["frame_pass2_ms"] > 0
 
 
+def test_frame_cache_fallback_marches_again(pkg, monkeypatch):
+    """Tiles that get no cache rows march the field again in pass 2: with the
+    rows capped (none, or a few thousand) the frame's bits do not change."""
+    import torch
+    sc = scenes.blobs64(width=96, height=80)
+    views = sc.views
+    want = None
+    for cap in (None, "0", "3000"):
+        if cap is None:
+            monkeypatch.delenv("MBOIT_FRAME_CACHE_ROWS", raising=False)
+        else:
+            monkeypatch.setenv("MBOIT_FRAME_CACHE_ROWS", cap)
+        vol = pkg.Volume(sc)   # a new volume records a new frame graph
+        m, c = pkg.Volume.moment_buffer(views), pkg.Volume.color_buffer(views)
+        vol.render_frame(views, m, c)
+        vol.synchronize()
+        sync()
+        if want is None:
+            want = (m.clone(), c.clone())
+        else:
+            assert torch.equal(m, want[0]) and torch.equal(c, want[1])
+        st = vol.stats()
+        assert st["samples_pass1"] == st["samples_pass2"] > 0
+        vol.close()
+
+
 def test_per_piece_path_and_composites(pkg, blobs):
     sc, ref, vol = blobs
     views = sc.views
