@@ -211,6 +211,24 @@ def run_reference(args, rank):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def reduce_max(x, world, device):
+    """The largest x over the ranks of the default process group (x itself
+    for one rank): the whole-job time is the slowest replica's."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(samples_per_replica, world, ms_max):
+    """Whole-job throughput of `world` replicas that each render the frame:
+    every replica's samples over the slowest replica's frame time (Gsamples/s)."""
+    return samples_per_replica * world / (ms_max * 1e-3) / 1e9
+
+
 def pin_to_gpu_cpus(device):
     """Runs this process on the host cores next to the GPU (its PCI device's
     local CPU list), so that pinned host buffers land in the nearby memory;
@@ -270,11 +288,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, "cuda")
 
     sc = workload(args.workload)
     if args.image:
@@ -311,7 +325,7 @@ def main():
     st = vol.stats()
     samples = st["samples_pass1"]
     ms_max = max_over_ranks(ms)
-    value = samples * world / (ms_max * 1e-3) / 1e9
+    value = job_rate(samples, world, ms_max)
 
     # the two kernels of the frame: CUDA events recorded inside its graph, on
     # the launching stream, averaged over a few frames
