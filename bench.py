@@ -430,6 +430,7 @@ def main():
         uvol = pkg.Volume(usc)
         uv = usc.views
         umom, urgba = pkg.Volume.moment_buffer(uv), pkg.Volume.color_buffer(uv)
+        utune = uvol.autotune(uv, umom, urgba)   # the ray packet (one window configuration here)
         uframe = lambda: uvol.render_frame(uv, umom, urgba)  # noqa: E731
         for _ in range(3):
             uframe()
@@ -465,7 +466,8 @@ def main():
             torch.cuda.empty_cache()
         uframe()
         uvol.synchronize()
-        out_u = {"config": config_of(usc, name), "samples_per_frame": su, "ms_per_frame": ms_u,
+        out_u = {"config": dict(config_of(usc, name), packet="4x8" if utune[2] == pkg.MBOIT_PACKET_4X8 else "8x4"),
+                 "samples_per_frame": su, "ms_per_frame": ms_u,
                  "gsamples_per_s": su / (ms_u * 1e-3) / 1e9, "per_piece_fp32_ms_per_frame": ms_up,
                  "speedup_of_batched": ms_up / ms_u, "sortlast_gpu": usl}
         if rank == 0 and not args.no_cpu_baseline:
@@ -548,7 +550,8 @@ def main():
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": dict(config_of(sc, args.workload), parallelism="replicas" if world > 1 else "single",
                           form="batched: 2 persistent kernels per frame, CUDA graph",
-                          tuning={"pass1": tuning[0], "pass2": tuning[1]}),
+                          tuning={"pass1": tuning[0], "pass2": tuning[1],
+                                  "packet": "4x8" if tuning[2] == pkg.MBOIT_PACKET_4X8 else "8x4"}),
            "samples_per_frame": samples, "ms_per_frame": ms_max, "singular_pixels": st["singular_pixels"], "per_piece_fp32": per_piece,
            "sortlast_gpu": sortlast, "amr_72_pieces": amr, "tets_72_pieces": tets,
            "precision_sweep_amr_2048": sweep,

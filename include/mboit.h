@@ -75,6 +75,8 @@ typedef enum { MBOIT_POWER4 = 0, MBOIT_TRIG6 = 1, MBOIT_TRIG8 = 2 } mboit_moment
  * by b0 (kept in float32) in float16 or bfloat16 (nearest-even rounding). */
 typedef enum { MBOIT_STORE_F32 = 0, MBOIT_STORE_F16 = 1, MBOIT_STORE_BF16 = 2 } mboit_storage;
 typedef enum { MBOIT_ORTHO = 0, MBOIT_PERSPECTIVE = 1 } mboit_projection;
+/* Ray packet of one warp (32 rays): 8 x 4 or 4 x 8 neighbouring pixels. */
+typedef enum { MBOIT_PACKET_8X4 = 0, MBOIT_PACKET_4X8 = 1 } mboit_packet;
 
 /* pass-1 output layout */
 typedef enum {
@@ -188,6 +190,8 @@ typedef struct {
     float frame_pass1_ms;       /* device time of pass 1 in the last mboit_render_frame (CUDA events
                                  * recorded in its graph); -1 before the first frame */
     float frame_pass2_ms;       /* the same for pass 2 */
+    int32_t packet;             /* mboit_packet in use (see mboit_set_packet) */
+    int32_t reserved2;
 } mboit_stats;
 
 /* Number of window configurations of the fused passes.  Each fused kernel
@@ -306,11 +310,18 @@ MBOIT_API mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* v
  * captured frame graphs are re-recorded. */
 MBOIT_API mboit_status mboit_set_tuning(mboit_volume v, int32_t pass1, int32_t pass2);
 
-/* Autotuner (the benchmark spec batching pattern): times every eligible
- * configuration of pass 1 and of pass 2 on these views (3 launches each,
- * CUDA events on `stream`, after one warm launch), keeps the fastest of
- * each, and writes them to chosen[0..1] (HOST, may be NULL).  The buffers
- * are as for mboit_render_frame and are overwritten.  Synchronous. */
+/* Selects the ray packet of every pass (mboit_packet).  Results do not
+ * depend on it (every ray is marched alone); speed does.  Captured frame
+ * graphs are re-recorded. */
+MBOIT_API mboit_status mboit_set_packet(mboit_volume v, int32_t packet);
+
+/* Autotuner (the batching pattern's tuner): for each ray packet, times every
+ * eligible window configuration of pass 1 and of pass 2 on these views (3
+ * launches each, CUDA events on `stream`, after one warm launch), and keeps
+ * the packet with the smallest sum of its fastest pass-1 and pass-2 times
+ * and those two configurations; writes pass 1's, pass 2's configuration and
+ * the packet to chosen[0..2] (HOST, may be NULL).  The buffers are as for
+ * mboit_render_frame and are overwritten.  Synchronous. */
 MBOIT_API mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch,
                                       float* rgba, void* stream, int32_t* chosen);
 

@@ -27,6 +27,7 @@ MBOIT_STORE_F32, MBOIT_STORE_F16, MBOIT_STORE_BF16 = 0, 1, 2
 MOMENT_SET_IDS = {"power4": MBOIT_POWER4, "trig6": MBOIT_TRIG6, "trig8": MBOIT_TRIG8}
 STORAGE_IDS = {"f32": MBOIT_STORE_F32, "f16": MBOIT_STORE_F16, "bf16": MBOIT_STORE_BF16}
 MBOIT_ORTHO, MBOIT_PERSPECTIVE = 0, 1
+MBOIT_PACKET_8X4, MBOIT_PACKET_4X8 = 0, 1
 MBOIT_MOMENTS_PER_PIECE, MBOIT_MOMENTS_REDUCED = 0, 1
 MBOIT_COLOR_PER_PIECE, MBOIT_COLOR_REDUCED, MBOIT_COLOR_RESOLVED = 0, 1, 2
 MBOIT_OP_MOMENTS_SUM, MBOIT_OP_COLOR_SUM_RESOLVE = 0, 1
@@ -35,7 +36,8 @@ MBOIT_FLAG_RAW_SUM, MBOIT_FLAG_DETERMINISTIC = 0x1, 0x2
 EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume", "mboit_destroy_volume",
             "mboit_add_piece", "mboit_render_moments", "mboit_reconstruct_blend", "mboit_composite",
             "mboit_render_frame", "mboit_render_frame_host", "mboit_synchronize", "mboit_get_stats",
-            "mboit_render_moments_noalloc", "mboit_set_tuning", "mboit_autotune", "mboit_render_sortlast"]
+            "mboit_render_moments_noalloc", "mboit_set_tuning", "mboit_set_packet", "mboit_autotune",
+            "mboit_render_sortlast"]
 MBOIT_NUM_TUNINGS = 5
 
 
@@ -68,7 +70,8 @@ class mboit_stats(ctypes.Structure):
                 ("singular_pixels", ctypes.c_int64), ("n_pieces", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("tuning_pass1", ctypes.c_int32), ("tuning_pass2", ctypes.c_int32),
                 ("sortlast_segments", ctypes.c_int64), ("sortlast_max_segments", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("frame_pass1_ms", ctypes.c_float), ("frame_pass2_ms", ctypes.c_float)]
+                ("reserved", ctypes.c_int32), ("frame_pass1_ms", ctypes.c_float), ("frame_pass2_ms", ctypes.c_float),
+                ("packet", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 _lib = None
@@ -98,6 +101,7 @@ def load_library(path=LIB_PATH):
         "mboit_get_stats": (ctypes.c_int, [P, P]),
         "mboit_render_moments_noalloc": (ctypes.c_int, [P, P, P, I32, P, P]),
         "mboit_set_tuning": (ctypes.c_int, [P, I32, I32]),
+        "mboit_set_packet": (ctypes.c_int, [P, I32]),
         "mboit_autotune": (ctypes.c_int, [P, P, I32, P, P, P, P]),
         "mboit_render_sortlast": (ctypes.c_int, [P, P, I32, P, P, P]),
     }
@@ -241,11 +245,16 @@ def mboit_set_tuning(v, pass1, pass2):
     _check(load_library().mboit_set_tuning(v, int(pass1), int(pass2)))
 
 
+def mboit_set_packet(v, packet):
+    _check(load_library().mboit_set_packet(v, int(packet)))
+
+
 def mboit_autotune(v, views, moments_scratch, rgba, stream=None):
+    """Returns (pass-1 configuration, pass-2 configuration, ray packet)."""
     arr, n = _views(views)
-    out = (ctypes.c_int32 * 2)()
+    out = (ctypes.c_int32 * 3)()
     _check(load_library().mboit_autotune(v, arr, n, _ptr(moments_scratch), _ptr(rgba), _stream(stream), out))
-    return int(out[0]), int(out[1])
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def mboit_render_sortlast(v, views, rgba, segments_per_pixel=None, stream=None):
@@ -398,6 +407,9 @@ class Volume:
 
     def set_tuning(self, pass1, pass2):
         mboit_set_tuning(self.handle, pass1, pass2)
+
+    def set_packet(self, packet):
+        mboit_set_packet(self.handle, packet)
 
     def autotune(self, views, moments_scratch, rgba, stream=None):
         return mboit_autotune(self.handle, views, moments_scratch, rgba, stream)

@@ -94,6 +94,7 @@ struct mboit_volume_s {
     bool frame_timed = false;
     std::vector<GraphEntry> graphs;
     int32_t tune1 = 0, tune2 = 0;
+    int32_t packet = MBOIT_PACKET_8X4;
     // sort-last baseline buffers (grow only)
     int32_t* sl_counts = nullptr;
     int64_t* sl_starts = nullptr;
@@ -169,7 +170,8 @@ mboit_status check_volume(mboit_volume v) {
 }
 
 // Validates views and lays out tiles and output offsets.
-mboit_status build_views(const mboit_view* views, int32_t n_views, mb::ViewTable& vt, int64_t bpp = 20) {
+mboit_status build_views(const mboit_view* views, int32_t n_views, mb::ViewTable& vt, int64_t bpp = 20,
+                         int32_t packet = MBOIT_PACKET_8X4) {
     if (!views) return fail(MBOIT_ERR_INVALID_ARG, "views is NULL");
     if (n_views < 1 || n_views > mb::kMaxViews)
         return fail(MBOIT_ERR_INVALID_ARG, "n_views must be in [1, " + std::to_string(mb::kMaxViews) + "]");
@@ -206,8 +208,10 @@ mboit_status build_views(const mboit_view* views, int32_t n_views, mb::ViewTable
         const double ln_n = std::log((double)V.near), ln_f = std::log((double)V.far);
         S.v.warp_a = (float)(2.0 * std::log(2.0) / (ln_f - ln_n));
         S.v.warp_b = (float)(-2.0 * ln_n / (ln_f - ln_n) - 1.0);
-        S.ntx = (V.width + mb::kTileW - 1) / mb::kTileW;
-        const int64_t nty = (V.height + mb::kTileH - 1) / mb::kTileH;
+        S.tw_log2 = packet == MBOIT_PACKET_4X8 ? 2 : 3;
+        const int tw = 1 << S.tw_log2, th = 32 >> S.tw_log2;
+        S.ntx = (V.width + tw - 1) / tw;
+        const int64_t nty = (V.height + th - 1) / th;
         S.tile_base = (int32_t)tiles;
         tiles += (int64_t)S.ntx * nty;
         S.plane = (int32_t)((((int64_t)V.width * V.height) + 3) / 4 * 4);
@@ -857,7 +861,7 @@ mboit_status mboit_render_moments(mboit_volume v, const mboit_view* views, int32
     std::lock_guard<std::mutex> lk(v->mu);
     DeviceGuard dg(v->device);
     mb::ViewTable vt;
-    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set))) != MBOIT_OK) return st;
+    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set), v->packet)) != MBOIT_OK) return st;
     std::vector<int32_t> list;
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, pieces, n_pieces, list, &mask)) != MBOIT_OK) return st;
@@ -892,7 +896,7 @@ mboit_status mboit_reconstruct_blend(mboit_volume v, const mboit_view* views, in
     std::lock_guard<std::mutex> lk(v->mu);
     DeviceGuard dg(v->device);
     mb::ViewTable vt;
-    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set))) != MBOIT_OK) return st;
+    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set), v->packet)) != MBOIT_OK) return st;
     std::vector<int32_t> list;
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, pieces, n_pieces, list, &mask)) != MBOIT_OK) return st;
@@ -960,7 +964,7 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
     std::lock_guard<std::mutex> lk(v->mu);
     DeviceGuard dg(v->device);
     mb::ViewTable vt;
-    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set))) != MBOIT_OK) return st;
+    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set), v->packet)) != MBOIT_OK) return st;
     std::vector<int32_t> list;
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, nullptr, 0, list, &mask)) != MBOIT_OK) return st;
@@ -1009,7 +1013,7 @@ mboit_status mboit_render_frame_host(mboit_volume v, const float* field_host, co
     if (st != MBOIT_OK) return st;
     if (!field_host || !rgba_host || !rgba_device) return fail(MBOIT_ERR_INVALID_ARG, "NULL buffer");
     mb::ViewTable vt;
-    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set))) != MBOIT_OK) return st;
+    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set), v->packet)) != MBOIT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     {
         DeviceGuard dg(v->device);
@@ -1061,6 +1065,8 @@ mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out) {
     out->sortlast_segments = v->sl_segments;
     out->sortlast_max_segments = c.max_segments;
     out->reserved = 0;
+    out->packet = v->packet;
+    out->reserved2 = 0;
     out->frame_pass1_ms = out->frame_pass2_ms = -1.0f;
     if (v->frame_timed && (cudaEventElapsedTime(&out->frame_pass1_ms, v->frame_ev[0], v->frame_ev[1]) != cudaSuccess ||
                            cudaEventElapsedTime(&out->frame_pass2_ms, v->frame_ev[1], v->frame_ev[2]) != cudaSuccess)) {
@@ -1079,7 +1085,7 @@ mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int3
     std::lock_guard<std::mutex> lk(v->mu);
     DeviceGuard dg(v->device);
     mb::ViewTable vt;
-    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set))) != MBOIT_OK) return st;
+    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set), v->packet)) != MBOIT_OK) return st;
     int64_t total_px = 0;
     for (int i = 0; i < n_views; ++i) total_px += (int64_t)views[i].width * views[i].height;
     const int32_t K = (int32_t)v->boxes.size();
@@ -1137,6 +1143,16 @@ mboit_status mboit_set_tuning(mboit_volume v, int32_t pass1, int32_t pass2) {
     return MBOIT_OK;
 }
 
+mboit_status mboit_set_packet(mboit_volume v, int32_t packet) {
+    g_err.clear();
+    if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
+    if (packet != MBOIT_PACKET_8X4 && packet != MBOIT_PACKET_4X8) return fail(MBOIT_ERR_INVALID_ARG, "unknown packet");
+    std::lock_guard<std::mutex> lk(v->mu);
+    v->packet = packet;
+    drop_graphs(v);
+    return MBOIT_OK;
+}
+
 mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch, float* rgba,
                             void* stream, int32_t* chosen) {
     g_err.clear();
@@ -1145,15 +1161,10 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
     if (!moments_scratch || !rgba) return fail(MBOIT_ERR_INVALID_ARG, "moments_scratch and rgba must be non-NULL");
     std::lock_guard<std::mutex> lk(v->mu);
     DeviceGuard dg(v->device);
-    mb::ViewTable vt;
-    if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set))) != MBOIT_OK) return st;
     std::vector<int32_t> list;
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, nullptr, 0, list, &mask)) != MBOIT_OK) return st;
-    if (v->kind != MBOIT_GRID) {  // one configuration only
-        if (chosen) chosen[0] = chosen[1] = 0;
-        return MBOIT_OK;
-    }
+    const bool grid = v->kind == MBOIT_GRID;  // octrees and meshes have one window configuration
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     MB_CUDA(cudaEventCreate(&e0));
@@ -1162,41 +1173,63 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
         cudaEventDestroy(e0);
         return fail(MBOIT_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
     }
-    float best_ms[2] = {3.0e38f, 3.0e38f};
-    int best[2] = {v->tune1, v->tune2};
-    for (int pass = 0; pass < 2 && ce == cudaSuccess; ++pass) {
-        for (int cfg = 0; cfg < mb::kNumStageConfigs && ce == cudaSuccess; ++cfg) {
-            if (!mb::stage_config_eligible(v->grid, cfg)) continue;
-            auto launch = [&]() {
-                return pass == 0 ? mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s, cfg)
-                                 : mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba,
-                                                          mb::kColorResolved, v->d_ctr, s, cfg);
-            };
-            ce = launch();
-            if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
-            for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = launch();
-            if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
-            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-            float ms = 0.0f;
-            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
-            if (ce == cudaSuccess && ms < best_ms[pass]) {
-                best_ms[pass] = ms;
-                best[pass] = cfg;
-            }
+    float best_total = 3.0e38f;
+    int best[3] = {v->tune1, v->tune2, v->packet};
+    for (int packet = MBOIT_PACKET_8X4; packet <= MBOIT_PACKET_4X8 && ce == cudaSuccess; ++packet) {
+        mb::ViewTable vt;
+        if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set), packet)) != MBOIT_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
         }
-        // pass 2 is timed on the moments of the fastest pass 1
-        if (pass == 0 && ce == cudaSuccess)
-            ce = mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s, best[0]);
+        float best_ms[2] = {3.0e38f, 3.0e38f};
+        int pick[2] = {0, 0};
+        for (int pass = 0; pass < 2 && ce == cudaSuccess; ++pass) {
+            for (int cfg = 0; cfg < mb::kNumStageConfigs && ce == cudaSuccess; ++cfg) {
+                if (grid ? !mb::stage_config_eligible(v->grid, cfg) : cfg != 0) continue;
+                auto launch = [&]() {
+                    if (!grid)
+                        return pass == 0 ? pass1_batched(v, mask, vt, moments_scratch, s)
+                                         : pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved, s);
+                    return pass == 0 ? mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s, cfg)
+                                     : mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba,
+                                                              mb::kColorResolved, v->d_ctr, s, cfg);
+                };
+                ce = launch();
+                if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+                for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = launch();
+                if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                if (ce == cudaSuccess && ms < best_ms[pass]) {
+                    best_ms[pass] = ms;
+                    pick[pass] = cfg;
+                }
+            }
+            // pass 2 is timed on the moments of the fastest pass 1
+            if (pass == 0 && ce == cudaSuccess)
+                ce = grid ? mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s, pick[0])
+                          : pass1_batched(v, mask, vt, moments_scratch, s);
+        }
+        if (ce == cudaSuccess && best_ms[0] + best_ms[1] < best_total) {
+            best_total = best_ms[0] + best_ms[1];
+            best[0] = pick[0];
+            best[1] = pick[1];
+            best[2] = packet;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (ce != cudaSuccess) return fail(MBOIT_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
     v->tune1 = best[0];
     v->tune2 = best[1];
+    v->packet = best[2];
     drop_graphs(v);
     if (chosen) {
         chosen[0] = best[0];
         chosen[1] = best[1];
+        chosen[2] = best[2];
     }
     return MBOIT_OK;
 }

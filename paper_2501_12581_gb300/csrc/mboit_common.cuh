@@ -359,8 +359,7 @@ __device__ __forceinline__ bool next_tile(const ViewTable& vt, int32_t* head, in
     vi = find_view(vt, tile);
     const ViewSlot& S = vt.s[vi];
     const int lt = tile - S.tile_base;
-    px = (lt % S.ntx) * kTileW + (lane & 7);
-    py = (lt / S.ntx) * kTileH + (lane >> 3);
+    tile_pixel(S, lt, lane, px, py);
     return true;
 }
 

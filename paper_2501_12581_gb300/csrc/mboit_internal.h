@@ -10,8 +10,6 @@
 namespace mb {
 
 constexpr int kMaxViews = 16;
-constexpr int kTileW = 8;   // a warp's ray tile: 8 x 4 pixels
-constexpr int kTileH = 4;
 
 struct ViewSlot {
     ViewD v;
@@ -20,8 +18,15 @@ struct ViewSlot {
     int64_t moment_off;     // byte offset of this view's first moment slab
     int64_t color_off;      // float offset of this view's first RGBA image
     int32_t plane;          // pixels per moment plane (w*h rounded up to 4)
-    int32_t pad0;
+    int32_t tw_log2;        // a warp's ray tile (packet) is 2^tw_log2 x 2^(5 - tw_log2) pixels: 8 x 4 or 4 x 8
 };
+
+// Pixel of lane `lane` in tile `lt` of a view (tiles row-major, ntx per row).
+MB_HD void tile_pixel(const ViewSlot& S, int lt, int lane, int& px, int& py) {
+    const int tw = 1 << S.tw_log2;
+    px = (lt % S.ntx) * tw + (lane & (tw - 1));
+    py = (lt / S.ntx) * (32 >> S.tw_log2) + (lane >> S.tw_log2);
+}
 
 struct ViewTable {
     int32_t n;

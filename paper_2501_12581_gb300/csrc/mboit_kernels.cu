@@ -257,8 +257,8 @@ __global__ void __launch_bounds__(256) k_tile_rows(const __grid_constant__ GridD
         const int vi = find_view(vt, tile);
         const ViewSlot& S = vt.s[vi];
         const int lt = tile - S.tile_base;
-        const int px = (lt % S.ntx) * kTileW + (lane & 7);
-        const int py = (lt / S.ntx) * kTileH + (lane >> 3);
+        int px, py;
+        tile_pixel(S, lt, lane, px, py);
         const bool valid = px < S.v.width && py < S.v.height;
         float o[3], d[3];
         int k0, k1;

@@ -138,8 +138,8 @@ __global__ void __launch_bounds__(128) k_pass1_piece(const __grid_constant__ V v
     const int vi = find_view(vt, tile);
     const ViewSlot& S = vt.s[vi];
     const int lt = tile - S.tile_base;
-    const int px = (lt % S.ntx) * kTileW + (lane & 7);
-    const int py = (lt / S.ntx) * kTileH + (lane >> 3);
+    int px, py;
+    tile_pixel(S, lt, lane, px, py);
     unsigned n = 0;
     if (px < S.v.width && py < S.v.height) {
         auto body = make_moment_body<MS>(s_sig, g, S.v);
@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ V v
     const int vi = find_view(vt, tile);
     const ViewSlot& S = vt.s[vi];
     const int lt = tile - S.tile_base;
-    const int px = (lt % S.ntx) * kTileW + (lane & 7);
-    const int py = (lt / S.ntx) * kTileH + (lane >> 3);
+    int px, py;
+    tile_pixel(S, lt, lane, px, py);
     unsigned n = 0;
     if (px < S.v.width && py < S.v.height) {
         const int pix = py * S.v.width + px;
@@ -579,8 +579,8 @@ __global__ void __launch_bounds__(128) k_sortlast_piece(const __grid_constant__ 
     const int vi = find_view(vt, tile);
     const ViewSlot& S = vt.s[vi];
     const int lt = tile - S.tile_base;
-    const int px = (lt % S.ntx) * kTileW + (lane & 7);
-    const int py = (lt / S.ntx) * kTileH + (lane >> 3);
+    int px, py;
+    tile_pixel(S, lt, lane, px, py);
     if (px >= S.v.width || py >= S.v.height) return;
     const int64_t npix = (int64_t)S.v.width * S.v.height;
     const int64_t gpix = S.color_off / 4 + py * S.v.width + px;  // pixel index over all views

@@ -52,6 +52,37 @@ def test_all_tunings_bit_identical(pkg, name):
     vol.close()
 
 
+@pytest.mark.parametrize("name", ["blobs64", "amr", "tets"])
+def test_packets_bit_identical(pkg, name):
+    """A warp's 32 rays as 8 x 4 or 4 x 8 pixels: every ray is marched alone,
+    so moments and images keep their bits (ragged views included)."""
+    import torch
+    if name == "blobs64":
+        sc = scenes.blobs64(width=61, height=37)
+    elif name == "amr":
+        sc = scenes.amr_blobs(base=4, max_level=2, width=45, height=38, n_pieces=5)
+    else:
+        sc = scenes.tet_mesh(n=8, n_pieces=3, width=43, height=29, seed=7)
+    vol = pkg.Volume(sc)
+    out = []
+    for packet in (pkg.MBOIT_PACKET_8X4, pkg.MBOIT_PACKET_4X8):
+        vol.set_packet(packet)
+        m, c = pkg.Volume.moment_buffer(sc.views), pkg.Volume.color_buffer(sc.views)
+        vol.render_frame(sc.views, m, c)
+        m2, c2 = pkg.Volume.moment_buffer(sc.views), pkg.Volume.color_buffer(sc.views)
+        vol.render_moments(sc.views, m2)
+        vol.reconstruct_blend(sc.views, m2, c2)
+        vol.synchronize()
+        torch.cuda.synchronize()
+        assert vol.stats()["packet"] == packet
+        out.append((m, c, m2, c2))
+    for a, b in zip(out[0], out[1]):
+        assert torch.equal(a, b)
+    with pytest.raises(pkg.MboitError):
+        vol.set_packet(2)
+    vol.close()
+
+
 def test_vector_tunings_refused_when_rows_unaligned(pkg):
     sc = small.linear_scene()          # nx = 17
     view = scenes.ortho_view(sc.dims, (0.36, 0.48, 0.8), 12, 10)
@@ -73,10 +104,10 @@ def test_autotune_then_frame_matches_oracle(pkg):
     vol = pkg.Volume(sc)
     mom = pkg.Volume.moment_buffer(sc.views)
     col = pkg.Volume.color_buffer(sc.views)
-    p1, p2 = vol.autotune(sc.views, mom, col)
-    assert 0 <= p1 < pkg.MBOIT_NUM_TUNINGS and 0 <= p2 < pkg.MBOIT_NUM_TUNINGS
+    p1, p2, pk = vol.autotune(sc.views, mom, col)
+    assert 0 <= p1 < pkg.MBOIT_NUM_TUNINGS and 0 <= p2 < pkg.MBOIT_NUM_TUNINGS and pk in (0, 1)
     st = vol.stats()
-    assert (st["tuning_pass1"], st["tuning_pass2"]) == (p1, p2)
+    assert (st["tuning_pass1"], st["tuning_pass2"], st["packet"]) == (p1, p2, pk)
     vol.render_frame(sc.views, mom, col)
     vol.synchronize()
     ref = oracle.render_grid(sc, want=("mboit",))
