@@ -708,7 +708,11 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
         for (int c = 0; c < 3; ++c) m.bdim[c] = th.bdim[c];
         m.bin_shift = th.bin_shift;
         m.qscale = std::ldexp(1.0f, d->quantum_log2);
+        // walk steps before the bin search takes over; MBOIT_TET_MAX_WALK
+        // overrides it (1: every point is found by the search), to exercise
+        // and measure the fallback
         m.max_walk = 64;
+        if (const char* w = std::getenv("MBOIT_TET_MAX_WALK")) m.max_walk = std::max(1, std::atoi(w));
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&v->cap_stream, cudaStreamNonBlocking);
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&v->frame_ev[i]);

@@ -179,6 +179,39 @@ def test_tet_host_frame_equals_device_frame(pkg, small_tet):
     np.testing.assert_array_equal(host.numpy(), want)
 
 
+@pytest.mark.parametrize("max_walk", [None, "1", "2"])
+def test_tet_mesh_with_a_hole_and_bin_search(pkg, monkeypatch, max_walk):
+    """A mesh with a cavity (tets near a centre point removed, neighbours
+    recomputed): walks leave the mesh inside the box and fall back to the
+    bin search, points in the cavity belong to no tet.  With the walk capped
+    at one or two steps every point is found by the search: the same owners,
+    so the same counts and images."""
+    import torch
+    if max_walk is None:
+        monkeypatch.delenv("MBOIT_TET_MAX_WALK", raising=False)
+    else:
+        monkeypatch.setenv("MBOIT_TET_MAX_WALK", max_walk)
+    sc = scenes.tet_mesh(n=8, n_pieces=3, width=40, height=36, seed=51)
+    cen = sc.verts[sc.tets, :3].astype(np.float64).mean(axis=1)
+    keep = np.linalg.norm(cen - np.array([4.2, 3.7, 4.4]), axis=1) > 2.3
+    assert 0 < (~keep).sum() < len(keep)
+    sc.tets = np.ascontiguousarray(sc.tets[keep])
+    sc.piece_of_tet = np.ascontiguousarray(sc.piece_of_tet[keep])
+    sc.neighbors = scenes.tet_neighbors(sc.tets)
+    vol = pkg.Volume(sc)
+    v = sc.views
+    mom = pkg.Volume.moment_buffer(v)
+    col = pkg.Volume.color_buffer(v)
+    vol.render_frame(v, mom, col)
+    vol.synchronize()
+    torch.cuda.synchronize()
+    ref = oracle.render(sc, want=("moments", "mboit", "nsamples"))
+    assert_moments_close(unpack_moments(mom, v)[0][0], ref["moments"])
+    assert_rgba_close(unpack_color(col, v)[0][0], ref["mboit"])
+    assert vol.stats()["samples_pass1"] == int(ref["nsamples"].sum())
+    vol.close()
+
+
 def test_tet_full_size_sampled(pkg):
     """4,423,680 tets, 72 pieces, 1024x1024 perspective."""
     import torch
