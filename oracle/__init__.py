@@ -65,14 +65,14 @@ class _Tet(ctypes.Structure):
                 ("moment_set", ctypes.c_int32), ("storage", ctypes.c_int32), ("trig_zone", ctypes.c_double)]
 
 
-MOMENT_SETS = {"power4": 0, "trig6": 3, "trig8": 4}
+MOMENT_SETS = {"power4": 0, "trig6": 3, "trig8": 4, "power6": 6, "power8": 8}
 STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
 TRIG_ZONE = 0.1
 
 
 def _nm(scene):
     n = MOMENT_SETS[getattr(scene, "moment_set", "power4")]
-    return 1 + 2 * n if n else 5
+    return 1 + 2 * n if n in (3, 4) else 1 + (n or 4)
 
 
 def _set_moment_fields(st, scene):
@@ -102,6 +102,11 @@ def _load():
             lib.orc_mboit_bound.restype = ctypes.c_double
             lib.orc_mboit_bound.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+            lib.orc_power_bound.restype = ctypes.c_double
+            lib.orc_power_bound.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+            lib.orc_power_bias.restype = None
+            lib.orc_power_bias.argtypes = [ctypes.c_int, ctypes.c_void_p]
             lib.orc_log_warp.restype = ctypes.c_double
             lib.orc_log_warp.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
             lib.orc_render_grid.restype = ctypes.c_int
@@ -145,6 +150,27 @@ def mboit_bound(m, z0, moment_bias, overestimation, bias_vector=BIAS_VECTOR_POWE
     A = lib.orc_mboit_bound(m.ctypes.data, float(z0), float(moment_bias), bv.ctypes.data,
                             float(overestimation), ctypes.byref(fl))
     return A, fl.value
+
+
+def power_bias(n):
+    """b1..b2n of the bias measure of the 2n-power-moment sets (arcsine law)."""
+    out = np.zeros(2 * n)
+    _load().orc_power_bias(int(n), out.ctypes.data)
+    return out
+
+
+def power_bound(m, n, z0, moment_bias, overestimation, bias=None):
+    """Alg. 3 with 2n power moments m = b0..b2n: returns (A, branch, nodes);
+    branch 0 generic (nodes = z0 and the n roots), k = a k-atom measure
+    (nodes = its atoms, the rest NaN)."""
+    lib = _load()
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    bv = np.ascontiguousarray(power_bias(n) if bias is None else bias, dtype=np.float64)
+    fl = ctypes.c_int(0)
+    nodes = np.full(n + 1, np.nan)
+    A = lib.orc_power_bound(m.ctypes.data, int(n), float(z0), float(moment_bias), bv.ctypes.data,
+                            float(overestimation), ctypes.byref(fl), nodes.ctypes.data)
+    return A, fl.value, nodes
 
 
 def trig_nodes(m, n, phi0, moment_bias):

@@ -188,13 +188,30 @@ typedef struct {
     double vmin, vmax, step, moment_bias, overestimation, absorbance_max;
     const double* bias_vector;
     int n_trig;                    /* 0: power moments; 3 or 4 complex trigonometric moments */
+    int n_power;                   /* 2n power moments b0..b_2n: n = 2, 3 or 4 (0 with trig moments) */
+    double power_bias[8];          /* bias measure of the 6- and 8-moment sets */
     int storage;                   /* 0, 1 float16, 2 bfloat16 (normalised trig moments) */
     double trig_zone;
 } vol_t;
 
 #define ORC_MAX_NM 9
 
-static int n_moments(const vol_t* g) { return g->n_trig ? 1 + 2 * g->n_trig : 5; }
+static int n_moments(const vol_t* g) { return g->n_trig ? 1 + 2 * g->n_trig : 1 + 2 * g->n_power; }
+
+/* moment_set 0 / 6 / 8: 4 / 6 / 8 power moments (FP64, no storage rounding);
+ * 3 / 4: complex trigonometric moments, optionally rounded to 16 bits. */
+static int set_moments(vol_t* v, int32_t moment_set, int32_t storage, double trig_zone)
+{
+    int trig = moment_set == 3 || moment_set == 4;
+    if (!trig && moment_set != 0 && moment_set != 6 && moment_set != 8) return -1;
+    if (storage < 0 || storage > 2 || (storage && !trig)) return -1;
+    v->n_trig = trig ? moment_set : 0;
+    v->n_power = trig ? 0 : moment_set == 0 ? 2 : moment_set / 2;
+    if (v->n_power > 2) orc_power_bias(v->n_power, v->power_bias);
+    v->storage = storage;
+    v->trig_zone = trig_zone;
+    return 0;
+}
 
 /* round-to-nearest-even float -> float16 -> float (finite inputs) */
 static float round_f16(float x)
@@ -400,12 +417,174 @@ static double trig_bound_impl(const double* m, int n, double phi0, double moment
     return A;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Alg. 3 with 2n power moments (n = 2, 3, 4)                                */
+
+void orc_power_bias(int n, double* bias)
+{
+    double c = 1.0;  /* C(2k, k) / 4^k = prod_{i <= k} (2i - 1) / (2i) */
+    for (int j = 1; j <= 2 * n; ++j) {
+        if (j % 2) {
+            bias[j - 1] = 0.0;
+            continue;
+        }
+        c *= (double)(j - 1) / (double)j;
+        bias[j - 1] = c;
+    }
+}
+
+/* x = B^-1 r for the leading n1 x n1 block of B = L D L^T */
+static void hankel_solve(int n1, double L[5][5], const double D[5], const double* r, double* x)
+{
+    double y[5];
+    for (int i = 0; i < n1; ++i) {
+        y[i] = r[i];
+        for (int k = 0; k < i; ++k) y[i] -= L[i][k] * y[k];
+    }
+    for (int i = 0; i < n1; ++i) y[i] /= D[i];
+    for (int i = n1 - 1; i >= 0; --i) {
+        x[i] = y[i];
+        for (int k = i + 1; k < n1; ++k) x[i] -= L[k][i] * x[k];
+    }
+}
+
+/* Real parts of the roots of c[0] + c[1] x + .. + c[deg] x^deg, ascending
+ * (the roots are real here: zeros of a kernel or orthogonal polynomial).
+ * Returns their number (the degree after dropping zero leading terms). */
+static int real_roots(int deg, const double* c, double* r)
+{
+    while (deg > 0 && c[deg] == 0.0) --deg;
+    if (deg <= 0) return 0;
+    double complex cc[5], rc[4];
+    for (int k = 0; k <= deg; ++k) cc[k] = c[k];
+    poly_roots(deg, cc, rc);
+    for (int k = 0; k < deg; ++k) r[k] = creal(rc[k]);
+    for (int a = 1; a < deg; ++a)
+        for (int b = a; b > 0 && r[b - 1] > r[b]; --b) {
+            double t = r[b];
+            r[b] = r[b - 1];
+            r[b - 1] = t;
+        }
+    return deg;
+}
+
+double orc_power_bound(const double* m, int n, double z0, double moment_bias, const double* bias,
+                       double overestimation, int* flags, double* nodes)
+{
+    if (flags) *flags = 0;
+    if (!(m[0] > 0.0) || n < 1 || n > 4) return 0.0;
+    const int n1 = n + 1;
+
+    /* b_tmp = (b1..b2n) / b0, mixed with the bias measure */
+    double b[9];
+    b[0] = 1.0;
+    for (int j = 1; j <= 2 * n; ++j) b[j] = (1.0 - moment_bias) * (m[j] / m[0]) + moment_bias * bias[j - 1];
+
+    /* Hankel matrix B[i][j] = b[i + j] as L D L^T, column by column; the
+     * first pivot that is not positive ends it: k atoms */
+    double L[5][5], D[5];
+    int k = n1;
+    for (int j = 0; j < n1; ++j) {
+        double s = b[2 * j];
+        for (int l = 0; l < j; ++l) s -= L[j][l] * L[j][l] * D[l];
+        double scale = fabs(b[2 * j]) > 1.0 ? fabs(b[2 * j]) : 1.0;
+        if (s <= ORC_TAU * scale) {
+            k = j;
+            break;
+        }
+        D[j] = s;
+        L[j][j] = 1.0;
+        for (int i = j + 1; i < n1; ++i) {
+            double t = b[i + j];
+            for (int l = 0; l < j; ++l) t -= L[i][l] * L[j][l] * D[l];
+            L[i][j] = t / D[j];
+        }
+    }
+
+    if (k < n1) {
+        /* a measure of k atoms: the roots of x^k + sum_{j<k} e_j x^j with
+         * H_k e = -(b_k, .., b_2k-1), H_k the leading k x k block */
+        double r[4], e[5], x[4];
+        for (int i = 0; i < k; ++i) r[i] = -b[i + k];
+        hankel_solve(k, L, D, r, e);
+        e[k] = 1.0;
+        int na = real_roots(k, e, x);
+        /* weight of atom i: the integral of its Lagrange basis polynomial */
+        double A = 0.0;
+        for (int i = 0; i < na; ++i) {
+            double c[5] = {1.0, 0.0, 0.0, 0.0, 0.0}, den = 1.0;
+            int deg = 0;
+            for (int o = 0; o < na; ++o) {
+                if (o == i) continue;
+                c[deg + 1] = c[deg];
+                for (int t = deg; t >= 1; --t) c[t] = c[t - 1] - x[o] * c[t];
+                c[0] = -x[o] * c[0];
+                ++deg;
+                den *= x[i] - x[o];
+            }
+            double rho = 0.0;
+            for (int t = 0; t <= deg; ++t) rho += c[t] * b[t];
+            A += rho / den * step_weight(x[i], z0, overestimation);
+            if (nodes) nodes[i] = x[i];
+        }
+        if (flags) *flags = k;
+        return A;
+    }
+
+    /* SolveMat: q = B^-1 (1, z0, .., z0^n) */
+    double v[5], q[5];
+    v[0] = 1.0;
+    for (int i = 1; i < n1; ++i) v[i] = v[i - 1] * z0;
+    hankel_solve(n1, L, D, v, q);
+
+    /* SolvePowerEquation: the other n support points are the roots of
+     * sum_j q_j x^j */
+    double z[5];
+    z[0] = z0;
+    int nr = real_roots(n, q, z + 1);
+    if (nodes)
+        for (int i = 0; i <= n; ++i) nodes[i] = i <= nr ? z[i] : NAN;
+
+    /* weights: overestimation at z0, indicator z_i < z0 elsewhere; Newton
+     * divided differences over the distinct support points */
+    double X[5], F[5];
+    int nd = 0;
+    for (int i = 0; i <= nr; ++i) {
+        int dup = 0;
+        for (int l = 0; l < nd; ++l) dup |= X[l] == z[i];
+        if (dup) continue;
+        X[nd] = z[i];
+        F[nd] = (i == 0) ? overestimation : (z[i] < z0 ? 1.0 : 0.0);
+        ++nd;
+    }
+    for (int j = 1; j < nd; ++j)
+        for (int i = nd - 1; i >= j; --i) F[i] = (F[i] - F[i - 1]) / (X[i] - X[i - j]);
+
+    /* solvePolynomial: p(x) = sum_j F[j] prod_{l<j} (x - X[l]) expanded */
+    double p[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int deg = 0;
+    p[0] = F[nd - 1];
+    for (int j = nd - 2; j >= 0; --j) {
+        p[deg + 1] = p[deg];
+        for (int t = deg; t >= 1; --t) p[t] = p[t - 1] - X[j] * p[t];
+        p[0] = F[j] - X[j] * p[0];
+        ++deg;
+    }
+
+    /* absorbance = p . (1, b_tmp) */
+    double A = 0.0;
+    for (int t = 0; t <= deg; ++t) A += p[t] * b[t];
+    return A;
+}
+
 static double transmittance(const double* m, double z0, const vol_t* g)
 {
     double A;
     if (g->n_trig)
         A = orc_trig_bound(m, g->n_trig, z0 * (1.0 - g->trig_zone) * ORC_PI, g->moment_bias, g->overestimation,
                            NULL, NULL);
+    else if (g->n_power > 2)
+        A = orc_power_bound(m, g->n_power, z0, g->moment_bias, g->power_bias, g->overestimation, NULL, NULL);
     else
         A = orc_mboit_bound(m, z0, g->moment_bias, g->bias_vector, g->overestimation, NULL);
     double T = exp(-m[0] * A);
@@ -657,8 +836,7 @@ static int tet_vol(const orc_tet* m, vol_t* v)
     if (!m || !m->verts || !m->tets || !m->piece_of_tet || !m->tf || m->n_tets <= 0 || m->n_verts <= 0 ||
         m->n_pieces <= 0 || m->quantum_log2 < 0 || m->quantum_log2 > 24)
         return -1;
-    if ((m->moment_set != 0 && m->moment_set != 3 && m->moment_set != 4) || m->storage < 0 || m->storage > 2 ||
-        (m->storage && !m->moment_set))
+    if (set_moments(v, m->moment_set, m->storage, m->trig_zone) != 0)
         return -1;
     const int s = m->quantum_log2;
     v->kind = 2;
@@ -726,9 +904,6 @@ static int tet_vol(const orc_tet* m, vol_t* v)
     v->overestimation = m->overestimation;
     v->absorbance_max = m->absorbance_max;
     v->bias_vector = m->bias_vector;
-    v->n_trig = m->moment_set;
-    v->storage = m->storage;
-    v->trig_zone = m->trig_zone;
     return 0;
 }
 
@@ -800,11 +975,7 @@ static int grid_vol(const orc_grid* g, vol_t* v)
     v->overestimation = g->overestimation;
     v->absorbance_max = g->absorbance_max;
     v->bias_vector = g->bias_vector;
-    if (g->moment_set != 0 && g->moment_set != 3 && g->moment_set != 4) return -1;
-    if (g->storage < 0 || g->storage > 2 || (g->storage && !g->moment_set)) return -1;
-    v->n_trig = g->moment_set;
-    v->storage = g->storage;
-    v->trig_zone = g->trig_zone;
+    if (set_moments(v, g->moment_set, g->storage, g->trig_zone) != 0) return -1;
     return 0;
 }
 
@@ -868,14 +1039,10 @@ int orc_render_amr(const orc_amr* a, const orc_view* V,
     v.overestimation = a->overestimation;
     v.absorbance_max = a->absorbance_max;
     v.bias_vector = a->bias_vector;
-    if ((a->moment_set != 0 && a->moment_set != 3 && a->moment_set != 4) || a->storage < 0 || a->storage > 2 ||
-        (a->storage && !a->moment_set)) {
+    if (set_moments(&v, a->moment_set, a->storage, a->trig_zone) != 0) {
         free(fmap);
         return -1;
     }
-    v.n_trig = a->moment_set;
-    v.storage = a->storage;
-    v.trig_zone = a->trig_zone;
     int rc = render_impl(&v, V, pixels, n_pixels, moments, piece_moments, piece_color, mboit_rgba, raw_rgba,
                          exact_rgba, sortlast_rgba, nsamples, nsegments);
     free(fmap);
@@ -961,7 +1128,7 @@ static int render_impl(const vol_t* g, const orc_view* V,
                 }
             } else {
                 double zp = 1.0;
-                for (int j = 0; j <= 4; ++j) {
+                for (int j = 0; j <= 2 * g->n_power; ++j) {
                     mp[j] += zp * S[i].a;
                     zp *= S[i].z;
                 }

@@ -36,7 +36,8 @@ typedef struct {
     double overestimation;         /* weight w0 of the sample's own depth (Alg. 3) */
     double absorbance_max;         /* ABSORBANCE_MAX_VALUE (Alg. 2) */
     double bias_vector[4];
-    int32_t moment_set;            /* 0: 4 power moments; 3 / 4: that many complex trigonometric moments */
+    int32_t moment_set;            /* 0: 4 power moments; 3 / 4: that many complex trigonometric moments;
+                                      6 / 8: that many power moments (bias vector: orc_power_bias) */
     int32_t storage;               /* 0 FP64 moments; 1 / 2: normalised trig moments rounded to float16 / bfloat16 */
     double trig_zone;              /* zeta: angles phi = z (1 - zeta) pi leave a wrapping zone of 2 zeta pi */
 } orc_grid;
@@ -62,6 +63,24 @@ typedef struct {
  * *flags (optional) gets 1 for the one-atom, 2 for the two-atom branch. */
 double orc_mboit_bound(const double m[5], double z0, double moment_bias,
                        const double bias_vector[4], double overestimation, int* flags);
+
+/* Alg. 3 with 2n power moments, n = 2, 3 or 4 (the 4-, 6- and 8-moment
+ * variants of Sec. 4.3 / Fig. 3): m = b0..b_2n raw; normalise, mix with
+ * bias[0..2n-1] (b1'..b2n' of the bias measure), LDL^T of the (n+1) x (n+1)
+ * Hankel matrix, q = B^-1 (1, z0, .., z0^n), the n roots of sum q_j x^j,
+ * weights (overestimation at z0, indicator x_i < z0 elsewhere), the degree-n
+ * polynomial interpolating them, A = p . (1, b1', .., bn').  A Hankel matrix
+ * whose leading k x k block is the last positive-definite one (k <= n) means
+ * a measure of k atoms, and A sums their weights.  *flags (optional): 0
+ * generic, else k.  nodes (optional, n + 1 entries): z0 and the roots
+ * (generic case) or the k atoms. */
+double orc_power_bound(const double* m, int n, double z0, double moment_bias, const double* bias,
+                       double overestimation, int* flags, double* nodes);
+
+/* The bias measure of the 6- and 8-moment sets: moments b1..b_2n of the
+ * arcsine (Chebyshev) distribution on [-1, 1], b_2k = C(2k, k) / 4^k, odd
+ * moments 0.  Its Hankel matrices are positive definite at every order. */
+void orc_power_bias(int n, double* bias);
 
 /* Trigonometric moments (n = 3 or 4 complex moments, "6 / 8 trigonometric
  * moments" of Sec. 4.3 / Fig. 3): warped depth z -> angle phi = z (1 - zeta) pi,
@@ -89,8 +108,8 @@ double orc_log_warp(double t, double znear, double zfar);
 
 /* Renders the listed pixels (index y*width + x) of one view.  Every output
  * pointer may be NULL.  Per pixel: moments = summed global moments [NM]
- * (NM = 5 for power moments: b0..b4; 1 + 2n for n trigonometric moments:
- * b0, Re t1, Im t1, ...); piece_moments [K][NM]; piece_color [K][4];
+ * (NM = 1 + 2n for 2n power moments: b0..b_2n; 1 + 2n for n trigonometric
+ * moments: b0, Re t1, Im t1, ...); piece_moments [K][NM]; piece_color [K][4];
  * mboit_rgba = renormalised resolve; raw_rgba = sum of T*alpha*(c,1);
  * exact_rgba = front-to-back blend of the same samples; sortlast_rgba =
  * per-piece segments sorted and blended; nsamples = owned samples.

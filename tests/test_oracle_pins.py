@@ -499,6 +499,230 @@ def test_trig_node_just_behind_is_not_counted(n):
 
 
 # --------------------------------------------------------------------------
+# Alg. 3 with 6 and 8 power moments (the moment-count variants of Sec. 4.3 /
+# Fig. 3): the bound of order n uses b0..b_2n and a (n+1) x (n+1) Hankel matrix
+
+
+def power_moments(x, a, n):
+    x = np.asarray(x, float)
+    a = np.asarray(a, float)
+    return np.array([np.sum(a * x ** j) for j in range(2 * n + 1)])
+
+
+def arcsine_moments(n):
+    """b1..b2n of the arcsine law on [-1, 1]: b_2k = C(2k, k) / 4^k."""
+    return np.array([0.0 if j % 2 else math.comb(j, j // 2) / 4.0 ** (j // 2) for j in range(1, 2 * n + 1)])
+
+
+def test_power_bias_is_arcsine_law():
+    for n in (3, 4):
+        np.testing.assert_allclose(oracle.power_bias(n), arcsine_moments(n), rtol=0, atol=1e-15)
+
+
+def test_power_order_two_equals_four_moment_routine():
+    """The order-n routine at n = 2 (bias (0, 3/8, 0, 3/8)) reproduces the
+    4-moment routine on generic and one-/two-atom measures."""
+    rng = np.random.default_rng(40)
+    for _ in range(1000):
+        k = rng.integers(1, 12)
+        m = power_moments(rng.uniform(-1, 1, k), rng.uniform(0.01, 1, k), 2)
+        z0, beta, w0 = rng.uniform(-1, 1), rng.choice([0.0, 5e-5, 1e-2]), rng.uniform(0, 1)
+        A4, b4 = oracle.mboit_bound(m, z0, beta, w0)
+        An, bn, _ = oracle.power_bound(m, 2, z0, beta, w0, bias=oracle.BIAS_VECTOR_POWER4)
+        assert bn == b4
+        assert An == pytest.approx(A4, abs=1e-11)
+
+
+@pytest.mark.parametrize("n", [3, 4])
+def test_power_few_atoms_exact(n):
+    """k <= n absorbers, no bias: the Hankel matrix is singular, the measure
+    is recovered and T(z) = exp(-sum of the absorbances in front)."""
+    rng = np.random.default_rng(41 + n)
+    for k in range(1, n + 1):
+        done = 0
+        while done < 60:
+            x = np.sort(rng.uniform(-1, 1, k))
+            if k > 1 and np.diff(x).min() < 0.05:
+                continue
+            a = rng.uniform(0.05, 3.0, k)
+            m = power_moments(x, a, n)
+            for z in rng.uniform(-1, 1, 6):
+                if np.min(np.abs(z - x)) < 1e-4:
+                    continue
+                A, branch, nodes = oracle.power_bound(m, n, z, 0.0, rng.uniform(0, 1))
+                assert branch == k
+                np.testing.assert_allclose(nodes[:k], x, atol=1e-7)
+                assert math.exp(-m[0] * A) == pytest.approx(math.exp(-a[x < z].sum()), abs=1e-9)
+            done += 1
+
+
+@pytest.mark.parametrize("n", [3, 4])
+def test_power_n_plus_one_atoms_canonical(n):
+    """Generic branch.  n+1 atoms are the canonical representation through
+    each of their atoms, so at z0 = x_j the bound is exactly
+    (sum_{x_i < x_j} a_i + w0 a_j) / sum a."""
+    rng = np.random.default_rng(50 + n)
+    done = 0
+    while done < 200:
+        x = np.sort(rng.uniform(-1, 1, n + 1))
+        if np.diff(x).min() < 0.1:
+            continue
+        a = rng.uniform(0.1, 2.0, n + 1)
+        w0 = rng.uniform(0, 1)
+        m = power_moments(x, a, n)
+        for j in range(n + 1):
+            A, branch, _ = oracle.power_bound(m, n, x[j], 0.0, w0)
+            assert branch == 0
+            assert A == pytest.approx((a[x < x[j]].sum() + w0 * a[j]) / a.sum(), abs=1e-8)
+        done += 1
+
+
+@pytest.mark.parametrize("n", [3, 4])
+def test_power_full_bias_is_arcsine_gauss_rule(n):
+    """Mix amount 1 leaves the arcsine law, whose (n+1)-point Gauss rule has
+    nodes cos((2k - 1) pi / (2n + 2)) and weights 1/(n+1) and integrates
+    degree 2n+1 exactly: through one of its nodes it is the canonical
+    representation, so A = (w0 + nodes in front) / (n + 1)."""
+    m = power_moments([0.3, -0.2, 0.9], [0.5, 1.0, 0.2], n)
+    g = np.sort(np.cos((2 * np.arange(1, n + 2) - 1) * np.pi / (2 * n + 2)))
+    for j, z0 in enumerate(g):
+        for w0 in (0.0, 0.3, 1.0):
+            A, branch, nodes = oracle.power_bound(m, n, z0, 1.0, w0)
+            assert branch == 0
+            np.testing.assert_allclose(np.sort(nodes), g, atol=1e-9)
+            assert A == pytest.approx((w0 + j) / (n + 1), abs=1e-10)
+
+
+@pytest.mark.parametrize("n", [3, 4])
+def test_power_representation_christoffel_weights(n):
+    """The support points are a quadrature exact to degree 2n: with the
+    Christoffel weights 1 / K(x, x) (K(x, y) = v(x)^T H^-1 v(y), H the biased
+    Hankel matrix) they reproduce every biased moment b0'..b2n', and the
+    bound equals w0 rho(z0) + the weights of the points in front."""
+    rng = np.random.default_rng(60 + n)
+    for _ in range(100):
+        k = rng.integers(n + 1, 25)
+        m = power_moments(rng.uniform(-1, 1, k), rng.uniform(0.01, 1, k), n)
+        beta = rng.choice([0.0, 1e-3, 5e-2])
+        b = np.concatenate([[1.0], (1 - beta) * m[1:] / m[0] + beta * arcsine_moments(n)])
+        H = np.array([[b[i + j] for j in range(n + 1)] for i in range(n + 1)])
+        Hinv = np.linalg.inv(H)
+        for z0 in rng.uniform(-1, 1, 4):
+            w0 = rng.uniform(0, 1)
+            A, branch, x = oracle.power_bound(m, n, z0, beta, w0)
+            assert branch == 0 and x[0] == z0
+            rho = np.array([1.0 / (x[i] ** np.arange(n + 1) @ Hinv @ x[i] ** np.arange(n + 1)) for i in range(n + 1)])
+            assert np.all(rho > 0)
+            for j in range(2 * n + 1):
+                assert np.sum(rho * x ** j) == pytest.approx(b[j], abs=1e-8)
+            assert A == pytest.approx(w0 * rho[0] + rho[1:][x[1:] < z0].sum(), abs=1e-8)
+
+
+def test_power_bounds_nest_and_contain():
+    """Chebyshev-Markov-Stieltjes with more moments: the lower bound (w0 = 0)
+    rises and the upper bound (w0 = 1) falls as n goes 2 -> 3 -> 4, and both
+    keep containing the true mass in front of z."""
+    rng = np.random.default_rng(70)
+    for _ in range(400):
+        k = rng.integers(6, 30)
+        x = rng.uniform(-1, 1, k)
+        a = rng.uniform(0.01, 1.0, k)
+        z = rng.uniform(-1, 1)
+        lo, hi = [], []
+        for n in (2, 3, 4):
+            m = power_moments(x, a, n)
+            bias = oracle.BIAS_VECTOR_POWER4 if n == 2 else None
+            lo.append(oracle.power_bound(m, n, z, 0.0, 0.0, bias=bias)[0])
+            hi.append(oracle.power_bound(m, n, z, 0.0, 1.0, bias=bias)[0])
+        before, upto = a[x < z].sum() / a.sum(), a[x <= z].sum() / a.sum()
+        e = 1e-9
+        assert lo[0] <= lo[1] + e and lo[1] <= lo[2] + e and lo[2] <= before + e
+        assert upto <= hi[2] + e and hi[2] <= hi[1] + e and hi[1] <= hi[0] + e
+
+
+@pytest.mark.parametrize("n", [3, 4])
+def test_power_bound_equals_linear_program(n):
+    """Brute force: over all non-negative measures on a fine grid with the
+    given 2n+1 moments, the largest mass in (-inf, z0] is the bound with
+    w0 = 1 and the smallest mass in (-inf, z0) the bound with w0 = 0 (up to
+    the grid's resolution)."""
+    opt = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(80 + n)
+    done = 0
+    while done < 6:
+        k = rng.integers(n + 2, 10)
+        x = np.round(rng.uniform(-1, 1, k), 3)
+        z0 = round(float(rng.uniform(-0.8, 0.8)), 3)
+        if np.min(np.abs(x - z0)) < 0.01:
+            continue
+        a = rng.uniform(0.05, 1.0, k)
+        m = power_moments(x, a, n)
+        b = m / m[0]
+        hi = oracle.power_bound(m, n, z0, 0.0, 1.0)[0]
+        lo, _, nodes = oracle.power_bound(m, n, z0, 0.0, 0.0)
+        R = max(1.0, float(np.nanmax(np.abs(nodes)))) + 0.25
+        grid = np.unique(np.concatenate([np.linspace(-R, R, int(2 * R / 5e-4) + 1), [z0], x]))
+        # equality constraints in the Chebyshev basis of [-R, R] (well scaled)
+        V = np.polynomial.chebyshev.chebvander(grid / R, 2 * n).T
+        C = np.zeros((2 * n + 1, 2 * n + 1))
+        for j in range(2 * n + 1):
+            c = np.polynomial.chebyshev.cheb2poly(np.eye(2 * n + 1)[j])
+            C[j, :len(c)] = c / R ** np.arange(len(c))
+        rhs = C @ b
+        r_hi = opt.linprog(-(grid <= z0).astype(float), A_eq=V, b_eq=rhs, bounds=(0, None), method="highs")
+        r_lo = opt.linprog((grid < z0).astype(float), A_eq=V, b_eq=rhs, bounds=(0, None), method="highs")
+        if r_hi.status != 0 or r_lo.status != 0:
+            continue
+        assert -r_hi.fun == pytest.approx(hi, abs=2e-4)
+        assert r_lo.fun == pytest.approx(lo, abs=2e-4)
+        done += 1
+
+
+@pytest.mark.parametrize("n", [3, 4])
+def test_power_bound_monotone_and_in_range(n):
+    rng = np.random.default_rng(90 + n)
+    zs = np.linspace(-1, 1, 201)
+    for _ in range(60):
+        k = rng.integers(1, 20)
+        m = power_moments(rng.uniform(-1, 1, k), rng.uniform(0.01, 2.0, k), n)
+        beta = 10 ** rng.uniform(-5, -1)
+        A = np.array([oracle.power_bound(m, n, z, beta, W0)[0] for z in zs])
+        assert np.all(A >= -1e-9) and np.all(A <= 1 + 1e-9)
+        assert np.all(np.diff(A) >= -1e-7)
+
+
+def test_power_render_more_moments_closer_to_exact():
+    """Rendering with 6 and 8 power moments: the moment images of the pieces
+    add up to the global ones, alpha is exact, and the image moves towards the
+    exact blend as moments are added (Fig. 3)."""
+    import copy
+    sc = scenes.blobs64(width=40, height=40)
+    rmse, first5 = {}, None
+    for ms, beta in (("power4", 5e-5), ("power6", 5e-5), ("power8", 5e-5)):
+        s2 = copy.copy(sc)
+        s2.moment_set, s2.moment_bias = ms, beta
+        out = oracle.render_grid(s2, want=("mboit", "exact", "moments", "piece_moments"))
+        nm = {"power4": 5, "power6": 7, "power8": 9}[ms]
+        mo = out["moments"].reshape(-1, out["moments"].shape[-1])
+        assert mo.shape[-1] == nm
+        np.testing.assert_allclose(out["piece_moments"].sum(axis=-2), out["moments"], rtol=1e-12, atol=1e-12)
+        # the same samples: b0..b4 agree across the sets; every pixel's
+        # normalised Hankel matrix is positive semidefinite (|z| <= 1 too)
+        if first5 is None:
+            first5 = mo[:, :5]
+        np.testing.assert_allclose(mo[:, :5], first5, rtol=1e-12, atol=1e-12)
+        hit = mo[:, 0] > 1e-3
+        b = mo[hit] / mo[hit, :1]
+        h = (nm - 1) // 2
+        H = np.stack([np.stack([b[:, i + j] for j in range(h + 1)], -1) for i in range(h + 1)], -2)
+        assert np.linalg.eigvalsh(H).min() > -1e-9
+        assert np.all(np.abs(b) <= 1 + 1e-12)
+        np.testing.assert_allclose(out["mboit"][..., 3], out["exact"][..., 3], atol=1e-12)
+        rmse[ms] = float(np.sqrt(((out["mboit"] - out["exact"]) ** 2).mean()))
+    assert rmse["power8"] < rmse["power6"] < rmse["power4"]
+
+
+# --------------------------------------------------------------------------
 # tetrahedral meshes (Sec. 5: unstructured pieces)
 
 
