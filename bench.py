@@ -46,8 +46,9 @@ CACHE_BYTES_PER_SAMPLE = 4
 # FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x
 # 2 FLOP x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-KERNEL_SOURCES = ["paper_2501_12581_gb300/csrc/mboit_grid.cu", "paper_2501_12581_gb300/csrc/mboit_common.cuh",
-                  "paper_2501_12581_gb300/csrc/mboit_device.cuh", "paper_2501_12581_gb300/csrc/mboit_trig.cuh"]
+KERNEL_SOURCES = ["paper_2501_12581_gb300/csrc/mboit_grid.cuh", "paper_2501_12581_gb300/csrc/mboit_grid.cu",
+                  "paper_2501_12581_gb300/csrc/mboit_common.cuh", "paper_2501_12581_gb300/csrc/mboit_device.cuh",
+                  "paper_2501_12581_gb300/csrc/mboit_trig.cuh", "paper_2501_12581_gb300/csrc/mboit_power.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "frame_fused_blobs512_traffic.txt")
 
 
@@ -495,8 +496,9 @@ def main():
         spix = sample_pixels(2048, 2048, 64, 32)
         sweep = []
         exact_ref = None
-        for ms, st, beta in (("power4", "f32", 5e-5), ("trig6", "f16", 2e-3), ("trig6", "bf16", 2e-2),
-                             ("trig8", "f16", 2e-3), ("trig8", "bf16", 2e-2)):
+        for ms, st, beta in (("power4", "f32", 5e-5), ("power6", "f32", 5e-5), ("power8", "f32", 5e-5),
+                             ("trig6", "f16", 2e-3), ("trig6", "bf16", 2e-2), ("trig8", "f16", 2e-3),
+                             ("trig8", "bf16", 2e-2)):
             sc2 = copy.copy(base)
             sc2.moment_set, sc2.storage, sc2.moment_bias = ms, st, beta
             svol = pkg.Volume(sc2)

@@ -32,7 +32,9 @@
  *   - Images are row-major, pixel index y * width + x, x to the right.
  *   - Moment images: per (view[, piece]) one slab, P = width * height rounded
  *     up to a multiple of 4.  Power moments: b0 as P float32, then (b1, b2,
- *     b3, b4) as P float4 (20 * P bytes).  Trigonometric moments: b0 as P
+ *     b3, b4) as P float4 (20 * P bytes); with 6 power moments then (b5, b6)
+ *     as P float2 (28 * P bytes), with 8 then (b5, .., b8) as P float4
+ *     (36 * P bytes).  Trigonometric moments: b0 as P
  *     float32, then for j = 1..n a plane of P 16-bit pairs (Re, Im of
  *     t_j / b0) ((4 + 4 n) * P bytes).  mboit_moment_image_bytes() gives the
  *     slab size.
@@ -67,10 +69,20 @@ typedef enum {
 } mboit_status;
 
 typedef enum { MBOIT_GRID = 0, MBOIT_AMR = 1, MBOIT_TET = 2 } mboit_volume_kind;
-/* Moment sets (Sec. 4.3, Fig. 3): 4 power moments of the warped depth, or 3 / 4
- * complex trigonometric moments ("6 / 8 trigonometric moments") of the angle
- * phi = z (1 - 0.1) pi (a wrapping zone of 0.2 pi separates far from near). */
-typedef enum { MBOIT_POWER4 = 0, MBOIT_TRIG6 = 1, MBOIT_TRIG8 = 2 } mboit_moment_set;
+/* Moment sets (Sec. 4.3, Fig. 3): 4, 6 or 8 power moments of the warped depth
+ * z (Alg. 2: b_j = sum a z^j; Alg. 3 with a 3x3, 4x4 or 5x5 Hankel matrix), or
+ * 3 / 4 complex trigonometric moments ("6 / 8 trigonometric moments") of the
+ * angle phi = z (1 - 0.1) pi (a wrapping zone of 0.2 pi separates far from
+ * near).  The 6- and 8-moment sets mix the normalised moments with those of
+ * the arcsine law on [-1, 1] (b_2k = C(2k, k) / 4^k, odd moments 0) and need
+ * moment_bias > 0. */
+typedef enum {
+    MBOIT_POWER4 = 0,
+    MBOIT_TRIG6 = 1,
+    MBOIT_TRIG8 = 2,
+    MBOIT_POWER6 = 3,
+    MBOIT_POWER8 = 4
+} mboit_moment_set;
 /* Moment storage: power moments in float32; trigonometric moments normalised
  * by b0 (kept in float32) in float16 or bfloat16 (nearest-even rounding). */
 typedef enum { MBOIT_STORE_F32 = 0, MBOIT_STORE_F16 = 1, MBOIT_STORE_BF16 = 2 } mboit_storage;
@@ -125,7 +137,8 @@ typedef struct {
                                  * k < 2^22 is sampled (t exact in float32) */
     float moment_bias;          /* mix amount of the bias vector (Alg. 3 "mix"), in [0, 1); for
                                  * trigonometric moments the mix is with the uniform measure and
-                                 * must be >= 2e-3 (float16) / 2e-2 (bfloat16) */
+                                 * must be >= 2e-3 (float16) / 2e-2 (bfloat16); 6 and 8 power
+                                 * moments need it > 0 */
     float overestimation;       /* weight of the sample's own depth (Alg. 3), paper: 0.3 */
     float absorbance_max;       /* ABSORBANCE_MAX_VALUE of Alg. 2, > 0 */
     /* MBOIT_AMR (brick octree) only; `field` is then unused.  dims = finest
@@ -203,7 +216,9 @@ typedef struct {
 /* Message of the last failing call on this thread ("" if none). */
 MBOIT_API const char* mboit_last_error(void);
 
-/* Bytes of one moment slab for a width x height image (20 * P, P = w*h rounded up to 4). */
+/* Bytes of one moment slab for a width x height image (P = w*h rounded up to
+ * 4): 20 P, 28 P or 36 P for 4, 6 or 8 power moments (float32), (4 + 4 n) P
+ * for n complex trigonometric moments (16-bit); 0 for an invalid pair. */
 MBOIT_API size_t mboit_moment_image_bytes(int32_t width, int32_t height, int32_t moment_set, int32_t storage);
 
 /* Creates a volume on the current CUDA device.  Validates the descriptor,

@@ -22,9 +22,10 @@ MBOIT_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "UNSUPPORTED", 5: "STATE",
                 6: "TIMEOUT", 7: "DEVICE_ASSERT"}
 MBOIT_GRID, MBOIT_AMR, MBOIT_TET = 0, 1, 2
-MBOIT_POWER4, MBOIT_TRIG6, MBOIT_TRIG8 = 0, 1, 2
+MBOIT_POWER4, MBOIT_TRIG6, MBOIT_TRIG8, MBOIT_POWER6, MBOIT_POWER8 = 0, 1, 2, 3, 4
 MBOIT_STORE_F32, MBOIT_STORE_F16, MBOIT_STORE_BF16 = 0, 1, 2
-MOMENT_SET_IDS = {"power4": MBOIT_POWER4, "trig6": MBOIT_TRIG6, "trig8": MBOIT_TRIG8}
+MOMENT_SET_IDS = {"power4": MBOIT_POWER4, "trig6": MBOIT_TRIG6, "trig8": MBOIT_TRIG8, "power6": MBOIT_POWER6,
+                  "power8": MBOIT_POWER8}
 STORAGE_IDS = {"f32": MBOIT_STORE_F32, "f16": MBOIT_STORE_F16, "bf16": MBOIT_STORE_BF16}
 MBOIT_ORTHO, MBOIT_PERSPECTIVE = 0, 1
 MBOIT_PACKET_8X4, MBOIT_PACKET_4X8 = 0, 1

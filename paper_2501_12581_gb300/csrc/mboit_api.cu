@@ -116,6 +116,7 @@ constexpr double kTrigZone = 0.1;  // wrapping zone: phi = z (1 - zeta) pi
 void fill_trig(mb::TrigTables& T, int32_t moment_set, int32_t storage, float beta) {
     std::memset(&T, 0, sizeof T);
     T.n = moment_set == MBOIT_TRIG6 ? 3 : moment_set == MBOIT_TRIG8 ? 4 : 0;
+    T.sel = T.n ? T.n : moment_set == MBOIT_POWER6 ? 6 : moment_set == MBOIT_POWER8 ? 8 : 0;
     T.storage = storage;
     T.beta = beta;
     T.zone_scale = (float)((1.0 - kTrigZone) * 3.14159265358979323846);
@@ -142,8 +143,16 @@ void fill_trig(mb::TrigTables& T, int32_t moment_set, int32_t storage, float bet
     }
 }
 
+bool is_trig(int32_t moment_set) { return moment_set == MBOIT_TRIG6 || moment_set == MBOIT_TRIG8; }
+
 int64_t slab_bytes_per_px(int32_t moment_set) {
-    return moment_set == MBOIT_TRIG6 ? 16 : moment_set == MBOIT_TRIG8 ? 20 : 20;
+    switch (moment_set) {
+        case MBOIT_TRIG6: return 16;
+        case MBOIT_TRIG8: return 20;
+        case MBOIT_POWER6: return 28;
+        case MBOIT_POWER8: return 36;
+        default: return 20;
+    }
 }
 
 template <class T>
@@ -492,9 +501,9 @@ const char* mboit_last_error(void) { return g_err.c_str(); }
 
 size_t mboit_moment_image_bytes(int32_t width, int32_t height, int32_t moment_set, int32_t storage) {
     if (width < 1 || height < 1) return 0;
-    const bool power = moment_set == MBOIT_POWER4 && storage == MBOIT_STORE_F32;
-    const bool trig = (moment_set == MBOIT_TRIG6 || moment_set == MBOIT_TRIG8) &&
-                      (storage == MBOIT_STORE_F16 || storage == MBOIT_STORE_BF16);
+    const bool power = (moment_set == MBOIT_POWER4 || moment_set == MBOIT_POWER6 || moment_set == MBOIT_POWER8) &&
+                       storage == MBOIT_STORE_F32;
+    const bool trig = is_trig(moment_set) && (storage == MBOIT_STORE_F16 || storage == MBOIT_STORE_BF16);
     if (!power && !trig) return 0;
     const size_t P = (((size_t)width * (size_t)height) + 3) / 4 * 4;
     return (size_t)slab_bytes_per_px(moment_set) * P;
@@ -507,12 +516,14 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
         return fail(MBOIT_ERR_UNSUPPORTED, "unknown volume kind");
     const bool is_amr = d->kind == MBOIT_AMR;
     const bool is_tet = d->kind == MBOIT_TET;
-    if (d->moment_set < MBOIT_POWER4 || d->moment_set > MBOIT_TRIG8) return fail(MBOIT_ERR_UNSUPPORTED, "unknown moment set");
-    if (d->moment_set == MBOIT_POWER4 && d->storage != MBOIT_STORE_F32)
+    if (d->moment_set < MBOIT_POWER4 || d->moment_set > MBOIT_POWER8) return fail(MBOIT_ERR_UNSUPPORTED, "unknown moment set");
+    if (!is_trig(d->moment_set) && d->storage != MBOIT_STORE_F32)
         return fail(MBOIT_ERR_UNSUPPORTED, "power moments are stored in float32");
-    if (d->moment_set != MBOIT_POWER4 && d->storage != MBOIT_STORE_F16 && d->storage != MBOIT_STORE_BF16)
+    if (is_trig(d->moment_set) && d->storage != MBOIT_STORE_F16 && d->storage != MBOIT_STORE_BF16)
         return fail(MBOIT_ERR_UNSUPPORTED, "trigonometric moments are stored in float16 or bfloat16");
-    if (d->moment_set != MBOIT_POWER4 &&
+    if ((d->moment_set == MBOIT_POWER6 || d->moment_set == MBOIT_POWER8) && !(d->moment_bias > 0.0f))
+        return fail(MBOIT_ERR_INVALID_ARG, "6 and 8 power moments need moment_bias > 0");
+    if (is_trig(d->moment_set) &&
         !(d->moment_bias >= (d->storage == MBOIT_STORE_F16 ? 2e-3f : 2e-2f)))
         return fail(MBOIT_ERR_INVALID_ARG, "trigonometric moments in 16 bits need moment_bias >= 2e-3 (float16) or "
                                            ">= 2e-2 (bfloat16) to keep the stored Toeplitz matrices positive definite");

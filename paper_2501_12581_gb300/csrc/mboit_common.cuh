@@ -13,6 +13,7 @@
 #include <cuda_fp16.h>
 
 #include "mboit_internal.h"
+#include "mboit_power.cuh"
 #include "mboit_trig.cuh"
 
 namespace mb {
@@ -187,7 +188,7 @@ struct BlendBody {
 
 // Bytes of one moment slab of P pixels in the volume's format.
 __device__ __forceinline__ int64_t slab_bytes(const GridD& g, int plane) {
-    return g.trig.n ? (int64_t)(4 + 4 * g.trig.n) * plane : (int64_t)20 * plane;
+    return g.trig.n ? (int64_t)(4 + 4 * g.trig.n) * plane : (int64_t)(4 + 4 * (g.trig.sel ? g.trig.sel : 4)) * plane;
 }
 
 __device__ __forceinline__ uint32_t pack16(const GridD& g, float x, float y) {
@@ -289,6 +290,90 @@ struct TrigBlendBody {
     __device__ __forceinline__ bool singular() const { return b0 > 0.0f && F.n == 0; }
 };
 
+// Slab of 2N power moments: b0 plane (float), the float4 plane of b1..b4,
+// then b5, b6 (float2 plane, N = 3) or b5..b8 (float4 plane, N = 4).
+template <int N>
+__device__ __forceinline__ void store_power(char* base, const ViewSlot& S, int64_t slab_off, int pix, const float* m) {
+    char* slab = base + slab_off;
+    reinterpret_cast<float*>(slab)[pix] = m[0];
+    reinterpret_cast<float4*>(slab + (size_t)4 * S.plane)[pix] = make_float4(m[1], m[2], m[3], m[4]);
+    if constexpr (N == 3)
+        reinterpret_cast<float2*>(slab + (size_t)20 * S.plane)[pix] = make_float2(m[5], m[6]);
+    else
+        reinterpret_cast<float4*>(slab + (size_t)20 * S.plane)[pix] = make_float4(m[5], m[6], m[7], m[8]);
+}
+
+template <int N>
+__device__ __forceinline__ void load_power(const char* base, const ViewSlot& S, int64_t slab_off, int pix, float* m) {
+    const char* slab = base + slab_off;
+    m[0] = __ldg(reinterpret_cast<const float*>(slab) + pix);
+    const float4 q = __ldg(reinterpret_cast<const float4*>(slab + (size_t)4 * S.plane) + pix);
+    m[1] = q.x; m[2] = q.y; m[3] = q.z; m[4] = q.w;
+    if constexpr (N == 3) {
+        const float2 r = __ldg(reinterpret_cast<const float2*>(slab + (size_t)20 * S.plane) + pix);
+        m[5] = r.x; m[6] = r.y;
+    } else {
+        const float4 r = __ldg(reinterpret_cast<const float4*>(slab + (size_t)20 * S.plane) + pix);
+        m[5] = r.x; m[6] = r.y; m[7] = r.z; m[8] = r.w;
+    }
+}
+
+// Pass 1 with 2N power moments: b_j += a z^j, j = 0..2N (Alg. 2).
+template <int N>
+struct PowerMomentBody {
+    const float2* s_sig;
+    float tf_scale, tf_bias, amax, wa, wb;
+    float m[2 * N + 1];
+    unsigned n = 0;
+    __device__ __forceinline__ void operator()(float t, float val) {
+        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+        const int i = (int)xt;
+        const float f = xt - (float)i;
+        const float2 s = s_sig[i];
+        const float a = fmin_(ffma(f, s.y, s.x), amax);
+        const float z = warp_depth(t, wa, wb);
+        m[0] += a;
+        float p = a;
+#pragma unroll
+        for (int j = 1; j <= 2 * N; ++j) {
+            m[j] = ffma(p, z, m[j]);
+            if (j < 2 * N) p *= z;
+        }
+        ++n;
+    }
+    __device__ __forceinline__ void store(const GridD&, char* base, const ViewSlot& S, int64_t off, int pix) {
+        store_power<N>(base, S, off, pix, m);
+    }
+};
+
+// Pass 2 with 2N power moments.
+template <int N>
+struct PowerBlendBody {
+    const float4* s_tf;
+    PowerFrame<N> F;
+    float tf_scale, tf_bias, amax, wa, wb, w0;
+    float b0;
+    float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    unsigned n = 0;
+    __device__ __forceinline__ void operator()(float t, float val) {
+        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+        const int i = (int)xt;
+        const float f = xt - (float)i;
+        const float4 e0 = s_tf[2 * i], de = s_tf[2 * i + 1];
+        const float a = fmin_(ffma(f, de.w, e0.w), amax);
+        const float alpha = one_minus_exp_neg(a);
+        const float z = warp_depth(t, wa, wb);
+        const float A = power_fraction<N>(F, z, w0);
+        const float wgt = fclamp(fexp2(-F.m0_log2e * A), 0.0f, 1.0f) * alpha;
+        C.x = ffma(wgt, ffma(f, de.x, e0.x), C.x);
+        C.y = ffma(wgt, ffma(f, de.y, e0.y), C.y);
+        C.z = ffma(wgt, ffma(f, de.z, e0.z), C.z);
+        C.w += wgt;
+        ++n;
+    }
+    __device__ __forceinline__ bool singular() const { return F.kind == kFrameFourMoments; }
+};
+
 template <int MS> struct Bodies;
 template <> struct Bodies<0> {
     using Moment = MomentBody;
@@ -302,6 +387,14 @@ template <> struct Bodies<4> {
     using Moment = TrigMomentBody<4>;
     using Blend = TrigBlendBody<4>;
 };
+template <> struct Bodies<6> {
+    using Moment = PowerMomentBody<3>;
+    using Blend = PowerBlendBody<3>;
+};
+template <> struct Bodies<8> {
+    using Moment = PowerMomentBody<4>;
+    using Blend = PowerBlendBody<4>;
+};
 
 template <int MS>
 __device__ __forceinline__ typename Bodies<MS>::Moment make_moment_body(const float2* s_sig, const GridD& g,
@@ -313,10 +406,12 @@ __device__ __forceinline__ typename Bodies<MS>::Moment make_moment_body(const fl
     b.amax = g.absorbance_max;
     b.wa = v.warp_a;
     b.wb = v.warp_b;
-    if constexpr (MS != 0) {
+    if constexpr (MS == 3 || MS == 4) {
         b.zs = g.trig.zone_scale;
         for (int j = 0; j < MS; ++j) b.t[j] = {0.0f, 0.0f};
     }
+    if constexpr (MS == 6 || MS == 8)
+        for (int j = 0; j <= MS; ++j) b.m[j] = 0.0f;
     return b;
 }
 
@@ -337,6 +432,12 @@ __device__ __forceinline__ typename Bodies<MS>::Blend make_blend_body(const floa
         float m[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         if (valid) load_moments(moments, S, off, pix, m);
         b.F = make_frame(m, g.moment_bias, g.bias_vector);
+        b.b0 = m[0];
+    } else if constexpr (MS == 6 || MS == 8) {
+        float m[MS + 1];
+        for (int j = 0; j <= MS; ++j) m[j] = 0.0f;
+        if (valid) load_power<MS / 2>(moments, S, off, pix, m);
+        b.F = make_power_frame<MS / 2>(m, g.moment_bias);
         b.b0 = m[0];
     } else {
         cf tau[MS];

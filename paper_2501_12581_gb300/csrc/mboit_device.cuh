@@ -138,6 +138,8 @@ struct TrigTables {
     float beta;
     int32_t n;            // 3 or 4 complex moments (0: power moments)
     int32_t storage;      // 1 float16, 2 bfloat16
+    int32_t sel;          // kernel variant: 0 four power moments, 3 / 4 trigonometric, 6 / 8 power moments
+    int32_t pad;
 };
 
 struct GridD {

@@ -332,7 +332,8 @@ cudaError_t launch_moments_sum(const GridD& g, const ViewTable& vt, int32_t n_in
                 k_moments_sum_trig<4><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(g, src, dst, S.plane, npix, n_inputs);
             continue;
         }
-        const int64_t n4 = (int64_t)5 * S.plane / 4;
+        // power moments: 2n + 1 float planes (plane is a multiple of 4 pixels)
+        const int64_t n4 = (int64_t)(1 + (g.trig.sel ? g.trig.sel : 4)) * S.plane / 4;
         const float4* src = reinterpret_cast<const float4*>(static_cast<const char*>(in) + S.moment_off * n_inputs);
         float4* dst = reinterpret_cast<float4*>(static_cast<char*>(out) + S.moment_off);
         const int blocks = (int)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096);

@@ -1,0 +1,646 @@
+// Kernel templates of the octree and tetrahedral-mesh passes and of the plain
+// per-piece and sort-last marches of every volume kind (sm_103a), shared by
+// mboit_units.cu (launchers; four power and trigonometric moments) and
+// mboit_units_power.cu (the 6- and 8-power-moment instantiations, compiled in
+// parallel).  Internal: an unnamed namespace per translation unit.
+//
+// The fused octree / mesh passes are persistent like the grid's (one warp =
+// one 8 x 4 ray tile from the work queue); the octree finds each lattice
+// point's leaf in a finest-brick map, the mesh walks between face neighbours
+// with exact predicates.  The per-piece kernels are the plain form: one
+// launch per piece, rays clipped to the piece's box, non-owned units skipped,
+// one image per piece.
+#pragma once
+#include "mboit_common.cuh"
+
+namespace mb {
+namespace {
+
+// ------------------------------------------------------------------------
+// plain per-piece passes
+
+// Sampling units: the bricks of a grid or the leaves of an octree.  For a
+// point inside the domain: its unit (-1: none), the trilinear value there,
+// and the unit's box (for skipping units a piece does not own).
+__device__ __forceinline__ const GridD& common(const GridD& g) { return g; }
+__device__ __forceinline__ const GridD& common(const AmrD& a) { return a.g; }
+__device__ __forceinline__ const GridD& common(const TetD& m) { return m.g; }
+
+__device__ __forceinline__ int unit_of(const GridD& g, const float p[3]) {
+    const int ix = (int)p[0], iy = (int)p[1], iz = (int)p[2];
+    return ((iz >> g.brick_log2) * g.nby + (iy >> g.brick_log2)) * g.nbx + (ix >> g.brick_log2);
+}
+
+__device__ __forceinline__ float unit_value(const GridD& g, const float p[3], int) {
+    const int ix = (int)p[0], iy = (int)p[1], iz = (int)p[2];
+    const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * (size_t)g.ny;
+    const float* __restrict__ c = g.field + (size_t)iz * sz + (size_t)iy * sy + (size_t)ix;
+    return trilinear8(__ldg(c), __ldg(c + 1), __ldg(c + sy), __ldg(c + sy + 1), __ldg(c + sz), __ldg(c + sz + 1),
+                      __ldg(c + sz + sy), __ldg(c + sz + sy + 1), p[0] - (float)ix, p[1] - (float)iy, p[2] - (float)iz);
+}
+
+__device__ __forceinline__ void unit_box(const GridD& g, const float p[3], int, float lo[3], float& size) {
+    size = (float)(1 << g.brick_log2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) lo[c] = floorf(p[c] / size) * size;
+}
+
+__device__ __forceinline__ int unit_of(const AmrD& a, const float p[3]) {
+    const int bl = a.g.brick_log2;
+    const int fx = (int)p[0] >> bl, fy = (int)p[1] >> bl, fz = (int)p[2] >> bl;
+    return __ldg(a.fmap + ((size_t)fz * a.fdim + fy) * (size_t)a.fdim + fx);
+}
+
+// Local coordinates (p - origin) / h are exact in float32 (h a power of two,
+// |p - origin| below the leaf size), so cells match the oracle's.
+__device__ __forceinline__ float unit_value(const AmrD& a, const float p[3], int leaf) {
+    const int4 L = __ldg(a.leaves + leaf);
+    const float inv_h = __int_as_float((127 - (a.max_level - L.w)) << 23);  // 2^-(max_level - level)
+    const float qx = (p[0] - (float)L.x) * inv_h, qy = (p[1] - (float)L.y) * inv_h, qz = (p[2] - (float)L.z) * inv_h;
+    const int cx = min((int)qx, a.nv - 2), cy = min((int)qy, a.nv - 2), cz = min((int)qz, a.nv - 2);
+    const int nv = a.nv;
+    const float* __restrict__ c = a.values + (size_t)leaf * nv * nv * nv + (cz * nv + cy) * nv + cx;
+    const int sy = nv, sz = nv * nv;
+    return trilinear8(__ldg(c), __ldg(c + 1), __ldg(c + sy), __ldg(c + sy + 1), __ldg(c + sz), __ldg(c + sz + 1),
+                      __ldg(c + sz + sy), __ldg(c + sz + sy + 1), qx - (float)cx, qy - (float)cy, qz - (float)cz);
+}
+
+__device__ __forceinline__ void unit_box(const AmrD& a, const float[3], int leaf, float lo[3], float& size) {
+    const int4 L = __ldg(a.leaves + leaf);
+    size = (float)((1 << a.g.brick_log2) << (a.max_level - L.w));
+    lo[0] = (float)L.x;
+    lo[1] = (float)L.y;
+    lo[2] = (float)L.z;
+}
+
+// Next lattice index worth testing after point k fell in a unit the piece
+// does not own: the ray's exit from that unit's box, pulled back by a
+// padding that covers float32 position rounding, and by one lattice step.
+template <class V>
+__device__ __forceinline__ int skip_unit(const V& vol, int unit, const float o[3], const float d[3], float t, int k) {
+    const GridD& g = common(vol);
+    const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+    float lo[3], size;
+    unit_box(vol, p, unit, lo, size);
+    float t_exit = 3.0e38f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (d[c] == 0.0f) continue;
+        const float face = d[c] > 0.0f ? lo[c] + size : lo[c];
+        const float inv = 1.0f / d[c];
+        const float tc = (face - o[c]) * inv;
+        const float pad = (fabsf(o[c]) + fabsf(face) + 1.0f) * 3.814697265625e-06f * fabsf(inv);
+        t_exit = fmin_(t_exit, tc - pad);
+    }
+    const float kn = ceilf(t_exit / g.step - 0.5f) - 1.0f;
+    if (!(kn > (float)(k + 1))) return k + 1;
+    return kn > 4194303.0f ? 4194304 : (int)kn;
+}
+
+// Per-ray state of a sampler: none for grids and octrees (a point's unit is
+// a table lookup), the current tet for meshes (the walk starts there).
+struct NoWalk {};
+struct TetWalk;
+template <class V> struct WalkOf { using type = NoWalk; };
+template <bool kNarrow> struct WalkOf<TetT<kNarrow>> { using type = TetWalk; };
+
+// One owned sample of `piece` at lattice index k, or the next index to try.
+template <class V>
+__device__ __forceinline__ bool piece_sample(const V& vol, const int32_t* __restrict__ pou, int piece, float t,
+                                             const float o[3], const float d[3], int k, float& val, int& k_next,
+                                             NoWalk&) {
+    const GridD& g = common(vol);
+    k_next = k + 1;
+    const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+    if (!(p[0] >= 0.0f && p[0] < g.hx && p[1] >= 0.0f && p[1] < g.hy && p[2] >= 0.0f && p[2] < g.hz)) return false;
+    const int u = unit_of(vol, p);
+    if (u < 0) return false;
+    if (__ldg(pou + u) != piece) {
+        k_next = skip_unit(vol, u, o, d, t, k);
+        return false;
+    }
+    val = unit_value(vol, p, u);
+    return true;
+}
+
+template <class V, int MS>
+__global__ void __launch_bounds__(128) k_pass1_piece(const __grid_constant__ V vol, const float4* __restrict__ tf,
+                                                     const int32_t* __restrict__ pob, int piece,
+                                                     const __grid_constant__ PieceBox box,
+                                                     const __grid_constant__ ViewTable vt, int slot, int n_slots,
+                                                     char* __restrict__ moments, Counters* __restrict__ ctr) {
+    const GridD& g = common(vol);
+    __shared__ float2 s_sig[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const float s0 = tf[i].w;
+        s_sig[i] = make_float2(s0, i < 255 ? tf[i + 1].w - s0 : 0.0f);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tile >= vt.total_tiles) return;
+    const int vi = find_view(vt, tile);
+    const ViewSlot& S = vt.s[vi];
+    const int lt = tile - S.tile_base;
+    int px, py;
+    tile_pixel(S, lt, lane, px, py);
+    unsigned n = 0;
+    if (px < S.v.width && py < S.v.height) {
+        auto body = make_moment_body<MS>(s_sig, g, S.v);
+        float o[3], d[3];
+        make_ray(S.v, px, py, o, d);
+        int k0, k1;
+        if (lattice_range(o, d, box.lo, box.hi, g.step, &k0, &k1)) {
+            typename WalkOf<V>::type walk;
+            for (int k = k0; k <= k1;) {
+                const float t = lattice_t(k, g.step);
+                float val;
+                int kn;
+                const bool owned = piece_sample(vol, pob, piece, t, o, d, k, val, kn, walk);
+                k = kn;
+                if (owned) body(t, val);
+            }
+        }
+        n = body.n;
+        body.store(g, moments, S, S.moment_off * n_slots + slot * slab_bytes(g, S.plane), py * S.v.width + px);
+    }
+    warp_add_u64(&ctr->samples[0], n);
+}
+
+template <class V, int MS>
+__global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ V vol, const float4* __restrict__ tf,
+                                                     const int32_t* __restrict__ pob, int piece,
+                                                     const __grid_constant__ PieceBox box,
+                                                     const __grid_constant__ ViewTable vt, int slot, int n_slots,
+                                                     const char* __restrict__ moments, float* __restrict__ color,
+                                                     Counters* __restrict__ ctr) {
+    const GridD& g = common(vol);
+    __shared__ float4 s_tf[512];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const float4 e0 = tf[i], e1 = i < 255 ? tf[i + 1] : tf[i];
+        s_tf[2 * i] = e0;
+        s_tf[2 * i + 1] = make_float4(e1.x - e0.x, e1.y - e0.y, e1.z - e0.z, e1.w - e0.w);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tile >= vt.total_tiles) return;
+    const int vi = find_view(vt, tile);
+    const ViewSlot& S = vt.s[vi];
+    const int lt = tile - S.tile_base;
+    int px, py;
+    tile_pixel(S, lt, lane, px, py);
+    unsigned n = 0;
+    if (px < S.v.width && py < S.v.height) {
+        const int pix = py * S.v.width + px;
+        float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float o[3], d[3];
+        make_ray(S.v, px, py, o, d);
+        int k0, k1;
+        if (lattice_range(o, d, box.lo, box.hi, g.step, &k0, &k1)) {
+            auto body = make_blend_body<MS>(s_tf, g, S, moments, S.moment_off, pix, true);
+            typename WalkOf<V>::type walk;
+            for (int k = k0; k <= k1;) {
+                const float t = lattice_t(k, g.step);
+                float val;
+                int kn;
+                const bool owned = piece_sample(vol, pob, piece, t, o, d, k, val, kn, walk);
+                k = kn;
+                if (owned) body(t, val);
+            }
+            C = body.C;
+            n = body.n;
+        }
+        const int64_t img = (int64_t)4 * S.v.width * S.v.height;
+        reinterpret_cast<float4*>(color + S.color_off * n_slots + slot * img)[pix] = C;
+    }
+    warp_add_u64(&ctr->samples[1], n);
+}
+
+// ------------------------------------------------------------------------
+// tetrahedral meshes: exact point location.  A point snaps to integer
+// quanta; D_i(q), six times the signed volume of the tet with corner i
+// replaced by q, is n_i . (q - b_i) with n_i the cross product of two edges
+// of face i and b_i a corner of it.  All of it is exact in 64-bit integers
+// (the volume checks the coordinate range), so the two tets of a face see
+// exactly opposite signs; a zero is decided by the symbolic perturbation
+// q + (e, e^2, e^3): the sign of n_i.x, then n_i.y, then n_i.z.
+
+__device__ __forceinline__ void snap_point(const TetD& m, const float p[3], int q[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) q[c] = __float2int_rn(fmul(p[c], m.qscale));
+}
+
+// Sign of D for face (a, b) around `base` at q, D itself in D.  Narrow:
+// edges below 2^15 quanta, so the normal's components fit in 32 bits and D
+// is three 32 x 32 -> 64-bit multiply-adds.
+template <bool kNarrow>
+__device__ __forceinline__ bool face_positive(const int4 a, const int4 b, const int4 base, const int q[3],
+                                              long long& D) {
+    const int ax = a.x - base.x, ay = a.y - base.y, az = a.z - base.z;
+    const int bx = b.x - base.x, by = b.y - base.y, bz = b.z - base.z;
+    const int dx = q[0] - base.x, dy = q[1] - base.y, dz = q[2] - base.z;
+    long long nx, ny, nz;
+    if (kNarrow) {
+        const int n0 = ay * bz - az * by, n1 = az * bx - ax * bz, n2 = ax * by - ay * bx;
+        D = (long long)n0 * dx + (long long)n1 * dy + (long long)n2 * dz;
+        nx = n0;
+        ny = n1;
+        nz = n2;
+    } else {
+        nx = (long long)ay * bz - (long long)az * by;
+        ny = (long long)az * bx - (long long)ax * bz;
+        nz = (long long)ax * by - (long long)ay * bx;
+        D = nx * dx + ny * dy + nz * dz;
+    }
+    if (D != 0) return D > 0;
+    if (nx != 0) return nx > 0;
+    if (ny != 0) return ny > 0;
+    return nz > 0;
+}
+
+// D_0..D_3 of q; returns -1 if q is inside, else a face that q lies
+// strictly outside of (the first one from `rot`, so that walks do not
+// always prefer one face).  Face `skip` (-1: none) is known to pass, its D
+// already in D[skip].
+template <bool kNarrow>
+__device__ __forceinline__ int tet_exit_face(const int4 v[4], const int q[3], long long D[4], int rot, int skip) {
+    unsigned out = 0;  // bit i: q is outside face i
+    if (skip != 0 && !face_positive<kNarrow>(v[2], v[1], v[3], q, D[0])) out |= 1u;
+    if (skip != 1 && !face_positive<kNarrow>(v[2], v[3], v[0], q, D[1])) out |= 2u;
+    if (skip != 2 && !face_positive<kNarrow>(v[3], v[1], v[0], q, D[2])) out |= 4u;
+    if (skip != 3 && !face_positive<kNarrow>(v[1], v[2], v[0], q, D[3])) out |= 8u;
+    if (!out) return -1;
+    rot &= 3;
+    const unsigned r = ((out >> rot) | (out << (4 - rot))) & 15u;
+    return (rot + __ffs(r) - 1) & 3;
+}
+
+__device__ __forceinline__ int pick(const int4 a, int i) { return i == 0 ? a.x : i == 1 ? a.y : i == 2 ? a.z : a.w; }
+
+__device__ __forceinline__ int bin_of(const TetD& m, const int q[3]) {
+    int b[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) b[c] = min(max(q[c] >> m.bin_shift, 0), m.bdim[c] - 1);
+    return (b[2] * m.bdim[1] + b[1]) * m.bdim[0] + b[0];
+}
+
+// Per-ray walk state: the current tet, its neighbours and its corners
+// (snapped x, y, z, value bits).
+struct TetWalk {
+    int T = -1;
+    int4 nb;
+    int4 v[4];
+};
+
+__device__ __forceinline__ void load_tet(const TetD& m, int T, TetWalk& w) {
+    w.T = T;
+    w.nb = __ldg(m.nbrs + T);
+    const int4* c = m.corners + 4 * (size_t)T;
+    w.v[0] = __ldg(c);
+    w.v[1] = __ldg(c + 1);
+    w.v[2] = __ldg(c + 2);
+    w.v[3] = __ldg(c + 3);
+}
+
+// Tests the tets listed in q's bin one by one (the walk's fallback); on
+// success w holds the owner and D its volumes, else w is unchanged.
+template <bool kNarrow>
+__device__ __forceinline__ bool tet_search(const TetD& m, TetWalk& w, const int q[3], long long D[4]) {
+    const int b = bin_of(m, q);
+    const int j1 = __ldg(m.bin_start + b + 1);
+    for (int j = __ldg(m.bin_start + b); j < j1; ++j) {
+        TetWalk u;
+        load_tet(m, __ldg(m.bin_tets + j), u);
+        if (tet_exit_face<kNarrow>(u.v, q, D, 0, -1) < 0) {
+            w = u;
+            return true;
+        }
+    }
+    return false;
+}
+
+// Finds the tet owning q.  The walk starts at w.T (the tet of the previous
+// sample; -1: the first tet listed in q's bin) and crosses a face that q is
+// outside of, at most max_walk times; after a crossing the entry face is
+// known to pass (its D is the exact negative of the exit face's).  If the
+// walk leaves the mesh or runs long, the tets listed in q's bin are tested
+// one by one.  On success w holds the owner and D its four volumes at q; on
+// failure (no tet owns q) w still holds one tet near q.
+template <bool kNarrow>
+__device__ __forceinline__ bool tet_walk(const TetD& m, TetWalk& w, const int q[3], long long D[4]) {
+    if (w.T < 0) {
+        const int b = bin_of(m, q);
+        const int j0 = __ldg(m.bin_start + b);
+        if (j0 == __ldg(m.bin_start + b + 1)) return false;  // no tet comes near q
+        load_tet(m, __ldg(m.bin_tets + j0), w);
+    }
+    int skip = -1;
+    for (int step = 0;; ++step) {
+        const int f = tet_exit_face<kNarrow>(w.v, q, D, step, skip);
+        if (f < 0) return true;
+        if (step + 1 >= m.max_walk) break;
+        const int nt = pick(w.nb, f);
+        if (nt < 0) break;
+        const int from = w.T;
+        const long long Df = f == 0 ? D[0] : f == 1 ? D[1] : f == 2 ? D[2] : D[3];
+        load_tet(m, nt, w);
+        skip = w.nb.x == from ? 0 : w.nb.y == from ? 1 : w.nb.z == from ? 2 : 3;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (skip == i) D[i] = -Df;
+    }
+    return tet_search<kNarrow>(m, w, q, D);
+}
+
+// 0 <= x < 2^23 as float, exactly: x is the mantissa of 2^23 + x.
+__device__ __forceinline__ float small_to_float(long long x) {
+    return __int_as_float(0x4b000000 | (int)x) - 8388608.0f;
+}
+
+// Barycentric interpolation of the corner values: lambda_i = D_i / sum D.
+// Inside a tet every D_i >= 0; all four are shifted right together until
+// the sum fits in 23 bits, so each weight is off by at most 2^-23 and no
+// 64-bit conversion (a double-precision-pipe instruction) is needed.
+__device__ __forceinline__ float tet_value(const long long D[4], const int4 v[4]) {
+    const long long tot = D[0] + D[1] + D[2] + D[3];
+    const int sh = max(0, 41 - __clzll(tot));
+    const float inv = 1.0f / small_to_float(tot >> sh);
+    float s = small_to_float(D[0] >> sh) * __int_as_float(v[0].w);
+    s = ffma(small_to_float(D[1] >> sh), __int_as_float(v[1].w), s);
+    s = ffma(small_to_float(D[2] >> sh), __int_as_float(v[2].w), s);
+    s = ffma(small_to_float(D[3] >> sh), __int_as_float(v[3].w), s);
+    return s * inv;
+}
+
+template <bool kNarrow>
+__device__ __forceinline__ bool piece_sample(const TetT<kNarrow>& m, const int32_t* __restrict__ pou, int piece,
+                                             float t, const float o[3], const float d[3], int k, float& val,
+                                             int& k_next, TetWalk& w) {
+    const GridD& g = m.g;
+    k_next = k + 1;
+    const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+    if (!(p[0] >= 0.0f && p[0] < g.hx && p[1] >= 0.0f && p[1] < g.hy && p[2] >= 0.0f && p[2] < g.hz)) return false;
+    int q[3];
+    snap_point(m, p, q);
+    long long D[4];
+    if (!tet_walk<kNarrow>(m, w, q, D)) return false;
+    if (__ldg(pou + w.T) != piece) return false;
+    val = tet_value(D, w.v);
+    return true;
+}
+
+// ------------------------------------------------------------------------
+// fused, persistent passes over a brick octree or a tetrahedral mesh
+// (direct gathers).  Octree: the leaf of each lattice point comes from the
+// finest-brick map, its value from the leaf's own vertex block.  Mesh: the
+// tet comes from a walk that starts at the previous sample's tet.
+
+// Batched march over a mesh.  One iteration is one tet test for every lane
+// of the warp: it either places the current lattice point (the sample is
+// taken, the next point comes up) or crosses a face towards it, so the
+// lanes stay together in the test and part only for the sample or the
+// crossing.  The owners are those of tet_walk: the same walk, the same
+// fallback.  `store` gets every lattice point's value (NaN: not sampled).
+template <bool kSel, class Body, bool kNarrow, class Store = NoStore>
+__device__ __forceinline__ void march_unit(const TetT<kNarrow>& m, const uint8_t* __restrict__ sel, const float o[3],
+                                           const float d[3], int k0, int k1, Body& body, Store store = Store{}) {
+    const GridD& g = m.g;
+    if (k0 > k1) return;
+    store.seek(k0);
+    const float tz = lattice_t(k1, g.step);
+    float t = lattice_t(k0, g.step);
+    int q[3];
+    {
+        const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+        snap_point(m, p, q);
+    }
+    TetWalk w;
+    {
+        const int b = bin_of(m, q);
+        const int j0 = __ldg(m.bin_start + b);
+        if (j0 < __ldg(m.bin_start + b + 1)) load_tet(m, __ldg(m.bin_tets + j0), w);
+    }
+    long long D[4];
+    int skip = -1, steps = 0;
+    while (t <= tz) {
+        const int f = w.T >= 0 ? tet_exit_face<kNarrow>(w.v, q, D, steps, skip) : -2;
+        if (f >= 0) {
+            const int nt = pick(w.nb, f);
+            if (nt >= 0 && steps + 1 < m.max_walk) {
+                const int from = w.T;
+                const long long Df = f == 0 ? D[0] : f == 1 ? D[1] : f == 2 ? D[2] : D[3];
+                load_tet(m, nt, w);
+                skip = w.nb.x == from ? 0 : w.nb.y == from ? 1 : w.nb.z == from ? 2 : 3;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (skip == i) D[i] = -Df;
+                ++steps;
+                continue;
+            }
+        }
+        const bool found = f == -1 || tet_search<kNarrow>(m, w, q, D);
+        float val = __int_as_float(0x7fc00000);
+        if (found && (!kSel || __ldg(sel + w.T))) {
+            val = tet_value(D, w.v);
+            body(t, val);
+        }
+        store.put(val);
+        t += g.step;
+        const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+        snap_point(m, p, q);
+        skip = -1;
+        steps = 0;
+    }
+}
+
+template <bool kSel, class Body, class Store = NoStore>
+__device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restrict__ sel, const float o[3],
+                                           const float d[3], int k0, int k1, Body& body, Store store = Store{}) {
+    const GridD& g = a.g;
+    if (k0 > k1) return;
+    store.seek(k0);
+    const float tz = lattice_t(k1, g.step);
+    for (float t = lattice_t(k0, g.step); t <= tz; t += g.step) {
+        const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+        const int u = unit_of(a, p);
+        if (u < 0 || (kSel && !__ldg(sel + u))) {
+            store.put(__int_as_float(0x7fc00000));
+            continue;
+        }
+        const float val = unit_value(a, p, u);
+        store.put(val);
+        body(t, val);
+    }
+}
+
+// Resident 256-thread blocks per SM the unit kernels are compiled for (the
+// walks and gathers are latency-bound: more warps hide more of it); the
+// trigonometric and 6-/8-power-moment bodies get 2, so that they keep their
+// registers.
+#ifndef MB_TET_MIN_BLOCKS
+#define MB_TET_MIN_BLOCKS 3
+#endif
+template <class V, int kPass> struct MinBlocks { static constexpr int value = kPass == 2 ? 4 : 1; };
+template <bool k, int kPass> struct MinBlocks<TetT<k>, kPass> { static constexpr int value = MB_TET_MIN_BLOCKS; };
+
+template <class V, bool kSel, int MS, bool kCache = false>
+__global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 1>::value : 2) k_pass1_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
+                                                    const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
+                                                    char* __restrict__ moments, Counters* __restrict__ ctr,
+                                                    const TileCache cache) {
+    __shared__ float2 s_sig[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const float s0 = tf[i].w;
+        s_sig[i] = make_float2(s0, i < 255 ? tf[i + 1].w - s0 : 0.0f);
+    }
+    __syncthreads();
+    const GridD& g = a.g;
+    int vi, px, py, tile;
+    while (next_tile(vt, &ctr->tile_next[0], vi, px, py, tile)) {
+        const ViewSlot& S = vt.s[vi];
+        const bool valid = px < S.v.width && py < S.v.height;
+        float o[3], d[3];
+        int k0, k1;
+        ray_range(g, S.v, valid, px, py, o, d, k0, k1);
+        auto body = make_moment_body<MS>(s_sig, g, S.v);
+        if constexpr (kCache) {
+            RowStore st{tile_rows(cache, ctr, tile, k0, k1)};
+            march_unit<kSel>(a, sel, o, d, k0, k1, body, st);
+        } else {
+            march_unit<kSel>(a, sel, o, d, k0, k1, body);
+        }
+        if (valid) body.store(g, moments, S, S.moment_off, py * S.v.width + px);
+        warp_add_u64(&ctr->samples[0], body.n);
+    }
+}
+
+template <class V, bool kSel, int MS, bool kCache = false>
+__global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 2>::value : 2) k_pass2_unit(const __grid_constant__ V a, const float4* __restrict__ tf,
+                                                    const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
+                                                    const char* __restrict__ moments, float* __restrict__ color, int mode,
+                                                    Counters* __restrict__ ctr, const TileCache cache) {
+    __shared__ float4 s_tf[512];
+    __shared__ __align__(16) float s_rows[kCache ? kFusedWarps : 1][kCache ? kRowBuf : 4];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const float4 e0 = tf[i], e1 = i < 255 ? tf[i + 1] : tf[i];
+        s_tf[2 * i] = e0;
+        s_tf[2 * i + 1] = make_float4(e1.x - e0.x, e1.y - e0.y, e1.z - e0.z, e1.w - e0.w);
+    }
+    __syncthreads();
+    const GridD& g = a.g;
+    const bool raw = (g.flags & 1u) != 0;
+    int vi, px, py, tile;
+    while (next_tile(vt, &ctr->tile_next[1], vi, px, py, tile)) {
+        const ViewSlot& S = vt.s[vi];
+        const bool valid = px < S.v.width && py < S.v.height;
+        const int pix = valid ? py * S.v.width + px : 0;
+        auto body = make_blend_body<MS>(s_tf, g, S, moments, S.moment_off, pix, valid);
+        if (valid && body.singular()) atomicAdd(&ctr->singular, 1ull);
+        float o[3], d[3];
+        int k0, k1;
+        ray_range(g, S.v, valid, px, py, o, d, k0, k1);
+        const long long tb = kCache ? cache.tile_base[tile] : -1;
+        if (kCache && tb >= 0) {
+            const int kmin = __reduce_min_sync(0xffffffffu, k0), kmax = __reduce_max_sync(0xffffffffu, k1);
+            march_rows<true>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, s_rows[kCache ? threadIdx.x >> 5 : 0], body);
+        } else {
+            march_unit<kSel>(a, sel, o, d, k0, k1, body);
+        }
+        if (valid) {
+            float4* out = reinterpret_cast<float4*>(color + S.color_off) + pix;
+            *out = mode == kColorResolved ? resolve_pixel(body.C, body.b0, make_float4(0.0f, 0.0f, 0.0f, 0.0f), raw)
+                                          : body.C;
+        }
+        warp_add_u64(&ctr->samples[1], body.n);
+    }
+}
+
+// ------------------------------------------------------------------------
+// GPU exact sort-last baseline (the segment-layer compositor of Sec. 5).
+// Every piece, like a rank, turns each maximal run of consecutive lattice
+// points it owns into one segment (front-to-back "over" inside the run:
+// premultiplied colour and opacity, keyed by the run's first lattice index);
+// per pixel the segments of all pieces are sorted by that key and blended
+// front to back.  Counting and filling are separate marches so the segment
+// buffer can be sized exactly.
+
+template <class V, bool kFill>
+__global__ void __launch_bounds__(128) k_sortlast_piece(const __grid_constant__ V vol, const float4* __restrict__ tf,
+                                                        const int32_t* __restrict__ pob, int piece,
+                                                        const __grid_constant__ PieceBox box,
+                                                        const __grid_constant__ ViewTable vt, int slot, int n_slots,
+                                                        int32_t* __restrict__ counts, const int64_t* __restrict__ starts,
+                                                        int32_t* __restrict__ seg_key, float4* __restrict__ seg_col) {
+    const GridD& g = common(vol);
+    __shared__ float4 s_tf[256];
+    if (kFill) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tf[i] = tf[i];
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tile >= vt.total_tiles) return;
+    const int vi = find_view(vt, tile);
+    const ViewSlot& S = vt.s[vi];
+    const int lt = tile - S.tile_base;
+    int px, py;
+    tile_pixel(S, lt, lane, px, py);
+    if (px >= S.v.width || py >= S.v.height) return;
+    const int64_t npix = (int64_t)S.v.width * S.v.height;
+    const int64_t gpix = S.color_off / 4 + py * S.v.width + px;  // pixel index over all views
+    const int64_t cidx = (S.color_off / 4) * n_slots + slot * npix + (py * S.v.width + px);
+    float o[3], d[3];
+    make_ray(S.v, px, py, o, d);
+    int k0, k1;
+    int nseg = 0;
+    if (lattice_range(o, d, box.lo, box.hi, g.step, &k0, &k1)) {
+        int64_t out = kFill ? starts[cidx] : 0;
+        int prev = -2, key = 0;
+        float4 cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float tr = 1.0f;
+        typename WalkOf<V>::type walk;
+        for (int k = k0; k <= k1;) {
+            const float t = lattice_t(k, g.step);
+            float val;
+            int kn;
+            if (!piece_sample(vol, pob, piece, t, o, d, k, val, kn, walk)) {
+                k = kn;
+                continue;
+            }
+            if (k != prev + 1) {
+                if (kFill && nseg > 0) {
+                    seg_key[out] = key;
+                    seg_col[out] = make_float4(cur.x, cur.y, cur.z, 1.0f - tr);
+                    ++out;
+                }
+                ++nseg;
+                key = k;
+                cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                tr = 1.0f;
+            }
+            prev = k;
+            k = kn;
+            if (kFill) {
+                int i;
+                const float f = tf_coord(g, val, i);
+                const float4 e0 = s_tf[i], e1 = s_tf[i + 1];
+                const float a = fmin_(ffma(f, e1.w - e0.w, e0.w), g.absorbance_max);
+                const float w = tr * one_minus_exp_neg(a);
+                cur.x = ffma(w, ffma(f, e1.x - e0.x, e0.x), cur.x);
+                cur.y = ffma(w, ffma(f, e1.y - e0.y, e0.y), cur.y);
+                cur.z = ffma(w, ffma(f, e1.z - e0.z, e0.z), cur.z);
+                tr *= fexp2(-a * kLog2e);
+            }
+        }
+        if (kFill && nseg > 0) {
+            seg_key[out] = key;
+            seg_col[out] = make_float4(cur.x, cur.y, cur.z, 1.0f - tr);
+        }
+    }
+    if (!kFill) counts[cidx] = nseg;
+    (void)gpix;
+}
+
+}  // namespace
+}  // namespace mb

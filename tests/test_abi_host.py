@@ -44,6 +44,11 @@ def test_moment_image_bytes(lib):
     assert pkg.mboit_moment_image_bytes(7, 3) == 20 * 24       # plane rounded up to 4 pixels
     assert pkg.mboit_moment_image_bytes(0, 3) == 0
     assert pkg.mboit_moment_image_bytes(4, 4, moment_set=9) == 0
+    # 6 and 8 power moments: b0 plane, float4 plane of b1..b4, then a float2 / float4 plane
+    assert pkg.mboit_moment_image_bytes(7, 3, moment_set=pkg.MBOIT_POWER6) == 28 * 24
+    assert pkg.mboit_moment_image_bytes(7, 3, moment_set=pkg.MBOIT_POWER8) == 36 * 24
+    assert pkg.mboit_moment_image_bytes(7, 3, moment_set=pkg.MBOIT_POWER8, storage=pkg.MBOIT_STORE_F16) == 0
+    assert pkg.mboit_moment_image_bytes(7, 3, moment_set=pkg.MBOIT_TRIG6, storage=pkg.MBOIT_STORE_F16) == 16 * 24
 
 
 def _desc(**kw):
@@ -65,7 +70,9 @@ def _desc(**kw):
 
 @pytest.mark.parametrize("bad, status", [
     (dict(kind=7), 4),
-    (dict(moment_set=3), 4),
+    (dict(moment_set=5), 4),
+    (dict(moment_set=3, storage=1), 4),        # 6 power moments are float32
+    (dict(moment_set=4, moment_bias=0.0), 1),  # 8 power moments need a bias
     (dict(field=None), 1),
     (dict(brick_log2=9), 1),
     (dict(step=0.3), 1),
