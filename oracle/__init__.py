@@ -47,7 +47,7 @@ class _Grid(ctypes.Structure):
 class _Amr(ctypes.Structure):
     _fields_ = [("values", ctypes.c_void_p), ("leaves", ctypes.c_void_p), ("n_leaves", ctypes.c_int32),
                 ("max_level", ctypes.c_int32), ("finest_cells", ctypes.c_int32), ("brick_log2", ctypes.c_int32),
-                ("piece_of_leaf", ctypes.c_void_p), ("n_pieces", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("piece_of_leaf", ctypes.c_void_p), ("n_pieces", ctypes.c_int32), ("adaptive_step", ctypes.c_int32),
                 ("piece_selected", ctypes.c_void_p), ("tf", ctypes.c_void_p), ("vmin", ctypes.c_double),
                 ("vmax", ctypes.c_double), ("step", ctypes.c_double), ("moment_bias", ctypes.c_double),
                 ("overestimation", ctypes.c_double), ("absorbance_max", ctypes.c_double),
@@ -255,6 +255,7 @@ def _amr_struct(scene, pieces):
     a.values, a.leaves, a.n_leaves = keep["values"].ctypes.data, keep["leaves"].ctypes.data, scene.leaves.shape[0]
     a.max_level, a.finest_cells, a.brick_log2 = scene.max_level, scene.finest_cells, scene.brick_log2
     a.piece_of_leaf, a.n_pieces = keep["pol"].ctypes.data, K
+    a.adaptive_step = 1 if getattr(scene, "adaptive_step", False) else 0
     a.piece_selected = _ptr(keep["sel"])
     a.tf = keep["tf"].ctypes.data
     a.vmin, a.vmax = float(scene.tf_range[0]), float(scene.tf_range[1])

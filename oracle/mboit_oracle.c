@@ -683,7 +683,7 @@ static int locate_grid(const orc_grid* g, const float p[3], double* val)
 
 /* Octree: the leaf whose half-open box holds the point; local coordinates in
  * the leaf's cells; trilinear value of that cell's 8 vertices. */
-static int locate_amr(const vol_t* vol, const float p[3], double* val)
+static int locate_amr(const vol_t* vol, const float p[3], double* val, int* shift)
 {
     const orc_amr* a = vol->a;
     int64_t fb[3];
@@ -694,6 +694,7 @@ static int locate_amr(const vol_t* vol, const float p[3], double* val)
     if (piece < 0) return -1;
     const int32_t* L = a->leaves + 4 * (int64_t)leaf;
     double h = ldexp(1.0, a->max_level - L[3]);    /* finest cells per leaf cell */
+    *shift = a->max_level - L[3];
     int n = 1 << a->brick_log2, nv = n + 1;
     int cell[3];
     double f[3];
@@ -918,10 +919,20 @@ static int take_sample(const vol_t* g, const orc_view* V, const float o[3], cons
     for (int c = 0; c < 3; ++c)
         if (!(p[c] >= 0.0f && p[c] < (float)g->hi[c])) return 0;
     double val;
-    int piece = (g->kind == 0) ? locate_grid(g->g, p, &val) : (g->kind == 1) ? locate_amr(g, p, &val)
+    int shift = 0;
+    int piece = (g->kind == 0) ? locate_grid(g->g, p, &val) : (g->kind == 1) ? locate_amr(g, p, &val, &shift)
                                                                              : locate_tet_piece(g, p, &val);
     if (piece < 0) return 0;
     if (g->piece_selected && !g->piece_selected[piece]) return 0;
+    /* adaptive dyadic step (octrees): a leaf of level L samples the nested
+     * lattice of spacing 2^(max_level - L) steps, each sample standing for
+     * that longer interval */
+    double step_len = g->step;
+    if (g->kind == 1 && g->a->adaptive_step) {
+        int64_t stride = (int64_t)1 << shift;
+        if (((k % stride) + stride) % stride != 0) return 0;
+        step_len = g->step * (double)stride;
+    }
 
     /* transfer function: normalise, 256-entry linear lookup of (r, g, b, sigma) */
     double x = (val - g->vmin) / (g->vmax - g->vmin);
@@ -935,7 +946,7 @@ static int take_sample(const vol_t* g, const orc_view* V, const float o[3], cons
     double sigma = (1.0 - f) * sig_tab[i] + f * sig_tab[i + 1];
 
     /* Alg. 2: absorbance = -log(transmittance of the sample), clamped */
-    double a = sigma * g->step;
+    double a = sigma * step_len;
     if (a > g->absorbance_max) a = g->absorbance_max;
     s->k = k;
     s->piece = piece;

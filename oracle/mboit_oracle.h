@@ -49,7 +49,9 @@ typedef struct {
     int32_t finest_cells;          /* D: the domain is [0, D]^3 in finest-cell units */
     int32_t brick_log2;            /* a leaf is 2^brick_log2 cells of its level on a side */
     const int32_t* piece_of_leaf;  /* [n_leaves] */
-    int32_t n_pieces, reserved;
+    int32_t n_pieces;
+    int32_t adaptive_step;         /* 1: a lattice point in a leaf of level L counts only if k is a multiple
+                                      of 2^(max_level - L), with absorbance sigma * step * 2^(max_level - L) */
     const uint8_t* piece_selected; /* [n_pieces], NULL = every piece */
     const float* tf;
     double vmin, vmax, step, moment_bias, overestimation, absorbance_max;

@@ -305,6 +305,7 @@ class AmrScene:
     overestimation: float = 0.3
     absorbance_max: float = 10.0
     brick_log2: int = 3
+    adaptive_step: bool = False  # nested lattice of 2^(max_level - level) steps per leaf
 
     @property
     def dims(self):

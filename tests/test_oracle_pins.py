@@ -393,6 +393,77 @@ def test_amr_leaf_lookup_brute_force():
     assert hit > 30
 
 
+def test_amr_adaptive_step_brute_force():
+    """Adaptive dyadic step: a lattice point k in a leaf of level L counts
+    only if k is a multiple of 2^(max_level - L), with absorbance
+    sigma * step * 2^(max_level - L).  Each ray's sample count, b0 and b1
+    against the enumerated lattice points, the leaf found by testing every
+    box."""
+    import copy
+    amr, _ = small.linear_amr()
+    n = len(amr.leaves)
+    const = (np.arange(n) % 7) / 8.0 + 0.125
+    amr.values = np.broadcast_to(const[:, None, None, None], (n, 9, 9, 9)).astype(np.float32).copy()
+    amr.tf_range = (np.float32(0.0), np.float32(1.0))
+    amr = copy.copy(amr)
+    amr.adaptive_step = True
+    view = small.axis_view(amr.dims, 9, 7, -20.0, 60.0, w=(0.36, 0.48, 0.8), u=(0.8, -0.6, 0.0),
+                           v=(0.48, 0.64, -0.6), near=4.0, far=300.0, centre=(40.0, 44.0))
+    view.eye = np.array([30.0, 20.0, -20.0], np.float32)
+    r = oracle.render_amr(amr, view=view, want=("moments", "nsamples"))
+    size = (8 << amr.max_level) >> amr.leaves[:, 3]
+    lo, hi = amr.leaves[:, :3].astype(np.float64), amr.leaves[:, :3] + size[:, None]
+    hit = skipped = 0
+    for py in range(view.height):
+        for px in range(view.width):
+            S = _brute_samples(view, amr.dims, amr.step, px, py)
+            m0 = m1 = 0.0
+            count = 0
+            for t, p in S:
+                k = int(round(t / amr.step - 0.5))
+                inside = np.all((lo <= p) & (np.array(p) < hi), axis=1)
+                leaf = np.argmax(inside)
+                stride = 1 << (amr.max_level - int(amr.leaves[leaf, 3]))
+                if k % stride:
+                    skipped += 1
+                    continue
+                a = (0.04 + 0.2 * const[leaf]) * amr.step * stride
+                z = min(max(2 * math.log(t / 4.0) / math.log(300.0 / 4.0) - 1, -1), 1)
+                m0 += a
+                m1 += a * z
+                count += 1
+            idx = py * view.width + px
+            assert r["nsamples"][idx] == count
+            np.testing.assert_allclose(r["moments"][idx, :2], [m0, m1], rtol=2e-6, atol=1e-9)
+            hit += count > 0
+    assert hit > 30 and skipped > 100
+
+
+def test_amr_adaptive_step_single_level_and_pieces():
+    """With one level the nested lattice is the full one (adaptive = fixed,
+    bit for bit); on a three-level octree the pieces' moments still add up
+    to the global ones, the sort-last route still equals the exact blend of
+    the same samples, and fewer samples are taken."""
+    import copy
+    one = scenes.amr_blobs(base=4, max_level=0, width=24, height=20, n_pieces=3)
+    ad = copy.copy(one)
+    ad.adaptive_step = True
+    a = oracle.render_amr(ad, want=("moments", "mboit", "nsamples"))
+    f = oracle.render_amr(one, want=("moments", "mboit", "nsamples"))
+    np.testing.assert_array_equal(a["nsamples"], f["nsamples"])
+    np.testing.assert_array_equal(a["moments"], f["moments"])
+    np.testing.assert_array_equal(a["mboit"], f["mboit"])
+    sc = scenes.amr_blobs(base=4, max_level=2, width=32, height=28, n_pieces=5)
+    ad = copy.copy(sc)
+    ad.adaptive_step = True
+    r = oracle.render_amr(ad, want=("piece_moments", "moments", "exact", "sortlast", "nsamples"))
+    fixed = oracle.render_amr(sc, want=("nsamples",))
+    np.testing.assert_allclose(r["piece_moments"].sum(axis=1), r["moments"], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(r["sortlast"], r["exact"], atol=1e-12)
+    assert r["nsamples"].sum() < 0.8 * fixed["nsamples"].sum()
+    assert np.all(r["nsamples"] <= fixed["nsamples"])
+
+
 # --------------------------------------------------------------------------
 # trigonometric moments (Sec. 4.3, Fig. 3: "different moments")
 
