@@ -263,6 +263,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-piece", action="store_true")
     ap.add_argument("--no-sortlast", action="store_true")
+    ap.add_argument("--no-gear", action="store_true", help="skip the gear-teeth stress test")
+    ap.add_argument("--gear-k", default="8,16,32,64,128", help="piece counts of the gear-teeth stress test")
+    ap.add_argument("--heatmap", default="", help="directory for the gear-teeth segments-per-pixel images (PGM)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -471,19 +474,109 @@ def main():
                  "samples_per_frame": su, "ms_per_frame": ms_u,
                  "gsamples_per_s": su / (ms_u * 1e-3) / 1e9, "per_piece_fp32_ms_per_frame": ms_up,
                  "speedup_of_batched": ms_up / ms_u, "sortlast_gpu": usl}
+        upix = sample_pixels(uw, uh, 64, 32)
+        fixed_exact = None
         if rank == 0 and not args.no_cpu_baseline:
-            upix = sample_pixels(uw, uh, 64, 32)
-            ref = __import__("oracle").render(usc, pixels=upix, want=("mboit",))["mboit"]
+            r = __import__("oracle").render(usc, pixels=upix, want=("mboit", "exact") if name == "amr" else ("mboit",))
+            ref, fixed_exact = r["mboit"], r.get("exact")
             got = urgba.view(-1, 4)[torch.from_numpy(upix).cuda()].double().cpu().numpy()
             out_u["quality"] = {"pixels": int(upix.size), "max_abs_vs_oracle": float(np.abs(got - ref).max()),
                                 "rmse_vs_oracle": float(np.sqrt(((got - ref) ** 2).mean()))}
         uvol.close()
         del uvol, umom, urgba
         torch.cuda.empty_cache()
+        if name == "amr":
+            out_u["adaptive_step"] = adaptive_block(usc, upix, ms_u, su, fixed_exact)
         return out_u
+
+    # the octree workload with the adaptive dyadic step (a level-L leaf samples
+    # every 2^(max_level - L)-th lattice point, each sample over that interval)
+    def adaptive_block(usc, upix, ms_fixed, samples_fixed, fixed_exact):
+        import copy
+        asc = copy.copy(usc)
+        asc.adaptive_step = True
+        avol = pkg.Volume(asc)
+        av = asc.views
+        amom, argba = pkg.Volume.moment_buffer(av), pkg.Volume.color_buffer(av)
+        atune = avol.autotune(av, amom, argba)
+        aframe = lambda: avol.render_frame(av, amom, argba)  # noqa: E731
+        for _ in range(3):
+            aframe()
+        ms_a = timed(aframe, max(3, args.steps // 3))
+        avol.synchronize()
+        sa = avol.stats()["samples_pass1"]
+        out_a = {"packet": "4x8" if atune[2] == pkg.MBOIT_PACKET_4X8 else "8x4", "samples_per_frame": sa,
+                 "sample_fraction_of_fixed_step": sa / samples_fixed, "ms_per_frame": ms_a,
+                 "gsamples_per_s": sa / (ms_a * 1e-3) / 1e9,
+                 "fixed_step_lattice_gsamples_per_s": samples_fixed / (ms_a * 1e-3) / 1e9,
+                 "speedup_of_fixed_step_frame": ms_fixed / ms_a}
+        if rank == 0 and not args.no_cpu_baseline:
+            r = __import__("oracle").render(asc, pixels=upix, want=("mboit", "exact"))
+            got = argba.view(-1, 4)[torch.from_numpy(upix).cuda()].double().cpu().numpy()
+            out_a["quality"] = {"pixels": int(upix.size),
+                                "max_abs_vs_oracle": float(np.abs(got - r["mboit"]).max()),
+                                "rmse_vs_oracle": float(np.sqrt(((got - r["mboit"]) ** 2).mean())),
+                                "rmse_vs_fixed_step_exact": float(np.sqrt(((got - fixed_exact) ** 2).mean())),
+                                "exact_adaptive_vs_exact_fixed_rmse":
+                                    float(np.sqrt(((r["exact"] - fixed_exact) ** 2).mean()))}
+        avol.close()
+        del avol, amom, argba
+        torch.cuda.empty_cache()
+        return out_a
 
     amr = unit_block("amr") if args.workload == "blobs512" and not args.no_amr else None
     tets = unit_block("tets") if args.workload == "blobs512" and not args.no_tets else None
+
+    # the gear-teeth stress test of Sec. 5: K pieces of 4 interleaved layers,
+    # batched MBOIT against the exact sort-last baseline as K grows
+    gear = None
+    if args.workload == "blobs512" and not args.no_gear:
+        import scenes as _scenes
+        gear = []
+        for K in [int(x) for x in args.gear_k.split(",") if x]:
+            gsc = _scenes.gear_teeth(n_pieces=K)
+            gvol = pkg.Volume(gsc)
+            gv = gsc.views
+            gmom, grgba = gvol.moments_for(gv), pkg.Volume.color_buffer(gv)
+            gframe = lambda: gvol.render_frame(gv, gmom, grgba)  # noqa: E731
+            for _ in range(2):
+                gframe()
+            ms_g = timed(gframe, 3)
+            gvol.synchronize()
+            sg = gvol.stats()["samples_pass1"]
+            row = {"pieces": K, "layers": 4 * K, "field": "x".join(str(n) for n in gsc.dims) + " float32",
+                   "views": len(gv), "image": f"{gv[0].width}x{gv[0].height} per view", "samples_per_frame": sg,
+                   "mboit_ms_per_frame": ms_g, "mboit_gsamples_per_s": sg / (ms_g * 1e-3) / 1e9}
+            if not args.no_sortlast:
+                gex = pkg.Volume.color_buffer(gv)
+                segs = torch.zeros(sum(v.width * v.height for v in gv), dtype=torch.int32, device="cuda")
+                gvol.render_sortlast(gv, gex, segs)
+                ms_sl = timed(lambda: gvol.render_sortlast(gv, gex, segs), 1)
+                gframe()
+                gvol.synchronize()
+                sn = segs.cpu().numpy()
+                hit = sn[sn > 0]
+                d = (grgba - gex).view(-1, 4).double()
+                row.update({"sortlast_ms_per_frame": ms_sl, "speedup_of_batched_mboit": ms_sl / ms_g,
+                            "segments_per_hit_pixel_mean": float(hit.mean()) if hit.size else 0.0,
+                            "segments_per_pixel_max": int(sn.max()),
+                            "segments_histogram": {"bin_edges": np.linspace(0, 4 * K, 9).tolist(),
+                                                   "pixels": np.histogram(sn, bins=8, range=(0, 4 * K))[0].tolist()},
+                            "mboit_vs_exact_rmse": float(d.pow(2).mean().sqrt())})
+                if args.heatmap:
+                    os.makedirs(args.heatmap, exist_ok=True)
+                    off = 0
+                    for i, v in enumerate(gv):
+                        img = sn[off:off + v.width * v.height].reshape(v.height, v.width)
+                        off += v.width * v.height
+                        with open(os.path.join(args.heatmap, f"gear_teeth{K}_view{i}_segments.pgm"), "wb") as fh:
+                            fh.write(f"P5 {v.width} {v.height} 255\n".encode())
+                            fh.write(np.clip(img * 255.0 / (4 * K), 0, 255).astype(np.uint8).tobytes())
+                del gex, segs
+            gear.append(row)
+            gvol.close()
+            del gvol, gmom, grgba
+            torch.cuda.empty_cache()
 
     # precision sweep on the octree field with the 2048^2 view: moment sets and storages
     sweep = None
@@ -556,6 +649,7 @@ def main():
                                   "packet": "4x8" if tuning[2] == pkg.MBOIT_PACKET_4X8 else "8x4"}),
            "samples_per_frame": samples, "ms_per_frame": ms_max, "singular_pixels": st["singular_pixels"], "per_piece_fp32": per_piece,
            "sortlast_gpu": sortlast, "amr_72_pieces": amr, "tets_72_pieces": tets,
+           "gear_teeth_stress": gear,
            "precision_sweep_amr_2048": sweep,
            "quality": quality, "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
            "gpu_launches": 2 * args.steps, "clocks": clk.summary()}

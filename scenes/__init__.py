@@ -281,6 +281,48 @@ def blobs512(width=2048, height=2048, n_pieces=64, seed=1002, n=512):
                      (np.float32(f.min()), np.float32(f.max())), 0.5, [view])
 
 
+def gear_teeth(n_pieces=8, layers_per_piece=4, layer_cells=2, footprint=512, width=512, height=512, n_views=4,
+               tilt_deg=20.0, b0_target=3.0):
+    """Weak-scaling stress test of Sec. 5 ("gear teeth", Fig. 7): every one of
+    K = n_pieces pieces owns `layers_per_piece` layers of footprint x
+    footprint x layer_cells cells, interleaved so that K - 1 layers of other
+    pieces lie between two layers of a piece (layer s belongs to piece
+    s mod K).  A ray through the stack meets 4K segments of alternating
+    pieces, so an exact sort-last compositor sorts 4K fragments per pixel.
+
+    Field: per layer the value (piece + 1/2) / K (a piece colour through the
+    table) plus a gentle in-plane wobble; vertex plane z takes the value of
+    layer floor(z / layer_cells).  Bricks of layer_cells^3 cells, so a layer
+    is one brick thick.  Constant opacity with sigma * depth = b0_target
+    (a semi-transparent stack at every K).  n_views perspective views on an
+    orbit tilted `tilt_deg` from the stacking axis."""
+    K = n_pieces
+    n_layers = layers_per_piece * K
+    nz = n_layers * layer_cells + 1
+    nx = ny = footprint + 1
+    bl = int(layer_cells).bit_length() - 1
+    assert (1 << bl) == layer_cells and footprint % layer_cells == 0
+    x = np.arange(nx, dtype=np.float64)
+    wob = (0.03 * np.sin(2 * np.pi * x / 128.0)[None, :] * np.sin(2 * np.pi * x / 96.0)[:, None]).astype(np.float32)
+    layer = np.minimum(np.arange(nz) // layer_cells, n_layers - 1)
+    base = ((layer % K) + 0.5) / K * 0.8 + 0.1
+    field = np.empty((nz, ny, nx), np.float32)
+    for z in range(nz):
+        field[z] = np.float32(base[z]) + wob
+    nb = footprint // layer_cells
+    pob = np.repeat((np.arange(n_layers) % K).astype(np.int32), nb * nb)
+    sigma = b0_target / float(n_layers * layer_cells)
+    xs = np.arange(256) / 255.0
+    tf = np.stack([0.5 + 0.5 * np.cos(2 * np.pi * (xs + 0.0)), 0.5 + 0.5 * np.cos(2 * np.pi * (xs + 1 / 3)),
+                   0.5 + 0.5 * np.cos(2 * np.pi * (xs + 2 / 3)), np.full(256, 1.0 - np.exp(-sigma))], 1)
+    dims = (nx, ny, nz)
+    t = np.radians(tilt_deg)
+    views = [perspective_view(dims, (np.sin(t) * np.cos(a), np.sin(t) * np.sin(a), np.cos(t)), width, height)
+             for a in np.radians(45.0 + 90.0 * np.arange(n_views))]
+    return GridScene(f"gear_teeth{K}", field, bl, pob, K, tf.astype(np.float32), (np.float32(0.0), np.float32(1.0)),
+                     0.5, views)
+
+
 # ---------------------------------------------------------------------------
 # AMR brick octree
 

@@ -464,6 +464,29 @@ def test_amr_adaptive_step_single_level_and_pieces():
     assert np.all(r["nsamples"] <= fixed["nsamples"])
 
 
+def test_gear_teeth_layout_and_segments():
+    """Sec. 5 stress test: piece p owns layers p, p + K, p + 2K, p + 3K (one
+    brick thick), so a ray along the stacking axis meets exactly 4K segments
+    of alternating pieces; the sort-last route equals the exact blend and the
+    pieces' moments add up."""
+    K = 3
+    sc = scenes.gear_teeth(n_pieces=K, footprint=16, width=8, height=8, n_views=1)
+    nb = sc.brick_dims
+    layers = sc.piece_of_brick.reshape(nb[2], nb[1], nb[0])
+    assert np.all(layers == (np.arange(nb[2]) % K)[:, None, None])
+    for p in range(K):
+        assert np.flatnonzero(layers[:, 0, 0] == p).tolist() == [p, p + K, p + 2 * K, p + 3 * K]
+    view = small.axis_view(sc.dims, 6, 6, -10.0, 12.0, near=5.0, far=60.0)
+    r = oracle.render_grid(sc, view=view, want=("exact", "sortlast", "moments", "piece_moments"))
+    _, segs = oracle.render_segments(sc, view=view)
+    assert np.all(segs == 4 * K)
+    np.testing.assert_allclose(r["sortlast"], r["exact"], atol=1e-12)
+    np.testing.assert_allclose(r["piece_moments"].sum(axis=1), r["moments"], rtol=1e-12, atol=1e-14)
+    # b0 = sigma * depth on these axis-aligned rays (24 cells, 48 samples)
+    sigma = -np.log1p(-np.float64(sc.tf[0, 3]))
+    np.testing.assert_allclose(r["moments"][:, 0], sigma * 0.5 * 48, rtol=1e-9)
+
+
 # --------------------------------------------------------------------------
 # trigonometric moments (Sec. 4.3, Fig. 3: "different moments")
 
