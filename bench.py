@@ -589,11 +589,11 @@ def main():
         spix = sample_pixels(2048, 2048, 64, 32)
         sweep = []
         exact_ref = None
-        for ms, st, beta in (("power4", "f32", 5e-5), ("power6", "f32", 5e-5), ("power8", "f32", 5e-5),
+        for ms, stor, beta in (("power4", "f32", 5e-5), ("power6", "f32", 5e-5), ("power8", "f32", 5e-5),
                              ("trig6", "f16", 2e-3), ("trig6", "bf16", 2e-2), ("trig8", "f16", 2e-3),
                              ("trig8", "bf16", 2e-2)):
             sc2 = copy.copy(base)
-            sc2.moment_set, sc2.storage, sc2.moment_bias = ms, st, beta
+            sc2.moment_set, sc2.storage, sc2.moment_bias = ms, stor, beta
             svol = pkg.Volume(sc2)
             sv = sc2.views
             smom, srgba = svol.moments_for(sv), pkg.Volume.color_buffer(sv)
@@ -603,7 +603,7 @@ def main():
             ms_s = timed(sframe, 3)
             svol.synchronize()
             ns = svol.stats()["samples_pass1"]
-            row = {"moments": ms, "storage": st, "moment_bias": beta,
+            row = {"moments": ms, "storage": stor, "moment_bias": beta,
                    "moment_bytes_per_pixel": pkg.mboit_moment_image_bytes(4, 1, svol.moment_set, svol.storage) // 4,
                    "ms_per_frame": ms_s, "gsamples_per_s": ns / (ms_s * 1e-3) / 1e9}
             if rank == 0 and not args.no_cpu_baseline:

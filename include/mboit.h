@@ -111,6 +111,12 @@ typedef enum {
 /* volume flags */
 #define MBOIT_FLAG_RAW_SUM 0x1u       /* resolve without renormalisation: out = sum T*alpha*(c, 1) */
 #define MBOIT_FLAG_DETERMINISTIC 0x2u /* accepted; every path here is run-to-run deterministic */
+/* Octrees only: adaptive dyadic step.  A lattice point k in a leaf of level L
+ * is sampled only if k is a multiple of 2^(max_level - L), and that sample's
+ * absorbance covers the longer interval (sigma * step * 2^(max_level - L)):
+ * coarse leaves are sampled at their own resolution on a nested lattice, so
+ * pieces still partition the samples and their moments still add up. */
+#define MBOIT_FLAG_ADAPTIVE_STEP 0x4u
 
 typedef struct mboit_volume_s* mboit_volume;
 

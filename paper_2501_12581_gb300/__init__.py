@@ -32,7 +32,7 @@ MBOIT_PACKET_8X4, MBOIT_PACKET_4X8 = 0, 1
 MBOIT_MOMENTS_PER_PIECE, MBOIT_MOMENTS_REDUCED = 0, 1
 MBOIT_COLOR_PER_PIECE, MBOIT_COLOR_REDUCED, MBOIT_COLOR_RESOLVED = 0, 1, 2
 MBOIT_OP_MOMENTS_SUM, MBOIT_OP_COLOR_SUM_RESOLVE = 0, 1
-MBOIT_FLAG_RAW_SUM, MBOIT_FLAG_DETERMINISTIC = 0x1, 0x2
+MBOIT_FLAG_RAW_SUM, MBOIT_FLAG_DETERMINISTIC, MBOIT_FLAG_ADAPTIVE_STEP = 0x1, 0x2, 0x4
 
 EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume", "mboit_destroy_volume",
             "mboit_add_piece", "mboit_render_moments", "mboit_reconstruct_blend", "mboit_composite",
@@ -317,6 +317,8 @@ class Volume:
         d.kind = MBOIT_TET if tet else MBOIT_AMR if amr else MBOIT_GRID
         self.moment_set = MOMENT_SET_IDS[getattr(scene, "moment_set", "power4")]
         self.storage = STORAGE_IDS[getattr(scene, "storage", "f32")]
+        if amr and getattr(scene, "adaptive_step", False):
+            flags |= MBOIT_FLAG_ADAPTIVE_STEP
         d.moment_set, d.storage, d.flags = self.moment_set, self.storage, flags
         if tet:
             verts = np.ascontiguousarray(scene.verts, dtype=np.float32)

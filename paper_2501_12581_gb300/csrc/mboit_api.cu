@@ -463,9 +463,12 @@ cudaError_t pass2_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTab
 // The tile-row sample cache of a frame: its exact row count for these views
 // (one small kernel, synchronous; done once per recorded frame graph), then
 // grow-only buffers.  Left off (c.vals NULL, pass 2 marches again) when the
-// device lacks the memory with 1 GiB to spare.
+// device lacks the memory with 1 GiB to spare, and for octrees with the
+// adaptive step (a sample's weight depends on its leaf's level, which the
+// cache does not hold; pass 2 skips the same points again instead).
 mboit_status tile_cache(mboit_volume v, const mb::ViewTable& vt, mb::TileCache& c) {
     c = mb::TileCache{};
+    if (v->kind == MBOIT_AMR && (v->desc.flags & MBOIT_FLAG_ADAPTIVE_STEP)) return MBOIT_OK;
     cudaStream_t cs = v->cap_stream;
     if (!v->d_rows) MB_CUDA(cudaMalloc(&v->d_rows, sizeof(unsigned long long)));
     MB_CUDA(cudaMemsetAsync(v->d_rows, 0, sizeof(unsigned long long), cs));
@@ -527,7 +530,10 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
         !(d->moment_bias >= (d->storage == MBOIT_STORE_F16 ? 2e-3f : 2e-2f)))
         return fail(MBOIT_ERR_INVALID_ARG, "trigonometric moments in 16 bits need moment_bias >= 2e-3 (float16) or "
                                            ">= 2e-2 (bfloat16) to keep the stored Toeplitz matrices positive definite");
-    if (d->flags & ~(MBOIT_FLAG_RAW_SUM | MBOIT_FLAG_DETERMINISTIC)) return fail(MBOIT_ERR_INVALID_ARG, "unknown flag bits");
+    if (d->flags & ~(MBOIT_FLAG_RAW_SUM | MBOIT_FLAG_DETERMINISTIC | MBOIT_FLAG_ADAPTIVE_STEP))
+        return fail(MBOIT_ERR_INVALID_ARG, "unknown flag bits");
+    if ((d->flags & MBOIT_FLAG_ADAPTIVE_STEP) && !is_amr)
+        return fail(MBOIT_ERR_INVALID_ARG, "MBOIT_FLAG_ADAPTIVE_STEP applies to octrees only");
     if (!is_amr && !is_tet && !d->field) return fail(MBOIT_ERR_INVALID_ARG, "field is NULL");
     if (is_amr) {
         if (!d->leaf_values || !d->leaf_table) return fail(MBOIT_ERR_INVALID_ARG, "leaf_values and leaf_table are required");

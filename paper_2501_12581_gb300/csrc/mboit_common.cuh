@@ -138,13 +138,13 @@ struct MomentBody {
     float tf_scale, tf_bias, amax, wa, wb;
     float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f;
     unsigned n = 0;
-    __device__ __forceinline__ void operator()(float t, float val) {
+    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) {
         // entry 255 has a zero delta, so xt = 255 needs no special index
         const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
         const int i = (int)xt;
         const float f = xt - (float)i;
         const float2 s = s_sig[i];
-        const float a = fmin_(ffma(f, s.y, s.x), amax);
+        const float a = fmin_(ffma(f, s.y, s.x) * ws, amax);
         const float z = warp_depth(t, wa, wb);
         m0 += a;
         m1 = ffma(a, z, m1);
@@ -168,12 +168,12 @@ struct BlendBody {
     float b0;
     float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     unsigned n = 0;
-    __device__ __forceinline__ void operator()(float t, float val) {
+    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) {
         const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
         const int i = (int)xt;
         const float f = xt - (float)i;
         const float4 e0 = s_tf[2 * i], de = s_tf[2 * i + 1];
-        const float a = fmin_(ffma(f, de.w, e0.w), amax);
+        const float a = fmin_(ffma(f, de.w, e0.w) * ws, amax);
         const float alpha = one_minus_exp_neg(a);
         const float z = warp_depth(t, wa, wb);
         const float wgt = transmittance(F, z, w0) * alpha;
@@ -236,12 +236,12 @@ struct TrigMomentBody {
     float m0 = 0.0f;
     cf t[N];
     unsigned n = 0;
-    __device__ __forceinline__ void operator()(float tt, float val) {
+    __device__ __forceinline__ void operator()(float tt, float val, float ws = 1.0f) {
         const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
         const int i = (int)xt;
         const float f = xt - (float)i;
         const float2 s = s_sig[i];
-        const float a = fmin_(ffma(f, s.y, s.x), amax);
+        const float a = fmin_(ffma(f, s.y, s.x) * ws, amax);
         const float phi = warp_depth(tt, wa, wb) * zs;
         float sn, cs;
         __sincosf(phi, &sn, &cs);
@@ -271,12 +271,12 @@ struct TrigBlendBody {
     float b0;
     float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     unsigned n = 0;
-    __device__ __forceinline__ void operator()(float t, float val) {
+    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) {
         const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
         const int i = (int)xt;
         const float f = xt - (float)i;
         const float4 e0 = s_tf[2 * i], de = s_tf[2 * i + 1];
-        const float a = fmin_(ffma(f, de.w, e0.w), amax);
+        const float a = fmin_(ffma(f, de.w, e0.w) * ws, amax);
         const float alpha = one_minus_exp_neg(a);
         const float z = warp_depth(t, wa, wb);
         const float A = trig_fraction<N>(F, *T, z, w0);
@@ -325,12 +325,12 @@ struct PowerMomentBody {
     float tf_scale, tf_bias, amax, wa, wb;
     float m[2 * N + 1];
     unsigned n = 0;
-    __device__ __forceinline__ void operator()(float t, float val) {
+    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) {
         const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
         const int i = (int)xt;
         const float f = xt - (float)i;
         const float2 s = s_sig[i];
-        const float a = fmin_(ffma(f, s.y, s.x), amax);
+        const float a = fmin_(ffma(f, s.y, s.x) * ws, amax);
         const float z = warp_depth(t, wa, wb);
         m[0] += a;
         float p = a;
@@ -355,12 +355,12 @@ struct PowerBlendBody {
     float b0;
     float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     unsigned n = 0;
-    __device__ __forceinline__ void operator()(float t, float val) {
+    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) {
         const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
         const int i = (int)xt;
         const float f = xt - (float)i;
         const float4 e0 = s_tf[2 * i], de = s_tf[2 * i + 1];
-        const float a = fmin_(ffma(f, de.w, e0.w), amax);
+        const float a = fmin_(ffma(f, de.w, e0.w) * ws, amax);
         const float alpha = one_minus_exp_neg(a);
         const float z = warp_depth(t, wa, wb);
         const float A = power_fraction<N>(F, z, w0);

@@ -142,6 +142,10 @@ struct TrigTables {
     int32_t pad;
 };
 
+// GridD::flags bits (the descriptor's MBOIT_FLAG_* values)
+constexpr uint32_t kFlagRawSum = 0x1u;
+constexpr uint32_t kFlagAdaptiveStep = 0x4u;
+
 struct GridD {
     const float* field;           // [nz][ny][nx]
     int32_t nx, ny, nz;

@@ -97,6 +97,24 @@ __device__ __forceinline__ int skip_unit(const V& vol, int unit, const float o[3
     return kn > 4194303.0f ? 4194304 : (int)kn;
 }
 
+// Adaptive dyadic step of octrees: the level shift max_level - L of unit u's
+// leaf, whose points count only at multiples of 2^shift (-1: every point
+// counts, as on grids or without MBOIT_FLAG_ADAPTIVE_STEP).
+__device__ __forceinline__ int step_shift(const GridD&, int) { return -1; }
+__device__ __forceinline__ int step_shift(const AmrD& a, int u) {
+    return (a.g.flags & kFlagAdaptiveStep) ? a.max_level - __ldg(a.leaves + u).w : -1;
+}
+
+// Next lattice index to test after point k of unit u, which is not on the
+// unit's nested lattice of 2^shift steps: its next lattice point, or the
+// first index that may lie outside the unit (never beyond k_end).
+template <class V>
+__device__ __forceinline__ int next_on_lattice(const V& vol, int u, int shift, const float o[3], const float d[3],
+                                               float t, int k, int k_end) {
+    const int kn = min((k | ((1 << shift) - 1)) + 1, skip_unit(vol, u, o, d, t, k));
+    return min(kn, k_end);
+}
+
 // Per-ray state of a sampler: none for grids and octrees (a point's unit is
 // a table lookup), the current tet for meshes (the walk starts there).
 struct NoWalk {};
@@ -108,9 +126,10 @@ template <bool kNarrow> struct WalkOf<TetT<kNarrow>> { using type = TetWalk; };
 template <class V>
 __device__ __forceinline__ bool piece_sample(const V& vol, const int32_t* __restrict__ pou, int piece, float t,
                                              const float o[3], const float d[3], int k, float& val, int& k_next,
-                                             NoWalk&) {
+                                             float& ws, NoWalk&) {
     const GridD& g = common(vol);
     k_next = k + 1;
+    ws = 1.0f;
     const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
     if (!(p[0] >= 0.0f && p[0] < g.hx && p[1] >= 0.0f && p[1] < g.hy && p[2] >= 0.0f && p[2] < g.hz)) return false;
     const int u = unit_of(vol, p);
@@ -118,6 +137,14 @@ __device__ __forceinline__ bool piece_sample(const V& vol, const int32_t* __rest
     if (__ldg(pou + u) != piece) {
         k_next = skip_unit(vol, u, o, d, t, k);
         return false;
+    }
+    const int shift = step_shift(vol, u);
+    if (shift > 0) {
+        if (k & ((1 << shift) - 1)) {
+            k_next = next_on_lattice(vol, u, shift, o, d, t, k, 4194304);
+            return false;
+        }
+        ws = (float)(1 << shift);
     }
     val = unit_value(vol, p, u);
     return true;
@@ -154,11 +181,11 @@ __global__ void __launch_bounds__(128) k_pass1_piece(const __grid_constant__ V v
             typename WalkOf<V>::type walk;
             for (int k = k0; k <= k1;) {
                 const float t = lattice_t(k, g.step);
-                float val;
+                float val, ws;
                 int kn;
-                const bool owned = piece_sample(vol, pob, piece, t, o, d, k, val, kn, walk);
+                const bool owned = piece_sample(vol, pob, piece, t, o, d, k, val, kn, ws, walk);
                 k = kn;
-                if (owned) body(t, val);
+                if (owned) body(t, val, ws);
             }
         }
         n = body.n;
@@ -202,11 +229,11 @@ __global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ V v
             typename WalkOf<V>::type walk;
             for (int k = k0; k <= k1;) {
                 const float t = lattice_t(k, g.step);
-                float val;
+                float val, ws;
                 int kn;
-                const bool owned = piece_sample(vol, pob, piece, t, o, d, k, val, kn, walk);
+                const bool owned = piece_sample(vol, pob, piece, t, o, d, k, val, kn, ws, walk);
                 k = kn;
-                if (owned) body(t, val);
+                if (owned) body(t, val, ws);
             }
             C = body.C;
             n = body.n;
@@ -376,7 +403,8 @@ __device__ __forceinline__ float tet_value(const long long D[4], const int4 v[4]
 template <bool kNarrow>
 __device__ __forceinline__ bool piece_sample(const TetT<kNarrow>& m, const int32_t* __restrict__ pou, int piece,
                                              float t, const float o[3], const float d[3], int k, float& val,
-                                             int& k_next, TetWalk& w) {
+                                             int& k_next, float& ws, TetWalk& w) {
+    ws = 1.0f;
     const GridD& g = m.g;
     k_next = k + 1;
     const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
@@ -460,6 +488,31 @@ __device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restr
     const GridD& g = a.g;
     if (k0 > k1) return;
     store.seek(k0);
+    if (g.flags & kFlagAdaptiveStep) {
+        // adaptive dyadic step: a point counts only on its leaf's nested
+        // lattice; the points in between are skipped while inside the leaf
+        for (int k = k0; k <= k1;) {
+            const float t = lattice_t(k, g.step);
+            const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
+            const int u = unit_of(a, p);
+            if (u < 0 || (kSel && !__ldg(sel + u))) {
+                store.put(__int_as_float(0x7fc00000));
+                ++k;
+                continue;
+            }
+            const int shift = step_shift(a, u);
+            if (k & ((1 << shift) - 1)) {
+                const int kn = next_on_lattice(a, u, shift, o, d, t, k, k1 + 1);
+                for (; k < kn; ++k) store.put(__int_as_float(0x7fc00000));
+                continue;
+            }
+            const float val = unit_value(a, p, u);
+            store.put(val);
+            body(t, val, (float)(1 << shift));
+            ++k;
+        }
+        return;
+    }
     const float tz = lattice_t(k1, g.step);
     for (float t = lattice_t(k0, g.step); t <= tz; t += g.step) {
         const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
@@ -602,9 +655,9 @@ __global__ void __launch_bounds__(128) k_sortlast_piece(const __grid_constant__ 
         typename WalkOf<V>::type walk;
         for (int k = k0; k <= k1;) {
             const float t = lattice_t(k, g.step);
-            float val;
+            float val, ws;
             int kn;
-            if (!piece_sample(vol, pob, piece, t, o, d, k, val, kn, walk)) {
+            if (!piece_sample(vol, pob, piece, t, o, d, k, val, kn, ws, walk)) {
                 k = kn;
                 continue;
             }
@@ -625,7 +678,7 @@ __global__ void __launch_bounds__(128) k_sortlast_piece(const __grid_constant__ 
                 int i;
                 const float f = tf_coord(g, val, i);
                 const float4 e0 = s_tf[i], e1 = s_tf[i + 1];
-                const float a = fmin_(ffma(f, e1.w - e0.w, e0.w), g.absorbance_max);
+                const float a = fmin_(ffma(f, e1.w - e0.w, e0.w) * ws, g.absorbance_max);
                 const float w = tr * one_minus_exp_neg(a);
                 cur.x = ffma(w, ffma(f, e1.x - e0.x, e0.x), cur.x);
                 cur.y = ffma(w, ffma(f, e1.y - e0.y, e0.y), cur.y);

@@ -120,3 +120,94 @@ def test_amr_full_size_sampled(pkg):
     assert_rgba_close(unpack_color(col, v)[0][0][pix], ref["mboit"])
     assert vol.stats()["samples_pass1"] > 1e9
     vol.close()
+
+
+@pytest.fixture(scope="module")
+def adaptive_amr(pkg):
+    import copy
+    sc = copy.copy(scenes.amr_blobs(base=4, max_level=2, width=48, height=40, n_pieces=5))
+    sc.adaptive_step = True
+    ref = oracle.render_amr(sc, want=("moments", "piece_moments", "piece_color", "mboit", "nsamples"))
+    vol = pkg.Volume(sc)
+    yield sc, ref, vol
+    vol.close()
+
+
+def test_amr_adaptive_step_frame(pkg, adaptive_amr):
+    """Adaptive dyadic step, batched frame (pass 2 marches again and skips
+    the same points): the sample count is the oracle's exactly, moments and
+    image within the usual tolerances, and the split calls give the same
+    bits."""
+    import torch
+    sc, ref, vol = adaptive_amr
+    v = sc.views
+    mom = pkg.Volume.moment_buffer(v)
+    col = pkg.Volume.color_buffer(v)
+    vol.render_frame(v, mom, col)
+    vol.synchronize()
+    torch.cuda.synchronize()
+    st = vol.stats()
+    assert st["samples_pass1"] == st["samples_pass2"] == int(ref["nsamples"].sum())
+    assert_moments_close(unpack_moments(mom, v)[0][0], ref["moments"])
+    assert_rgba_close(unpack_color(col, v)[0][0], ref["mboit"])
+    mom2 = pkg.Volume.moment_buffer(v)
+    col2 = pkg.Volume.color_buffer(v)
+    vol.render_moments(v, mom2)
+    vol.reconstruct_blend(v, mom2, col2)
+    torch.cuda.synchronize()
+    assert torch.equal(mom, mom2) and torch.equal(col, col2)
+
+
+def test_amr_adaptive_step_per_piece_and_sortlast(pkg, adaptive_amr):
+    """Per-piece passes and their image sums, and the sort-last baseline's
+    segments (runs of consecutive counted points), with the adaptive step."""
+    import torch
+    sc, ref, vol = adaptive_amr
+    v = sc.views
+    K = sc.n_pieces
+    per = pkg.Volume.moment_buffer(v, K)
+    vol.render_moments(v, per, mode=pkg.MBOIT_MOMENTS_PER_PIECE)
+    glob = pkg.Volume.moment_buffer(v)
+    vol.composite(pkg.MBOIT_OP_MOMENTS_SUM, v[0].width, v[0].height, 1, K, per, glob)
+    pc = pkg.Volume.color_buffer(v, K)
+    vol.reconstruct_blend(v, glob, pc, mode=pkg.MBOIT_COLOR_PER_PIECE)
+    out = pkg.Volume.color_buffer(v)
+    vol.composite(pkg.MBOIT_OP_COLOR_SUM_RESOLVE, v[0].width, v[0].height, 1, K, pc, out, glob)
+    torch.cuda.synchronize()
+    got = unpack_moments(per, v, K)[0]
+    for P in range(K):
+        assert_moments_close(got[P], ref["piece_moments"][:, P])
+    assert_rgba_close(unpack_color(out, v)[0][0], ref["mboit"])
+    rgba = pkg.Volume.color_buffer(v)
+    segs = torch.zeros(v[0].width * v[0].height, dtype=torch.int32, device="cuda")
+    vol.render_sortlast(v, rgba, segs)
+    torch.cuda.synchronize()
+    ref_rgba, ref_segs = oracle.render_segments(sc)
+    np.testing.assert_array_equal(segs.cpu().numpy(), ref_segs)
+    assert_rgba_close(rgba.view(-1, 4).cpu().numpy().astype(np.float64), ref_rgba)
+
+
+def test_amr_adaptive_step_full_size_sampled(pkg):
+    """The 72-piece 2560x2560 octree workload with the adaptive step: sampled
+    pixels against the oracle, and about a third of the fixed step's
+    samples."""
+    import copy
+    import torch
+    sc = copy.copy(scenes.amr_blobs())
+    sc.adaptive_step = True
+    vol = pkg.Volume(sc)
+    v = sc.views
+    mom = pkg.Volume.moment_buffer(v)
+    col = pkg.Volume.color_buffer(v)
+    vol.render_frame(v, mom, col)
+    vol.synchronize()
+    torch.cuda.synchronize()
+    W = v[0].width
+    ys, xs = np.meshgrid(np.arange(11, W, 40), np.arange(23, W, 40), indexing="ij")
+    pix = (ys * W + xs).ravel()
+    ref = oracle.render_amr(sc, pixels=pix, want=("moments", "mboit"))
+    assert_moments_close(unpack_moments(mom, v)[0][0][pix], ref["moments"])
+    assert_rgba_close(unpack_color(col, v)[0][0][pix], ref["mboit"])
+    n = vol.stats()["samples_pass1"]
+    assert 1.0e9 < n < 1.6e9  # 4.05 G with the fixed step
+    vol.close()
