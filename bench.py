@@ -566,11 +566,12 @@ def main():
                 if args.heatmap:
                     os.makedirs(args.heatmap, exist_ok=True)
                     off = 0
-                    for i, v in enumerate(gv):
-                        img = sn[off:off + v.width * v.height].reshape(v.height, v.width)
-                        off += v.width * v.height
+                    for i, gview in enumerate(gv):
+                        w_, h_ = gview.width, gview.height
+                        img = sn[off:off + w_ * h_].reshape(h_, w_)
+                        off += w_ * h_
                         with open(os.path.join(args.heatmap, f"gear_teeth{K}_view{i}_segments.pgm"), "wb") as fh:
-                            fh.write(f"P5 {v.width} {v.height} 255\n".encode())
+                            fh.write(f"P5 {w_} {h_} 255\n".encode())
                             fh.write(np.clip(img * 255.0 / (4 * K), 0, 255).astype(np.uint8).tobytes())
                 del gex, segs
             gear.append(row)
@@ -627,7 +628,8 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         frame()
         vol.synchronize()
-        pix = sample_pixels(v.width, v.height, 8, 4) if args.workload == "blobs512" else sample_pixels(v.width, v.height, 1, 1)
+        v0 = sc.views[0]
+        pix = sample_pixels(v0.width, v0.height, 8, 4) if args.workload == "blobs512" else sample_pixels(v0.width, v0.height, 1, 1)
         r, dt = time_oracle(sc, pix)
         ns = int(r["nsamples"].sum())
         got = rgba.view(-1, 4)[torch.from_numpy(pix).cuda()].double().cpu().numpy()

@@ -463,12 +463,9 @@ cudaError_t pass2_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTab
 // The tile-row sample cache of a frame: its exact row count for these views
 // (one small kernel, synchronous; done once per recorded frame graph), then
 // grow-only buffers.  Left off (c.vals NULL, pass 2 marches again) when the
-// device lacks the memory with 1 GiB to spare, and for octrees with the
-// adaptive step (a sample's weight depends on its leaf's level, which the
-// cache does not hold; pass 2 skips the same points again instead).
+// device lacks the memory with 1 GiB to spare.
 mboit_status tile_cache(mboit_volume v, const mb::ViewTable& vt, mb::TileCache& c) {
     c = mb::TileCache{};
-    if (v->kind == MBOIT_AMR && (v->desc.flags & MBOIT_FLAG_ADAPTIVE_STEP)) return MBOIT_OK;
     cudaStream_t cs = v->cap_stream;
     if (!v->d_rows) MB_CUDA(cudaMalloc(&v->d_rows, sizeof(unsigned long long)));
     MB_CUDA(cudaMemsetAsync(v->d_rows, 0, sizeof(unsigned long long), cs));

@@ -109,12 +109,22 @@ __device__ __forceinline__ float4 resolve_pixel(float4 C, float m0, float4 bg, b
     return make_float4(ffma(C.x, k, T * bg.x), ffma(C.y, k, T * bg.y), ffma(C.z, k, T * bg.z), A + T * bg.w);
 }
 
+// a - b per component, one rounding each (fma(b, -1, a)), as one packed
+// FP32x2 instruction.
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
+// Trilinear interpolation: x lerps of the four edges, y lerps of the two
+// faces, z lerp.  The z = 0 and z = 1 halves go through the packed FP32x2
+// pipe together (two IEEE operations per instruction), so every value is
+// rounded exactly as in the scalar form a = fma(fx, v1 - v0, v0).
 __device__ __forceinline__ float trilinear8(float v000, float v100, float v010, float v110, float v001, float v101,
                                             float v011, float v111, float fx, float fy, float fz) {
-    const float a00 = ffma(fx, v100 - v000, v000), a10 = ffma(fx, v110 - v010, v010);
-    const float a01 = ffma(fx, v101 - v001, v001), a11 = ffma(fx, v111 - v011, v011);
-    const float b0 = ffma(fy, a10 - a00, a00), b1 = ffma(fy, a11 - a01, a01);
-    return ffma(fz, b1 - b0, b0);
+    const float2 fx2 = make_float2(fx, fx);
+    const float2 lo0 = make_float2(v000, v001), lo1 = make_float2(v010, v011);
+    const float2 a0 = __ffma2_rn(fx2, fsub2(make_float2(v100, v101), lo0), lo0);  // (a00, a01)
+    const float2 a1 = __ffma2_rn(fx2, fsub2(make_float2(v110, v111), lo1), lo1);  // (a10, a11)
+    const float2 b = __ffma2_rn(make_float2(fy, fy), fsub2(a1, a0), a0);          // (b0, b1)
+    return ffma(fz, b.y - b.x, b.x);
 }
 
 // Where a march puts every lattice point's value: nowhere, or a tile-cache
@@ -513,9 +523,21 @@ constexpr int kRowBuf = 2 * kRowChunk * 32;     // floats of a warp's double buf
 // into its shared-memory buffer 8 rows (1 KiB) at a time, one chunk ahead of
 // the one it blends, and every lane takes its own column over its own
 // [k0, k1].  buf: 16-byte aligned, kRowBuf floats, this warp's only.
-template <bool kSel, class Body>
+// Octree adaptive step: a sample value carries its leaf's level shift in its
+// low mantissa bits, as few as max_level needs (2 for max_level 2 or 3: the
+// value moves by at most 3 ulp, the same in both passes, the split calls and
+// the per-piece path), so that pass 2 can weigh cached samples.
+__device__ __forceinline__ int tag_mask(int max_level) { return (1 << (32 - __clz(max_level))) - 1; }
+__device__ __forceinline__ float tag_shift(float v, int shift, int mask) {
+    return __int_as_float((__float_as_int(v) & ~mask) | shift);
+}
+__device__ __forceinline__ float tagged_weight(float v, int mask) {
+    return __int_as_float((127 + (__float_as_int(v) & mask)) << 23);  // 2^shift
+}
+
+template <bool kSel, class Body, bool kTagged = false>
 __device__ __forceinline__ void march_rows(const GridD& g, const float* __restrict__ rows, int kmin, int kmax, int k0,
-                                           int k1, float* __restrict__ buf, Body& body) {
+                                           int k1, float* __restrict__ buf, Body& body, int tmask = 0) {
     if (kmin > kmax) return;
     const int lane = threadIdx.x & 31;
     const int nrows = kmax - kmin + 1;
@@ -549,14 +571,15 @@ __device__ __forceinline__ void march_rows(const GridD& g, const float* __restri
 #pragma unroll
             for (int i = 0; i < kRowChunk; ++i, t += g.step) {
                 const float val = src[i * 32];
-                if (!kSel || val == val) body(t, val);
+                if (!kSel || val == val) body(t, val, kTagged ? tagged_weight(val, tmask) : 1.0f);
             }
         } else {
             for (int i = 0; i < n; ++i, t += g.step) {
                 const int k = kc + i;
                 if (k < k0 || k > k1) continue;
                 const float val = src[i * 32];
-                if (!kSel || val == val) body(t, val);  // every in-domain point is owned when no piece is left out
+                // every in-domain point is owned when no piece is left out
+                if (!kSel || val == val) body(t, val, kTagged ? tagged_weight(val, tmask) : 1.0f);
             }
         }
         __syncwarp();  // every lane is done with the chunk before it is refilled

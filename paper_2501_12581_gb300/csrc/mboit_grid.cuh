@@ -197,7 +197,7 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
 
 
 template <bool kSel, class Cfg, int MS, bool kCache = false>
-__global__ void __launch_bounds__(256) k_pass1_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
+__global__ void __launch_bounds__(256, MS == 0 ? 5 : 1) k_pass1_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
                                                      const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                      char* __restrict__ moments, Counters* __restrict__ ctr,
                                                      const TileCache cache) {

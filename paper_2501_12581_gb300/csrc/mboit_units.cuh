@@ -11,6 +11,7 @@
 // launch per piece, rays clipped to the piece's box, non-owned units skipped,
 // one image per piece.
 #pragma once
+#include <type_traits>
 #include "mboit_common.cuh"
 
 namespace mb {
@@ -104,6 +105,9 @@ __device__ __forceinline__ int step_shift(const GridD&, int) { return -1; }
 __device__ __forceinline__ int step_shift(const AmrD& a, int u) {
     return (a.g.flags & kFlagAdaptiveStep) ? a.max_level - __ldg(a.leaves + u).w : -1;
 }
+// Mantissa bits that carry the level shift of an adaptive-step sample.
+__device__ __forceinline__ int shift_tag_mask(const GridD&) { return 0; }
+__device__ __forceinline__ int shift_tag_mask(const AmrD& a) { return tag_mask(a.max_level); }
 
 // Next lattice index to test after point k of unit u, which is not on the
 // unit's nested lattice of 2^shift steps: its next lattice point, or the
@@ -139,12 +143,14 @@ __device__ __forceinline__ bool piece_sample(const V& vol, const int32_t* __rest
         return false;
     }
     const int shift = step_shift(vol, u);
-    if (shift > 0) {
+    if (shift >= 0) {
         if (k & ((1 << shift) - 1)) {
             k_next = next_on_lattice(vol, u, shift, o, d, t, k, 4194304);
             return false;
         }
         ws = (float)(1 << shift);
+        val = tag_shift(unit_value(vol, p, u), shift, shift_tag_mask(vol));
+        return true;
     }
     val = unit_value(vol, p, u);
     return true;
@@ -486,33 +492,39 @@ template <bool kSel, class Body, class Store = NoStore>
 __device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restrict__ sel, const float o[3],
                                            const float d[3], int k0, int k1, Body& body, Store store = Store{}) {
     const GridD& g = a.g;
-    if (k0 > k1) return;
-    store.seek(k0);
     if (g.flags & kFlagAdaptiveStep) {
         // adaptive dyadic step: a point counts only on its leaf's nested
-        // lattice; the points in between are skipped while inside the leaf
-        for (int k = k0; k <= k1;) {
+        // lattice.  The warp walks the lattice indices in lockstep (each lane
+        // active inside its own [k0, k1]; all 32 lanes reach the reductions),
+        // so lanes in leaves of one level skip the same points together
+        // instead of diverging.
+        const unsigned full = 0xffffffffu;
+        const bool any = k0 <= k1;
+        const int kmin = __reduce_min_sync(full, any ? k0 : 0x7fffffff);
+        const int kmax = __reduce_max_sync(full, any ? k1 : -1);
+        if (any) store.seek(k0);
+        for (int k = kmin; k <= kmax; ++k) {
+            if (k < k0 || k > k1) continue;
             const float t = lattice_t(k, g.step);
             const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
             const int u = unit_of(a, p);
             if (u < 0 || (kSel && !__ldg(sel + u))) {
                 store.put(__int_as_float(0x7fc00000));
-                ++k;
                 continue;
             }
             const int shift = step_shift(a, u);
             if (k & ((1 << shift) - 1)) {
-                const int kn = next_on_lattice(a, u, shift, o, d, t, k, k1 + 1);
-                for (; k < kn; ++k) store.put(__int_as_float(0x7fc00000));
+                store.put(__int_as_float(0x7fc00000));
                 continue;
             }
-            const float val = unit_value(a, p, u);
+            const float val = tag_shift(unit_value(a, p, u), shift, tag_mask(a.max_level));
             store.put(val);
             body(t, val, (float)(1 << shift));
-            ++k;
         }
         return;
     }
+    if (k0 > k1) return;
+    store.seek(k0);
     const float tz = lattice_t(k1, g.step);
     for (float t = lattice_t(k0, g.step); t <= tz; t += g.step) {
         const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
@@ -596,7 +608,17 @@ __global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 2>::value : 2) k_p
         const long long tb = kCache ? cache.tile_base[tile] : -1;
         if (kCache && tb >= 0) {
             const int kmin = __reduce_min_sync(0xffffffffu, k0), kmax = __reduce_max_sync(0xffffffffu, k1);
-            march_rows<true>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, s_rows[kCache ? threadIdx.x >> 5 : 0], body);
+            float* buf = s_rows[kCache ? threadIdx.x >> 5 : 0];
+            bool tagged = false;  // octree samples of the adaptive step carry their weight
+            int tmask = 0;
+            if constexpr (std::is_same<V, AmrD>::value) {
+                tagged = (g.flags & kFlagAdaptiveStep) != 0;
+                tmask = tag_mask(a.max_level);
+            }
+            if (tagged)
+                march_rows<true, decltype(body), true>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, buf, body, tmask);
+            else
+                march_rows<true>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, buf, body);
         } else {
             march_unit<kSel>(a, sel, o, d, k0, k1, body);
         }
