@@ -376,18 +376,20 @@ class Volume:
         return torch.zeros(total, dtype=torch.float32, device="cuda")
 
     @staticmethod
-    def unpack_moments(buf, views, n_slots=1):
-        """Device slab buffer -> list per view of [n_slots][H*W][5] float32 tensors."""
+    def unpack_moments(buf, views, n_slots=1, moment_set=MBOIT_POWER4):
+        """Device slab buffer of power moments -> list per view of
+        [n_slots][H*W][2n + 1] float32 tensors (b0..b2n; n = 2, 3 or 4)."""
+        nm = {MBOIT_POWER4: 5, MBOIT_POWER6: 7, MBOIT_POWER8: 9}[moment_set]
         out, off = [], 0
         for v in views:
             npx = v.width * v.height
             P = (npx + 3) // 4 * 4
             slabs = []
             for j in range(n_slots):
-                s = buf[off + j * 5 * P: off + (j + 1) * 5 * P]
-                slabs.append(torch_cat_moments(s, P, npx))
+                s = buf[off + j * nm * P: off + (j + 1) * nm * P]
+                slabs.append(torch_cat_moments(s, P, npx, nm))
             out.append(slabs)
-            off += n_slots * 5 * P
+            off += n_slots * nm * P
         return out
 
     def render_moments(self, views, moments, pieces=None, mode=MBOIT_MOMENTS_REDUCED, stream=None):
@@ -421,9 +423,11 @@ class Volume:
         return mboit_get_stats(self.handle)
 
 
-def torch_cat_moments(slab, P, npx):
-    """One moment slab (5*P floats: b0 plane, then float4 plane) -> [npx][5]."""
+def torch_cat_moments(slab, P, npx, nm=5):
+    """One power-moment slab (nm * P floats: b0 plane, float4 plane of b1..b4,
+    then a float2 plane (nm = 7) or float4 plane (nm = 9)) -> [npx][nm]."""
     import torch
-    b0 = slab[:P][:npx, None]
-    rest = slab[P:5 * P].view(P, 4)[:npx]
-    return torch.cat([b0, rest], dim=1)
+    parts = [slab[:P][:npx, None], slab[P:5 * P].view(P, 4)[:npx]]
+    if nm > 5:
+        parts.append(slab[5 * P:nm * P].view(P, nm - 5)[:npx])
+    return torch.cat(parts, dim=1)

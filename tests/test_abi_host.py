@@ -209,3 +209,26 @@ def test_tet_quantum_range_checked(lib):
     d = _tet_desc(sc)
     d.tet_cells = None
     assert lib.mboit_create_volume(ctypes.byref(d), ctypes.byref(h)) == 1
+
+
+def test_unpack_moments_layouts():
+    """The binding's slab unpacking follows the documented planes: b0, the
+    float4 plane of b1..b4, then a float2 (6 moments) or float4 (8 moments)
+    plane; the plane is the pixel count rounded up to 4."""
+    import torch
+
+    class V:
+        width, height = 3, 2
+    P = 8
+    for ms, nm in ((pkg.MBOIT_POWER4, 5), (pkg.MBOIT_POWER6, 7), (pkg.MBOIT_POWER8, 9)):
+        buf = torch.arange(2 * nm * P, dtype=torch.float32)
+        slabs = pkg.Volume.unpack_moments(buf, [V()], 2, ms)[0]
+        for j in range(2):
+            s = slabs[j]
+            assert s.shape == (6, nm)
+            for px in range(6):
+                o = j * nm * P
+                want = [o + px] + [o + P + 4 * px + c for c in range(4)]
+                if nm > 5:
+                    want += [o + 5 * P + (nm - 5) * px + c for c in range(nm - 5)]
+                assert s[px].tolist() == want
