@@ -107,6 +107,10 @@ def _load():
                                             ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_power_bias.restype = None
             lib.orc_power_bias.argtypes = [ctypes.c_int, ctypes.c_void_p]
+            lib.orc_split_cells.restype = ctypes.c_int
+            lib.orc_split_cells.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_void_p]
             lib.orc_log_warp.restype = ctypes.c_double
             lib.orc_log_warp.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
             lib.orc_render_grid.restype = ctypes.c_int
@@ -171,6 +175,34 @@ def power_bound(m, n, z0, moment_bias, overestimation, bias=None):
     A = lib.orc_power_bound(m.ctypes.data, int(n), float(z0), float(moment_bias), bv.ctypes.data,
                             float(overestimation), ctypes.byref(fl), nodes.ctypes.data)
     return A, fl.value, nodes
+
+
+def split_cells(scene):
+    """A mixed-cell scene (tets, pyramids, prisms) split into tetrahedra by
+    the oracle's own rule: returns (tets [m][4] int32, cell_of_tet [m] int64)."""
+    import numpy as _np
+    verts = _np.ascontiguousarray(scene.verts, dtype=_np.float32)
+    cells = _np.ascontiguousarray(scene.cells, dtype=_np.int32)
+    types = _np.ascontiguousarray(scene.cell_types, dtype=_np.int32)
+    cap = 3 * len(cells)
+    tets = _np.zeros((cap, 4), _np.int32)
+    cot = _np.zeros(cap, _np.int64)
+    n = ctypes.c_int64(0)
+    if _load().orc_split_cells(verts.ctypes.data, len(verts), cells.ctypes.data, types.ctypes.data, len(cells),
+                               int(scene.quantum_log2), tets.ctypes.data, cot.ctypes.data, cap, ctypes.byref(n)) != 0:
+        raise ValueError("oracle rejected the cells (bad ids or types, or a flat tet)")
+    return tets[:n.value].copy(), cot[:n.value].copy()
+
+
+def tet_scene_of(scene):
+    """The oracle's tetrahedral scene of a mixed-cell scene (its own split;
+    face neighbours from the scene module)."""
+    import scenes as _scenes
+    tets, cot = split_cells(scene)
+    return _scenes.TetScene(scene.name + "_tets", scene.verts, tets, _scenes.tet_neighbors(tets), scene.box,
+                            scene.quantum_log2, scene.piece_of_cell[cot].astype(np.int32), scene.n_pieces, scene.tf,
+                            scene.tf_range, scene.step, list(scene.views), scene.moment_bias, scene.overestimation,
+                            scene.absorbance_max)
 
 
 def trig_nodes(m, n, phi0, moment_bias):

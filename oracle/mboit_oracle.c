@@ -1278,3 +1278,87 @@ int orc_tet_locate(const orc_tet* m, const float* points, int64_t n, int32_t* te
     tet_free(&v);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* mixed cells -> tetrahedra                                                 */
+
+static int emit_tet(const float* verts, int64_t n_verts, int s, int32_t a, int32_t b, int32_t c, int32_t d,
+                    int64_t cell, int32_t* out, int64_t* cot, int64_t max_tets, int64_t* n)
+{
+    int32_t v[4] = {a, b, c, d};
+    int64_t P[4][3];
+    for (int i = 0; i < 4; ++i) {
+        if (v[i] < 0 || v[i] >= n_verts) return -1;
+        for (int k = 0; k < 3; ++k) P[i][k] = snap((double)verts[4 * (int64_t)v[i] + k], s);
+    }
+    i128 o = orient4(P);
+    if (o == 0) return -1;
+    if (o < 0) {
+        int32_t t = v[2];
+        v[2] = v[3];
+        v[3] = t;
+    }
+    if (*n >= max_tets) return -1;
+    memcpy(out + 4 * *n, v, sizeof v);
+    cot[*n] = cell;
+    ++*n;
+    return 0;
+}
+
+int orc_split_cells(const float* verts, int64_t n_verts, const int32_t* cells, const int32_t* types, int64_t n_cells,
+                    int32_t quantum_log2, int32_t* tets_out, int64_t* cell_of_tet, int64_t max_tets, int64_t* n_tets)
+{
+    if (!verts || !cells || !types || !tets_out || !cell_of_tet || !n_tets || quantum_log2 < 0 || quantum_log2 > 24)
+        return -1;
+    int64_t n = 0;
+    const int s = quantum_log2;
+    for (int64_t i = 0; i < n_cells; ++i) {
+        const int32_t* c = cells + 6 * i;
+        int rc = 0;
+        if (types[i] == 4) {
+            rc = emit_tet(verts, n_verts, s, c[0], c[1], c[2], c[3], i, tets_out, cell_of_tet, max_tets, &n);
+        } else if (types[i] == 5) {
+            /* the base quad's diagonal through its smallest id */
+            int32_t m = c[0];
+            for (int k = 1; k < 4; ++k) m = c[k] < m ? c[k] : m;
+            int j = (m == c[0] || m == c[2]) ? 0 : 1;
+            rc = emit_tet(verts, n_verts, s, c[j], c[j + 1], c[(j + 2) % 4], c[4], i, tets_out, cell_of_tet, max_tets, &n);
+            if (!rc)
+                rc = emit_tet(verts, n_verts, s, c[j], c[(j + 2) % 4], c[(j + 3) % 4], c[4], i, tets_out, cell_of_tet,
+                              max_tets, &n);
+        } else if (types[i] == 6) {
+            /* relabel (triangle rotations, bottom/top flip) so that local
+             * vertex 0 has the smallest id; its two quad faces are cut
+             * through it, the opposite quad (1, 2, 5, 4) by its own smallest */
+            int best = -1, L[6] = {0, 0, 0, 0, 0, 0};
+            for (int r = 0; r < 3; ++r)
+                for (int f = 0; f < 2; ++f) {
+                    int p[6];
+                    for (int k = 0; k < 3; ++k) {
+                        p[k] = (k + r) % 3 + 3 * f;
+                        p[k + 3] = (k + r) % 3 + 3 * (1 - f);
+                    }
+                    if (best < 0 || c[p[0]] < c[L[0]]) {
+                        best = 1;
+                        memcpy(L, p, sizeof p);
+                    }
+                }
+            int32_t v[6];
+            for (int k = 0; k < 6; ++k) v[k] = c[L[k]];
+            int32_t m15 = v[1] < v[5] ? v[1] : v[5], m24 = v[2] < v[4] ? v[2] : v[4];
+            if (m15 < m24) {
+                rc = emit_tet(verts, n_verts, s, v[0], v[1], v[2], v[5], i, tets_out, cell_of_tet, max_tets, &n);
+                if (!rc) rc = emit_tet(verts, n_verts, s, v[0], v[1], v[5], v[4], i, tets_out, cell_of_tet, max_tets, &n);
+            } else {
+                rc = emit_tet(verts, n_verts, s, v[0], v[1], v[2], v[4], i, tets_out, cell_of_tet, max_tets, &n);
+                if (!rc) rc = emit_tet(verts, n_verts, s, v[0], v[4], v[2], v[5], i, tets_out, cell_of_tet, max_tets, &n);
+            }
+            if (!rc) rc = emit_tet(verts, n_verts, s, v[0], v[4], v[5], v[3], i, tets_out, cell_of_tet, max_tets, &n);
+        } else {
+            return -1;
+        }
+        if (rc) return -1;
+    }
+    *n_tets = n;
+    return 0;
+}

@@ -179,6 +179,20 @@ int orc_render_tet(const orc_tet* m, const orc_view* view,
 int orc_tet_locate(const orc_tet* m, const float* points, int64_t n, int32_t* tet_out, int32_t* n_pass_out,
                    double* value_out, int32_t brute_force);
 
+/* Mixed cells (Sec. 5: the FUN3D pieces hold tetrahedra, pyramids and
+ * prisms) split into tetrahedra.  cells[6 i ..]: the vertex ids of cell i,
+ * types[i] = 4 (tet), 5 (pyramid: base quad in cyclic order, apex) or 6
+ * (prism: bottom triangle, top triangle, vertex j + 3 above vertex j).
+ * Every quad face is cut along the diagonal through its smallest vertex id,
+ * so two cells sharing a face cut it alike (a conforming split): a pyramid
+ * gives 2 tets, a prism 3 (the smallest id fixes which of its two
+ * three-tet splits fits the three cuts).  Each tet is made positively
+ * oriented on the snapped coordinates (its last two vertices swapped if
+ * not).  tets_out [max_tets][4], cell_of_tet [max_tets]; *n_tets = count.
+ * Returns 0, -1 on bad arguments, a flat tet or too small a buffer. */
+int orc_split_cells(const float* verts, int64_t n_verts, const int32_t* cells, const int32_t* types, int64_t n_cells,
+                    int32_t quantum_log2, int32_t* tets_out, int64_t* cell_of_tet, int64_t max_tets, int64_t* n_tets);
+
 #ifdef __cplusplus
 }
 #endif

@@ -323,6 +323,105 @@ def gear_teeth(n_pieces=8, layers_per_piece=4, layer_cells=2, footprint=512, wid
                      0.5, views)
 
 
+@dataclass
+class MixedScene:
+    """Unstructured mesh of tetrahedra, pyramids and prisms (the cell mix of
+    the paper's FUN3D data) filling the box [0, n]^3.  cells[i] lists the
+    vertex ids of cell i, padded with -1: a tet (4), a pyramid (5: base quad
+    in cyclic order, then the apex) or a prism (6: bottom triangle, then the
+    top triangle with vertex j + 3 above vertex j); cell_types[i] is that
+    count."""
+    name: str
+    verts: np.ndarray           # float32 [nv][4]: x, y, z, value
+    cells: np.ndarray           # int32 [nc][6]
+    cell_types: np.ndarray      # int32 [nc]: 4, 5 or 6
+    box: tuple
+    quantum_log2: int
+    piece_of_cell: np.ndarray   # int32 [nc]
+    n_pieces: int
+    tf: np.ndarray
+    tf_range: tuple
+    step: float
+    views: List[View] = dc_field(default_factory=list)
+    moment_bias: float = 5e-5
+    overestimation: float = 0.3
+    absorbance_max: float = 10.0
+
+    @property
+    def dims(self):
+        return tuple(int(b) + 1 for b in self.box)
+
+
+def mixed_mesh(n=24, n_pieces=8, width=256, height=256, seed=1006, alpha_max=None):
+    """n^3 hex grid whose every hex becomes, at random: 6 tets around its main
+    diagonal (Kuhn), 2 prisms (cut by the vertical plane through its (0, 0)
+    and (1, 1) edges), or 6 pyramids on its faces with an apex at its centre.
+    Vertex ids grow with x, then y, then z, so every quad face these cells
+    share is cut, when split into tets along the diagonal through its
+    smallest vertex id, the same way from both sides.  Values: the 64^3
+    workload's 8 blobs scaled to n; pieces: equal-count ranges of the Morton
+    order of cell centroids; a perspective view; step 0.5."""
+    s = Stream(seed)
+    nv1 = n + 1
+    g = np.arange(nv1, dtype=np.float64)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    P = [np.stack([X, Y, Z], -1).reshape(-1, 3)]
+    vid = lambda x, y, z: (z * nv1 + y) * nv1 + x  # noqa: E731
+    kind = np.floor(s.uniform(n ** 3) * 3).astype(np.int64)
+    cells, types, cen = [], [], []
+    n_extra = 0
+    for h in range(n ** 3):
+        x, y, z = h % n, (h // n) % n, h // (n * n)
+        c = {(a, b, e): vid(x + a, y + b, z + e) for a in (0, 1) for b in (0, 1) for e in (0, 1)}
+        centre = (x + 0.5, y + 0.5, z + 0.5)
+        if kind[h] == 0:      # Kuhn: paths v000 -> +e_a -> +e_a + e_b -> v111
+            for a, b in ((0, 1), (0, 2), (1, 0), (1, 2), (2, 0), (2, 1)):
+                u = [0, 0, 0]
+                u[a] = 1
+                w = list(u)
+                w[b] = 1
+                cells.append([c[(0, 0, 0)], c[tuple(u)], c[tuple(w)], c[(1, 1, 1)], -1, -1])
+                types.append(4)
+                cen.append(centre)
+        elif kind[h] == 1:    # two prisms, vertical cut through (0, 0)-(1, 1)
+            for tri in (((0, 0), (1, 0), (1, 1)), ((0, 0), (1, 1), (0, 1))):
+                cells.append([c[(a, b, 0)] for a, b in tri] + [c[(a, b, 1)] for a, b in tri])
+                types.append(6)
+                cen.append(centre)
+        else:                 # six pyramids around a centre vertex
+            apex = nv1 ** 3 + n_extra
+            n_extra += 1
+            P.append(np.array([centre]))
+            faces = [[(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0)], [(0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)],
+                     [(0, 0, 0), (1, 0, 0), (1, 0, 1), (0, 0, 1)], [(0, 1, 0), (1, 1, 0), (1, 1, 1), (0, 1, 1)],
+                     [(0, 0, 0), (0, 1, 0), (0, 1, 1), (0, 0, 1)], [(1, 0, 0), (1, 1, 0), (1, 1, 1), (1, 0, 1)]]
+            for f in faces:
+                cells.append([c[q] for q in f] + [apex, -1])
+                types.append(5)
+                cen.append(centre)
+    P = np.concatenate(P, 0)
+    k = n / 64.0
+    cb = s.uniform(24).reshape(8, 3) * n
+    sg = s.uniform(8, 4.0 * k, 12.0 * k)
+    am = s.uniform(8, 0.3, 1.0)
+    val = np.zeros(len(P))
+    for i in range(8):
+        val += am[i] * np.exp(-((P - cb[i]) ** 2).sum(1) / (2 * sg[i] ** 2))
+    verts = np.concatenate([P, val[:, None]], 1).astype(np.float32)
+    cen = np.array(cen)
+    q = np.clip((cen / n * 1023).astype(np.int64), 0, 1023)
+    order = np.argsort(morton3(q[:, 0], q[:, 1], q[:, 2], 10), kind="stable")
+    piece = np.empty(len(cells), np.int32)
+    bounds = np.linspace(0, len(cells), n_pieces + 1).round().astype(np.int64)
+    for p in range(n_pieces):
+        piece[order[bounds[p]:bounds[p + 1]]] = p
+    tf = tf_table(Stream(seed + 7), alpha_max if alpha_max is not None else min(0.13 * 64.0 / n, 0.4))
+    view = perspective_view((n + 1,) * 3, (0.57, 0.49, 0.66), width, height)
+    vf = verts[:, 3]
+    return MixedScene(f"mixed{n}", verts, np.array(cells, np.int32), np.array(types, np.int32), (float(n),) * 3, 14,
+                      piece, n_pieces, tf, (np.float32(vf.min()), np.float32(vf.max())), 0.5, [view])
+
+
 # ---------------------------------------------------------------------------
 # AMR brick octree
 

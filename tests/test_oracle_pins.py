@@ -933,3 +933,65 @@ def test_tet_inverted_mesh_rejected():
     sc.tets[5, [2, 3]] = sc.tets[5, [3, 2]]
     with pytest.raises(ValueError):
         oracle.tet_locate(sc, np.zeros((1, 3), np.float32))
+
+
+# --------------------------------------------------------------------------
+# mixed cells (Sec. 5: the FUN3D pieces hold tetrahedra, pyramids and prisms)
+
+
+def test_mixed_split_is_conforming():
+    """Pyramids split into 2 tets, prisms into 3, along the quad diagonals
+    through the smallest vertex id: every tet is positively oriented, each
+    cell keeps its volume, the only unpaired faces are the 2 triangles of
+    each boundary quad, and exactly one tet owns every point of the box
+    (faces, edges and vertices included)."""
+    n = 5
+    m = scenes.mixed_mesh(n=n, n_pieces=3, width=4, height=4, seed=41)
+    assert set(np.unique(m.cell_types)) == {4, 5, 6}
+    tets, cot = oracle.split_cells(m)
+    np.testing.assert_array_equal(np.bincount(cot, minlength=len(m.cells)), m.cell_types - 3)
+    P = m.verts[:, :3].astype(np.float64)
+    vol = np.linalg.det(np.stack([P[tets[:, i]] - P[tets[:, 0]] for i in (1, 2, 3)], 2)) / 6.0
+    assert vol.min() > 0
+    cell_vol = np.bincount(cot, weights=vol)
+    want = np.where(m.cell_types == 5, 1.0 / 6.0, np.where(m.cell_types == 6, 0.5, 1.0 / 6.0))
+    np.testing.assert_allclose(cell_vol, want, rtol=1e-12)
+    nb = scenes.tet_neighbors(tets)
+    assert (nb < 0).sum() == 12 * n * n
+    ts = oracle.tet_scene_of(m)
+    rng = np.random.default_rng(4)
+    pts = np.concatenate([(rng.random((3000, 3)) * n).astype(np.float32), _special_points(ts)])
+    inside = np.all((pts >= 0) & (pts < n), axis=1)
+    owner, npass, _ = oracle.tet_locate(ts, pts, brute_force=True)
+    np.testing.assert_array_equal(npass[inside], 1)
+
+
+def test_mixed_linear_field_equals_grid():
+    """Linear interpolation on the split tets reproduces a linear field, and
+    the mixed mesh's vertices sit exactly on the lattice, so its render
+    equals the regular grid's: the same samples, and moments equal up to
+    the mesh path's 2^-14 snap of sample positions (at most 3.1e-5 in each
+    coordinate, 4e-6 in this field's value: 2e-4 of the pixel's largest moment)."""
+    n = 5
+    lin = lambda x, y, z: 0.25 + x / 16.0 + y / 32.0 + z / 8.0  # noqa: E731
+    m = scenes.mixed_mesh(n=n, n_pieces=3, width=4, height=4, seed=43)
+    P = m.verts[:, :3].astype(np.float64)
+    m.verts[:, 3] = lin(P[:, 0], P[:, 1], P[:, 2])
+    g = np.arange(n + 1.0)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    field = lin(X, Y, Z).astype(np.float32)
+    tf = small.linear_tf(0.05, 0.3)
+    vr = (np.float32(field.min()), np.float32(field.max()))
+    m.tf, m.tf_range = tf, vr
+    grid = scenes.GridScene("lin", field, 1, np.zeros(((n + 1) // 2) ** 3, np.int32), 1, tf, vr, 0.5, [])
+    ts = oracle.tet_scene_of(m)
+    for v in [scenes.ortho_view(ts.dims, (0.4, 0.5, 0.77), 20, 18),
+              scenes.perspective_view(ts.dims, (-0.6, 0.45, 0.66), 16, 14, fov_deg=35.0)]:
+        a = oracle.render(ts, view=v, want=("moments", "mboit", "nsamples"))
+        b = oracle.render_grid(grid, view=v, want=("moments", "mboit", "nsamples"))
+        np.testing.assert_array_equal(a["nsamples"], b["nsamples"])
+        scale = np.abs(b["moments"]).max(axis=1, keepdims=True) + 1e-12  # odd moments cancel: per-pixel scale
+        assert (np.abs(a["moments"] - b["moments"]) / scale).max() <= 2e-4
+        np.testing.assert_allclose(a["mboit"], b["mboit"], atol=1e-4)
+        assert a["nsamples"].sum() > 100
+
