@@ -144,6 +144,8 @@ def sample_pixels(width, height, row_stride, col_stride):
 
 def time_oracle(sc, pixels):
     import oracle
+    if hasattr(sc, "cells"):
+        sc = oracle.tet_scene_of(sc)  # the oracle's own split of mixed cells
     t0 = time.perf_counter()
     r = oracle.render(sc, pixels=pixels, want=("mboit", "exact", "nsamples"))
     dt = time.perf_counter() - t0
@@ -160,11 +162,21 @@ def workload(name):
         return scenes.amr_blobs()
     if name == "tets":
         return scenes.tet_mesh()
+    if name == "mixed":
+        return scenes.mixed_mesh(n=64, n_pieces=72, width=1024, height=1024)
     raise SystemExit(f"unknown workload {name}")
 
 
 def config_of(sc, name):
     v = sc.views[0]
+    if hasattr(sc, "cells"):
+        nc = np.bincount(sc.cell_types, minlength=7)
+        return {"workload": name,
+                "field": (f"mixed cells of a {int(sc.box[0])}^3 hex grid: {nc[4]} tets, {nc[5]} pyramids, {nc[6]} prisms "
+                          f"({sc.verts.shape[0]} vertices), split into tets by the library, float32 vertex values"),
+                "pieces": sc.n_pieces, "image": f"{v.width}x{v.height}",
+                "projection": "perspective" if v.projection else "orthographic", "step_voxels": sc.step,
+                "moments": "4 power, float32", "moment_bias": sc.moment_bias, "overestimation": sc.overestimation}
     if hasattr(sc, "tets"):
         return {"workload": name,
                 "field": (f"tetrahedral mesh, {sc.tets.shape[0]} tets ({sc.verts.shape[0]} vertices, jittered "
@@ -255,7 +267,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="blobs512", choices=["blobs512", "blobs64", "amr", "tets"])
+    ap.add_argument("--workload", default="blobs512", choices=["blobs512", "blobs64", "amr", "tets", "mixed"])
     ap.add_argument("--image", type=int, default=0, help="square image size for the main workload (profiling)")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-tets", action="store_true")
@@ -361,7 +373,7 @@ def main():
         return d
     k1s = kstats(p1, FLOP_PASS1, CACHE_BYTES_PER_SAMPLE)
     k2s = kstats(p2, FLOP_PASS2_FRAME, CACHE_BYTES_PER_SAMPLE)
-    kname = "k_pass{}_fused" if not (hasattr(sc, "leaves") or hasattr(sc, "tets")) else "k_pass{}_unit"
+    kname = "k_pass{}_fused" if not (hasattr(sc, "leaves") or hasattr(sc, "tets") or hasattr(sc, "cells")) else "k_pass{}_unit"
     dom, dname, dflop = (k2s, kname.format(2) + ", frame form (reads the cached samples; reconstruct + blend + resolve)",
                          FLOP_PASS2_FRAME) if p2 >= p1 else \
         (k1s, kname.format(1) + ", frame form (march + moments + sample store)", FLOP_PASS1)
@@ -374,7 +386,8 @@ def main():
                                 "pass2_achieved_tflops": FLOP_PASS2 * samples / (ms_p2 * 1e-3) / 1e12}}
 
     # end to end through the host API: field upload, frame, image download
-    host_values = sc.values if hasattr(sc, "leaves") else sc.verts[:, 3] if hasattr(sc, "tets") else sc.field
+    host_values = (sc.values if hasattr(sc, "leaves") else sc.verts[:, 3] if (hasattr(sc, "tets") or hasattr(sc, "cells"))
+                   else sc.field)
     field_host = torch.from_numpy(np.ascontiguousarray(host_values, dtype=np.float32)).pin_memory()
     rgba_host = torch.empty(rgba.numel(), dtype=torch.float32).pin_memory()
     e2e_step = lambda: pkg.mboit_render_frame_host(vol.handle, field_host, views, mom, rgba, rgba_host)  # noqa: E731
@@ -477,7 +490,9 @@ def main():
         upix = sample_pixels(uw, uh, 64, 32)
         fixed_exact = None
         if rank == 0 and not args.no_cpu_baseline:
-            r = __import__("oracle").render(usc, pixels=upix, want=("mboit", "exact") if name == "amr" else ("mboit",))
+            _orc = __import__("oracle")
+            oscene = _orc.tet_scene_of(usc) if hasattr(usc, "cells") else usc
+            r = _orc.render(oscene, pixels=upix, want=("mboit", "exact") if name == "amr" else ("mboit",))
             ref, fixed_exact = r["mboit"], r.get("exact")
             got = urgba.view(-1, 4)[torch.from_numpy(upix).cuda()].double().cpu().numpy()
             out_u["quality"] = {"pixels": int(upix.size), "max_abs_vs_oracle": float(np.abs(got - ref).max()),
@@ -526,6 +541,7 @@ def main():
 
     amr = unit_block("amr") if args.workload == "blobs512" and not args.no_amr else None
     tets = unit_block("tets") if args.workload == "blobs512" and not args.no_tets else None
+    mixed = unit_block("mixed") if args.workload == "blobs512" and not args.no_tets else None
 
     # the gear-teeth stress test of Sec. 5: K pieces of 4 interleaved layers,
     # batched MBOIT against the exact sort-last baseline as K grows
@@ -651,6 +667,7 @@ def main():
                                   "packet": "4x8" if tuning[2] == pkg.MBOIT_PACKET_4X8 else "8x4"}),
            "samples_per_frame": samples, "ms_per_frame": ms_max, "singular_pixels": st["singular_pixels"], "per_piece_fp32": per_piece,
            "sortlast_gpu": sortlast, "amr_72_pieces": amr, "tets_72_pieces": tets,
+           "mixed_cells_72_pieces": mixed,
            "gear_teeth_stress": gear,
            "precision_sweep_amr_2048": sweep,
            "quality": quality, "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,

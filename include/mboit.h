@@ -227,6 +227,27 @@ MBOIT_API const char* mboit_last_error(void);
  * for n complex trigonometric moments (16-bit); 0 for an invalid pair. */
 MBOIT_API size_t mboit_moment_image_bytes(int32_t width, int32_t height, int32_t moment_set, int32_t storage);
 
+/* Mixed unstructured cells (Sec. 5: the FUN3D pieces hold tetrahedra,
+ * pyramids and prisms) as the tetrahedral mesh MBOIT_TET volumes take.  All
+ * pointers are HOST memory; nothing is kept.
+ *   verts [n_verts][4]: x, y, z, value (as tet_verts);
+ *   cells [n_cells][6]: vertex ids, padded with -1; cell_types[i] = 4 (tet),
+ *     5 (pyramid: base quad in cyclic order, then the apex) or 6 (prism:
+ *     bottom triangle, then the top triangle with vertex j + 3 above j).
+ * Every quad face is cut along its diagonal through the smallest vertex id,
+ * so cells that share a face cut it alike (a conforming mesh); a pyramid
+ * gives 2 tets, a prism 3.  Each tet is oriented positively on the vertices
+ * snapped to 2^-quantum_log2 (its last two vertices swapped if needed).
+ * Outputs: tets_out [max_tets][4] and neighbors_out [max_tets][4] (the tet
+ * across the face opposite vertex i, -1 on the boundary: ready for
+ * tet_cells / tet_neighbors), cell_of_tet [max_tets] (for piece ids), and
+ * *n_tets.  At most 3 tets per cell.  INVALID_ARG for a bad id or type, a
+ * flat tet, a face shared by more than two tets, or max_tets too small. */
+MBOIT_API mboit_status mboit_split_cells(const float* verts, int64_t n_verts, const int32_t* cells,
+                                         const int32_t* cell_types, int64_t n_cells, int32_t quantum_log2,
+                                         int32_t* tets_out, int32_t* neighbors_out, int64_t* cell_of_tet,
+                                         int64_t max_tets, int64_t* n_tets);
+
 /* Creates a volume on the current CUDA device.  Validates the descriptor,
  * copies the transfer function (converted to extinction sigma = -ln(1-alpha)
  * per voxel), allocates the brick-ownership table.  The field stays

@@ -38,7 +38,7 @@ EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume
             "mboit_add_piece", "mboit_render_moments", "mboit_reconstruct_blend", "mboit_composite",
             "mboit_render_frame", "mboit_render_frame_host", "mboit_synchronize", "mboit_get_stats",
             "mboit_render_moments_noalloc", "mboit_set_tuning", "mboit_set_packet", "mboit_autotune",
-            "mboit_render_sortlast"]
+            "mboit_render_sortlast", "mboit_split_cells"]
 MBOIT_NUM_TUNINGS = 5
 
 
@@ -105,6 +105,7 @@ def load_library(path=LIB_PATH):
         "mboit_set_packet": (ctypes.c_int, [P, I32]),
         "mboit_autotune": (ctypes.c_int, [P, P, I32, P, P, P, P]),
         "mboit_render_sortlast": (ctypes.c_int, [P, P, I32, P, P, P]),
+        "mboit_split_cells": (ctypes.c_int, [P, I64, P, P, I64, I32, P, P, P, I64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -171,6 +172,24 @@ def _pieces(pieces):
 
 def mboit_last_error():
     return load_library().mboit_last_error().decode(errors="replace")
+
+
+def mboit_split_cells(verts, cells, cell_types, quantum_log2):
+    """Mixed cells (4 tet, 5 pyramid, 6 prism) -> (tets [m][4] int32,
+    neighbours [m][4] int32, cell_of_tet [m] int64), split by the library."""
+    verts = np.ascontiguousarray(verts, dtype=np.float32)
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    types = np.ascontiguousarray(cell_types, dtype=np.int32)
+    cap = 3 * len(cells)
+    tets = np.zeros((cap, 4), np.int32)
+    nbrs = np.zeros((cap, 4), np.int32)
+    cot = np.zeros(cap, np.int64)
+    n = ctypes.c_int64(0)
+    _check(load_library().mboit_split_cells(verts.ctypes.data, len(verts), cells.ctypes.data, types.ctypes.data,
+                                            len(cells), int(quantum_log2), tets.ctypes.data, nbrs.ctypes.data,
+                                            cot.ctypes.data, cap, ctypes.byref(n)))
+    m = n.value
+    return tets[:m].copy(), nbrs[:m].copy(), cot[:m].copy()
 
 
 def mboit_moment_image_bytes(width, height, moment_set=MBOIT_POWER4, storage=MBOIT_STORE_F32):
@@ -305,6 +324,14 @@ class Volume:
         import torch
         load_library()
         self.scene = scene
+        if hasattr(scene, "cells"):
+            # mixed cells: the library's split into tets, pieces by cell
+            tets, nbrs, cot = mboit_split_cells(scene.verts, scene.cells, scene.cell_types, scene.quantum_log2)
+            import copy as _copy
+            mixed = scene
+            scene = _copy.copy(scene)
+            scene.tets, scene.neighbors = tets, nbrs
+            scene.piece_of_tet = np.asarray(mixed.piece_of_cell)[cot].astype(np.int32)
         amr = hasattr(scene, "leaves")
         tet = hasattr(scene, "tets")
         if tet:

@@ -499,6 +499,118 @@ extern "C" {
 
 const char* mboit_last_error(void) { return g_err.c_str(); }
 
+mboit_status mboit_split_cells(const float* verts, int64_t n_verts, const int32_t* cells, const int32_t* cell_types,
+                               int64_t n_cells, int32_t quantum_log2, int32_t* tets_out, int32_t* neighbors_out,
+                               int64_t* cell_of_tet, int64_t max_tets, int64_t* n_tets) {
+    g_err.clear();
+    if (!verts || !cells || !cell_types || !tets_out || !neighbors_out || !cell_of_tet || !n_tets)
+        return fail(MBOIT_ERR_INVALID_ARG, "NULL pointer");
+    if (n_verts < 4 || n_verts > INT32_MAX) return fail(MBOIT_ERR_INVALID_ARG, "n_verts must be in [4, 2^31)");
+    if (n_cells < 1 || max_tets < 1) return fail(MBOIT_ERR_INVALID_ARG, "n_cells and max_tets must be >= 1");
+    if (quantum_log2 < 0 || quantum_log2 > 24) return fail(MBOIT_ERR_INVALID_ARG, "quantum_log2 must be in [0, 24]");
+    const int qs = quantum_log2;
+    auto q = [&](int32_t v, int c) { return (long long)std::nearbyint(std::ldexp((double)verts[4 * (int64_t)v + c], qs)); };
+    int64_t n = 0;
+    std::string err;
+    // one tet, positively oriented on the snapped vertices (exact: 64-bit
+    // differences, 128-bit products)
+    auto emit = [&](int32_t a, int32_t b, int32_t c, int32_t d, int64_t cell) {
+        int32_t t[4] = {a, b, c, d};
+        for (int i = 0; i < 4; ++i)
+            if (t[i] < 0 || t[i] >= n_verts) {
+                err = "cell " + std::to_string(cell) + ": vertex id out of range";
+                return false;
+            }
+        long long e[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c2 = 0; c2 < 3; ++c2) e[r][c2] = q(t[r + 1], c2) - q(t[0], c2);
+        const __int128 det = (__int128)e[0][0] * ((__int128)e[1][1] * e[2][2] - (__int128)e[1][2] * e[2][1]) -
+                             (__int128)e[0][1] * ((__int128)e[1][0] * e[2][2] - (__int128)e[1][2] * e[2][0]) +
+                             (__int128)e[0][2] * ((__int128)e[1][0] * e[2][1] - (__int128)e[1][1] * e[2][0]);
+        if (det == 0) {
+            err = "cell " + std::to_string(cell) + " gives a flat tet after snapping";
+            return false;
+        }
+        if (det < 0) std::swap(t[2], t[3]);
+        if (n >= max_tets) {
+            err = "max_tets too small";
+            return false;
+        }
+        std::memcpy(tets_out + 4 * n, t, sizeof t);
+        cell_of_tet[n++] = cell;
+        return true;
+    };
+    for (int64_t i = 0; i < n_cells; ++i) {
+        const int32_t* c = cells + 6 * i;
+        bool ok = true;
+        switch (cell_types[i]) {
+            case 4:
+                ok = emit(c[0], c[1], c[2], c[3], i);
+                break;
+            case 5: {
+                // base quad c0 c1 c2 c3: cut along the diagonal holding its smallest id
+                const int32_t mn = std::min(std::min(c[0], c[1]), std::min(c[2], c[3]));
+                const int j = (mn == c[0] || mn == c[2]) ? 0 : 1;
+                ok = emit(c[j], c[j + 1], c[j + 2], c[4], i) && emit(c[j], c[j + 2], c[(j + 3) & 3], c[4], i);
+                break;
+            }
+            case 6: {
+                // the smallest id becomes local vertex 0: swap the triangles if
+                // it is on top, then rotate them; its two quad faces are cut
+                // through it, the opposite quad (1 2 5 4) through its smallest
+                int im = 0;
+                for (int k = 1; k < 6; ++k)
+                    if (c[k] < c[im]) im = k;
+                const int lo = im < 3 ? 0 : 3, hi = 3 - lo, r = im % 3;
+                int32_t v[6];
+                for (int k = 0; k < 3; ++k) {
+                    v[k] = c[lo + (r + k) % 3];
+                    v[k + 3] = c[hi + (r + k) % 3];
+                }
+                if (std::min(v[1], v[5]) < std::min(v[2], v[4]))
+                    ok = emit(v[0], v[1], v[2], v[5], i) && emit(v[0], v[1], v[5], v[4], i);
+                else
+                    ok = emit(v[0], v[1], v[2], v[4], i) && emit(v[0], v[4], v[2], v[5], i);
+                ok = ok && emit(v[0], v[4], v[5], v[3], i);
+                break;
+            }
+            default:
+                err = "cell " + std::to_string(i) + ": type must be 4, 5 or 6";
+                ok = false;
+        }
+        if (!ok) return fail(MBOIT_ERR_INVALID_ARG, err);
+    }
+    // face neighbours: sort the faces by their vertex triple; equal triples pair up
+    struct Face {
+        int32_t a, b, c, tet, slot;
+    };
+    std::vector<Face> faces((size_t)n * 4);
+    for (int64_t t = 0; t < n; ++t)
+        for (int i = 0; i < 4; ++i) {
+            int32_t f[3], m = 0;
+            for (int k = 0; k < 4; ++k)
+                if (k != i) f[m++] = tets_out[4 * t + k];
+            std::sort(f, f + 3);
+            faces[(size_t)(4 * t + i)] = Face{f[0], f[1], f[2], (int32_t)t, i};
+        }
+    std::sort(faces.begin(), faces.end(), [](const Face& x, const Face& y) {
+        return x.a != y.a ? x.a < y.a : x.b != y.b ? x.b < y.b : x.c < y.c;
+    });
+    for (int64_t t = 0; t < 4 * n; ++t) neighbors_out[t] = -1;
+    for (size_t k = 0; k < faces.size();) {
+        size_t e = k + 1;
+        while (e < faces.size() && faces[e].a == faces[k].a && faces[e].b == faces[k].b && faces[e].c == faces[k].c) ++e;
+        if (e - k > 2) return fail(MBOIT_ERR_INVALID_ARG, "a face is shared by more than two tets");
+        if (e - k == 2) {
+            neighbors_out[4 * (int64_t)faces[k].tet + faces[k].slot] = faces[k + 1].tet;
+            neighbors_out[4 * (int64_t)faces[k + 1].tet + faces[k + 1].slot] = faces[k].tet;
+        }
+        k = e;
+    }
+    *n_tets = n;
+    return MBOIT_OK;
+}
+
 size_t mboit_moment_image_bytes(int32_t width, int32_t height, int32_t moment_set, int32_t storage) {
     if (width < 1 || height < 1) return 0;
     const bool power = (moment_set == MBOIT_POWER4 || moment_set == MBOIT_POWER6 || moment_set == MBOIT_POWER8) &&

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import paper_2501_12581_gb300 as pkg
+import scenes
 from paper_2501_12581_gb300 import build as pkg_build
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mboit.h")
@@ -232,3 +233,28 @@ def test_unpack_moments_layouts():
                 if nm > 5:
                     want += [o + 5 * P + (nm - 5) * px + c for c in range(nm - 5)]
                 assert s[px].tolist() == want
+
+
+def test_split_cells_matches_oracle_and_rejects_bad_cells(lib):
+    """The library's mixed-cell split gives the oracle's tets in the same
+    order (both cut quads along the min-id diagonal and orient on the
+    snapped vertices) and the face neighbours of the scene module; bad cells
+    are rejected before anything is written out."""
+    import oracle
+    m = scenes.mixed_mesh(n=5, n_pieces=3, width=4, height=4, seed=17)
+    t, nb, cot = pkg.mboit_split_cells(m.verts, m.cells, m.cell_types, m.quantum_log2)
+    to, co = oracle.split_cells(m)
+    np.testing.assert_array_equal(t, to)
+    np.testing.assert_array_equal(cot, co)
+    np.testing.assert_array_equal(nb, scenes.tet_neighbors(t))
+    V = np.array([[0, 0, 0, 0], [1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0], [1, 1, 1, 0], [2, 0, 0, 0]], np.float32)
+
+    def split(cells, types, q=14):
+        return pkg.mboit_split_cells(V, np.array(cells, np.int32).reshape(-1, 6), np.array(types, np.int32), q)
+    assert split([0, 1, 2, 3, -1, -1], [4])[0].shape == (1, 4)
+    for cells, types in (([0, 1, 2, 3, -1, -1], [7]),          # unknown type
+                         ([0, 1, 2, 9, -1, -1], [4]),          # vertex id out of range
+                         ([0, 1, 5, 3, -1, -1], [4]),          # flat (0, 1, 5 collinear)
+                         ([0, 1, 2, 3, -1, -1] * 3, [4] * 3)):  # one face in three tets
+        with pytest.raises(pkg.MboitError):
+            split(cells, types)
