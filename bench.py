@@ -645,7 +645,8 @@ def main():
         frame()
         vol.synchronize()
         v0 = sc.views[0]
-        pix = sample_pixels(v0.width, v0.height, 8, 4) if args.workload == "blobs512" else sample_pixels(v0.width, v0.height, 1, 1)
+        big = v0.width * v0.height > (1 << 18)  # above 512^2: every 8th row, 4th column (a bounded CPU sample)
+        pix = sample_pixels(v0.width, v0.height, 8, 4) if big else sample_pixels(v0.width, v0.height, 1, 1)
         r, dt = time_oracle(sc, pix)
         ns = int(r["nsamples"].sum())
         got = rgba.view(-1, 4)[torch.from_numpy(pix).cuda()].double().cpu().numpy()
