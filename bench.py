@@ -656,7 +656,7 @@ def main():
                    "oracle_mboit_vs_exact_rmse": float(np.sqrt(((r["mboit"] - r["exact"]) ** 2).mean())),
                    "oracle_mboit_vs_exact_max": float(np.abs(r["mboit"] - r["exact"]).max())}
         cpu_baseline = {"value": ns / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-                        "sample": f"{pix.size} pixels (every 8th row, 4th column) of the frame, {ns} samples, "
+                        "sample": f"{pix.size} pixels ({'every 8th row, 4th column' if big else 'all'}) of the frame, {ns} samples, "
                                   f"{dt:.1f} s, FP64 single thread"}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
