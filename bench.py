@@ -69,16 +69,22 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when it covers another kernel or the sources changed since."""
+def measured_ncu(kernel, workload):
+    """The committed ncu record of `kernel` on `workload` (DRAM bytes per
+    launch and the binding units' activity), or None when it covers another
+    kernel or workload or the kernel sources changed since."""
     try:
         kv = dict(tok.split("=", 1) for tok in open(TRAFFIC_FILE).read().split() if "=" in tok)
-        if kv.get("kernel") == kernel and kv.get("kernel_sha") == kernel_hash():
-            return int(kv["dram_bytes_per_launch"])
+        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("kernel_sha") == kernel_hash():
+            return {k: float(v) for k, v in kv.items() if k not in ("kernel", "workload", "kernel_sha")}
     except (OSError, ValueError, KeyError):
         pass
     return None
+
+
+def measured_traffic(kernel, workload="blobs512"):
+    rec = measured_ncu(kernel, workload)
+    return int(rec["dram_bytes_per_launch"]) if rec and "dram_bytes_per_launch" in rec else None
 
 
 class ClockSampler:
@@ -377,9 +383,13 @@ def main():
     dom, dname, dflop = (k2s, kname.format(2) + ", frame form (reads the cached samples; reconstruct + blend + resolve)",
                          FLOP_PASS2_FRAME) if p2 >= p1 else \
         (k1s, kname.format(1) + ", frame form (march + moments + sample store)", FLOP_PASS1)
-    traffic = measured_traffic("k_pass2_fused_frame" if p2 >= p1 else "k_pass1_fused_frame")
+    dom_key = "k_pass2_fused_frame" if p2 >= p1 else "k_pass1_fused_frame"
+    traffic = measured_traffic(dom_key, args.workload)
+    ncu_rec = measured_ncu(dom_key, args.workload)
     roofline = {"bound": "alu", "kernel": dname, "achieved": dom["achieved_tflops"], "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": dom["achieved_tflops"] / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "binding_units_ncu": None if ncu_rec is None else
+                {k: v for k, v in ncu_rec.items() if k != "dram_bytes_per_launch"},
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "flop_per_sample": dflop,
                 "launch_ms": dom["launch_ms"], "frame_pass1": k1s, "frame_pass2": k2s,
                 "split_calls": {"pass1_ms": ms_p1, "pass2_ms": ms_p2, "pass2_flop_per_sample": FLOP_PASS2,
