@@ -202,7 +202,9 @@ def config_of(sc, name):
             "projection": "perspective" if v.projection else "orthographic", "step_voxels": sc.step,
             "moments": "4 power, float32", "moment_bias": sc.moment_bias, "overestimation": sc.overestimation,
             "l2": f"inputs larger than L2 ({(sc.values if hasattr(sc, 'leaves') else sc.field).nbytes >> 20} MiB "
-                  "volume re-read every frame)"}
+                  "volume re-read every frame)",
+            **({"step_rule": "adaptive dyadic (a level-L leaf samples every 2^(max_level - L)-th lattice point)"}
+               if getattr(sc, "adaptive_step", False) else {})}
 
 
 def run_reference(args, rank):
@@ -275,6 +277,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="blobs512", choices=["blobs512", "blobs64", "amr", "tets", "mixed"])
     ap.add_argument("--image", type=int, default=0, help="square image size for the main workload (profiling)")
+    ap.add_argument("--adaptive", action="store_true", help="octree workload: the adaptive dyadic step")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-tets", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
@@ -313,6 +316,9 @@ def main():
         return reduce_max(x, world, "cuda")
 
     sc = workload(args.workload)
+    if args.adaptive:
+        assert hasattr(sc, "leaves"), "--adaptive applies to the octree workload"
+        sc.adaptive_step = True
     if args.image:
         for vw in sc.views:
             assert vw.width == vw.height, "--image rescales square views only"
