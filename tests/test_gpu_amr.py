@@ -211,3 +211,26 @@ def test_amr_adaptive_step_full_size_sampled(pkg):
     n = vol.stats()["samples_pass1"]
     assert 1.0e9 < n < 1.6e9  # 4.05 G with the fixed step
     vol.close()
+
+
+@pytest.mark.parametrize("ms, st, beta, tol", [("power6", "f32", 5e-5, 1e-3), ("trig6", "f16", 2e-3, 3e-3)])
+def test_amr_adaptive_step_other_moment_sets(pkg, ms, st, beta, tol):
+    """The adaptive step's sample weight reaches the 6-power-moment and the
+    trigonometric bodies too: frame image against the oracle's adaptive
+    render within each set's tolerance, sample counts exact."""
+    import copy
+    import torch
+    sc = copy.copy(scenes.amr_blobs(base=4, max_level=2, width=40, height=36, n_pieces=4))
+    sc.adaptive_step = True
+    sc.moment_set, sc.storage, sc.moment_bias = ms, st, beta
+    vol = pkg.Volume(sc)
+    v = sc.views
+    mom = vol.moments_for(v)
+    col = pkg.Volume.color_buffer(v)
+    vol.render_frame(v, mom, col)
+    vol.synchronize()
+    torch.cuda.synchronize()
+    ref = oracle.render_amr(sc, want=("mboit", "nsamples"))
+    assert vol.stats()["samples_pass1"] == int(ref["nsamples"].sum())
+    assert np.abs(col.view(-1, 4).cpu().numpy() - ref["mboit"]).max() <= tol
+    vol.close()
