@@ -39,9 +39,18 @@ UNIT = "Gsamples/s"
 # colour accumulation 9).  FMA = 2 FLOPs.  In the batched frame pass 2 reads
 # the values pass 1 stored, so it skips the position and the trilinear
 # interpolation; pass 1 stores 4 bytes per lattice point, pass 2 reads them.
-FLOP_PASS1 = 43
-FLOP_PASS2 = 76
-FLOP_PASS2_FRAME = FLOP_PASS2 - 6 - 21
+# FP32 operations per owned sample on the algorithm's path (fma = 2, add / mul = 1;
+# MUFU ops, min / max and conversions not counted):
+# pass 1: position 6, cell fractions 3, trilinear 21, table coordinate 3,
+#   extinction lerp 2, depth warp 2, moments 12 (m0 add, four fma, three products);
+# pass 2 from the sample cache: table coordinate 3, extinction lerp 2, opacity
+#   1 - e^-a 11 (series branch), depth warp 2, moment bound 35 (both branches'
+#   arithmetic, which the kernel evaluates before selecting), exponent 1,
+#   weight 1, colour 13; the split form adds the march (position, fractions,
+#   trilinear: 30).
+FLOP_PASS1 = 49
+FLOP_PASS2_FRAME = 68
+FLOP_PASS2 = FLOP_PASS2_FRAME + 6 + 3 + 21
 CACHE_BYTES_PER_SAMPLE = 4
 # FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x
 # 2 FLOP x 2.070 GHz.
