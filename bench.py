@@ -51,11 +51,13 @@ UNIT = "Gsamples/s"
 FLOP_PASS1 = 49
 FLOP_PASS2_FRAME = 68
 FLOP_PASS2 = FLOP_PASS2_FRAME + 6 + 3 + 21
+FLOP_FRAME_ONE_LAUNCH = FLOP_PASS1 + FLOP_PASS2_FRAME   # both passes of a sample in one kernel
 CACHE_BYTES_PER_SAMPLE = 4
 # FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x
 # 2 FLOP x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 KERNEL_SOURCES = ["paper_2501_12581_gb300/csrc/mboit_grid.cuh", "paper_2501_12581_gb300/csrc/mboit_grid.cu",
+                  "paper_2501_12581_gb300/csrc/mboit_grid_frame.cu",
                   "paper_2501_12581_gb300/csrc/mboit_common.cuh", "paper_2501_12581_gb300/csrc/mboit_device.cuh",
                   "paper_2501_12581_gb300/csrc/mboit_trig.cuh", "paper_2501_12581_gb300/csrc/mboit_power.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "frame_fused_blobs512_traffic.txt")
@@ -392,13 +394,23 @@ def main():
         if hbm:
             d["hbm_frac_of_measured"] = d["cache_gbs"] / hbm
         return d
-    k1s = kstats(p1, FLOP_PASS1, CACHE_BYTES_PER_SAMPLE)
-    k2s = kstats(p2, FLOP_PASS2_FRAME, CACHE_BYTES_PER_SAMPLE)
-    kname = "k_pass{}_fused" if not (hasattr(sc, "leaves") or hasattr(sc, "tets") or hasattr(sc, "cells")) else "k_pass{}_unit"
-    dom, dname, dflop = (k2s, kname.format(2) + ", frame form (reads the cached samples; reconstruct + blend + resolve)",
-                         FLOP_PASS2_FRAME) if p2 >= p1 else \
-        (k1s, kname.format(1) + ", frame form (march + moments + sample store)", FLOP_PASS1)
-    dom_key = "k_pass2_fused_frame" if p2 >= p1 else "k_pass1_fused_frame"
+    launches = stf["frame_launches"]
+    if launches == 1:
+        # one kernel per frame: the event pair brackets it, the second pair is empty
+        k1s = kstats(p1 + p2, FLOP_FRAME_ONE_LAUNCH, 2 * CACHE_BYTES_PER_SAMPLE)
+        frame_kernels = {"frame_one_launch": k1s}
+        dom, dflop, dom_key = k1s, FLOP_FRAME_ONE_LAUNCH, "k_frame_fused"
+        dname = ("k_frame_fused, one launch per frame (per ray tile: march + moments + sample store, "
+                 "then reconstruct + blend + resolve)")
+    else:
+        k1s = kstats(p1, FLOP_PASS1, CACHE_BYTES_PER_SAMPLE)
+        k2s = kstats(p2, FLOP_PASS2_FRAME, CACHE_BYTES_PER_SAMPLE)
+        frame_kernels = {"frame_pass1": k1s, "frame_pass2": k2s}
+        kname = "k_pass{}_fused" if not (hasattr(sc, "leaves") or hasattr(sc, "tets") or hasattr(sc, "cells")) else "k_pass{}_unit"
+        dom, dname, dflop = (k2s, kname.format(2) + ", frame form (reads the cached samples; reconstruct + blend + resolve)",
+                             FLOP_PASS2_FRAME) if p2 >= p1 else \
+            (k1s, kname.format(1) + ", frame form (march + moments + sample store)", FLOP_PASS1)
+        dom_key = "k_pass2_fused_frame" if p2 >= p1 else "k_pass1_fused_frame"
     traffic = measured_traffic(dom_key, args.workload)
     ncu_rec = measured_ncu(dom_key, args.workload)
     roofline = {"bound": "alu", "kernel": dname, "achieved": dom["achieved_tflops"], "peak": FP32_PEAK_TFLOPS,
@@ -406,7 +418,7 @@ def main():
                 "binding_units_ncu": None if ncu_rec is None else
                 {k: v for k, v in ncu_rec.items() if k != "dram_bytes_per_launch"},
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "flop_per_sample": dflop,
-                "launch_ms": dom["launch_ms"], "frame_pass1": k1s, "frame_pass2": k2s,
+                "launch_ms": dom["launch_ms"], **frame_kernels,
                 "split_calls": {"pass1_ms": ms_p1, "pass2_ms": ms_p2, "pass2_flop_per_sample": FLOP_PASS2,
                                 "pass2_achieved_tflops": FLOP_PASS2 * samples / (ms_p2 * 1e-3) / 1e12}}
 
@@ -688,16 +700,18 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": dict(config_of(sc, args.workload), parallelism="replicas" if world > 1 else "single",
-                          form="batched: 2 persistent kernels per frame, CUDA graph",
+                          form=("batched: 1 persistent kernel per frame (pass 1 then pass 2 per ray tile), CUDA graph"
+                                if launches == 1 else "batched: 2 persistent kernels per frame, CUDA graph"),
                           tuning={"pass1": tuning[0], "pass2": tuning[1],
-                                  "packet": "4x8" if tuning[2] == pkg.MBOIT_PACKET_4X8 else "8x4"}),
+                                  "packet": "4x8" if tuning[2] == pkg.MBOIT_PACKET_4X8 else "8x4",
+                                  "frame_launches": launches}),
            "samples_per_frame": samples, "ms_per_frame": ms_max, "singular_pixels": st["singular_pixels"], "per_piece_fp32": per_piece,
            "sortlast_gpu": sortlast, "amr_72_pieces": amr, "tets_72_pieces": tets,
            "mixed_cells_72_pieces": mixed,
            "gear_teeth_stress": gear,
            "precision_sweep_amr_2048": sweep,
            "quality": quality, "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
-           "gpu_launches": 2 * args.steps, "clocks": clk.summary()}
+           "gpu_launches": launches * args.steps, "clocks": clk.summary()}
     vol.close()
     if rank == 0:
         print(json.dumps(out))

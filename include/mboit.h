@@ -210,7 +210,8 @@ typedef struct {
                                  * recorded in its graph); -1 before the first frame */
     float frame_pass2_ms;       /* the same for pass 2 */
     int32_t packet;             /* mboit_packet in use (see mboit_set_packet) */
-    int32_t reserved2;
+    int32_t frame_launches;     /* kernel launches of mboit_render_frame (see mboit_set_frame_launches);
+                                 * with 1, frame_pass1_ms is that launch and frame_pass2_ms about 0 */
 } mboit_stats;
 
 /* Number of window configurations of the fused passes.  Each fused kernel
@@ -352,6 +353,17 @@ MBOIT_API mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* v
  * captured frame graphs are re-recorded. */
 MBOIT_API mboit_status mboit_set_tuning(mboit_volume v, int32_t pass1, int32_t pass2);
 
+/* Number of kernel launches of mboit_render_frame: 2 (pass 1, then pass 2
+ * over the whole frame) or 1 (Sec. 4.1-4.2 per ray tile: the
+ * warp that marched every selected piece of its 32 rays holds their summed
+ * moments, so it blends those rays at once, from the sample values it just
+ * stored; window configuration: pass 1's).  Both give bit-identical images and
+ * moments.  Default: 1 for MBOIT_GRID volumes with MBOIT_POWER4, else 2.
+ * 1 is for MBOIT_GRID volumes with MBOIT_POWER4 only, else
+ * MBOIT_ERR_UNSUPPORTED; other values MBOIT_ERR_INVALID_ARG.  Captured frame
+ * graphs are re-recorded. */
+MBOIT_API mboit_status mboit_set_frame_launches(mboit_volume v, int32_t launches);
+
 /* Selects the ray packet of every pass (mboit_packet).  Results do not
  * depend on it (every ray is marched alone); speed does.  Captured frame
  * graphs are re-recorded. */
@@ -361,8 +373,13 @@ MBOIT_API mboit_status mboit_set_packet(mboit_volume v, int32_t packet);
  * eligible window configuration of pass 1 and of pass 2 on these views (3
  * launches each, CUDA events on `stream`, after one warm launch), and keeps
  * the packet with the smallest sum of its fastest pass-1 and pass-2 times
- * and those two configurations; writes pass 1's, pass 2's configuration and
- * the packet to chosen[0..2] (HOST, may be NULL).  The buffers are as for
+ * and those two configurations.  For regular grids with four power moments
+ * it then times, on that packet and with the frame's sample cache, the frame
+ * in those two launches against one launch (mboit_set_frame_launches) in
+ * each eligible configuration, and keeps the faster form (in one launch, the
+ * configuration found there is pass 1's).  Writes pass 1's, pass 2's
+ * configuration and the packet to chosen[0..2] (HOST, may be NULL); the form
+ * is in mboit_stats.frame_launches.  The buffers are as for
  * mboit_render_frame and are overwritten.  Synchronous. */
 MBOIT_API mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch,
                                       float* rgba, void* stream, int32_t* chosen);

@@ -37,7 +37,8 @@ MBOIT_FLAG_RAW_SUM, MBOIT_FLAG_DETERMINISTIC, MBOIT_FLAG_ADAPTIVE_STEP = 0x1, 0x
 EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume", "mboit_destroy_volume",
             "mboit_add_piece", "mboit_render_moments", "mboit_reconstruct_blend", "mboit_composite",
             "mboit_render_frame", "mboit_render_frame_host", "mboit_synchronize", "mboit_get_stats",
-            "mboit_render_moments_noalloc", "mboit_set_tuning", "mboit_set_packet", "mboit_autotune",
+            "mboit_render_moments_noalloc", "mboit_set_tuning", "mboit_set_packet", "mboit_set_frame_launches",
+            "mboit_autotune",
             "mboit_render_sortlast", "mboit_split_cells"]
 MBOIT_NUM_TUNINGS = 5
 
@@ -72,7 +73,7 @@ class mboit_stats(ctypes.Structure):
                 ("tuning_pass1", ctypes.c_int32), ("tuning_pass2", ctypes.c_int32),
                 ("sortlast_segments", ctypes.c_int64), ("sortlast_max_segments", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("frame_pass1_ms", ctypes.c_float), ("frame_pass2_ms", ctypes.c_float),
-                ("packet", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("packet", ctypes.c_int32), ("frame_launches", ctypes.c_int32)]
 
 
 _lib = None
@@ -103,6 +104,7 @@ def load_library(path=LIB_PATH):
         "mboit_render_moments_noalloc": (ctypes.c_int, [P, P, P, I32, P, P]),
         "mboit_set_tuning": (ctypes.c_int, [P, I32, I32]),
         "mboit_set_packet": (ctypes.c_int, [P, I32]),
+        "mboit_set_frame_launches": (ctypes.c_int, [P, I32]),
         "mboit_autotune": (ctypes.c_int, [P, P, I32, P, P, P, P]),
         "mboit_render_sortlast": (ctypes.c_int, [P, P, I32, P, P, P]),
         "mboit_split_cells": (ctypes.c_int, [P, I64, P, P, I64, I32, P, P, P, I64, P]),
@@ -267,6 +269,10 @@ def mboit_set_tuning(v, pass1, pass2):
 
 def mboit_set_packet(v, packet):
     _check(load_library().mboit_set_packet(v, int(packet)))
+
+
+def mboit_set_frame_launches(v, launches):
+    _check(load_library().mboit_set_frame_launches(v, int(launches)))
 
 
 def mboit_autotune(v, views, moments_scratch, rgba, stream=None):
@@ -442,6 +448,9 @@ class Volume:
 
     def set_packet(self, packet):
         mboit_set_packet(self.handle, packet)
+
+    def set_frame_launches(self, launches):
+        mboit_set_frame_launches(self.handle, launches)
 
     def autotune(self, views, moments_scratch, rgba, stream=None):
         return mboit_autotune(self.handle, views, moments_scratch, rgba, stream)

@@ -95,6 +95,7 @@ struct mboit_volume_s {
     std::vector<GraphEntry> graphs;
     int32_t tune1 = 0, tune2 = 0;
     int32_t packet = MBOIT_PACKET_8X4;
+    int32_t frame_launches = 2;  // 1: one launch per frame (grids with four power moments: the default)
     // sort-last baseline buffers (grow only)
     int32_t* sl_counts = nullptr;
     int64_t* sl_starts = nullptr;
@@ -761,6 +762,7 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
     v->nbricks = (int64_t)g.nbx * g.nby * g.nbz;
     v->field_bytes = (size_t)g.nx * g.ny * g.nz * sizeof(float);
     v->kind = d->kind;
+    v->frame_launches = (d->kind == MBOIT_GRID && d->moment_set == MBOIT_POWER4) ? 1 : 2;
     if (is_amr) {
         g.field = nullptr;
         v->nbricks = d->n_leaves;  // the units of an octree are its leaves
@@ -1114,9 +1116,16 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
         cudaError_t e = cudaMemsetAsync(&v->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), cs);
         // external record nodes: the events are recorded each time the graph runs
         if (e == cudaSuccess) e = cudaEventRecordWithFlags(v->frame_ev[0], cs, cudaEventRecordExternal);
-        if (e == cudaSuccess) e = pass1_batched(v, mask, vt, moments_scratch, cs, tc);
-        if (e == cudaSuccess) e = cudaEventRecordWithFlags(v->frame_ev[1], cs, cudaEventRecordExternal);
-        if (e == cudaSuccess) e = pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved, cs, tc);
+        if (v->frame_launches == 1) {
+            if (e == cudaSuccess)
+                e = mb::launch_frame_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba, mb::kColorResolved,
+                                           v->d_ctr, cs, v->tune1, tc);
+            if (e == cudaSuccess) e = cudaEventRecordWithFlags(v->frame_ev[1], cs, cudaEventRecordExternal);
+        } else {
+            if (e == cudaSuccess) e = pass1_batched(v, mask, vt, moments_scratch, cs, tc);
+            if (e == cudaSuccess) e = cudaEventRecordWithFlags(v->frame_ev[1], cs, cudaEventRecordExternal);
+            if (e == cudaSuccess) e = pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved, cs, tc);
+        }
         if (e == cudaSuccess) e = cudaEventRecordWithFlags(v->frame_ev[2], cs, cudaEventRecordExternal);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
@@ -1196,7 +1205,7 @@ mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out) {
     out->sortlast_max_segments = c.max_segments;
     out->reserved = 0;
     out->packet = v->packet;
-    out->reserved2 = 0;
+    out->frame_launches = v->frame_launches;
     out->frame_pass1_ms = out->frame_pass2_ms = -1.0f;
     if (v->frame_timed && (cudaEventElapsedTime(&out->frame_pass1_ms, v->frame_ev[0], v->frame_ev[1]) != cudaSuccess ||
                            cudaEventElapsedTime(&out->frame_pass2_ms, v->frame_ev[1], v->frame_ev[2]) != cudaSuccess)) {
@@ -1269,6 +1278,18 @@ mboit_status mboit_set_tuning(mboit_volume v, int32_t pass1, int32_t pass2) {
     std::lock_guard<std::mutex> lk(v->mu);
     v->tune1 = pass1;
     v->tune2 = pass2;
+    drop_graphs(v);
+    return MBOIT_OK;
+}
+
+mboit_status mboit_set_frame_launches(mboit_volume v, int32_t launches) {
+    g_err.clear();
+    if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
+    if (launches != 1 && launches != 2) return fail(MBOIT_ERR_INVALID_ARG, "launches must be 1 or 2");
+    if (launches == 1 && (v->kind != MBOIT_GRID || v->desc.moment_set != MBOIT_POWER4))
+        return fail(MBOIT_ERR_UNSUPPORTED, "the one-launch frame covers regular grids with four power moments");
+    std::lock_guard<std::mutex> lk(v->mu);
+    v->frame_launches = launches;
     drop_graphs(v);
     return MBOIT_OK;
 }
@@ -1349,9 +1370,55 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
             best[2] = packet;
         }
     }
+    // The frame's form (grids, four power moments): the two launches with the
+    // chosen configurations against one launch in each eligible
+    // configuration, all with the frame's sample cache, on the chosen packet.
+    int launches = v->frame_launches, cfg1 = best[0];
+    if (ce == cudaSuccess && grid && v->desc.moment_set == MBOIT_POWER4) {
+        mb::ViewTable vt;
+        mb::TileCache tc;
+        st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set), best[2]);
+        if (st == MBOIT_OK) st = tile_cache(v, vt, tc);
+        if (st != MBOIT_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
+        }
+        if (tc.vals) {
+            float best_ms = 3.0e38f;
+            for (int form = 0; form <= mb::kNumStageConfigs && ce == cudaSuccess; ++form) {
+                // form 0: two launches; form c + 1: one launch in configuration c
+                if (form > 0 && !mb::stage_config_eligible(v->grid, form - 1)) continue;
+                auto launch = [&]() {
+                    if (form > 0)
+                        return mb::launch_frame_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba,
+                                                      mb::kColorResolved, v->d_ctr, s, form - 1, tc);
+                    cudaError_t e = mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s,
+                                                           best[0], tc);
+                    return e != cudaSuccess ? e
+                                            : mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba,
+                                                                     mb::kColorResolved, v->d_ctr, s, best[1], tc);
+                };
+                ce = launch();
+                if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+                for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = launch();
+                if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                if (ce == cudaSuccess && ms < best_ms) {
+                    best_ms = ms;
+                    launches = form == 0 ? 2 : 1;
+                    cfg1 = form == 0 ? best[0] : form - 1;
+                }
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (ce != cudaSuccess) return fail(MBOIT_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+    best[0] = cfg1;
+    v->frame_launches = launches;
     v->tune1 = best[0];
     v->tune2 = best[1];
     v->packet = best[2];

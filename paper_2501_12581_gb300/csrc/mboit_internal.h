@@ -117,6 +117,13 @@ cudaError_t launch_pass1_fused(const GridD& g, const float4* tf, const uint8_t* 
 cudaError_t launch_pass2_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
                                const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
                                int cfg = 0, TileCache cache = TileCache{});
+// One-launch frame (four power moments, regular grid): each warp takes its
+// ray tile through pass 1 and then pass 2, RESOLVED or REDUCED colour; the
+// cache rows are handed out as in the two-launch frame (no room: pass 2
+// marches again).  Results equal launch_pass1_fused + launch_pass2_fused.
+cudaError_t launch_frame_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
+                               void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s, int cfg,
+                               TileCache cache);
 // Rows a frame's tile cache needs over the domain box of `g` (sum over the
 // ray tiles of kmax - kmin + 1), added to *rows.
 cudaError_t launch_tile_rows(const GridD& g, const ViewTable& vt, unsigned long long* rows, cudaStream_t s);

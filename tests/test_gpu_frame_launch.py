@@ -1,0 +1,141 @@
+"""The one-launch frame (each warp blends its ray tile right after marching
+it, Sec. 4.1-4.2 per tile) against the two-launch frame: the same moments
+and images bit for bit, in every window configuration, for several and
+ragged views, with a brick mask, with the sample cache capped (tiles that
+get no rows march the field again) and at the full 512^3 / 2048^2 size; the
+two-launch frame's parity against the oracle is tested elsewhere, and here
+once more for the form the autotuner picks."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from tests import _scenes_small as small
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    import __graft_entry__
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+    import paper_2501_12581_gb300 as p
+    return p
+
+
+def frame(pkg, vol, views, launches, tuning=None):
+    import torch
+    vol.set_frame_launches(launches)
+    if tuning is not None:
+        vol.set_tuning(*tuning)
+    m, c = pkg.Volume.moment_buffer(views), pkg.Volume.color_buffer(views)
+    vol.render_frame(views, m, c)
+    vol.render_frame(views, m, c)      # the replayed graph
+    vol.synchronize()
+    torch.cuda.synchronize()
+    st = vol.stats()
+    assert st["frame_launches"] == launches
+    assert st["samples_pass1"] == st["samples_pass2"]
+    return m, c, st
+
+
+def test_one_launch_equals_two_launches_every_tuning(pkg):
+    import torch
+    sc = scenes.blobs64(width=96, height=80)
+    views = [sc.views[0],
+             scenes.ortho_view(sc.dims, (0.3, -0.8, 0.5), 37, 23),
+             scenes.perspective_view(sc.dims, (-0.5, 0.6, -0.62), 61, 37, fov_deg=40.0),
+             small.axis_view(sc.dims, 9, 5, -10.0, 4.0, centre=(300.0, 300.0))]   # misses the domain
+    vol = pkg.Volume(sc)
+    for cfg in range(pkg.MBOIT_NUM_TUNINGS):
+        m2, c2, s2 = frame(pkg, vol, views, 2, (cfg, cfg))
+        m1, c1, s1 = frame(pkg, vol, views, 1, (cfg, cfg))
+        assert torch.equal(m1, m2), f"moments differ in configuration {cfg}"
+        assert torch.equal(c1, c2), f"image differs in configuration {cfg}"
+        assert s1["samples_pass1"] == s2["samples_pass1"] > 0
+        assert s1["frame_pass1_ms"] > 0
+    vol.close()
+
+
+def test_one_launch_with_a_brick_mask(pkg):
+    """A volume whose pieces leave bricks unowned: the kernel variant that
+    tests each sample's brick."""
+    import torch
+    sc = scenes.blobs64(width=64, height=48)
+    pob = np.asarray(sc.piece_of_brick).copy()
+    pob[pob == sc.n_pieces - 1] = -1
+    sc = dataclasses.replace(sc, piece_of_brick=pob, n_pieces=sc.n_pieces - 1)
+    vol = pkg.Volume(sc)
+    m2, c2, _ = frame(pkg, vol, sc.views, 2)
+    m1, c1, _ = frame(pkg, vol, sc.views, 1)
+    assert torch.equal(m1, m2) and torch.equal(c1, c2)
+    ref = oracle.render_grid(sc, want=("mboit",))
+    assert np.abs(c1.view(-1, 4).cpu().numpy() - ref["mboit"]).max() <= 2e-4
+    vol.close()
+
+
+def test_one_launch_cache_fallback(pkg, monkeypatch):
+    import torch
+    sc = scenes.blobs64(width=96, height=80)
+    want = None
+    for cap in (None, "0", "3000"):
+        if cap is None:
+            monkeypatch.delenv("MBOIT_FRAME_CACHE_ROWS", raising=False)
+        else:
+            monkeypatch.setenv("MBOIT_FRAME_CACHE_ROWS", cap)
+        vol = pkg.Volume(sc)
+        m, c, st = frame(pkg, vol, sc.views, 1)
+        assert st["samples_pass1"] > 0
+        if want is None:
+            want = (m.clone(), c.clone())
+        else:
+            assert torch.equal(m, want[0]) and torch.equal(c, want[1])
+        vol.close()
+
+
+def test_one_launch_full_size(pkg):
+    """512^3 field, 64 pieces, 2048^2: the two forms agree bit for bit."""
+    import torch
+    sc = scenes.blobs512()
+    vol = pkg.Volume(sc)
+    m2, c2, s2 = frame(pkg, vol, sc.views, 2, (3, 3))
+    m1, c1, s1 = frame(pkg, vol, sc.views, 1, (3, 3))
+    assert torch.equal(m1, m2) and torch.equal(c1, c2)
+    assert s1["samples_pass1"] == s2["samples_pass1"] > 1e9
+    vol.close()
+
+
+def test_autotune_form_matches_oracle(pkg):
+    sc = scenes.blobs64(width=64, height=48)
+    vol = pkg.Volume(sc)
+    mom, col = pkg.Volume.moment_buffer(sc.views), pkg.Volume.color_buffer(sc.views)
+    p1, p2, pk = vol.autotune(sc.views, mom, col)
+    st = vol.stats()
+    assert st["frame_launches"] in (1, 2)
+    assert (st["tuning_pass1"], st["tuning_pass2"], st["packet"]) == (p1, p2, pk)
+    vol.render_frame(sc.views, mom, col)
+    vol.synchronize()
+    ref = oracle.render_grid(sc, want=("mboit",))
+    assert np.abs(col.view(-1, 4).cpu().numpy() - ref["mboit"]).max() <= 2e-4
+    vol.close()
+
+
+def test_one_launch_refused_outside_its_scope(pkg):
+    sc = scenes.amr_blobs(base=4, max_level=2, width=45, height=38, n_pieces=5)
+    vol = pkg.Volume(sc)
+    with pytest.raises(pkg.MboitError) as e:
+        vol.set_frame_launches(1)
+    assert e.value.status == 4                  # MBOIT_ERR_UNSUPPORTED
+    vol.set_frame_launches(2)
+    vol.close()
+    g = pkg.Volume(scenes.blobs64(width=16, height=16))
+    for bad in (0, 3, -1):
+        with pytest.raises(pkg.MboitError) as e:
+            g.set_frame_launches(bad)
+        assert e.value.status == 1              # MBOIT_ERR_INVALID_ARG
+    g.close()

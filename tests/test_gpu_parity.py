@@ -133,7 +133,8 @@ def test_frame_sample_cache_equals_split_calls(pkg, blobs):
     m3, c3 = pkg.Volume.moment_buffer(sc.views), pkg.Volume.color_buffer(sc.views)
     vol.render_frame(sc.views, m3, c3)
     st = vol.stats()
-    assert st["frame_pass1_ms"] > 0 and st["frame_pass2_ms"] > 0
+    # one launch (the default for this volume): the second event pair is empty
+    assert st["frame_pass1_ms"] > 0 and (st["frame_pass2_ms"] > 0 or st["frame_launches"] == 1)
 
 
 def test_frame_cache_fallback_marches_again(pkg, monkeypatch):
