@@ -354,14 +354,14 @@ MBOIT_API mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* v
 MBOIT_API mboit_status mboit_set_tuning(mboit_volume v, int32_t pass1, int32_t pass2);
 
 /* Number of kernel launches of mboit_render_frame: 2 (pass 1, then pass 2
- * over the whole frame) or 1 (Sec. 4.1-4.2 per ray tile: the
- * warp that marched every selected piece of its 32 rays holds their summed
- * moments, so it blends those rays at once, from the sample values it just
- * stored; window configuration: pass 1's).  Both give bit-identical images and
- * moments.  Default: 1 for MBOIT_GRID volumes with MBOIT_POWER4, else 2.
- * 1 is for MBOIT_GRID volumes with MBOIT_POWER4 only, else
- * MBOIT_ERR_UNSUPPORTED; other values MBOIT_ERR_INVALID_ARG.  Captured frame
- * graphs are re-recorded. */
+ * over the whole frame) or 1 (Sec. 4.1-4.2 per ray tile: the warp that
+ * marched every selected piece of its 32 rays holds their summed moments, so
+ * it blends those rays at once, from the sample values it just stored; grid
+ * window configuration: pass 1's).  Both give bit-identical images and
+ * moments.  Default: 1 for MBOIT_GRID volumes with MBOIT_POWER4, else 2
+ * (mboit_autotune times both forms).  1 is for MBOIT_POWER4 volumes (every
+ * kind) only, else MBOIT_ERR_UNSUPPORTED; other values MBOIT_ERR_INVALID_ARG.
+ * Captured frame graphs are re-recorded. */
 MBOIT_API mboit_status mboit_set_frame_launches(mboit_volume v, int32_t launches);
 
 /* Selects the ray packet of every pass (mboit_packet).  Results do not
@@ -373,8 +373,8 @@ MBOIT_API mboit_status mboit_set_packet(mboit_volume v, int32_t packet);
  * eligible window configuration of pass 1 and of pass 2 on these views (3
  * launches each, CUDA events on `stream`, after one warm launch), and keeps
  * the packet with the smallest sum of its fastest pass-1 and pass-2 times
- * and those two configurations.  For regular grids with four power moments
- * it then times, on that packet and with the frame's sample cache, the frame
+ * and those two configurations.  For volumes with four power moments it
+ * then times, on that packet and with the frame's sample cache, the frame
  * in those two launches against one launch (mboit_set_frame_launches) in
  * each eligible configuration, and keeps the faster form (in one launch, the
  * configuration found there is pass 1's).  Writes pass 1's, pass 2's

@@ -95,7 +95,7 @@ struct mboit_volume_s {
     std::vector<GraphEntry> graphs;
     int32_t tune1 = 0, tune2 = 0;
     int32_t packet = MBOIT_PACKET_8X4;
-    int32_t frame_launches = 2;  // 1: one launch per frame (grids with four power moments: the default)
+    int32_t frame_launches = 2;  // 1: one launch per frame (four power moments)
     // sort-last baseline buffers (grow only)
     int32_t* sl_counts = nullptr;
     int64_t* sl_starts = nullptr;
@@ -461,6 +461,16 @@ cudaError_t pass2_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTab
     return mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s, v->tune2, tc);
 }
 
+// The one-launch frame of the volume's kind (four power moments).
+cudaError_t frame_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, void* moments, float* color,
+                          cudaStream_t s, int cfg, mb::TileCache tc) {
+    if (v->kind == MBOIT_AMR)
+        return mb::launch_frame_amr(v->amr, v->d_tf, mask, vt, moments, color, mb::kColorResolved, v->d_ctr, s, tc);
+    if (v->kind == MBOIT_TET)
+        return mb::launch_frame_tet(v->tet, v->d_tf, mask, vt, moments, color, mb::kColorResolved, v->d_ctr, s, tc);
+    return mb::launch_frame_fused(v->grid, v->d_tf, mask, vt, moments, color, mb::kColorResolved, v->d_ctr, s, cfg, tc);
+}
+
 // The tile-row sample cache of a frame: its exact row count for these views
 // (one small kernel, synchronous; done once per recorded frame graph), then
 // grow-only buffers.  Left off (c.vals NULL, pass 2 marches again) when the
@@ -762,6 +772,8 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
     v->nbricks = (int64_t)g.nbx * g.nby * g.nbz;
     v->field_bytes = (size_t)g.nx * g.ny * g.nz * sizeof(float);
     v->kind = d->kind;
+    // one launch where it measured faster without tuning (grids); the
+    // autotuner times both forms for every kind with four power moments
     v->frame_launches = (d->kind == MBOIT_GRID && d->moment_set == MBOIT_POWER4) ? 1 : 2;
     if (is_amr) {
         g.field = nullptr;
@@ -1117,9 +1129,7 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
         // external record nodes: the events are recorded each time the graph runs
         if (e == cudaSuccess) e = cudaEventRecordWithFlags(v->frame_ev[0], cs, cudaEventRecordExternal);
         if (v->frame_launches == 1) {
-            if (e == cudaSuccess)
-                e = mb::launch_frame_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba, mb::kColorResolved,
-                                           v->d_ctr, cs, v->tune1, tc);
+            if (e == cudaSuccess) e = frame_batched(v, mask, vt, moments_scratch, rgba, cs, v->tune1, tc);
             if (e == cudaSuccess) e = cudaEventRecordWithFlags(v->frame_ev[1], cs, cudaEventRecordExternal);
         } else {
             if (e == cudaSuccess) e = pass1_batched(v, mask, vt, moments_scratch, cs, tc);
@@ -1286,8 +1296,8 @@ mboit_status mboit_set_frame_launches(mboit_volume v, int32_t launches) {
     g_err.clear();
     if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
     if (launches != 1 && launches != 2) return fail(MBOIT_ERR_INVALID_ARG, "launches must be 1 or 2");
-    if (launches == 1 && (v->kind != MBOIT_GRID || v->desc.moment_set != MBOIT_POWER4))
-        return fail(MBOIT_ERR_UNSUPPORTED, "the one-launch frame covers regular grids with four power moments");
+    if (launches == 1 && v->desc.moment_set != MBOIT_POWER4)
+        return fail(MBOIT_ERR_UNSUPPORTED, "the one-launch frame covers four power moments");
     std::lock_guard<std::mutex> lk(v->mu);
     v->frame_launches = launches;
     drop_graphs(v);
@@ -1370,11 +1380,11 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
             best[2] = packet;
         }
     }
-    // The frame's form (grids, four power moments): the two launches with the
-    // chosen configurations against one launch in each eligible
-    // configuration, all with the frame's sample cache, on the chosen packet.
+    // The frame's form (four power moments): the two launches with the chosen
+    // configurations against one launch in each eligible configuration, all
+    // with the frame's sample cache, on the chosen packet.
     int launches = v->frame_launches, cfg1 = best[0];
-    if (ce == cudaSuccess && grid && v->desc.moment_set == MBOIT_POWER4) {
+    if (ce == cudaSuccess && v->desc.moment_set == MBOIT_POWER4) {
         mb::ViewTable vt;
         mb::TileCache tc;
         st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set), best[2]);
@@ -1388,11 +1398,15 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
             float best_ms = 3.0e38f;
             for (int form = 0; form <= mb::kNumStageConfigs && ce == cudaSuccess; ++form) {
                 // form 0: two launches; form c + 1: one launch in configuration c
-                if (form > 0 && !mb::stage_config_eligible(v->grid, form - 1)) continue;
+                if (form > 0 && (grid ? !mb::stage_config_eligible(v->grid, form - 1) : form != 1)) continue;
                 auto launch = [&]() {
-                    if (form > 0)
-                        return mb::launch_frame_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba,
-                                                      mb::kColorResolved, v->d_ctr, s, form - 1, tc);
+                    if (form > 0) return frame_batched(v, mask, vt, moments_scratch, rgba, s, form - 1, tc);
+                    if (!grid) {
+                        cudaError_t e = pass1_batched(v, mask, vt, moments_scratch, s, tc);
+                        return e != cudaSuccess ? e
+                                                : pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved,
+                                                                s, tc);
+                    }
                     cudaError_t e = mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s,
                                                            best[0], tc);
                     return e != cudaSuccess ? e

@@ -19,24 +19,6 @@
 namespace mb {
 namespace {
 
-// Pass-2 body of a pixel from the float32 moments pass 1 left in registers.
-__device__ __forceinline__ BlendBody blend_body_of(const float4* s_tf, const GridD& g, const ViewSlot& S,
-                                                   const MomentBody& mb, bool valid) {
-    BlendBody b;
-    b.s_tf = s_tf;
-    b.tf_scale = g.tf_scale;
-    b.tf_bias = g.tf_bias;
-    b.amax = g.absorbance_max;
-    b.wa = S.v.warp_a;
-    b.wb = S.v.warp_b;
-    b.w0 = g.overestimation;
-    const float m[5] = {valid ? mb.m0 : 0.0f, valid ? mb.m1 : 0.0f, valid ? mb.m2 : 0.0f, valid ? mb.m3 : 0.0f,
-                        valid ? mb.m4 : 0.0f};
-    b.F = make_frame(m, g.moment_bias, g.bias_vector);
-    b.b0 = m[0];
-    return b;
-}
-
 template <bool kSel, class Cfg>
 __global__ void __launch_bounds__(256) k_frame_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
                                                      const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,

@@ -153,6 +153,10 @@ cudaError_t launch_pass1_amr(const AmrD& a, const float4* tf, const uint8_t* uni
 cudaError_t launch_pass2_amr(const AmrD& a, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
                              const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
                              TileCache cache = TileCache{});
+// One-launch frame (four power moments), as launch_frame_fused.
+cudaError_t launch_frame_amr(const AmrD& a, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
+                             void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
+                             TileCache cache);
 cudaError_t launch_pass1_piece(const AmrD& a, const float4* tf, const int32_t* piece_of_unit, int32_t piece,
                                const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
                                void* moments, Counters* ctr, cudaStream_t s);
@@ -170,6 +174,9 @@ cudaError_t launch_pass1_tet(const TetD& m, const float4* tf, const uint8_t* uni
 cudaError_t launch_pass2_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
                              const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
                              TileCache cache = TileCache{});
+cudaError_t launch_frame_tet(const TetD& m, const float4* tf, const uint8_t* unit_sel, const ViewTable& vt,
+                             void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
+                             TileCache cache);
 cudaError_t launch_pass1_piece(const TetD& m, const float4* tf, const int32_t* piece_of_unit, int32_t piece,
                                const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,
                                void* moments, Counters* ctr, cudaStream_t s);

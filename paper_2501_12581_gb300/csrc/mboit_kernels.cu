@@ -290,6 +290,7 @@ int persistent_blocks(const void* fn, int threads, size_t smem) {
 
 cudaError_t prepare_grid_kernels();
 cudaError_t prepare_frame_kernels();
+cudaError_t prepare_frame_unit_kernels();
 cudaError_t prepare_unit_kernels();
 
 cudaError_t prepare_kernels() {
@@ -308,6 +309,7 @@ cudaError_t prepare_kernels() {
     }
     cudaError_t e = prepare_grid_kernels();
     if (e == cudaSuccess) e = prepare_frame_kernels();
+    if (e == cudaSuccess) e = prepare_frame_unit_kernels();
     if (e == cudaSuccess) e = prepare_unit_kernels();
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -1,8 +1,9 @@
 """The one-launch frame (each warp blends its ray tile right after marching
 it, Sec. 4.1-4.2 per tile) against the two-launch frame: the same moments
-and images bit for bit, in every window configuration, for several and
-ragged views, with a brick mask, with the sample cache capped (tiles that
-get no rows march the field again) and at the full 512^3 / 2048^2 size; the
+and images bit for bit, on grids in every window configuration, for several
+and ragged views, with a brick mask, with the sample cache capped (tiles
+that get no rows march the field again) and at the full 512^3 / 2048^2
+size, and on octrees (fixed and adaptive step) and tetrahedral meshes; the
 two-launch frame's parity against the oracle is tested elsewhere, and here
 once more for the form the autotuner picks."""
 import dataclasses
@@ -125,9 +126,34 @@ def test_autotune_form_matches_oracle(pkg):
     vol.close()
 
 
+@pytest.mark.parametrize("kind", ["amr", "amr_adaptive", "tets"])
+def test_one_launch_units_equal_two_launches(pkg, kind, monkeypatch):
+    """Octrees and meshes: the same bits in one launch and in two, also with the
+    cache capped so that some tiles march again."""
+    import torch
+    if kind == "tets":
+        sc = scenes.tet_mesh(n=8, n_pieces=3, width=43, height=29, seed=7)
+    else:
+        sc = scenes.amr_blobs(base=4, max_level=2, width=45, height=38, n_pieces=5)
+        sc.adaptive_step = kind == "amr_adaptive"
+    for cap in (None, "40"):
+        if cap is None:
+            monkeypatch.delenv("MBOIT_FRAME_CACHE_ROWS", raising=False)
+        else:
+            monkeypatch.setenv("MBOIT_FRAME_CACHE_ROWS", cap)
+        vol = pkg.Volume(sc)
+        m2, c2, s2 = frame(pkg, vol, sc.views, 2)
+        m1, c1, s1 = frame(pkg, vol, sc.views, 1)
+        assert torch.equal(m1, m2) and torch.equal(c1, c2)
+        assert s1["samples_pass1"] == s2["samples_pass1"] > 0
+        vol.close()
+
+
 def test_one_launch_refused_outside_its_scope(pkg):
-    sc = scenes.amr_blobs(base=4, max_level=2, width=45, height=38, n_pieces=5)
+    sc = scenes.blobs64(width=32, height=24)
+    sc.moment_set, sc.storage = "power6", "f32"
     vol = pkg.Volume(sc)
+    assert vol.stats()["frame_launches"] == 2
     with pytest.raises(pkg.MboitError) as e:
         vol.set_frame_launches(1)
     assert e.value.status == 4                  # MBOIT_ERR_UNSUPPORTED
