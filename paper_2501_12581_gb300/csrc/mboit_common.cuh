@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -178,7 +179,9 @@ struct BlendBody {
     float b0;
     float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     unsigned n = 0;
-    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) {
+    // kGeneric: the frame is known to be generic (no test of its kind)
+    template <bool kGeneric = false>
+    __device__ __forceinline__ void sample(float t, float val, float ws) {
         const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
         const int i = (int)xt;
         const float f = xt - (float)i;
@@ -186,14 +189,22 @@ struct BlendBody {
         const float a = fmin_(ffma(f, de.w, e0.w) * ws, amax);
         const float alpha = one_minus_exp_neg(a);
         const float z = warp_depth(t, wa, wb);
-        const float wgt = transmittance(F, z, w0) * alpha;
+        const float wgt = (kGeneric ? transmittance_generic(F, z, w0) : transmittance(F, z, w0)) * alpha;
         C.x = ffma(wgt, ffma(f, de.x, e0.x), C.x);
         C.y = ffma(wgt, ffma(f, de.y, e0.y), C.y);
         C.z = ffma(wgt, ffma(f, de.z, e0.z), C.z);
         C.w += wgt;
         ++n;
     }
+    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) { sample<false>(t, val, ws); }
     __device__ __forceinline__ bool singular() const { return F.kind == kFrameOneAtom || F.kind == kFrameTwoAtoms; }
+};
+
+// The pass-2 body for a warp whose lanes with samples all have a generic
+// frame: the same operations without the per-sample test of the frame's kind.
+struct GenericBlend {
+    BlendBody& b;
+    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) { b.sample<true>(t, val, ws); }
 };
 
 // Bytes of one moment slab of P pixels in the volume's format.
@@ -602,6 +613,23 @@ __device__ __forceinline__ void march_rows(const GridD& g, const float* __restri
         }
         __syncwarp();  // every lane is done with the chunk before it is refilled
     }
+}
+
+// Pass 2 from the tile's cache rows.  With four power moments, a warp whose
+// lanes with samples all have a generic frame (lanes without samples never
+// call the body) takes the loop without the per-sample test of the frame's
+// kind; the arithmetic, and so the result, is the same.
+template <bool kSel, bool kTagged = false, class Body>
+__device__ __forceinline__ void blend_rows(const GridD& g, const float* __restrict__ rows, int kmin, int kmax, int k0,
+                                           int k1, float* __restrict__ buf, Body& body, int tmask = 0) {
+    if constexpr (std::is_same<Body, BlendBody>::value) {
+        if (__all_sync(0xffffffffu, k0 > k1 || body.F.kind == kFrameGeneric)) {
+            GenericBlend gb{body};
+            march_rows<kSel, GenericBlend, kTagged>(g, rows, kmin, kmax, k0, k1, buf, gb, tmask);
+            return;
+        }
+    }
+    march_rows<kSel, Body, kTagged>(g, rows, kmin, kmax, k0, k1, buf, body, tmask);
 }
 
 // Pass 1: the tile's rows of the cache (lane 0 takes them, all lanes get the

@@ -294,30 +294,34 @@ MB_HD Frame make_frame(const float m_in[5], float moment_bias, const float bias_
 
 MB_HD float step_weight(float x, float z0, float w0) { return x < z0 ? 1.0f : (x == z0 ? w0 : 0.0f); }
 
+// Alg. 3 for a generic frame (three support points): fraction A(z0) of the
+// optical depth in front of warped depth z0.
+MB_HD float bound_generic(const Frame& F, float z0, float w0) {
+    const float inv_s = F.p0, nmu = F.p1, g = F.p2, inv_d = F.p3;
+    float x0 = ffma(z0, inv_s, nmu);
+    float y3 = ffma(x0, x0 - g, -1.0f);
+    float e = y3 * inv_d;                         // leading coefficient of K(., x0)
+    float rho0 = frcp(ffma(y3, e, ffma(x0, x0, 1.0f)));
+    // x0 outside [x1, x2]: left of both iff K'(x0) < 0
+    float slope = ffma(ffma(2.0f, x0, -g), e, x0);
+    float A_out = slope < 0.0f ? w0 * rho0 : ffma(w0 - 1.0f, rho0, 1.0f);
+    // x1 < x0 < x2 (y3 < 0, so e < 0): the weight rho1 of the smaller root
+    // from the representation's moments of order 0 and 1 (rho0 + rho1 +
+    // rho2 = 1, rho0 x0 + rho1 x1 + rho2 x2 = 0) and the roots' sum and
+    // spread (-c1/e, sqrt(c1^2 - 4 e c0)/|e|):
+    //   rho1 = R/2 + (R c1/2 - rho0 x0 e) / sqrt(c1^2 - 4 e c0),  R = 1 - rho0
+    float c1 = ffma(-g, e, x0);
+    float c0 = 1.0f - e;
+    float disc = fmax_(ffma(c1, c1, -4.0f * e * c0), 1e-30f);
+    float R = 1.0f - rho0;
+    float rho1 = ffma(ffma(0.5f * R, c1, -rho0 * x0 * e), frsqrt_fast(disc), 0.5f * R);
+    rho1 = fclamp(rho1, 0.0f, R);
+    return y3 < 0.0f ? ffma(w0, rho0, rho1) : A_out;
+}
+
 // Alg. 3: fraction A(z0) of the optical depth in front of warped depth z0.
 MB_HD float bound_fraction(const Frame& F, float z0, float w0) {
-    if (F.kind == kFrameGeneric) {
-        const float inv_s = F.p0, nmu = F.p1, g = F.p2, inv_d = F.p3;
-        float x0 = ffma(z0, inv_s, nmu);
-        float y3 = ffma(x0, x0 - g, -1.0f);
-        float e = y3 * inv_d;                         // leading coefficient of K(., x0)
-        float rho0 = frcp(ffma(y3, e, ffma(x0, x0, 1.0f)));
-        // x0 outside [x1, x2]: left of both iff K'(x0) < 0
-        float slope = ffma(ffma(2.0f, x0, -g), e, x0);
-        float A_out = slope < 0.0f ? w0 * rho0 : ffma(w0 - 1.0f, rho0, 1.0f);
-        // x1 < x0 < x2 (y3 < 0, so e < 0): the weight rho1 of the smaller root
-        // from the representation's moments of order 0 and 1 (rho0 + rho1 +
-        // rho2 = 1, rho0 x0 + rho1 x1 + rho2 x2 = 0) and the roots' sum and
-        // spread (-c1/e, sqrt(c1^2 - 4 e c0)/|e|):
-        //   rho1 = R/2 + (R c1/2 - rho0 x0 e) / sqrt(c1^2 - 4 e c0),  R = 1 - rho0
-        float c1 = ffma(-g, e, x0);
-        float c0 = 1.0f - e;
-        float disc = fmax_(ffma(c1, c1, -4.0f * e * c0), 1e-30f);
-        float R = 1.0f - rho0;
-        float rho1 = ffma(ffma(0.5f * R, c1, -rho0 * x0 * e), frsqrt_fast(disc), 0.5f * R);
-        rho1 = fclamp(rho1, 0.0f, R);
-        return y3 < 0.0f ? ffma(w0, rho0, rho1) : A_out;
-    }
+    if (F.kind == kFrameGeneric) return bound_generic(F, z0, w0);
     if (F.kind == kFrameOneAtom) return step_weight(F.p0, z0, w0);
     if (F.kind == kFrameTwoAtoms) return F.p2 * step_weight(F.p0, z0, w0) + F.p3 * step_weight(F.p1, z0, w0);
     return 0.0f;
@@ -325,6 +329,10 @@ MB_HD float bound_fraction(const Frame& F, float z0, float w0) {
 
 MB_HD float transmittance(const Frame& F, float z0, float w0) {
     float A = bound_fraction(F, z0, w0);
+    return fclamp(fexp2(-F.m0_log2e * A), 0.0f, 1.0f);
+}
+MB_HD float transmittance_generic(const Frame& F, float z0, float w0) {
+    float A = bound_generic(F, z0, w0);
     return fclamp(fexp2(-F.m0_log2e * A), 0.0f, 1.0f);
 }
 

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ Gri
         const long long tb = kCache ? cache.tile_base[tile] : -1;
         if (kCache && tb >= 0) {
             const int kmin = __reduce_min_sync(0xffffffffu, k0), kmax = __reduce_max_sync(0xffffffffu, k1);
-            march_rows<kSel>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, win, body);
+            blend_rows<kSel>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, win, body);
         } else {
             march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
         }

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256) k_frame_fused(const __grid_constant__ Gri
         if (valid && body.singular()) atomicAdd(&ctr->singular, 1ull);
         __syncwarp();  // the rows' stores before any lane reads them; the window slot is free
         if (base >= 0)
-            march_rows<kSel>(g, cache.vals + base * 32, kmin, kmax, k0, k1, win, body);
+            blend_rows<kSel>(g, cache.vals + base * 32, kmin, kmax, k0, k1, win, body);
         else
             march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
         if (valid) {

@@ -616,9 +616,9 @@ __global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 2>::value : 2) k_p
                 tmask = tag_mask(a.max_level);
             }
             if (tagged)
-                march_rows<true, decltype(body), true>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, buf, body, tmask);
+                blend_rows<true, true>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, buf, body, tmask);
             else
-                march_rows<true>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, buf, body);
+                blend_rows<true>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, buf, body);
         } else {
             march_unit<kSel>(a, sel, o, d, k0, k1, body);
         }
