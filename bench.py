@@ -99,7 +99,9 @@ def measured_traffic(kernel, workload="blobs512"):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    """nvidia-smi clock/throttle samples every 25 ms while running; begin() and
+    end() bracket the timed region, and the summary keeps the samples that
+    arrived inside it (else the first one after it)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -107,12 +109,13 @@ class ClockSampler:
     def __init__(self, device):
         self.device = device
         self.proc = None
-        self.lines = []
+        self.lines = []          # (arrival time, line)
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                          "-lms", "25", "-i", str(self.device)], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -122,7 +125,21 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def begin(self, wait_s=5.0):
+        """Waits for the first sample (nvidia-smi takes a while to start), then
+        marks the start of the timed region."""
+        t_end = time.monotonic() + wait_s
+        while self.proc and not self.lines and time.monotonic() < t_end:
+            time.sleep(0.01)
+        self.t0 = time.monotonic()
+
+    def end(self):
+        self.t1 = time.monotonic()
+        t_end = self.t1 + 1.0   # one sample after the region, in case none fell inside it
+        while self.proc and not any(t > self.t1 for t, _ in self.lines) and time.monotonic() < t_end:
+            time.sleep(0.01)
 
     def __exit__(self, *a):
         if self.proc:
@@ -136,7 +153,10 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        inside = [ln for t, ln in self.lines if self.t0 is not None and self.t0 <= t <= self.t1]
+        if not inside and self.t1 is not None:
+            inside = [ln for t, ln in self.lines if t > self.t1][:1]
+        for ln in inside:
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 9:
                 continue
@@ -150,7 +170,8 @@ class ClockSampler:
                     reasons.add(n)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "in_timed_region": bool(self.t0 is not None and any(self.t0 <= t <= self.t1 for t, _ in self.lines))}
 
 
 def sample_pixels(width, height, row_stride, col_stride):
@@ -359,7 +380,9 @@ def main():
         frame()
     vol.synchronize()
     with ClockSampler(local) as clk:
+        clk.begin()
         ms = timed(frame, args.steps)
+        clk.end()
     vol.synchronize()
     st = vol.stats()
     samples = st["samples_pass1"]
