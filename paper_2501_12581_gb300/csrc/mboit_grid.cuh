@@ -196,6 +196,22 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
 }
 
 
+// Pass 2 marching the field: with four power moments, a warp whose lanes
+// with samples all have a generic frame takes the body without the
+// per-sample test of the frame's kind (the same arithmetic and result).
+template <class Cfg, bool kSel, class Body>
+__device__ __forceinline__ void blend_fused(const GridD& g, const uint8_t* __restrict__ sel, float* __restrict__ win,
+                                            const float o[3], const float d[3], int k0, int k1, Body& body) {
+    if constexpr (std::is_same<Body, BlendBody>::value) {
+        if (__all_sync(0xffffffffu, k0 > k1 || body.F.kind == kFrameGeneric)) {
+            GenericBlend gb{body};
+            march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, gb);
+            return;
+        }
+    }
+    march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
+}
+
 template <bool kSel, class Cfg, int MS, bool kCache = false>
 __global__ void __launch_bounds__(256, MS == 0 ? 5 : 1) k_pass1_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
                                                      const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
@@ -259,7 +275,7 @@ __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ Gri
             const int kmin = __reduce_min_sync(0xffffffffu, k0), kmax = __reduce_max_sync(0xffffffffu, k1);
             blend_rows<kSel>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, win, body);
         } else {
-            march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
+            blend_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
         }
         if (valid) {
             float4* out = reinterpret_cast<float4*>(color + S.color_off) + pix;

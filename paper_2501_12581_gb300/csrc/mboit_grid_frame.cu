@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_frame_fused(const __grid_constant__ Gri
         if (base >= 0)
             blend_rows<kSel>(g, cache.vals + base * 32, kmin, kmax, k0, k1, win, body);
         else
-            march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
+            blend_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
         if (valid) {
             float4* out = reinterpret_cast<float4*>(color + S.color_off) + pix;
             if (mode == kColorResolved)
