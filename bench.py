@@ -418,18 +418,20 @@ def main():
             d["hbm_frac_of_measured"] = d["cache_gbs"] / hbm
         return d
     launches = stf["frame_launches"]
+    unit_scene = hasattr(sc, "leaves") or hasattr(sc, "tets") or hasattr(sc, "cells")
     if launches == 1:
         # one kernel per frame: the event pair brackets it, the second pair is empty
         k1s = kstats(p1 + p2, FLOP_FRAME_ONE_LAUNCH, 2 * CACHE_BYTES_PER_SAMPLE)
         frame_kernels = {"frame_one_launch": k1s}
-        dom, dflop, dom_key = k1s, FLOP_FRAME_ONE_LAUNCH, "k_frame_fused"
-        dname = ("k_frame_fused, one launch per frame (per ray tile: march + moments + sample store, "
+        dom_key = "k_frame_unit" if unit_scene else "k_frame_fused"
+        dom, dflop = k1s, FLOP_FRAME_ONE_LAUNCH
+        dname = (dom_key + ", one launch per frame (per ray tile: march + moments + sample store, "
                  "then reconstruct + blend + resolve)")
     else:
         k1s = kstats(p1, FLOP_PASS1, CACHE_BYTES_PER_SAMPLE)
         k2s = kstats(p2, FLOP_PASS2_FRAME, CACHE_BYTES_PER_SAMPLE)
         frame_kernels = {"frame_pass1": k1s, "frame_pass2": k2s}
-        kname = "k_pass{}_fused" if not (hasattr(sc, "leaves") or hasattr(sc, "tets") or hasattr(sc, "cells")) else "k_pass{}_unit"
+        kname = "k_pass{}_unit" if unit_scene else "k_pass{}_fused"
         dom, dname, dflop = (k2s, kname.format(2) + ", frame form (reads the cached samples; reconstruct + blend + resolve)",
                              FLOP_PASS2_FRAME) if p2 >= p1 else \
             (k1s, kname.format(1) + ", frame form (march + moments + sample store)", FLOP_PASS1)

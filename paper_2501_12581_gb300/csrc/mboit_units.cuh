@@ -52,12 +52,12 @@ __device__ __forceinline__ int unit_of(const AmrD& a, const float p[3]) {
     return __ldg(a.fmap + ((size_t)fz * a.fdim + fy) * (size_t)a.fdim + fx);
 }
 
-// Local coordinates (p - origin) / h are exact in float32 (h a power of two,
-// |p - origin| below the leaf size), so cells match the oracle's.
-__device__ __forceinline__ float unit_value(const AmrD& a, const float p[3], int leaf) {
-    const int4 L = __ldg(a.leaves + leaf);
-    const float inv_h = __int_as_float((127 - (a.max_level - L.w)) << 23);  // 2^-(max_level - level)
-    const float qx = (p[0] - (float)L.x) * inv_h, qy = (p[1] - (float)L.y) * inv_h, qz = (p[2] - (float)L.z) * inv_h;
+// Trilinear value in leaf `leaf` with origin lo (finest cells) and inverse
+// cell size inv_h.  Local coordinates (p - origin) / h are exact in float32
+// (h a power of two, |p - origin| below the leaf size), so cells match the
+// oracle's.
+__device__ __forceinline__ float leaf_value(const AmrD& a, const float p[3], int leaf, const float lo[3], float inv_h) {
+    const float qx = (p[0] - lo[0]) * inv_h, qy = (p[1] - lo[1]) * inv_h, qz = (p[2] - lo[2]) * inv_h;
     const int cx = min((int)qx, a.nv - 2), cy = min((int)qy, a.nv - 2), cz = min((int)qz, a.nv - 2);
     const int nv = a.nv;
     const float* __restrict__ c = a.values + (size_t)leaf * nv * nv * nv + (cz * nv + cy) * nv + cx;
@@ -65,6 +65,49 @@ __device__ __forceinline__ float unit_value(const AmrD& a, const float p[3], int
     return trilinear8(__ldg(c), __ldg(c + 1), __ldg(c + sy), __ldg(c + sy + 1), __ldg(c + sz), __ldg(c + sz + 1),
                       __ldg(c + sz + sy), __ldg(c + sz + sy + 1), qx - (float)cx, qy - (float)cy, qz - (float)cz);
 }
+
+__device__ __forceinline__ float leaf_inv_h(const AmrD& a, int level) {
+    return __int_as_float((127 - (a.max_level - level)) << 23);  // 2^-(max_level - level)
+}
+
+__device__ __forceinline__ float unit_value(const AmrD& a, const float p[3], int leaf) {
+    const int4 L = __ldg(a.leaves + leaf);
+    const float lo[3] = {(float)L.x, (float)L.y, (float)L.z};
+    return leaf_value(a, p, leaf, lo, leaf_inv_h(a, L.w));
+}
+
+// The leaf of a lane's previous sample: a sample inside its box (half-open,
+// in finest cells, like the finest-brick map it stands for) skips the map and
+// the leaf table, two dependent loads.  u: the leaf, or -1 where the box
+// holds no selected leaf (outside every leaf, or a leaf of a piece left out).
+struct LeafCache {
+    int u = -1, shift = 0;
+    float lo[3] = {0.0f, 0.0f, 0.0f}, size = 0.0f, inv_h = 0.0f;   // size 0: no box
+    __device__ __forceinline__ bool holds(const float p[3]) const {
+        // p - lo is exact (both below 2^24, p >= lo in the test that matters)
+        return p[0] >= lo[0] && p[0] - lo[0] < size && p[1] >= lo[1] && p[1] - lo[1] < size && p[2] >= lo[2] &&
+               p[2] - lo[2] < size;
+    }
+    // Looks p up; returns its selected leaf or -1.
+    template <bool kSel>
+    __device__ __forceinline__ int find(const AmrD& a, const uint8_t* __restrict__ sel, const float p[3]) {
+        if (holds(p)) return u;
+        const int v = unit_of(a, p);
+        if (v < 0) {
+            // no leaf: forget the box, so the next sample looks up again
+            u = -1;
+            size = 0.0f;
+            return -1;
+        }
+        const int4 L = __ldg(a.leaves + v);
+        size = (float)((1 << a.g.brick_log2) << (a.max_level - L.w));
+        lo[0] = (float)L.x; lo[1] = (float)L.y; lo[2] = (float)L.z;
+        inv_h = leaf_inv_h(a, L.w);
+        shift = a.max_level - L.w;
+        u = (kSel && !__ldg(sel + v)) ? -1 : v;
+        return u;
+    }
+};
 
 __device__ __forceinline__ void unit_box(const AmrD& a, const float[3], int leaf, float lo[3], float& size) {
     const int4 L = __ldg(a.leaves + leaf);
@@ -503,21 +546,22 @@ __device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restr
         const int kmin = __reduce_min_sync(full, any ? k0 : 0x7fffffff);
         const int kmax = __reduce_max_sync(full, any ? k1 : -1);
         if (any) store.seek(k0);
+        LeafCache lc;
         for (int k = kmin; k <= kmax; ++k) {
             if (k < k0 || k > k1) continue;
             const float t = lattice_t(k, g.step);
             const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
-            const int u = unit_of(a, p);
-            if (u < 0 || (kSel && !__ldg(sel + u))) {
+            const int u = lc.find<kSel>(a, sel, p);
+            if (u < 0) {
                 store.put(__int_as_float(0x7fc00000));
                 continue;
             }
-            const int shift = step_shift(a, u);
+            const int shift = lc.shift;
             if (k & ((1 << shift) - 1)) {
                 store.put(__int_as_float(0x7fc00000));
                 continue;
             }
-            const float val = tag_shift(unit_value(a, p, u), shift, tag_mask(a.max_level));
+            const float val = tag_shift(leaf_value(a, p, u, lc.lo, lc.inv_h), shift, tag_mask(a.max_level));
             store.put(val);
             body(t, val, (float)(1 << shift));
         }
@@ -526,14 +570,15 @@ __device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restr
     if (k0 > k1) return;
     store.seek(k0);
     const float tz = lattice_t(k1, g.step);
+    LeafCache lc;
     for (float t = lattice_t(k0, g.step); t <= tz; t += g.step) {
         const float p[3] = {ffma(t, d[0], o[0]), ffma(t, d[1], o[1]), ffma(t, d[2], o[2])};
-        const int u = unit_of(a, p);
-        if (u < 0 || (kSel && !__ldg(sel + u))) {
+        const int u = lc.find<kSel>(a, sel, p);
+        if (u < 0) {
             store.put(__int_as_float(0x7fc00000));
             continue;
         }
-        const float val = unit_value(a, p, u);
+        const float val = leaf_value(a, p, u, lc.lo, lc.inv_h);
         store.put(val);
         body(t, val);
     }
@@ -547,6 +592,9 @@ __device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restr
 #define MB_TET_MIN_BLOCKS 3
 #endif
 template <class V, int kPass> struct MinBlocks { static constexpr int value = kPass == 2 ? 4 : 1; };
+// octrees: 4 for both passes (pass 1 fits 56 registers; at 5 blocks, 48
+// registers, its warps share the L1 that serves their gathers and it slows)
+template <int kPass> struct MinBlocks<AmrD, kPass> { static constexpr int value = 4; };
 template <bool k, int kPass> struct MinBlocks<TetT<k>, kPass> { static constexpr int value = MB_TET_MIN_BLOCKS; };
 
 template <class V, bool kSel, int MS, bool kCache = false>
