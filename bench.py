@@ -389,7 +389,7 @@ def main():
     ms_max = max_over_ranks(ms)
     value = job_rate(samples, world, ms_max)
 
-    # the two kernels of the frame: CUDA events recorded inside its graph, on
+    # the frame's kernels (one or two): CUDA events recorded inside its graph, on
     # the launching stream, averaged over a few frames
     p1 = p2 = 0.0
     nf = max(5, args.steps // 2)

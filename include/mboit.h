@@ -311,7 +311,10 @@ MBOIT_API mboit_status mboit_composite(mboit_volume v, int32_t op, int32_t width
  * the device lacks that memory with 1 GiB to spare, pass 2 samples again
  * (so does every ray tile past the row count in the environment variable
  * MBOIT_FRAME_CACHE_ROWS, read when a graph is recorded, if it is set).
- * The first call for a set of views synchronises once to size the cache. */
+ * The first call for a set of views synchronises once to size the cache.
+ * The frame runs as one kernel launch (each warp takes its ray tile through
+ * pass 1 and then pass 2) or as two (see mboit_set_frame_launches); both
+ * give the same bits. */
 MBOIT_API mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch,
                                 float* rgba, void* stream);
 
