@@ -165,3 +165,36 @@ def test_one_launch_refused_outside_its_scope(pkg):
             g.set_frame_launches(bad)
         assert e.value.status == 1              # MBOIT_ERR_INVALID_ARG
     g.close()
+
+
+def test_one_launch_with_singular_frames_in_every_warp(pkg):
+    """Zero bias, and rays that cross one absorber (a plane at z = 8), two (a
+    second plane at z = 12 for x < 6), many (a block for y >= 10) or none
+    (x >= 12): every 8 x 4 warp holds generic, one- and two-atom and empty
+    frames, so the one-launch kernel takes its blend loop that tests each
+    sample's frame kind.  The transfer function is opaque only above 0.9 and
+    the lattice meets the planes exactly (eye at z = -6.25, step 0.5)."""
+    import torch
+    n = 17
+    field = np.zeros((n, n, n), np.float32)
+    field[8, :, :12] = 1.0
+    field[12, :, :6] = 1.0
+    field[2:15, 10:, :] = 1.0
+    B = 4
+    nb = (n - 1) // B
+    bz = np.repeat(np.arange(nb), nb * nb)
+    pob = (bz >= 2).astype(np.int32)
+    tf = small.constant_tf(0.0)
+    tf[230:, 3] = 0.3
+    sc = scenes.GridScene("planes", field, 2, pob, 2, tf, (np.float32(0.0), np.float32(1.0)), 0.5, [])
+    sc.moment_bias = 0.0
+    view = small.axis_view(sc.dims, 16, 16, -6.25, 16.0, near=2.0, far=40.0)
+    vol = pkg.Volume(sc)
+    m2, c2, s2 = frame(pkg, vol, [view], 2)
+    m1, c1, s1 = frame(pkg, vol, [view], 1)
+    assert torch.equal(m1, m2) and torch.equal(c1, c2)
+    assert s1["singular_pixels"] == s2["singular_pixels"] > 0
+    sc.views = [view]
+    ref = oracle.render_grid(sc, want=("mboit",))
+    assert np.abs(c1.view(-1, 4).cpu().numpy() - ref["mboit"]).max() <= 2e-4
+    vol.close()
