@@ -133,3 +133,68 @@ def linear_tets(n=6, n_pieces=3, seed=21):
     nb = (n + B - 1) // B
     grid = scenes.GridScene("linear_grid", field, 1, np.zeros(nb ** 3, np.int32), 1, tf, (vmin, vmax), 0.5, [])
     return sc, grid
+
+
+# Transfer function of the two-absorber scene: three plateaus of constant
+# (r, g, b, alpha) over the table entries, zero opacity outside them.  A
+# sample whose table coordinate lies inside a plateau (both neighbouring
+# entries in it) takes the plateau's values exactly.
+ABSORBER_A = (0.35, (0.9, 0.3, 0.1))     # alpha, rgb over entries 185..200
+ABSORBER_B = (0.6, (0.1, 0.4, 0.95))     # alpha, rgb over entries 221..255
+
+
+def absorber_tf():
+    tf = np.zeros((256, 4), np.float32)
+    tf[:, 0:3] = 0.5
+    tf[185:201, 3] = ABSORBER_A[0]
+    tf[185:201, 0:3] = ABSORBER_A[1]
+    tf[221:256, 3] = ABSORBER_B[0]
+    tf[221:256, 0:3] = ABSORBER_B[1]
+    return tf
+
+
+def two_absorber_scene(overestimation, moment_bias=0.0):
+    """Every ray crosses one or two absorbing lattice points, at known depths,
+    with known colours, and nothing else absorbs.
+
+    Field: varies with z only inside three x-bands of vertices (0..5, 6..11,
+    12..17); zero except two z-levels of vertices.  An orthographic view looks
+    along +z from z = -8 with step 0.5, so the lattice points sit at
+    z = j + 1/4 and z = j + 3/4 and the trilinear values there are 3/4 and 1/4
+    blends of two vertex values.  Band 1 (g(8) = 1, g(9) = 0.6): lattice values
+    0.75 at z = 7.75 (table coordinate 191.25: absorber A) and 0.9 at 8.25
+    (229.5: absorber B), every other one below table coordinate 185 (zero
+    opacity).  Band 2 (g(7) = 0.6, g(8) = 1): B at 7.75, then A at 8.25.
+    Band 3 (g(8) = 1, g(9) = 0.2): A at 7.75 only (0.8 at 8.25 falls in the
+    zero-opacity gap 201..220).  The log-depth warp's near / far (15.9375,
+    16.0625) lie between the two lattice depths t = 15.75 and 16.25, so the
+    front point warps to exactly -1 and the back one to exactly +1.  Bricks of
+    2 cells; the two points fall in bricks of different z, dealt to 4 pieces.
+
+    Returns (scene, pixels, absorbers): the pixels whose rays stay inside one
+    band, and per pixel the front-to-back list of absorbers ("A" / "B")."""
+    nx, ny, nz = 18, 4, 16
+    field = np.zeros((nz, ny, nx), np.float32)
+    field[8, :, 0:6], field[9, :, 0:6] = 1.0, 0.6
+    field[7, :, 6:12], field[8, :, 6:12] = 0.6, 1.0
+    field[8, :, 12:18], field[9, :, 12:18] = 1.0, 0.2
+    B = 2
+    nb = [(n - 1 + B - 1) // B for n in (nx, ny, nz)]
+    bz, by, bx = np.meshgrid(np.arange(nb[2]), np.arange(nb[1]), np.arange(nb[0]), indexing="ij")
+    pob = ((bz % 2) + 2 * (bx % 2)).astype(np.int32).ravel()
+    sc = scenes.GridScene("two_absorbers", field, 1, pob, 4, absorber_tf(), (np.float32(0.0), np.float32(1.0)),
+                          0.5, [], moment_bias=moment_bias, overestimation=overestimation)
+    W, H = nx - 1, ny - 1
+    # o = eye + ((px + 1/2) / W - 1/2) * W * u: rays at x = px + 1/2, y = py + 1/2
+    view = scenes.View(np.array([W / 2.0, H / 2.0, -8.0], np.float32), np.array([1, 0, 0], np.float32),
+                       np.array([0, 1, 0], np.float32), np.array([0, 0, 1], np.float32), W, H, scenes.ORTHO,
+                       np.float32(W), np.float32(H), np.float32(15.9375), np.float32(16.0625))
+    sc.views = [view]
+    pixels, absorbers = [], []
+    for py in range(H):
+        for px in range(W):
+            if px in (5, 11):
+                continue   # the ray's cell mixes two bands
+            pixels.append(py * W + px)
+            absorbers.append(("A", "B") if px < 5 else ("B", "A") if px < 11 else ("A",))
+    return sc, np.array(pixels, np.int64), absorbers

@@ -995,3 +995,63 @@ def test_mixed_linear_field_equals_grid():
         np.testing.assert_allclose(a["mboit"], b["mboit"], atol=1e-4)
         assert a["nsamples"].sum() > 100
 
+
+
+# --------------------------------------------------------------------------
+# Alg. 1 loop 2 and the resolve (Sec. 4.2, 4.3) at render level
+
+
+def _absorber_values(name, step=0.5, amax=10.0):
+    """(a, alpha, rgb) of absorber A or B from its table plateau (R6/R7:
+    sigma = -ln(1 - alpha_TF) per voxel, a = min(sigma * step, A_max),
+    opacity 1 - e^-a)."""
+    alpha_tf, rgb = small.ABSORBER_A if name == "A" else small.ABSORBER_B
+    sigma = -math.log1p(-float(np.float32(alpha_tf)))
+    a = min(sigma * step, amax)
+    return a, -math.expm1(-a), np.array([float(np.float32(c)) for c in rgb])
+
+
+def _closed_form_raw(absorbers, w0):
+    """Alg. 1 loop 2 with the exact canonical bound of one or two atoms:
+    sample k sees T = exp(-sum_{j<k} a_j - w0 a_k) (the atoms in front count
+    fully, its own atom with the overestimation weight), and adds
+    T alpha_k (r, g, b, 1)."""
+    C = np.zeros(4)
+    front = 0.0
+    for name in absorbers:
+        a, alpha, rgb = _absorber_values(name)
+        T = math.exp(-front - w0 * a)
+        C[:3] += T * alpha * rgb
+        C[3] += T * alpha
+        front += a
+    return C, front
+
+
+@pytest.mark.parametrize("w0", [0.0, W0, 1.0])
+def test_render_one_and_two_absorbers_closed_form(w0):
+    """Rays through one or two absorbing lattice points (depths warped to
+    exactly -1 and +1, zero bias): the raw sum, the renormalised image and the
+    moments equal their closed forms; with w0 = 0 the raw sum is the exact
+    front-to-back blend in all four channels.  A blend with the absorbance a
+    in place of the opacity alpha, a transmittance taken at the next sample's
+    depth, or a resolve that drops the (1 - e^-b0) / C.a factor fails here."""
+    sc, pix, absorbers = small.two_absorber_scene(w0)
+    r = oracle.render_grid(sc, pixels=pix, want=("moments", "raw", "mboit", "exact", "nsamples"))
+    assert np.all(r["nsamples"] == 30)   # z = 0.25, 0.75, ..., 14.75: the domain depth [0, 15) at step 0.5
+    for n, ab in enumerate(absorbers):
+        C, b0 = _closed_form_raw(ab, w0)
+        np.testing.assert_allclose(r["raw"][n], C, rtol=0, atol=1e-13)
+        # stage one: b_j = sum_k a_k z_k^j with z = -1 (front), +1 (back)
+        a = [_absorber_values(x)[0] for x in ab]
+        z = [-1.0, 1.0][:len(ab)]
+        m = [sum(ak * zk ** j for ak, zk in zip(a, z)) for j in range(5)]
+        np.testing.assert_allclose(r["moments"][n], m, rtol=0, atol=1e-13)
+        # resolve (Sec. 4.3): colour renormalised to the alpha of the zeroth moment
+        A = -math.expm1(-b0)
+        np.testing.assert_allclose(r["mboit"][n, :3], C[:3] * A / C[3], rtol=0, atol=1e-13)
+        assert r["mboit"][n, 3] == pytest.approx(A, abs=1e-15)
+        if w0 == 0.0:
+            np.testing.assert_allclose(r["raw"][n], r["exact"][n], rtol=0, atol=1e-13)
+    # the closed form really distinguishes the cases: swapped order changes colour
+    if w0 == W0:
+        assert np.abs(r["raw"][0] - r["raw"][absorbers.index(("B", "A"))]).max() > 0.05
