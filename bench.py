@@ -1,19 +1,24 @@
 """Benchmark of the MBOIT puzzle-piece render on GB300.
 
-Workload (default): 512^3 float32 field (64 Gaussian blobs + 3-octave value
-noise), 64 jittered Morton pieces of 16^3-cell bricks, 2048x2048
-perspective view, step 0.5 voxel, 4 power moments in float32.
+Workload (default, "amr"): brick octree of 81,549 leaves of 8^3 cells over
+three levels (41.8 M cells, finest 832^3), float32 vertex values of the
+512^3 workload's analytic field (64 Gaussian blobs + 3-octave value noise),
+72 Morton pieces of uneven size (largest / smallest = 8), 2560x2560
+perspective view, step 0.5 finest voxel, 4 power moments in float32.
 
 One step = one frame: pass 1 (moments of all pieces, summed) + pass 2
 (transmittance reconstruction, blend, colour sum and renormalisation),
 replayed from a CUDA graph.  value = owned lattice samples per frame (each
-marched once per pass) / frame time, in Gsamples/s, summed over ranks.
+marched once per pass) / frame time, in Gsamples/s, summed over ranks.  The
+512^3 regular-grid workload, the tetrahedral and mixed-cell meshes, the
+gear-teeth stress test and the precision sweep follow as further keys.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle (the only reference this method
-has) on a bounded pixel sample of the same workload.  Under torchrun (N > 1)
-every rank renders its own replica (no data-path collective); rank 0 prints.
+has) on every host core, on a bounded pixel sample of the same workload.
+Under torchrun (N > 1) every rank renders its own replica (no data-path
+collective); rank 0 prints.
 """
 import argparse
 import hashlib
@@ -32,35 +37,28 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gsamples/s & ms/frame: batched mixed-prec vs plain FP32, RMSE vs FP64 oracle"
 UNIT = "Gsamples/s"
-# FP32 FLOPs per owned sample executed by the fused kernels' per-sample code
-# (position 6, trilinear 21, table coordinate 2, extinction lerp 3, warp 2,
-# moment update 9 for pass 1; pass 2 replaces the moment update by opacity 2,
-# colour lerps 9, moment-bound reconstruction 20 (outside case) and the
-# colour accumulation 9).  FMA = 2 FLOPs.  In the batched frame pass 2 reads
-# the values pass 1 stored, so it skips the position and the trilinear
-# interpolation; pass 1 stores 4 bytes per lattice point, pass 2 reads them.
 # FP32 operations per owned sample on the algorithm's path (fma = 2, add / mul = 1;
 # MUFU ops, min / max and conversions not counted):
-# pass 1: position 6, cell fractions 3, trilinear 21, table coordinate 3,
+# pass 1 on a grid: position 6, cell fractions 3, trilinear 21, table coordinate 3,
 #   extinction lerp 2, depth warp 2, moments 12 (m0 add, four fma, three products);
+# pass 1 on an octree: the same plus the leaf-local coordinates (p - origin) / h (6);
 # pass 2 from the sample cache: table coordinate 3, extinction lerp 2, opacity
 #   1 - e^-a 11 (series branch), depth warp 2, moment bound 35 (both branches'
 #   arithmetic, which the kernel evaluates before selecting), exponent 1,
 #   weight 1, colour 13; the split form adds the march (position, fractions,
 #   trilinear: 30).
-FLOP_PASS1 = 49
+FLOP_PASS1 = {"grid": 49, "amr": 55}
 FLOP_PASS2_FRAME = 68
 FLOP_PASS2 = FLOP_PASS2_FRAME + 6 + 3 + 21
-FLOP_FRAME_ONE_LAUNCH = FLOP_PASS1 + FLOP_PASS2_FRAME   # both passes of a sample in one kernel
 CACHE_BYTES_PER_SAMPLE = 4
 # FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x
 # 2 FLOP x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-KERNEL_SOURCES = ["paper_2501_12581_gb300/csrc/mboit_grid.cuh", "paper_2501_12581_gb300/csrc/mboit_grid.cu",
-                  "paper_2501_12581_gb300/csrc/mboit_grid_frame.cu",
-                  "paper_2501_12581_gb300/csrc/mboit_common.cuh", "paper_2501_12581_gb300/csrc/mboit_device.cuh",
-                  "paper_2501_12581_gb300/csrc/mboit_trig.cuh", "paper_2501_12581_gb300/csrc/mboit_power.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "frame_fused_blobs512_traffic.txt")
+CSRC = os.path.join(ROOT, "paper_2501_12581_gb300", "csrc")
+# committed ncu records of the frame kernel per workload (DRAM bytes per launch
+# and the binding units' activity), valid while the kernel sources are unchanged
+NCU_RECORDS = {"blobs512": os.path.join(ROOT, "profiles", "frame_fused_blobs512_traffic.txt"),
+               "amr": os.path.join(ROOT, "profiles", "frame_unit_amr_traffic.txt")}
 
 
 def _measured_peaks():
@@ -74,28 +72,67 @@ MEASURED = _measured_peaks()
 
 
 def kernel_hash():
+    """Hash of every kernel and device-header source of the library (the host
+    side of the C ABI, mboit_api.cu, is left out)."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith((".cu", ".cuh", ".h")) and f != "mboit_api.cu":
+            h.update(f.encode())
+            h.update(open(os.path.join(CSRC, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def measured_ncu(kernel, workload):
     """The committed ncu record of `kernel` on `workload` (DRAM bytes per
-    launch and the binding units' activity), or None when it covers another
-    kernel or workload or the kernel sources changed since."""
+    launch and the binding units' activity), or None when there is none for
+    that kernel and workload or the kernel sources changed since."""
     try:
-        kv = dict(tok.split("=", 1) for tok in open(TRAFFIC_FILE).read().split() if "=" in tok)
+        kv = dict(tok.split("=", 1) for tok in open(NCU_RECORDS[workload]).read().split() if "=" in tok)
         if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("kernel_sha") == kernel_hash():
-            return {k: float(v) for k, v in kv.items() if k not in ("kernel", "workload", "kernel_sha")}
+            return {k: float(v) for k, v in kv.items() if k not in ("kernel", "workload", "kernel_sha", "note")}
     except (OSError, ValueError, KeyError):
         pass
     return None
 
 
-def measured_traffic(kernel, workload="blobs512"):
+def measured_traffic(kernel, workload):
     rec = measured_ncu(kernel, workload)
     return int(rec["dram_bytes_per_launch"]) if rec and "dram_bytes_per_launch" in rec else None
+
+
+def write_ncu_record(csv_path, kernel, workload, samples, out_path):
+    """Writes the record `measured_ncu` reads from an `ncu --page raw --csv`
+    dump of one launch of the frame kernel: DRAM bytes of the launch, the
+    binding units' activity and the owned samples that launch processed."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    hdr, units, vals = rows[0], rows[1], rows[2]
+    d = dict(zip(hdr, vals))
+    u = dict(zip(hdr, units))
+
+    def num(name):
+        v = float(d[name].replace(",", ""))
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}.get(u.get(name, ""), 1)
+        return v * scale
+    dram = num("dram__bytes_read.sum") + num("dram__bytes_write.sum")
+    inst = num("smsp__inst_executed.sum")
+    rec = {"kernel": kernel, "workload": workload, "kernel_sha": kernel_hash(),
+           "dram_bytes_per_launch": int(dram), "samples_per_launch": int(samples),
+           "launch_ms": num("gpu__time_duration.sum") * ({"usecond": 1e-3, "msecond": 1, "nsecond": 1e-6}
+                                                           .get(u.get("gpu__time_duration.sum"), 1)),
+           "issue_active_pct": num("smsp__issue_active.avg.pct_of_peak_sustained_active"),
+           "sm_sol_pct": num("sm__throughput.avg.pct_of_peak_sustained_elapsed"),
+           "l1_data_pipe_pct": num("l1tex__throughput.avg.pct_of_peak_sustained_active"),
+           "l2_throughput_pct": num("lts__throughput.avg.pct_of_peak_sustained_elapsed"),
+           "dram_throughput_pct": num("gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed"),
+           "alu_pipe_pct": num("sm__inst_executed_pipe_alu.avg.pct_of_peak_sustained_active"),
+           "fma_pipe_pct": num("sm__inst_executed_pipe_fma.avg.pct_of_peak_sustained_active"),
+           "xu_pipe_pct": num("sm__inst_executed_pipe_xu.avg.pct_of_peak_sustained_active"),
+           "lsu_pipe_pct": num("sm__inst_executed_pipe_lsu.avg.pct_of_peak_sustained_active"),
+           "inst_per_sample": inst * 32 / samples}
+    with open(out_path, "w") as f:
+        f.write(" ".join(f"{k}={v:.6g}" if isinstance(v, float) else f"{k}={v}" for k, v in rec.items()) + "\n")
+    return rec
 
 
 class ClockSampler:
@@ -180,14 +217,52 @@ def sample_pixels(width, height, row_stride, col_stride):
     return (ys * width + xs).ravel()
 
 
-def time_oracle(sc, pixels):
+def host_cores():
+    """Host cores this process may run on (its affinity mask)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
+def time_oracle(sc, pixels, threads=1, want=("mboit", "exact", "nsamples")):
+    """Runs the FP64 oracle on `pixels`: single-threaded as it stands
+    (threads = 1), or its per-pixel entry on disjoint pixel chunks from a
+    pool of `threads` host threads (ctypes releases the GIL during each call).
+    Returns (results in pixel order, wall seconds)."""
     import oracle
+    from concurrent.futures import ThreadPoolExecutor
     if hasattr(sc, "cells"):
         sc = oracle.tet_scene_of(sc)  # the oracle's own split of mixed cells
+    if threads <= 1:
+        t0 = time.perf_counter()
+        r = oracle.render(sc, pixels=pixels, want=want)
+        return r, time.perf_counter() - t0
+    chunks = [c for c in np.array_split(pixels, 8 * threads) if c.size]
     t0 = time.perf_counter()
-    r = oracle.render(sc, pixels=pixels, want=("mboit", "exact", "nsamples"))
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(lambda c: oracle.render(sc, pixels=c, want=want), chunks))
     dt = time.perf_counter() - t0
-    return r, dt
+    return {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}, dt
+
+
+def cpu_sample(v):
+    """The bounded pixel sample of a view the CPU legs run: every 8th row and
+    4th column above 512^2 pixels, else every pixel."""
+    big = v.width * v.height > (1 << 18)
+    return (sample_pixels(v.width, v.height, 8, 4) if big else sample_pixels(v.width, v.height, 1, 1),
+            "every 8th row, 4th column" if big else "every pixel")
 
 
 def workload(name):
@@ -233,34 +308,39 @@ def config_of(sc, name):
             "pieces": sc.n_pieces, "brick_cells": 1 << sc.brick_log2, "image": f"{v.width}x{v.height}",
             "projection": "perspective" if v.projection else "orthographic", "step_voxels": sc.step,
             "moments": "4 power, float32", "moment_bias": sc.moment_bias, "overestimation": sc.overestimation,
-            "l2": f"inputs larger than L2 ({(sc.values if hasattr(sc, 'leaves') else sc.field).nbytes >> 20} MiB "
-                  "volume re-read every frame)",
+            "l2": (lambda nb: f"inputs larger than L2 ({nb >> 20} MiB volume re-read every frame)" if nb > (129 << 20)
+                   else f"volume of {nb >> 20} MiB fits in L2")((sc.values if hasattr(sc, 'leaves') else sc.field).nbytes),
             **({"step_rule": "adaptive dyadic (a level-L leaf samples every 2^(max_level - L)-th lattice point)"}
                if getattr(sc, "adaptive_step", False) else {})}
 
 
 def run_reference(args, rank):
+    """The reference arm: the FP64 oracle as it stands, on every host core
+    (disjoint pixel chunks), on the bounded pixel sample of the workload."""
     if rank != 0:
         return
     sc = workload(args.workload)
     v = sc.views[0]
-    pix = sample_pixels(v.width, v.height, 32, 16) if args.workload == "blobs512" else sample_pixels(v.width, v.height, 4, 4)
+    pix, how = cpu_sample(v)
+    cores = host_cores()
     for _ in range(args.warmup):
-        time_oracle(sc, pix[: max(1, pix.size // 8)])
+        time_oracle(sc, pix[: max(1, pix.size // 64)], cores)
     times, samples = [], 0
     for _ in range(args.steps):
-        r, dt = time_oracle(sc, pix)
+        r, dt = time_oracle(sc, pix, cores, want=("mboit", "nsamples"))
         times.append(dt)
         samples = int(r["nsamples"].sum())
     total = sum(times)
     value = samples * args.steps / total / 1e9
-    sample_desc = f"{pix.size} pixels of the {v.width}x{v.height} frame (every 32nd row, 16th column), {samples} samples"
+    sample_desc = (f"{pix.size} pixels of the {v.width}x{v.height} frame ({how}), {samples} samples per step, "
+                   f"FP64, {cores} threads over pixel chunks")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_of(sc, args.workload),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc},
+        "config": dict(config_of(sc, args.workload), parallelism="replicas" if args.gpus > 1 else "single"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample_desc,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -307,10 +387,11 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="blobs512", choices=["blobs512", "blobs64", "amr", "tets", "mixed"])
+    ap.add_argument("--workload", default="amr", choices=["blobs512", "blobs64", "amr", "tets", "mixed"])
     ap.add_argument("--image", type=int, default=0, help="square image size for the main workload (profiling)")
     ap.add_argument("--adaptive", action="store_true", help="octree workload: the adaptive dyadic step")
-    ap.add_argument("--no-amr", action="store_true")
+    ap.add_argument("--no-amr", action="store_true", help="skip the adaptive-step octree frame")
+    ap.add_argument("--no-grid", action="store_true", help="skip the 512^3 regular-grid workload")
     ap.add_argument("--no-tets", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -319,7 +400,13 @@ def main():
     ap.add_argument("--no-gear", action="store_true", help="skip the gear-teeth stress test")
     ap.add_argument("--gear-k", default="8,16,32,64,128", help="piece counts of the gear-teeth stress test")
     ap.add_argument("--heatmap", default="", help="directory for the gear-teeth segments-per-pixel images (PGM)")
+    ap.add_argument("--ncu-record", nargs=4, metavar=("CSV", "KERNEL", "SAMPLES", "OUT"),
+                    help="write the frame kernel's ncu record for --workload from a raw CSV dump and exit")
     args = ap.parse_args()
+    if args.ncu_record:
+        csv_path, kernel, nsamp, out_path = args.ncu_record
+        print(json.dumps(write_ncu_record(csv_path, kernel, args.workload, int(nsamp), out_path)))
+        return
     args.warmup = max(args.warmup, 3)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -419,33 +506,45 @@ def main():
         return d
     launches = stf["frame_launches"]
     unit_scene = hasattr(sc, "leaves") or hasattr(sc, "tets") or hasattr(sc, "cells")
+    flop1 = FLOP_PASS1["amr" if hasattr(sc, "leaves") else "grid"]
     if launches == 1:
         # one kernel per frame: the event pair brackets it, the second pair is empty
-        k1s = kstats(p1 + p2, FLOP_FRAME_ONE_LAUNCH, 2 * CACHE_BYTES_PER_SAMPLE)
+        k1s = kstats(p1 + p2, flop1 + FLOP_PASS2_FRAME, 2 * CACHE_BYTES_PER_SAMPLE)
         frame_kernels = {"frame_one_launch": k1s}
         dom_key = "k_frame_unit" if unit_scene else "k_frame_fused"
-        dom, dflop = k1s, FLOP_FRAME_ONE_LAUNCH
+        dom, dflop = k1s, flop1 + FLOP_PASS2_FRAME
         dname = (dom_key + ", one launch per frame (per ray tile: march + moments + sample store, "
                  "then reconstruct + blend + resolve)")
     else:
-        k1s = kstats(p1, FLOP_PASS1, CACHE_BYTES_PER_SAMPLE)
+        k1s = kstats(p1, flop1, CACHE_BYTES_PER_SAMPLE)
         k2s = kstats(p2, FLOP_PASS2_FRAME, CACHE_BYTES_PER_SAMPLE)
         frame_kernels = {"frame_pass1": k1s, "frame_pass2": k2s}
         kname = "k_pass{}_unit" if unit_scene else "k_pass{}_fused"
         dom, dname, dflop = (k2s, kname.format(2) + ", frame form (reads the cached samples; reconstruct + blend + resolve)",
                              FLOP_PASS2_FRAME) if p2 >= p1 else \
-            (k1s, kname.format(1) + ", frame form (march + moments + sample store)", FLOP_PASS1)
-        dom_key = "k_pass2_fused_frame" if p2 >= p1 else "k_pass1_fused_frame"
-    traffic = measured_traffic(dom_key, args.workload)
+            (k1s, kname.format(1) + ", frame form (march + moments + sample store)", flop1)
+        dom_key = kname.format(2 if p2 >= p1 else 1) + "_frame"
+    rec_traffic = measured_traffic(dom_key, args.workload)
     ncu_rec = measured_ncu(dom_key, args.workload)
+    # a record taken on a reduced view scales to this launch by its owned samples
+    traffic = None
+    if rec_traffic is not None:
+        traffic = int(rec_traffic * (samples / ncu_rec["samples_per_launch"] if "samples_per_launch" in ncu_rec else 1.0))
     roofline = {"bound": "alu", "kernel": dname, "achieved": dom["achieved_tflops"], "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": dom["achieved_tflops"] / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_source": None if ncu_rec is None else
+                ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch"
+                 + (f" on {int(ncu_rec['samples_per_launch'])} owned samples, scaled by owned samples"
+                    if "samples_per_launch" in ncu_rec else "")),
                 "binding_units_ncu": None if ncu_rec is None else
                 {k: v for k, v in ncu_rec.items() if k != "dram_bytes_per_launch"},
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "flop_per_sample": dflop,
                 "launch_ms": dom["launch_ms"], **frame_kernels,
                 "split_calls": {"pass1_ms": ms_p1, "pass2_ms": ms_p2, "pass2_flop_per_sample": FLOP_PASS2,
                                 "pass2_achieved_tflops": FLOP_PASS2 * samples / (ms_p2 * 1e-3) / 1e12}}
+    if traffic is not None and hbm:
+        roofline["hbm"] = {"traffic_gbs": traffic / (dom["launch_ms"] * 1e-3) / 1e9, "peak_gbs": hbm,
+                           "frac_of_measured": traffic / (dom["launch_ms"] * 1e-3) / 1e9 / hbm}
 
     # end to end through the host API: field upload, frame, image download
     host_values = (sc.values if hasattr(sc, "leaves") else sc.verts[:, 3] if (hasattr(sc, "tets") or hasattr(sc, "cells"))
@@ -502,8 +601,8 @@ def main():
         del exact
         torch.cuda.empty_cache()
 
-    # the 72-piece brick-octree workload (2560x2560) and the 72-piece
-    # tetrahedral workload (1024x1024) as further lines of results
+    # the 512^3 regular grid (64 pieces, 2048x2048), the 72-piece tetrahedral
+    # (1024x1024) and mixed-cell workloads as further lines of results
     def unit_block(name):
         usc = workload(name)
         uvol = pkg.Volume(usc)
@@ -550,20 +649,17 @@ def main():
                  "gsamples_per_s": su / (ms_u * 1e-3) / 1e9, "per_piece_fp32_ms_per_frame": ms_up,
                  "speedup_of_batched": ms_up / ms_u, "sortlast_gpu": usl}
         upix = sample_pixels(uw, uh, 64, 32)
-        fixed_exact = None
         if rank == 0 and not args.no_cpu_baseline:
             _orc = __import__("oracle")
             oscene = _orc.tet_scene_of(usc) if hasattr(usc, "cells") else usc
-            r = _orc.render(oscene, pixels=upix, want=("mboit", "exact") if name == "amr" else ("mboit",))
-            ref, fixed_exact = r["mboit"], r.get("exact")
+            r, _ = time_oracle(oscene, upix, host_cores(), want=("mboit",))
+            ref = r["mboit"]
             got = urgba.view(-1, 4)[torch.from_numpy(upix).cuda()].double().cpu().numpy()
             out_u["quality"] = {"pixels": int(upix.size), "max_abs_vs_oracle": float(np.abs(got - ref).max()),
                                 "rmse_vs_oracle": float(np.sqrt(((got - ref) ** 2).mean()))}
         uvol.close()
         del uvol, umom, urgba
         torch.cuda.empty_cache()
-        if name == "amr":
-            out_u["adaptive_step"] = adaptive_block(usc, upix, ms_u, su, fixed_exact)
         return out_u
 
     # the octree workload with the adaptive dyadic step (a level-L leaf samples
@@ -588,7 +684,7 @@ def main():
                  "fixed_step_lattice_gsamples_per_s": samples_fixed / (ms_a * 1e-3) / 1e9,
                  "speedup_of_fixed_step_frame": ms_fixed / ms_a}
         if rank == 0 and not args.no_cpu_baseline:
-            r = __import__("oracle").render(asc, pixels=upix, want=("mboit", "exact"))
+            r, _ = time_oracle(asc, upix, host_cores(), want=("mboit", "exact"))
             got = argba.view(-1, 4)[torch.from_numpy(upix).cuda()].double().cpu().numpy()
             out_a["quality"] = {"pixels": int(upix.size),
                                 "max_abs_vs_oracle": float(np.abs(got - r["mboit"]).max()),
@@ -601,14 +697,15 @@ def main():
         torch.cuda.empty_cache()
         return out_a
 
-    amr = unit_block("amr") if args.workload == "blobs512" and not args.no_amr else None
-    tets = unit_block("tets") if args.workload == "blobs512" and not args.no_tets else None
-    mixed = unit_block("mixed") if args.workload == "blobs512" and not args.no_tets else None
+    headline = args.workload == "amr" and not args.image
+    grid = unit_block("blobs512") if headline and not args.no_grid else None
+    tets = unit_block("tets") if headline and not args.no_tets else None
+    mixed = unit_block("mixed") if headline and not args.no_tets else None
 
     # the gear-teeth stress test of Sec. 5: K pieces of 4 interleaved layers,
     # batched MBOIT against the exact sort-last baseline as K grows
     gear = None
-    if args.workload == "blobs512" and not args.no_gear:
+    if headline and not args.no_gear:
         import scenes as _scenes
         gear = []
         for K in [int(x) for x in args.gear_k.split(",") if x]:
@@ -659,7 +756,7 @@ def main():
 
     # precision sweep on the octree field with the 2048^2 view: moment sets and storages
     sweep = None
-    if args.workload == "blobs512" and not args.no_sweep:
+    if headline and not args.no_sweep:
         import copy
         import scenes as _scenes
         import oracle as _oracle
@@ -668,11 +765,11 @@ def main():
         spix = sample_pixels(2048, 2048, 64, 32)
         sweep = []
         exact_ref = None
-        for ms, stor, beta in (("power4", "f32", 5e-5), ("power6", "f32", 5e-5), ("power8", "f32", 5e-5),
+        for mset, stor, beta in (("power4", "f32", 5e-5), ("power6", "f32", 5e-5), ("power8", "f32", 5e-5),
                              ("trig6", "f16", 2e-3), ("trig6", "bf16", 2e-2), ("trig8", "f16", 2e-3),
                              ("trig8", "bf16", 2e-2)):
             sc2 = copy.copy(base)
-            sc2.moment_set, sc2.storage, sc2.moment_bias = ms, stor, beta
+            sc2.moment_set, sc2.storage, sc2.moment_bias = mset, stor, beta
             svol = pkg.Volume(sc2)
             sv = sc2.views
             smom, srgba = svol.moments_for(sv), pkg.Volume.color_buffer(sv)
@@ -682,7 +779,7 @@ def main():
             ms_s = timed(sframe, 3)
             svol.synchronize()
             ns = svol.stats()["samples_pass1"]
-            row = {"moments": ms, "storage": stor, "moment_bias": beta,
+            row = {"moments": mset, "storage": stor, "moment_bias": beta,
                    "moment_bytes_per_pixel": pkg.mboit_moment_image_bytes(4, 1, svol.moment_set, svol.storage) // 4,
                    "ms_per_frame": ms_s, "gsamples_per_s": ns / (ms_s * 1e-3) / 1e9}
             if rank == 0 and not args.no_cpu_baseline:
@@ -701,38 +798,49 @@ def main():
             torch.cuda.empty_cache()
 
 
-    # parity on a pixel sample and the oracle's own speed (rank 0, one GPU)
-    cpu_baseline, quality = None, None
+    # parity on a pixel sample and the oracle's own speed (rank 0, one GPU):
+    # the FP64 oracle single-threaded as it stands, and its per-pixel entry on
+    # disjoint pixel chunks over every host core
+    cpu_baseline, quality, adaptive = None, None, None
     if rank == 0 and not args.no_cpu_baseline:
         frame()
         vol.synchronize()
         v0 = sc.views[0]
-        big = v0.width * v0.height > (1 << 18)  # above 512^2: every 8th row, 4th column (a bounded CPU sample)
-        pix = sample_pixels(v0.width, v0.height, 8, 4) if big else sample_pixels(v0.width, v0.height, 1, 1)
-        r, dt = time_oracle(sc, pix)
+        pix, how = cpu_sample(v0)
+        cores = host_cores()
+        r, dt_all = time_oracle(sc, pix, cores)
+        one = pix[:: max(1, pix.size // 16384)]   # the single-thread leg on a 1/N subset of the sample
+        r1, dt1 = time_oracle(sc, one, 1, want=("nsamples",))
         ns = int(r["nsamples"].sum())
+        ns1 = int(r1["nsamples"].sum())
         got = rgba.view(-1, 4)[torch.from_numpy(pix).cuda()].double().cpu().numpy()
         d = got - r["mboit"]
         quality = {"pixels": int(pix.size), "max_abs_vs_oracle": float(np.abs(d).max()),
                    "rmse_vs_oracle": float(np.sqrt((d ** 2).mean())),
                    "oracle_mboit_vs_exact_rmse": float(np.sqrt(((r["mboit"] - r["exact"]) ** 2).mean())),
                    "oracle_mboit_vs_exact_max": float(np.abs(r["mboit"] - r["exact"]).max())}
-        cpu_baseline = {"value": ns / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-                        "sample": f"{pix.size} pixels ({'every 8th row, 4th column' if big else 'all'}) of the frame, {ns} samples, "
-                                  f"{dt:.1f} s, FP64 single thread"}
+        rate = ns / dt_all / 1e9
+        cpu_baseline = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+                        "sample": (f"{pix.size} pixels ({how}) of the {v0.width}x{v0.height} frame, {ns} samples, "
+                                   f"{dt_all:.2f} s, FP64, {cores} threads over pixel chunks"),
+                        "frame_s_extrapolated": samples / (rate * 1e9),
+                        "single_thread": {"value": ns1 / dt1 / 1e9, "unit": UNIT, "cores": 1,
+                                          "sample": f"{one.size} pixels (every {pix.size // one.size}th of the sample), "
+                                                    f"{ns1} samples, {dt1:.2f} s"}}
+        if hasattr(sc, "leaves") and not args.no_amr and not args.image:
+            adaptive = adaptive_block(sc, pix, ms, samples, r["exact"])
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": dict(config_of(sc, args.workload), parallelism="replicas" if world > 1 else "single",
-                          form=("batched: 1 persistent kernel per frame (pass 1 then pass 2 per ray tile), CUDA graph"
-                                if launches == 1 else "batched: 2 persistent kernels per frame, CUDA graph"),
-                          tuning={"pass1": tuning[0], "pass2": tuning[1],
-                                  "packet": "4x8" if tuning[2] == pkg.MBOIT_PACKET_4X8 else "8x4",
-                                  "frame_launches": launches}),
-           "samples_per_frame": samples, "ms_per_frame": ms_max, "singular_pixels": st["singular_pixels"], "per_piece_fp32": per_piece,
-           "sortlast_gpu": sortlast, "amr_72_pieces": amr, "tets_72_pieces": tets,
-           "mixed_cells_72_pieces": mixed,
+           "config": dict(config_of(sc, args.workload), parallelism="replicas" if world > 1 else "single"),
+           "form": ("batched: 1 persistent kernel per frame (pass 1 then pass 2 per ray tile), CUDA graph"
+                    if launches == 1 else "batched: 2 persistent kernels per frame, CUDA graph"),
+           "tuning": {"pass1": tuning[0], "pass2": tuning[1],
+                      "packet": "4x8" if tuning[2] == pkg.MBOIT_PACKET_4X8 else "8x4", "frame_launches": launches},
+           "samples_per_frame": samples, "ms_per_frame": ms_max, "singular_pixels": st["singular_pixels"],
+           "per_piece_fp32": per_piece, "sortlast_gpu": sortlast, "adaptive_step": adaptive,
+           "grid_512_64_pieces": grid, "tets_72_pieces": tets, "mixed_cells_72_pieces": mixed,
            "gear_teeth_stress": gear,
            "precision_sweep_amr_2048": sweep,
            "quality": quality, "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,

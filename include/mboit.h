@@ -407,12 +407,18 @@ MBOIT_API mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, i
  * 256 + 4096 + 1,048,576 bytes inside the library, which every device that
  * loads the library keeps until the process exits.  Limit: at most
  * 1,048,576 bricks (MBOIT_ERR_INVALID_ARG beyond).  The call makes no
- * cudaMalloc, cudaFree or other allocating call.  Its first call on a
- * device looks up the array's device address (set-up) and should come
- * before any stream capture on that device.  All calls share the array:
- * calls whose work overlaps on the GPU (two streams, or two host threads)
- * race and give wrong results; order them on one stream.  A brick mask from
- * pinned memory must stay unchanged until the call's work has run. */
+ * cudaMalloc, cudaFree or other allocating call.  Every call looks up the
+ * array's device address in the current context (a lookup, so a context
+ * re-created after cudaDeviceReset gets its own copy); the first call on a
+ * device also loads the library's kernels there (set-up) and should come
+ * before any stream capture on that device.  The transfer function travels
+ * by value in a kernel argument, so the caller's table is free once the
+ * call returns.  The brick mask is copied from the caller's memory by a
+ * copy on `stream`: pinned memory is read when that copy runs and must stay
+ * unchanged until then.  All calls share the array: calls whose work
+ * overlaps on the GPU (two streams, or two host threads) race and give
+ * wrong results; order them on one stream.  Argument checks are those of
+ * mboit_create_volume for a grid (MBOIT_ERR_INVALID_ARG). */
 MBOIT_API mboit_status mboit_render_moments_noalloc(const mboit_volume_desc* desc, const uint8_t* brick_selected,
                                                     const mboit_view* views, int32_t n_views, void* moments,
                                                     void* stream);

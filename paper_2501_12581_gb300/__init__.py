@@ -306,9 +306,20 @@ def grid_desc(scene, field, flags=0):
 
 
 def mboit_render_moments_noalloc(desc, views, moments, brick_selected=None, stream=None):
-    """Pass 1 without any device allocation (see include/mboit.h)."""
+    """Pass 1 without any device allocation (see include/mboit.h).
+
+    brick_selected: None (every brick) or one byte per brick of the grid,
+    nbx * nby * nbz with nb = ceil((dims - 1) / 2^brick_log2) per axis."""
     arr, n = _views(views)
-    sel = None if brick_selected is None else np.ascontiguousarray(brick_selected, dtype=np.uint8)
+    sel = None
+    if brick_selected is not None:
+        sel = np.ascontiguousarray(brick_selected, dtype=np.uint8).ravel()
+        B = 1 << int(desc.brick_log2)
+        nbricks = 1
+        for c in range(3):
+            nbricks *= (int(desc.dims[c]) - 1 + B - 1) // B
+        if sel.size != nbricks:
+            raise ValueError(f"brick_selected has {sel.size} entries; the grid has {nbricks} bricks")
     _check(load_library().mboit_render_moments_noalloc(ctypes.byref(desc), _ptr(sel), arr, n, _ptr(moments),
                                                        _stream(stream)))
 

@@ -146,6 +146,66 @@ void fill_trig(mb::TrigTables& T, int32_t moment_set, int32_t storage, float bet
 
 bool is_trig(int32_t moment_set) { return moment_set == MBOIT_TRIG6 || moment_set == MBOIT_TRIG8; }
 
+// Scalar sampling parameters every volume kind shares (tf_range, step,
+// moment_bias, overestimation, absorbance_max): checked the same way by
+// mboit_create_volume and mboit_render_moments_noalloc.
+mboit_status check_sampling(const mboit_volume_desc* d) {
+    if (!d->tf_rgba) return fail(MBOIT_ERR_INVALID_ARG, "tf_rgba is NULL");
+    if (!std::isfinite(d->tf_range[0]) || !std::isfinite(d->tf_range[1]) || !(d->tf_range[1] > d->tf_range[0]))
+        return fail(MBOIT_ERR_INVALID_ARG, "tf_range must be finite with tf_range[1] > tf_range[0]");
+    int ex = 0;
+    if (!(d->step > 0.0f) || !std::isfinite(d->step) || std::frexp(d->step, &ex) != 0.5f)
+        return fail(MBOIT_ERR_INVALID_ARG, "step must be a positive power of two");
+    if (!(d->moment_bias >= 0.0f && d->moment_bias < 1.0f)) return fail(MBOIT_ERR_INVALID_ARG, "moment_bias must be in [0, 1)");
+    if (!(d->overestimation >= 0.0f && d->overestimation <= 1.0f))
+        return fail(MBOIT_ERR_INVALID_ARG, "overestimation must be in [0, 1]");
+    if (!(d->absorbance_max > 0.0f) || !std::isfinite(d->absorbance_max))
+        return fail(MBOIT_ERR_INVALID_ARG, "absorbance_max must be positive");
+    return MBOIT_OK;
+}
+
+// The 256 transfer-function entries as the kernels read them: (r, g, b,
+// absorbance of one sample = sigma * step) with sigma = -ln(1 - alpha) per
+// voxel (Alg. 2: absorbance = -log of the sample's transmittance).
+mboit_status convert_tf(const mboit_volume_desc* d, float4* tf) {
+    for (int j = 0; j < 256; ++j) {
+        const float* e = d->tf_rgba + 4 * j;
+        for (int c = 0; c < 4; ++c)
+            if (!std::isfinite(e[c])) return fail(MBOIT_ERR_INVALID_ARG, "non-finite transfer-function entry");
+        if (!(e[3] >= 0.0f && e[3] < 1.0f)) return fail(MBOIT_ERR_INVALID_ARG, "transfer-function alpha must be in [0, 1)");
+        const double sigma = -std::log1p(-(double)e[3]);
+        tf[j] = make_float4(e[0], e[1], e[2], (float)(sigma * (double)d->step));
+    }
+    return MBOIT_OK;
+}
+
+// Grid geometry and sampling parameters of a descriptor (validated).
+void fill_grid(const mboit_volume_desc* d, mb::GridD& g) {
+    const int B = 1 << d->brick_log2;
+    g.field = d->field;
+    g.nx = d->dims[0];
+    g.ny = d->dims[1];
+    g.nz = d->dims[2];
+    g.brick_log2 = d->brick_log2;
+    g.nbx = (g.nx - 1 + B - 1) / B;
+    g.nby = (g.ny - 1 + B - 1) / B;
+    g.nbz = (g.nz - 1 + B - 1) / B;
+    g.hx = (float)(g.nx - 1);
+    g.hy = (float)(g.ny - 1);
+    g.hz = (float)(g.nz - 1);
+    g.step = d->step;
+    g.tf_scale = (float)(255.0 / ((double)d->tf_range[1] - (double)d->tf_range[0]));
+    g.tf_bias = (float)(-(double)d->tf_range[0] * 255.0 / ((double)d->tf_range[1] - (double)d->tf_range[0]));
+    g.absorbance_max = d->absorbance_max;
+    g.moment_bias = d->moment_bias;
+    g.overestimation = d->overestimation;
+    g.bias_vector[0] = 0.0f;
+    g.bias_vector[1] = 0.375f;
+    g.bias_vector[2] = 0.0f;
+    g.bias_vector[3] = 0.375f;
+    g.flags = d->flags;
+}
+
 int64_t slab_bytes_per_px(int32_t moment_set) {
     switch (moment_set) {
         case MBOIT_TRIG6: return 16;
@@ -667,27 +727,11 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
             if (d->dims[c] < 2 || d->dims[c] > (1 << 20)) return fail(MBOIT_ERR_INVALID_ARG, "dims must be in [2, 2^20]");
         if (d->brick_log2 < 0 || d->brick_log2 > 7) return fail(MBOIT_ERR_INVALID_ARG, "brick_log2 must be in [0, 7]");
     }
-    if (!d->tf_rgba) return fail(MBOIT_ERR_INVALID_ARG, "tf_rgba is NULL");
-    if (!std::isfinite(d->tf_range[0]) || !std::isfinite(d->tf_range[1]) || !(d->tf_range[1] > d->tf_range[0]))
-        return fail(MBOIT_ERR_INVALID_ARG, "tf_range must be finite with tf_range[1] > tf_range[0]");
-    int ex = 0;
-    if (!(d->step > 0.0f) || !std::isfinite(d->step) || std::frexp(d->step, &ex) != 0.5f)
-        return fail(MBOIT_ERR_INVALID_ARG, "step must be a positive power of two");
-    if (!(d->moment_bias >= 0.0f && d->moment_bias < 1.0f)) return fail(MBOIT_ERR_INVALID_ARG, "moment_bias must be in [0, 1)");
-    if (!(d->overestimation >= 0.0f && d->overestimation <= 1.0f))
-        return fail(MBOIT_ERR_INVALID_ARG, "overestimation must be in [0, 1]");
-    if (!(d->absorbance_max > 0.0f) || !std::isfinite(d->absorbance_max))
-        return fail(MBOIT_ERR_INVALID_ARG, "absorbance_max must be positive");
+    mboit_status cs = check_sampling(d);
+    if (cs != MBOIT_OK) return cs;
     std::vector<float4> tf(256);
-    for (int j = 0; j < 256; ++j) {
-        const float* e = d->tf_rgba + 4 * j;
-        for (int c = 0; c < 4; ++c)
-            if (!std::isfinite(e[c])) return fail(MBOIT_ERR_INVALID_ARG, "non-finite transfer-function entry");
-        if (!(e[3] >= 0.0f && e[3] < 1.0f)) return fail(MBOIT_ERR_INVALID_ARG, "transfer-function alpha must be in [0, 1)");
-        // extinction per voxel, times the step: absorbance of one sample
-        const double sigma = -std::log1p(-(double)e[3]);
-        tf[j] = make_float4(e[0], e[1], e[2], (float)(sigma * (double)d->step));
-    }
+    cs = convert_tf(d, tf.data());
+    if (cs != MBOIT_OK) return cs;
     // octree: leaf table checks and the finest-brick -> leaf map (host)
     std::vector<int32_t> fmap;
     int64_t fdim = 0;
@@ -744,30 +788,8 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
     v->device = dev;
     v->desc = *d;
     v->desc.tf_rgba = nullptr;
-    const int B = 1 << d->brick_log2;
     mb::GridD& g = v->grid;
-    g.field = d->field;
-    g.nx = d->dims[0];
-    g.ny = d->dims[1];
-    g.nz = d->dims[2];
-    g.brick_log2 = d->brick_log2;
-    g.nbx = (g.nx - 1 + B - 1) / B;
-    g.nby = (g.ny - 1 + B - 1) / B;
-    g.nbz = (g.nz - 1 + B - 1) / B;
-    g.hx = (float)(g.nx - 1);
-    g.hy = (float)(g.ny - 1);
-    g.hz = (float)(g.nz - 1);
-    g.step = d->step;
-    g.tf_scale = (float)(255.0 / ((double)d->tf_range[1] - (double)d->tf_range[0]));
-    g.tf_bias = (float)(-(double)d->tf_range[0] * 255.0 / ((double)d->tf_range[1] - (double)d->tf_range[0]));
-    g.absorbance_max = d->absorbance_max;
-    g.moment_bias = d->moment_bias;
-    g.overestimation = d->overestimation;
-    g.bias_vector[0] = 0.0f;
-    g.bias_vector[1] = 0.375f;
-    g.bias_vector[2] = 0.0f;
-    g.bias_vector[3] = 0.375f;
-    g.flags = d->flags;
+    fill_grid(d, g);
     fill_trig(g.trig, d->moment_set, d->storage, d->moment_bias);
     v->nbricks = (int64_t)g.nbx * g.nby * g.nbz;
     v->field_bytes = (size_t)g.nx * g.ny * g.nz * sizeof(float);
@@ -1463,9 +1485,22 @@ static_assert(sizeof(mb::Counters) <= kNoallocTfOff, "counters must fit their sl
 // address: the device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-constexpr int kNoallocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-unsigned char* g_noalloc_dev[kNoallocMaxDevices] = {};
+// The converted transfer function, passed by value: the launch copies it, so
+// no host buffer has to outlive the call.
+struct NoallocTf {
+    float4 e[256];
+};
+static_assert(sizeof(NoallocTf) <= 4096, "kernel parameters are limited to 4 KB");
+
+// Writes the transfer function into its slot of the scratch array and
+// clears the work-queue head and counters (the array keeps the previous
+// call's contents).
+__global__ void __launch_bounds__(256) k_noalloc_setup(const NoallocTf tf) {
+    float4* dst = reinterpret_cast<float4*>(g_noalloc_scratch + kNoallocTfOff);
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) dst[i] = tf.e[i];
+    uint32_t* ctr = reinterpret_cast<uint32_t*>(g_noalloc_scratch);
+    for (int i = threadIdx.x; i < (int)(sizeof(mb::Counters) / sizeof(uint32_t)); i += blockDim.x) ctr[i] = 0u;
+}
 
 }  // namespace
 
@@ -1478,18 +1513,12 @@ extern "C" mboit_status mboit_render_moments_noalloc(const mboit_volume_desc* d,
     if (d->moment_set != MBOIT_POWER4 || d->storage != MBOIT_STORE_F32)
         return fail(MBOIT_ERR_UNSUPPORTED, "only float32 power moments are implemented");
     if (d->flags & ~(MBOIT_FLAG_RAW_SUM | MBOIT_FLAG_DETERMINISTIC)) return fail(MBOIT_ERR_INVALID_ARG, "unknown flag bits");
-    if (!d->field || !d->tf_rgba) return fail(MBOIT_ERR_INVALID_ARG, "field and tf_rgba must be non-NULL");
+    if (!d->field) return fail(MBOIT_ERR_INVALID_ARG, "field must be non-NULL");
     for (int c = 0; c < 3; ++c)
         if (d->dims[c] < 2 || d->dims[c] > (1 << 20)) return fail(MBOIT_ERR_INVALID_ARG, "dims must be in [2, 2^20]");
     if (d->brick_log2 < 0 || d->brick_log2 > 7) return fail(MBOIT_ERR_INVALID_ARG, "brick_log2 must be in [0, 7]");
-    if (!std::isfinite(d->tf_range[0]) || !std::isfinite(d->tf_range[1]) || !(d->tf_range[1] > d->tf_range[0]))
-        return fail(MBOIT_ERR_INVALID_ARG, "tf_range must be finite with tf_range[1] > tf_range[0]");
-    int ex = 0;
-    if (!(d->step > 0.0f) || !std::isfinite(d->step) || std::frexp(d->step, &ex) != 0.5f)
-        return fail(MBOIT_ERR_INVALID_ARG, "step must be a positive power of two");
-    if (!(d->moment_bias >= 0.0f && d->moment_bias < 1.0f)) return fail(MBOIT_ERR_INVALID_ARG, "moment_bias must be in [0, 1)");
-    if (!(d->absorbance_max > 0.0f) || !std::isfinite(d->absorbance_max))
-        return fail(MBOIT_ERR_INVALID_ARG, "absorbance_max must be positive");
+    mboit_status st = check_sampling(d);
+    if (st != MBOIT_OK) return st;
     const int B = 1 << d->brick_log2;
     const int64_t nbx = (d->dims[0] - 1 + B - 1) / B, nby = (d->dims[1] - 1 + B - 1) / B,
                   nbz = (d->dims[2] - 1 + B - 1) / B;
@@ -1498,69 +1527,39 @@ extern "C" mboit_status mboit_render_moments_noalloc(const mboit_volume_desc* d,
         return fail(MBOIT_ERR_INVALID_ARG, "the volume has " + std::to_string(nbricks) +
                                                " bricks; the allocation-free pass 1 handles at most " +
                                                std::to_string(kNoallocMaxBricks) + " (use a larger brick_log2)");
-    float4 tf[256];  // converted on the stack: the copy below stages pageable memory before returning
-    for (int j = 0; j < 256; ++j) {
-        const float* e = d->tf_rgba + 4 * j;
-        for (int c = 0; c < 4; ++c)
-            if (!std::isfinite(e[c])) return fail(MBOIT_ERR_INVALID_ARG, "non-finite transfer-function entry");
-        if (!(e[3] >= 0.0f && e[3] < 1.0f)) return fail(MBOIT_ERR_INVALID_ARG, "transfer-function alpha must be in [0, 1)");
-        tf[j] = make_float4(e[0], e[1], e[2], (float)(-std::log1p(-(double)e[3]) * (double)d->step));
-    }
+    NoallocTf tf;
+    st = convert_tf(d, tf.e);
+    if (st != MBOIT_OK) return st;
     mb::ViewTable vt;
-    mboit_status st = build_views(views, n_views, vt);
+    st = build_views(views, n_views, vt);
     if (st != MBOIT_OK) return st;
 
     int dev = 0;
     MB_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(MBOIT_ERR_UNSUPPORTED, "device index too large");
     cudaPointerAttributes attr{};
     if (cudaPointerGetAttributes(&attr, d->field) != cudaSuccess ||
         (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) || attr.device != dev) {
         cudaGetLastError();
         return fail(MBOIT_ERR_INVALID_ARG, "field must be a device pointer on the current device");
     }
-    unsigned char* scratch = nullptr;
-    {
-        // set-up, once per device, with that device current
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_dev[dev]) {
-            void* p = nullptr;
-            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p)
-                return fail(MBOIT_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-            g_noalloc_dev[dev] = static_cast<unsigned char*>(p);
-        }
-        scratch = g_noalloc_dev[dev];
-    }
+    // The array's address in the current device's context, looked up on every
+    // call (a lookup, no allocation), so that a context created anew after a
+    // cudaDeviceReset is served its own copy.
+    void* p = nullptr;
+    const cudaError_t ge = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (ge != cudaSuccess || !p)
+        return fail(MBOIT_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(ge));
+    unsigned char* scratch = static_cast<unsigned char*>(p);
 
     mb::GridD g{};
-    g.field = d->field;
-    g.nx = d->dims[0];
-    g.ny = d->dims[1];
-    g.nz = d->dims[2];
-    g.brick_log2 = d->brick_log2;
-    g.nbx = (int32_t)nbx;
-    g.nby = (int32_t)nby;
-    g.nbz = (int32_t)nbz;
-    g.hx = (float)(g.nx - 1);
-    g.hy = (float)(g.ny - 1);
-    g.hz = (float)(g.nz - 1);
-    g.step = d->step;
-    g.tf_scale = (float)(255.0 / ((double)d->tf_range[1] - (double)d->tf_range[0]));
-    g.tf_bias = (float)(-(double)d->tf_range[0] * 255.0 / ((double)d->tf_range[1] - (double)d->tf_range[0]));
-    g.absorbance_max = d->absorbance_max;
-    g.moment_bias = d->moment_bias;
-    g.overestimation = d->overestimation;
-    g.bias_vector[1] = 0.375f;
-    g.bias_vector[3] = 0.375f;
-    g.flags = d->flags;
+    fill_grid(d, g);
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     mb::Counters* ctr = reinterpret_cast<mb::Counters*>(scratch);
     float4* tf_dev = reinterpret_cast<float4*>(scratch + kNoallocTfOff);
     uint8_t* sel_dev = brick_selected ? scratch + kNoallocSelOff : nullptr;
-    MB_CUDA(cudaMemsetAsync(ctr, 0, sizeof(mb::Counters), s));  // the array keeps the last call's contents
-    MB_CUDA(cudaMemcpyAsync(tf_dev, tf, sizeof tf, cudaMemcpyHostToDevice, s));
+    k_noalloc_setup<<<1, 256, 0, s>>>(tf);
+    MB_CUDA(cudaGetLastError());
     if (sel_dev) MB_CUDA(cudaMemcpyAsync(sel_dev, brick_selected, (size_t)nbricks, cudaMemcpyHostToDevice, s));
     MB_CUDA(mb::launch_pass1_fused(g, tf_dev, sel_dev, vt, moments, ctr, s));
     return MBOIT_OK;

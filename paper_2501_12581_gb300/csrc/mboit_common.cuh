@@ -68,10 +68,12 @@ __device__ __forceinline__ bool field_sample(const GridD& g, const uint8_t* __re
     return true;
 }
 
-__device__ __forceinline__ float tf_coord(const GridD& g, float v, int& i) {
-    const float xt = fclamp(ffma(v, g.tf_scale, g.tf_bias), 0.0f, 255.0f);
-    i = min((int)xt, 254);
-    return xt - (float)i;
+// Transfer-function table coordinate of sample value v (O5): the value
+// normalised to [0, 1] by the table's range, times 255, clamped.  The
+// marches hand this to the per-sample bodies, and the frame's sample cache
+// stores it, so pass 2 repeats none of it.
+__device__ __forceinline__ float tf_x(const GridD& g, float v) {
+    return fclamp(ffma(v, g.tf_scale, g.tf_bias), 0.0f, 255.0f);
 }
 
 __device__ __forceinline__ int find_view(const ViewTable& vt, int tile) {
@@ -144,30 +146,55 @@ struct RowStore {
     }
 };
 
+// Depth terms of lattice depth t for four power moments: the warped depth z
+// (Alg. 2) and its powers z^2 = z z, z^3 = z^2 z, z^4 = z^3 z.  They depend on
+// t only, so a warp whose lanes sit at the same lattice index can compute
+// them once per row (DepthRows) and share them.
+__device__ __forceinline__ float4 depth_powers(float t, float wa, float wb) {
+    const float z = warp_depth(t, wa, wb);
+    const float z2 = z * z, z3 = z2 * z;
+    return make_float4(z, z2, z3, z3 * z);
+}
+
 struct MomentBody {
     const float2* s_sig;  // (sigma*step of entry i, of entry i+1 minus entry i)
     float tf_scale, tf_bias, amax, wa, wb;
     float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f;
     unsigned n = 0;
-    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) {
-        // entry 255 has a zero delta, so xt = 255 needs no special index
-        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+    // b_j += a z^j from the sample's table coordinate xt (tf_x) and the depth
+    // powers zp of its lattice point; entry 255 has a zero delta, so xt = 255
+    // needs no special index
+    __device__ __forceinline__ void add(float xt, float ws, float4 zp) {
         const int i = (int)xt;
         const float f = xt - (float)i;
         const float2 s = s_sig[i];
         const float a = fmin_(ffma(f, s.y, s.x) * ws, amax);
-        const float z = warp_depth(t, wa, wb);
         m0 += a;
-        m1 = ffma(a, z, m1);
-        const float az = a * z;
-        m2 = ffma(az, z, m2);
-        const float az2 = az * z;
-        m3 = ffma(az2, z, m3);
-        m4 = ffma(az2 * z, z, m4);
+        m1 = ffma(a, zp.x, m1);
+        m2 = ffma(a, zp.y, m2);
+        m3 = ffma(a, zp.z, m3);
+        m4 = ffma(a, zp.w, m4);
         ++n;
+    }
+    __device__ __forceinline__ void operator()(float t, float xt, float ws = 1.0f) {
+        add(xt, ws, depth_powers(t, wa, wb));
     }
     __device__ __forceinline__ void store(const GridD&, char* base, const ViewSlot& S, int64_t off, int pix) {
         store_moments(base, S, off, pix, m0, m1, m2, m3, m4);
+    }
+};
+
+// A warp's shared depth terms of kDepthRows consecutive lattice rows (one
+// float4 per row in the warp's shared memory): lanes 0..kDepthRows-1 compute
+// one row each, every lane reads the rows it samples.
+constexpr int kDepthRows = 8;
+struct DepthRows {
+    float4* z;   // this warp's kDepthRows slots
+    __device__ __forceinline__ void fill(int kw, float step, float wa, float wb) {
+        const int lane = threadIdx.x & 31;
+        __syncwarp();   // every lane is done with the previous rows
+        if (lane < kDepthRows) z[lane] = depth_powers(lattice_t(kw + lane, step), wa, wb);
+        __syncwarp();
     }
 };
 
@@ -181,8 +208,7 @@ struct BlendBody {
     unsigned n = 0;
     // kGeneric: the frame is known to be generic (no test of its kind)
     template <bool kGeneric = false>
-    __device__ __forceinline__ void sample(float t, float val, float ws) {
-        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+    __device__ __forceinline__ void sample(float t, float xt, float ws) {
         const int i = (int)xt;
         const float f = xt - (float)i;
         const float4 e0 = s_tf[2 * i], de = s_tf[2 * i + 1];
@@ -196,16 +222,68 @@ struct BlendBody {
         C.w += wgt;
         ++n;
     }
-    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) { sample<false>(t, val, ws); }
+    __device__ __forceinline__ void operator()(float t, float xt, float ws = 1.0f) { sample<false>(t, xt, ws); }
     __device__ __forceinline__ bool singular() const { return F.kind == kFrameOneAtom || F.kind == kFrameTwoAtoms; }
+
+    // Two consecutive lattice points (depths ta, tb = ta + step) of a generic
+    // frame: the arithmetic of sample<true> on both, each operation in one
+    // packed FP32x2 instruction with the scalar form's rounding, and the
+    // colour sums taken for a, then b.  The result equals two sample<true>
+    // calls bit for bit.  A point with ok = false adds nothing: its table
+    // coordinate is replaced by 0 (no NaN enters) and its weight by 0, and
+    // fma(0, c, C) = C.
+    __device__ __forceinline__ void pair_generic(float ta, float tb, float xa, float xb, float wsa, float wsb,
+                                                 bool oka, bool okb) {
+        xa = oka ? xa : 0.0f;
+        xb = okb ? xb : 0.0f;
+        const int ia = (int)xa, ib = (int)xb;
+        const float fa = xa - (float)ia, fb = xb - (float)ib;
+        const float4 ea = s_tf[2 * ia], da = s_tf[2 * ia + 1], eb = s_tf[2 * ib], db = s_tf[2 * ib + 1];
+        const float2 a = make_float2(fmin_(ffma(fa, da.w, ea.w) * wsa, amax), fmin_(ffma(fb, db.w, eb.w) * wsb, amax));
+        // opacity 1 - e^-a: the series and the direct form for both, then the
+        // one one_minus_exp_neg takes
+        float2 p = __ffma2_rn(a, make_float2(-1.0f / 720.0f, -1.0f / 720.0f), make_float2(1.0f / 120.0f, 1.0f / 120.0f));
+        p = __ffma2_rn(a, p, make_float2(-1.0f / 24.0f, -1.0f / 24.0f));
+        p = __ffma2_rn(a, p, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+        p = __ffma2_rn(a, p, make_float2(-0.5f, -0.5f));
+        p = __ffma2_rn(a, p, make_float2(1.0f, 1.0f));
+        const float2 ser = __fmul2_rn(a, p);
+        const float2 ng = __fmul2_rn(a, make_float2(-kLog2e, -kLog2e));
+        const float2 dir = __ffma2_rn(make_float2(fexp2(ng.x), fexp2(ng.y)), make_float2(-1.0f, -1.0f),
+                                      make_float2(1.0f, 1.0f));
+        const float2 alpha = make_float2(a.x < 0.25f ? ser.x : dir.x, a.y < 0.25f ? ser.y : dir.y);
+        const float2 zl = __ffma2_rn(make_float2(flog2(ta), flog2(tb)), make_float2(wa, wa), make_float2(wb, wb));
+        const float2 z = make_float2(fclamp(zl.x, -1.0f, 1.0f), fclamp(zl.y, -1.0f, 1.0f));
+        const float2 A = bound_generic2(F, z, w0);
+        const float2 ex = __fmul2_rn(make_float2(-F.m0_log2e, -F.m0_log2e), A);
+        float2 wgt = __fmul2_rn(make_float2(fclamp(fexp2(ex.x), 0.0f, 1.0f), fclamp(fexp2(ex.y), 0.0f, 1.0f)), alpha);
+        wgt.x = oka ? wgt.x : 0.0f;
+        wgt.y = okb ? wgt.y : 0.0f;
+        C.x = ffma(wgt.x, ffma(fa, da.x, ea.x), C.x);
+        C.y = ffma(wgt.x, ffma(fa, da.y, ea.y), C.y);
+        C.z = ffma(wgt.x, ffma(fa, da.z, ea.z), C.z);
+        C.w += wgt.x;
+        C.x = ffma(wgt.y, ffma(fb, db.x, eb.x), C.x);
+        C.y = ffma(wgt.y, ffma(fb, db.y, eb.y), C.y);
+        C.z = ffma(wgt.y, ffma(fb, db.z, eb.z), C.z);
+        C.w += wgt.y;
+        n += (unsigned)oka + (unsigned)okb;
+    }
 };
 
 // The pass-2 body for a warp whose lanes with samples all have a generic
 // frame: the same operations without the per-sample test of the frame's kind.
 struct GenericBlend {
     BlendBody& b;
-    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) { b.sample<true>(t, val, ws); }
+    __device__ __forceinline__ void operator()(float t, float xt, float ws = 1.0f) { b.sample<true>(t, xt, ws); }
+    __device__ __forceinline__ void pair(float ta, float tb, float xa, float xb, float wsa, float wsb, bool oka,
+                                         bool okb) {
+        b.pair_generic(ta, tb, xa, xb, wsa, wsb, oka, okb);
+    }
 };
+// Bodies that take two lattice points at once (pair(...), equal to two calls).
+template <class B> struct HasPair : std::false_type {};
+template <> struct HasPair<GenericBlend> : std::true_type {};
 
 // Bytes of one moment slab of P pixels in the volume's format.
 __device__ __forceinline__ int64_t slab_bytes(const GridD& g, int plane) {
@@ -257,8 +335,7 @@ struct TrigMomentBody {
     float m0 = 0.0f;
     cf t[N];
     unsigned n = 0;
-    __device__ __forceinline__ void operator()(float tt, float val, float ws = 1.0f) {
-        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+    __device__ __forceinline__ void operator()(float tt, float xt, float ws = 1.0f) {
         const int i = (int)xt;
         const float f = xt - (float)i;
         const float2 s = s_sig[i];
@@ -292,8 +369,7 @@ struct TrigBlendBody {
     float b0;
     float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     unsigned n = 0;
-    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) {
-        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+    __device__ __forceinline__ void operator()(float t, float xt, float ws = 1.0f) {
         const int i = (int)xt;
         const float f = xt - (float)i;
         const float4 e0 = s_tf[2 * i], de = s_tf[2 * i + 1];
@@ -346,8 +422,7 @@ struct PowerMomentBody {
     float tf_scale, tf_bias, amax, wa, wb;
     float m[2 * N + 1];
     unsigned n = 0;
-    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) {
-        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+    __device__ __forceinline__ void operator()(float t, float xt, float ws = 1.0f) {
         const int i = (int)xt;
         const float f = xt - (float)i;
         const float2 s = s_sig[i];
@@ -376,8 +451,7 @@ struct PowerBlendBody {
     float b0;
     float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     unsigned n = 0;
-    __device__ __forceinline__ void operator()(float t, float val, float ws = 1.0f) {
-        const float xt = fclamp(ffma(val, tf_scale, tf_bias), 0.0f, 255.0f);
+    __device__ __forceinline__ void operator()(float t, float xt, float ws = 1.0f) {
         const int i = (int)xt;
         const float f = xt - (float)i;
         const float4 e0 = s_tf[2 * i], de = s_tf[2 * i + 1];
@@ -552,10 +626,11 @@ constexpr int kRowBuf = 2 * kRowChunk * 32;     // floats of a warp's double buf
 // into its shared-memory buffer 8 rows (1 KiB) at a time, one chunk ahead of
 // the one it blends, and every lane takes its own column over its own
 // [k0, k1].  buf: 16-byte aligned, kRowBuf floats, this warp's only.
-// Octree adaptive step: a sample value carries its leaf's level shift in its
-// low mantissa bits, as few as max_level needs (2 for max_level 2 or 3: the
-// value moves by at most 3 ulp, the same in both passes, the split calls and
-// the per-piece path), so that pass 2 can weigh cached samples.
+// Octree adaptive step: a sample's table coordinate carries its leaf's level
+// shift in its low mantissa bits, as few as max_level needs (2 for max_level
+// 2 or 3: the coordinate moves by at most 3 ulp, the same in both passes, the
+// split calls and the per-piece path), so that pass 2 can weigh cached
+// samples.
 __device__ __forceinline__ int tag_mask(int max_level) { return (1 << (32 - __clz(max_level))) - 1; }
 __device__ __forceinline__ float tag_shift(float v, int shift, int mask) {
     return __int_as_float((__float_as_int(v) & ~mask) | shift);
@@ -597,10 +672,25 @@ __device__ __forceinline__ void march_rows(const GridD& g, const float* __restri
         if (kc >= k0 && kc + kRowChunk - 1 <= k1) {
             // the whole chunk lies in this lane's interval (and, without a
             // selection, every point of it is owned)
+            if constexpr (HasPair<Body>::value && !kTagged) {
+                // two lattice points per call (packed FP32x2 arithmetic); with a
+                // selection, a pair no lane of this branch samples is skipped.
+                // (The adaptive step leaves most points unsampled, lane-coherently:
+                // there the single-point loop below skips more.)
+                const unsigned act = __activemask();
 #pragma unroll
-            for (int i = 0; i < kRowChunk; ++i, t += g.step) {
-                const float val = src[i * 32];
-                if (!kSel || val == val) body(t, val, kTagged ? tagged_weight(val, tmask) : 1.0f);
+                for (int i = 0; i < kRowChunk; i += 2, t += 2.0f * g.step) {
+                    const float va = src[i * 32], vb = src[(i + 1) * 32];
+                    const bool oka = !kSel || va == va, okb = !kSel || vb == vb;
+                    if (kSel && !__any_sync(act, oka || okb)) continue;
+                    body.pair(t, t + g.step, va, vb, 1.0f, 1.0f, oka, okb);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < kRowChunk; ++i, t += g.step) {
+                    const float val = src[i * 32];
+                    if (!kSel || val == val) body(t, val, kTagged ? tagged_weight(val, tmask) : 1.0f);
+                }
             }
         } else {
             for (int i = 0; i < n; ++i, t += g.step) {

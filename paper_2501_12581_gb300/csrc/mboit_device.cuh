@@ -327,6 +327,38 @@ MB_HD float bound_fraction(const Frame& F, float z0, float w0) {
     return 0.0f;
 }
 
+#if defined(__CUDACC__)
+// bound_generic for two depths at once: every operation of the scalar form
+// on both, as one packed FP32x2 instruction (each half rounded exactly as the
+// scalar instruction), the MUFU reciprocal / square root per half.  Equal to
+// (bound_generic(F, z0.x, w0), bound_generic(F, z0.y, w0)) bit for bit.
+__device__ __forceinline__ float2 bound_generic2(const Frame& F, float2 z0, float w0) {
+    const float2 one = make_float2(1.0f, 1.0f), mone = make_float2(-1.0f, -1.0f);
+    const float2 ng = make_float2(-F.p2, -F.p2), inv_d = make_float2(F.p3, F.p3);
+    const float2 x0 = __ffma2_rn(z0, make_float2(F.p0, F.p0), make_float2(F.p1, F.p1));
+    const float2 y3 = __ffma2_rn(x0, __fadd2_rn(x0, ng), mone);
+    const float2 e = __fmul2_rn(y3, inv_d);
+    const float2 K = __ffma2_rn(y3, e, __ffma2_rn(x0, x0, one));
+    const float2 rho0 = make_float2(frcp(K.x), frcp(K.y));
+    const float2 slope = __ffma2_rn(__ffma2_rn(make_float2(2.0f, 2.0f), x0, ng), e, x0);
+    const float2 lo = __fmul2_rn(make_float2(w0, w0), rho0);
+    const float2 hi = __ffma2_rn(make_float2(w0 - 1.0f, w0 - 1.0f), rho0, one);
+    const float2 c1 = __ffma2_rn(ng, e, x0);
+    const float2 c0 = __ffma2_rn(e, mone, one);
+    const float2 dq = __ffma2_rn(c1, c1, __fmul2_rn(__fmul2_rn(make_float2(-4.0f, -4.0f), e), c0));
+    const float2 R = __ffma2_rn(rho0, mone, one);
+    const float2 hR = __fmul2_rn(make_float2(0.5f, 0.5f), R);
+    // -rho0 * x0 * e = ((-rho0) x0) e, with the sign moved onto x0 (exact)
+    const float2 q = __fmul2_rn(__fmul2_rn(rho0, __fmul2_rn(x0, mone)), e);
+    const float2 in = __ffma2_rn(hR, c1, q);
+    float2 rho1 = __ffma2_rn(in, make_float2(frsqrt_fast(fmax_(dq.x, 1e-30f)), frsqrt_fast(fmax_(dq.y, 1e-30f))), hR);
+    rho1 = make_float2(fclamp(rho1.x, 0.0f, R.x), fclamp(rho1.y, 0.0f, R.y));
+    const float2 Ain = __ffma2_rn(make_float2(w0, w0), rho0, rho1);
+    return make_float2(y3.x < 0.0f ? Ain.x : (slope.x < 0.0f ? lo.x : hi.x),
+                       y3.y < 0.0f ? Ain.y : (slope.y < 0.0f ? lo.y : hi.y));
+}
+#endif
+
 MB_HD float transmittance(const Frame& F, float z0, float w0) {
     float A = bound_fraction(F, z0, w0);
     return fclamp(fexp2(-F.m0_log2e * A), 0.0f, 1.0f);

@@ -95,8 +95,9 @@ __device__ __forceinline__ bool window_box(const GridD& g, const float o[3], con
 
 
 // Marches the lattice indices [k0, k1] of this lane's ray (exactly the
-// in-domain points; k0 > k1: none), calling body(t, value) for every owned
-// sample in depth order.  All 32 lanes of the warp call it together.
+// in-domain points; k0 > k1: none), calling body(t, xt) with the table
+// coordinate xt of every owned sample in depth order (and storing xt, NaN for
+// a point not sampled).  All 32 lanes of the warp call it together.
 template <class Cfg, bool kSel, class Body, class Store = NoStore>
 __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __restrict__ sel, float* __restrict__ win,
                                             const float o[3], const float d[3], int k0, int k1, Body& body,
@@ -175,8 +176,9 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
                                              c[Cfg::Plane + 1], c[Cfg::Plane + Cfg::Pitch],
                                              c[Cfg::Plane + Cfg::Pitch + 1], p0 - (float)ix, p1 - (float)iy,
                                              p2 - (float)iz);
-                store.put(val);
-                body(t, val);
+                const float xt = tf_x(g, val);
+                store.put(xt);
+                body(t, xt);
             }
         } else {
             const float tz = lattice_t(kz, g.step);
@@ -187,8 +189,9 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
                     store.put(__int_as_float(0x7fc00000));
                     continue;
                 }
-                store.put(val);
-                body(t, val);
+                const float xt = tf_x(g, val);
+                store.put(xt);
+                body(t, xt);
             }
         }
         kb = ke + 1;

@@ -169,7 +169,8 @@ struct TetWalk;
 template <class V> struct WalkOf { using type = NoWalk; };
 template <bool kNarrow> struct WalkOf<TetT<kNarrow>> { using type = TetWalk; };
 
-// One owned sample of `piece` at lattice index k, or the next index to try.
+// One owned sample of `piece` at lattice index k (its table coordinate in
+// `val`), or the next index to try.
 template <class V>
 __device__ __forceinline__ bool piece_sample(const V& vol, const int32_t* __restrict__ pou, int piece, float t,
                                              const float o[3], const float d[3], int k, float& val, int& k_next,
@@ -192,10 +193,10 @@ __device__ __forceinline__ bool piece_sample(const V& vol, const int32_t* __rest
             return false;
         }
         ws = (float)(1 << shift);
-        val = tag_shift(unit_value(vol, p, u), shift, shift_tag_mask(vol));
+        val = tag_shift(tf_x(g, unit_value(vol, p, u)), shift, shift_tag_mask(vol));
         return true;
     }
-    val = unit_value(vol, p, u);
+    val = tf_x(g, unit_value(vol, p, u));
     return true;
 }
 
@@ -463,7 +464,7 @@ __device__ __forceinline__ bool piece_sample(const TetT<kNarrow>& m, const int32
     long long D[4];
     if (!tet_walk<kNarrow>(m, w, q, D)) return false;
     if (__ldg(pou + w.T) != piece) return false;
-    val = tet_value(D, w.v);
+    val = tf_x(g, tet_value(D, w.v));
     return true;
 }
 
@@ -519,7 +520,7 @@ __device__ __forceinline__ void march_unit(const TetT<kNarrow>& m, const uint8_t
         const bool found = f == -1 || tet_search<kNarrow>(m, w, q, D);
         float val = __int_as_float(0x7fc00000);
         if (found && (!kSel || __ldg(sel + w.T))) {
-            val = tet_value(D, w.v);
+            val = tf_x(g, tet_value(D, w.v));
             body(t, val);
         }
         store.put(val);
@@ -531,9 +532,78 @@ __device__ __forceinline__ void march_unit(const TetT<kNarrow>& m, const uint8_t
     }
 }
 
+// Fixed-step octree march of pass 1 for leaves of NV^3 vertices, in
+// lockstep: the warp walks the lattice rows kmin..kmax in windows of
+// kDepthRows, each lane sampling the rows of its own [k0, k1], and the depth
+// powers of a window's rows are computed once for the warp (DepthRows).  A
+// lane keeps its previous sample's leaf: q = (p - lo) / h is exact in float32
+// (lo a multiple of ulp(p), h a power of two), p lies in the leaf's half-open
+// box iff 0 <= q < NV - 1 per axis (one unsigned compare of the float bits:
+// negative values and NaN have the sign bit or a large exponent), and then q
+// is also the sample's local coordinate, its cell (int)q <= NV - 2.  Points
+// outside every leaf (holes) and in unselected leaves are stored as NaN, as
+// in march_unit.  Results equal march_unit's with MomentBody bit for bit.
+template <int NV, bool kSel, class Store>
+__device__ __forceinline__ void march_amr_rows(const AmrD& a, const uint8_t* __restrict__ sel, const float o[3],
+                                               const float d[3], int k0, int k1, MomentBody& body, Store& store,
+                                               DepthRows rows) {
+    const GridD& g = a.g;
+    const unsigned full = 0xffffffffu;
+    const bool any = k0 <= k1;
+    const int kmin = __reduce_min_sync(full, any ? k0 : 0x7fffffff);
+    const int kmax = __reduce_max_sync(full, any ? k1 : -1);
+    if (any) store.seek(k0);
+    constexpr unsigned kEdge = 0x41000000u;            // bits of 8.0f = NV - 1 for NV = 9
+    static_assert(NV == 9, "the box test's bound is NV - 1 = 8");
+    const float* blk = nullptr;                         // the cached leaf's vertex block (NULL: none selected)
+    float lo0 = __int_as_float(0x7f800000), lo1 = lo0, lo2 = lo0, inv_h = 1.0f;   // no box yet
+    for (int kw = kmin; kw <= kmax; kw += kDepthRows) {
+        rows.fill(kw, g.step, body.wa, body.wb);
+        const int ka = max(kw, k0), kz = min(kw + kDepthRows - 1, k1);
+        float t = lattice_t(ka, g.step);
+        for (int k = ka; k <= kz; ++k, t += g.step) {
+            const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
+            float q0 = (p0 - lo0) * inv_h, q1 = (p1 - lo1) * inv_h, q2 = (p2 - lo2) * inv_h;
+            if (!(__float_as_uint(q0) < kEdge && __float_as_uint(q1) < kEdge && __float_as_uint(q2) < kEdge)) {
+                // a new leaf: the finest-brick map, then the leaf record
+                const float p[3] = {p0, p1, p2};
+                const int v = unit_of(a, p);
+                if (v < 0) {
+                    lo0 = lo1 = lo2 = __int_as_float(0x7f800000);
+                    blk = nullptr;
+                    store.put(__int_as_float(0x7fc00000));
+                    continue;
+                }
+                const int4 L = __ldg(a.leaves + v);
+                lo0 = (float)L.x;
+                lo1 = (float)L.y;
+                lo2 = (float)L.z;
+                inv_h = leaf_inv_h(a, L.w);
+                blk = (kSel && !__ldg(sel + v)) ? nullptr : a.values + (size_t)v * (NV * NV * NV);
+                q0 = (p0 - lo0) * inv_h;
+                q1 = (p1 - lo1) * inv_h;
+                q2 = (p2 - lo2) * inv_h;
+            }
+            if (kSel && !blk) {
+                store.put(__int_as_float(0x7fc00000));
+                continue;
+            }
+            const int cx = (int)q0, cy = (int)q1, cz = (int)q2;
+            const float* __restrict__ c = blk + (cz * NV + cy) * NV + cx;
+            const float val = tf_x(g, trilinear8(__ldg(c), __ldg(c + 1), __ldg(c + NV), __ldg(c + NV + 1),
+                                                 __ldg(c + NV * NV), __ldg(c + NV * NV + 1), __ldg(c + NV * NV + NV),
+                                                 __ldg(c + NV * NV + NV + 1), q0 - (float)cx, q1 - (float)cy,
+                                                 q2 - (float)cz));
+            store.put(val);
+            body.add(val, 1.0f, rows.z[k - kw]);
+        }
+    }
+}
+
 template <bool kSel, class Body, class Store = NoStore>
 __device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restrict__ sel, const float o[3],
-                                           const float d[3], int k0, int k1, Body& body, Store store = Store{}) {
+                                           const float d[3], int k0, int k1, Body& body, Store store = Store{},
+                                           float4* zrows = nullptr) {
     const GridD& g = a.g;
     if (g.flags & kFlagAdaptiveStep) {
         // adaptive dyadic step: a point counts only on its leaf's nested
@@ -561,11 +631,17 @@ __device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restr
                 store.put(__int_as_float(0x7fc00000));
                 continue;
             }
-            const float val = tag_shift(leaf_value(a, p, u, lc.lo, lc.inv_h), shift, tag_mask(a.max_level));
+            const float val = tag_shift(tf_x(g, leaf_value(a, p, u, lc.lo, lc.inv_h)), shift, tag_mask(a.max_level));
             store.put(val);
             body(t, val, (float)(1 << shift));
         }
         return;
+    }
+    if constexpr (std::is_same<Body, MomentBody>::value) {
+        if (zrows && a.nv == 9) {
+            march_amr_rows<9, kSel>(a, sel, o, d, k0, k1, body, store, DepthRows{zrows});
+            return;
+        }
     }
     if (k0 > k1) return;
     store.seek(k0);
@@ -578,7 +654,7 @@ __device__ __forceinline__ void march_unit(const AmrD& a, const uint8_t* __restr
             store.put(__int_as_float(0x7fc00000));
             continue;
         }
-        const float val = leaf_value(a, p, u, lc.lo, lc.inv_h);
+        const float val = tf_x(g, leaf_value(a, p, u, lc.lo, lc.inv_h));
         store.put(val);
         body(t, val);
     }
@@ -603,12 +679,14 @@ __global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 1>::value : 2) k_p
                                                     char* __restrict__ moments, Counters* __restrict__ ctr,
                                                     const TileCache cache) {
     __shared__ float2 s_sig[256];
+    __shared__ float4 s_z[kFusedWarps][kDepthRows];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float s0 = tf[i].w;
         s_sig[i] = make_float2(s0, i < 255 ? tf[i + 1].w - s0 : 0.0f);
     }
     __syncthreads();
     const GridD& g = a.g;
+    float4* zrows = s_z[threadIdx.x >> 5];
     int vi, px, py, tile;
     while (next_tile(vt, &ctr->tile_next[0], vi, px, py, tile)) {
         const ViewSlot& S = vt.s[vi];
@@ -617,7 +695,14 @@ __global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 1>::value : 2) k_p
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
         auto body = make_moment_body<MS>(s_sig, g, S.v);
-        if constexpr (kCache) {
+        if constexpr (std::is_same<V, AmrD>::value) {
+            if constexpr (kCache) {
+                RowStore st{tile_rows(cache, ctr, tile, k0, k1)};
+                march_unit<kSel>(a, sel, o, d, k0, k1, body, st, zrows);
+            } else {
+                march_unit<kSel>(a, sel, o, d, k0, k1, body, NoStore{}, zrows);
+            }
+        } else if constexpr (kCache) {
             RowStore st{tile_rows(cache, ctr, tile, k0, k1)};
             march_unit<kSel>(a, sel, o, d, k0, k1, body, st);
         } else {
@@ -745,8 +830,9 @@ __global__ void __launch_bounds__(128) k_sortlast_piece(const __grid_constant__ 
             prev = k;
             k = kn;
             if (kFill) {
-                int i;
-                const float f = tf_coord(g, val, i);
+                // val is the table coordinate; a tagged one may sit a few ulp above 255
+                const int i = min((int)val, 254);
+                const float f = fmin_(val - (float)i, 1.0f);
                 const float4 e0 = s_tf[i], e1 = s_tf[i + 1];
                 const float a = fmin_(ffma(f, e1.w - e0.w, e0.w) * ws, g.absorbance_max);
                 const float w = tr * one_minus_exp_neg(a);

@@ -63,7 +63,10 @@ __global__ void __launch_bounds__(256, FrameMinBlocks<V>::value) k_frame_unit(
         // pass 1: moments of every selected piece, summed in registers
         auto m1 = make_moment_body<0>(s_sig, g, S.v);
         RowStore st{base >= 0 ? cache.vals + (base - kmin) * 32 + lane : nullptr};
-        march_unit<kSel>(a, sel, o, d, k0, k1, m1, st);
+        if constexpr (std::is_same<V, AmrD>::value)
+            march_unit<kSel>(a, sel, o, d, k0, k1, m1, st, reinterpret_cast<float4*>(buf));
+        else
+            march_unit<kSel>(a, sel, o, d, k0, k1, m1, st);
         if (valid) m1.store(g, moments, S, S.moment_off, pix);
         warp_add_u64(&ctr->samples[0], m1.n);
 

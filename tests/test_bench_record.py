@@ -1,23 +1,52 @@
 """The committed ncu record the benchmark reports beside its roofline covers
-the current sources of the frame kernels (it turns stale, and this fails,
-when those sources change without a new capture), and applies only to its
-own kernel and workload."""
+the current sources of the frame kernel of the headline workload (it turns
+stale, and this fails, when those sources change without a new capture), and
+applies only to its own kernel and workload."""
 import bench
 
 
-KERNEL = "k_frame_fused"   # the frame's kernel: one launch per frame
+KERNEL = "k_frame_unit"   # the octree frame's kernel: one launch per frame
 
 
 def test_ncu_record_matches_current_kernel_sources():
-    rec = bench.measured_ncu(KERNEL, "blobs512")
+    rec = bench.measured_ncu(KERNEL, "amr")
     assert rec is not None, "profiles/ record is stale: re-capture the frame kernel"
-    assert rec["dram_bytes_per_launch"] > 1e9
+    assert rec["dram_bytes_per_launch"] > 1e9 and rec["samples_per_launch"] > 1e8
     assert 0 < rec["issue_active_pct"] <= 100 and 0 < rec["l1_data_pipe_pct"] <= 100
-    assert bench.measured_traffic(KERNEL, "blobs512") == int(rec["dram_bytes_per_launch"])
+    assert bench.measured_traffic(KERNEL, "amr") == int(rec["dram_bytes_per_launch"])
 
 
 def test_ncu_record_is_not_reused_for_other_kernels_or_workloads():
-    assert bench.measured_ncu("k_pass2_fused_frame", "blobs512") is None
-    assert bench.measured_ncu("k_pass1_fused_frame", "blobs512") is None
-    assert bench.measured_ncu(KERNEL, "amr") is None
+    assert bench.measured_ncu("k_pass2_unit_frame", "amr") is None
+    assert bench.measured_ncu("k_pass1_unit_frame", "amr") is None
+    assert bench.measured_ncu(KERNEL, "blobs512") is None
     assert bench.measured_traffic(KERNEL, "tets") is None
+
+
+def test_ncu_record_round_trip(tmp_path):
+    """The record writer reads an ncu raw CSV dump and the reader takes it
+    back only for the same kernel, workload and sources."""
+    csv = tmp_path / "raw.csv"
+    names = ["dram__bytes_read.sum", "dram__bytes_write.sum", "smsp__inst_executed.sum", "gpu__time_duration.sum",
+             "smsp__issue_active.avg.pct_of_peak_sustained_active", "sm__throughput.avg.pct_of_peak_sustained_elapsed",
+             "l1tex__throughput.avg.pct_of_peak_sustained_active", "lts__throughput.avg.pct_of_peak_sustained_elapsed",
+             "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed",
+             "sm__inst_executed_pipe_alu.avg.pct_of_peak_sustained_active",
+             "sm__inst_executed_pipe_fma.avg.pct_of_peak_sustained_active",
+             "sm__inst_executed_pipe_xu.avg.pct_of_peak_sustained_active",
+             "sm__inst_executed_pipe_lsu.avg.pct_of_peak_sustained_active"]
+    units = ["Gbyte", "Mbyte", "inst", "msecond"] + ["%"] * 9
+    vals = ["1.5", "500", "3200000", "2.0"] + ["50"] * 9
+    csv.write_text("\n".join(",".join(f'"{x}"' for x in row) for row in (names, units, vals)) + "\n")
+    out = tmp_path / "rec.txt"
+    old = dict(bench.NCU_RECORDS)
+    try:
+        bench.NCU_RECORDS["blobs64"] = str(out)
+        rec = bench.write_ncu_record(str(csv), "k_test", "blobs64", 400000, str(out))
+        assert rec["dram_bytes_per_launch"] == 2_000_000_000 and rec["inst_per_sample"] == 256.0
+        back = bench.measured_ncu("k_test", "blobs64")
+        assert back["dram_bytes_per_launch"] == 2e9 and back["samples_per_launch"] == 400000
+        assert bench.measured_ncu("k_other", "blobs64") is None
+    finally:
+        bench.NCU_RECORDS.clear()
+        bench.NCU_RECORDS.update(old)

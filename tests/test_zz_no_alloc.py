@@ -7,8 +7,12 @@ implicit synchronisation of an allocation.  Its scratch is a fixed array
 inside the library (at most 1,048,576 bricks).  These tests call it through
 the C ABI and compare it with mboit_render_moments (REDUCED), which uses a
 volume's allocated scratch, within the moment tolerance of the other GPU
-tests, on two calls in a row (the array keeps the previous call's contents).
-This file is collected last on purpose."""
+tests.  Calls follow one another on one stream with a brick mask, without
+one, and with another transfer function, so that nothing the shared array
+keeps from a previous call (the mask, the table, the queue head) can pass
+unnoticed.  This file is collected last on purpose."""
+import copy
+
 import numpy as np
 import pytest
 
@@ -28,9 +32,7 @@ def env():
     __graft_entry__.build()
     import paper_2501_12581_gb300 as pkg
     sc = scenes.blobs64(width=96, height=80)
-    vol = pkg.Volume(sc)
-    yield torch, pkg, sc, vol
-    vol.close()
+    yield torch, pkg, sc
 
 
 def _pixels(buf, view):
@@ -47,32 +49,71 @@ def _close(got, ref):
     assert err.max() <= TOL_MOM, f"moment error {err.max():.3e}"
 
 
-@pytest.mark.parametrize("pieces", [None, [1, 3]])
-def test_noalloc_pass1_matches_render_moments(env, pieces):
-    torch, pkg, sc, vol = env
-    views = sc.views
-    ref = pkg.Volume.moment_buffer(views)
-    vol.render_moments(views, ref, pieces=pieces)
+def _reference(torch, pkg, sc, pieces):
+    """mboit_render_moments of a volume built from the same inputs."""
+    vol = pkg.Volume(sc)
+    ref = pkg.Volume.moment_buffer(sc.views)
+    vol.render_moments(sc.views, ref, pieces=pieces)
     torch.cuda.synchronize()
-    want = _pixels(ref, views[0])
+    want = _pixels(ref, sc.views[0])
+    vol.close()
     assert want[:, 0].max() > 0
-    desc, keep = pkg.grid_desc(sc, vol.field)
-    mask = None if pieces is None else np.isin(sc.piece_of_brick, pieces).astype(np.uint8)
-    for _ in range(2):
-        out = torch.full_like(ref, float("nan"))
-        pkg.mboit_render_moments_noalloc(desc, views, out, brick_selected=mask)
+    return want
+
+
+def test_noalloc_pass1_matches_render_moments(env):
+    torch, pkg, sc = env
+    other = copy.copy(sc)
+    tf2 = sc.tf.copy()
+    tf2[:, 3] = np.clip(tf2[:, 3] * 1.7 + 0.01, 0.0, 0.9)   # another opacity table
+    tf2[:, :3] = tf2[::-1, :3]
+    other.tf = tf2.astype(np.float32)
+    # (scene, selected pieces) in call order: masked, unmasked, masked again,
+    # another transfer function without a mask, then the first scene again
+    calls = [(sc, [1, 3]), (sc, None), (sc, [0, 2]), (other, None), (sc, None)]
+    field = torch.from_numpy(np.ascontiguousarray(sc.field)).cuda()
+    for scene, pieces in calls:
+        want = _reference(torch, pkg, scene, pieces)
+        desc, keep = pkg.grid_desc(scene, field)
+        mask = None if pieces is None else np.isin(scene.piece_of_brick, pieces).astype(np.uint8)
+        out = pkg.Volume.moment_buffer(scene.views).fill_(float("nan"))
+        pkg.mboit_render_moments_noalloc(desc, scene.views, out, brick_selected=mask)
         torch.cuda.synchronize()
-        _close(_pixels(out, views[0]), want)
-    del keep
+        _close(_pixels(out, scene.views[0]), want)
+        del keep
 
 
-def test_noalloc_rejects_volumes_beyond_its_scratch(env):
-    torch, pkg, sc, vol = env
-    desc, keep = pkg.grid_desc(sc, vol.field)
-    desc.dims[:] = [1 << 12, 1 << 12, 2]   # 2^22 one-cell bricks > 2^20
-    desc.brick_log2 = 0
-    out = pkg.Volume.moment_buffer(sc.views)
-    with pytest.raises(pkg.MboitError) as e:
+def test_noalloc_two_calls_in_a_row(env):
+    """Two calls back to back on one stream, synchronised only at the end."""
+    torch, pkg, sc = env
+    want = _reference(torch, pkg, sc, None)
+    field = torch.from_numpy(np.ascontiguousarray(sc.field)).cuda()
+    desc, keep = pkg.grid_desc(sc, field)
+    outs = [pkg.Volume.moment_buffer(sc.views).fill_(float("nan")) for _ in range(2)]
+    for out in outs:
         pkg.mboit_render_moments_noalloc(desc, sc.views, out)
-    assert e.value.status == 1 and "at most" in str(e.value)
+    torch.cuda.synchronize()
+    for out in outs:
+        _close(_pixels(out, sc.views[0]), want)
     del keep
+
+
+def test_noalloc_rejects_bad_arguments(env):
+    torch, pkg, sc = env
+    field = torch.from_numpy(np.ascontiguousarray(sc.field)).cuda()
+    desc, keep = pkg.grid_desc(sc, field)
+    out = pkg.Volume.moment_buffer(sc.views)
+    with pytest.raises(ValueError):
+        pkg.mboit_render_moments_noalloc(desc, sc.views, out, brick_selected=np.ones(7, np.uint8))
+    bad, keep_bad = pkg.grid_desc(sc, field)
+    bad.overestimation = 1.5
+    with pytest.raises(pkg.MboitError) as e:
+        pkg.mboit_render_moments_noalloc(bad, sc.views, out)
+    assert e.value.status == 1 and "overestimation" in str(e.value)
+    big, keep_big = pkg.grid_desc(sc, field)
+    big.dims[:] = [1 << 12, 1 << 12, 2]   # 2^22 one-cell bricks > 2^20
+    big.brick_log2 = 0
+    with pytest.raises(pkg.MboitError) as e:
+        pkg.mboit_render_moments_noalloc(big, sc.views, out)
+    assert e.value.status == 1 and "at most" in str(e.value)
+    del keep, keep_bad, keep_big
