@@ -55,10 +55,14 @@ CACHE_BYTES_PER_SAMPLE = 4
 # 2 FLOP x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 CSRC = os.path.join(ROOT, "paper_2501_12581_gb300", "csrc")
-# committed ncu records of the frame kernel per workload (DRAM bytes per launch
-# and the binding units' activity), valid while the kernel sources are unchanged
-NCU_RECORDS = {"blobs512": os.path.join(ROOT, "profiles", "frame_fused_blobs512_traffic.txt"),
-               "amr": os.path.join(ROOT, "profiles", "frame_unit_amr_traffic.txt")}
+# committed ncu records of the frame kernels (DRAM bytes per launch and the
+# binding units' activity), one file per (kernel, workload), valid while the
+# kernel sources are unchanged
+NCU_DIR = os.path.join(ROOT, "profiles")
+
+
+def ncu_record_path(kernel, workload):
+    return os.path.join(NCU_DIR, f"ncu_{kernel}_{workload}.txt")
 
 
 def _measured_peaks():
@@ -87,7 +91,7 @@ def measured_ncu(kernel, workload):
     launch and the binding units' activity), or None when there is none for
     that kernel and workload or the kernel sources changed since."""
     try:
-        kv = dict(tok.split("=", 1) for tok in open(NCU_RECORDS[workload]).read().split() if "=" in tok)
+        kv = dict(tok.split("=", 1) for tok in open(ncu_record_path(kernel, workload)).read().split() if "=" in tok)
         if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("kernel_sha") == kernel_hash():
             return {k: float(v) for k, v in kv.items() if k not in ("kernel", "workload", "kernel_sha", "note")}
     except (OSError, ValueError, KeyError):

@@ -63,6 +63,7 @@ struct mboit_volume_s {
     mb::GridD grid{};
     mb::AmrD amr{};             // octree volumes: amr.g aliases the sampling parameters
     int4* d_leaves = nullptr;
+    float4* d_leaf_box = nullptr;
     int32_t* d_fmap = nullptr;
     std::vector<int32_t> leaf_table;
     mb::TetD tet{};             // tetrahedral meshes: amr-like parameters plus the device tables below
@@ -838,13 +839,24 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
             e = cudaMemcpy(v->d_leaves, d->leaf_table, (size_t)d->n_leaves * sizeof(int4), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(v->d_fmap, fmap.data(), fmap.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+        // per leaf its origin in finest cells and 1 / cell size, as the march reads them
+        std::vector<float4> box((size_t)d->n_leaves);
+        for (int32_t l = 0; l < d->n_leaves; ++l) {
+            const int32_t* L = d->leaf_table + 4 * (size_t)l;
+            box[(size_t)l] = make_float4((float)L[0], (float)L[1], (float)L[2], std::ldexp(1.0f, L[3] - d->max_level));
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&v->d_leaf_box, box.size() * sizeof(float4));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(v->d_leaf_box, box.data(), box.size() * sizeof(float4), cudaMemcpyHostToDevice);
         v->amr.g = g;
         v->amr.values = d->leaf_values;
         v->amr.leaves = v->d_leaves;
+        v->amr.leaf_box = v->d_leaf_box;
         v->amr.fmap = v->d_fmap;
         v->amr.fdim = (int32_t)fdim;
         v->amr.nv = (1 << d->brick_log2) + 1;
         v->amr.max_level = d->max_level;
+        v->amr.complete = std::find(fmap.begin(), fmap.end(), -1) == fmap.end() ? 1 : 0;
     }
     if (e == cudaSuccess && is_tet) {
         auto up = [&](auto*& dst, const auto& src) {
@@ -902,6 +914,7 @@ mboit_status mboit_destroy_volume(mboit_volume v) {
             if (ev) cudaEventDestroy(ev);
         cudaFree(v->d_tf);
         cudaFree(v->d_leaves);
+        cudaFree(v->d_leaf_box);
         cudaFree(v->d_fmap);
         cudaFree(v->d_tcorners);
         cudaFree(v->d_tnbrs);

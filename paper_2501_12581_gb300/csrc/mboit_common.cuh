@@ -225,21 +225,22 @@ struct BlendBody {
     __device__ __forceinline__ void operator()(float t, float xt, float ws = 1.0f) { sample<false>(t, xt, ws); }
     __device__ __forceinline__ bool singular() const { return F.kind == kFrameOneAtom || F.kind == kFrameTwoAtoms; }
 
-    // Two consecutive lattice points (depths ta, tb = ta + step) of a generic
-    // frame: the arithmetic of sample<true> on both, each operation in one
+    // Two consecutive lattice points (warped depths z.x, z.y; weight 1, the
+    // fixed step) of a generic frame: the arithmetic of sample<true> on both,
+    // each operation in one
     // packed FP32x2 instruction with the scalar form's rounding, and the
     // colour sums taken for a, then b.  The result equals two sample<true>
     // calls bit for bit.  A point with ok = false adds nothing: its table
     // coordinate is replaced by 0 (no NaN enters) and its weight by 0, and
     // fma(0, c, C) = C.
-    __device__ __forceinline__ void pair_generic(float ta, float tb, float xa, float xb, float wsa, float wsb,
-                                                 bool oka, bool okb) {
+    __device__ __forceinline__ float depth(float t) const { return warp_depth(t, wa, wb); }
+    __device__ __forceinline__ void pair_generic(float2 z, float xa, float xb, bool oka, bool okb) {
         xa = oka ? xa : 0.0f;
         xb = okb ? xb : 0.0f;
         const int ia = (int)xa, ib = (int)xb;
         const float fa = xa - (float)ia, fb = xb - (float)ib;
         const float4 ea = s_tf[2 * ia], da = s_tf[2 * ia + 1], eb = s_tf[2 * ib], db = s_tf[2 * ib + 1];
-        const float2 a = make_float2(fmin_(ffma(fa, da.w, ea.w) * wsa, amax), fmin_(ffma(fb, db.w, eb.w) * wsb, amax));
+        const float2 a = make_float2(fmin_(ffma(fa, da.w, ea.w), amax), fmin_(ffma(fb, db.w, eb.w), amax));
         // opacity 1 - e^-a: the series and the direct form for both, then the
         // one one_minus_exp_neg takes
         float2 p = __ffma2_rn(a, make_float2(-1.0f / 720.0f, -1.0f / 720.0f), make_float2(1.0f / 120.0f, 1.0f / 120.0f));
@@ -252,8 +253,6 @@ struct BlendBody {
         const float2 dir = __ffma2_rn(make_float2(fexp2(ng.x), fexp2(ng.y)), make_float2(-1.0f, -1.0f),
                                       make_float2(1.0f, 1.0f));
         const float2 alpha = make_float2(a.x < 0.25f ? ser.x : dir.x, a.y < 0.25f ? ser.y : dir.y);
-        const float2 zl = __ffma2_rn(make_float2(flog2(ta), flog2(tb)), make_float2(wa, wa), make_float2(wb, wb));
-        const float2 z = make_float2(fclamp(zl.x, -1.0f, 1.0f), fclamp(zl.y, -1.0f, 1.0f));
         const float2 A = bound_generic2(F, z, w0);
         const float2 ex = __fmul2_rn(make_float2(-F.m0_log2e, -F.m0_log2e), A);
         float2 wgt = __fmul2_rn(make_float2(fclamp(fexp2(ex.x), 0.0f, 1.0f), fclamp(fexp2(ex.y), 0.0f, 1.0f)), alpha);
@@ -276,9 +275,9 @@ struct BlendBody {
 struct GenericBlend {
     BlendBody& b;
     __device__ __forceinline__ void operator()(float t, float xt, float ws = 1.0f) { b.sample<true>(t, xt, ws); }
-    __device__ __forceinline__ void pair(float ta, float tb, float xa, float xb, float wsa, float wsb, bool oka,
-                                         bool okb) {
-        b.pair_generic(ta, tb, xa, xb, wsa, wsb, oka, okb);
+    __device__ __forceinline__ float depth(float t) const { return b.depth(t); }
+    __device__ __forceinline__ void pair(float2 z, float xa, float xb, bool oka, bool okb) {
+        b.pair_generic(z, xa, xb, oka, okb);
     }
 };
 // Bodies that take two lattice points at once (pair(...), equal to two calls).
@@ -619,13 +618,16 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 constexpr int kRowChunk = 8;                    // cache rows per prefetch
-constexpr int kRowBuf = 2 * kRowChunk * 32;     // floats of a warp's double buffer
+constexpr int kRowZ = 2 * kRowChunk * 32;       // floats of a warp's double buffer of rows
+constexpr int kRowBuf = kRowZ + kRowChunk;      // ... followed by the warped depths of a chunk's rows
 
 // Pass 2 of the batched frame from the tile cache.  The tile's rows are
 // contiguous (rows[r * 32 + lane], r = k - kmin), so the warp copies them
 // into its shared-memory buffer 8 rows (1 KiB) at a time, one chunk ahead of
 // the one it blends, and every lane takes its own column over its own
-// [k0, k1].  buf: 16-byte aligned, kRowBuf floats, this warp's only.
+// [k0, k1].  buf: 16-byte aligned, kRowBuf floats, this warp's only.  For a
+// body that takes two points at once, lanes 0..7 also compute the warped
+// depths of the chunk's 8 rows into buf[kRowZ..], which every lane reads.
 // Octree adaptive step: a sample's table coordinate carries its leaf's level
 // shift in its low mantissa bits, as few as max_level needs (2 for max_level
 // 2 or 3: the coordinate moves by at most 3 ulp, the same in both passes, the
@@ -665,9 +667,12 @@ __device__ __forceinline__ void march_rows(const GridD& g, const float* __restri
         } else {
             cp_async_wait<0>();
         }
+        const int kc = kmin + c * kRowChunk;
+        if constexpr (HasPair<Body>::value && !kTagged) {
+            if (lane < kRowChunk) buf[kRowZ + lane] = body.depth(lattice_t(kc + lane, g.step));
+        }
         __syncwarp();
         const float* src = buf + (c & 1) * kRowChunk * 32 + lane;
-        const int kc = kmin + c * kRowChunk;
         const int n = min(kRowChunk, kmax - kc + 1);
         if (kc >= k0 && kc + kRowChunk - 1 <= k1) {
             // the whole chunk lies in this lane's interval (and, without a
@@ -678,13 +683,15 @@ __device__ __forceinline__ void march_rows(const GridD& g, const float* __restri
                 // (The adaptive step leaves most points unsampled, lane-coherently:
                 // there the single-point loop below skips more.)
                 const unsigned act = __activemask();
+                const float2* zr = reinterpret_cast<const float2*>(buf + kRowZ);
 #pragma unroll
-                for (int i = 0; i < kRowChunk; i += 2, t += 2.0f * g.step) {
+                for (int i = 0; i < kRowChunk; i += 2) {
                     const float va = src[i * 32], vb = src[(i + 1) * 32];
                     const bool oka = !kSel || va == va, okb = !kSel || vb == vb;
                     if (kSel && !__any_sync(act, oka || okb)) continue;
-                    body.pair(t, t + g.step, va, vb, 1.0f, 1.0f, oka, okb);
+                    body.pair(zr[i / 2], va, vb, oka, okb);
                 }
+                t += kRowChunk * g.step;
             } else {
 #pragma unroll
                 for (int i = 0; i < kRowChunk; ++i, t += g.step) {

@@ -60,8 +60,10 @@ struct AmrD {
     GridD g;
     const float* values;    // [n_leaves][nv^3] vertex values, [z][y][x]
     const int4* leaves;     // origin x, y, z (finest cells), level
+    const float4* leaf_box; // the same origin as floats, and 2^-(max_level - level) = 1 / cell size
     const int32_t* fmap;    // [fdim^3] finest brick (2^brick_log2 cells) -> leaf, -1 none
-    int32_t fdim, nv, max_level, pad;
+    int32_t fdim, nv, max_level;
+    int32_t complete;       // 1: every finest brick has a leaf (no holes)
 };
 
 // Tetrahedral mesh as the kernels see it.  `g` carries the box

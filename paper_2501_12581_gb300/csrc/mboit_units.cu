@@ -175,7 +175,7 @@ cudaError_t launch_pass1_amr(const AmrD& a, const float4* tf, const uint8_t* uni
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
     if (e == cudaSuccess && cache.vals) e = cudaMemsetAsync(&ctr->cache_rows, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    const bool sel = unit_sel != nullptr;
+    const bool sel = unit_sel != nullptr || !a.complete;   // octrees with holes take the checked kernels
     const void* fn = cache.vals ? unit1_fn<AmrD, true>(sel, a.g.trig.sel) : unit1_fn<AmrD>(sel, a.g.trig.sel);
     char* m = static_cast<char*>(moments);
     void* args[] = {(void*)&a, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&m, (void*)&ctr, (void*)&cache};
@@ -187,7 +187,7 @@ cudaError_t launch_pass2_amr(const AmrD& a, const float4* tf, const uint8_t* uni
                              TileCache cache) {
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[1], 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const bool sel = unit_sel != nullptr;
+    const bool sel = unit_sel != nullptr || !a.complete;
     const void* fn = cache.vals ? unit2_fn<AmrD, true>(sel, a.g.trig.sel) : unit2_fn<AmrD>(sel, a.g.trig.sel);
     const char* m = static_cast<const char*>(moments);
     int md = mode;

@@ -104,7 +104,7 @@ struct LeafCache {
         lo[0] = (float)L.x; lo[1] = (float)L.y; lo[2] = (float)L.z;
         inv_h = leaf_inv_h(a, L.w);
         shift = a.max_level - L.w;
-        u = (kSel && !__ldg(sel + v)) ? -1 : v;
+        u = (kSel && sel && !__ldg(sel + v)) ? -1 : v;
         return u;
     }
 };
@@ -161,6 +161,13 @@ __device__ __forceinline__ int next_on_lattice(const V& vol, int u, int shift, c
     const int kn = min((k | ((1 << shift) - 1)) + 1, skip_unit(vol, u, o, d, t, k));
     return min(kn, k_end);
 }
+
+// Whether pass 2 from the cache must test its rows for unsampled points
+// (NaN).  Octrees launch the kSel kernels when a piece is left out or when a
+// finest brick has no leaf (holes; sel is then NULL), so an unchecked octree
+// kernel sees every in-domain point sampled; meshes are always checked.
+template <class V, bool kSel> struct RowsChecked { static constexpr bool value = true; };
+template <bool kSel> struct RowsChecked<AmrD, kSel> { static constexpr bool value = kSel; };
 
 // Per-ray state of a sampler: none for grids and octrees (a point's unit is
 // a table lookup), the current tet for meshes (the walk starts there).
@@ -565,7 +572,7 @@ __device__ __forceinline__ void march_amr_rows(const AmrD& a, const uint8_t* __r
             const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
             float q0 = (p0 - lo0) * inv_h, q1 = (p1 - lo1) * inv_h, q2 = (p2 - lo2) * inv_h;
             if (!(__float_as_uint(q0) < kEdge && __float_as_uint(q1) < kEdge && __float_as_uint(q2) < kEdge)) {
-                // a new leaf: the finest-brick map, then the leaf record
+                // a new leaf: the finest-brick map, then the leaf's box
                 const float p[3] = {p0, p1, p2};
                 const int v = unit_of(a, p);
                 if (v < 0) {
@@ -574,12 +581,12 @@ __device__ __forceinline__ void march_amr_rows(const AmrD& a, const uint8_t* __r
                     store.put(__int_as_float(0x7fc00000));
                     continue;
                 }
-                const int4 L = __ldg(a.leaves + v);
-                lo0 = (float)L.x;
-                lo1 = (float)L.y;
-                lo2 = (float)L.z;
-                inv_h = leaf_inv_h(a, L.w);
-                blk = (kSel && !__ldg(sel + v)) ? nullptr : a.values + (size_t)v * (NV * NV * NV);
+                const float4 L = __ldg(a.leaf_box + v);
+                lo0 = L.x;
+                lo1 = L.y;
+                lo2 = L.z;
+                inv_h = L.w;
+                blk = (kSel && sel && !__ldg(sel + v)) ? nullptr : a.values + (size_t)v * (NV * NV * NV);
                 q0 = (p0 - lo0) * inv_h;
                 q1 = (p1 - lo1) * inv_h;
                 q2 = (p2 - lo2) * inv_h;
@@ -751,7 +758,7 @@ __global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 2>::value : 2) k_p
             if (tagged)
                 blend_rows<true, true>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, buf, body, tmask);
             else
-                blend_rows<true>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, buf, body);
+                blend_rows<RowsChecked<V, kSel>::value>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, buf, body);
         } else {
             march_unit<kSel>(a, sel, o, d, k0, k1, body);
         }

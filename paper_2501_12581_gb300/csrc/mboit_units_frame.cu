@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256, FrameMinBlocks<V>::value) k_frame_unit(
             if (tagged)
                 blend_rows<true, true>(g, cache.vals + base * 32, kmin, kmax, k0, k1, buf, body, tmask);
             else
-                blend_rows<true>(g, cache.vals + base * 32, kmin, kmax, k0, k1, buf, body);
+                blend_rows<RowsChecked<V, kSel>::value>(g, cache.vals + base * 32, kmin, kmax, k0, k1, buf, body);
         } else {
             march_unit<kSel>(a, sel, o, d, k0, k1, body);
         }
@@ -98,6 +98,10 @@ TetT<kN> as_tet(const TetD& m) {
     return t;
 }
 
+// Octrees with holes take the checked kernels (see RowsChecked).
+template <class V> bool complete_units(const V&) { return true; }
+template <> bool complete_units<AmrD>(const AmrD& a) { return a.complete != 0; }
+
 template <class V>
 const void* frame_unit_fn(bool sel) {
     return sel ? (const void*)k_frame_unit<V, true> : (const void*)k_frame_unit<V, false>;
@@ -110,7 +114,7 @@ cudaError_t launch_frame_unit(const V& vol, const float4* tf, const uint8_t* uni
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&ctr->cache_rows, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    const void* fn = frame_unit_fn<V>(unit_sel != nullptr);
+    const void* fn = frame_unit_fn<V>(unit_sel != nullptr || !complete_units(vol));
     char* mo = static_cast<char*>(moments);
     int md = mode;
     void* args[] = {(void*)&vol, (void*)&tf, (void*)&unit_sel, (void*)&vt, (void*)&mo, (void*)&color, (void*)&md,

@@ -1,26 +1,32 @@
-"""The committed ncu record the benchmark reports beside its roofline covers
-the current sources of the frame kernel of the headline workload (it turns
-stale, and this fails, when those sources change without a new capture), and
+"""The committed ncu records the benchmark reports beside its roofline cover
+the current sources of the headline workload's frame kernels, in either form
+the autotuner may pick (one launch, or pass 1 + pass 2); they turn stale, and
+this fails, when those sources change without a new capture.  A record
 applies only to its own kernel and workload."""
+import pytest
+
 import bench
 
 
-KERNEL = "k_frame_unit"   # the octree frame's kernel: one launch per frame
+KERNEL = "k_frame_unit"   # the octree frame's kernel in one launch
 
 
-def test_ncu_record_matches_current_kernel_sources():
-    rec = bench.measured_ncu(KERNEL, "amr")
-    assert rec is not None, "profiles/ record is stale: re-capture the frame kernel"
-    assert rec["dram_bytes_per_launch"] > 1e9 and rec["samples_per_launch"] > 1e8
+@pytest.mark.parametrize("kernel", ["k_frame_unit", "k_pass1_unit_frame", "k_pass2_unit_frame"])
+def test_ncu_record_matches_current_kernel_sources(kernel):
+    rec = bench.measured_ncu(kernel, "amr")
+    assert rec is not None, f"profiles/ record of {kernel} is stale: re-capture it"
+    assert rec["dram_bytes_per_launch"] > 1e8 and rec["samples_per_launch"] > 1e8
     assert 0 < rec["issue_active_pct"] <= 100 and 0 < rec["l1_data_pipe_pct"] <= 100
-    assert bench.measured_traffic(KERNEL, "amr") == int(rec["dram_bytes_per_launch"])
+    assert bench.measured_traffic(kernel, "amr") == int(rec["dram_bytes_per_launch"])
 
 
 def test_ncu_record_is_not_reused_for_other_kernels_or_workloads():
-    assert bench.measured_ncu("k_pass2_unit_frame", "amr") is None
-    assert bench.measured_ncu("k_pass1_unit_frame", "amr") is None
-    assert bench.measured_ncu(KERNEL, "blobs512") is None
+    assert bench.measured_ncu("k_pass2_unit", "amr") is None          # the split form has no record
+    assert bench.measured_ncu(KERNEL, "tets") is None
     assert bench.measured_traffic(KERNEL, "tets") is None
+    one = bench.measured_ncu(KERNEL, "amr")
+    two = bench.measured_ncu("k_pass1_unit_frame", "amr")
+    assert one["launch_ms"] != two["launch_ms"]
 
 
 def test_ncu_record_round_trip(tmp_path):
@@ -38,15 +44,14 @@ def test_ncu_record_round_trip(tmp_path):
     units = ["Gbyte", "Mbyte", "inst", "msecond"] + ["%"] * 9
     vals = ["1.5", "500", "3200000", "2.0"] + ["50"] * 9
     csv.write_text("\n".join(",".join(f'"{x}"' for x in row) for row in (names, units, vals)) + "\n")
-    out = tmp_path / "rec.txt"
-    old = dict(bench.NCU_RECORDS)
+    old = bench.NCU_DIR
     try:
-        bench.NCU_RECORDS["blobs64"] = str(out)
+        bench.NCU_DIR = str(tmp_path)
+        out = tmp_path / "ncu_k_test_blobs64.txt"
         rec = bench.write_ncu_record(str(csv), "k_test", "blobs64", 400000, str(out))
         assert rec["dram_bytes_per_launch"] == 2_000_000_000 and rec["inst_per_sample"] == 256.0
         back = bench.measured_ncu("k_test", "blobs64")
         assert back["dram_bytes_per_launch"] == 2e9 and back["samples_per_launch"] == 400000
         assert bench.measured_ncu("k_other", "blobs64") is None
     finally:
-        bench.NCU_RECORDS.clear()
-        bench.NCU_RECORDS.update(old)
+        bench.NCU_DIR = old
