@@ -843,6 +843,7 @@ def main():
            "tuning": {"pass1": tuning[0], "pass2": tuning[1],
                       "packet": "4x8" if tuning[2] == pkg.MBOIT_PACKET_4X8 else "8x4", "frame_launches": launches},
            "samples_per_frame": samples, "ms_per_frame": ms_max, "singular_pixels": st["singular_pixels"],
+           "fp64_setup_pixels": st["fp64_pixels"],
            "per_piece_fp32": per_piece, "sortlast_gpu": sortlast, "adaptive_step": adaptive,
            "grid_512_64_pieces": grid, "tets_72_pieces": tets, "mixed_cells_72_pieces": mixed,
            "gear_teeth_stress": gear,

@@ -205,7 +205,10 @@ typedef struct {
     int32_t tuning_pass2;
     int64_t sortlast_segments;  /* segments of the last mboit_render_sortlast */
     int32_t sortlast_max_segments; /* most segments on one pixel in it */
-    int32_t reserved;
+    int32_t fp64_pixels;        /* pixels of the last pass 2 whose reconstruction frame (four power moments) was
+                                 * set up in FP64: a variance or Schur complement of the biased Hankel matrix
+                                 * within 1e-4 of b2 or b4 (near-singular); every other pixel is set up in
+                                 * float-float FP32 arithmetic */
     float frame_pass1_ms;       /* device time of pass 1 in the last mboit_render_frame (CUDA events
                                  * recorded in its graph); -1 before the first frame */
     float frame_pass2_ms;       /* the same for pass 2 */

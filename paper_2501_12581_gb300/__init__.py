@@ -72,7 +72,7 @@ class mboit_stats(ctypes.Structure):
                 ("singular_pixels", ctypes.c_int64), ("n_pieces", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("tuning_pass1", ctypes.c_int32), ("tuning_pass2", ctypes.c_int32),
                 ("sortlast_segments", ctypes.c_int64), ("sortlast_max_segments", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("frame_pass1_ms", ctypes.c_float), ("frame_pass2_ms", ctypes.c_float),
+                ("fp64_pixels", ctypes.c_int32), ("frame_pass1_ms", ctypes.c_float), ("frame_pass2_ms", ctypes.c_float),
                 ("packet", ctypes.c_int32), ("frame_launches", ctypes.c_int32)]
 
 

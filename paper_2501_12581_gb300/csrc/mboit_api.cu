@@ -1081,6 +1081,7 @@ mboit_status mboit_reconstruct_blend(mboit_volume v, const mboit_view* views, in
     if ((st = select_pieces(v, pieces, n_pieces, list, &mask)) != MBOIT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->samples[1], 0, 2 * sizeof(unsigned long long), s));
+    MB_CUDA(cudaMemsetAsync(&v->d_ctr->fp64_pixels, 0, sizeof(unsigned long long), s));
     if (mode == MBOIT_COLOR_PER_PIECE) {
         const int32_t slots = (int32_t)list.size();
         for (int32_t j = 0; j < slots; ++j) {
@@ -1161,6 +1162,7 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
         cudaStream_t cs = v->cap_stream;
         MB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemsetAsync(&v->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&v->d_ctr->fp64_pixels, 0, sizeof(unsigned long long), cs);
         // external record nodes: the events are recorded each time the graph runs
         if (e == cudaSuccess) e = cudaEventRecordWithFlags(v->frame_ev[0], cs, cudaEventRecordExternal);
         if (v->frame_launches == 1) {
@@ -1248,7 +1250,7 @@ mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out) {
     out->tuning_pass2 = v->tune2;
     out->sortlast_segments = v->sl_segments;
     out->sortlast_max_segments = c.max_segments;
-    out->reserved = 0;
+    out->fp64_pixels = (int32_t)std::min<unsigned long long>(c.fp64_pixels, 0x7fffffffull);
     out->packet = v->packet;
     out->frame_launches = v->frame_launches;
     out->frame_pass1_ms = out->frame_pass2_ms = -1.0f;

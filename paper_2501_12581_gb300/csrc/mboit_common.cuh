@@ -206,6 +206,7 @@ struct BlendBody {
     float b0;
     float4 C = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     unsigned n = 0;
+    bool fp64 = false;    // the frame was set up in FP64 (near-singular Hankel matrix)
     // kGeneric: the frame is known to be generic (no test of its kind)
     template <bool kGeneric = false>
     __device__ __forceinline__ void sample(float t, float xt, float ws) {
@@ -522,7 +523,7 @@ __device__ __forceinline__ BlendBody blend_body_of(const float4* s_tf, const Gri
     b.w0 = g.overestimation;
     const float m[5] = {valid ? mb.m0 : 0.0f, valid ? mb.m1 : 0.0f, valid ? mb.m2 : 0.0f, valid ? mb.m3 : 0.0f,
                         valid ? mb.m4 : 0.0f};
-    b.F = make_frame(m, g.moment_bias, g.bias_vector);
+    b.F = make_frame_ff(m, g.moment_bias, g.bias_vector, &b.fp64);
     b.b0 = m[0];
     return b;
 }
@@ -543,7 +544,7 @@ __device__ __forceinline__ typename Bodies<MS>::Blend make_blend_body(const floa
     if constexpr (MS == 0) {
         float m[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         if (valid) load_moments(moments, S, off, pix, m);
-        b.F = make_frame(m, g.moment_bias, g.bias_vector);
+        b.F = make_frame_ff(m, g.moment_bias, g.bias_vector, &b.fp64);
         b.b0 = m[0];
     } else if constexpr (MS == 6 || MS == 8) {
         float m[MS + 1];
@@ -561,6 +562,21 @@ __device__ __forceinline__ typename Bodies<MS>::Blend make_blend_body(const floa
     return b;
 }
 
+
+// Per-pixel statistics of pass 2: pixels on a one- or two-atom branch, and
+// pixels whose frame was set up in FP64.  Called by all 32 lanes together.
+template <class Body>
+__device__ __forceinline__ void count_frames(Counters* ctr, const Body& body, bool valid) {
+    const unsigned full = 0xffffffffu;
+    const unsigned sing = __ballot_sync(full, valid && body.singular());
+    bool f64 = false;
+    if constexpr (std::is_same<Body, BlendBody>::value) f64 = body.fp64;
+    const unsigned dp = __ballot_sync(full, valid && f64);
+    if ((threadIdx.x & 31) == 0) {
+        if (sing) atomicAdd(&ctr->singular, (unsigned long long)__popc(sing));
+        if (dp) atomicAdd(&ctr->fp64_pixels, (unsigned long long)__popc(dp));
+    }
+}
 
 // Pops the next 8x4 ray tile of the work queue; returns false when empty.
 __device__ __forceinline__ bool next_tile(const ViewTable& vt, int32_t* head, int& vi, int& px, int& py, int& tile) {

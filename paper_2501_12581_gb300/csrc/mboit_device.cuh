@@ -292,6 +292,110 @@ MB_HD Frame make_frame(const float m_in[5], float moment_bias, const float bias_
     return F;
 }
 
+// ---------------------------------------------------------------------------
+// float-float arithmetic (an unevaluated sum hi + lo of two floats, ~48
+// significant bits) from error-free transformations: Knuth's TwoSum and the
+// fma-based TwoProduct, with Dekker's normalisation.  The per-pixel frame is
+// set up with it in FP32, so that only near-singular pixels need FP64.
+
+struct ff {
+    float hi, lo;
+};
+// s + e = a + b exactly (Knuth's TwoSum)
+MB_HD ff ff_two_sum(float a, float b) {
+    const float s = fadd(a, b);
+    const float bb = fadd(s, -a);
+    return {s, fadd(fadd(a, -fadd(s, -bb)), fadd(b, -bb))};
+}
+// s + e = a + b exactly, for |a| >= |b| or a = 0 (Dekker's FastTwoSum)
+MB_HD ff ff_fast_sum(float a, float b) {
+    const float s = fadd(a, b);
+    return {s, fadd(b, -fadd(s, -a))};
+}
+// p + e = a b exactly (the fma returns the product's rounding error)
+MB_HD ff ff_two_prod(float a, float b) {
+    const float p = fmul(a, b);
+    return {p, ffma(a, b, -p)};
+}
+MB_HD ff ff_add(ff a, ff b) {
+    ff s = ff_two_sum(a.hi, b.hi);
+    const ff t = ff_two_sum(a.lo, b.lo);
+    s = ff_fast_sum(s.hi, fadd(s.lo, t.hi));
+    return ff_fast_sum(s.hi, fadd(s.lo, t.lo));
+}
+MB_HD ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+MB_HD ff ff_mul(ff a, ff b) {
+    const ff p = ff_two_prod(a.hi, b.hi);
+    return ff_fast_sum(p.hi, ffma(a.hi, b.lo, ffma(a.lo, b.hi, p.lo)));
+}
+MB_HD ff ff_mulf(ff a, float b) {
+    const ff p = ff_two_prod(a.hi, b);
+    return ff_fast_sum(p.hi, ffma(a.lo, b, p.lo));
+}
+// a / b for floats: the quotient's rounding error from the exact remainder
+// a - q b (an fma), divided once more
+MB_HD ff ff_divf(float a, float b) {
+    const float q = fdiv(a, b);
+    return ff_fast_sum(q, fdiv(ffma(-q, b, a), b));
+}
+MB_HD ff ff_div(ff a, ff b) {
+    const float q1 = fdiv(a.hi, b.hi);
+    const ff r = ff_add(a, ff_neg(ff_mulf(b, q1)));
+    return ff_fast_sum(q1, fdiv(r.hi, b.hi));
+}
+
+// Frame of a pixel (as make_frame) with the set-up in float-float: the
+// cancellations in the central moments (variance b2 - b1^2, third and fourth
+// central moments, Schur complement D33) keep ~48 bits, so a generic frame
+// comes out as FP64 would give it, to a few float32 ulp in the outputs.  A
+// pixel whose variance or Schur complement is within 1e-4 of b2 or b4 (near
+// the 1e-6 thresholds of the one- and two-atom branches) is near-singular:
+// it is set up by make_frame in FP64, and *fp64 is set.
+MB_HD Frame make_frame_ff(const float m_in[5], float moment_bias, const float bias_vector[4], bool* fp64) {
+    *fp64 = false;
+    const float m0 = m_in[0];
+    if (!(m0 > 0.0f)) {
+        Frame F;
+        F.kind = kFrameEmpty;
+        F.m0_log2e = 0.0f;
+        F.p0 = F.p1 = F.p2 = F.p3 = 0.0f;
+        return F;
+    }
+    // b_j = (1 - beta) m_j / m0 + beta bv_j = n_j - beta (n_j - bv_j)
+    const float beta = moment_bias;
+    ff b[5];
+    for (int j = 1; j <= 4; ++j) {
+        const ff n = ff_divf(m_in[j], m0);
+        const ff dv = ff_add(n, {-bias_vector[j - 1], 0.0f});
+        b[j] = ff_add(n, ff_neg(ff_mulf(dv, beta)));
+    }
+    const ff mu = b[1];
+    const ff mu2 = ff_mul(mu, mu);
+    const ff var = ff_add(b[2], ff_neg(mu2));
+    // k3 = b3 - 3 mu b2 + 2 mu^3,  k4 = b4 - 4 mu b3 + 6 mu^2 b2 - 3 mu^4
+    const ff mub2 = ff_mul(mu, b[2]);
+    const ff mu3 = ff_mul(mu2, mu);
+    const ff k3 = ff_add(ff_add(b[3], ff_mulf(mub2, -3.0f)), ff_mulf(mu3, 2.0f));
+    const ff k4 = ff_add(ff_add(ff_add(b[4], ff_mulf(ff_mul(mu, b[3]), -4.0f)), ff_mulf(ff_mul(mu2, b[2]), 6.0f)),
+                         ff_mulf(ff_mul(mu2, mu2), -3.0f));
+    const bool near_one = !(var.hi > 1e-4f * b[2].hi);
+    ff D33 = {0.0f, 0.0f};
+    if (!near_one) D33 = ff_add(ff_add(k4, ff_neg(ff_mul(var, var))), ff_neg(ff_div(ff_mul(k3, k3), var)));
+    if (near_one || !(D33.hi > 1e-4f * b[4].hi)) {
+        *fp64 = true;
+        return make_frame(m_in, moment_bias, bias_vector);
+    }
+    Frame F;
+    F.kind = kFrameGeneric;
+    F.m0_log2e = fmul(m0, kLog2e);
+    const float s = fsqrt(var.hi);
+    F.p0 = fdiv(1.0f, s);
+    F.p1 = fdiv(-mu.hi, s);
+    F.p2 = fdiv(k3.hi, fmul(var.hi, s));
+    F.p3 = fdiv(fmul(var.hi, var.hi), D33.hi);
+    return F;
+}
+
 MB_HD float step_weight(float x, float z0, float w0) { return x < z0 ? 1.0f : (x == z0 ? w0 : 0.0f); }
 
 // Alg. 3 for a generic frame (three support points): fraction A(z0) of the

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_frame_fused(const __grid_constant__ Gri
 
         // pass 2 of the same rays
         BlendBody body = blend_body_of(s_tf, g, S, m1, valid);
-        if (valid && body.singular()) atomicAdd(&ctr->singular, 1ull);
+        count_frames(ctr, body, valid);
         __syncwarp();  // the rows' stores before any lane reads them; the window slot is free
         if (base >= 0)
             blend_rows<kSel>(g, cache.vals + base * 32, kmin, kmax, k0, k1, win, body);

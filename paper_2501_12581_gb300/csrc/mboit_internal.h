@@ -45,6 +45,7 @@ struct Counters {
     int32_t max_segments;            // most segments on one pixel
     int32_t pad2;
     unsigned long long cache_rows;   // rows of the frame's sample cache handed out so far
+    unsigned long long fp64_pixels;  // pixels whose reconstruction frame was set up in FP64
 };
 
 struct PieceBox {

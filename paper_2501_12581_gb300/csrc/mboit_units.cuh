@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 2>::value : 2) k_p
         const bool valid = px < S.v.width && py < S.v.height;
         const int pix = valid ? py * S.v.width + px : 0;
         auto body = make_blend_body<MS>(s_tf, g, S, moments, S.moment_off, pix, valid);
-        if (valid && body.singular()) atomicAdd(&ctr->singular, 1ull);
+        count_frames(ctr, body, valid);
         float o[3], d[3];
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);

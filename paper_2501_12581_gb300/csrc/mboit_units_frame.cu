@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256, FrameMinBlocks<V>::value) k_frame_unit(
 
         // pass 2 of the same rays
         BlendBody body = blend_body_of(s_tf, g, S, m1, valid);
-        if (valid && body.singular()) atomicAdd(&ctr->singular, 1ull);
+        count_frames(ctr, body, valid);
         __syncwarp();  // the rows' stores before any lane reads them
         if (base >= 0) {
             if (tagged)
