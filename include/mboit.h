@@ -332,8 +332,27 @@ MBOIT_API mboit_status mboit_render_frame_host(mboit_volume v, const float* fiel
                                      float* rgba_host, void* stream);
 
 /* Waits for `stream` and reports kernel-side errors recorded by this
- * volume's launches (MBOIT_ERR_TIMEOUT / MBOIT_ERR_DEVICE_ASSERT). */
+ * volume's launches since the last call: MBOIT_ERR_DEVICE_ASSERT when a
+ * table check found an entry out of range (an octree finest-brick map entry
+ * that is no leaf id, a mesh face neighbour or bin-list entry that is no tet
+ * id, a mesh bin range outside the bin list).  Every render of an octree or
+ * mesh first runs these checks over the whole tables on its stream (a few
+ * microseconds to tens of microseconds); when one fails, the passes launched
+ * after it return at entry, so no out-of-range index is ever used and the
+ * images of that render are not valid.  The error word is cleared when
+ * reported.  (The kernels have no waits, so MBOIT_ERR_TIMEOUT is not
+ * produced.)  The paper has no counterpart. */
 MBOIT_API mboit_status mboit_synchronize(mboit_volume v, void* stream);
+
+/* Test hook of the failure detection above; the paper has no counterpart.
+ * Overwrites a table the library owns, after the volume was validated:
+ * what = 1 (octree) sets every finest-brick map entry to a value that is no
+ * leaf id; what = 2 (mesh) sets every tet's neighbour
+ * across face 0 to a value that is no tet id.  The volume stays corrupt
+ * (destroy it afterwards); renders then report MBOIT_ERR_DEVICE_ASSERT from
+ * mboit_synchronize.  MBOIT_ERR_INVALID_ARG for another kind or `what`.
+ * Synchronous. */
+MBOIT_API mboit_status mboit_debug_corrupt(mboit_volume v, int32_t what);
 
 /* Counters of the last passes (synchronises the stream of the last render). */
 MBOIT_API mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out);

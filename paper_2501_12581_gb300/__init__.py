@@ -39,7 +39,7 @@ EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume
             "mboit_render_frame", "mboit_render_frame_host", "mboit_synchronize", "mboit_get_stats",
             "mboit_render_moments_noalloc", "mboit_set_tuning", "mboit_set_packet", "mboit_set_frame_launches",
             "mboit_autotune",
-            "mboit_render_sortlast", "mboit_split_cells"]
+            "mboit_render_sortlast", "mboit_split_cells", "mboit_debug_corrupt"]
 MBOIT_NUM_TUNINGS = 5
 
 
@@ -108,6 +108,7 @@ def load_library(path=LIB_PATH):
         "mboit_autotune": (ctypes.c_int, [P, P, I32, P, P, P, P]),
         "mboit_render_sortlast": (ctypes.c_int, [P, P, I32, P, P, P]),
         "mboit_split_cells": (ctypes.c_int, [P, I64, P, P, I64, I32, P, P, P, I64, P]),
+        "mboit_debug_corrupt": (ctypes.c_int, [P, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -322,6 +323,13 @@ def mboit_render_moments_noalloc(desc, views, moments, brick_selected=None, stre
             raise ValueError(f"brick_selected has {sel.size} entries; the grid has {nbricks} bricks")
     _check(load_library().mboit_render_moments_noalloc(ctypes.byref(desc), _ptr(sel), arr, n, _ptr(moments),
                                                        _stream(stream)))
+
+
+def mboit_debug_corrupt(handle, what):
+    """Test hook of the failure detection (see include/mboit.h): overwrites a
+    library-owned table of the volume (1: an octree map entry, 2: mesh face
+    neighbours) so that later renders report MBOIT_ERR_DEVICE_ASSERT."""
+    _check(load_library().mboit_debug_corrupt(handle, int(what)))
 
 
 # ---------------------------------------------------------------------------

@@ -506,8 +506,18 @@ mboit_status prepare_tets(const mboit_volume_desc* d, TetHost& h) {
 
 // The batched (fused, persistent) passes of the volume's kind.  `cache`:
 // mesh sample values shared by the two passes of one frame.
+// Checks the octree's or mesh's index tables on stream s before passes that
+// read them (grids have none).
+cudaError_t check_tables(mboit_volume v, cudaStream_t s) {
+    if (v->kind == MBOIT_AMR) return mb::launch_check_tables(v->amr, s);
+    if (v->kind == MBOIT_TET) return mb::launch_check_tables(v->tet, s);
+    return cudaSuccess;
+}
+
 cudaError_t pass1_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, void* moments, cudaStream_t s,
                           mb::TileCache tc = mb::TileCache{}) {
+    const cudaError_t e = check_tables(v, s);
+    if (e != cudaSuccess) return e;
     if (v->kind == MBOIT_AMR) return mb::launch_pass1_amr(v->amr, v->d_tf, mask, vt, moments, v->d_ctr, s, tc);
     if (v->kind == MBOIT_TET) return mb::launch_pass1_tet(v->tet, v->d_tf, mask, vt, moments, v->d_ctr, s, tc);
     return mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1, tc);
@@ -515,6 +525,8 @@ cudaError_t pass1_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTab
 
 cudaError_t pass2_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, const void* moments,
                           float* color, int32_t mode, cudaStream_t s, mb::TileCache tc = mb::TileCache{}) {
+    const cudaError_t e = check_tables(v, s);
+    if (e != cudaSuccess) return e;
     if (v->kind == MBOIT_AMR)
         return mb::launch_pass2_amr(v->amr, v->d_tf, mask, vt, moments, color, mode, v->d_ctr, s, tc);
     if (v->kind == MBOIT_TET)
@@ -525,6 +537,8 @@ cudaError_t pass2_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTab
 // The one-launch frame of the volume's kind (four power moments).
 cudaError_t frame_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, void* moments, float* color,
                           cudaStream_t s, int cfg, mb::TileCache tc) {
+    const cudaError_t e = check_tables(v, s);
+    if (e != cudaSuccess) return e;
     if (v->kind == MBOIT_AMR)
         return mb::launch_frame_amr(v->amr, v->d_tf, mask, vt, moments, color, mb::kColorResolved, v->d_ctr, s, tc);
     if (v->kind == MBOIT_TET)
@@ -857,6 +871,8 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
         v->amr.nv = (1 << d->brick_log2) + 1;
         v->amr.max_level = d->max_level;
         v->amr.complete = std::find(fmap.begin(), fmap.end(), -1) == fmap.end() ? 1 : 0;
+        v->amr.n_leaves = d->n_leaves;
+        v->amr.err = &v->d_ctr->error;
     }
     if (e == cudaSuccess && is_tet) {
         auto up = [&](auto*& dst, const auto& src) {
@@ -877,6 +893,9 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
         m.corners = v->d_tcorners;
         m.nbrs = v->d_tnbrs;
         m.narrow = th.narrow ? 1 : 0;
+        m.n_tets = (int32_t)d->n_tets;
+        m.n_bin_tets = (int32_t)th.bin_tets.size();
+        m.err = &v->d_ctr->error;
         m.bin_start = v->d_bin_start;
         m.bin_tets = v->d_bin_tets;
         for (int c = 0; c < 3; ++c) m.bdim[c] = th.bdim[c];
@@ -1050,6 +1069,7 @@ mboit_status mboit_render_moments(mboit_volume v, const mboit_view* views, int32
         MB_CUDA(pass1_batched(v, mask, vt, moments, s));
     } else {
         const int32_t slots = (int32_t)list.size();
+        MB_CUDA(check_tables(v, s));
         for (int32_t j = 0; j < slots; ++j) {
             const mb::PieceBox& box = v->boxes[list[j]];
             if (v->kind == MBOIT_AMR)
@@ -1084,6 +1104,7 @@ mboit_status mboit_reconstruct_blend(mboit_volume v, const mboit_view* views, in
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->fp64_pixels, 0, sizeof(unsigned long long), s));
     if (mode == MBOIT_COLOR_PER_PIECE) {
         const int32_t slots = (int32_t)list.size();
+        MB_CUDA(check_tables(v, s));
         for (int32_t j = 0; j < slots; ++j) {
             const mb::PieceBox& box = v->boxes[list[j]];
             if (v->kind == MBOIT_AMR)
@@ -1228,8 +1249,41 @@ mboit_status mboit_synchronize(mboit_volume v, void* stream) {
     MB_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
     int32_t err = 0;
     MB_CUDA(cudaMemcpy(&err, &v->d_ctr->error, sizeof err, cudaMemcpyDeviceToHost));
-    if (err == 1) return fail(MBOIT_ERR_TIMEOUT, "a kernel gave up waiting");
-    if (err != 0) return fail(MBOIT_ERR_DEVICE_ASSERT, "a kernel-side check failed (code " + std::to_string(err) + ")");
+    if (err == 0) return MBOIT_OK;
+    MB_CUDA(cudaMemset(&v->d_ctr->error, 0, sizeof err));   // reported once
+    std::string what;
+    if (err & mb::kErrLeafId) what += " an octree finest-brick map entry is not a leaf id;";
+    if (err & mb::kErrTetId) what += " a mesh face-neighbour or bin-list entry is not a tet id;";
+    if (err & mb::kErrBinRange) what += " a mesh bin's range leaves the bin list;";
+    return fail(MBOIT_ERR_DEVICE_ASSERT, "kernel-side checks failed (code " + std::to_string(err) + "):" + what +
+                                             " the accesses were skipped; the frame's images are not valid");
+}
+
+mboit_status mboit_debug_corrupt(mboit_volume v, int32_t what) {
+    g_err.clear();
+    mboit_status st = check_volume(v);
+    if (st != MBOIT_OK) return st;
+    std::lock_guard<std::mutex> lk(v->mu);
+    DeviceGuard dg(v->device);
+    if (what == 1) {
+        if (v->kind != MBOIT_AMR) return fail(MBOIT_ERR_INVALID_ARG, "what = 1 needs an octree volume");
+        // every finest brick maps to no leaf (a single entry could go unread:
+        // a lane inside a leaf's box does not consult the map)
+        const int64_t f = v->amr.fdim;
+        std::vector<int32_t> bad((size_t)(f * f * f), v->amr.n_leaves + 7);
+        MB_CUDA(cudaMemcpy(v->d_fmap, bad.data(), bad.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    } else if (what == 2) {
+        if (v->kind != MBOIT_TET) return fail(MBOIT_ERR_INVALID_ARG, "what = 2 needs a mesh volume");
+        // every tet's neighbour across face 0 becomes no tet
+        std::vector<int4> nb((size_t)v->tet.n_tets);
+        MB_CUDA(cudaMemcpy(nb.data(), v->d_tnbrs, nb.size() * sizeof(int4), cudaMemcpyDeviceToHost));
+        for (auto& n : nb)
+            if (n.x >= 0) n.x = v->tet.n_tets + 7;
+        MB_CUDA(cudaMemcpy(v->d_tnbrs, nb.data(), nb.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    } else {
+        return fail(MBOIT_ERR_INVALID_ARG, "what must be 1 (octree map) or 2 (mesh neighbours)");
+    }
+    drop_graphs(v);
     return MBOIT_OK;
 }
 
@@ -1284,6 +1338,7 @@ mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int3
     MB_CUDA(ensure_capacity(v->sl_bsum, v->cap_bsum, nb));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->segments, 0, sizeof(unsigned long long) + sizeof(int32_t), s));
+    MB_CUDA(check_tables(v, s));
     auto march = [&](bool fill, int32_t p) {
         const int64_t* st = fill ? v->sl_starts : nullptr;
         int32_t* key = fill ? v->sl_key : nullptr;

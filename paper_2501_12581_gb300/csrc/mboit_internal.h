@@ -34,10 +34,16 @@ struct ViewTable {
     ViewSlot s[kMaxViews];
 };
 
+// Bits of Counters::error: a kernel found a table entry out of range,
+// skipped the access it would have made and went on with a safe substitute.
+constexpr int32_t kErrLeafId = 0x2;   // an octree finest-brick map entry is not a leaf id (nor -1)
+constexpr int32_t kErrTetId = 0x4;    // a mesh face neighbour or bin-list entry is not a tet id
+constexpr int32_t kErrBinRange = 0x8; // a mesh bin's range of the bin list leaves the list
+
 // Device counters owned by a volume.
 struct Counters {
     int32_t tile_next[4];            // work-queue heads, one per concurrent pass
-    int32_t error;                   // nonzero: a kernel-side check failed
+    int32_t error;                   // kErr* bits of the kernel-side checks that failed since the last read
     int32_t pad;
     unsigned long long samples[2];   // pass 1, pass 2
     unsigned long long singular;     // pixels on a 1-/2-atom branch
@@ -65,6 +71,9 @@ struct AmrD {
     const int32_t* fmap;    // [fdim^3] finest brick (2^brick_log2 cells) -> leaf, -1 none
     int32_t fdim, nv, max_level;
     int32_t complete;       // 1: every finest brick has a leaf (no holes)
+    int32_t n_leaves;       // leaf ids are 0 .. n_leaves - 1 (checked where the map is read)
+    int32_t pad;
+    int32_t* err;           // the volume's Counters::error
 };
 
 // Tetrahedral mesh as the kernels see it.  `g` carries the box
@@ -84,7 +93,10 @@ struct TetD {
     float qscale;              // 2^quantum_log2
     int32_t max_walk;          // walk steps before a bin search takes over
     int32_t narrow;            // 1: every tet spans < 2^15 quanta, so face normals fit in 32 bits
+    int32_t n_tets;            // tet ids are 0 .. n_tets - 1 (checked before every tet load)
+    int32_t n_bin_tets;        // entries of bin_tets (bin ranges are checked against it)
     int32_t pad;
+    int32_t* err;              // the volume's Counters::error
 };
 
 // The kernels' view of a mesh, with the normal width as a type.
@@ -193,6 +205,14 @@ cudaError_t launch_sortlast_march(bool fill, const TetD& m, const float4* tf, co
 // Writes vertex values (values[vertex id]) into the .w words of the tets'
 // corner records.
 cudaError_t launch_tet_values(int4* corners, const int4* cells, int64_t n_tets, const float* values, cudaStream_t s);
+
+// Table checks before a render's passes (failure detection): octree
+// finest-brick map entries are leaf ids or -1; mesh face neighbours are tet
+// ids or -1, bin offsets are ordered and inside the bin list, bin-list entries
+// are tet ids.  A failure sets kErr* bits in the volume's error word, and the
+// passes launched after it on the stream return at entry.
+cudaError_t launch_check_tables(const AmrD& a, cudaStream_t s);
+cudaError_t launch_check_tables(const TetD& m, cudaStream_t s);
 
 // Image-space reductions.
 cudaError_t launch_moments_sum(const GridD& g, const ViewTable& vt, int32_t n_inputs, const void* in, void* out,

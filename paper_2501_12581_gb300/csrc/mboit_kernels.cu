@@ -269,6 +269,66 @@ __global__ void __launch_bounds__(256) k_tile_rows(const __grid_constant__ GridD
     if (lane == 0 && mine) atomicAdd(rows, mine);
 }
 
+// ------------------------------------------------------------------------
+// table checks of octrees and meshes (failure detection): every entry of a
+// library-owned index table is tested against its range before a render's
+// passes run; a bad one sets a kErr* bit of the volume's error word, and the
+// passes then return at entry (tables_bad), so no out-of-range index is used.
+
+// Ors `code` into *err from one lane of each warp that saw a bad entry.
+__device__ __forceinline__ void flag_warp(bool bad, int32_t* err, int32_t code) {
+    const unsigned m = __ballot_sync(0xffffffffu, bad);
+    if (m && (threadIdx.x & 31) == 0) atomicOr(err, code);
+}
+
+// Every ids[i] in [lo, hi].
+__global__ void __launch_bounds__(256) k_check_ids(const int32_t* __restrict__ ids, int64_t n, int32_t lo, int32_t hi,
+                                                   int32_t* err, int32_t code) {
+    bool bad = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i - threadIdx.x % 32 < n; i += stride) {
+        if (i < n) {
+            const int32_t v = __ldg(ids + i);
+            bad |= v < lo || v > hi;
+        }
+    }
+    flag_warp(bad, err, code);
+}
+
+// Every face neighbour -1 (boundary) or a tet id.
+__global__ void __launch_bounds__(256) k_check_nbrs(const int4* __restrict__ nb, int64_t n, int32_t n_tets,
+                                                    int32_t* err) {
+    bool bad = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i - threadIdx.x % 32 < n; i += stride) {
+        if (i < n) {
+            const int4 v = __ldg(nb + i);
+            bad |= v.x < -1 || v.x >= n_tets || v.y < -1 || v.y >= n_tets || v.z < -1 || v.z >= n_tets || v.w < -1 ||
+                   v.w >= n_tets;
+        }
+    }
+    flag_warp(bad, err, kErrTetId);
+}
+
+// Bin offsets non-decreasing from >= 0 to <= the list's length.
+__global__ void __launch_bounds__(256) k_check_bins(const int32_t* __restrict__ start, int64_t nbins,
+                                                    int32_t n_list, int32_t* err) {
+    bool bad = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i - threadIdx.x % 32 < nbins; i += stride) {
+        if (i < nbins) {
+            const int32_t a = __ldg(start + i), b = __ldg(start + i + 1);
+            bad |= a < 0 || b < a || b > n_list;
+        }
+    }
+    flag_warp(bad, err, kErrBinRange);
+}
+
+int check_blocks(int64_t n) {
+    const int64_t b = (n + 255) / 256;
+    return (int)(b < 1216 ? (b > 0 ? b : 1) : 1216);  // up to 8 blocks per SM, grid-stride beyond
+}
+
 }  // namespace
 
 // Resident CTAs per SM x SMs for a persistent kernel, cached per function.
@@ -377,6 +437,20 @@ cudaError_t launch_sortlast_blend(const int64_t* base, int32_t* seg_key, float4*
                                   Counters* ctr, cudaStream_t s) {
     const int grid = (int)((total_px + 127) / 128 < 16384 ? (total_px + 127) / 128 : 16384);
     k_sortlast_blend<<<grid, 128, 0, s>>>(base, seg_key, seg_col, rgba, total_px, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_tables(const AmrD& a, cudaStream_t s) {
+    const int64_t n = (int64_t)a.fdim * a.fdim * a.fdim;
+    k_check_ids<<<check_blocks(n), 256, 0, s>>>(a.fmap, n, -1, a.n_leaves - 1, a.err, kErrLeafId);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_tables(const TetD& m, cudaStream_t s) {
+    const int64_t nbins = (int64_t)m.bdim[0] * m.bdim[1] * m.bdim[2];
+    k_check_nbrs<<<check_blocks(m.n_tets), 256, 0, s>>>(m.nbrs, m.n_tets, m.n_tets, m.err);
+    k_check_bins<<<check_blocks(nbins), 256, 0, s>>>(m.bin_start, nbins, m.n_bin_tets, m.err);
+    k_check_ids<<<check_blocks(m.n_bin_tets), 256, 0, s>>>(m.bin_tets, m.n_bin_tets, 0, m.n_tets - 1, m.err, kErrTetId);
     return cudaGetLastError();
 }
 

@@ -46,11 +46,22 @@ __device__ __forceinline__ void unit_box(const GridD& g, const float p[3], int, 
     for (int c = 0; c < 3; ++c) lo[c] = floorf(p[c] / size) * size;
 }
 
+// The leaf of an in-domain point from the finest-brick map (-1: a hole).
+// Every entry was checked to be a leaf id or -1 before the kernel ran (see
+// tables_bad).
 __device__ __forceinline__ int unit_of(const AmrD& a, const float p[3]) {
     const int bl = a.g.brick_log2;
     const int fx = (int)p[0] >> bl, fy = (int)p[1] >> bl, fz = (int)p[2] >> bl;
     return __ldg(a.fmap + ((size_t)fz * a.fdim + fy) * (size_t)a.fdim + fx);
 }
+
+// True when the table checks of this render (k_check_* in mboit_kernels.cu,
+// launched before the passes on the same stream) found an entry out of range
+// in the volume's tables; every kernel that reads those tables then returns
+// at once, so no out-of-range index is ever used.  Grids have no such tables.
+__device__ __forceinline__ bool tables_bad(const GridD&) { return false; }
+__device__ __forceinline__ bool tables_bad(const AmrD& a) { return *(volatile const int32_t*)a.err != 0; }
+__device__ __forceinline__ bool tables_bad(const TetD& m) { return *(volatile const int32_t*)m.err != 0; }
 
 // Trilinear value in leaf `leaf` with origin lo (finest cells) and inverse
 // cell size inv_h.  Local coordinates (p - origin) / h are exact in float32
@@ -213,6 +224,7 @@ __global__ void __launch_bounds__(128) k_pass1_piece(const __grid_constant__ V v
                                                      const __grid_constant__ PieceBox box,
                                                      const __grid_constant__ ViewTable vt, int slot, int n_slots,
                                                      char* __restrict__ moments, Counters* __restrict__ ctr) {
+    if (tables_bad(vol)) return;
     const GridD& g = common(vol);
     __shared__ float2 s_sig[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
@@ -258,6 +270,7 @@ __global__ void __launch_bounds__(128) k_pass2_piece(const __grid_constant__ V v
                                                      const __grid_constant__ ViewTable vt, int slot, int n_slots,
                                                      const char* __restrict__ moments, float* __restrict__ color,
                                                      Counters* __restrict__ ctr) {
+    if (tables_bad(vol)) return;
     const GridD& g = common(vol);
     __shared__ float4 s_tf[512];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
@@ -362,6 +375,12 @@ __device__ __forceinline__ int tet_exit_face(const int4 v[4], const int q[3], lo
 
 __device__ __forceinline__ int pick(const int4 a, int i) { return i == 0 ? a.x : i == 1 ? a.y : i == 2 ? a.z : a.w; }
 
+// The range [j0, j1) of bin b's entries in the bin list.
+__device__ __forceinline__ void bin_range(const TetD& m, int b, int& j0, int& j1) {
+    j0 = __ldg(m.bin_start + b);
+    j1 = __ldg(m.bin_start + b + 1);
+}
+
 __device__ __forceinline__ int bin_of(const TetD& m, const int q[3]) {
     int b[3];
 #pragma unroll
@@ -391,9 +410,9 @@ __device__ __forceinline__ void load_tet(const TetD& m, int T, TetWalk& w) {
 // success w holds the owner and D its volumes, else w is unchanged.
 template <bool kNarrow>
 __device__ __forceinline__ bool tet_search(const TetD& m, TetWalk& w, const int q[3], long long D[4]) {
-    const int b = bin_of(m, q);
-    const int j1 = __ldg(m.bin_start + b + 1);
-    for (int j = __ldg(m.bin_start + b); j < j1; ++j) {
+    int j0, j1;
+    bin_range(m, bin_of(m, q), j0, j1);
+    for (int j = j0; j < j1; ++j) {
         TetWalk u;
         load_tet(m, __ldg(m.bin_tets + j), u);
         if (tet_exit_face<kNarrow>(u.v, q, D, 0, -1) < 0) {
@@ -415,8 +434,9 @@ template <bool kNarrow>
 __device__ __forceinline__ bool tet_walk(const TetD& m, TetWalk& w, const int q[3], long long D[4]) {
     if (w.T < 0) {
         const int b = bin_of(m, q);
-        const int j0 = __ldg(m.bin_start + b);
-        if (j0 == __ldg(m.bin_start + b + 1)) return false;  // no tet comes near q
+        int j0, j1;
+        bin_range(m, b, j0, j1);
+        if (j0 == j1) return false;  // no tet comes near q
         load_tet(m, __ldg(m.bin_tets + j0), w);
     }
     int skip = -1;
@@ -503,8 +523,9 @@ __device__ __forceinline__ void march_unit(const TetT<kNarrow>& m, const uint8_t
     TetWalk w;
     {
         const int b = bin_of(m, q);
-        const int j0 = __ldg(m.bin_start + b);
-        if (j0 < __ldg(m.bin_start + b + 1)) load_tet(m, __ldg(m.bin_tets + j0), w);
+        int j0, j1;
+        bin_range(m, b, j0, j1);
+        if (j0 < j1) load_tet(m, __ldg(m.bin_tets + j0), w);
     }
     long long D[4];
     int skip = -1, steps = 0;
@@ -685,6 +706,7 @@ __global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 1>::value : 2) k_p
                                                     const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                     char* __restrict__ moments, Counters* __restrict__ ctr,
                                                     const TileCache cache) {
+    if (tables_bad(a)) return;
     __shared__ float2 s_sig[256];
     __shared__ float4 s_z[kFusedWarps][kDepthRows];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
@@ -725,6 +747,7 @@ __global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 2>::value : 2) k_p
                                                     const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                     const char* __restrict__ moments, float* __restrict__ color, int mode,
                                                     Counters* __restrict__ ctr, const TileCache cache) {
+    if (tables_bad(a)) return;
     __shared__ float4 s_tf[512];
     __shared__ __align__(16) float s_rows[kCache ? kFusedWarps : 1][kCache ? kRowBuf : 4];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
@@ -787,6 +810,7 @@ __global__ void __launch_bounds__(128) k_sortlast_piece(const __grid_constant__ 
                                                         const __grid_constant__ ViewTable vt, int slot, int n_slots,
                                                         int32_t* __restrict__ counts, const int64_t* __restrict__ starts,
                                                         int32_t* __restrict__ seg_key, float4* __restrict__ seg_col) {
+    const bool bad = tables_bad(vol);   // bad tables: count no segments, fill none
     const GridD& g = common(vol);
     __shared__ float4 s_tf[256];
     if (kFill) {
@@ -809,7 +833,7 @@ __global__ void __launch_bounds__(128) k_sortlast_piece(const __grid_constant__ 
     make_ray(S.v, px, py, o, d);
     int k0, k1;
     int nseg = 0;
-    if (lattice_range(o, d, box.lo, box.hi, g.step, &k0, &k1)) {
+    if (!bad && lattice_range(o, d, box.lo, box.hi, g.step, &k0, &k1)) {
         int64_t out = kFill ? starts[cidx] : 0;
         int prev = -2, key = 0;
         float4 cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);

@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(256, FrameMinBlocks<V>::value) k_frame_unit(
     const __grid_constant__ V a, const float4* __restrict__ tf, const uint8_t* __restrict__ sel,
     const __grid_constant__ ViewTable vt, char* __restrict__ moments, float* __restrict__ color, int mode,
     Counters* __restrict__ ctr, const TileCache cache) {
+    if (tables_bad(a)) return;
     __shared__ float2 s_sig[256];
     __shared__ float4 s_tf[512];
     __shared__ __align__(16) float s_rows[kFusedWarps][kRowBuf];
