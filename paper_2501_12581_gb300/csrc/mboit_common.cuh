@@ -159,7 +159,8 @@ __device__ __forceinline__ float4 depth_powers(float t, float wa, float wb) {
 struct MomentBody {
     const float2* s_sig;  // (sigma*step of entry i, of entry i+1 minus entry i)
     float tf_scale, tf_bias, amax, wa, wb;
-    float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f, m4 = 0.0f;
+    float m0 = 0.0f;
+    float2 m12 = make_float2(0.0f, 0.0f), m34 = make_float2(0.0f, 0.0f);   // (b1, b2), (b3, b4)
     unsigned n = 0;
     // b_j += a z^j from the sample's table coordinate xt (tf_x) and the depth
     // powers zp of its lattice point; entry 255 has a zero delta, so xt = 255
@@ -170,17 +171,18 @@ struct MomentBody {
         const float2 s = s_sig[i];
         const float a = fmin_(ffma(f, s.y, s.x) * ws, amax);
         m0 += a;
-        m1 = ffma(a, zp.x, m1);
-        m2 = ffma(a, zp.y, m2);
-        m3 = ffma(a, zp.z, m3);
-        m4 = ffma(a, zp.w, m4);
+        // b_j += a z^j for j = 1, 2 and j = 3, 4 as two packed FP32x2 fmas
+        // (each half rounded as a scalar fma)
+        const float2 aa = make_float2(a, a);
+        m12 = __ffma2_rn(aa, make_float2(zp.x, zp.y), m12);
+        m34 = __ffma2_rn(aa, make_float2(zp.z, zp.w), m34);
         ++n;
     }
     __device__ __forceinline__ void operator()(float t, float xt, float ws = 1.0f) {
         add(xt, ws, depth_powers(t, wa, wb));
     }
     __device__ __forceinline__ void store(const GridD&, char* base, const ViewSlot& S, int64_t off, int pix) {
-        store_moments(base, S, off, pix, m0, m1, m2, m3, m4);
+        store_moments(base, S, off, pix, m0, m12.x, m12.y, m34.x, m34.y);
     }
 };
 
@@ -235,37 +237,44 @@ struct BlendBody {
     // coordinate is replaced by 0 (no NaN enters) and its weight by 0, and
     // fma(0, c, C) = C.
     __device__ __forceinline__ float depth(float t) const { return warp_depth(t, wa, wb); }
-    __device__ __forceinline__ void pair_generic(float2 z, float xa, float xb, bool oka, bool okb) {
+    __device__ __forceinline__ void pair_generic(float2 z, float xa, float xb, bool oka, bool okb, unsigned act) {
         xa = oka ? xa : 0.0f;
         xb = okb ? xb : 0.0f;
         const int ia = (int)xa, ib = (int)xb;
         const float fa = xa - (float)ia, fb = xb - (float)ib;
         const float4 ea = s_tf[2 * ia], da = s_tf[2 * ia + 1], eb = s_tf[2 * ib], db = s_tf[2 * ib + 1];
-        const float2 a = make_float2(fmin_(ffma(fa, da.w, ea.w), amax), fmin_(ffma(fb, db.w, eb.w), amax));
-        // opacity 1 - e^-a: the series and the direct form for both, then the
-        // one one_minus_exp_neg takes
+        // the table lerps as pairs: (r, g) and (b, absorbance) of each point
+        const float2 rga = __ffma2_rn(make_float2(fa, fa), make_float2(da.x, da.y), make_float2(ea.x, ea.y));
+        const float2 bwa = __ffma2_rn(make_float2(fa, fa), make_float2(da.z, da.w), make_float2(ea.z, ea.w));
+        const float2 rgb = __ffma2_rn(make_float2(fb, fb), make_float2(db.x, db.y), make_float2(eb.x, eb.y));
+        const float2 bwb = __ffma2_rn(make_float2(fb, fb), make_float2(db.z, db.w), make_float2(eb.z, eb.w));
+        const float2 a = make_float2(fmin_(bwa.y, amax), fmin_(bwb.y, amax));
+        // opacity 1 - e^-a: the series, and the direct form only when a lane of
+        // the branch has an absorbance at or above 1/4 (one_minus_exp_neg)
         float2 p = __ffma2_rn(a, make_float2(-1.0f / 720.0f, -1.0f / 720.0f), make_float2(1.0f / 120.0f, 1.0f / 120.0f));
         p = __ffma2_rn(a, p, make_float2(-1.0f / 24.0f, -1.0f / 24.0f));
         p = __ffma2_rn(a, p, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
         p = __ffma2_rn(a, p, make_float2(-0.5f, -0.5f));
         p = __ffma2_rn(a, p, make_float2(1.0f, 1.0f));
-        const float2 ser = __fmul2_rn(a, p);
-        const float2 ng = __fmul2_rn(a, make_float2(-kLog2e, -kLog2e));
-        const float2 dir = __ffma2_rn(make_float2(fexp2(ng.x), fexp2(ng.y)), make_float2(-1.0f, -1.0f),
-                                      make_float2(1.0f, 1.0f));
-        const float2 alpha = make_float2(a.x < 0.25f ? ser.x : dir.x, a.y < 0.25f ? ser.y : dir.y);
+        float2 alpha = __fmul2_rn(a, p);
+        if (__any_sync(act, a.x >= 0.25f || a.y >= 0.25f)) {
+            const float2 ng = __fmul2_rn(a, make_float2(-kLog2e, -kLog2e));
+            const float2 dir = __ffma2_rn(make_float2(fexp2(ng.x), fexp2(ng.y)), make_float2(-1.0f, -1.0f),
+                                          make_float2(1.0f, 1.0f));
+            alpha = make_float2(a.x < 0.25f ? alpha.x : dir.x, a.y < 0.25f ? alpha.y : dir.y);
+        }
         const float2 A = bound_generic2(F, z, w0);
         const float2 ex = __fmul2_rn(make_float2(-F.m0_log2e, -F.m0_log2e), A);
-        float2 wgt = __fmul2_rn(make_float2(fclamp(fexp2(ex.x), 0.0f, 1.0f), fclamp(fexp2(ex.y), 0.0f, 1.0f)), alpha);
+        float2 wgt = __fmul2_rn(make_float2(fexp2(ex.x), fexp2(ex.y)), alpha);
         wgt.x = oka ? wgt.x : 0.0f;
         wgt.y = okb ? wgt.y : 0.0f;
-        C.x = ffma(wgt.x, ffma(fa, da.x, ea.x), C.x);
-        C.y = ffma(wgt.x, ffma(fa, da.y, ea.y), C.y);
-        C.z = ffma(wgt.x, ffma(fa, da.z, ea.z), C.z);
+        C.x = ffma(wgt.x, rga.x, C.x);
+        C.y = ffma(wgt.x, rga.y, C.y);
+        C.z = ffma(wgt.x, bwa.x, C.z);
         C.w += wgt.x;
-        C.x = ffma(wgt.y, ffma(fb, db.x, eb.x), C.x);
-        C.y = ffma(wgt.y, ffma(fb, db.y, eb.y), C.y);
-        C.z = ffma(wgt.y, ffma(fb, db.z, eb.z), C.z);
+        C.x = ffma(wgt.y, rgb.x, C.x);
+        C.y = ffma(wgt.y, rgb.y, C.y);
+        C.z = ffma(wgt.y, bwb.x, C.z);
         C.w += wgt.y;
         n += (unsigned)oka + (unsigned)okb;
     }
@@ -277,8 +286,8 @@ struct GenericBlend {
     BlendBody& b;
     __device__ __forceinline__ void operator()(float t, float xt, float ws = 1.0f) { b.sample<true>(t, xt, ws); }
     __device__ __forceinline__ float depth(float t) const { return b.depth(t); }
-    __device__ __forceinline__ void pair(float2 z, float xa, float xb, bool oka, bool okb) {
-        b.pair_generic(z, xa, xb, oka, okb);
+    __device__ __forceinline__ void pair(float2 z, float xa, float xb, bool oka, bool okb, unsigned act) {
+        b.pair_generic(z, xa, xb, oka, okb, act);
     }
 };
 // Bodies that take two lattice points at once (pair(...), equal to two calls).
@@ -521,8 +530,8 @@ __device__ __forceinline__ BlendBody blend_body_of(const float4* s_tf, const Gri
     b.wa = S.v.warp_a;
     b.wb = S.v.warp_b;
     b.w0 = g.overestimation;
-    const float m[5] = {valid ? mb.m0 : 0.0f, valid ? mb.m1 : 0.0f, valid ? mb.m2 : 0.0f, valid ? mb.m3 : 0.0f,
-                        valid ? mb.m4 : 0.0f};
+    const float m[5] = {valid ? mb.m0 : 0.0f, valid ? mb.m12.x : 0.0f, valid ? mb.m12.y : 0.0f,
+                        valid ? mb.m34.x : 0.0f, valid ? mb.m34.y : 0.0f};
     b.F = make_frame_ff(m, g.moment_bias, g.bias_vector, &b.fp64);
     b.b0 = m[0];
     return b;
@@ -705,7 +714,7 @@ __device__ __forceinline__ void march_rows(const GridD& g, const float* __restri
                     const float va = src[i * 32], vb = src[(i + 1) * 32];
                     const bool oka = !kSel || va == va, okb = !kSel || vb == vb;
                     if (kSel && !__any_sync(act, oka || okb)) continue;
-                    body.pair(zr[i / 2], va, vb, oka, okb);
+                    body.pair(zr[i / 2], va, vb, oka, okb, act);
                 }
                 t += kRowChunk * g.step;
             } else {

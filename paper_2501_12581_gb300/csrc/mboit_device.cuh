@@ -463,13 +463,19 @@ __device__ __forceinline__ float2 bound_generic2(const Frame& F, float2 z0, floa
 }
 #endif
 
+// T = exp(-b0 A(z0)), A from the frame's representation; A lies in [0, 1]
+// for the one- and two-atom frames, and in [0, 1] up to rounding for a
+// generic frame (below), so T needs no clamp.
 MB_HD float transmittance(const Frame& F, float z0, float w0) {
     float A = bound_fraction(F, z0, w0);
-    return fclamp(fexp2(-F.m0_log2e * A), 0.0f, 1.0f);
+    return fexp2(-F.m0_log2e * A);
 }
+// For a generic frame A >= 0 up to rounding (w0 rho0 >= 0, 1 - (1 - w0) rho0 >=
+// w0 since rho0 = 1 / K(x0, x0) <= 1, rho1 clamped to [0, 1 - rho0]), so T
+// exceeds 1 by at most a rounding error and needs no clamp.
 MB_HD float transmittance_generic(const Frame& F, float z0, float w0) {
     float A = bound_generic(F, z0, w0);
-    return fclamp(fexp2(-F.m0_log2e * A), 0.0f, 1.0f);
+    return fexp2(-F.m0_log2e * A);
 }
 
 }  // namespace mb
