@@ -98,15 +98,10 @@ __device__ __forceinline__ bool window_box(const GridD& g, const float o[3], con
 // in-domain points; k0 > k1: none), calling body(t, xt) with the table
 // coordinate xt of every owned sample in depth order (and storing xt, NaN for
 // a point not sampled).  All 32 lanes of the warp call it together.
-// With MomentBody and `zrows` (2 S float4 of this warp's shared memory), the
-// depth powers of a window's rows are computed once for the warp (lanes
-// 0 .. rows-1) and every lane reads the rows it samples, as in the octree's
-// pass 1; the results are the same bits as the body computing them per sample.
 template <class Cfg, bool kSel, class Body, class Store = NoStore>
 __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __restrict__ sel, float* __restrict__ win,
                                             const float o[3], const float d[3], int k0, int k1, Body& body,
-                                            Store store = Store{}, float4* zrows = nullptr) {
-    constexpr bool kMom = std::is_same<Body, MomentBody>::value;
+                                            Store store = Store{}) {
     const unsigned full = 0xffffffffu;
     const int kmin = __reduce_min_sync(full, k0);
     const int kmax = __reduce_max_sync(full, k1);
@@ -121,14 +116,6 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
             fits = window_box<Cfg>(g, o, d, max(kb, k0), min(ke, k1), LO);
         }
         const int ka = max(kb, k0), kz = min(ke, k1);
-        if constexpr (kMom) {
-            if (zrows) {
-                __syncwarp();   // every lane is done with the previous window's rows
-                const int lane = threadIdx.x & 31;
-                if (lane <= ke - kb) zrows[lane] = depth_powers(lattice_t(kb + lane, g.step), body.wa, body.wb);
-                __syncwarp();
-            }
-        }
         if (fits) {
             __syncwarp();
             const int lane = threadIdx.x & 31;
@@ -172,9 +159,9 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
             const float* wbase = win - LO[2] * Cfg::Plane - LO[1] * Cfg::Pitch - LO[0];
             // t_{k+1} = t_k + step exactly (odd multiples of step/2 below 2^24), so the
             // loop runs on t itself
+            const float tz = lattice_t(kz, g.step);
             store.seek(ka);
-            float t = lattice_t(ka, g.step);
-            for (int k = ka; k <= kz; ++k, t += g.step) {
+            for (float t = lattice_t(ka, g.step); t <= tz; t += g.step) {
                 const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
                 const int ix = (int)p0, iy = (int)p1, iz = (int)p2;
                 if (kSel) {
@@ -191,18 +178,12 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
                                              p2 - (float)iz);
                 const float xt = tf_x(g, val);
                 store.put(xt);
-                if constexpr (kMom) {
-                    if (zrows) {
-                        body.add(xt, 1.0f, zrows[k - kb]);
-                        continue;
-                    }
-                }
                 body(t, xt);
             }
         } else {
+            const float tz = lattice_t(kz, g.step);
             store.seek(ka);
-            float t = lattice_t(ka, g.step);
-            for (int k = ka; k <= kz; ++k, t += g.step) {
+            for (float t = lattice_t(ka, g.step); t <= tz; t += g.step) {
                 float val;
                 if (!field_sample<kSel>(g, sel, t, o, d, val)) {
                     store.put(__int_as_float(0x7fc00000));
@@ -210,12 +191,6 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
                 }
                 const float xt = tf_x(g, val);
                 store.put(xt);
-                if constexpr (kMom) {
-                    if (zrows) {
-                        body.add(xt, 1.0f, zrows[k - kb]);
-                        continue;
-                    }
-                }
                 body(t, xt);
             }
         }
@@ -247,14 +222,12 @@ __global__ void __launch_bounds__(256, MS == 0 ? 5 : 1) k_pass1_fused(const __gr
                                                      const TileCache cache) {
     __shared__ float2 s_sig[256];
     __shared__ __align__(16) float s_win[kFusedWarps][Cfg::Floats];
-    __shared__ float4 s_z[kFusedWarps][2 * Cfg::S];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float s0 = tf[i].w;
         s_sig[i] = make_float2(s0, i < 255 ? tf[i + 1].w - s0 : 0.0f);
     }
     __syncthreads();
     float* win = s_win[threadIdx.x >> 5];
-    float4* zrows = MS == 0 ? s_z[threadIdx.x >> 5] : nullptr;
     int vi, px, py, tile;
     while (next_tile(vt, &ctr->tile_next[0], vi, px, py, tile)) {
         const ViewSlot& S = vt.s[vi];
@@ -265,9 +238,9 @@ __global__ void __launch_bounds__(256, MS == 0 ? 5 : 1) k_pass1_fused(const __gr
         auto body = make_moment_body<MS>(s_sig, g, S.v);
         if constexpr (kCache) {
             RowStore st{tile_rows(cache, ctr, tile, k0, k1)};
-            march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body, st, zrows);
+            march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body, st);
         } else {
-            march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body, NoStore{}, zrows);
+            march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
         }
         if (valid) body.store(g, moments, S, S.moment_off, py * S.v.width + px);
         warp_add_u64(&ctr->samples[0], body.n);

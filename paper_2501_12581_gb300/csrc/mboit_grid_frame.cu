@@ -28,7 +28,6 @@ __global__ void __launch_bounds__(256) k_frame_fused(const __grid_constant__ Gri
     __shared__ float2 s_sig[256];
     __shared__ float4 s_tf[512];
     __shared__ __align__(16) float s_win[kFusedWarps][Cfg::Floats];
-    __shared__ float4 s_z[kFusedWarps][2 * Cfg::S];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float4 e0 = tf[i], e1 = i < 255 ? tf[i + 1] : tf[i];
         s_tf[2 * i] = e0;
@@ -61,7 +60,7 @@ __global__ void __launch_bounds__(256) k_frame_fused(const __grid_constant__ Gri
         // pass 1: moments of every selected piece, summed in registers
         auto m1 = make_moment_body<0>(s_sig, g, S.v);
         RowStore st{base >= 0 ? cache.vals + (base - kmin) * 32 + lane : nullptr};
-        march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, m1, st, s_z[threadIdx.x >> 5]);
+        march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, m1, st);
         if (valid) m1.store(g, moments, S, S.moment_off, pix);
         warp_add_u64(&ctr->samples[0], m1.n);
 
