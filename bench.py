@@ -75,14 +75,25 @@ def _measured_peaks():
 MEASURED = _measured_peaks()
 
 
-def kernel_hash():
-    """Hash of every kernel and device-header source of the library (the host
-    side of the C ABI, mboit_api.cu, is left out)."""
+# device headers every frame kernel includes
+COMMON_SOURCES = ["mboit_common.cuh", "mboit_device.cuh", "mboit_internal.h", "mboit_power.cuh", "mboit_trig.cuh"]
+
+
+def kernel_sources(kernel):
+    """The library sources a frame kernel is compiled from: the octree / mesh
+    kernels (k_*_unit) or the grid kernels (k_*_fused), plus the shared device
+    headers."""
+    fam = "mboit_units" if "unit" in kernel else "mboit_grid"
+    own = sorted(f for f in os.listdir(CSRC) if f.startswith(fam) and f.endswith((".cu", ".cuh")))
+    return own + COMMON_SOURCES
+
+
+def kernel_hash(kernel="k_frame_unit"):
+    """Hash of the sources `kernel` is compiled from."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(CSRC)):
-        if f.endswith((".cu", ".cuh", ".h")) and f != "mboit_api.cu":
-            h.update(f.encode())
-            h.update(open(os.path.join(CSRC, f), "rb").read())
+    for f in kernel_sources(kernel):
+        h.update(f.encode())
+        h.update(open(os.path.join(CSRC, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -92,7 +103,7 @@ def measured_ncu(kernel, workload):
     that kernel and workload or the kernel sources changed since."""
     try:
         kv = dict(tok.split("=", 1) for tok in open(ncu_record_path(kernel, workload)).read().split() if "=" in tok)
-        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("kernel_sha") == kernel_hash():
+        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("kernel_sha") == kernel_hash(kernel):
             return {k: float(v) for k, v in kv.items() if k not in ("kernel", "workload", "kernel_sha", "note")}
     except (OSError, ValueError, KeyError):
         pass
@@ -120,7 +131,7 @@ def write_ncu_record(csv_path, kernel, workload, samples, out_path):
         return v * scale
     dram = num("dram__bytes_read.sum") + num("dram__bytes_write.sum")
     inst = num("smsp__inst_executed.sum")
-    rec = {"kernel": kernel, "workload": workload, "kernel_sha": kernel_hash(),
+    rec = {"kernel": kernel, "workload": workload, "kernel_sha": kernel_hash(kernel),
            "dram_bytes_per_launch": int(dram), "samples_per_launch": int(samples),
            "launch_ms": num("gpu__time_duration.sum") * ({"usecond": 1e-3, "msecond": 1, "nsecond": 1e-6}
                                                            .get(u.get("gpu__time_duration.sum"), 1)),
