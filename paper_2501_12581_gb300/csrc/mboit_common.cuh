@@ -263,7 +263,7 @@ struct BlendBody {
                                           make_float2(1.0f, 1.0f));
             alpha = make_float2(a.x < 0.25f ? alpha.x : dir.x, a.y < 0.25f ? alpha.y : dir.y);
         }
-        const float2 A = bound_generic2(F, z, w0);
+        const float2 A = bound_generic2(F, z, w0, act);
         const float2 ex = __fmul2_rn(make_float2(-F.m0_log2e, -F.m0_log2e), A);
         float2 wgt = __fmul2_rn(make_float2(fexp2(ex.x), fexp2(ex.y)), alpha);
         wgt.x = oka ? wgt.x : 0.0f;
@@ -642,9 +642,13 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-constexpr int kRowChunk = 8;                    // cache rows per prefetch
-constexpr int kRowZ = 2 * kRowChunk * 32;       // floats of a warp's double buffer of rows
-constexpr int kRowBuf = kRowZ + kRowChunk;      // ... followed by the warped depths of a chunk's rows
+// A warp's buffer for chunks of `chunk` cache rows: a double buffer of rows
+// (2 chunk 32 floats) followed by the warped depths of a chunk's rows.
+constexpr int row_buf_floats(int chunk) { return 2 * chunk * 32 + chunk; }
+constexpr int kRowChunk = 8;                    // cache rows per prefetch (grids: the window slot is the buffer)
+constexpr int kRowBuf = row_buf_floats(kRowChunk);
+constexpr int kUnitRowChunk = 16;               // octrees and meshes: their own buffer, longer chunks
+constexpr int kUnitRowBuf = row_buf_floats(kUnitRowChunk);
 
 // Pass 2 of the batched frame from the tile cache.  The tile's rows are
 // contiguous (rows[r * 32 + lane], r = k - kmin), so the warp copies them
@@ -666,9 +670,10 @@ __device__ __forceinline__ float tagged_weight(float v, int mask) {
     return __int_as_float((127 + (__float_as_int(v) & mask)) << 23);  // 2^shift
 }
 
-template <bool kSel, class Body, bool kTagged = false>
+template <bool kSel, class Body, bool kTagged = false, int kRowChunk = mb::kRowChunk>
 __device__ __forceinline__ void march_rows(const GridD& g, const float* __restrict__ rows, int kmin, int kmax, int k0,
                                            int k1, float* __restrict__ buf, Body& body, int tmask = 0) {
+    constexpr int kRowZ = 2 * kRowChunk * 32;
     if (kmin > kmax) return;
     const int lane = threadIdx.x & 31;
     const int nrows = kmax - kmin + 1;
@@ -741,17 +746,17 @@ __device__ __forceinline__ void march_rows(const GridD& g, const float* __restri
 // lanes with samples all have a generic frame (lanes without samples never
 // call the body) takes the loop without the per-sample test of the frame's
 // kind; the arithmetic, and so the result, is the same.
-template <bool kSel, bool kTagged = false, class Body>
+template <bool kSel, bool kTagged = false, int kChunk = kRowChunk, class Body>
 __device__ __forceinline__ void blend_rows(const GridD& g, const float* __restrict__ rows, int kmin, int kmax, int k0,
                                            int k1, float* __restrict__ buf, Body& body, int tmask = 0) {
     if constexpr (std::is_same<Body, BlendBody>::value) {
         if (__all_sync(0xffffffffu, k0 > k1 || body.F.kind == kFrameGeneric)) {
             GenericBlend gb{body};
-            march_rows<kSel, GenericBlend, kTagged>(g, rows, kmin, kmax, k0, k1, buf, gb, tmask);
+            march_rows<kSel, GenericBlend, kTagged, kChunk>(g, rows, kmin, kmax, k0, k1, buf, gb, tmask);
             return;
         }
     }
-    march_rows<kSel, Body, kTagged>(g, rows, kmin, kmax, k0, k1, buf, body, tmask);
+    march_rows<kSel, Body, kTagged, kChunk>(g, rows, kmin, kmax, k0, k1, buf, body, tmask);
 }
 
 // Pass 1: the tile's rows of the cache (lane 0 takes them, all lanes get the

@@ -21,8 +21,10 @@
 // positive terms (no cancellation).  With x1 < x2:
 //   K(., x0) opens downward (y3(x0) < 0)  <=>  x1 < x0 < x2:  A = w0 rho0 + rho1
 //   otherwise x0 < x1 (A = w0 rho0) or x0 > x2 (A = w0 rho0 + 1 - rho0).
-// The per-pixel frame (mu, s, g, d) is built once per ray in FP64 from the
-// FP32 moments; per sample only FP32 arithmetic remains.
+// The per-pixel frame (mu, s, g, d) is built once per ray from the FP32
+// moments in float-float FP32 (make_frame_ff), in FP64 only for a
+// near-singular Hankel matrix (make_frame); per sample only FP32 arithmetic
+// remains.
 #pragma once
 #include <stdint.h>
 
@@ -406,9 +408,11 @@ MB_HD float bound_generic(const Frame& F, float z0, float w0) {
     float y3 = ffma(x0, x0 - g, -1.0f);
     float e = y3 * inv_d;                         // leading coefficient of K(., x0)
     float rho0 = frcp(ffma(y3, e, ffma(x0, x0, 1.0f)));
-    // x0 outside [x1, x2]: left of both iff K'(x0) < 0
-    float slope = ffma(ffma(2.0f, x0, -g), e, x0);
-    float A_out = slope < 0.0f ? w0 * rho0 : ffma(w0 - 1.0f, rho0, 1.0f);
+    // x0 outside [x1, x2] (y3 >= 0): left of both iff K'(x0) < 0, and
+    // K'(x0) = x0 (1 + 2e) - g e has the sign of x0 there (y3 >= 0 puts x0 at
+    // or beyond a root of x^2 - g x - 1, whose roots r- < 0 < r+ satisfy r- <= g
+    // for g < 0 and r+ >= g for g > 0), so the sign of x0 decides
+    float A_out = x0 < 0.0f ? w0 * rho0 : ffma(w0 - 1.0f, rho0, 1.0f);
     // x1 < x0 < x2 (y3 < 0, so e < 0): the weight rho1 of the smaller root
     // from the representation's moments of order 0 and 1 (rho0 + rho1 +
     // rho2 = 1, rho0 x0 + rho1 x1 + rho2 x2 = 0) and the roots' sum and
@@ -436,7 +440,9 @@ MB_HD float bound_fraction(const Frame& F, float z0, float w0) {
 // on both, as one packed FP32x2 instruction (each half rounded exactly as the
 // scalar instruction), the MUFU reciprocal / square root per half.  Equal to
 // (bound_generic(F, z0.x, w0), bound_generic(F, z0.y, w0)) bit for bit.
-__device__ __forceinline__ float2 bound_generic2(const Frame& F, float2 z0, float w0) {
+// `act`: the lanes calling together; the branch between the roots (y3 < 0)
+// runs only when one of them needs it.
+__device__ __forceinline__ float2 bound_generic2(const Frame& F, float2 z0, float w0, unsigned act) {
     const float2 one = make_float2(1.0f, 1.0f), mone = make_float2(-1.0f, -1.0f);
     const float2 ng = make_float2(-F.p2, -F.p2), inv_d = make_float2(F.p3, F.p3);
     const float2 x0 = __ffma2_rn(z0, make_float2(F.p0, F.p0), make_float2(F.p1, F.p1));
@@ -444,22 +450,25 @@ __device__ __forceinline__ float2 bound_generic2(const Frame& F, float2 z0, floa
     const float2 e = __fmul2_rn(y3, inv_d);
     const float2 K = __ffma2_rn(y3, e, __ffma2_rn(x0, x0, one));
     const float2 rho0 = make_float2(frcp(K.x), frcp(K.y));
-    const float2 slope = __ffma2_rn(__ffma2_rn(make_float2(2.0f, 2.0f), x0, ng), e, x0);
     const float2 lo = __fmul2_rn(make_float2(w0, w0), rho0);
     const float2 hi = __ffma2_rn(make_float2(w0 - 1.0f, w0 - 1.0f), rho0, one);
-    const float2 c1 = __ffma2_rn(ng, e, x0);
-    const float2 c0 = __ffma2_rn(e, mone, one);
-    const float2 dq = __ffma2_rn(c1, c1, __fmul2_rn(__fmul2_rn(make_float2(-4.0f, -4.0f), e), c0));
-    const float2 R = __ffma2_rn(rho0, mone, one);
-    const float2 hR = __fmul2_rn(make_float2(0.5f, 0.5f), R);
-    // -rho0 * x0 * e = ((-rho0) x0) e, with the sign moved onto x0 (exact)
-    const float2 q = __fmul2_rn(__fmul2_rn(rho0, __fmul2_rn(x0, mone)), e);
-    const float2 in = __ffma2_rn(hR, c1, q);
-    float2 rho1 = __ffma2_rn(in, make_float2(frsqrt_fast(fmax_(dq.x, 1e-30f)), frsqrt_fast(fmax_(dq.y, 1e-30f))), hR);
-    rho1 = make_float2(fclamp(rho1.x, 0.0f, R.x), fclamp(rho1.y, 0.0f, R.y));
-    const float2 Ain = __ffma2_rn(make_float2(w0, w0), rho0, rho1);
-    return make_float2(y3.x < 0.0f ? Ain.x : (slope.x < 0.0f ? lo.x : hi.x),
-                       y3.y < 0.0f ? Ain.y : (slope.y < 0.0f ? lo.y : hi.y));
+    float2 A = make_float2(x0.x < 0.0f ? lo.x : hi.x, x0.y < 0.0f ? lo.y : hi.y);
+    if (__any_sync(act, y3.x < 0.0f || y3.y < 0.0f)) {
+        const float2 c1 = __ffma2_rn(ng, e, x0);
+        const float2 c0 = __ffma2_rn(e, mone, one);
+        const float2 dq = __ffma2_rn(c1, c1, __fmul2_rn(__fmul2_rn(make_float2(-4.0f, -4.0f), e), c0));
+        const float2 R = __ffma2_rn(rho0, mone, one);
+        const float2 hR = __fmul2_rn(make_float2(0.5f, 0.5f), R);
+        // -rho0 * x0 * e = ((-rho0) x0) e, with the sign moved onto x0 (exact)
+        const float2 q = __fmul2_rn(__fmul2_rn(rho0, __fmul2_rn(x0, mone)), e);
+        const float2 in = __ffma2_rn(hR, c1, q);
+        float2 rho1 =
+            __ffma2_rn(in, make_float2(frsqrt_fast(fmax_(dq.x, 1e-30f)), frsqrt_fast(fmax_(dq.y, 1e-30f))), hR);
+        rho1 = make_float2(fclamp(rho1.x, 0.0f, R.x), fclamp(rho1.y, 0.0f, R.y));
+        const float2 Ain = __ffma2_rn(make_float2(w0, w0), rho0, rho1);
+        A = make_float2(y3.x < 0.0f ? Ain.x : A.x, y3.y < 0.0f ? Ain.y : A.y);
+    }
+    return A;
 }
 #endif
 

@@ -12,8 +12,8 @@
 // selected pieces: summing the pieces' moment images (the Allreduce add) is
 // done in registers because addition commutes.  Pass 2 (Sec. 4.2, Alg. 1
 // loop 2, Alg. 3) builds the per-pixel reconstruction frame from the global
-// moments in FP64 once per ray, then adds T * alpha * (r, g, b, 1) per sample
-// in FP32; the resolved mode also applies the renormalisation (Sec. 4.3) in
+// moments once per ray (float-float FP32; FP64 for near-singular Hankel
+// matrices), then adds T * alpha * (r, g, b, 1) per sample in FP32; the resolved mode also applies the renormalisation (Sec. 4.3) in
 // the epilogue, so the frame needs no separate colour reduction.
 //
 // In a batched frame (mboit_render_frame) pass 1 also stores every lattice

@@ -749,7 +749,7 @@ __global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 2>::value : 2) k_p
                                                     Counters* __restrict__ ctr, const TileCache cache) {
     if (tables_bad(a)) return;
     __shared__ float4 s_tf[512];
-    __shared__ __align__(16) float s_rows[kCache ? kFusedWarps : 1][kCache ? kRowBuf : 4];
+    __shared__ __align__(16) float s_rows[kCache ? kFusedWarps : 1][kCache ? kUnitRowBuf : 4];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float4 e0 = tf[i], e1 = i < 255 ? tf[i + 1] : tf[i];
         s_tf[2 * i] = e0;
@@ -779,9 +779,10 @@ __global__ void __launch_bounds__(256, MS == 0 ? MinBlocks<V, 2>::value : 2) k_p
                 tmask = tag_mask(a.max_level);
             }
             if (tagged)
-                blend_rows<true, true>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, buf, body, tmask);
+                blend_rows<true, true, kUnitRowChunk>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, buf, body, tmask);
             else
-                blend_rows<RowsChecked<V, kSel>::value>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, buf, body);
+                blend_rows<RowsChecked<V, kSel>::value, false, kUnitRowChunk>(g, cache.vals + tb * 32, kmin, kmax, k0,
+                                                                               k1, buf, body);
         } else {
             march_unit<kSel>(a, sel, o, d, k0, k1, body);
         }

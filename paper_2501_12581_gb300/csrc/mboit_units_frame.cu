@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(256, FrameMinBlocks<V>::value) k_frame_unit(
     if (tables_bad(a)) return;
     __shared__ float2 s_sig[256];
     __shared__ float4 s_tf[512];
-    __shared__ __align__(16) float s_rows[kFusedWarps][kRowBuf];
+    __shared__ __align__(16) float s_rows[kFusedWarps][kUnitRowBuf];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float4 e0 = tf[i], e1 = i < 255 ? tf[i + 1] : tf[i];
         s_tf[2 * i] = e0;
@@ -77,9 +77,10 @@ __global__ void __launch_bounds__(256, FrameMinBlocks<V>::value) k_frame_unit(
         __syncwarp();  // the rows' stores before any lane reads them
         if (base >= 0) {
             if (tagged)
-                blend_rows<true, true>(g, cache.vals + base * 32, kmin, kmax, k0, k1, buf, body, tmask);
+                blend_rows<true, true, kUnitRowChunk>(g, cache.vals + base * 32, kmin, kmax, k0, k1, buf, body, tmask);
             else
-                blend_rows<RowsChecked<V, kSel>::value>(g, cache.vals + base * 32, kmin, kmax, k0, k1, buf, body);
+                blend_rows<RowsChecked<V, kSel>::value, false, kUnitRowChunk>(g, cache.vals + base * 32, kmin, kmax,
+                                                                               k0, k1, buf, body);
         } else {
             march_unit<kSel>(a, sel, o, d, k0, k1, body);
         }
