@@ -585,45 +585,54 @@ __device__ __forceinline__ void march_amr_rows(const AmrD& a, const uint8_t* __r
     static_assert(NV == 9, "the box test's bound is NV - 1 = 8");
     const float* blk = nullptr;                         // the cached leaf's vertex block (NULL: none selected)
     float lo0 = __int_as_float(0x7f800000), lo1 = lo0, lo2 = lo0, inv_h = 1.0f;   // no box yet
+    // one lattice point: leaf box test (a leaf change where it fails), the
+    // trilinear value, the store and the moments; j = the point's row in the window
+    auto point = [&](float t, int j) {
+        const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
+        float q0 = (p0 - lo0) * inv_h, q1 = (p1 - lo1) * inv_h, q2 = (p2 - lo2) * inv_h;
+        if (!(__float_as_uint(q0) < kEdge && __float_as_uint(q1) < kEdge && __float_as_uint(q2) < kEdge)) {
+            // a new leaf: the finest-brick map, then the leaf's box
+            const float p[3] = {p0, p1, p2};
+            const int v = unit_of(a, p);
+            if (v < 0) {
+                lo0 = lo1 = lo2 = __int_as_float(0x7f800000);
+                blk = nullptr;
+                store.put(__int_as_float(0x7fc00000));
+                return;
+            }
+            const float4 L = __ldg(a.leaf_box + v);
+            lo0 = L.x;
+            lo1 = L.y;
+            lo2 = L.z;
+            inv_h = L.w;
+            blk = (kSel && sel && !__ldg(sel + v)) ? nullptr : a.values + (size_t)v * (NV * NV * NV);
+            q0 = (p0 - lo0) * inv_h;
+            q1 = (p1 - lo1) * inv_h;
+            q2 = (p2 - lo2) * inv_h;
+        }
+        if (kSel && !blk) {
+            store.put(__int_as_float(0x7fc00000));
+            return;
+        }
+        const int cx = (int)q0, cy = (int)q1, cz = (int)q2;
+        const float* __restrict__ c = blk + (cz * NV + cy) * NV + cx;
+        const float val = tf_x(g, trilinear8(__ldg(c), __ldg(c + 1), __ldg(c + NV), __ldg(c + NV + 1),
+                                             __ldg(c + NV * NV), __ldg(c + NV * NV + 1), __ldg(c + NV * NV + NV),
+                                             __ldg(c + NV * NV + NV + 1), q0 - (float)cx, q1 - (float)cy,
+                                             q2 - (float)cz));
+        store.put(val);
+        body.add(val, 1.0f, rows.z[j]);
+    };
     for (int kw = kmin; kw <= kmax; kw += kDepthRows) {
         rows.fill(kw, g.step, body.wa, body.wb);
         const int ka = max(kw, k0), kz = min(kw + kDepthRows - 1, k1);
         float t = lattice_t(ka, g.step);
-        for (int k = ka; k <= kz; ++k, t += g.step) {
-            const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
-            float q0 = (p0 - lo0) * inv_h, q1 = (p1 - lo1) * inv_h, q2 = (p2 - lo2) * inv_h;
-            if (!(__float_as_uint(q0) < kEdge && __float_as_uint(q1) < kEdge && __float_as_uint(q2) < kEdge)) {
-                // a new leaf: the finest-brick map, then the leaf's box
-                const float p[3] = {p0, p1, p2};
-                const int v = unit_of(a, p);
-                if (v < 0) {
-                    lo0 = lo1 = lo2 = __int_as_float(0x7f800000);
-                    blk = nullptr;
-                    store.put(__int_as_float(0x7fc00000));
-                    continue;
-                }
-                const float4 L = __ldg(a.leaf_box + v);
-                lo0 = L.x;
-                lo1 = L.y;
-                lo2 = L.z;
-                inv_h = L.w;
-                blk = (kSel && sel && !__ldg(sel + v)) ? nullptr : a.values + (size_t)v * (NV * NV * NV);
-                q0 = (p0 - lo0) * inv_h;
-                q1 = (p1 - lo1) * inv_h;
-                q2 = (p2 - lo2) * inv_h;
-            }
-            if (kSel && !blk) {
-                store.put(__int_as_float(0x7fc00000));
-                continue;
-            }
-            const int cx = (int)q0, cy = (int)q1, cz = (int)q2;
-            const float* __restrict__ c = blk + (cz * NV + cy) * NV + cx;
-            const float val = tf_x(g, trilinear8(__ldg(c), __ldg(c + 1), __ldg(c + NV), __ldg(c + NV + 1),
-                                                 __ldg(c + NV * NV), __ldg(c + NV * NV + 1), __ldg(c + NV * NV + NV),
-                                                 __ldg(c + NV * NV + NV + 1), q0 - (float)cx, q1 - (float)cy,
-                                                 q2 - (float)cz));
-            store.put(val);
-            body.add(val, 1.0f, rows.z[k - kw]);
+        if (ka == kw && kz == kw + kDepthRows - 1) {
+            // the lane samples every row of the window: unrolled
+#pragma unroll
+            for (int j = 0; j < kDepthRows; ++j, t += g.step) point(t, j);
+        } else {
+            for (int k = ka; k <= kz; ++k, t += g.step) point(t, k - kw);
         }
     }
 }
