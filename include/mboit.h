@@ -221,7 +221,7 @@ typedef struct {
  * stages, per warp, the block of the field its 32 rays traverse over the
  * next S lattice steps in shared memory; configurations differ in block
  * shape, S and load width.  All give bit-identical results. */
-#define MBOIT_NUM_TUNINGS 5
+#define MBOIT_NUM_TUNINGS 6
 
 /* Message of the last failing call on this thread ("" if none). */
 MBOIT_API const char* mboit_last_error(void);
@@ -372,10 +372,14 @@ MBOIT_API mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* v
                                              int32_t* segments_per_pixel, void* stream);
 
 /* Selects the window configuration (0 .. MBOIT_NUM_TUNINGS-1) of the fused
- * pass 1 and pass 2.  Configurations 2-4 read 16-byte chunks and need
- * dims[0] % 4 == 0 and a 16-byte aligned field; otherwise
- * MBOIT_ERR_INVALID_ARG and nothing changes.  Takes effect for the next call;
- * captured frame graphs are re-recorded. */
+ * pass 1 and pass 2.  Configurations 2-5 read 16-byte chunks and need
+ * dims[0] % 4 == 0 and a 16-byte aligned field; configuration 5 is
+ * configuration 3's window (16 x 8 x 8 floats) filled in pass 1 by one TMA
+ * tensor copy per warp (cp.async.bulk.tensor.3d from the field's tensor map,
+ * completed on an mbarrier; pass 2 takes configuration 3) and also needs the
+ * driver's tensor-map encoder; otherwise MBOIT_ERR_INVALID_ARG and nothing
+ * changes.  Every configuration gives the same bits.  Takes effect for the
+ * next call; captured frame graphs are re-recorded. */
 MBOIT_API mboit_status mboit_set_tuning(mboit_volume v, int32_t pass1, int32_t pass2);
 
 /* Number of kernel launches of mboit_render_frame: 2 (pass 1, then pass 2

@@ -95,6 +95,8 @@ struct mboit_volume_s {
     bool frame_timed = false;
     std::vector<GraphEntry> graphs;
     int32_t tune1 = 0, tune2 = 0;
+    CUtensorMap field_map;      // grids: the field's tensor map for TMA windows (configuration 5)
+    bool has_field_map = false;
     int32_t packet = MBOIT_PACKET_8X4;
     int32_t frame_launches = 2;  // 1: one launch per frame (four power moments)
     // sort-last baseline buffers (grow only)
@@ -506,6 +508,14 @@ mboit_status prepare_tets(const mboit_volume_desc* d, TetHost& h) {
 
 // The batched (fused, persistent) passes of the volume's kind.  `cache`:
 // mesh sample values shared by the two passes of one frame.
+// The field's tensor map of a grid volume, or NULL (no TMA windows).
+const CUtensorMap* field_map_of(mboit_volume v) { return v->has_field_map ? &v->field_map : nullptr; }
+
+// Whether window configuration cfg can run on this volume.
+bool config_usable(mboit_volume v, int cfg) {
+    return mb::stage_config_eligible(v->grid, cfg) && (cfg != 5 || v->has_field_map);
+}
+
 // Checks the octree's or mesh's index tables on stream s before passes that
 // read them (grids have none).
 cudaError_t check_tables(mboit_volume v, cudaStream_t s) {
@@ -520,7 +530,7 @@ cudaError_t pass1_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTab
     if (e != cudaSuccess) return e;
     if (v->kind == MBOIT_AMR) return mb::launch_pass1_amr(v->amr, v->d_tf, mask, vt, moments, v->d_ctr, s, tc);
     if (v->kind == MBOIT_TET) return mb::launch_pass1_tet(v->tet, v->d_tf, mask, vt, moments, v->d_ctr, s, tc);
-    return mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1, tc);
+    return mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1, tc, field_map_of(v));
 }
 
 cudaError_t pass2_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, const void* moments,
@@ -543,7 +553,8 @@ cudaError_t frame_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTab
         return mb::launch_frame_amr(v->amr, v->d_tf, mask, vt, moments, color, mb::kColorResolved, v->d_ctr, s, tc);
     if (v->kind == MBOIT_TET)
         return mb::launch_frame_tet(v->tet, v->d_tf, mask, vt, moments, color, mb::kColorResolved, v->d_ctr, s, tc);
-    return mb::launch_frame_fused(v->grid, v->d_tf, mask, vt, moments, color, mb::kColorResolved, v->d_ctr, s, cfg, tc);
+    return mb::launch_frame_fused(v->grid, v->d_tf, mask, vt, moments, color, mb::kColorResolved, v->d_ctr, s, cfg, tc,
+                                  field_map_of(v));
 }
 
 // The tile-row sample cache of a frame: its exact row count for these views
@@ -812,6 +823,7 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
     // one launch where it measured faster without tuning (grids); the
     // autotuner times both forms for every kind with four power moments
     v->frame_launches = (d->kind == MBOIT_GRID && d->moment_set == MBOIT_POWER4) ? 1 : 2;
+    if (d->kind == MBOIT_GRID) v->has_field_map = mb::encode_field_map(g, &v->field_map);
     if (is_amr) {
         g.field = nullptr;
         v->nbricks = d->n_leaves;  // the units of an octree are its leaves
@@ -1251,6 +1263,9 @@ mboit_status mboit_synchronize(mboit_volume v, void* stream) {
     MB_CUDA(cudaMemcpy(&err, &v->d_ctr->error, sizeof err, cudaMemcpyDeviceToHost));
     if (err == 0) return MBOIT_OK;
     MB_CUDA(cudaMemset(&v->d_ctr->error, 0, sizeof err));   // reported once
+    if (err & mb::kErrTmaTimeout)
+        return fail(MBOIT_ERR_TIMEOUT, "a TMA window load did not complete within its wait limit (code " +
+                                           std::to_string(err) + "); the render stopped early and its images are not valid");
     std::string what;
     if (err & mb::kErrLeafId) what += " an octree finest-brick map entry is not a leaf id;";
     if (err & mb::kErrTetId) what += " a mesh face-neighbour or bin-list entry is not a tet id;";
@@ -1374,9 +1389,10 @@ mboit_status mboit_set_tuning(mboit_volume v, int32_t pass1, int32_t pass2) {
     if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
     if (v->kind != MBOIT_GRID && (pass1 != 0 || pass2 != 0))
         return fail(MBOIT_ERR_INVALID_ARG, "octree and mesh volumes have one configuration (0)");
-    if (!mb::stage_config_eligible(v->grid, pass1) || !mb::stage_config_eligible(v->grid, pass2))
+    if (v->kind == MBOIT_GRID && (!config_usable(v, pass1) || !config_usable(v, pass2)))
         return fail(MBOIT_ERR_INVALID_ARG, "tuning must be in [0, " + std::to_string(mb::kNumStageConfigs - 1) +
-                                               "]; 2-4 need dims[0] % 4 == 0 and a 16-byte aligned field");
+                                               "]; 2-5 need dims[0] % 4 == 0 and a 16-byte aligned field, 5 also "
+                                               "the field's tensor map (TMA)");
     std::lock_guard<std::mutex> lk(v->mu);
     v->tune1 = pass1;
     v->tune2 = pass2;
@@ -1439,12 +1455,13 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
         int pick[2] = {0, 0};
         for (int pass = 0; pass < 2 && ce == cudaSuccess; ++pass) {
             for (int cfg = 0; cfg < mb::kNumStageConfigs && ce == cudaSuccess; ++cfg) {
-                if (grid ? !mb::stage_config_eligible(v->grid, cfg) : cfg != 0) continue;
+                if (grid ? !config_usable(v, cfg) : cfg != 0) continue;
                 auto launch = [&]() {
                     if (!grid)
                         return pass == 0 ? pass1_batched(v, mask, vt, moments_scratch, s)
                                          : pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved, s);
-                    return pass == 0 ? mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s, cfg)
+                    return pass == 0 ? mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s, cfg,
+                                                              mb::TileCache{}, field_map_of(v))
                                      : mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba,
                                                               mb::kColorResolved, v->d_ctr, s, cfg);
                 };
@@ -1462,7 +1479,8 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
             }
             // pass 2 is timed on the moments of the fastest pass 1
             if (pass == 0 && ce == cudaSuccess)
-                ce = grid ? mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s, pick[0])
+                ce = grid ? mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s, pick[0],
+                                                   mb::TileCache{}, field_map_of(v))
                           : pass1_batched(v, mask, vt, moments_scratch, s);
         }
         if (ce == cudaSuccess && best_ms[0] + best_ms[1] < best_total) {
@@ -1490,7 +1508,7 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
             float best_ms = 3.0e38f;
             for (int form = 0; form <= mb::kNumStageConfigs && ce == cudaSuccess; ++form) {
                 // form 0: two launches; form c + 1: one launch in configuration c
-                if (form > 0 && (grid ? !mb::stage_config_eligible(v->grid, form - 1) : form != 1)) continue;
+                if (form > 0 && (grid ? !config_usable(v, form - 1) : form != 1)) continue;
                 auto launch = [&]() {
                     if (form > 0) return frame_batched(v, mask, vt, moments_scratch, rgba, s, form - 1, tc);
                     if (!grid) {
@@ -1500,7 +1518,7 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
                                                                 s, tc);
                     }
                     cudaError_t e = mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s,
-                                                           best[0], tc);
+                                                           best[0], tc, field_map_of(v));
                     return e != cudaSuccess ? e
                                             : mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba,
                                                                      mb::kColorResolved, v->d_ctr, s, best[1], tc);

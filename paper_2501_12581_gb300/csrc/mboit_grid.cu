@@ -1,5 +1,7 @@
 // Fused, persistent grid passes: kernel selection and launchers (the kernel
 // templates and their design are in mboit_grid.cuh).
+#include <cstring>
+
 #include "mboit_grid.cuh"
 
 namespace mb {
@@ -32,7 +34,7 @@ const void* pass2_fn(int cfg, bool sel, int ms) {
 }
 
 
-bool vec_config(int cfg) { return cfg == 2 || cfg == 3 || cfg == 4; }
+bool vec_config(int cfg) { return cfg == 2 || cfg == 3 || cfg == 4 || cfg == 5; }
 
 }  // namespace
 
@@ -61,16 +63,48 @@ cudaError_t prepare_grid_kernels() {
 }
 
 cudaError_t launch_pass1_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
-                               void* moments, Counters* ctr, cudaStream_t s, int cfg, TileCache cache) {
+                               void* moments, Counters* ctr, cudaStream_t s, int cfg, TileCache cache,
+                               const CUtensorMap* tmap) {
     if (!stage_config_eligible(g, cfg)) cfg = 0;
+    if (cfg == 5 && !tmap) cfg = 3;   // no tensor map: the same window by plain loads
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
     if (e == cudaSuccess && cache.vals) e = cudaMemsetAsync(&ctr->cache_rows, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const bool sel = brick_sel != nullptr;
     const void* fn = cache.vals ? pass1_fn<true>(cfg, sel, g.trig.sel) : pass1_fn(cfg, sel, g.trig.sel);
     char* m = static_cast<char*>(moments);
-    void* args[] = {(void*)&g, (void*)&tf, (void*)&brick_sel, (void*)&vt, (void*)&m, (void*)&ctr, (void*)&cache};
+    CUtensorMap map;
+    if (tmap)
+        map = *tmap;
+    else
+        std::memset(&map, 0, sizeof map);   // not read by configurations without TMA
+    void* args[] = {(void*)&g, (void*)&tf, (void*)&brick_sel, (void*)&vt, (void*)&m, (void*)&ctr, (void*)&cache,
+                    (void*)&map};
     return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
+}
+
+bool encode_field_map(const GridD& g, CUtensorMap* out) {
+    if (!stage_config_eligible(g, 5)) return false;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return false;
+    }
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4};   // bytes, dims 1 and 2
+    const cuuint32_t box[3] = {(cuuint32_t)Stage5::WX, (cuuint32_t)Stage5::WY, (cuuint32_t)Stage5::WZ};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = reinterpret_cast<Encode>(fn)(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                                                    const_cast<float*>(g.field), dims, strides, box, estr,
+                                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 cudaError_t launch_pass2_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,

@@ -45,17 +45,20 @@ namespace {
 // row is fetched once per window instead of eight times per lattice step.  A
 // box that does not fit (widely spread rays) falls back to direct loads.
 
-template <int S_, int WX_, int WY_, int WZ_, bool kVec_>
+template <int S_, int WX_, int WY_, int WZ_, bool kVec_, bool kTma_ = false>
 struct StageCfg {
     static constexpr int S = S_, WX = WX_, WY = WY_, WZ = WZ_;
     static constexpr bool kVec = kVec_;  // 16-byte loads: x origin rounded down to a multiple of 4
+    static constexpr bool kTma = kTma_;  // the window arrives by one tensor copy (TMA) of the warp
     // scalar windows pad rows to an odd pitch; vector windows keep 16-byte rows
-    // and shift each plane by 4 floats, both to spread shared-memory banks
+    // and shift each plane by 4 floats, both to spread shared-memory banks; a
+    // TMA window is the box as the copy lays it out, [z][y][x] without padding
     static constexpr int Pitch = kVec_ ? WX_ : WX_ + 1;
-    static constexpr int Plane = kVec_ ? WY_ * WX_ + 4 : WY_ * (WX_ + 1);
+    static constexpr int Plane = kTma_ ? WY_ * WX_ : (kVec_ ? WY_ * WX_ + 4 : WY_ * (WX_ + 1));
     static constexpr int Floats = WZ_ * Plane;
     static constexpr int Elems = WX_ * WY_ * WZ_;
     static_assert(!kVec_ || WX_ % 4 == 0, "vector windows need a multiple of 4 in x");
+    static_assert(!kTma_ || (kVec_ && Floats % 32 == 0), "TMA windows start on the x-origin rule and 128-byte slots");
 };
 // The configurations the autotuner chooses from (index = tuning id).
 using Stage0 = StageCfg<6, 8, 8, 8, false>;
@@ -63,6 +66,80 @@ using Stage1 = StageCfg<8, 8, 8, 8, false>;
 using Stage2 = StageCfg<6, 12, 8, 8, true>;
 using Stage3 = StageCfg<6, 16, 8, 8, true>;
 using Stage4 = StageCfg<8, 16, 8, 10, true>;
+using Stage5 = StageCfg<6, 16, 8, 8, true, true>;   // configuration 3's window by TMA
+
+// ------------------------------------------------------------------------
+// TMA window loads.  One lane of the warp arms the warp's mbarrier with the
+// window's byte count and issues cp.async.bulk.tensor.3d from the field's
+// tensor map (encoded on the host: dims nx, ny, nz, box WX x WY x WZ floats,
+// no swizzle, zero fill outside the field, which no sample reads); every lane
+// then waits on the barrier's phase.  The x coordinate is a multiple of 4
+// floats (16 bytes), as the tiled copy requires.  A wait gives up after
+// kTmaSpin polls: the kernel records kErrTmaTimeout, waits once more, bounded,
+// for the copy in flight, and returns.
+
+constexpr int kTmaSpin = 1 << 20;      // polls of at most ~1 us each (the suspend-time hint): ~1 s in all
+
+struct TmaWin {
+    const CUtensorMap* map;    // the field's tensor map (a __grid_constant__ kernel parameter)
+    uint64_t* bar;             // this warp's mbarrier
+    unsigned phase;            // parity of its next completion
+    int32_t* err;              // the volume's error word
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    for (int i = 0; i < kTmaSpin; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Copies the WX x WY x WZ box at (x, y, z) of the field into `win` (this
+// warp's 128-byte aligned slot); all 32 lanes call it.  False when the copy
+// did not complete in time.
+template <class Cfg>
+__device__ __forceinline__ bool tma_window(TmaWin& tw, float* win, int x, int y, int z) {
+    const unsigned bar = smem_addr(tw.bar);
+    if ((threadIdx.x & 31) == 0) {
+        constexpr unsigned bytes = Cfg::Elems * 4;
+        // the lanes' earlier reads of the slot (ordered by the caller's
+        // __syncwarp) before the copy's writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];" ::"r"(smem_addr(win)),
+            "l"(reinterpret_cast<uint64_t>(tw.map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+            : "memory");
+    }
+    const bool ok = mbar_wait(bar, tw.phase);
+    if (!ok) {
+        if ((threadIdx.x & 31) == 0) atomicOr(tw.err, kErrTmaTimeout);
+        mbar_wait(bar, tw.phase);   // the copy in flight, once more, bounded
+    }
+    tw.phase ^= 1u;
+    return ok;
+}
+
+// Initialises the warps' barriers (one arrival per phase); before the
+// kernel's first __syncthreads.
+template <class Cfg>
+__device__ __forceinline__ void tma_init(uint64_t* bars) {
+    if constexpr (Cfg::kTma) {
+        if ((threadIdx.x & 31) == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + (threadIdx.x >> 5))) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
+}
 
 // Bounding box of the cells that lane samples in [ka, kz] can touch, reduced
 // over the warp; true if it fits the window.
@@ -98,10 +175,12 @@ __device__ __forceinline__ bool window_box(const GridD& g, const float o[3], con
 // in-domain points; k0 > k1: none), calling body(t, xt) with the table
 // coordinate xt of every owned sample in depth order (and storing xt, NaN for
 // a point not sampled).  All 32 lanes of the warp call it together.
+// Returns false when a TMA window did not arrive in time (the kernel must
+// stop; kErrTmaTimeout is recorded).
 template <class Cfg, bool kSel, class Body, class Store = NoStore>
-__device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __restrict__ sel, float* __restrict__ win,
+__device__ __forceinline__ bool march_fused(const GridD& g, const uint8_t* __restrict__ sel, float* __restrict__ win,
                                             const float o[3], const float d[3], int k0, int k1, Body& body,
-                                            Store store = Store{}) {
+                                            Store store = Store{}, TmaWin* tma = nullptr) {
     const unsigned full = 0xffffffffu;
     const int kmin = __reduce_min_sync(full, k0);
     const int kmax = __reduce_max_sync(full, k1);
@@ -119,7 +198,9 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
         if (fits) {
             __syncwarp();
             const int lane = threadIdx.x & 31;
-            if (Cfg::kVec) {
+            if constexpr (Cfg::kTma) {
+                if (!tma_window<Cfg>(*tma, win, LO[0], LO[1], LO[2])) return false;
+            } else if (Cfg::kVec) {
                 // nx % 4 == 0 and a 16-byte aligned field (checked by the launcher):
                 // every chunk start gx is a multiple of 4 and gx + 3 < nx
                 constexpr int QX = Cfg::WX / 4;
@@ -196,6 +277,7 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
         }
         kb = ke + 1;
     }
+    return true;
 }
 
 
@@ -203,31 +285,34 @@ __device__ __forceinline__ void march_fused(const GridD& g, const uint8_t* __res
 // with samples all have a generic frame takes the body without the
 // per-sample test of the frame's kind (the same arithmetic and result).
 template <class Cfg, bool kSel, class Body>
-__device__ __forceinline__ void blend_fused(const GridD& g, const uint8_t* __restrict__ sel, float* __restrict__ win,
-                                            const float o[3], const float d[3], int k0, int k1, Body& body) {
+__device__ __forceinline__ bool blend_fused(const GridD& g, const uint8_t* __restrict__ sel, float* __restrict__ win,
+                                            const float o[3], const float d[3], int k0, int k1, Body& body,
+                                            TmaWin* tma = nullptr) {
     if constexpr (std::is_same<Body, BlendBody>::value) {
         if (__all_sync(0xffffffffu, k0 > k1 || body.F.kind == kFrameGeneric)) {
             GenericBlend gb{body};
-            march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, gb);
-            return;
+            return march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, gb, NoStore{}, tma);
         }
     }
-    march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
+    return march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body, NoStore{}, tma);
 }
 
 template <bool kSel, class Cfg, int MS, bool kCache = false>
 __global__ void __launch_bounds__(256, MS == 0 ? 5 : 1) k_pass1_fused(const __grid_constant__ GridD g, const float4* __restrict__ tf,
                                                      const uint8_t* __restrict__ sel, const __grid_constant__ ViewTable vt,
                                                      char* __restrict__ moments, Counters* __restrict__ ctr,
-                                                     const TileCache cache) {
+                                                     const TileCache cache, const __grid_constant__ CUtensorMap tmap) {
     __shared__ float2 s_sig[256];
-    __shared__ __align__(16) float s_win[kFusedWarps][Cfg::Floats];
+    __shared__ __align__(128) float s_win[kFusedWarps][Cfg::Floats];
+    __shared__ __align__(8) uint64_t s_bar[Cfg::kTma ? kFusedWarps : 1];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const float s0 = tf[i].w;
         s_sig[i] = make_float2(s0, i < 255 ? tf[i + 1].w - s0 : 0.0f);
     }
+    tma_init<Cfg>(s_bar);
     __syncthreads();
     float* win = s_win[threadIdx.x >> 5];
+    TmaWin tw{&tmap, s_bar + (Cfg::kTma ? threadIdx.x >> 5 : 0), 0u, &ctr->error};
     int vi, px, py, tile;
     while (next_tile(vt, &ctr->tile_next[0], vi, px, py, tile)) {
         const ViewSlot& S = vt.s[vi];
@@ -236,12 +321,14 @@ __global__ void __launch_bounds__(256, MS == 0 ? 5 : 1) k_pass1_fused(const __gr
         int k0, k1;
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
         auto body = make_moment_body<MS>(s_sig, g, S.v);
+        bool ok;
         if constexpr (kCache) {
             RowStore st{tile_rows(cache, ctr, tile, k0, k1)};
-            march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body, st);
+            ok = march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body, st, &tw);
         } else {
-            march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
+            ok = march_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body, NoStore{}, &tw);
         }
+        if (!ok) return;
         if (valid) body.store(g, moments, S, S.moment_off, py * S.v.width + px);
         warp_add_u64(&ctr->samples[0], body.n);
     }
@@ -278,7 +365,7 @@ __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ Gri
             const int kmin = __reduce_min_sync(0xffffffffu, k0), kmax = __reduce_max_sync(0xffffffffu, k1);
             blend_rows<kSel>(g, cache.vals + tb * 32, kmin, kmax, k0, k1, win, body);
         } else {
-            blend_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);
+            blend_fused<Cfg, kSel>(g, sel, win, o, d, k0, k1, body);   // pass 2 has no TMA windows
         }
         if (valid) {
             float4* out = reinterpret_cast<float4*>(color + S.color_off) + pix;
@@ -296,14 +383,15 @@ const void* pass1_fn_ms(int cfg, bool sel) {
     if (sel) return (const void*)k_pass1_fused<true, Stage0, MS, kC>;
     if constexpr (MS != 0) {
         // other moment sets: configurations 0 and 3 only
-        return cfg == 3 ? (const void*)k_pass1_fused<false, Stage3, MS, kC>
-                        : (const void*)k_pass1_fused<false, Stage0, MS, kC>;
+        return cfg == 3 || cfg == 5 ? (const void*)k_pass1_fused<false, Stage3, MS, kC>
+                                    : (const void*)k_pass1_fused<false, Stage0, MS, kC>;
     } else {
         switch (cfg) {
             case 1: return (const void*)k_pass1_fused<false, Stage1, MS, kC>;
             case 2: return (const void*)k_pass1_fused<false, Stage2, MS, kC>;
             case 3: return (const void*)k_pass1_fused<false, Stage3, MS, kC>;
             case 4: return (const void*)k_pass1_fused<false, Stage4, MS, kC>;
+            case 5: return (const void*)k_pass1_fused<false, Stage5, MS, kC>;
             default: return (const void*)k_pass1_fused<false, Stage0, MS, kC>;
         }
     }
@@ -314,13 +402,14 @@ const void* pass2_fn_ms(int cfg, bool sel) {
     if (sel) return (const void*)k_pass2_fused<true, Stage0, MS, kC>;
     if constexpr (MS != 0) {
         // other moment sets: configurations 0 and 3 only
-        return cfg == 3 ? (const void*)k_pass2_fused<false, Stage3, MS, kC>
-                        : (const void*)k_pass2_fused<false, Stage0, MS, kC>;
+        return cfg == 3 || cfg == 5 ? (const void*)k_pass2_fused<false, Stage3, MS, kC>
+                                    : (const void*)k_pass2_fused<false, Stage0, MS, kC>;
     } else {
         switch (cfg) {
             case 1: return (const void*)k_pass2_fused<false, Stage1, MS, kC>;
             case 2: return (const void*)k_pass2_fused<false, Stage2, MS, kC>;
-            case 3: return (const void*)k_pass2_fused<false, Stage3, MS, kC>;
+            case 3:
+            case 5: return (const void*)k_pass2_fused<false, Stage3, MS, kC>;   // pass 2 windows without TMA
             case 4: return (const void*)k_pass2_fused<false, Stage4, MS, kC>;
             default: return (const void*)k_pass2_fused<false, Stage0, MS, kC>;
         }

@@ -2,6 +2,7 @@
 // kernels (mboit_grid.cu, mboit_units.cu, mboit_kernels.cu).  Not part of
 // the public ABI.
 #pragma once
+#include <cuda.h>   // CUtensorMap (the type only; the library calls the driver through the runtime's entry point)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -39,6 +40,7 @@ struct ViewTable {
 constexpr int32_t kErrLeafId = 0x2;   // an octree finest-brick map entry is not a leaf id (nor -1)
 constexpr int32_t kErrTetId = 0x4;    // a mesh face neighbour or bin-list entry is not a tet id
 constexpr int32_t kErrBinRange = 0x8; // a mesh bin's range of the bin list leaves the list
+constexpr int32_t kErrTmaTimeout = 0x10;  // a TMA window load did not complete within its wait limit
 
 // Device counters owned by a volume.
 struct Counters {
@@ -116,9 +118,11 @@ struct TileCache {
 };
 
 // Number of shared-memory window configurations of the fused passes (the
-// autotuner's choices).  Configurations 2-4 use 16-byte loads and need
+// autotuner's choices).  Configurations 2-5 use 16-byte loads and need
 // nx % 4 == 0 and a 16-byte aligned field; 0 and 1 work everywhere.
-constexpr int kNumStageConfigs = 5;
+// Configuration 5 is configuration 3's window filled by a TMA tensor copy in
+// pass 1 (pass 2 takes configuration 3); it needs the field's tensor map.
+constexpr int kNumStageConfigs = 6;
 bool stage_config_eligible(const GridD& g, int cfg);
 
 // Loads all kernels and caches launch shapes (call before any capture).
@@ -127,7 +131,7 @@ cudaError_t prepare_kernels();
 // means every brick is sampled.  An ineligible `cfg` falls back to 0.
 cudaError_t launch_pass1_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
                                void* moments, Counters* ctr, cudaStream_t s, int cfg = 0,
-                               TileCache cache = TileCache{});
+                               TileCache cache = TileCache{}, const CUtensorMap* tmap = nullptr);
 // Fused pass 2 over all selected pieces, REDUCED or RESOLVED output.
 cudaError_t launch_pass2_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
                                const void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s,
@@ -138,7 +142,11 @@ cudaError_t launch_pass2_fused(const GridD& g, const float4* tf, const uint8_t* 
 // marches again).  Results equal launch_pass1_fused + launch_pass2_fused.
 cudaError_t launch_frame_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,
                                void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s, int cfg,
-                               TileCache cache);
+                               TileCache cache, const CUtensorMap* tmap = nullptr);
+// The field's tensor map for TMA windows (dims nx, ny, nz floats, box of
+// configuration 5's window); false when the driver offers no encoder or the
+// field does not qualify (nx % 4, alignment).
+bool encode_field_map(const GridD& g, CUtensorMap* out);
 // Rows a frame's tile cache needs over the domain box of `g` (sum over the
 // ray tiles of kmax - kmin + 1), added to *rows.
 cudaError_t launch_tile_rows(const GridD& g, const ViewTable& vt, unsigned long long* rows, cudaStream_t s);
