@@ -133,6 +133,9 @@ def _load():
             lib.orc_tet_locate.restype = ctypes.c_int
             lib.orc_tet_locate.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
+            lib.orc_render_grid_given.restype = ctypes.c_int
+            lib.orc_render_grid_given.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_render_grid_segments.restype = ctypes.c_int
             lib.orc_render_grid_segments.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
@@ -404,6 +407,25 @@ def render_segments(scene, view=0, pixels=None, pieces=None):
                                     rgba.ctypes.data, nseg.ctypes.data) != 0:
         raise ValueError("oracle rejected its arguments")
     return rgba, nseg
+
+
+def render_grid_given(scene, moments, view=0, pixels=None, pieces=None):
+    """Stage two of a grid scene from given global moments (Alg. 1 loop 2):
+    `moments` [n][nm] per listed pixel in the order render_grid returns them
+    (b0, b1.. or b0, Re t1, Im t1, ..; t_j not normalised).  Returns
+    {"mboit", "raw"} [n][4]."""
+    lib = _load()
+    v = scene.views[view] if isinstance(view, int) else view
+    pix = np.arange(v.width * v.height, dtype=np.int64) if pixels is None else \
+        np.ascontiguousarray(pixels, dtype=np.int64)
+    given = np.ascontiguousarray(moments, dtype=np.float64).reshape(pix.size, _nm(scene))
+    g, keep = _grid_struct(scene, pieces)
+    out = {"mboit": np.zeros((pix.size, 4)), "raw": np.zeros((pix.size, 4))}
+    vs = _view_struct(v)
+    if lib.orc_render_grid_given(ctypes.byref(g), ctypes.byref(vs), pix.ctypes.data, pix.size, given.ctypes.data,
+                                 out["mboit"].ctypes.data, out["raw"].ctypes.data) != 0:
+        raise ValueError("oracle rejected its arguments")
+    return out
 
 
 def render_grid(scene, view=0, pixels=None, pieces=None, want=("mboit",)):

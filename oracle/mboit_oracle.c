@@ -192,6 +192,7 @@ typedef struct {
     double power_bias[8];          /* bias measure of the 6- and 8-moment sets */
     int storage;                   /* 0, 1 float16, 2 bfloat16 (normalised trig moments) */
     double trig_zone;
+    const double* given_moments;   /* NULL, or per listed pixel the global moments stage two uses */
 } vol_t;
 
 #define ORC_MAX_NM 9
@@ -1070,6 +1071,20 @@ int orc_render_grid(const orc_grid* g, const orc_view* V,
                             exact_rgba, sortlast_rgba, nsamples, NULL);
 }
 
+/* Stage two (Alg. 1 loop 2, Sec. 4.2) of the listed pixels from given global
+ * moments instead of the ones stage one finds: given_moments holds per pixel
+ * the moments in the order of `moments` (b0, then b1.. for power moments, or
+ * b0, Re t1, Im t1, .. for trigonometric moments, t_j un-normalised).  The
+ * samples, their colours and the blend are the oracle's own. */
+int orc_render_grid_given(const orc_grid* g, const orc_view* V, const int64_t* pixels, int64_t n_pixels,
+                          const double* given_moments, double* mboit_rgba, double* raw_rgba)
+{
+    vol_t v;
+    if (!given_moments || grid_vol(g, &v) != 0) return -1;
+    v.given_moments = given_moments;
+    return render_impl(&v, V, pixels, n_pixels, NULL, NULL, NULL, mboit_rgba, raw_rgba, NULL, NULL, NULL, NULL);
+}
+
 int orc_render_grid_segments(const orc_grid* g, const orc_view* V,
                              const int64_t* pixels, int64_t n_pixels,
                              double* sortlast_rgba, int64_t* nsegments)
@@ -1152,6 +1167,8 @@ static int render_impl(const vol_t* g, const orc_view* V,
         double ms[ORC_MAX_NM];
         memcpy(ms, m, sizeof m);
         store_moments(g, ms);
+        /* stage two from given global moments (as stored by another renderer) */
+        if (g->given_moments) memcpy(ms, g->given_moments + (size_t)NM * n, (size_t)NM * sizeof(double));
 
         /* stage two (Sec. 4.2): each piece blends its own samples with the
          * transmittance reconstructed from the (stored) global moments */

@@ -193,6 +193,12 @@ int orc_tet_locate(const orc_tet* m, const float* points, int64_t n, int32_t* te
 int orc_split_cells(const float* verts, int64_t n_verts, const int32_t* cells, const int32_t* types, int64_t n_cells,
                     int32_t quantum_log2, int32_t* tets_out, int64_t* cell_of_tet, int64_t max_tets, int64_t* n_tets);
 
+/* Stage two of the listed pixels of a grid from given global moments
+ * (per pixel in the order of orc_render_grid's `moments`); writes the
+ * renormalised image and / or the raw sum.  Returns -1 on bad arguments. */
+int orc_render_grid_given(const orc_grid* g, const orc_view* V, const int64_t* pixels, int64_t n_pixels,
+                          const double* given_moments, double* mboit_rgba, double* raw_rgba);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,7 +10,13 @@ format, the oracle in FP64: the stored values may differ by one unit in the
 last place of the format (2^-11 for float16 at |tau| < 1, 2^-8 for bfloat16),
 which moves A by about that much and the renormalised colour by at most
 b0 times it: the images must agree to 3e-3 (float16) and 2e-2 (bfloat16),
-b0 is float32 in both, and the moment planes within one 16-bit unit."""
+b0 is float32 in both, and the moment planes within one 16-bit unit.
+(3) The two error sources apart: the oracle's stage two run on the GPU's own
+stored 16-bit moments (oracle.render_grid_given) leaves only the FP32
+arithmetic of the bound, |dA| <= 2e-4, so each T_k moves by a relative
+b0 * 2e-4 at most and the renormalised colour, a ratio of two T-weighted sums
+times the exact alpha, by at most twice that: |d rgb| <= 4e-4 b0 per pixel
+(alpha exact), for both formats."""
 import copy
 
 import numpy as np
@@ -150,8 +156,17 @@ def test_trig_frame_matches_oracle(pkg, ms, n, st):
     hit = ref["moments"][:, 0] > 0
     tau_ref = (ref["moments"][:, 1::2] + 1j * ref["moments"][:, 2::2])[hit] / ref["moments"][hit, 0:1]
     assert np.abs(tau[hit] - tau_ref).max() <= 1.5 * ULP[st]
-    err = np.abs(col.view(-1, 4).cpu().numpy() - ref["mboit"]).max()
+    img = col.view(-1, 4).cpu().numpy().astype(np.float64)
+    err = np.abs(img - ref["mboit"]).max()
     assert err <= IMG_TOL[st], err
+    # stage two of the oracle on the GPU's stored moments: the arithmetic alone
+    given = np.zeros((npx, 1 + 2 * n))
+    given[:, 0] = b0
+    given[:, 1::2] = (tau * b0[:, None]).real
+    given[:, 2::2] = (tau * b0[:, None]).imag
+    same = oracle.render_grid_given(sc, given)["mboit"]
+    bound = 4e-4 * b0[:, None] + 1e-6
+    assert np.all(np.abs(img - same) <= bound), np.abs(img - same).max()
     vol.close()
 
 

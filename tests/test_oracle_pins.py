@@ -1055,3 +1055,36 @@ def test_render_one_and_two_absorbers_closed_form(w0):
     # the closed form really distinguishes the cases: swapped order changes colour
     if w0 == W0:
         assert np.abs(r["raw"][0] - r["raw"][absorbers.index(("B", "A"))]).max() > 0.05
+
+
+@pytest.mark.parametrize("w0", [0.0, W0])
+def test_stage_two_from_given_moments(w0):
+    """Stage two from given global moments: the closed-form moments of the
+    one- and two-absorber rays reproduce the closed-form image, and moments
+    of other absorbers change it as the bound says (here: the absorbers'
+    weights swapped between front and back)."""
+    sc, pix, absorbers = small.two_absorber_scene(w0)
+    given = []
+    for ab in absorbers:
+        a = [_absorber_values(x)[0] for x in ab]
+        z = [-1.0, 1.0][:len(ab)]
+        given.append([sum(ak * zk ** j for ak, zk in zip(a, z)) for j in range(5)])
+    given = np.array(given)
+    r = oracle.render_grid_given(sc, given, pixels=pix)
+    for n, ab in enumerate(absorbers):
+        C, b0 = _closed_form_raw(ab, w0)
+        np.testing.assert_allclose(r["raw"][n], C, rtol=0, atol=1e-13)
+    # two-absorber rays with the front / back absorbances swapped in the moments:
+    # the front sample now sees w0 a_back, the back one a_back + w0 a_front
+    n2 = [n for n, ab in enumerate(absorbers) if len(ab) == 2]
+    sw = given.copy()
+    for n in n2:
+        a = [_absorber_values(x)[0] for x in absorbers[n]]
+        sw[n] = [sum(ak * zk ** j for ak, zk in zip(a[::-1], [-1.0, 1.0])) for j in range(5)]
+    r2 = oracle.render_grid_given(sc, sw, pixels=pix)
+    for n in n2:
+        (fa, falpha, frgb), (ba, balpha, brgb) = [_absorber_values(x) for x in absorbers[n]]
+        Tf = math.exp(-w0 * ba)
+        Tb = math.exp(-ba - w0 * fa)
+        want = Tf * falpha * np.append(frgb, 1.0) + Tb * balpha * np.append(brgb, 1.0)
+        np.testing.assert_allclose(r2["raw"][n], want, rtol=0, atol=1e-13)
