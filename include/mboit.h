@@ -340,17 +340,24 @@ MBOIT_API mboit_status mboit_render_frame_host(mboit_volume v, const float* fiel
  * microseconds to tens of microseconds); when one fails, the passes launched
  * after it return at entry, so no out-of-range index is ever used and the
  * images of that render are not valid.  The error word is cleared when
- * reported.  (The kernels have no waits, so MBOIT_ERR_TIMEOUT is not
- * produced.)  The paper has no counterpart. */
+ * reported.  MBOIT_ERR_TIMEOUT (reported first when both apply) when a
+ * grid kernel's TMA window load (tuning configuration 5) did not complete
+ * within its wait limit, about a second: the warp that gave up waits once
+ * more, bounded, for the copy in flight and stops, so the images of that
+ * render are not valid.  The paper has no counterpart. */
 MBOIT_API mboit_status mboit_synchronize(mboit_volume v, void* stream);
 
 /* Test hook of the failure detection above; the paper has no counterpart.
  * Overwrites a table the library owns, after the volume was validated:
  * what = 1 (octree) sets every finest-brick map entry to a value that is no
  * leaf id; what = 2 (mesh) sets every tet's neighbour
- * across face 0 to a value that is no tet id.  The volume stays corrupt
- * (destroy it afterwards); renders then report MBOIT_ERR_DEVICE_ASSERT from
- * mboit_synchronize.  MBOIT_ERR_INVALID_ARG for another kind or `what`.
+ * across face 0 to a value that is no tet id; renders then report
+ * MBOIT_ERR_DEVICE_ASSERT from mboit_synchronize.  what = 3 (grid) makes
+ * every TMA window load (tuning configuration 5) arm its barrier without
+ * issuing the copy, so each wait runs to its limit (a completion that
+ * nothing delivers; no copy is left in flight); renders with configuration
+ * 5 then report MBOIT_ERR_TIMEOUT.  The volume stays corrupt (destroy it
+ * afterwards).  MBOIT_ERR_INVALID_ARG for another kind or `what`.
  * Synchronous. */
 MBOIT_API mboit_status mboit_debug_corrupt(mboit_volume v, int32_t what);
 

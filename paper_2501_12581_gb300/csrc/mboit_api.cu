@@ -1295,8 +1295,12 @@ mboit_status mboit_debug_corrupt(mboit_volume v, int32_t what) {
         for (auto& n : nb)
             if (n.x >= 0) n.x = v->tet.n_tets + 7;
         MB_CUDA(cudaMemcpy(v->d_tnbrs, nb.data(), nb.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    } else if (what == 3) {
+        if (v->kind != MBOIT_GRID) return fail(MBOIT_ERR_INVALID_ARG, "what = 3 needs a grid volume");
+        // TMA window loads arm their barrier and issue no copy: every wait runs out
+        v->grid.flags |= mb::kFlagDebugNoCopy;
     } else {
-        return fail(MBOIT_ERR_INVALID_ARG, "what must be 1 (octree map) or 2 (mesh neighbours)");
+        return fail(MBOIT_ERR_INVALID_ARG, "what must be 1 (octree map), 2 (mesh neighbours) or 3 (grid TMA loads)");
     }
     drop_graphs(v);
     return MBOIT_OK;

@@ -85,6 +85,7 @@ struct TmaWin {
     uint64_t* bar;             // this warp's mbarrier
     unsigned phase;            // parity of its next completion
     int32_t* err;              // the volume's error word
+    bool no_copy;              // kFlagDebugNoCopy: arm the barrier, issue no copy
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -114,13 +115,16 @@ __device__ __forceinline__ bool tma_window(TmaWin& tw, float* win, int x, int y,
         // __syncwarp) before the copy's writes
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-            "[%5];" ::"r"(smem_addr(win)),
-            "l"(reinterpret_cast<uint64_t>(tw.map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-            : "memory");
+        if (!tw.no_copy)
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4}], [%5];" ::"r"(smem_addr(win)),
+                "l"(reinterpret_cast<uint64_t>(tw.map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+                : "memory");
     }
-    const bool ok = mbar_wait(bar, tw.phase);
+    // one verdict for the warp: lanes that saw the phase complete and a lane
+    // that gave up must not part (the caller returns on false)
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, tw.phase));
     if (!ok) {
         if ((threadIdx.x & 31) == 0) atomicOr(tw.err, kErrTmaTimeout);
         mbar_wait(bar, tw.phase);   // the copy in flight, once more, bounded
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(256, MS == 0 ? 5 : 1) k_pass1_fused(const __gr
     tma_init<Cfg>(s_bar);
     __syncthreads();
     float* win = s_win[threadIdx.x >> 5];
-    TmaWin tw{&tmap, s_bar + (Cfg::kTma ? threadIdx.x >> 5 : 0), 0u, &ctr->error};
+    TmaWin tw{&tmap, s_bar + (Cfg::kTma ? threadIdx.x >> 5 : 0), 0u, &ctr->error, (g.flags & kFlagDebugNoCopy) != 0};
     int vi, px, py, tile;
     while (next_tile(vt, &ctr->tile_next[0], vi, px, py, tile)) {
         const ViewSlot& S = vt.s[vi];
@@ -348,6 +352,9 @@ __global__ void __launch_bounds__(256) k_pass2_fused(const __grid_constant__ Gri
         s_tf[2 * i + 1] = make_float4(e1.x - e0.x, e1.y - e0.y, e1.z - e0.z, e1.w - e0.w);
     }
     __syncthreads();
+    // a pass 1 that gave up on a window load left some tiles' cache bases
+    // unwritten: nothing of this pass is valid then, and no stale base is read
+    if (kCache && (*(volatile const int32_t*)&ctr->error & kErrTmaTimeout)) return;
     float* win = s_win[threadIdx.x >> 5];
     const bool raw = (g.flags & 1u) != 0;
     int vi, px, py, tile;

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) k_frame_fused(const __grid_constant__ Gri
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     float* win = s_win[threadIdx.x >> 5];
-    TmaWin tw{&tmap, s_bar + (Cfg::kTma ? threadIdx.x >> 5 : 0), 0u, &ctr->error};
+    TmaWin tw{&tmap, s_bar + (Cfg::kTma ? threadIdx.x >> 5 : 0), 0u, &ctr->error, (g.flags & kFlagDebugNoCopy) != 0};
     const bool raw = (g.flags & 1u) != 0;
     int vi, px, py, tile;
     while (next_tile(vt, &ctr->tile_next[0], vi, px, py, tile)) {

@@ -107,7 +107,7 @@ MB_HD void cubic3(float a, float b, float c, float r[3]) {
     const float q = ffma(ffma(2.0f * a3, a3, -b), a3, c);  // 2 a3^3 - b a3 + c
     const float pm = fmin_(p, -1e-30f);
     const float m = 2.0f * fsqrt_fast(-pm * (1.0f / 3.0f));
-    const float arg = fclamp(3.0f * q / (pm * m), -1.0f, 1.0f);
+    const float arg = fclamp(fdiv_fast(3.0f * q, pm * m), -1.0f, 1.0f);
     const float th = acosf(arg) * (1.0f / 3.0f);  // th in [0, pi/3]: the fast cosine is accurate on this range
     const float k2 = 2.0943951023931957f;  // 2 pi / 3
     r[0] = ffma(m, fcos(th), -a3);
@@ -117,7 +117,7 @@ MB_HD void cubic3(float a, float b, float c, float r[3]) {
         const float s = r[i];
         const float f = ffma(ffma(s + a, s, b), s, c);
         const float df = ffma(ffma(3.0f, s, 2.0f * a), s, b);
-        if (df != 0.0f) r[i] = s - f / df;
+        if (df != 0.0f) r[i] = s - fdiv_fast(f, df);   // Newton corrects the 2-ulp quotient
     }
 }
 
@@ -143,7 +143,7 @@ MB_HD void quartic4(float a, float b, float c, float d, float r[4]) {
         cubic3(p, ffma(0.25f * p, p, -rr), -0.125f * q * q, mr);
         const float m = fmax_(fmax_(mr[0], mr[1]), fmax_(mr[2], 1e-30f));
         const float sq = fsqrt_fast(2.0f * m);
-        const float h = 0.5f * p + m, g = q / (2.0f * sq);
+        const float h = 0.5f * p + m, g = fdiv_fast(q, 2.0f * sq);
         // y^2 - sq y + (h + g) = 0 and y^2 + sq y + (h - g) = 0
         const float d1 = fsqrt_fast(fmax_(ffma(sq, sq, -4.0f * (h + g)), 0.0f));
         const float d2 = fsqrt_fast(fmax_(ffma(sq, sq, -4.0f * (h - g)), 0.0f));
@@ -155,7 +155,7 @@ MB_HD void quartic4(float a, float b, float c, float d, float r[4]) {
         for (int it = 0; it < 2; ++it) {
             const float f = ffma(ffma(ffma(s + a, s, b), s, c), s, d);
             const float df = ffma(ffma(ffma(4.0f, s, 3.0f * a), s, 2.0f * b), s, c);
-            if (df != 0.0f) s = s - f / df;
+            if (df != 0.0f) s = s - fdiv_fast(f, df);
         }
         r[i] = s;
     }

@@ -1,12 +1,19 @@
 """Failure detection through the device error word (mboit_synchronize).
 
-The kernels test every table-derived index (octree leaf ids from the
-finest-brick map, mesh tet ids from face neighbours and bin lists, bin ranges)
-before the access it would make; a bad one is reported in the volume's error
-word and the access is skipped.  Here a library-owned table is corrupted on
-the host after validation (mboit_debug_corrupt), the volume renders, and
-mboit_synchronize must report MBOIT_ERR_DEVICE_ASSERT once; no kernel reads
-outside the tables, so the context stays usable."""
+Every octree or mesh render first checks the library-owned index tables as a
+whole (octree leaf ids in the finest-brick map, mesh tet ids in face
+neighbours and bin lists, bin ranges); a bad entry is reported in the volume's
+error word and the kernels that read those tables return at entry.  Here a
+table is corrupted on the host after validation (mboit_debug_corrupt), the
+volume renders, and mboit_synchronize must report MBOIT_ERR_DEVICE_ASSERT
+once; no kernel reads outside the tables, so the context stays usable.
+
+The grid kernels' one wait, the TMA window load of tuning configuration 5, is
+bounded: the hook arms the barrier without issuing the copy (a completion that
+nothing delivers, no copy in flight), every wait runs to its limit, and
+mboit_synchronize must report MBOIT_ERR_TIMEOUT."""
+import time
+
 import numpy as np
 import pytest
 
@@ -15,6 +22,7 @@ from tests import _scenes_small as small
 
 pytestmark = pytest.mark.gpu
 
+TIMEOUT = 6
 DEVICE_ASSERT = 7
 
 
@@ -72,5 +80,44 @@ def test_corrupt_hook_rejects_wrong_kind(pkg):
     vol = pkg.Volume(sc)
     with pytest.raises(pkg.MboitError) as e:
         pkg.mboit_debug_corrupt(vol.handle, 1)
+    assert e.value.status == 1
+    vol.close()
+
+
+@pytest.mark.parametrize("launches", [1, 2])
+def test_tma_wait_limit_is_reported(pkg, launches):
+    sc = scenes.blobs64(width=48, height=40)
+    views = sc.views
+    vol = pkg.Volume(sc)
+    vol.set_tuning(5, 3)
+    vol.set_frame_launches(launches)
+    mom, col = pkg.Volume.moment_buffer(views), pkg.Volume.color_buffer(views)
+    vol.render_frame(views, mom, col)
+    vol.synchronize()
+    good = col.clone()
+    pkg.mboit_debug_corrupt(vol.handle, 3)
+    t0 = time.perf_counter()
+    vol.render_frame(views, mom, col)
+    with pytest.raises(pkg.MboitError) as e:
+        vol.synchronize()
+    waited = time.perf_counter() - t0
+    assert e.value.status == TIMEOUT and "TMA" in str(e.value)
+    assert waited < 60.0                    # two bounded waits per warp, the warps side by side
+    vol.synchronize()                       # reported once, then cleared
+    vol.close()
+    vol = pkg.Volume(sc)
+    vol.set_tuning(5, 3)
+    vol.set_frame_launches(launches)
+    vol.render_frame(views, mom, col)
+    vol.synchronize()
+    assert np.array_equal(col.cpu().numpy(), good.cpu().numpy())
+    vol.close()
+
+
+def test_tma_hook_rejects_wrong_kind(pkg):
+    sc = scenes.tet_mesh(n=4, n_pieces=2, width=8, height=8)
+    vol = pkg.Volume(sc)
+    with pytest.raises(pkg.MboitError) as e:
+        pkg.mboit_debug_corrupt(vol.handle, 3)
     assert e.value.status == 1
     vol.close()
