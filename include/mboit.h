@@ -221,7 +221,7 @@ typedef struct {
  * stages, per warp, the block of the field its 32 rays traverse over the
  * next S lattice steps in shared memory; configurations differ in block
  * shape, S and load width.  All give bit-identical results. */
-#define MBOIT_NUM_TUNINGS 6
+#define MBOIT_NUM_TUNINGS 7
 
 /* Message of the last failing call on this thread ("" if none). */
 MBOIT_API const char* mboit_last_error(void);
@@ -341,7 +341,7 @@ MBOIT_API mboit_status mboit_render_frame_host(mboit_volume v, const float* fiel
  * after it return at entry, so no out-of-range index is ever used and the
  * images of that render are not valid.  The error word is cleared when
  * reported.  MBOIT_ERR_TIMEOUT (reported first when both apply) when a
- * grid kernel's TMA window load (tuning configuration 5) did not complete
+ * grid kernel's TMA window load (tuning configurations 5, 6) did not complete
  * within its wait limit, about a second: the warp that gave up waits once
  * more, bounded, for the copy in flight and stops, so the images of that
  * render are not valid.  The paper has no counterpart. */
@@ -353,7 +353,7 @@ MBOIT_API mboit_status mboit_synchronize(mboit_volume v, void* stream);
  * leaf id; what = 2 (mesh) sets every tet's neighbour
  * across face 0 to a value that is no tet id; renders then report
  * MBOIT_ERR_DEVICE_ASSERT from mboit_synchronize.  what = 3 (grid) makes
- * every TMA window load (tuning configuration 5) arm its barrier without
+ * every TMA window load (tuning configurations 5, 6) arm its barrier without
  * issuing the copy, so each wait runs to its limit (a completion that
  * nothing delivers; no copy is left in flight); renders with configuration
  * 5 then report MBOIT_ERR_TIMEOUT.  The volume stays corrupt (destroy it
@@ -379,11 +379,12 @@ MBOIT_API mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* v
                                              int32_t* segments_per_pixel, void* stream);
 
 /* Selects the window configuration (0 .. MBOIT_NUM_TUNINGS-1) of the fused
- * pass 1 and pass 2.  Configurations 2-5 read 16-byte chunks and need
- * dims[0] % 4 == 0 and a 16-byte aligned field; configuration 5 is
- * configuration 3's window (16 x 8 x 8 floats) filled in pass 1 by one TMA
- * tensor copy per warp (cp.async.bulk.tensor.3d from the field's tensor map,
- * completed on an mbarrier; pass 2 takes configuration 3) and also needs the
+ * pass 1 and pass 2.  Configurations 2-6 read 16-byte chunks and need
+ * dims[0] % 4 == 0 and a 16-byte aligned field; configurations 5 and 6 fill
+ * pass 1's window by one TMA tensor copy per warp (cp.async.bulk.tensor.3d
+ * from the field's tensor map, completed on an mbarrier; pass 2 takes
+ * configuration 3): 5 with configuration 3's 16 x 8 x 8 floats, 6 with 12 x
+ * 11 x 8, whose dense layout spreads shared-memory banks; both also need the
  * driver's tensor-map encoder; otherwise MBOIT_ERR_INVALID_ARG and nothing
  * changes.  Every configuration gives the same bits.  Takes effect for the
  * next call; captured frame graphs are re-recorded. */
@@ -407,16 +408,17 @@ MBOIT_API mboit_status mboit_set_packet(mboit_volume v, int32_t packet);
 
 /* Autotuner (the batching pattern's tuner): for each ray packet, times every
  * eligible window configuration of pass 1 and of pass 2 on these views (3
- * launches each, CUDA events on `stream`, after one warm launch), and keeps
- * the packet with the smallest sum of its fastest pass-1 and pass-2 times
- * and those two configurations.  For volumes with four power moments it
- * then times, on that packet and with the frame's sample cache, the frame
- * in those two launches against one launch (mboit_set_frame_launches) in
- * each eligible configuration, and keeps the faster form (in one launch, the
- * configuration found there is pass 1's).  Writes pass 1's, pass 2's
- * configuration and the packet to chosen[0..2] (HOST, may be NULL); the form
- * is in mboit_stats.frame_launches.  The buffers are as for
- * mboit_render_frame and are overwritten.  Synchronous. */
+ * launches each, CUDA events on `stream`, after one warm launch) and takes
+ * the fastest of each.  For volumes with four power moments it then times,
+ * on the same packet and with the frame's sample cache, the frame in those
+ * two launches against one launch (mboit_set_frame_launches) in each
+ * eligible configuration, and keeps the packet and form of the fastest
+ * frame (in one launch, the configuration found there is pass 1's); for
+ * other moment sets, the packet with the smallest sum of its pass-1 and
+ * pass-2 times.  Writes pass 1's, pass 2's configuration and the packet to
+ * chosen[0..2] (HOST, may be NULL); the form is in
+ * mboit_stats.frame_launches.  The buffers are as for mboit_render_frame
+ * and are overwritten.  Synchronous. */
 MBOIT_API mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch,
                                       float* rgba, void* stream, int32_t* chosen);
 

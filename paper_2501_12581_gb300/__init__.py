@@ -40,7 +40,7 @@ EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume
             "mboit_render_moments_noalloc", "mboit_set_tuning", "mboit_set_packet", "mboit_set_frame_launches",
             "mboit_autotune",
             "mboit_render_sortlast", "mboit_split_cells", "mboit_debug_corrupt"]
-MBOIT_NUM_TUNINGS = 6
+MBOIT_NUM_TUNINGS = 7
 
 
 class MboitError(RuntimeError):

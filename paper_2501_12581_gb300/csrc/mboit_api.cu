@@ -95,7 +95,7 @@ struct mboit_volume_s {
     bool frame_timed = false;
     std::vector<GraphEntry> graphs;
     int32_t tune1 = 0, tune2 = 0;
-    CUtensorMap field_map;      // grids: the field's tensor map for TMA windows (configuration 5)
+    CUtensorMap field_map[2];   // grids: the field's tensor maps for TMA windows (configurations 5 and 6)
     bool has_field_map = false;
     int32_t packet = MBOIT_PACKET_8X4;
     int32_t frame_launches = 2;  // 1: one launch per frame (four power moments)
@@ -509,11 +509,13 @@ mboit_status prepare_tets(const mboit_volume_desc* d, TetHost& h) {
 // The batched (fused, persistent) passes of the volume's kind.  `cache`:
 // mesh sample values shared by the two passes of one frame.
 // The field's tensor map of a grid volume, or NULL (no TMA windows).
-const CUtensorMap* field_map_of(mboit_volume v) { return v->has_field_map ? &v->field_map : nullptr; }
+const CUtensorMap* field_map_of(mboit_volume v, int cfg) {
+    return v->has_field_map && (cfg == 5 || cfg == 6) ? &v->field_map[cfg - 5] : nullptr;
+}
 
 // Whether window configuration cfg can run on this volume.
 bool config_usable(mboit_volume v, int cfg) {
-    return mb::stage_config_eligible(v->grid, cfg) && (cfg != 5 || v->has_field_map);
+    return mb::stage_config_eligible(v->grid, cfg) && ((cfg != 5 && cfg != 6) || v->has_field_map);
 }
 
 // Checks the octree's or mesh's index tables on stream s before passes that
@@ -530,7 +532,8 @@ cudaError_t pass1_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTab
     if (e != cudaSuccess) return e;
     if (v->kind == MBOIT_AMR) return mb::launch_pass1_amr(v->amr, v->d_tf, mask, vt, moments, v->d_ctr, s, tc);
     if (v->kind == MBOIT_TET) return mb::launch_pass1_tet(v->tet, v->d_tf, mask, vt, moments, v->d_ctr, s, tc);
-    return mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1, tc, field_map_of(v));
+    return mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments, v->d_ctr, s, v->tune1, tc,
+                                  field_map_of(v, v->tune1));
 }
 
 cudaError_t pass2_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTable& vt, const void* moments,
@@ -554,7 +557,7 @@ cudaError_t frame_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTab
     if (v->kind == MBOIT_TET)
         return mb::launch_frame_tet(v->tet, v->d_tf, mask, vt, moments, color, mb::kColorResolved, v->d_ctr, s, tc);
     return mb::launch_frame_fused(v->grid, v->d_tf, mask, vt, moments, color, mb::kColorResolved, v->d_ctr, s, cfg, tc,
-                                  field_map_of(v));
+                                  field_map_of(v, cfg));
 }
 
 // The tile-row sample cache of a frame: its exact row count for these views
@@ -823,7 +826,7 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
     // one launch where it measured faster without tuning (grids); the
     // autotuner times both forms for every kind with four power moments
     v->frame_launches = (d->kind == MBOIT_GRID && d->moment_set == MBOIT_POWER4) ? 1 : 2;
-    if (d->kind == MBOIT_GRID) v->has_field_map = mb::encode_field_map(g, &v->field_map);
+    if (d->kind == MBOIT_GRID) v->has_field_map = mb::encode_field_maps(g, v->field_map);
     if (is_amr) {
         g.field = nullptr;
         v->nbricks = d->n_leaves;  // the units of an octree are its leaves
@@ -1395,8 +1398,8 @@ mboit_status mboit_set_tuning(mboit_volume v, int32_t pass1, int32_t pass2) {
         return fail(MBOIT_ERR_INVALID_ARG, "octree and mesh volumes have one configuration (0)");
     if (v->kind == MBOIT_GRID && (!config_usable(v, pass1) || !config_usable(v, pass2)))
         return fail(MBOIT_ERR_INVALID_ARG, "tuning must be in [0, " + std::to_string(mb::kNumStageConfigs - 1) +
-                                               "]; 2-5 need dims[0] % 4 == 0 and a 16-byte aligned field, 5 also "
-                                               "the field's tensor map (TMA)");
+                                               "]; 2-6 need dims[0] % 4 == 0 and a 16-byte aligned field, 5 and 6 "
+                                               "also the field's tensor maps (TMA)");
     std::lock_guard<std::mutex> lk(v->mu);
     v->tune1 = pass1;
     v->tune2 = pass2;
@@ -1446,8 +1449,26 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
         cudaEventDestroy(e0);
         return fail(MBOIT_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
     }
+    // times `launch` (one warm-up, then 3 runs) in ms
+    auto time3 = [&](auto&& launch, float& ms) {
+        ce = launch();
+        if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = launch();
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        ms = 3.0e38f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    };
+    // Per packet: the split calls' configurations (pass 1, then pass 2 on the
+    // fastest pass 1's moments); with four power moments also the frame's
+    // form on that packet (two launches with those configurations against
+    // one launch in each eligible configuration, all with the frame's sample
+    // cache).  The packet whose frame is fastest wins (without frame forms:
+    // whose split calls are).
     float best_total = 3.0e38f;
     int best[3] = {v->tune1, v->tune2, v->packet};
+    int launches = v->frame_launches;
+    const bool forms = v->desc.moment_set == MBOIT_POWER4;
     for (int packet = MBOIT_PACKET_8X4; packet <= MBOIT_PACKET_4X8 && ce == cudaSuccess; ++packet) {
         mb::ViewTable vt;
         if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set), packet)) != MBOIT_OK) {
@@ -1460,22 +1481,16 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
         for (int pass = 0; pass < 2 && ce == cudaSuccess; ++pass) {
             for (int cfg = 0; cfg < mb::kNumStageConfigs && ce == cudaSuccess; ++cfg) {
                 if (grid ? !config_usable(v, cfg) : cfg != 0) continue;
-                auto launch = [&]() {
+                float ms;
+                time3([&]() {
                     if (!grid)
                         return pass == 0 ? pass1_batched(v, mask, vt, moments_scratch, s)
                                          : pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved, s);
                     return pass == 0 ? mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s, cfg,
-                                                              mb::TileCache{}, field_map_of(v))
+                                                              mb::TileCache{}, field_map_of(v, cfg))
                                      : mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba,
                                                               mb::kColorResolved, v->d_ctr, s, cfg);
-                };
-                ce = launch();
-                if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
-                for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = launch();
-                if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
-                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-                float ms = 0.0f;
-                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                }, ms);
                 if (ce == cudaSuccess && ms < best_ms[pass]) {
                     best_ms[pass] = ms;
                     pick[pass] = cfg;
@@ -1484,68 +1499,59 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
             // pass 2 is timed on the moments of the fastest pass 1
             if (pass == 0 && ce == cudaSuccess)
                 ce = grid ? mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s, pick[0],
-                                                   mb::TileCache{}, field_map_of(v))
+                                                   mb::TileCache{}, field_map_of(v, pick[0]))
                           : pass1_batched(v, mask, vt, moments_scratch, s);
         }
-        if (ce == cudaSuccess && best_ms[0] + best_ms[1] < best_total) {
-            best_total = best_ms[0] + best_ms[1];
-            best[0] = pick[0];
-            best[1] = pick[1];
-            best[2] = packet;
-        }
-    }
-    // The frame's form (four power moments): the two launches with the chosen
-    // configurations against one launch in each eligible configuration, all
-    // with the frame's sample cache, on the chosen packet.
-    int launches = v->frame_launches, cfg1 = best[0];
-    if (ce == cudaSuccess && v->desc.moment_set == MBOIT_POWER4) {
-        mb::ViewTable vt;
-        mb::TileCache tc;
-        st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set), best[2]);
-        if (st == MBOIT_OK) st = tile_cache(v, vt, tc);
-        if (st != MBOIT_OK) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return st;
-        }
-        if (tc.vals) {
-            float best_ms = 3.0e38f;
-            for (int form = 0; form <= mb::kNumStageConfigs && ce == cudaSuccess; ++form) {
-                // form 0: two launches; form c + 1: one launch in configuration c
-                if (form > 0 && (grid ? !config_usable(v, form - 1) : form != 1)) continue;
-                auto launch = [&]() {
-                    if (form > 0) return frame_batched(v, mask, vt, moments_scratch, rgba, s, form - 1, tc);
-                    if (!grid) {
-                        cudaError_t e = pass1_batched(v, mask, vt, moments_scratch, s, tc);
+        float total = best_ms[0] + best_ms[1];
+        int form_launches = launches, cfg1 = pick[0];
+        if (ce == cudaSuccess && forms) {
+            mb::TileCache tc;
+            st = tile_cache(v, vt, tc);
+            if (st != MBOIT_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return st;
+            }
+            if (tc.vals) {
+                total = 3.0e38f;
+                for (int form = 0; form <= mb::kNumStageConfigs && ce == cudaSuccess; ++form) {
+                    // form 0: two launches; form c + 1: one launch in configuration c
+                    if (form > 0 && (grid ? !config_usable(v, form - 1) : form != 1)) continue;
+                    float ms;
+                    time3([&]() {
+                        if (form > 0) return frame_batched(v, mask, vt, moments_scratch, rgba, s, form - 1, tc);
+                        if (!grid) {
+                            cudaError_t e = pass1_batched(v, mask, vt, moments_scratch, s, tc);
+                            return e != cudaSuccess ? e
+                                                    : pass2_batched(v, mask, vt, moments_scratch, rgba,
+                                                                    mb::kColorResolved, s, tc);
+                        }
+                        cudaError_t e = mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr,
+                                                               s, pick[0], tc, field_map_of(v, pick[0]));
                         return e != cudaSuccess ? e
-                                                : pass2_batched(v, mask, vt, moments_scratch, rgba, mb::kColorResolved,
-                                                                s, tc);
+                                                : mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch,
+                                                                         rgba, mb::kColorResolved, v->d_ctr, s, pick[1],
+                                                                         tc);
+                    }, ms);
+                    if (ce == cudaSuccess && ms < total) {
+                        total = ms;
+                        form_launches = form == 0 ? 2 : 1;
+                        cfg1 = form == 0 ? pick[0] : form - 1;
                     }
-                    cudaError_t e = mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr, s,
-                                                           best[0], tc, field_map_of(v));
-                    return e != cudaSuccess ? e
-                                            : mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch, rgba,
-                                                                     mb::kColorResolved, v->d_ctr, s, best[1], tc);
-                };
-                ce = launch();
-                if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
-                for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = launch();
-                if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
-                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-                float ms = 0.0f;
-                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
-                if (ce == cudaSuccess && ms < best_ms) {
-                    best_ms = ms;
-                    launches = form == 0 ? 2 : 1;
-                    cfg1 = form == 0 ? best[0] : form - 1;
                 }
             }
+        }
+        if (ce == cudaSuccess && total < best_total) {
+            best_total = total;
+            best[0] = cfg1;
+            best[1] = pick[1];
+            best[2] = packet;
+            launches = form_launches;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (ce != cudaSuccess) return fail(MBOIT_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
-    best[0] = cfg1;
     v->frame_launches = launches;
     v->tune1 = best[0];
     v->tune2 = best[1];

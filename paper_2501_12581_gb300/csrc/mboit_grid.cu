@@ -34,7 +34,7 @@ const void* pass2_fn(int cfg, bool sel, int ms) {
 }
 
 
-bool vec_config(int cfg) { return cfg == 2 || cfg == 3 || cfg == 4 || cfg == 5; }
+bool vec_config(int cfg) { return cfg >= 2 && cfg <= 6; }
 
 }  // namespace
 
@@ -66,7 +66,7 @@ cudaError_t launch_pass1_fused(const GridD& g, const float4* tf, const uint8_t* 
                                void* moments, Counters* ctr, cudaStream_t s, int cfg, TileCache cache,
                                const CUtensorMap* tmap) {
     if (!stage_config_eligible(g, cfg)) cfg = 0;
-    if (cfg == 5 && !tmap) cfg = 3;   // no tensor map: the same window by plain loads
+    if ((cfg == 5 || cfg == 6) && !tmap) cfg = 3;   // no tensor map: a window by plain loads
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
     if (e == cudaSuccess && cache.vals) e = cudaMemsetAsync(&ctr->cache_rows, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
@@ -83,7 +83,7 @@ cudaError_t launch_pass1_fused(const GridD& g, const float4* tf, const uint8_t* 
     return cudaLaunchKernel(fn, dim3(persistent_blocks(fn, 256, 0)), dim3(256), args, 0, s);
 }
 
-bool encode_field_map(const GridD& g, CUtensorMap* out) {
+bool encode_field_maps(const GridD& g, CUtensorMap out[2]) {
     if (!stage_config_eligible(g, 5)) return false;
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -97,14 +97,18 @@ bool encode_field_map(const GridD& g, CUtensorMap* out) {
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
     const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
     const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4};   // bytes, dims 1 and 2
-    const cuuint32_t box[3] = {(cuuint32_t)Stage5::WX, (cuuint32_t)Stage5::WY, (cuuint32_t)Stage5::WZ};
+    const cuuint32_t boxes[2][3] = {{(cuuint32_t)Stage5::WX, (cuuint32_t)Stage5::WY, (cuuint32_t)Stage5::WZ},
+                                    {(cuuint32_t)Stage6::WX, (cuuint32_t)Stage6::WY, (cuuint32_t)Stage6::WZ}};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = reinterpret_cast<Encode>(fn)(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                                                    const_cast<float*>(g.field), dims, strides, box, estr,
-                                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
+    for (int i = 0; i < 2; ++i) {
+        const CUresult r = reinterpret_cast<Encode>(fn)(out + i, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                                                        const_cast<float*>(g.field), dims, strides, boxes[i], estr,
+                                                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    return true;
 }
 
 cudaError_t launch_pass2_fused(const GridD& g, const float4* tf, const uint8_t* brick_sel, const ViewTable& vt,

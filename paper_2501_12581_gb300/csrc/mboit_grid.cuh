@@ -67,6 +67,10 @@ using Stage2 = StageCfg<6, 12, 8, 8, true>;
 using Stage3 = StageCfg<6, 16, 8, 8, true>;
 using Stage4 = StageCfg<8, 16, 8, 10, true>;
 using Stage5 = StageCfg<6, 16, 8, 8, true, true>;   // configuration 3's window by TMA
+// A TMA window keeps the box's dense layout, so its planes cannot be shifted
+// the way configuration 3's are; rows of 12 floats in planes of 11 rows (132
+// floats, 4 banks apart) spread the corner gathers' banks about as well.
+using Stage6 = StageCfg<6, 12, 11, 8, true, true>;
 
 // ------------------------------------------------------------------------
 // TMA window loads.  One lane of the warp arms the warp's mbarrier with the
@@ -390,8 +394,8 @@ const void* pass1_fn_ms(int cfg, bool sel) {
     if (sel) return (const void*)k_pass1_fused<true, Stage0, MS, kC>;
     if constexpr (MS != 0) {
         // other moment sets: configurations 0 and 3 only
-        return cfg == 3 || cfg == 5 ? (const void*)k_pass1_fused<false, Stage3, MS, kC>
-                                    : (const void*)k_pass1_fused<false, Stage0, MS, kC>;
+        return cfg == 3 || cfg == 5 || cfg == 6 ? (const void*)k_pass1_fused<false, Stage3, MS, kC>
+                                                : (const void*)k_pass1_fused<false, Stage0, MS, kC>;
     } else {
         switch (cfg) {
             case 1: return (const void*)k_pass1_fused<false, Stage1, MS, kC>;
@@ -399,6 +403,7 @@ const void* pass1_fn_ms(int cfg, bool sel) {
             case 3: return (const void*)k_pass1_fused<false, Stage3, MS, kC>;
             case 4: return (const void*)k_pass1_fused<false, Stage4, MS, kC>;
             case 5: return (const void*)k_pass1_fused<false, Stage5, MS, kC>;
+            case 6: return (const void*)k_pass1_fused<false, Stage6, MS, kC>;
             default: return (const void*)k_pass1_fused<false, Stage0, MS, kC>;
         }
     }
@@ -409,14 +414,15 @@ const void* pass2_fn_ms(int cfg, bool sel) {
     if (sel) return (const void*)k_pass2_fused<true, Stage0, MS, kC>;
     if constexpr (MS != 0) {
         // other moment sets: configurations 0 and 3 only
-        return cfg == 3 || cfg == 5 ? (const void*)k_pass2_fused<false, Stage3, MS, kC>
-                                    : (const void*)k_pass2_fused<false, Stage0, MS, kC>;
+        return cfg == 3 || cfg == 5 || cfg == 6 ? (const void*)k_pass2_fused<false, Stage3, MS, kC>
+                                                : (const void*)k_pass2_fused<false, Stage0, MS, kC>;
     } else {
         switch (cfg) {
             case 1: return (const void*)k_pass2_fused<false, Stage1, MS, kC>;
             case 2: return (const void*)k_pass2_fused<false, Stage2, MS, kC>;
             case 3:
-            case 5: return (const void*)k_pass2_fused<false, Stage3, MS, kC>;   // pass 2 windows without TMA
+            case 5:
+            case 6: return (const void*)k_pass2_fused<false, Stage3, MS, kC>;   // pass 2 windows without TMA
             case 4: return (const void*)k_pass2_fused<false, Stage4, MS, kC>;
             default: return (const void*)k_pass2_fused<false, Stage0, MS, kC>;
         }

@@ -98,6 +98,7 @@ const void* frame_fn(int cfg, bool sel) {
         case 3: return (const void*)k_frame_fused<false, Stage3>;
         case 4: return (const void*)k_frame_fused<false, Stage4>;
         case 5: return (const void*)k_frame_fused<false, Stage5>;
+        case 6: return (const void*)k_frame_fused<false, Stage6>;
         default: return (const void*)k_frame_fused<false, Stage0>;
     }
 }
@@ -122,7 +123,7 @@ cudaError_t launch_frame_fused(const GridD& g, const float4* tf, const uint8_t* 
                                void* moments, float* color, int32_t mode, Counters* ctr, cudaStream_t s, int cfg,
                                TileCache cache, const CUtensorMap* tmap) {
     if (!stage_config_eligible(g, cfg)) cfg = 0;
-    if (cfg == 5 && !tmap) cfg = 3;
+    if ((cfg == 5 || cfg == 6) && !tmap) cfg = 3;
     cudaError_t e = cudaMemsetAsync(&ctr->tile_next[0], 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&ctr->cache_rows, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;

@@ -122,7 +122,7 @@ struct TileCache {
 // nx % 4 == 0 and a 16-byte aligned field; 0 and 1 work everywhere.
 // Configuration 5 is configuration 3's window filled by a TMA tensor copy in
 // pass 1 (pass 2 takes configuration 3); it needs the field's tensor map.
-constexpr int kNumStageConfigs = 6;
+constexpr int kNumStageConfigs = 7;
 bool stage_config_eligible(const GridD& g, int cfg);
 
 // Loads all kernels and caches launch shapes (call before any capture).
@@ -146,7 +146,7 @@ cudaError_t launch_frame_fused(const GridD& g, const float4* tf, const uint8_t* 
 // The field's tensor map for TMA windows (dims nx, ny, nz floats, box of
 // configuration 5's window); false when the driver offers no encoder or the
 // field does not qualify (nx % 4, alignment).
-bool encode_field_map(const GridD& g, CUtensorMap* out);
+bool encode_field_maps(const GridD& g, CUtensorMap out[2]);
 // Rows a frame's tile cache needs over the domain box of `g` (sum over the
 // ray tiles of kmax - kmin + 1), added to *rows.
 cudaError_t launch_tile_rows(const GridD& g, const ViewTable& vt, unsigned long long* rows, cudaStream_t s);

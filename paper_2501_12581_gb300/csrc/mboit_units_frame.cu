@@ -77,9 +77,9 @@ __global__ void __launch_bounds__(256, FrameMinBlocks<V>::value) k_frame_unit(
         __syncwarp();  // the rows' stores before any lane reads them
         if (base >= 0) {
             if (tagged)
-                blend_rows<true, true, kUnitRowChunk>(g, cache.vals + base * 32, kmin, kmax, k0, k1, buf, body, tmask);
+                blend_rows<true, true, kRowChunk>(g, cache.vals + base * 32, kmin, kmax, k0, k1, buf, body, tmask);
             else
-                blend_rows<RowsChecked<V, kSel>::value, false, kUnitRowChunk>(g, cache.vals + base * 32, kmin, kmax,
+                blend_rows<RowsChecked<V, kSel>::value, false, kRowChunk>(g, cache.vals + base * 32, kmin, kmax,
                                                                                k0, k1, buf, body);
         } else {
             march_unit<kSel>(a, sel, o, d, k0, k1, body);

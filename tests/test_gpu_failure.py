@@ -8,8 +8,8 @@ table is corrupted on the host after validation (mboit_debug_corrupt), the
 volume renders, and mboit_synchronize must report MBOIT_ERR_DEVICE_ASSERT
 once; no kernel reads outside the tables, so the context stays usable.
 
-The grid kernels' one wait, the TMA window load of tuning configuration 5, is
-bounded: the hook arms the barrier without issuing the copy (a completion that
+The grid kernels' one wait, the TMA window load of tuning configurations 5
+and 6, is bounded: the hook arms the barrier without issuing the copy (a completion that
 nothing delivers, no copy in flight), every wait runs to its limit, and
 mboit_synchronize must report MBOIT_ERR_TIMEOUT."""
 import time
@@ -84,12 +84,13 @@ def test_corrupt_hook_rejects_wrong_kind(pkg):
     vol.close()
 
 
+@pytest.mark.parametrize("cfg", [5, 6])
 @pytest.mark.parametrize("launches", [1, 2])
-def test_tma_wait_limit_is_reported(pkg, launches):
+def test_tma_wait_limit_is_reported(pkg, launches, cfg):
     sc = scenes.blobs64(width=48, height=40)
     views = sc.views
     vol = pkg.Volume(sc)
-    vol.set_tuning(5, 3)
+    vol.set_tuning(cfg, 3)
     vol.set_frame_launches(launches)
     mom, col = pkg.Volume.moment_buffer(views), pkg.Volume.color_buffer(views)
     vol.render_frame(views, mom, col)
@@ -106,7 +107,7 @@ def test_tma_wait_limit_is_reported(pkg, launches):
     vol.synchronize()                       # reported once, then cleared
     vol.close()
     vol = pkg.Volume(sc)
-    vol.set_tuning(5, 3)
+    vol.set_tuning(cfg, 3)
     vol.set_frame_launches(launches)
     vol.render_frame(views, mom, col)
     vol.synchronize()
