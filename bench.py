@@ -413,6 +413,7 @@ def main():
     ap.add_argument("--no-per-piece", action="store_true")
     ap.add_argument("--no-sortlast", action="store_true")
     ap.add_argument("--no-gear", action="store_true", help="skip the gear-teeth stress test")
+    ap.add_argument("--no-multi", action="store_true", help="skip the multi-volume frame")
     ap.add_argument("--gear-k", default="8,16,32,64,128", help="piece counts of the gear-teeth stress test")
     ap.add_argument("--heatmap", default="", help="directory for the gear-teeth segments-per-pixel images (PGM)")
     ap.add_argument("--ncu-record", nargs=4, metavar=("CSV", "KERNEL", "SAMPLES", "OUT"),
@@ -717,6 +718,48 @@ def main():
     tets = unit_block("tets") if headline and not args.no_tets else None
     mixed = unit_block("mixed") if headline and not args.no_tets else None
 
+    # several independent volumes in one persistent launch per pass: 8 grids
+    # of 64^3 (the blobs64 field flipped and scaled per volume, one transfer
+    # function), one 256^2 view each, against 8 single-volume frames
+    multi = None
+    if headline and not args.no_multi:
+        import dataclasses
+        import scenes as _scenes
+        base = _scenes.blobs64()
+        mscs = []
+        for i in range(8):
+            f = np.ascontiguousarray(np.flip(base.field, axis=i % 3) * np.float32(1.0 - 0.05 * i)).astype(np.float32)
+            mscs.append(dataclasses.replace(base, name=f"blobs64_{i}", field=f,
+                                            tf_range=(np.float32(f.min()), np.float32(f.max()))))
+        mvols = [pkg.Volume(s_) for s_ in mscs]
+        mviews = [_scenes.ortho_view(base.dims, (0.62 - 0.05 * i, 0.48, 0.62), 256, 256) for i in range(8)]
+        mmom, mrgba = pkg.Volume.moment_buffer(mviews), pkg.Volume.color_buffer(mviews)
+        owner = list(range(8))
+        mframe = lambda: pkg.Volume.render_frame_multi(mvols, mviews, owner, mmom, mrgba)  # noqa: E731
+        singles = [(mv, [vw], pkg.Volume.moment_buffer([vw]), pkg.Volume.color_buffer([vw]))
+                   for mv, vw in zip(mvols, mviews)]
+
+        def sframes():
+            for mv, vw, m_, c_ in singles:
+                mv.render_frame(vw, m_, c_)
+        for _ in range(3):
+            mframe()
+            sframes()
+        ms_m = timed(mframe, 20)
+        ms_s = timed(sframes, 20)
+        mframe()
+        mvols[0].synchronize()
+        sm = mvols[0].stats()["samples_pass1"]
+        multi = {"volumes": 8, "field": "64x64x64 float32 each", "image": "256x256 per volume",
+                 "samples_per_frame": sm, "multi_ms_per_frame": ms_m, "multi_gsamples_per_s": sm / (ms_m * 1e-3) / 1e9,
+                 "launches_per_frame": 2, "single_volume_frames_ms": ms_s,
+                 "single_volume_launches": sum(1 if mv.stats()["frame_launches"] == 1 else 2 for mv in mvols),
+                 "speedup_of_one_launch_per_pass": ms_s / ms_m}
+        for mv in mvols:
+            mv.close()
+        del mvols, singles, mmom, mrgba
+        torch.cuda.empty_cache()
+
     # the gear-teeth stress test of Sec. 5: K pieces of 4 interleaved layers,
     # batched MBOIT against the exact sort-last baseline as K grows
     gear = None
@@ -858,6 +901,7 @@ def main():
            "per_piece_fp32": per_piece, "sortlast_gpu": sortlast, "adaptive_step": adaptive,
            "grid_512_64_pieces": grid, "tets_72_pieces": tets, "mixed_cells_72_pieces": mixed,
            "gear_teeth_stress": gear,
+           "multi_volume_8_grids": multi,
            "precision_sweep_amr_2048": sweep,
            "quality": quality, "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
            "gpu_launches": launches * args.steps, "clocks": clk.summary()}

@@ -36,7 +36,8 @@ MBOIT_FLAG_RAW_SUM, MBOIT_FLAG_DETERMINISTIC, MBOIT_FLAG_ADAPTIVE_STEP = 0x1, 0x
 
 EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume", "mboit_destroy_volume",
             "mboit_add_piece", "mboit_render_moments", "mboit_reconstruct_blend", "mboit_composite",
-            "mboit_render_frame", "mboit_render_frame_host", "mboit_synchronize", "mboit_get_stats",
+            "mboit_render_frame", "mboit_render_frame_host", "mboit_render_frame_multi", "mboit_synchronize",
+            "mboit_get_stats",
             "mboit_render_moments_noalloc", "mboit_set_tuning", "mboit_set_packet", "mboit_set_frame_launches",
             "mboit_autotune",
             "mboit_render_sortlast", "mboit_split_cells", "mboit_debug_corrupt"]
@@ -99,6 +100,7 @@ def load_library(path=LIB_PATH):
         "mboit_composite": (ctypes.c_int, [P, I32, I32, I32, I32, I32, P, P, P, P, P]),
         "mboit_render_frame": (ctypes.c_int, [P, P, I32, P, P, P]),
         "mboit_render_frame_host": (ctypes.c_int, [P, P, P, I32, P, P, P, P]),
+        "mboit_render_frame_multi": (ctypes.c_int, [P, I32, P, P, I32, P, P, P]),
         "mboit_synchronize": (ctypes.c_int, [P, P]),
         "mboit_get_stats": (ctypes.c_int, [P, P]),
         "mboit_render_moments_noalloc": (ctypes.c_int, [P, P, P, I32, P, P]),
@@ -246,6 +248,19 @@ def mboit_composite(v, op, width, height, n_views, n_inputs, inp, out, global_mo
 def mboit_render_frame(v, views, moments_scratch, rgba, stream=None):
     arr, n = _views(views)
     _check(load_library().mboit_render_frame(v, arr, n, _ptr(moments_scratch), _ptr(rgba), _stream(stream)))
+
+
+def mboit_render_frame_multi(vols, views, view_volume, moments_scratch, rgba, stream=None):
+    """One frame over several grid volumes: view i samples vols[view_volume[i]]."""
+    vols = list(vols)
+    handles = (ctypes.c_void_p * len(vols))(*vols)
+    arr, n = _views(views)
+    vv = list(view_volume)
+    if len(vv) != n:
+        raise ValueError(f"view_volume has {len(vv)} entries for {n} views")
+    owner = (ctypes.c_int32 * n)(*vv)
+    _check(load_library().mboit_render_frame_multi(handles, len(vols), arr, owner, n, _ptr(moments_scratch),
+                                                   _ptr(rgba), _stream(stream)))
 
 
 def mboit_render_frame_host(v, field_host, views, moments_scratch, rgba_device, rgba_host, stream=None):
@@ -455,6 +470,11 @@ class Volume:
 
     def render_frame(self, views, moments_scratch, rgba, stream=None):
         mboit_render_frame(self.handle, views, moments_scratch, rgba, stream)
+
+    @staticmethod
+    def render_frame_multi(volumes, views, view_volume, moments_scratch, rgba, stream=None):
+        """One frame over several grid volumes (view i samples volumes[view_volume[i]])."""
+        mboit_render_frame_multi([v.handle for v in volumes], views, view_volume, moments_scratch, rgba, stream)
 
     def synchronize(self, stream=None):
         mboit_synchronize(self.handle, stream)

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -82,6 +83,7 @@ struct mboit_volume_s {
     int64_t nbricks = 0;
     size_t field_bytes = 0;
     float4* d_tf = nullptr;
+    std::vector<float4> tf_host;   // the converted table as uploaded (multi-volume frames compare them)
     int32_t* d_pob = nullptr;
     uint8_t* d_sel = nullptr;
     mb::Counters* d_ctr = nullptr;
@@ -564,6 +566,8 @@ cudaError_t frame_batched(mboit_volume v, const uint8_t* mask, const mb::ViewTab
 // (one small kernel, synchronous; done once per recorded frame graph), then
 // grow-only buffers.  Left off (c.vals NULL, pass 2 marches again) when the
 // device lacks the memory with 1 GiB to spare.
+mboit_status cache_buffers(mboit_volume v, unsigned long long rows, int32_t total_tiles, mb::TileCache& c);
+
 mboit_status tile_cache(mboit_volume v, const mb::ViewTable& vt, mb::TileCache& c) {
     c = mb::TileCache{};
     cudaStream_t cs = v->cap_stream;
@@ -573,7 +577,14 @@ mboit_status tile_cache(mboit_volume v, const mb::ViewTable& vt, mb::TileCache& 
     unsigned long long rows = 0;
     MB_CUDA(cudaMemcpyAsync(&rows, v->d_rows, sizeof rows, cudaMemcpyDeviceToHost, cs));
     MB_CUDA(cudaStreamSynchronize(cs));
-    const size_t nvals = (size_t)rows * 32, ntiles = (size_t)std::max(vt.total_tiles, 1);
+    return cache_buffers(v, rows, vt.total_tiles, c);
+}
+
+// Grow-only cache buffers of `v` for `rows` rows over `total_tiles` tiles
+// (left off, c.vals NULL, without 1 GiB to spare).
+mboit_status cache_buffers(mboit_volume v, unsigned long long rows, int32_t total_tiles, mb::TileCache& c) {
+    c = mb::TileCache{};
+    const size_t nvals = (size_t)rows * 32, ntiles = (size_t)std::max(total_tiles, 1);
     size_t free_b = 0, total_b = 0;
     MB_CUDA(cudaMemGetInfo(&free_b, &total_b));
     const size_t grow = (nvals > v->cap_tcvals ? nvals * sizeof(float) : 0) +
@@ -859,6 +870,7 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
     if (e == cudaSuccess) e = cudaMalloc(&v->d_sel, (size_t)v->nbricks);
     if (e == cudaSuccess) e = cudaMalloc(&v->d_ctr, sizeof(mb::Counters));
     if (e == cudaSuccess) e = cudaMemcpy(v->d_tf, tf.data(), 256 * sizeof(float4), cudaMemcpyHostToDevice);
+    v->tf_host = tf;
     if (e == cudaSuccess) e = cudaMemset(v->d_pob, 0xff, (size_t)v->nbricks * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(v->d_ctr, 0, sizeof(mb::Counters));
     if (e == cudaSuccess && is_amr) {
@@ -1225,6 +1237,78 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
     }
     MB_CUDA(cudaGraphLaunch(exec, static_cast<cudaStream_t>(stream)));
     v->frame_timed = true;
+    return MBOIT_OK;
+}
+
+mboit_status mboit_render_frame_multi(const mboit_volume* vols, int32_t n_vols, const mboit_view* views,
+                                      const int32_t* view_volume, int32_t n_views, void* moments_scratch, float* rgba,
+                                      void* stream) {
+    g_err.clear();
+    if (!vols || !view_volume || !moments_scratch || !rgba)
+        return fail(MBOIT_ERR_INVALID_ARG, "vols, view_volume, moments_scratch and rgba must be non-NULL");
+    if (n_vols < 1 || n_vols > mb::kMaxVolumes)
+        return fail(MBOIT_ERR_INVALID_ARG, "n_vols must be in [1, " + std::to_string(mb::kMaxVolumes) + "]");
+    for (int32_t i = 0; i < n_vols; ++i) {
+        const mboit_status st = check_volume(vols[i]);
+        if (st != MBOIT_OK) return st;
+        const mboit_volume v = vols[i];
+        const std::string at = "volume " + std::to_string(i) + ": ";
+        if (v->kind != MBOIT_GRID || v->desc.moment_set != MBOIT_POWER4 || v->desc.storage != MBOIT_STORE_F32)
+            return fail(MBOIT_ERR_UNSUPPORTED, at + "multi-volume frames take grid volumes with four float32 power moments");
+        if (v->device != vols[0]->device) return fail(MBOIT_ERR_INVALID_ARG, at + "on another device");
+        if (v->tf_host.size() != vols[0]->tf_host.size() ||
+            std::memcmp(v->tf_host.data(), vols[0]->tf_host.data(), v->tf_host.size() * sizeof(float4)) != 0)
+            return fail(MBOIT_ERR_INVALID_ARG, at + "the volumes of one frame share one transfer function and step");
+        for (int32_t j = 0; j < i; ++j)
+            if (vols[j] == v) return fail(MBOIT_ERR_INVALID_ARG, at + "listed twice");
+    }
+    for (int32_t i = 0; i < n_views && views; ++i)
+        if (view_volume[i] < 0 || view_volume[i] >= n_vols)
+            return fail(MBOIT_ERR_INVALID_ARG, "view_volume[" + std::to_string(i) + "] out of range");
+    // every volume's lock, in one global (address) order
+    std::vector<mboit_volume> order(vols, vols + n_vols);
+    std::sort(order.begin(), order.end(), std::less<mboit_volume>());
+    std::vector<std::unique_lock<std::mutex>> locks;
+    for (mboit_volume v : order) locks.emplace_back(v->mu);
+    const mboit_volume v0 = vols[0];
+    DeviceGuard dg(v0->device);
+    mb::ViewTable vt;
+    mboit_status st = build_views(views, n_views, vt, slab_bytes_per_px(MBOIT_POWER4), v0->packet);
+    if (st != MBOIT_OK) return st;
+    mb::GridTable gt;
+    std::memset(&gt, 0, sizeof gt);
+    bool vec = true;
+    for (int32_t i = 0; i < n_vols; ++i) {
+        gt.g[i] = vols[i]->grid;
+        vec = vec && mb::stage_config_eligible(gt.g[i], 3);
+    }
+    for (int32_t i = 0; i < n_views; ++i) vt.s[i].vol = view_volume[i];
+    // the sample cache: rows of every volume's views, counted per volume
+    cudaStream_t cs = v0->cap_stream;
+    if (!v0->d_rows) MB_CUDA(cudaMalloc(&v0->d_rows, sizeof(unsigned long long)));
+    MB_CUDA(cudaMemsetAsync(v0->d_rows, 0, sizeof(unsigned long long), cs));
+    for (int32_t i = 0; i < n_vols; ++i) {
+        std::vector<mboit_view> mine;
+        for (int32_t j = 0; j < n_views; ++j)
+            if (view_volume[j] == i) mine.push_back(views[j]);
+        if (mine.empty()) continue;
+        mb::ViewTable sub;
+        if ((st = build_views(mine.data(), (int32_t)mine.size(), sub, slab_bytes_per_px(MBOIT_POWER4), v0->packet)) !=
+            MBOIT_OK)
+            return st;
+        MB_CUDA(mb::launch_tile_rows(gt.g[i], sub, v0->d_rows, cs));
+    }
+    unsigned long long rows = 0;
+    MB_CUDA(cudaMemcpyAsync(&rows, v0->d_rows, sizeof rows, cudaMemcpyDeviceToHost, cs));
+    MB_CUDA(cudaStreamSynchronize(cs));
+    mb::TileCache tc;
+    if ((st = cache_buffers(v0, rows, vt.total_tiles, tc)) != MBOIT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MB_CUDA(cudaMemsetAsync(&v0->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), s));
+    MB_CUDA(cudaMemsetAsync(&v0->d_ctr->fp64_pixels, 0, sizeof(unsigned long long), s));
+    MB_CUDA(mb::launch_pass1_multi(gt, v0->d_tf, vt, moments_scratch, v0->d_ctr, s, vec, tc));
+    MB_CUDA(mb::launch_pass2_multi(gt, v0->d_tf, vt, moments_scratch, rgba, v0->d_ctr, s, vec, tc));
+    v0->frame_timed = false;
     return MBOIT_OK;
 }
 

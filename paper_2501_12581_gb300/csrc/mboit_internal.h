@@ -20,6 +20,8 @@ struct ViewSlot {
     int64_t color_off;      // float offset of this view's first RGBA image
     int32_t plane;          // pixels per moment plane (w*h rounded up to 4)
     int32_t tw_log2;        // a warp's ray tile (packet) is 2^tw_log2 x 2^(5 - tw_log2) pixels: 8 x 4 or 4 x 8
+    int32_t vol;            // multi-volume frames: the view's volume in the GridTable (else 0)
+    int32_t pad;
 };
 
 // Pixel of lane `lane` in tile `lt` of a view (tiles row-major, ntx per row).
@@ -118,10 +120,10 @@ struct TileCache {
 };
 
 // Number of shared-memory window configurations of the fused passes (the
-// autotuner's choices).  Configurations 2-5 use 16-byte loads and need
+// autotuner's choices).  Configurations 2-6 use 16-byte loads and need
 // nx % 4 == 0 and a 16-byte aligned field; 0 and 1 work everywhere.
-// Configuration 5 is configuration 3's window filled by a TMA tensor copy in
-// pass 1 (pass 2 takes configuration 3); it needs the field's tensor map.
+// Configurations 5 and 6 fill pass 1's window by a TMA tensor copy (pass 2
+// takes configuration 3); they need the field's tensor maps.
 constexpr int kNumStageConfigs = 7;
 bool stage_config_eligible(const GridD& g, int cfg);
 
@@ -147,6 +149,21 @@ cudaError_t launch_frame_fused(const GridD& g, const float4* tf, const uint8_t* 
 // configuration 5's window); false when the driver offers no encoder or the
 // field does not qualify (nx % 4, alignment).
 bool encode_field_maps(const GridD& g, CUtensorMap out[2]);
+// Several grid volumes in one persistent launch per pass (four power
+// moments, one transfer function): view slot i samples volume vt.s[i].vol.
+constexpr int kMaxVolumes = 8;
+struct GridTable {
+    GridD g[kMaxVolumes];
+};
+// The multi-volume frame's two passes: `vec` selects configuration 3's
+// window (every volume has nx % 4 == 0 and a 16-byte aligned field), else
+// configuration 0's.  Pass 1 stores the tile cache when cache.vals is set and
+// pass 2 then blends from it; results equal each volume's own frame.
+cudaError_t launch_pass1_multi(const GridTable& gt, const float4* tf, const ViewTable& vt, void* moments,
+                               Counters* ctr, cudaStream_t s, bool vec, TileCache cache);
+cudaError_t launch_pass2_multi(const GridTable& gt, const float4* tf, const ViewTable& vt, const void* moments,
+                               float* color, Counters* ctr, cudaStream_t s, bool vec, TileCache cache);
+cudaError_t prepare_multi_kernels();
 // Rows a frame's tile cache needs over the domain box of `g` (sum over the
 // ray tiles of kmax - kmin + 1), added to *rows.
 cudaError_t launch_tile_rows(const GridD& g, const ViewTable& vt, unsigned long long* rows, cudaStream_t s);

@@ -370,6 +370,7 @@ cudaError_t prepare_kernels() {
     cudaError_t e = prepare_grid_kernels();
     if (e == cudaSuccess) e = prepare_frame_kernels();
     if (e == cudaSuccess) e = prepare_frame_unit_kernels();
+    if (e == cudaSuccess) e = prepare_multi_kernels();
     if (e == cudaSuccess) e = prepare_unit_kernels();
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
