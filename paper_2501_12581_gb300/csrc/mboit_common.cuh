@@ -268,14 +268,12 @@ struct BlendBody {
         float2 wgt = __fmul2_rn(make_float2(fexp2(ex.x), fexp2(ex.y)), alpha);
         wgt.x = oka ? wgt.x : 0.0f;
         wgt.y = okb ? wgt.y : 0.0f;
-        C.x = ffma(wgt.x, rga.x, C.x);
-        C.y = ffma(wgt.x, rga.y, C.y);
-        C.z = ffma(wgt.x, bwa.x, C.z);
-        C.w += wgt.x;
-        C.x = ffma(wgt.y, rgb.x, C.x);
-        C.y = ffma(wgt.y, rgb.y, C.y);
-        C.z = ffma(wgt.y, bwb.x, C.z);
-        C.w += wgt.y;
+        // colour sums as pairs: (r, g) and (b, alpha); C.w + w = fma(w, 1, C.w)
+        float2 cxy = __ffma2_rn(make_float2(wgt.x, wgt.x), rga, make_float2(C.x, C.y));
+        float2 czw = __ffma2_rn(make_float2(wgt.x, wgt.x), make_float2(bwa.x, 1.0f), make_float2(C.z, C.w));
+        cxy = __ffma2_rn(make_float2(wgt.y, wgt.y), rgb, cxy);
+        czw = __ffma2_rn(make_float2(wgt.y, wgt.y), make_float2(bwb.x, 1.0f), czw);
+        C = make_float4(cxy.x, cxy.y, czw.x, czw.y);
         n += (unsigned)oka + (unsigned)okb;
     }
 };
