@@ -895,7 +895,8 @@ def main():
            "form": ("batched: 1 persistent kernel per frame (pass 1 then pass 2 per ray tile), CUDA graph"
                     if launches == 1 else "batched: 2 persistent kernels per frame, CUDA graph"),
            "tuning": {"pass1": tuning[0], "pass2": tuning[1],
-                      "packet": "4x8" if tuning[2] == pkg.MBOIT_PACKET_4X8 else "8x4", "frame_launches": launches},
+                      "packet": "4x8" if tuning[2] == pkg.MBOIT_PACKET_4X8 else "8x4", "frame_launches": launches,
+                      "tile_order": "longest first" if stf["tile_order"] else "raster"},
            "samples_per_frame": samples, "ms_per_frame": ms_max, "singular_pixels": st["singular_pixels"],
            "fp64_setup_pixels": st["fp64_pixels"],
            "per_piece_fp32": per_piece, "sortlast_gpu": sortlast, "adaptive_step": adaptive,

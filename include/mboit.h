@@ -215,6 +215,8 @@ typedef struct {
     int32_t packet;             /* mboit_packet in use (see mboit_set_packet) */
     int32_t frame_launches;     /* kernel launches of mboit_render_frame (see mboit_set_frame_launches);
                                  * with 1, frame_pass1_ms is that launch and frame_pass2_ms about 0 */
+    int32_t tile_order;         /* 1: frames dequeue ray tiles longest first (see mboit_set_tile_order) */
+    int32_t reserved;
 } mboit_stats;
 
 /* Number of window configurations of the fused passes.  Each fused kernel
@@ -420,6 +422,18 @@ MBOIT_API mboit_status mboit_set_tuning(mboit_volume v, int32_t pass1, int32_t p
  * kind) only, else MBOIT_ERR_UNSUPPORTED; other values MBOIT_ERR_INVALID_ARG.
  * Captured frame graphs are re-recorded. */
 MBOIT_API mboit_status mboit_set_frame_launches(mboit_volume v, int32_t launches);
+
+/* Dequeue order of the ray tiles in mboit_render_frame (the batching
+ * pattern's cost-ordered work items): 0 = tile order (views in turn, rows
+ * of tiles top to bottom), 1 = longest first: when a frame graph is
+ * recorded, one small kernel counts each ray tile's lattice rows (the rows
+ * its warp walks in lockstep, the tile's cost) and the tiles are sorted by
+ * it, so the persistent kernels start the long tiles early and end on
+ * short ones.  The order lives with the recorded graph.  Results do not
+ * depend on it; mboit_autotune times both.  Other calls keep tile order.
+ * MBOIT_ERR_INVALID_ARG for another value.  Captured frame graphs are
+ * re-recorded. */
+MBOIT_API mboit_status mboit_set_tile_order(mboit_volume v, int32_t order);
 
 /* Selects the ray packet of every pass (mboit_packet).  Results do not
  * depend on it (every ray is marched alone); speed does.  Captured frame

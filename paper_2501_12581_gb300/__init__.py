@@ -39,7 +39,7 @@ EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume
             "mboit_render_frame", "mboit_render_frame_host", "mboit_render_frame_multi", "mboit_synchronize",
             "mboit_get_stats",
             "mboit_render_moments_noalloc", "mboit_set_tuning", "mboit_set_packet", "mboit_set_frame_launches",
-            "mboit_autotune",
+            "mboit_set_tile_order", "mboit_autotune",
             "mboit_render_sortlast", "mboit_split_cells", "mboit_debug_corrupt"]
 MBOIT_NUM_TUNINGS = 7
 
@@ -74,7 +74,8 @@ class mboit_stats(ctypes.Structure):
                 ("tuning_pass1", ctypes.c_int32), ("tuning_pass2", ctypes.c_int32),
                 ("sortlast_segments", ctypes.c_int64), ("sortlast_max_segments", ctypes.c_int32),
                 ("fp64_pixels", ctypes.c_int32), ("frame_pass1_ms", ctypes.c_float), ("frame_pass2_ms", ctypes.c_float),
-                ("packet", ctypes.c_int32), ("frame_launches", ctypes.c_int32)]
+                ("packet", ctypes.c_int32), ("frame_launches", ctypes.c_int32), ("tile_order", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -107,6 +108,7 @@ def load_library(path=LIB_PATH):
         "mboit_set_tuning": (ctypes.c_int, [P, I32, I32]),
         "mboit_set_packet": (ctypes.c_int, [P, I32]),
         "mboit_set_frame_launches": (ctypes.c_int, [P, I32]),
+        "mboit_set_tile_order": (ctypes.c_int, [P, I32]),
         "mboit_autotune": (ctypes.c_int, [P, P, I32, P, P, P, P]),
         "mboit_render_sortlast": (ctypes.c_int, [P, P, I32, P, P, P]),
         "mboit_split_cells": (ctypes.c_int, [P, I64, P, P, I64, I32, P, P, P, I64, P]),
@@ -289,6 +291,10 @@ def mboit_set_packet(v, packet):
 
 def mboit_set_frame_launches(v, launches):
     _check(load_library().mboit_set_frame_launches(v, int(launches)))
+
+
+def mboit_set_tile_order(v, order):
+    _check(load_library().mboit_set_tile_order(v, int(order)))
 
 
 def mboit_autotune(v, views, moments_scratch, rgba, stream=None):
@@ -490,6 +496,9 @@ class Volume:
 
     def set_frame_launches(self, launches):
         mboit_set_frame_launches(self.handle, launches)
+
+    def set_tile_order(self, order):
+        mboit_set_tile_order(self.handle, order)
 
     def autotune(self, views, moments_scratch, rgba, stream=None):
         return mboit_autotune(self.handle, views, moments_scratch, rgba, stream)

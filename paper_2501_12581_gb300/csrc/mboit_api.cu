@@ -53,6 +53,7 @@ bool finite3(const float* a) { return std::isfinite(a[0]) && std::isfinite(a[1])
 struct GraphEntry {
     std::vector<char> key;
     cudaGraphExec_t exec = nullptr;
+    int32_t* d_order = nullptr;   // the graph's tile order (cost-ordered dequeue), or NULL
 };
 
 }  // namespace
@@ -100,6 +101,7 @@ struct mboit_volume_s {
     CUtensorMap field_map[2];   // grids: the field's tensor maps for TMA windows (configurations 5 and 6)
     bool has_field_map = false;
     int32_t packet = MBOIT_PACKET_8X4;
+    int32_t tile_order = 0;     // 1: frames dequeue their ray tiles longest first (mboit_set_tile_order)
     int32_t frame_launches = 2;  // 1: one launch per frame (four power moments)
     // sort-last baseline buffers (grow only)
     int32_t* sl_counts = nullptr;
@@ -233,8 +235,10 @@ cudaError_t ensure_capacity(T*& p, size_t& cap, size_t n) {
 }
 
 void drop_graphs(mboit_volume v) {
-    for (auto& g : v->graphs)
+    for (auto& g : v->graphs) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
+        cudaFree(g.d_order);   // after the graph: cudaFree waits for work that may still read it
+    }
     v->graphs.clear();
 }
 
@@ -578,6 +582,44 @@ mboit_status tile_cache(mboit_volume v, const mb::ViewTable& vt, mb::TileCache& 
     MB_CUDA(cudaMemcpyAsync(&rows, v->d_rows, sizeof rows, cudaMemcpyDeviceToHost, cs));
     MB_CUDA(cudaStreamSynchronize(cs));
     return cache_buffers(v, rows, vt.total_tiles, c);
+}
+
+// The frame's cost-ordered dequeue: every ray tile's row count (the rows its
+// warp walks in lockstep, k_tile_rows), then the tiles sorted by it, longest
+// first (ties in tile order), in a new device buffer the caller owns.
+// Synchronous; for graph recording and the autotuner.
+mboit_status make_tile_order(mboit_volume v, const mb::ViewTable& vt, int32_t** out) {
+    *out = nullptr;
+    const size_t n = (size_t)std::max(vt.total_tiles, 1);
+    cudaStream_t cs = v->cap_stream;
+    int32_t* d_rows = nullptr;
+    MB_CUDA(cudaMalloc(&d_rows, n * sizeof(int32_t)));
+    if (!v->d_rows) {
+        const cudaError_t e = cudaMalloc(&v->d_rows, sizeof(unsigned long long));
+        if (e != cudaSuccess) {
+            cudaFree(d_rows);
+            return fail(MBOIT_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+    }
+    std::vector<int32_t> rows(n, 0);
+    cudaError_t e = cudaMemsetAsync(d_rows, 0, n * sizeof(int32_t), cs);
+    if (e == cudaSuccess) e = mb::launch_tile_rows(v->grid, vt, v->d_rows, cs, d_rows);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rows.data(), d_rows, n * sizeof(int32_t), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    cudaFree(d_rows);
+    if (e != cudaSuccess) return fail(MBOIT_ERR_CUDA, std::string("tile order: ") + cudaGetErrorString(e));
+    std::vector<int32_t> order(n);
+    for (size_t i = 0; i < n; ++i) order[i] = (int32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return rows[a] > rows[b]; });
+    int32_t* d = nullptr;
+    MB_CUDA(cudaMalloc(&d, n * sizeof(int32_t)));
+    e = cudaMemcpy(d, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return fail(MBOIT_ERR_CUDA, std::string("tile order upload: ") + cudaGetErrorString(e));
+    }
+    *out = d;
+    return MBOIT_OK;
 }
 
 // Grow-only cache buffers of `v` for `rows` rows over `total_tiles` tiles
@@ -1207,6 +1249,9 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
     if (!exec) {
         mb::TileCache tc;
         if ((st = tile_cache(v, vt, tc)) != MBOIT_OK) return st;
+        int32_t* d_order = nullptr;
+        if (v->tile_order && (st = make_tile_order(v, vt, &d_order)) != MBOIT_OK) return st;
+        vt.order = d_order;
         cudaStream_t cs = v->cap_stream;
         MB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemsetAsync(&v->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), cs);
@@ -1227,13 +1272,17 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
         if (e != cudaSuccess || e2 != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
             cudaGetLastError();
+            cudaFree(d_order);
             return fail(MBOIT_ERR_CUDA, std::string("capturing the frame: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
         }
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return fail(MBOIT_ERR_CUDA, std::string("instantiating the frame graph: ") + cudaGetErrorString(e));
+        if (e != cudaSuccess) {
+            cudaFree(d_order);
+            return fail(MBOIT_ERR_CUDA, std::string("instantiating the frame graph: ") + cudaGetErrorString(e));
+        }
         if (v->graphs.size() >= 8) drop_graphs(v);
-        v->graphs.push_back(GraphEntry{key, exec});
+        v->graphs.push_back(GraphEntry{key, exec, d_order});
     }
     MB_CUDA(cudaGraphLaunch(exec, static_cast<cudaStream_t>(stream)));
     v->frame_timed = true;
@@ -1413,6 +1462,7 @@ mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out) {
     out->fp64_pixels = (int32_t)std::min<unsigned long long>(c.fp64_pixels, 0x7fffffffull);
     out->packet = v->packet;
     out->frame_launches = v->frame_launches;
+    out->tile_order = v->tile_order;
     out->frame_pass1_ms = out->frame_pass2_ms = -1.0f;
     if (v->frame_timed && (cudaEventElapsedTime(&out->frame_pass1_ms, v->frame_ev[0], v->frame_ev[1]) != cudaSuccess ||
                            cudaEventElapsedTime(&out->frame_pass2_ms, v->frame_ev[1], v->frame_ev[2]) != cudaSuccess)) {
@@ -1503,6 +1553,16 @@ mboit_status mboit_set_frame_launches(mboit_volume v, int32_t launches) {
     return MBOIT_OK;
 }
 
+mboit_status mboit_set_tile_order(mboit_volume v, int32_t order) {
+    g_err.clear();
+    if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
+    if (order != 0 && order != 1) return fail(MBOIT_ERR_INVALID_ARG, "order must be 0 (tile order) or 1 (longest first)");
+    std::lock_guard<std::mutex> lk(v->mu);
+    v->tile_order = order;
+    drop_graphs(v);
+    return MBOIT_OK;
+}
+
 mboit_status mboit_set_packet(mboit_volume v, int32_t packet) {
     g_err.clear();
     if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
@@ -1551,7 +1611,7 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
     // whose split calls are).
     float best_total = 3.0e38f;
     int best[3] = {v->tune1, v->tune2, v->packet};
-    int launches = v->frame_launches;
+    int launches = v->frame_launches, order = v->tile_order;
     const bool forms = v->desc.moment_set == MBOIT_POWER4;
     for (int packet = MBOIT_PACKET_8X4; packet <= MBOIT_PACKET_4X8 && ce == cudaSuccess; ++packet) {
         mb::ViewTable vt;
@@ -1587,7 +1647,7 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
                           : pass1_batched(v, mask, vt, moments_scratch, s);
         }
         float total = best_ms[0] + best_ms[1];
-        int form_launches = launches, cfg1 = pick[0];
+        int form_launches = launches, cfg1 = pick[0], form_order = 0;
         if (ce == cudaSuccess && forms) {
             mb::TileCache tc;
             st = tile_cache(v, vt, tc);
@@ -1597,32 +1657,52 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
                 return st;
             }
             if (tc.vals) {
+                // form 0: two launches; form c + 1: one launch in configuration c
+                auto frame = [&](int form, const mb::ViewTable& t) {
+                    if (form > 0) return frame_batched(v, mask, t, moments_scratch, rgba, s, form - 1, tc);
+                    if (!grid) {
+                        cudaError_t e = pass1_batched(v, mask, t, moments_scratch, s, tc);
+                        return e != cudaSuccess ? e
+                                                : pass2_batched(v, mask, t, moments_scratch, rgba, mb::kColorResolved,
+                                                                s, tc);
+                    }
+                    cudaError_t e = mb::launch_pass1_fused(v->grid, v->d_tf, mask, t, moments_scratch, v->d_ctr, s,
+                                                           pick[0], tc, field_map_of(v, pick[0]));
+                    return e != cudaSuccess ? e
+                                            : mb::launch_pass2_fused(v->grid, v->d_tf, mask, t, moments_scratch, rgba,
+                                                                     mb::kColorResolved, v->d_ctr, s, pick[1], tc);
+                };
                 total = 3.0e38f;
+                int best_form = 0;
                 for (int form = 0; form <= mb::kNumStageConfigs && ce == cudaSuccess; ++form) {
-                    // form 0: two launches; form c + 1: one launch in configuration c
                     if (form > 0 && (grid ? !config_usable(v, form - 1) : form != 1)) continue;
                     float ms;
-                    time3([&]() {
-                        if (form > 0) return frame_batched(v, mask, vt, moments_scratch, rgba, s, form - 1, tc);
-                        if (!grid) {
-                            cudaError_t e = pass1_batched(v, mask, vt, moments_scratch, s, tc);
-                            return e != cudaSuccess ? e
-                                                    : pass2_batched(v, mask, vt, moments_scratch, rgba,
-                                                                    mb::kColorResolved, s, tc);
-                        }
-                        cudaError_t e = mb::launch_pass1_fused(v->grid, v->d_tf, mask, vt, moments_scratch, v->d_ctr,
-                                                               s, pick[0], tc, field_map_of(v, pick[0]));
-                        return e != cudaSuccess ? e
-                                                : mb::launch_pass2_fused(v->grid, v->d_tf, mask, vt, moments_scratch,
-                                                                         rgba, mb::kColorResolved, v->d_ctr, s, pick[1],
-                                                                         tc);
-                    }, ms);
+                    time3([&]() { return frame(form, vt); }, ms);
                     if (ce == cudaSuccess && ms < total) {
                         total = ms;
+                        best_form = form;
                         form_launches = form == 0 ? 2 : 1;
                         cfg1 = form == 0 ? pick[0] : form - 1;
                     }
                 }
+                // the fastest form again with its ray tiles dequeued longest first
+                int32_t* d_order = nullptr;
+                if (ce == cudaSuccess && (st = make_tile_order(v, vt, &d_order)) != MBOIT_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return st;
+                }
+                if (ce == cudaSuccess) {
+                    mb::ViewTable vto = vt;
+                    vto.order = d_order;
+                    float ms;
+                    time3([&]() { return frame(best_form, vto); }, ms);
+                    if (ce == cudaSuccess && ms < total) {
+                        total = ms;
+                        form_order = 1;
+                    }
+                }
+                cudaFree(d_order);
             }
         }
         if (ce == cudaSuccess && total < best_total) {
@@ -1631,12 +1711,14 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
             best[1] = pick[1];
             best[2] = packet;
             launches = form_launches;
+            order = form_order;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (ce != cudaSuccess) return fail(MBOIT_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
     v->frame_launches = launches;
+    v->tile_order = order;
     v->tune1 = best[0];
     v->tune2 = best[1];
     v->packet = best[2];

@@ -596,7 +596,10 @@ __device__ __forceinline__ void count_frames(Counters* ctr, const Body& body, bo
 __device__ __forceinline__ bool next_tile(const ViewTable& vt, int32_t* head, int& vi, int& px, int& py, int& tile) {
     const int lane = threadIdx.x & 31;
     tile = 0;
-    if (lane == 0) tile = atomicAdd(head, 1);
+    if (lane == 0) {
+        tile = atomicAdd(head, 1);
+        if (vt.order && tile < vt.total_tiles) tile = __ldg(vt.order + tile);
+    }
     tile = __shfl_sync(0xffffffffu, tile, 0);
     if (tile >= vt.total_tiles) return false;
     vi = find_view(vt, tile);

@@ -34,6 +34,10 @@ MB_HD void tile_pixel(const ViewSlot& S, int lt, int lane, int& px, int& py) {
 struct ViewTable {
     int32_t n;
     int32_t total_tiles;
+    // dequeue order: the queue's i-th pop takes tile order[i] (a permutation of
+    // the tiles, longest first); NULL: tiles in order (views in turn, rows of
+    // tiles top to bottom)
+    const int32_t* order;
     ViewSlot s[kMaxViews];
 };
 
@@ -166,7 +170,10 @@ cudaError_t launch_pass2_multi(const GridTable& gt, const float4* tf, const View
 cudaError_t prepare_multi_kernels();
 // Rows a frame's tile cache needs over the domain box of `g` (sum over the
 // ray tiles of kmax - kmin + 1), added to *rows.
-cudaError_t launch_tile_rows(const GridD& g, const ViewTable& vt, unsigned long long* rows, cudaStream_t s);
+// With per_tile set, also writes each tile's row count (its cost: the warp
+// walks those rows in lockstep) to per_tile[tile].
+cudaError_t launch_tile_rows(const GridD& g, const ViewTable& vt, unsigned long long* rows, cudaStream_t s,
+                             int32_t* per_tile = nullptr);
 // Plain per-piece passes: one launch = one piece, its own slab.
 cudaError_t launch_pass1_piece(const GridD& g, const float4* tf, const int32_t* piece_of_brick, int32_t piece,
                                const PieceBox& box, const ViewTable& vt, int32_t slot, int32_t n_slots,

@@ -249,7 +249,7 @@ __global__ void k_color_resolve(const float4* __restrict__ in, float4* __restric
 // One warp per ray tile: adds the tile's cache rows (kmax - kmin + 1 over its
 // rays' exact in-domain intervals, as pass 1 will take them) to *rows.
 __global__ void __launch_bounds__(256) k_tile_rows(const __grid_constant__ GridD g, const __grid_constant__ ViewTable vt,
-                                                   unsigned long long* __restrict__ rows) {
+                                                   unsigned long long* __restrict__ rows, int32_t* __restrict__ per_tile) {
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
     unsigned long long mine = 0;
@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(256) k_tile_rows(const __grid_constant__ GridD
         ray_range(g, S.v, valid, px, py, o, d, k0, k1);
         const int kmin = __reduce_min_sync(0xffffffffu, k0), kmax = __reduce_max_sync(0xffffffffu, k1);
         if (kmax >= kmin) mine += (unsigned long long)(kmax - kmin + 1);
+        if (per_tile && lane == 0) per_tile[tile] = kmax >= kmin ? kmax - kmin + 1 : 0;
     }
     if (lane == 0 && mine) atomicAdd(rows, mine);
 }
@@ -376,9 +377,10 @@ cudaError_t prepare_kernels() {
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_rows(const GridD& g, const ViewTable& vt, unsigned long long* rows, cudaStream_t s) {
+cudaError_t launch_tile_rows(const GridD& g, const ViewTable& vt, unsigned long long* rows, cudaStream_t s,
+                             int32_t* per_tile) {
     const int blocks = (vt.total_tiles + 7) / 8;
-    k_tile_rows<<<blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096, 256, 0, s>>>(g, vt, rows);
+    k_tile_rows<<<blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096, 256, 0, s>>>(g, vt, rows, per_tile);
     return cudaGetLastError();
 }
 

@@ -225,3 +225,32 @@ def test_one_launch_sixteen_views(pkg):
         assert float(a.max()) > 0.0
         off += npx
     vol.close()
+
+
+@pytest.mark.parametrize("name", ["blobs64", "amr", "tets"])
+def test_cost_ordered_tiles_bit_identical(pkg, name):
+    """Ray tiles dequeued longest first (mboit_set_tile_order(1)): every tile
+    is still marched once, so moments and images keep their bits, in both
+    frame forms and with several ragged views."""
+    import torch
+    if name == "blobs64":
+        sc = scenes.blobs64(width=61, height=37)
+        views = [sc.views[0], scenes.perspective_view(sc.dims, (-0.5, 0.6, -0.62), 48, 40, fov_deg=40.0)]
+    elif name == "amr":
+        sc = scenes.amr_blobs(base=4, max_level=2, width=45, height=38, n_pieces=5)
+        views = sc.views
+    else:
+        sc = scenes.tet_mesh(n=8, n_pieces=3, width=43, height=29, seed=7)
+        views = sc.views
+    vol = pkg.Volume(sc)
+    for launches in (1, 2):
+        vol.set_tile_order(0)
+        m0, c0, s0 = frame(pkg, vol, views, launches)
+        vol.set_tile_order(1)
+        m1, c1, s1 = frame(pkg, vol, views, launches)
+        assert s0["tile_order"] == 0 and s1["tile_order"] == 1
+        assert torch.equal(m0, m1) and torch.equal(c0, c1)
+        assert s0["samples_pass1"] == s1["samples_pass1"] > 0
+    with pytest.raises(pkg.MboitError):
+        vol.set_tile_order(2)
+    vol.close()
