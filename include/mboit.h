@@ -449,12 +449,23 @@ MBOIT_API mboit_status mboit_set_packet(mboit_volume v, int32_t packet);
  * eligible configuration, and keeps the packet and form of the fastest
  * frame (in one launch, the configuration found there is pass 1's); for
  * other moment sets, the packet with the smallest sum of its pass-1 and
- * pass-2 times.  Writes pass 1's, pass 2's configuration and the packet to
- * chosen[0..2] (HOST, may be NULL); the form is in
- * mboit_stats.frame_launches.  The buffers are as for mboit_render_frame
- * and are overwritten.  Synchronous. */
+ * pass-2 times; with four power moments it also times the fastest frame
+ * with its ray tiles dequeued longest first (mboit_set_tile_order).  Writes
+ * pass 1's, pass 2's configuration and the packet to chosen[0..2] (HOST,
+ * may be NULL); the form and the order are in mboit_stats.frame_launches and
+ * tile_order.  The buffers are as for mboit_render_frame and are
+ * overwritten.  Synchronous.  The choice is kept for the process, keyed by
+ * the volume's configuration (kind, shape, brick size, sampling step, moment
+ * set and storage, flags, leaf / tet / piece counts, the window
+ * configurations it can take), the views and the device's SM count: a later
+ * call with the same key, for this or another volume, takes it without
+ * timing anything (mboit_clear_tuning_cache forgets every choice). */
 MBOIT_API mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch,
                                       float* rgba, void* stream, int32_t* chosen);
+
+/* Forgets the autotuner's kept choices (the next mboit_autotune times again).
+ * Volumes keep the tuning they have. */
+MBOIT_API void mboit_clear_tuning_cache(void);
 
 /* Pass 1 for callers that must not allocate device memory.  The paper has
  * no counterpart; it serves embedders such as an in-situ adaptor linked into

@@ -39,7 +39,7 @@ EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume
             "mboit_render_frame", "mboit_render_frame_host", "mboit_render_frame_multi", "mboit_synchronize",
             "mboit_get_stats",
             "mboit_render_moments_noalloc", "mboit_set_tuning", "mboit_set_packet", "mboit_set_frame_launches",
-            "mboit_set_tile_order", "mboit_autotune",
+            "mboit_set_tile_order", "mboit_autotune", "mboit_clear_tuning_cache",
             "mboit_render_sortlast", "mboit_split_cells", "mboit_debug_corrupt"]
 MBOIT_NUM_TUNINGS = 7
 
@@ -109,6 +109,7 @@ def load_library(path=LIB_PATH):
         "mboit_set_packet": (ctypes.c_int, [P, I32]),
         "mboit_set_frame_launches": (ctypes.c_int, [P, I32]),
         "mboit_set_tile_order": (ctypes.c_int, [P, I32]),
+        "mboit_clear_tuning_cache": (None, []),
         "mboit_autotune": (ctypes.c_int, [P, P, I32, P, P, P, P]),
         "mboit_render_sortlast": (ctypes.c_int, [P, P, I32, P, P, P]),
         "mboit_split_cells": (ctypes.c_int, [P, I64, P, P, I64, I32, P, P, P, I64, P]),
@@ -291,6 +292,10 @@ def mboit_set_packet(v, packet):
 
 def mboit_set_frame_launches(v, launches):
     _check(load_library().mboit_set_frame_launches(v, int(launches)))
+
+
+def mboit_clear_tuning_cache():
+    load_library().mboit_clear_tuning_cache()
 
 
 def mboit_set_tile_order(v, order):

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <type_traits>
@@ -1573,14 +1574,79 @@ mboit_status mboit_set_packet(mboit_volume v, int32_t packet) {
     return MBOIT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The autotuner's choices, kept per process by configuration: the volume's
+// kind, shape, sampling and moment format, its piece count, which window
+// configurations it can take, the views, and the device's SM count.  The
+// field's values are not part of the key (they change the work little).
+struct Tuned {
+    int32_t tune1, tune2, packet, launches, order;
+};
+std::mutex g_tuned_mu;
+std::map<std::vector<char>, Tuned> g_tuned;
+
+std::vector<char> tuning_key(mboit_volume v, const mboit_view* views, int32_t n_views) {
+    std::vector<char> k;
+    auto put = [&](const void* p, size_t n) { k.insert(k.end(), (const char*)p, (const char*)p + n); };
+    const mboit_volume_desc& d = v->desc;
+    const int64_t ints[] = {d.kind, d.dims[0], d.dims[1], d.dims[2], d.brick_log2, d.moment_set, d.storage,
+                            (int64_t)d.flags, d.n_leaves, d.max_level, d.n_verts, d.n_tets,
+                            (int64_t)v->boxes.size(), n_views};
+    put(ints, sizeof ints);
+    put(&d.step, sizeof d.step);
+    int32_t usable = 0;
+    for (int c = 0; c < mb::kNumStageConfigs; ++c)
+        if (v->kind == MBOIT_GRID && config_usable(v, c)) usable |= 1 << c;
+    put(&usable, sizeof usable);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, v->device);
+    put(&sms, sizeof sms);
+    put(views, sizeof(mboit_view) * (size_t)n_views);
+    return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mboit_clear_tuning_cache(void) {
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    g_tuned.clear();
+}
+
 mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch, float* rgba,
                             void* stream, int32_t* chosen) {
     g_err.clear();
     mboit_status st = check_volume(v);
     if (st != MBOIT_OK) return st;
     if (!moments_scratch || !rgba) return fail(MBOIT_ERR_INVALID_ARG, "moments_scratch and rgba must be non-NULL");
+    if (!views || n_views < 1 || n_views > mb::kMaxViews)
+        return fail(MBOIT_ERR_INVALID_ARG, "n_views must be in [1, " + std::to_string(mb::kMaxViews) + "]");
     std::lock_guard<std::mutex> lk(v->mu);
     DeviceGuard dg(v->device);
+    const std::vector<char> key = tuning_key(v, views, n_views);
+    {
+        std::lock_guard<std::mutex> tl(g_tuned_mu);
+        const auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            const Tuned& t = it->second;
+            v->tune1 = t.tune1;
+            v->tune2 = t.tune2;
+            v->packet = t.packet;
+            v->frame_launches = t.launches;
+            v->tile_order = t.order;
+            drop_graphs(v);
+            if (chosen) {
+                chosen[0] = t.tune1;
+                chosen[1] = t.tune2;
+                chosen[2] = t.packet;
+            }
+            return MBOIT_OK;
+        }
+    }
     std::vector<int32_t> list;
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, nullptr, 0, list, &mask)) != MBOIT_OK) return st;
@@ -1722,6 +1788,10 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
     v->tune1 = best[0];
     v->tune2 = best[1];
     v->packet = best[2];
+    {
+        std::lock_guard<std::mutex> tl(g_tuned_mu);
+        g_tuned[key] = Tuned{best[0], best[1], best[2], launches, order};
+    }
     drop_graphs(v);
     if (chosen) {
         chosen[0] = best[0];

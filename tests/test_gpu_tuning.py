@@ -113,3 +113,42 @@ def test_autotune_then_frame_matches_oracle(pkg):
     ref = oracle.render_grid(sc, want=("mboit",))
     assert np.abs(col.view(-1, 4).cpu().numpy() - ref["mboit"]).max() <= 2e-4
     vol.close()
+
+
+def test_autotune_choice_is_kept_per_configuration(pkg):
+    """The autotuner's choice is kept for the process by (volume
+    configuration, views, SM count): a second volume of the same
+    configuration takes it without timing; other views are another key."""
+    import time
+    pkg.mboit_clear_tuning_cache()
+    sc = scenes.blobs64(width=64, height=48)
+    a, b = pkg.Volume(sc), pkg.Volume(sc)
+    views = sc.views
+    m, c = pkg.Volume.moment_buffer(views), pkg.Volume.color_buffer(views)
+    t0 = time.perf_counter()
+    ca = a.autotune(views, m, c)
+    t1 = time.perf_counter()
+    cb = b.autotune(views, m, c)
+    t2 = time.perf_counter()
+    assert ca == cb
+    sa, sb = a.stats(), b.stats()
+    for k in ("tuning_pass1", "tuning_pass2", "packet", "frame_launches", "tile_order"):
+        assert sa[k] == sb[k], k
+    assert t2 - t1 < 0.5 * (t1 - t0)             # no timing runs the second time
+    # the kept choice renders as the timed one did
+    a.render_frame(views, m, c)
+    ref = c.clone()
+    b.render_frame(views, m, c)
+    b.synchronize()
+    assert (ref == c).all()
+    # another view is another key, and a cleared cache times again
+    other = [scenes.ortho_view(sc.dims, (0.1, 0.2, 0.97), 40, 30)]
+    m2, c2 = pkg.Volume.moment_buffer(other), pkg.Volume.color_buffer(other)
+    p1, p2, pk = b.autotune(other, m2, c2)
+    assert 0 <= p1 < pkg.MBOIT_NUM_TUNINGS and 0 <= p2 < pkg.MBOIT_NUM_TUNINGS and pk in (0, 1)
+    pkg.mboit_clear_tuning_cache()
+    t3 = time.perf_counter()
+    assert a.autotune(views, m, c)[2] in (0, 1)
+    assert time.perf_counter() - t3 > t2 - t1
+    a.close()
+    b.close()
