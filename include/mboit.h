@@ -28,7 +28,13 @@
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Render calls are asynchronous on that stream; errors raised
  *     inside kernels (a wait limit or an index check) are reported by
- *     mboit_synchronize().
+ *     mboit_synchronize().  One volume serves one stream at a time: a
+ *     render call (passes, frame, host frame, multi-volume frame, sort-last)
+ *     on another stream while work of the volume's previous call may still
+ *     run returns MBOIT_ERR_STATE and enqueues nothing (an event recorded
+ *     after each call's work tells; calls made while a stream is being
+ *     captured into a graph are not tracked).  Calls from several host
+ *     threads on one volume are serialised by its lock.
  *   - Images are row-major, pixel index y * width + x, x to the right.
  *   - Moment images: per (view[, piece]) one slab, P = width * height rounded
  *     up to a multiple of 4.  Power moments: b0 as P float32, then (b1, b2,

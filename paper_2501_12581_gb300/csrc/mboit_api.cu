@@ -103,6 +103,11 @@ struct mboit_volume_s {
     bool has_field_map = false;
     int32_t packet = MBOIT_PACKET_8X4;
     int32_t tile_order = 0;     // 1: frames dequeue their ray tiles longest first (mboit_set_tile_order)
+    // one volume, one stream at a time: the stream of the last call that
+    // launched work and an event recorded after that work
+    cudaEvent_t done_ev = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool done_recorded = false;
     int32_t frame_launches = 2;  // 1: one launch per frame (four power moments)
     // sort-last baseline buffers (grow only)
     int32_t* sl_counts = nullptr;
@@ -241,6 +246,38 @@ void drop_graphs(mboit_volume v) {
         cudaFree(g.d_order);   // after the graph: cudaFree waits for work that may still read it
     }
     v->graphs.clear();
+}
+
+// The volume's queue heads, counters and frame cache serve one stream at a
+// time: a call on another stream while work of the volume's last call may
+// still run is refused (MBOIT_ERR_STATE).
+mboit_status claim_stream(mboit_volume v, cudaStream_t s) {
+    if (v->done_recorded && s != v->last_stream) {
+        const cudaError_t q = cudaEventQuery(v->done_ev);
+        if (q == cudaErrorNotReady)
+            return fail(MBOIT_ERR_STATE, "the volume's last call still runs on another stream; synchronise that "
+                                         "stream first (one volume, one stream at a time)");
+        if (q != cudaSuccess) cudaGetLastError();
+    }
+    return MBOIT_OK;
+}
+
+// Marks the end of this call's work on `s` (nothing to mark while `s` is
+// being captured into a graph: the caller's graph orders it).
+void release_stream(mboit_volume v, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        v->done_recorded = false;
+        return;
+    }
+    if (cudaEventRecord(v->done_ev, s) == cudaSuccess) {
+        v->done_recorded = true;
+        v->last_stream = s;
+    } else {
+        cudaGetLastError();
+        v->done_recorded = false;
+    }
 }
 
 mboit_status check_volume(mboit_volume v) {
@@ -979,6 +1016,7 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&v->cap_stream, cudaStreamNonBlocking);
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&v->frame_ev[i]);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->done_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = mb::prepare_kernels();
     if (e != cudaSuccess) {
         const mboit_status s = (e == cudaErrorMemoryAllocation) ? MBOIT_ERR_OUT_OF_MEMORY : MBOIT_ERR_CUDA;
@@ -1001,6 +1039,7 @@ mboit_status mboit_destroy_volume(mboit_volume v) {
         if (v->cap_stream) cudaStreamDestroy(v->cap_stream);
         for (cudaEvent_t ev : v->frame_ev)
             if (ev) cudaEventDestroy(ev);
+        if (v->done_ev) cudaEventDestroy(v->done_ev);
         cudaFree(v->d_tf);
         cudaFree(v->d_leaves);
         cudaFree(v->d_leaf_box);
@@ -1134,6 +1173,7 @@ mboit_status mboit_render_moments(mboit_volume v, const mboit_view* views, int32
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, pieces, n_pieces, list, &mask)) != MBOIT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((st = claim_stream(v, s)) != MBOIT_OK) return st;
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->samples[0], 0, sizeof(unsigned long long), s));
     if (mode == MBOIT_MOMENTS_REDUCED) {
         MB_CUDA(pass1_batched(v, mask, vt, moments, s));
@@ -1150,6 +1190,7 @@ mboit_status mboit_render_moments(mboit_volume v, const mboit_view* views, int32
                 MB_CUDA(mb::launch_pass1_piece(v->grid, v->d_tf, v->d_pob, list[j], box, vt, j, slots, moments, v->d_ctr, s));
         }
     }
+    release_stream(v, s);
     return MBOIT_OK;
 }
 
@@ -1170,6 +1211,7 @@ mboit_status mboit_reconstruct_blend(mboit_volume v, const mboit_view* views, in
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, pieces, n_pieces, list, &mask)) != MBOIT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((st = claim_stream(v, s)) != MBOIT_OK) return st;
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->samples[1], 0, 2 * sizeof(unsigned long long), s));
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->fp64_pixels, 0, sizeof(unsigned long long), s));
     if (mode == MBOIT_COLOR_PER_PIECE) {
@@ -1191,6 +1233,7 @@ mboit_status mboit_reconstruct_blend(mboit_volume v, const mboit_view* views, in
         const int32_t md = mode == MBOIT_COLOR_RESOLVED ? mb::kColorResolved : mb::kColorReduced;
         MB_CUDA(pass2_batched(v, mask, vt, global_moments, color, md, s));
     }
+    release_stream(v, s);
     return MBOIT_OK;
 }
 
@@ -1239,6 +1282,7 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
     std::vector<int32_t> list;
     const uint8_t* mask = nullptr;
     if ((st = select_pieces(v, nullptr, 0, list, &mask)) != MBOIT_OK) return st;
+    if ((st = claim_stream(v, static_cast<cudaStream_t>(stream))) != MBOIT_OK) return st;
     // graph key: the view table and the output pointers
     std::vector<char> key(sizeof vt + 2 * sizeof(void*));
     std::memcpy(key.data(), &vt, sizeof vt);
@@ -1287,6 +1331,7 @@ mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t
     }
     MB_CUDA(cudaGraphLaunch(exec, static_cast<cudaStream_t>(stream)));
     v->frame_timed = true;
+    release_stream(v, static_cast<cudaStream_t>(stream));
     return MBOIT_OK;
 }
 
@@ -1322,6 +1367,11 @@ mboit_status mboit_render_frame_multi(const mboit_volume* vols, int32_t n_vols, 
     for (mboit_volume v : order) locks.emplace_back(v->mu);
     const mboit_volume v0 = vols[0];
     DeviceGuard dg(v0->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int32_t i = 0; i < n_vols; ++i) {
+        const mboit_status cs = claim_stream(vols[i], s);
+        if (cs != MBOIT_OK) return cs;
+    }
     mb::ViewTable vt;
     mboit_status st = build_views(views, n_views, vt, slab_bytes_per_px(MBOIT_POWER4), v0->packet);
     if (st != MBOIT_OK) return st;
@@ -1353,12 +1403,12 @@ mboit_status mboit_render_frame_multi(const mboit_volume* vols, int32_t n_vols, 
     MB_CUDA(cudaStreamSynchronize(cs));
     mb::TileCache tc;
     if ((st = cache_buffers(v0, rows, vt.total_tiles, tc)) != MBOIT_OK) return st;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     MB_CUDA(cudaMemsetAsync(&v0->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), s));
     MB_CUDA(cudaMemsetAsync(&v0->d_ctr->fp64_pixels, 0, sizeof(unsigned long long), s));
     MB_CUDA(mb::launch_pass1_multi(gt, v0->d_tf, vt, moments_scratch, v0->d_ctr, s, vec, tc));
     MB_CUDA(mb::launch_pass2_multi(gt, v0->d_tf, vt, moments_scratch, rgba, v0->d_ctr, s, vec, tc));
     v0->frame_timed = false;
+    for (int32_t i = 0; i < n_vols; ++i) release_stream(vols[i], s);
     return MBOIT_OK;
 }
 
@@ -1371,6 +1421,10 @@ mboit_status mboit_render_frame_host(mboit_volume v, const float* field_host, co
     mb::ViewTable vt;
     if ((st = build_views(views, n_views, vt, slab_bytes_per_px(v->desc.moment_set), v->packet)) != MBOIT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        std::lock_guard<std::mutex> lk(v->mu);
+        if ((st = claim_stream(v, s)) != MBOIT_OK) return st;
+    }
     {
         DeviceGuard dg(v->device);
         if (v->kind == MBOIT_TET) {
@@ -1494,6 +1548,7 @@ mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int3
     MB_CUDA(ensure_capacity(v->sl_base, v->cap_base, (size_t)total_px + 1));
     MB_CUDA(ensure_capacity(v->sl_bsum, v->cap_bsum, nb));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((st = claim_stream(v, s)) != MBOIT_OK) return st;
     MB_CUDA(cudaMemsetAsync(&v->d_ctr->segments, 0, sizeof(unsigned long long) + sizeof(int32_t), s));
     MB_CUDA(check_tables(v, s));
     auto march = [&](bool fill, int32_t p) {
@@ -1523,6 +1578,7 @@ mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int3
         MB_CUDA(cudaMemcpyAsync(segments_per_pixel, v->sl_totals, (size_t)total_px * sizeof(int32_t),
                                 cudaMemcpyDeviceToDevice, s));
     v->sl_segments = total;
+    release_stream(v, s);
     return MBOIT_OK;
 }
 

@@ -22,6 +22,7 @@ from tests import _scenes_small as small
 
 pytestmark = pytest.mark.gpu
 
+STATE = 5
 TIMEOUT = 6
 DEVICE_ASSERT = 7
 
@@ -121,4 +122,35 @@ def test_tma_hook_rejects_wrong_kind(pkg):
     with pytest.raises(pkg.MboitError) as e:
         pkg.mboit_debug_corrupt(vol.handle, 3)
     assert e.value.status == 1
+    vol.close()
+
+
+def test_second_stream_while_busy_is_refused(pkg):
+    """One volume, one stream at a time: a frame on another stream while the
+    first stream's frame still runs is refused with MBOIT_ERR_STATE and
+    enqueues nothing; once that stream is done, the other stream may go."""
+    import torch
+    sc = scenes.blobs512(width=2048, height=2048)
+    vol = pkg.Volume(sc)
+    views = sc.views
+    mom, col = pkg.Volume.moment_buffer(views), pkg.Volume.color_buffer(views)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    vol.render_frame(views, mom, col, stream=sa)      # records the frame graph
+    sa.synchronize()
+    ref = col.clone()
+    refused = 0
+    for _ in range(3):
+        for _ in range(4):
+            vol.render_frame(views, mom, col, stream=sa)   # ~7 ms each, queued
+        try:
+            vol.render_frame(views, mom, col, stream=sb)
+        except pkg.MboitError as e:
+            assert e.status == STATE
+            refused += 1
+        sa.synchronize()
+        sb.synchronize()
+    assert refused == 3
+    vol.render_frame(views, mom, col, stream=sb)      # stream a is idle now
+    sb.synchronize()
+    assert torch.equal(col, ref)
     vol.close()
