@@ -414,6 +414,7 @@ def main():
     ap.add_argument("--no-sortlast", action="store_true")
     ap.add_argument("--no-gear", action="store_true", help="skip the gear-teeth stress test")
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-volume frame")
+    ap.add_argument("--no-fp64-setup", action="store_true", help="skip the frame with every pixel set up in FP64")
     ap.add_argument("--gear-k", default="8,16,32,64,128", help="piece counts of the gear-teeth stress test")
     ap.add_argument("--heatmap", default="", help="directory for the gear-teeth segments-per-pixel images (PGM)")
     ap.add_argument("--ncu-record", nargs=4, metavar=("CSV", "KERNEL", "SAMPLES", "OUT"),
@@ -718,6 +719,29 @@ def main():
     tets = unit_block("tets") if headline and not args.no_tets else None
     mixed = unit_block("mixed") if headline and not args.no_tets else None
 
+    # the headline frame with every pixel's reconstruction frame set up in FP64
+    # (MBOIT_FLAG_FP64_SETUP), the same tuning, against the float-float set-up
+    fp64_setup = None
+    if headline and not args.no_fp64_setup:
+        st0 = vol.stats()
+        v64 = pkg.Volume(sc, flags=pkg.MBOIT_FLAG_FP64_SETUP)
+        v64.set_tuning(st0["tuning_pass1"], st0["tuning_pass2"])
+        v64.set_packet(st0["packet"])
+        v64.set_frame_launches(st0["frame_launches"])
+        v64.set_tile_order(st0["tile_order"])
+        f64 = lambda: v64.render_frame(views, mom, rgba)  # noqa: E731
+        for _ in range(3):
+            f64()
+        ms64 = timed(f64, max(5, args.steps // 3))
+        v64.synchronize()
+        s64 = v64.stats()
+        fp64_setup = {"ms_per_frame": ms64, "fp64_pixels": s64["fp64_pixels"],
+                      "float_float_ms_per_frame": ms_max, "float_float_fp64_pixels": st0["fp64_pixels"],
+                      "time_ratio": ms64 / ms_max}
+        v64.close()
+        del v64
+        torch.cuda.empty_cache()
+
     # several independent volumes in one persistent launch per pass: 8 grids
     # of 64^3 (the blobs64 field flipped and scaled per volume, one transfer
     # function), one 256^2 view each, against 8 single-volume frames
@@ -903,6 +927,7 @@ def main():
            "grid_512_64_pieces": grid, "tets_72_pieces": tets, "mixed_cells_72_pieces": mixed,
            "gear_teeth_stress": gear,
            "multi_volume_8_grids": multi,
+           "fp64_setup_every_pixel": fp64_setup,
            "precision_sweep_amr_2048": sweep,
            "quality": quality, "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
            "gpu_launches": launches * args.steps, "clocks": clk.summary()}

@@ -123,6 +123,12 @@ typedef enum {
  * coarse leaves are sampled at their own resolution on a nested lattice, so
  * pieces still partition the samples and their moments still add up. */
 #define MBOIT_FLAG_ADAPTIVE_STEP 0x4u
+/* Every pixel's reconstruction frame (four power moments) set up in FP64,
+ * as the paper's reading of Alg. 3 does in double precision; without it
+ * the set-up is float-float FP32 and only near-singular Hankel matrices
+ * take FP64 (mboit_stats.fp64_pixels counts them).  For comparison: both
+ * give the same images to float32 rounding. */
+#define MBOIT_FLAG_FP64_SETUP 0x8u
 
 typedef struct mboit_volume_s* mboit_volume;
 

@@ -32,7 +32,7 @@ MBOIT_PACKET_8X4, MBOIT_PACKET_4X8 = 0, 1
 MBOIT_MOMENTS_PER_PIECE, MBOIT_MOMENTS_REDUCED = 0, 1
 MBOIT_COLOR_PER_PIECE, MBOIT_COLOR_REDUCED, MBOIT_COLOR_RESOLVED = 0, 1, 2
 MBOIT_OP_MOMENTS_SUM, MBOIT_OP_COLOR_SUM_RESOLVE = 0, 1
-MBOIT_FLAG_RAW_SUM, MBOIT_FLAG_DETERMINISTIC, MBOIT_FLAG_ADAPTIVE_STEP = 0x1, 0x2, 0x4
+MBOIT_FLAG_RAW_SUM, MBOIT_FLAG_DETERMINISTIC, MBOIT_FLAG_ADAPTIVE_STEP, MBOIT_FLAG_FP64_SETUP = 0x1, 0x2, 0x4, 0x8
 
 EXPORTED = ["mboit_last_error", "mboit_moment_image_bytes", "mboit_create_volume", "mboit_destroy_volume",
             "mboit_add_piece", "mboit_render_moments", "mboit_reconstruct_blend", "mboit_composite",
@@ -354,7 +354,9 @@ def mboit_render_moments_noalloc(desc, views, moments, brick_selected=None, stre
 def mboit_debug_corrupt(handle, what):
     """Test hook of the failure detection (see include/mboit.h): overwrites a
     library-owned table of the volume (1: an octree map entry, 2: mesh face
-    neighbours) so that later renders report MBOIT_ERR_DEVICE_ASSERT."""
+    neighbours) so that later renders report MBOIT_ERR_DEVICE_ASSERT, or (3,
+    grids) makes every TMA window load wait for a copy never issued, so that
+    renders in window configurations 5 and 6 report MBOIT_ERR_TIMEOUT."""
     _check(load_library().mboit_debug_corrupt(handle, int(what)))
 
 

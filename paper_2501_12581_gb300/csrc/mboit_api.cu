@@ -830,7 +830,7 @@ mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) 
         !(d->moment_bias >= (d->storage == MBOIT_STORE_F16 ? 2e-3f : 2e-2f)))
         return fail(MBOIT_ERR_INVALID_ARG, "trigonometric moments in 16 bits need moment_bias >= 2e-3 (float16) or "
                                            ">= 2e-2 (bfloat16) to keep the stored Toeplitz matrices positive definite");
-    if (d->flags & ~(MBOIT_FLAG_RAW_SUM | MBOIT_FLAG_DETERMINISTIC | MBOIT_FLAG_ADAPTIVE_STEP))
+    if (d->flags & ~(MBOIT_FLAG_RAW_SUM | MBOIT_FLAG_DETERMINISTIC | MBOIT_FLAG_ADAPTIVE_STEP | MBOIT_FLAG_FP64_SETUP))
         return fail(MBOIT_ERR_INVALID_ARG, "unknown flag bits");
     if ((d->flags & MBOIT_FLAG_ADAPTIVE_STEP) && !is_amr)
         return fail(MBOIT_ERR_INVALID_ARG, "MBOIT_FLAG_ADAPTIVE_STEP applies to octrees only");
@@ -1902,7 +1902,8 @@ extern "C" mboit_status mboit_render_moments_noalloc(const mboit_volume_desc* d,
     if (d->kind != MBOIT_GRID) return fail(MBOIT_ERR_UNSUPPORTED, "only MBOIT_GRID volumes are implemented");
     if (d->moment_set != MBOIT_POWER4 || d->storage != MBOIT_STORE_F32)
         return fail(MBOIT_ERR_UNSUPPORTED, "only float32 power moments are implemented");
-    if (d->flags & ~(MBOIT_FLAG_RAW_SUM | MBOIT_FLAG_DETERMINISTIC)) return fail(MBOIT_ERR_INVALID_ARG, "unknown flag bits");
+    if (d->flags & ~(MBOIT_FLAG_RAW_SUM | MBOIT_FLAG_DETERMINISTIC | MBOIT_FLAG_FP64_SETUP))
+        return fail(MBOIT_ERR_INVALID_ARG, "unknown flag bits");
     if (!d->field) return fail(MBOIT_ERR_INVALID_ARG, "field must be non-NULL");
     for (int c = 0; c < 3; ++c)
         if (d->dims[c] < 2 || d->dims[c] > (1 << 20)) return fail(MBOIT_ERR_INVALID_ARG, "dims must be in [2, 2^20]");

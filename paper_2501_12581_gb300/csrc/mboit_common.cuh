@@ -156,6 +156,16 @@ __device__ __forceinline__ float4 depth_powers(float t, float wa, float wb) {
     return make_float4(z, z2, z3, z3 * z);
 }
 
+// The pixel's reconstruction frame: float-float FP32 set-up with FP64 for
+// near-singular Hankel matrices, or FP64 for every pixel (kFlagFp64Setup).
+__device__ __forceinline__ Frame pixel_frame(const GridD& g, const float m[5], bool* fp64) {
+    if (g.flags & kFlagFp64Setup) {
+        *fp64 = m[0] > 0.0f;
+        return make_frame(m, g.moment_bias, g.bias_vector);
+    }
+    return make_frame_ff(m, g.moment_bias, g.bias_vector, fp64);
+}
+
 struct MomentBody {
     const float2* s_sig;  // (sigma*step of entry i, of entry i+1 minus entry i)
     float tf_scale, tf_bias, amax, wa, wb;
@@ -537,7 +547,7 @@ __device__ __forceinline__ BlendBody blend_body_of(const float4* s_tf, const Gri
     b.w0 = g.overestimation;
     const float m[5] = {valid ? mb.m0 : 0.0f, valid ? mb.m12.x : 0.0f, valid ? mb.m12.y : 0.0f,
                         valid ? mb.m34.x : 0.0f, valid ? mb.m34.y : 0.0f};
-    b.F = make_frame_ff(m, g.moment_bias, g.bias_vector, &b.fp64);
+    b.F = pixel_frame(g, m, &b.fp64);
     b.b0 = m[0];
     return b;
 }
@@ -558,7 +568,7 @@ __device__ __forceinline__ typename Bodies<MS>::Blend make_blend_body(const floa
     if constexpr (MS == 0) {
         float m[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         if (valid) load_moments(moments, S, off, pix, m);
-        b.F = make_frame_ff(m, g.moment_bias, g.bias_vector, &b.fp64);
+        b.F = pixel_frame(g, m, &b.fp64);
         b.b0 = m[0];
     } else if constexpr (MS == 6 || MS == 8) {
         float m[MS + 1];

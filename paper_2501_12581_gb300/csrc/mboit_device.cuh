@@ -147,6 +147,7 @@ struct TrigTables {
 // GridD::flags bits (the descriptor's MBOIT_FLAG_* values)
 constexpr uint32_t kFlagRawSum = 0x1u;
 constexpr uint32_t kFlagAdaptiveStep = 0x4u;
+constexpr uint32_t kFlagFp64Setup = 0x8u;   // every pixel's frame set up in FP64
 // Test hook of the TMA wait limit (set by mboit_debug_corrupt, never by a
 // descriptor): window loads arm their barrier but issue no copy.
 constexpr uint32_t kFlagDebugNoCopy = 0x80000000u;

@@ -233,6 +233,35 @@ def test_raw_sum_flag(pkg):
     vol.close()
 
 
+@pytest.mark.parametrize("name", ["blobs64", "amr"])
+def test_fp64_setup_flag(pkg, name):
+    """MBOIT_FLAG_FP64_SETUP sets every pixel's frame up in FP64: the same
+    images as the float-float set-up to float32 rounding, both within the
+    oracle bar, and every pixel with b0 > 0 counted in fp64_pixels."""
+    import torch
+    if name == "blobs64":
+        sc = scenes.blobs64(width=48, height=40)
+        ref = oracle.render_grid(sc, want=("mboit",))["mboit"]
+    else:
+        sc = scenes.amr_blobs(base=4, max_level=2, width=45, height=38, n_pieces=5)
+        ref = oracle.render_amr(sc, want=("mboit",))["mboit"]
+    out = []
+    for flags in (0, pkg.MBOIT_FLAG_FP64_SETUP):
+        vol = pkg.Volume(sc, flags=flags)
+        mom, col = pkg.Volume.moment_buffer(sc.views), pkg.Volume.color_buffer(sc.views)
+        vol.render_frame(sc.views, mom, col)
+        vol.synchronize()
+        st = vol.stats()
+        npx = sc.views[0].width * sc.views[0].height
+        hit = int((mom[:npx] > 0).sum())
+        out.append((col.view(-1, 4).double().cpu().numpy(), st["fp64_pixels"], hit))
+        vol.close()
+    (c_ff, n_ff, hit), (c_64, n_64, hit64) = out
+    assert hit == hit64 > 0 and n_64 == hit and n_ff < hit
+    assert np.abs(c_ff - c_64).max() <= 2e-6
+    assert np.abs(c_64 - ref).max() <= 2e-4
+
+
 @pytest.mark.parametrize("atoms, weights, in_front", [
     ((-0.875,), (0.5,), 0.5),                 # one absorber in front of the slab
     ((0.875,), (0.75,), 0.0),                 # one absorber behind it
