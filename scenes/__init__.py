@@ -594,7 +594,7 @@ def amr_blobs(width=2560, height=2560, n_pieces=72, seed=1003, base=26, max_leve
     order = np.argsort(code, kind="stable")
     leaves, values = leaves[order], values[order]
     u = s.uniform(n_pieces)
-    u = (u - u.min()) / (u.max() - u.min())
+    u = (u - u.min()) / (u.max() - u.min()) if n_pieces > 1 else np.zeros(1)
     piece = morton_pieces_linear(len(leaves), n_pieces, 8.0 ** u, s)
     vmin, vmax = float(values.min()), float(values.max())
     am = alpha_max if alpha_max is not None else 0.053 * 512.0 / D
