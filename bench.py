@@ -783,6 +783,40 @@ def main():
             mv.close()
         del mvols, singles, mmom, mrgba
         torch.cuda.empty_cache()
+        # four brick octrees (the headline octree at a quarter of its base, its
+        # leaf values scaled per volume), one 512^2 view each
+        abase = _scenes.amr_blobs(width=512, height=512, n_pieces=8, base=8, max_level=2)
+        oscs = []
+        for i in range(4):
+            vals = np.ascontiguousarray(abase.values * np.float32(1.0 - 0.1 * i)).astype(np.float32)
+            oscs.append(dataclasses.replace(abase, name=f"amr_blobs8_{i}", values=vals,
+                                            tf_range=(np.float32(vals.min()), np.float32(vals.max()))))
+        ovols = [pkg.Volume(s_) for s_ in oscs]
+        oviews = [_scenes.perspective_view(abase.dims, (0.57 - 0.1 * i, 0.49, 0.66), 512, 512) for i in range(4)]
+        omom, orgba = pkg.Volume.moment_buffer(oviews), pkg.Volume.color_buffer(oviews)
+        oframe = lambda: pkg.Volume.render_frame_multi(ovols, oviews, list(range(4)), omom, orgba)  # noqa: E731
+        osingles = [(ov, [vw], pkg.Volume.moment_buffer([vw]), pkg.Volume.color_buffer([vw]))
+                    for ov, vw in zip(ovols, oviews)]
+
+        def oframes():
+            for ov, vw, m_, c_ in osingles:
+                ov.render_frame(vw, m_, c_)
+        for _ in range(3):
+            oframe()
+            oframes()
+        ms_om = timed(oframe, 10)
+        ms_os = timed(oframes, 10)
+        oframe()
+        ovols[0].synchronize()
+        som = ovols[0].stats()["samples_pass1"]
+        multi["octrees"] = {"volumes": 4, "leaves": int(len(abase.leaves)), "image": "512x512 per volume",
+                            "samples_per_frame": som, "multi_ms_per_frame": ms_om,
+                            "multi_gsamples_per_s": som / (ms_om * 1e-3) / 1e9, "single_volume_frames_ms": ms_os,
+                            "speedup_of_one_launch_per_pass": ms_os / ms_om}
+        for ov in ovols:
+            ov.close()
+        del ovols, osingles, omom, orgba
+        torch.cuda.empty_cache()
 
     # the gear-teeth stress test of Sec. 5: K pieces of 4 interleaved layers,
     # batched MBOIT against the exact sort-last baseline as K grows

@@ -335,22 +335,26 @@ MBOIT_API mboit_status mboit_composite(mboit_volume v, int32_t op, int32_t width
 MBOIT_API mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch,
                                 float* rgba, void* stream);
 
-/* Whole frame over several grid volumes at once (the batching pattern of
- * Sec. 4 applied across independent volumes): one persistent launch per
- * pass takes the ray tiles of every view, and view i samples volume
- * vols[view_volume[i]].  Every volume is MBOIT_GRID with MBOIT_POWER4 and
- * MBOIT_STORE_F32 (else MBOIT_ERR_UNSUPPORTED), on one device, listed once,
- * and all share one transfer function and sampling step (else
- * MBOIT_ERR_INVALID_ARG); fields, domains, moment bias, overestimation and
- * flags stay each volume's own.  1 <= n_vols <= 8, 1 <= n_views <= 16.
- * moments_scratch and rgba are laid out as for mboit_render_frame over the
- * n_views views; every image equals, bit for bit, its volume's own
- * mboit_render_frame.  Pass 1 stores the sample cache of vols[0] (sized for
- * all views; synchronises once per call to size it) and pass 2 blends from
- * it; windows take configuration 3 when every field qualifies (dims[0] % 4,
- * alignment), else 0.  Counters (mboit_get_stats) land in vols[0].  Two
- * launches on `stream`, not captured into a graph; takes every volume's
- * lock.  The paper has no counterpart (its pieces are one volume's). */
+/* Whole frame over several volumes at once (the batching pattern of Sec. 4
+ * applied across independent volumes): one persistent launch per pass takes
+ * the ray tiles of every view, and view i samples volume
+ * vols[view_volume[i]].  The volumes are all MBOIT_GRID or all MBOIT_AMR
+ * (fixed step), with MBOIT_POWER4 and MBOIT_STORE_F32 (another kind, set,
+ * storage or the adaptive step: MBOIT_ERR_UNSUPPORTED; kinds mixed:
+ * MBOIT_ERR_INVALID_ARG), on one device, listed once, and share one transfer
+ * function and sampling step (else MBOIT_ERR_INVALID_ARG); fields, domains,
+ * moment bias, overestimation and flags stay each volume's own.
+ * 1 <= n_vols <= 8, 1 <= n_views <= 16.  moments_scratch and rgba are laid
+ * out as for mboit_render_frame over the n_views views; every image equals,
+ * bit for bit, its volume's own mboit_render_frame.  Pass 1 stores the
+ * sample cache of vols[0] (sized for all views; synchronises once per call
+ * to size it) and pass 2 blends from it; grid windows take configuration 3
+ * when every field qualifies (dims[0] % 4, alignment), else 0; octrees have
+ * their tables checked first, each into its own error word
+ * (mboit_synchronize on that volume reports a failure; that volume's tiles
+ * are skipped).  Counters (mboit_get_stats) land in vols[0].  Two launches
+ * on `stream`, not captured into a graph; takes every volume's lock.  The
+ * paper has no counterpart (its pieces are one volume's). */
 MBOIT_API mboit_status mboit_render_frame_multi(const mboit_volume* vols, int32_t n_vols, const mboit_view* views,
                                                 const int32_t* view_volume, int32_t n_views, void* moments_scratch,
                                                 float* rgba, void* stream);

@@ -16,7 +16,7 @@ INC = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libmboit.so")
 UNITS = ["mboit_api.cu", "mboit_kernels.cu", "mboit_grid.cu", "mboit_grid_frame.cu", "mboit_grid_power.cu", "mboit_units.cu",
-         "mboit_units_trig.cu", "mboit_units_power.cu", "mboit_units_frame.cu", "mboit_grid_multi.cu"]
+         "mboit_units_trig.cu", "mboit_units_power.cu", "mboit_units_frame.cu", "mboit_grid_multi.cu", "mboit_multi_amr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INC, "-I", SRC]

@@ -19,6 +19,7 @@
 
 #include "mboit.h"
 #include "mboit_internal.h"
+#include "mboit_multi.h"
 
 namespace {
 
@@ -1348,8 +1349,11 @@ mboit_status mboit_render_frame_multi(const mboit_volume* vols, int32_t n_vols, 
         if (st != MBOIT_OK) return st;
         const mboit_volume v = vols[i];
         const std::string at = "volume " + std::to_string(i) + ": ";
-        if (v->kind != MBOIT_GRID || v->desc.moment_set != MBOIT_POWER4 || v->desc.storage != MBOIT_STORE_F32)
-            return fail(MBOIT_ERR_UNSUPPORTED, at + "multi-volume frames take grid volumes with four float32 power moments");
+        if ((v->kind != MBOIT_GRID && v->kind != MBOIT_AMR) || v->desc.moment_set != MBOIT_POWER4 ||
+            v->desc.storage != MBOIT_STORE_F32 || (v->desc.flags & MBOIT_FLAG_ADAPTIVE_STEP))
+            return fail(MBOIT_ERR_UNSUPPORTED, at + "multi-volume frames take grid or octree volumes with four float32 "
+                                                    "power moments and the fixed step");
+        if (v->kind != vols[0]->kind) return fail(MBOIT_ERR_INVALID_ARG, at + "the volumes of one frame are of one kind");
         if (v->device != vols[0]->device) return fail(MBOIT_ERR_INVALID_ARG, at + "on another device");
         if (v->tf_host.size() != vols[0]->tf_host.size() ||
             std::memcmp(v->tf_host.data(), vols[0]->tf_host.data(), v->tf_host.size() * sizeof(float4)) != 0)
@@ -1375,12 +1379,19 @@ mboit_status mboit_render_frame_multi(const mboit_volume* vols, int32_t n_vols, 
     mb::ViewTable vt;
     mboit_status st = build_views(views, n_views, vt, slab_bytes_per_px(MBOIT_POWER4), v0->packet);
     if (st != MBOIT_OK) return st;
+    const bool amr = v0->kind == MBOIT_AMR;
     mb::GridTable gt;
+    mb::AmrTable at;
     std::memset(&gt, 0, sizeof gt);
-    bool vec = true;
+    std::memset(&at, 0, sizeof at);
+    bool vec = true, holes = false;
     for (int32_t i = 0; i < n_vols; ++i) {
         gt.g[i] = vols[i]->grid;
         vec = vec && mb::stage_config_eligible(gt.g[i], 3);
+        if (amr) {
+            at.a[i] = vols[i]->amr;
+            holes = holes || !vols[i]->amr.complete;
+        }
     }
     for (int32_t i = 0; i < n_views; ++i) vt.s[i].vol = view_volume[i];
     // the sample cache: rows of every volume's views, counted per volume
@@ -1405,8 +1416,15 @@ mboit_status mboit_render_frame_multi(const mboit_volume* vols, int32_t n_vols, 
     if ((st = cache_buffers(v0, rows, vt.total_tiles, tc)) != MBOIT_OK) return st;
     MB_CUDA(cudaMemsetAsync(&v0->d_ctr->samples[0], 0, 3 * sizeof(unsigned long long), s));
     MB_CUDA(cudaMemsetAsync(&v0->d_ctr->fp64_pixels, 0, sizeof(unsigned long long), s));
-    MB_CUDA(mb::launch_pass1_multi(gt, v0->d_tf, vt, moments_scratch, v0->d_ctr, s, vec, tc));
-    MB_CUDA(mb::launch_pass2_multi(gt, v0->d_tf, vt, moments_scratch, rgba, v0->d_ctr, s, vec, tc));
+    if (amr) {
+        // every octree's index tables checked on this stream first (its error word)
+        for (int32_t i = 0; i < n_vols; ++i) MB_CUDA(check_tables(vols[i], s));
+        MB_CUDA(mb::launch_pass1_multi_amr(at, v0->d_tf, vt, moments_scratch, v0->d_ctr, s, holes, tc));
+        MB_CUDA(mb::launch_pass2_multi_amr(at, v0->d_tf, vt, moments_scratch, rgba, v0->d_ctr, s, holes, tc));
+    } else {
+        MB_CUDA(mb::launch_pass1_multi(gt, v0->d_tf, vt, moments_scratch, v0->d_ctr, s, vec, tc));
+        MB_CUDA(mb::launch_pass2_multi(gt, v0->d_tf, vt, moments_scratch, rgba, v0->d_ctr, s, vec, tc));
+    }
     v0->frame_timed = false;
     for (int32_t i = 0; i < n_vols; ++i) release_stream(vols[i], s);
     return MBOIT_OK;

@@ -7,6 +7,7 @@
 #include <utility>
 
 #include "mboit_common.cuh"
+#include "mboit_multi.h"
 
 namespace mb {
 namespace {
@@ -372,6 +373,7 @@ cudaError_t prepare_kernels() {
     if (e == cudaSuccess) e = prepare_frame_kernels();
     if (e == cudaSuccess) e = prepare_frame_unit_kernels();
     if (e == cudaSuccess) e = prepare_multi_kernels();
+    if (e == cudaSuccess) e = prepare_multi_amr_kernels();
     if (e == cudaSuccess) e = prepare_unit_kernels();
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -1,4 +1,4 @@
-"""Several grid volumes in one frame (mboit_render_frame_multi): one
+"""Several volumes in one frame (mboit_render_frame_multi): one
 persistent launch per pass over the ray tiles of every volume's views.  Each
 view's moments and image must equal, bit for bit, its volume's own
 mboit_render_frame (the per-tile code is the same); the calls' argument
@@ -107,10 +107,42 @@ def test_multi_volume_frame_rejects(pkg):
     cases = [([va, vt], [0], 1),       # another transfer function
              ([va, va], [0], 1),       # a volume listed twice
              ([va, vb], [2], 1),       # view_volume out of range
-             ([va, vm], [0], 4)]       # an octree (MBOIT_ERR_UNSUPPORTED)
+             ([va, vm], [0], 1)]       # a grid and an octree
     for vols, owner, status in cases:
         with pytest.raises(pkg.MboitError) as e:
             pkg.Volume.render_frame_multi(vols, views, owner, mom, col)
         assert e.value.status == status
     for v in (va, vb, vt, vm):
         v.close()
+    # the adaptive step is not batched across volumes
+    ad = dataclasses.replace(amr)
+    ad.adaptive_step = True
+    vad = pkg.Volume(ad)
+    with pytest.raises(pkg.MboitError) as e:
+        pkg.Volume.render_frame_multi([vad], views, [0], mom, col)
+    assert e.value.status == 4
+    vad.close()
+
+
+def _amr_variant(sc, scale, name):
+    v = np.ascontiguousarray(sc.values * np.float32(scale)).astype(np.float32)
+    return dataclasses.replace(sc, name=name, values=v, tf_range=(np.float32(v.min()), np.float32(v.max())))
+
+
+def test_multi_octree_frame_equals_each_volume(pkg):
+    a = scenes.amr_blobs(base=4, max_level=2, width=45, height=38, n_pieces=5, seed=11)
+    b = _amr_variant(scenes.amr_blobs(base=4, max_level=2, width=8, height=8, n_pieces=3, seed=12), 0.8, "amr_b")
+    views = [a.views[0],
+             scenes.perspective_view(a.dims, (-0.5, 0.6, -0.62), 40, 33, fov_deg=40.0),
+             scenes.ortho_view(a.dims, (0.1, 0.2, 0.97), 29, 31)]
+    _check_multi(pkg, [a, b], views, [0, 1, 1])
+
+
+def test_multi_octree_with_holes(pkg):
+    # an octree with holes among the volumes: the checked kernels
+    amr, _ = small.linear_amr()
+    amr.views = [scenes.perspective_view(amr.dims, (0.57, 0.49, 0.66), 30, 24)]
+    holes = dataclasses.replace(amr, name="holes", leaves=amr.leaves[:-3], values=amr.values[:-3],
+                                piece_of_leaf=amr.piece_of_leaf[:-3])
+    views = [amr.views[0], scenes.ortho_view(amr.dims, (0.3, -0.8, 0.5), 27, 21)]
+    _check_multi(pkg, [amr, holes], views, [1, 0])
