@@ -396,6 +396,40 @@ def pin_to_gpu_cpus(device):
         pass
 
 
+def profile_moment_set(args):
+    """Frames of the workload with another moment set and storage (the biases of
+    the precision sweep), for a profiler: autotune, warm-up, timed frames."""
+    import torch
+    import paper_2501_12581_gb300 as pkg
+    mset, stor = (args.moment_set.split(":") + ["f32"])[:2]
+    beta = {"f32": 5e-5, "f16": 2e-3, "bf16": 2e-2}[stor]
+    sc = workload(args.workload)
+    if args.image:
+        for vw in sc.views:
+            vw.width = vw.height = args.image
+    sc.moment_set, sc.storage, sc.moment_bias = mset, stor, beta
+    vol = pkg.Volume(sc)
+    views = sc.views
+    mom, rgba = vol.moments_for(views), pkg.Volume.color_buffer(views)
+    vol.autotune(views, mom, rgba)
+    for _ in range(args.warmup):
+        vol.render_frame(views, mom, rgba)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(args.steps):
+        vol.render_frame(views, mom, rgba)
+    ev1.record()
+    torch.cuda.synchronize()
+    vol.synchronize()
+    st = vol.stats()
+    print(json.dumps({"workload": args.workload, "moments": mset, "storage": stor, "moment_bias": beta,
+                      "image": f"{views[0].width}x{views[0].height}", "samples_per_frame": st["samples_pass1"],
+                      "ms_per_frame": ev0.elapsed_time(ev1) / args.steps, "frame_pass1_ms": st["frame_pass1_ms"],
+                      "frame_pass2_ms": st["frame_pass2_ms"]}))
+    vol.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -417,6 +451,9 @@ def main():
     ap.add_argument("--no-fp64-setup", action="store_true", help="skip the frame with every pixel set up in FP64")
     ap.add_argument("--gear-k", default="8,16,32,64,128", help="piece counts of the gear-teeth stress test")
     ap.add_argument("--heatmap", default="", help="directory for the gear-teeth segments-per-pixel images (PGM)")
+    ap.add_argument("--moment-set", default="", metavar="SET:STORAGE",
+                    help="profiling only: frames of --workload with another moment set (power6:f32, power8:f32, "
+                         "trig6:f16, trig8:bf16, ...); prints their time, not the benchmark line")
     ap.add_argument("--ncu-record", nargs=4, metavar=("CSV", "KERNEL", "SAMPLES", "OUT"),
                     help="write the frame kernel's ncu record for --workload from a raw CSV dump and exit")
     args = ap.parse_args()
@@ -425,6 +462,9 @@ def main():
         print(json.dumps(write_ncu_record(csv_path, kernel, args.workload, int(nsamp), out_path)))
         return
     args.warmup = max(args.warmup, 3)
+    if args.moment_set:
+        profile_moment_set(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
