@@ -623,14 +623,63 @@ __device__ __forceinline__ void march_amr_rows(const AmrD& a, const uint8_t* __r
         store.put(val);
         body.add(val, 1.0f, rows.z[j]);
     };
+    // Without holes or a selection (every point has a leaf): the leaf of a
+    // point and its local coordinates, after a leaf change where its box test
+    // fails.
+    auto locate = [&](float t, float& q0, float& q1, float& q2) {
+        const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
+        q0 = (p0 - lo0) * inv_h;
+        q1 = (p1 - lo1) * inv_h;
+        q2 = (p2 - lo2) * inv_h;
+        if (!(__float_as_uint(q0) < kEdge && __float_as_uint(q1) < kEdge && __float_as_uint(q2) < kEdge)) {
+            const float p[3] = {p0, p1, p2};
+            const int v = unit_of(a, p);
+            const float4 L = __ldg(a.leaf_box + v);
+            lo0 = L.x;
+            lo1 = L.y;
+            lo2 = L.z;
+            inv_h = L.w;
+            blk = a.values + (size_t)v * (NV * NV * NV);
+            q0 = (p0 - lo0) * inv_h;
+            q1 = (p1 - lo1) * inv_h;
+            q2 = (p2 - lo2) * inv_h;
+        }
+        return blk;
+    };
+    auto value = [&](const float* b, float q0, float q1, float q2) {
+        const int cx = (int)q0, cy = (int)q1, cz = (int)q2;
+        const float* __restrict__ c = b + (cz * NV + cy) * NV + cx;
+        return tf_x(g, trilinear8(__ldg(c), __ldg(c + 1), __ldg(c + NV), __ldg(c + NV + 1), __ldg(c + NV * NV),
+                                  __ldg(c + NV * NV + 1), __ldg(c + NV * NV + NV), __ldg(c + NV * NV + NV + 1),
+                                  q0 - (float)cx, q1 - (float)cy, q2 - (float)cz));
+    };
     for (int kw = kmin; kw <= kmax; kw += kDepthRows) {
         rows.fill(kw, g.step, body.wa, body.wb);
         const int ka = max(kw, k0), kz = min(kw + kDepthRows - 1, k1);
         float t = lattice_t(ka, g.step);
         if (ka == kw && kz == kw + kDepthRows - 1) {
             // the lane samples every row of the window: unrolled
+            if constexpr (!kSel) {
+                // two rows at a time: both leaf tests, then both points'
+                // gathers (16 loads in flight together), then the store and
+                // the moments in row order
 #pragma unroll
-            for (int j = 0; j < kDepthRows; ++j, t += g.step) point(t, j);
+                for (int j = 0; j < kDepthRows; j += 2) {
+                    const float tb = t + g.step;
+                    float qa0, qa1, qa2, qb0, qb1, qb2;
+                    const float* ba = locate(t, qa0, qa1, qa2);
+                    const float* bb = locate(tb, qb0, qb1, qb2);
+                    const float va = value(ba, qa0, qa1, qa2), vb = value(bb, qb0, qb1, qb2);
+                    store.put(va);
+                    body.add(va, 1.0f, rows.z[j]);
+                    store.put(vb);
+                    body.add(vb, 1.0f, rows.z[j + 1]);
+                    t = tb + g.step;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kDepthRows; ++j, t += g.step) point(t, j);
+            }
         } else {
             for (int k = ka; k <= kz; ++k, t += g.step) point(t, k - kw);
         }
