@@ -250,7 +250,29 @@ __device__ __forceinline__ bool march_fused(const GridD& g, const uint8_t* __res
             // loop runs on t itself
             const float tz = lattice_t(kz, g.step);
             store.seek(ka);
-            for (float t = lattice_t(ka, g.step); t <= tz; t += g.step) {
+            float t0 = lattice_t(ka, g.step);
+            if constexpr (!kSel) {
+                // two points at a time: both positions, then both points' 16
+                // window reads, then the store and the body in order
+                auto window_value = [&](float t) {
+                    const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
+                    const int ix = (int)p0, iy = (int)p1, iz = (int)p2;
+                    const float* c = wbase + iz * Cfg::Plane + iy * Cfg::Pitch + ix;
+                    return tf_x(g, trilinear8(c[0], c[1], c[Cfg::Pitch], c[Cfg::Pitch + 1], c[Cfg::Plane],
+                                              c[Cfg::Plane + 1], c[Cfg::Plane + Cfg::Pitch],
+                                              c[Cfg::Plane + Cfg::Pitch + 1], p0 - (float)ix, p1 - (float)iy,
+                                              p2 - (float)iz));
+                };
+                for (; t0 + g.step <= tz; t0 += 2.0f * g.step) {
+                    const float tb = t0 + g.step;
+                    const float xa = window_value(t0), xb = window_value(tb);
+                    store.put(xa);
+                    body(t0, xa);
+                    store.put(xb);
+                    body(tb, xb);
+                }
+            }
+            for (float t = t0; t <= tz; t += g.step) {
                 const float p0 = ffma(t, d[0], o[0]), p1 = ffma(t, d[1], o[1]), p2 = ffma(t, d[2], o[2]);
                 const int ix = (int)p0, iy = (int)p1, iz = (int)p2;
                 if (kSel) {
