@@ -29,7 +29,8 @@
  *     stream).  Render calls are asynchronous on that stream; errors raised
  *     inside kernels (a wait limit or an index check) are reported by
  *     mboit_synchronize().  One volume serves one stream at a time: a
- *     render call (passes, frame, host frame, multi-volume frame, sort-last)
+ *     render call (passes, frame, host frame, multi-volume frame, sort-last,
+ *     autotuner)
  *     on another stream while work of the volume's previous call may still
  *     run returns MBOIT_ERR_STATE and enqueues nothing (an event recorded
  *     after each call's work tells; calls made while a stream is being

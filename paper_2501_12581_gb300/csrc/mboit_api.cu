@@ -1726,6 +1726,7 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
     if ((st = select_pieces(v, nullptr, 0, list, &mask)) != MBOIT_OK) return st;
     const bool grid = v->kind == MBOIT_GRID;  // octrees and meshes have one window configuration
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((st = claim_stream(v, s)) != MBOIT_OK) return st;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     MB_CUDA(cudaEventCreate(&e0));
     cudaError_t ce = cudaEventCreate(&e1);
@@ -1866,6 +1867,7 @@ mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_v
         std::lock_guard<std::mutex> tl(g_tuned_mu);
         g_tuned[key] = Tuned{best[0], best[1], best[2], launches, order};
     }
+    release_stream(v, s);
     drop_graphs(v);
     if (chosen) {
         chosen[0] = best[0];
