@@ -126,7 +126,7 @@ __device__ __forceinline__ bool tma_window(TmaWin& tw, float* win, int x, int y,
                 "l"(reinterpret_cast<uint64_t>(tw.map)), "r"(x), "r"(y), "r"(z), "r"(bar)
                 : "memory");
     }
-    // one verdict for the warp: lanes that saw the phase complete and a lane
+    // one outcome for the warp: lanes that saw the phase complete and a lane
     // that gave up must not part (the caller returns on false)
     const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, tw.phase));
     if (!ok) {
