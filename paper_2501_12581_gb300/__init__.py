@@ -514,6 +514,32 @@ class Volume:
         return mboit_get_stats(self.handle)
 
 
+def save_moments(path, moments, views, moment_set=MBOIT_POWER4, storage=MBOIT_STORE_F32, n_slots=1):
+    """Writes a moment buffer (as render_moments or render_frame leave it) to
+    `path` (.npz): its raw 32-bit words and the views' sizes and the moment
+    format, so that pass 2 (reconstruct_blend) can be replayed from it later."""
+    import numpy as np
+    import torch
+    words = moments.detach().cpu().contiguous().view(-1)
+    sizes = np.array([[v.width, v.height] for v in views], np.int32)
+    expect = sum(mboit_moment_image_bytes(int(w), int(h), moment_set, storage) for w, h in sizes) * n_slots
+    if words.numel() * 4 < expect:
+        raise ValueError(f"the buffer holds {words.numel() * 4} bytes, the views need {expect}")
+    np.savez(path, words=words.view(torch.int32).numpy(), sizes=sizes,
+             fmt=np.array([moment_set, storage, n_slots], np.int32))
+
+
+def load_moments(path, device="cuda"):
+    """Reads save_moments' file: (buffer as float32 words on `device`, view
+    sizes [(width, height)], moment set, storage, slots)."""
+    import numpy as np
+    import torch
+    z = np.load(path)
+    buf = torch.from_numpy(z["words"]).view(torch.float32).to(device)
+    ms, st, slots = (int(x) for x in z["fmt"])
+    return buf, [tuple(int(a) for a in r) for r in z["sizes"]], ms, st, slots
+
+
 def torch_cat_moments(slab, P, npx, nm=5):
     """One power-moment slab (nm * P floats: b0 plane, float4 plane of b1..b4,
     then a float2 plane (nm = 7) or float4 plane (nm = 9)) -> [npx][nm]."""

@@ -5,6 +5,7 @@
 // the batched frame, and error reporting.  Every step of the render runs in
 // the kernels of mboit_grid.cu, mboit_units.cu and mboit_kernels.cu.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <functional>
@@ -51,6 +52,15 @@ struct DeviceGuard {
 };
 
 bool finite3(const float* a) { return std::isfinite(a[0]) && std::isfinite(a[1]) && std::isfinite(a[2]); }
+
+// An NVTX range around an entry point, so that profilers show each call's
+// span beside its kernels (no cost without an attached tool).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 struct GraphEntry {
     std::vector<char> key;
@@ -815,6 +825,7 @@ size_t mboit_moment_image_bytes(int32_t width, int32_t height, int32_t moment_se
 
 mboit_status mboit_create_volume(const mboit_volume_desc* d, mboit_volume* out) {
     g_err.clear();
+    Range nvtx("mboit_create_volume");
     if (!d || !out) return fail(MBOIT_ERR_INVALID_ARG, "desc and out must be non-NULL");
     if (d->kind != MBOIT_GRID && d->kind != MBOIT_AMR && d->kind != MBOIT_TET)
         return fail(MBOIT_ERR_UNSUPPORTED, "unknown volume kind");
@@ -1162,6 +1173,7 @@ mboit_status mboit_add_piece(mboit_volume v, const int32_t* ids, int64_t n, int3
 mboit_status mboit_render_moments(mboit_volume v, const mboit_view* views, int32_t n_views, const int32_t* pieces,
                                   int32_t n_pieces, int32_t mode, void* moments, void* stream) {
     g_err.clear();
+    Range nvtx("mboit_render_moments");
     mboit_status st = check_volume(v);
     if (st != MBOIT_OK) return st;
     if (mode != MBOIT_MOMENTS_PER_PIECE && mode != MBOIT_MOMENTS_REDUCED) return fail(MBOIT_ERR_INVALID_ARG, "unknown mode");
@@ -1199,6 +1211,7 @@ mboit_status mboit_reconstruct_blend(mboit_volume v, const mboit_view* views, in
                                      int32_t n_pieces, const void* global_moments, int32_t mode, float* color,
                                      void* stream) {
     g_err.clear();
+    Range nvtx("mboit_reconstruct_blend");
     mboit_status st = check_volume(v);
     if (st != MBOIT_OK) return st;
     if (mode != MBOIT_COLOR_PER_PIECE && mode != MBOIT_COLOR_REDUCED && mode != MBOIT_COLOR_RESOLVED)
@@ -1242,6 +1255,7 @@ mboit_status mboit_composite(mboit_volume v, int32_t op, int32_t width, int32_t 
                              int32_t n_inputs, const void* in, void* out, const void* global_moments, const float* bg,
                              void* stream) {
     g_err.clear();
+    Range nvtx("mboit_composite");
     if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
     if (op != MBOIT_OP_MOMENTS_SUM && op != MBOIT_OP_COLOR_SUM_RESOLVE) return fail(MBOIT_ERR_INVALID_ARG, "unknown op");
     if (n_inputs < 1) return fail(MBOIT_ERR_INVALID_ARG, "n_inputs must be >= 1");
@@ -1273,6 +1287,7 @@ mboit_status mboit_composite(mboit_volume v, int32_t op, int32_t width, int32_t 
 mboit_status mboit_render_frame(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch,
                                 float* rgba, void* stream) {
     g_err.clear();
+    Range nvtx("mboit_render_frame");
     mboit_status st = check_volume(v);
     if (st != MBOIT_OK) return st;
     if (!moments_scratch || !rgba) return fail(MBOIT_ERR_INVALID_ARG, "moments_scratch and rgba must be non-NULL");
@@ -1340,6 +1355,7 @@ mboit_status mboit_render_frame_multi(const mboit_volume* vols, int32_t n_vols, 
                                       const int32_t* view_volume, int32_t n_views, void* moments_scratch, float* rgba,
                                       void* stream) {
     g_err.clear();
+    Range nvtx("mboit_render_frame_multi");
     if (!vols || !view_volume || !moments_scratch || !rgba)
         return fail(MBOIT_ERR_INVALID_ARG, "vols, view_volume, moments_scratch and rgba must be non-NULL");
     if (n_vols < 1 || n_vols > mb::kMaxVolumes)
@@ -1433,6 +1449,7 @@ mboit_status mboit_render_frame_multi(const mboit_volume* vols, int32_t n_vols, 
 mboit_status mboit_render_frame_host(mboit_volume v, const float* field_host, const mboit_view* views, int32_t n_views,
                                      void* moments_scratch, float* rgba_device, float* rgba_host, void* stream) {
     g_err.clear();
+    Range nvtx("mboit_render_frame_host");
     mboit_status st = check_volume(v);
     if (st != MBOIT_OK) return st;
     if (!field_host || !rgba_host || !rgba_device) return fail(MBOIT_ERR_INVALID_ARG, "NULL buffer");
@@ -1465,6 +1482,7 @@ mboit_status mboit_render_frame_host(mboit_volume v, const float* field_host, co
 
 mboit_status mboit_synchronize(mboit_volume v, void* stream) {
     g_err.clear();
+    Range nvtx("mboit_synchronize");
     if (!v) return fail(MBOIT_ERR_INVALID_ARG, "volume is NULL");
     DeviceGuard dg(v->device);
     MB_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
@@ -1548,6 +1566,7 @@ mboit_status mboit_get_stats(mboit_volume v, mboit_stats* out) {
 mboit_status mboit_render_sortlast(mboit_volume v, const mboit_view* views, int32_t n_views, float* rgba,
                                    int32_t* segments_per_pixel, void* stream) {
     g_err.clear();
+    Range nvtx("mboit_render_sortlast");
     mboit_status st = check_volume(v);
     if (st != MBOIT_OK) return st;
     if (!rgba) return fail(MBOIT_ERR_INVALID_ARG, "rgba is NULL");
@@ -1694,6 +1713,7 @@ void mboit_clear_tuning_cache(void) {
 mboit_status mboit_autotune(mboit_volume v, const mboit_view* views, int32_t n_views, void* moments_scratch, float* rgba,
                             void* stream, int32_t* chosen) {
     g_err.clear();
+    Range nvtx("mboit_autotune");
     mboit_status st = check_volume(v);
     if (st != MBOIT_OK) return st;
     if (!moments_scratch || !rgba) return fail(MBOIT_ERR_INVALID_ARG, "moments_scratch and rgba must be non-NULL");

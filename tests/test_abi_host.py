@@ -258,3 +258,21 @@ def test_split_cells_matches_oracle_and_rejects_bad_cells(lib):
                          ([0, 1, 2, 3, -1, -1] * 3, [4] * 3)):  # one face in three tets
         with pytest.raises(pkg.MboitError):
             split(cells, types)
+
+
+def test_save_and_load_moments_round_trip(lib, tmp_path):
+    """Moment images dumped for a later replay of pass 2 come back with the
+    same bits, view sizes and format; a buffer too small for the views is
+    refused."""
+    import torch
+    views = [scenes.ortho_view((16, 16, 16), (0.3, 0.4, 0.86), 7, 5),
+             scenes.ortho_view((16, 16, 16), (0.3, 0.4, 0.86), 4, 9)]
+    n = sum(pkg.mboit_moment_image_bytes(v.width, v.height) for v in views) // 4
+    buf = torch.from_numpy(np.random.default_rng(3).standard_normal(n).astype(np.float32))
+    path = tmp_path / "moments.npz"
+    pkg.save_moments(str(path), buf, views)
+    got, sizes, ms, st, slots = pkg.load_moments(str(path), device="cpu")
+    assert torch.equal(got.view(torch.int32), buf.view(torch.int32))
+    assert sizes == [(7, 5), (4, 9)] and (ms, st, slots) == (pkg.MBOIT_POWER4, pkg.MBOIT_STORE_F32, 1)
+    with pytest.raises(ValueError):
+        pkg.save_moments(str(tmp_path / "short.npz"), buf[:10], views)
