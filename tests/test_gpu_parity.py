@@ -362,3 +362,22 @@ def test_error_paths(pkg):
         pkg.mboit_render_moments(h, [view], mom)
     assert e.value.status == 5
     pkg.mboit_destroy_volume(h)
+
+
+def test_replay_pass2_from_saved_moments(pkg, tmp_path):
+    """Pass 2 replayed from moments dumped to a file gives the frame's image."""
+    import torch
+    sc = scenes.blobs64(width=40, height=32)
+    vol = pkg.Volume(sc)
+    views = sc.views
+    mom, col = pkg.Volume.moment_buffer(views), pkg.Volume.color_buffer(views)
+    vol.render_frame(views, mom, col)
+    vol.synchronize()
+    pkg.save_moments(str(tmp_path / "m.npz"), mom, views)
+    buf, sizes, ms, st, slots = pkg.load_moments(str(tmp_path / "m.npz"))
+    assert sizes == [(v.width, v.height) for v in views] and slots == 1
+    col2 = pkg.Volume.color_buffer(views)
+    vol.reconstruct_blend(views, buf, col2)
+    vol.synchronize()
+    assert torch.equal(col, col2)
+    vol.close()
