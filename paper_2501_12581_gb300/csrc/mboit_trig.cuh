@@ -121,6 +121,22 @@ MB_HD void cubic3(float a, float b, float c, float r[3]) {
     }
 }
 
+// The largest real root of the monic cubic s^3 + a s^2 + b s + c whose roots
+// are all real: Viete's root of the largest cosine (th in [0, pi/3]), then one
+// Newton step.
+MB_HD float cubic3_max(float a, float b, float c) {
+    const float a3 = a * (1.0f / 3.0f);
+    const float p = ffma(-a, a3, b);
+    const float q = ffma(ffma(2.0f * a3, a3, -b), a3, c);
+    const float pm = fmin_(p, -1e-30f);
+    const float m = 2.0f * fsqrt_fast(-pm * (1.0f / 3.0f));
+    const float arg = fclamp(fdiv_fast(3.0f * q, pm * m), -1.0f, 1.0f);
+    const float s = ffma(m, fcos(acosf(arg) * (1.0f / 3.0f)), -a3);
+    const float f = ffma(ffma(s + a, s, b), s, c);
+    const float df = ffma(ffma(3.0f, s, 2.0f * a), s, b);
+    return df != 0.0f ? s - fdiv_fast(f, df) : s;
+}
+
 // Real roots of the monic quartic s^4 + a s^3 + b s^2 + c s + d whose roots
 // are all real (Ferrari: resolvent cubic, two quadratics), then Newton steps.
 MB_HD void quartic4(float a, float b, float c, float d, float r[4]) {
@@ -139,9 +155,7 @@ MB_HD void quartic4(float a, float b, float c, float d, float r[4]) {
         y[0] = -y1; y[1] = -y2; y[2] = y2; y[3] = y1;
     } else {
         // m^3 + p m^2 + (p^2/4 - r) m - q^2/8 = 0, largest root (positive)
-        float mr[3];
-        cubic3(p, ffma(0.25f * p, p, -rr), -0.125f * q * q, mr);
-        const float m = fmax_(fmax_(mr[0], mr[1]), fmax_(mr[2], 1e-30f));
+        const float m = fmax_(cubic3_max(p, ffma(0.25f * p, p, -rr), -0.125f * q * q), 1e-30f);
         const float sq = fsqrt_fast(2.0f * m);
         const float h = 0.5f * p + m, g = fdiv_fast(q, 2.0f * sq);
         // y^2 - sq y + (h + g) = 0 and y^2 + sq y + (h - g) = 0
