@@ -166,7 +166,7 @@ MB_HD void quartic4(float a, float b, float c, float d, float r[4]) {
     }
     for (int i = 0; i < 4; ++i) {
         float s = y[i] - a4;
-        for (int it = 0; it < 2; ++it) {
+        for (int it = 0; it < 1; ++it) {
             const float f = ffma(ffma(ffma(s + a, s, b), s, c), s, d);
             const float df = ffma(ffma(ffma(4.0f, s, 3.0f * a), s, 2.0f * b), s, c);
             if (df != 0.0f) s = s - fdiv_fast(f, df);
