@@ -449,6 +449,7 @@ def main():
     ap.add_argument("--no-gear", action="store_true", help="skip the gear-teeth stress test")
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-volume frame")
     ap.add_argument("--no-fp64-setup", action="store_true", help="skip the frame with every pixel set up in FP64")
+    ap.add_argument("--no-orbit", action="store_true", help="skip the four-camera orbits (octree and 512^3 grid)")
     ap.add_argument("--gear-k", default="8,16,32,64,128", help="piece counts of the gear-teeth stress test")
     ap.add_argument("--heatmap", default="", help="directory for the gear-teeth segments-per-pixel images (PGM)")
     ap.add_argument("--moment-set", default="", metavar="SET:STORAGE",
@@ -659,6 +660,34 @@ def main():
         torch.cuda.empty_cache()
 
     # the 512^3 regular grid (64 pieces, 2048x2048), the 72-piece tetrahedral
+    # A volume seen from four cameras on an orbit about its z axis (the
+    # benchmark camera's direction (0.57, 0.49, 0.66) turned by 0, 90, 180 and
+    # 270 degrees; same elevation, distance and field of view), with the tuning
+    # the volume already has: one frame graph per camera; the frame rate's
+    # spread over the orbit.
+    def orbit_of(ovol, dims, width, height, om, orgba):
+        import scenes as _scenes
+        w0 = (0.57, 0.49, 0.66)
+        cams, rates, mss, ns = [], [], [], []
+        for deg in (0, 90, 180, 270):
+            c_, s_ = np.cos(np.radians(deg)), np.sin(np.radians(deg))
+            wd = (c_ * w0[0] - s_ * w0[1], s_ * w0[0] + c_ * w0[1], w0[2])
+            ov = [_scenes.perspective_view(dims, wd, width, height)]
+            of = lambda: ovol.render_frame(ov, om, orgba)  # noqa: E731,B023
+            for _ in range(3):
+                of()
+            ms_o = timed(of, max(5, args.steps // 3))
+            of()
+            ovol.synchronize()
+            so = ovol.stats()["samples_pass1"]
+            cams.append(deg)
+            mss.append(ms_o)
+            ns.append(so)
+            rates.append(so / (ms_o * 1e-3) / 1e9)
+        return {"azimuth_deg": cams, "ms_per_frame": mss, "samples_per_frame": ns, "gsamples_per_s": rates,
+                "mean_gsamples_per_s": float(np.mean(rates)), "min_gsamples_per_s": float(min(rates)),
+                "max_gsamples_per_s": float(max(rates)), "mean_ms_per_frame": float(np.mean(mss))}
+
     # (1024x1024) and mixed-cell workloads as further lines of results
     def unit_block(name):
         usc = workload(name)
@@ -705,6 +734,10 @@ def main():
                  "samples_per_frame": su, "ms_per_frame": ms_u,
                  "gsamples_per_s": su / (ms_u * 1e-3) / 1e9, "per_piece_fp32_ms_per_frame": ms_up,
                  "speedup_of_batched": ms_up / ms_u, "sortlast_gpu": usl}
+        if name == "blobs512" and not args.no_orbit:
+            out_u["orbit_4_cameras"] = orbit_of(uvol, usc.dims, uw, uh, umom, urgba)
+            uframe()
+            uvol.synchronize()
         upix = sample_pixels(uw, uh, 64, 32)
         if rank == 0 and not args.no_cpu_baseline:
             _orc = __import__("oracle")
@@ -781,6 +814,10 @@ def main():
         v64.close()
         del v64
         torch.cuda.empty_cache()
+
+    orbit = orbit_of(vol, sc.dims, v.width, v.height, mom, rgba) if headline and not args.no_orbit else None
+    vol.render_frame(views, mom, rgba)
+    vol.synchronize()
 
     # several independent volumes in one persistent launch per pass: 8 grids
     # of 64^3 (the blobs64 field flipped and scaled per volume, one transfer
@@ -1002,6 +1039,7 @@ def main():
            "gear_teeth_stress": gear,
            "multi_volume_8_grids": multi,
            "fp64_setup_every_pixel": fp64_setup,
+           "orbit_4_cameras": orbit,
            "precision_sweep_amr_2048": sweep,
            "quality": quality, "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
            "gpu_launches": launches * args.steps, "clocks": clk.summary()}
