@@ -548,7 +548,13 @@ __device__ __forceinline__ void march_unit(const TetT<kNarrow>& m, const uint8_t
         const bool found = f == -1 || tet_search<kNarrow>(m, w, q, D);
         float val = __int_as_float(0x7fc00000);
         if (found && (!kSel || __ldg(sel + w.T))) {
-            val = tf_x(g, tet_value(D, w.v));
+            // the corner values (the .w words) read again here rather than
+            // kept live through the walk, which only tests x, y, z: fewer
+            // spilled registers in the loop (the same bits, so the same value)
+            const int* cw = reinterpret_cast<const int*>(m.corners + 4 * (size_t)w.T);
+            const int4 vw[4] = {make_int4(0, 0, 0, __ldg(cw + 3)), make_int4(0, 0, 0, __ldg(cw + 7)),
+                                make_int4(0, 0, 0, __ldg(cw + 11)), make_int4(0, 0, 0, __ldg(cw + 15))};
+            val = tf_x(g, tet_value(D, vw));
             body(t, val);
         }
         store.put(val);
