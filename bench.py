@@ -54,6 +54,35 @@ CACHE_BYTES_PER_SAMPLE = 4
 # FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x
 # 2 FLOP x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# MUFU (special-function) results per second: 152 SMs x 16 per clock x 2.070 GHz;
+# per owned sample pass 1 takes 1 (log2 of the depth), pass 2 from the cache 4
+# (log2, rcp, rsqrt, exp2), the one-launch frame both.
+MUFU_PEAK_TOPS = 152 * 16 * 2.070e9 / 1e12
+MUFU_PASS1, MUFU_PASS2 = 1, 4
+
+
+def roofs_of(samples, launch_ms, flop, mufu, traffic, hbm_gbs, ncu_rec):
+    """The four roofs of one kernel launch (FP32 ALU, MUFU, HBM, L2) as
+    fractions of their peaks, and the binding one (the largest).  ALU and MUFU
+    from the algorithmic counts per owned sample and the launch time; HBM from
+    the ncu DRAM bytes of the launch (None without a record) and the measured
+    copy rate; L2 (and the issue slots, for reference) from the ncu record's
+    percentages of peak."""
+    sec = launch_ms * 1e-3
+    r = {"alu": flop * samples / sec / 1e12 / FP32_PEAK_TFLOPS,
+         "mufu": mufu * samples / sec / 1e12 / MUFU_PEAK_TOPS}
+    r["hbm"] = traffic / sec / 1e9 / hbm_gbs if (traffic is not None and hbm_gbs) else None
+    r["l2"] = ncu_rec["l2_throughput_pct"] / 100.0 if ncu_rec and "l2_throughput_pct" in ncu_rec else None
+    known = {k: v for k, v in r.items() if v is not None}
+    b = max(known, key=known.get)
+    out = {f"{k}_frac": v for k, v in r.items()}
+    out.update({"binding": b, "binding_frac": known[b],
+                "issue_active_frac_ncu": ncu_rec["issue_active_pct"] / 100.0
+                if ncu_rec and "issue_active_pct" in ncu_rec else None,
+                "peaks": {"alu_tflops": FP32_PEAK_TFLOPS, "mufu_tops": MUFU_PEAK_TOPS, "hbm_gbs": hbm_gbs,
+                          "sources": "ALU and MUFU derived from unit counts at 2.07 GHz; HBM measured copy rate; "
+                                     "L2 as ncu's percentage of its peak"}})
+    return out
 CSRC = os.path.join(ROOT, "paper_2501_12581_gb300", "csrc")
 # committed ncu records of the frame kernels (DRAM bytes per launch and the
 # binding units' activity), one file per (kernel, workload), valid while the
@@ -571,6 +600,7 @@ def main():
         frame_kernels = {"frame_one_launch": k1s}
         dom_key = "k_frame_unit" if unit_scene else "k_frame_fused"
         dom, dflop = k1s, flop1 + FLOP_PASS2_FRAME
+        dmufu = MUFU_PASS1 + MUFU_PASS2
         dname = (dom_key + ", one launch per frame (per ray tile: march + moments + sample store, "
                  "then reconstruct + blend + resolve)")
     else:
@@ -582,6 +612,7 @@ def main():
                              FLOP_PASS2_FRAME) if p2 >= p1 else \
             (k1s, kname.format(1) + ", frame form (march + moments + sample store)", flop1)
         dom_key = kname.format(2 if p2 >= p1 else 1) + "_frame"
+        dmufu = MUFU_PASS2 if p2 >= p1 else MUFU_PASS1
     rec_traffic = measured_traffic(dom_key, args.workload)
     ncu_rec = measured_ncu(dom_key, args.workload)
     # a record taken on a reduced view scales to this launch by its owned samples
@@ -603,6 +634,7 @@ def main():
     if traffic is not None and hbm:
         roofline["hbm"] = {"traffic_gbs": traffic / (dom["launch_ms"] * 1e-3) / 1e9, "peak_gbs": hbm,
                            "frac_of_measured": traffic / (dom["launch_ms"] * 1e-3) / 1e9 / hbm}
+    roofline["roofs"] = roofs_of(samples, dom["launch_ms"], dflop, dmufu, traffic, hbm, ncu_rec)
 
     # end to end through the host API: field upload, frame, image download
     host_values = (sc.values if hasattr(sc, "leaves") else sc.verts[:, 3] if (hasattr(sc, "tets") or hasattr(sc, "cells"))

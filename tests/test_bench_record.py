@@ -55,3 +55,25 @@ def test_ncu_record_round_trip(tmp_path):
         assert bench.measured_ncu("k_other", "blobs64") is None
     finally:
         bench.NCU_DIR = old
+
+
+def test_roofs_pick_the_largest_fraction():
+    """The four roofs of a launch: ALU and MUFU from the algorithmic counts
+    and the launch time (here chosen so that ALU is at 25 % and MUFU at 50 %
+    of their peaks), HBM from the DRAM bytes at 10 % of the copy rate, L2 from
+    the record's percentage; the binding roof is the largest of them, and a
+    roof without data is left out of the choice."""
+    samples, ms = 1.0e9, 10.0
+    flop = 0.25 * bench.FP32_PEAK_TFLOPS * 1e12 * ms * 1e-3 / samples
+    mufu = 0.5 * bench.MUFU_PEAK_TOPS * 1e12 * ms * 1e-3 / samples
+    hbm_gbs = 6000.0
+    traffic = 0.1 * hbm_gbs * 1e9 * ms * 1e-3
+    rec = {"l2_throughput_pct": 30.0, "issue_active_pct": 71.0}
+    r = bench.roofs_of(samples, ms, flop, mufu, traffic, hbm_gbs, rec)
+    assert r["alu_frac"] == pytest.approx(0.25) and r["mufu_frac"] == pytest.approx(0.5)
+    assert r["hbm_frac"] == pytest.approx(0.1) and r["l2_frac"] == pytest.approx(0.3)
+    assert r["binding"] == "mufu" and r["binding_frac"] == pytest.approx(0.5)
+    assert r["issue_active_frac_ncu"] == pytest.approx(0.71)
+    bare = bench.roofs_of(samples, ms, 4 * flop, mufu, None, hbm_gbs, None)
+    assert bare["hbm_frac"] is None and bare["l2_frac"] is None
+    assert bare["binding"] == "alu" and bare["binding_frac"] == pytest.approx(1.0)
